@@ -1,0 +1,333 @@
+"""Oracle for the entropy-variable hybridized DG local problem and Newton step.
+
+Follows Sec. 3.2 (Euler, Eqs. hDG1-hDG2) and Sec. 3.3 (Navier-Stokes, Eqs.
+hDG_NS0-hDG_NS2) on periodic meshes (no boundary term), with
+  * inviscid flux Eq. numericalFlux, sigma = sigma_SLF of Eq. sLxF at v* = vhat
+    (the choice of Sec. 5),
+  * viscous flux Eq. numericalFluxNS_2, G(vhat, q) . n (the choice of Sec. 5),
+  * time term (d u(v_h)/dt, w) discretised by BDF: mass_coef (u(v_h), w) - hist,
+    hist = sum_j c_j (u(v_h^{n-j}), w) (BDF1 / BDF2; BDF0 = steady).
+
+The local Newton system is the plain definition: the dense Jacobian of the local
+residuals R_l = (R_q, R_v) and of the element's trace residual R_t, taken by
+complex step (exact to rounding, no subtractive cancellation), then
+  S = D - C A^{-1} B,  g = R_t - C A^{-1} R_l   (static condensation, Sec. 3.2-3.3)
+with A^{-1} applied by LU with partial pivoting (numpy.linalg.solve). The assembled
+trace system sum_e P_e^T S_e P_e dvhat = -sum_e P_e^T g_e is solved densely (or by a
+sparse direct solve), and the interior update is dx_e = -A^{-1}(R_l + B P_e dvhat).
+
+Interior unknown order: [q (node, component, direction); v (node, component)];
+trace order: [local face, face node, component].
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from . import physics as ph
+from .mesh import Mesh
+
+CSTEP = 1e-30
+
+
+@dataclass
+class ElementTables:
+    W: np.ndarray          # [ng] volume weights * |det J|
+    phi: np.ndarray        # [ng, Np]
+    gphi: np.ndarray       # [ng, Np, d] physical gradients
+    Wf: list               # per face [ngf]
+    phif: list             # per face [ngf, Np]
+    psi: list              # per face [ngf, Nf] trace basis = element basis restricted to the face
+    nrm: list              # per face [d] outward unit normal
+
+
+class Problem:
+    """A mesh + physics + the element tables the residual needs."""
+
+    def __init__(self, mesh: Mesh, phys: ph.Physics):
+        self.mesh, self.phys = mesh, phys
+        ref = mesh.ref
+        self.d, self.m = mesh.dim, mesh.dim + 2
+        self.Np, self.Nf, self.nF = ref.Np, ref.Nf, ref.nF
+        self.viscous = phys.viscous
+        self.n_i = self.Np * self.m * (1 + (self.d if self.viscous else 0))
+        self.n_t = self.nF * self.Nf * self.m
+        self._phi = ref.phi(ref.qp)
+        self._dphi = ref.dphi(ref.qp)
+        self._phif = [ref.phi(x) for x in ref.fqp_ref]
+        self._cache = {}
+
+    def tables(self, e: int) -> ElementTables:
+        t = self._cache.get(e)
+        if t is not None:
+            return t
+        mesh, ref = self.mesh, self.mesh.ref
+        W = ref.qw * abs(mesh.detJ[e])
+        gphi = np.einsum("gar,rj->gaj", self._dphi, mesh.Jinv[e])
+        Wf, phif, psi, nrm = [], [], [], []
+        for f in range(ref.nF):
+            Wf.append(ref.fqw * mesh.face_jac[e, f])
+            phif.append(self._phif[f])
+            psi.append(self._phif[f][:, ref.face_nodes[f]])
+            nrm.append(mesh.normal[e, f])
+        t = ElementTables(W, self._phi, gphi, Wf, phif, psi, nrm)
+        if len(self._cache) < 64:
+            self._cache[e] = t
+        return t
+
+    # -- gather / scatter between global trace and element-local trace ------------------
+    def gather_trace(self, Vhat, e):
+        mesh = self.mesh
+        return Vhat[mesh.face_of[e][:, None], mesh.fnode_map[e]]          # [nF, Nf, m]
+
+    def trace_index(self, e):
+        """Global flat indices of the element's local trace unknowns (f, c, i)."""
+        mesh = self.mesh
+        base = (mesh.face_of[e][:, None] * self.Nf + mesh.fnode_map[e]) * self.m
+        return (base[:, :, None] + np.arange(self.m)).ravel()
+
+    @property
+    def n_trace(self):
+        return self.mesh.nFaces * self.Nf * self.m
+
+    # -- residuals ----------------------------------------------------------------------
+    def element_residual(self, e, Q, V, Vh, mass_coef=0.0, hist_w=None):
+        """Local residuals for a batch [B, ...] of states of element e.
+
+        Q [B, Np, m, d] (None for Euler), V [B, Np, m], Vh [B, nF, Nf, m].
+        Returns (Rq [B, Np, m, d] or None, Rv [B, Np, m], Rt [B, nF, Nf, m])."""
+        T = self.tables(e)
+        g = self.phys.gamma
+        v = np.einsum("ga,bam->bgm", T.phi, V)
+        u = ph.u_of_v(v, g)
+        flux = ph.inviscid_flux_v(v, g)
+        Rq = None
+        if self.viscous:
+            q = np.einsum("ga,bamk->bgmk", T.phi, Q)
+            flux = flux + ph.viscous_flux(v, q, self.phys)
+            # Eq. hDG_NS0: (q, r) + (v, div r) - <vhat, r.n>
+            Rq = (np.einsum("g,ga,bgmk->bamk", T.W, T.phi, q)
+                  + np.einsum("g,gak,bgm->bamk", T.W, T.gphi, v))
+        # Eq. hDG1 / hDG_NS1: (du/dt, w) - (F + G, grad w) + <fhat + ghat, w>
+        Rv = -np.einsum("g,gaj,bgmj->bam", T.W, T.gphi, flux)
+        if mass_coef != 0.0:
+            Rv = Rv + mass_coef * np.einsum("g,ga,bgm->bam", T.W, T.phi, u)
+        if hist_w is not None:
+            Rv = Rv - hist_w
+        Rt = np.zeros(Vh.shape, dtype=np.result_type(V, Vh))
+        for f in range(self.nF):
+            vf = np.einsum("ga,bam->bgm", T.phif[f], V)
+            vhf = np.einsum("gc,bcm->bgm", T.psi[f], Vh[:, f])
+            n = T.nrm[f]
+            fh = ph.numerical_flux_inviscid(vhf, vf, n, g)
+            if self.viscous:
+                qf = np.einsum("ga,bamk->bgmk", T.phif[f], Q)
+                fh = fh + np.einsum("bgmj,j->bgm", ph.viscous_flux(vhf, qf, self.phys), n)
+                Rq = Rq - np.einsum("g,ga,bgm,k->bamk", T.Wf[f], T.phif[f], vhf, n)
+            Rv = Rv + np.einsum("g,ga,bgm->bam", T.Wf[f], T.phif[f], fh)
+            # Eq. hDG2 / hDG_NS2: element contribution <fhat + ghat, mu>
+            Rt[:, f] = np.einsum("g,gc,bgm->bcm", T.Wf[f], T.psi[f], fh)
+        return Rq, Rv, Rt
+
+    def _pack_l(self, Rq, Rv):
+        B = Rv.shape[0]
+        if self.viscous:
+            return np.concatenate([Rq.reshape(B, -1), Rv.reshape(B, -1)], axis=1)
+        return Rv.reshape(B, -1)
+
+    def _unpack_x(self, x):
+        B = x.shape[0]
+        if self.viscous:
+            nq = self.Np * self.m * self.d
+            return (x[:, :nq].reshape(B, self.Np, self.m, self.d),
+                    x[:, nq:].reshape(B, self.Np, self.m))
+        return None, x.reshape(B, self.Np, self.m)
+
+    def local_residual(self, e, Q, V, Vh, mass_coef=0.0, hist_w=None):
+        """Real residuals (R_l [n_i], R_t [n_t]) of element e."""
+        Qb = None if Q is None else Q[None]
+        Rq, Rv, Rt = self.element_residual(e, Qb, V[None], Vh[None], mass_coef, hist_w)
+        return self._pack_l(Rq, Rv)[0], Rt.reshape(-1)
+
+    def local_jacobian(self, e, Q, V, Vh, mass_coef=0.0, hist_w=None):
+        """Dense blocks A, B, C, D of d(R_l, R_t)/d(x, vhat) by complex step."""
+        ni, nt = self.n_i, self.n_t
+        N = ni + nt
+        x0 = V.reshape(-1) if Q is None else np.concatenate([Q.reshape(-1), V.reshape(-1)])
+        y0 = Vh.reshape(-1)
+        X = np.tile(x0.astype(np.complex128), (N, 1))
+        Y = np.tile(y0.astype(np.complex128), (N, 1))
+        X[np.arange(ni), np.arange(ni)] += 1j * CSTEP
+        Y[ni + np.arange(nt), np.arange(nt)] += 1j * CSTEP
+        Qb, Vb = self._unpack_x(X)
+        Rq, Rv, Rt = self.element_residual(e, Qb, Vb, Y.reshape((N,) + Vh.shape), mass_coef, hist_w)
+        Jl = np.imag(self._pack_l(Rq, Rv)).T / CSTEP          # [ni, N]
+        Jt = np.imag(Rt.reshape(N, -1)).T / CSTEP             # [nt, N]
+        return Jl[:, :ni], Jl[:, ni:], Jt[:, :ni], Jt[:, ni:]
+
+    # -- condensation (Sec. 3.2: local elimination of the interior unknowns) -------------
+    def condense(self, e, Q, V, Vh, mass_coef=0.0, hist_w=None):
+        Rl, Rt = self.local_residual(e, Q, V, Vh, mass_coef, hist_w)
+        A, B, C, D = self.local_jacobian(e, Q, V, Vh, mass_coef, hist_w)
+        X = np.linalg.solve(A, B)
+        y = np.linalg.solve(A, Rl)
+        S = D - C @ X
+        g = Rt - C @ y
+        return dict(S=S, g=g, X=X, y=y, Rl=Rl, Rt=Rt, A=A, B=B, C=C, D=D)
+
+    # -- derived quantities -----------------------------------------------------------------
+    def consistent_q(self, e, V, Vh):
+        """Q solving Eq. hDG_NS0 exactly for given (v, vhat): M Q = -R_q(Q=0)."""
+        T = self.tables(e)
+        M = np.einsum("g,ga,gb->ab", T.W, T.phi, T.phi)
+        Rq, _, _ = self.element_residual(e, np.zeros((1, self.Np, self.m, self.d)),
+                                         V[None], Vh[None])
+        return -np.linalg.solve(M, Rq[0].reshape(self.Np, -1)).reshape(self.Np, self.m, self.d)
+
+    def history_weak(self, e, Vs, coefs):
+        """hist_w [Np, m] = sum_j c_j (u(v_h^{n-j}), phi_a)_K."""
+        T = self.tables(e)
+        out = np.zeros((self.Np, self.m))
+        for Vj, c in zip(Vs, coefs):
+            u = ph.u_of_v(T.phi @ Vj, self.phys.gamma)
+            out += c * np.einsum("g,ga,gm->am", T.W, T.phi, u)
+        return out
+
+    def integrals(self, V):
+        """(total u [m], total generalised entropy int H) over the mesh."""
+        tot_u = np.zeros(self.m)
+        tot_H = 0.0
+        for e in range(self.mesh.E):
+            T = self.tables(e)
+            u = ph.u_of_v(T.phi @ V[e], self.phys.gamma)
+            tot_u += T.W @ u
+            tot_H += T.W @ ph.entropy_H(u, self.phys.gamma)
+        return tot_u, tot_H
+
+
+# ---------------------------------------------------------------------------------------
+# State initialisation from primitive fields (interpolation at nodes)
+# ---------------------------------------------------------------------------------------
+def interpolate_state(prob: Problem, prim_fn):
+    """V at element nodes and Vhat at canonical face nodes from prim_fn(x) -> (rho, vel, p)."""
+    mesh, g = prob.mesh, prob.phys.gamma
+    rho, vel, p = prim_fn(mesh.xnode)
+    V = ph.v_of_u(ph.u_of_primitives(rho, vel, p, g), g)
+    Vhat = np.zeros((mesh.nFaces, prob.Nf, prob.m))
+    for F, sides in enumerate(mesh.face_elems):
+        e, f = sides[0]
+        Vhat[F] = V[e, mesh.ref.face_nodes[f]]
+    return V, Vhat
+
+
+def bdf_coefficients(order: int, dt: float):
+    """(mass_coef, history coefficients) of BDF1 / BDF2; order 0 = steady."""
+    if order == 0:
+        return 0.0, []
+    if order == 1:
+        return 1.0 / dt, [1.0 / dt]
+    if order == 2:
+        return 1.5 / dt, [2.0 / dt, -0.5 / dt]
+    raise ValueError(order)
+
+
+@dataclass
+class NewtonResult:
+    Q: np.ndarray | None
+    V: np.ndarray
+    Vhat: np.ndarray
+    res_norms: list = field(default_factory=list)
+    iters: int = 0
+
+
+def assemble_trace(prob: Problem, locs):
+    """Assembled trace matrix (sparse CSR) and right-hand side -sum P^T g."""
+    n = prob.n_trace
+    rows, cols, vals = [], [], []
+    rhs = np.zeros(n)
+    for e, L in enumerate(locs):
+        gi = prob.trace_index(e)
+        rows.append(np.repeat(gi, gi.size))
+        cols.append(np.tile(gi, gi.size))
+        vals.append(L["S"].ravel())
+        np.add.at(rhs, gi, -L["g"])
+    K = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(n, n))
+    return K, rhs
+
+
+def solve_trace(K, rhs, dense_max=12000):
+    if K.shape[0] <= dense_max:
+        return np.linalg.solve(K.toarray(), rhs)
+    return spla.spsolve(K.tocsc(), rhs)
+
+
+def residual_norm(prob: Problem, locs):
+    """sqrt(sum_e |R_l,e|^2 + |sum_e P_e^T R_t,e|^2)."""
+    rt = np.zeros(prob.n_trace)
+    s = 0.0
+    for e, L in enumerate(locs):
+        s += float(L["Rl"] @ L["Rl"])
+        np.add.at(rt, prob.trace_index(e), L["Rt"])
+    return math.sqrt(s + float(rt @ rt))
+
+
+def newton_iteration(prob: Problem, Q, V, Vhat, mass_coef, hist):
+    """One full Newton iteration: condense every element, solve the trace system,
+    recover the interior. Returns (Q', V', Vhat', residual norm before the update,
+    dvhat, per-element local data)."""
+    E = prob.mesh.E
+    locs = []
+    for e in range(E):
+        Qe = None if Q is None else Q[e]
+        locs.append(prob.condense(e, Qe, V[e], prob.gather_trace(Vhat, e), mass_coef,
+                                  None if hist is None else hist[e]))
+    rn = residual_norm(prob, locs)
+    K, rhs = assemble_trace(prob, locs)
+    dvh = solve_trace(K, rhs)
+    Vhat_new = Vhat + dvh.reshape(Vhat.shape)
+    Qn = None if Q is None else Q.copy()
+    Vn = V.copy()
+    for e, L in enumerate(locs):
+        dx = -(L["y"] + L["X"] @ dvh[prob.trace_index(e)])
+        if Q is None:
+            Vn[e] += dx.reshape(V[e].shape)
+        else:
+            nq = Q[e].size
+            Qn[e] += dx[:nq].reshape(Q[e].shape)
+            Vn[e] += dx[nq:].reshape(V[e].shape)
+    return Qn, Vn, Vhat_new, rn, dvh, locs
+
+
+def newton_solve(prob: Problem, Q, V, Vhat, mass_coef=0.0, hist=None, tol=1e-10, max_it=10):
+    """Undamped Newton with the exact Jacobian; converged when
+    |R| <= tol * max(1, |R_0|)."""
+    res = NewtonResult(Q, V, Vhat)
+    r0 = None
+    for it in range(max_it + 1):
+        Qn, Vn, Vhn, rn, _dvh, _ = newton_iteration(prob, res.Q, res.V, res.Vhat, mass_coef, hist)
+        res.res_norms.append(rn)
+        if r0 is None:
+            r0 = rn
+        if rn <= tol * max(1.0, r0) or it == max_it:
+            break
+        res.Q, res.V, res.Vhat = Qn, Vn, Vhn
+        res.iters = it + 1
+    return res
+
+
+def time_step(prob: Problem, Q, V, Vhat, Vhist, order, dt, tol=1e-10, max_it=10):
+    """One BDF step from history states Vhist = [V^n, V^{n-1}, ...]."""
+    mass_coef, coefs = bdf_coefficients(order, dt)
+    hist = np.stack([prob.history_weak(e, [Vj[e] for Vj in Vhist[:len(coefs)]], coefs)
+                     for e in range(prob.mesh.E)])
+    return newton_solve(prob, Q, V, Vhat, mass_coef, hist, tol, max_it)
+
+
+def consistent_Q(prob: Problem, V, Vhat):
+    if not prob.viscous:
+        return None
+    return np.stack([prob.consistent_q(e, V[e], prob.gather_trace(Vhat, e)) for e in range(prob.mesh.E)])

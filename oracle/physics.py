@@ -1,0 +1,189 @@
+"""Pointwise physics for the oracle; every function accepts complex arrays so that
+the residual can be differentiated by complex step.
+
+State layout: last axis is the component (m = d + 2): (rho, rho V_1..d, rho E) for
+u and (v_1, v_2..v_{d+1}, v_m) for the entropy variables.
+
+Nondimensionalisation (freestream density, speed and length 1): p_inf = 1/(gamma M^2),
+c_v = 1/(gamma (gamma-1) M^2), c_p = gamma c_v, mu = 1/Re, kappa = c_p mu / Pr, beta = 0
+(Sec. 2.2, Eq. closuresNS; Sec. 5 for Pr, gamma, beta).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+
+@dataclass(frozen=True)
+class Physics:
+    gamma: float = 1.4
+    mach: float = 0.5
+    reynolds: float = 0.0            # 0 = inviscid (Euler)
+    prandtl: float = 0.71
+
+    @property
+    def viscous(self) -> bool:
+        return self.reynolds > 0
+
+    @property
+    def cv(self) -> float:
+        return 1.0 / (self.gamma * (self.gamma - 1.0) * self.mach ** 2)
+
+    @property
+    def mu(self) -> float:
+        return 1.0 / self.reynolds if self.reynolds > 0 else 0.0
+
+    @property
+    def kappa(self) -> float:
+        return self.gamma * self.cv * self.mu / self.prandtl
+
+
+def cabs(x):
+    """|x| continued for complex step with d|x|/dx = sign(x), sign(0) = 0."""
+    re = np.real(x)
+    return x * np.sign(re)
+
+
+# -- conservation <-> entropy variables (Sec. 2.3) --------------------------------------
+def primitives_of_u(u, gamma):
+    rho = u[..., 0]
+    vel = u[..., 1:-1] / rho[..., None]
+    p = (gamma - 1.0) * (u[..., -1] - 0.5 * rho * np.sum(vel * vel, axis=-1))
+    return rho, vel, p
+
+
+def u_of_primitives(rho, vel, p, gamma):
+    rhoE = p / (gamma - 1.0) + 0.5 * rho * np.sum(vel * vel, axis=-1)
+    return np.concatenate([rho[..., None], rho[..., None] * vel, rhoE[..., None]], axis=-1)
+
+
+def thermo_entropy(rho, p, gamma):
+    """s = log(p / rho^gamma) with baseline s_0 = 0 (Sec. 2.3)."""
+    return np.log(p) - gamma * np.log(rho)
+
+
+def v_of_u(u, gamma):
+    """Entropy variables v = dH/du for H = -rho s, as printed in Sec. 2.3."""
+    rho, vel, p = primitives_of_u(u, gamma)
+    s = thermo_entropy(rho, p, gamma)
+    g1 = gamma - 1.0
+    v1 = -s + (gamma + 1.0) - g1 * u[..., -1] / p
+    vmid = g1 * u[..., 1:-1] / p[..., None]
+    vm = -g1 * rho / p
+    return np.concatenate([v1[..., None], vmid, vm[..., None]], axis=-1)
+
+
+def primitives_of_v(v, gamma):
+    """Inverse map (not printed in the paper): from the printed v(u),
+    s = gamma - v_1 + |w|^2/(2 v_m), log rho = (log(gamma-1) - log(-v_m) - s)/(gamma-1),
+    p = rho (gamma-1)/(-v_m), V = -w / v_m, with w = (v_2..v_{d+1})."""
+    g1 = gamma - 1.0
+    v1, w, vm = v[..., 0], v[..., 1:-1], v[..., -1]
+    s = gamma - v1 + np.sum(w * w, axis=-1) / (2.0 * vm)
+    lnrho = (np.log(g1) - np.log(-vm) - s) / g1
+    rho = np.exp(lnrho)
+    p = rho * g1 / (-vm)
+    vel = -w / vm[..., None]
+    return rho, vel, p
+
+
+def u_of_v(v, gamma):
+    rho, vel, p = primitives_of_v(v, gamma)
+    return u_of_primitives(rho, vel, p, gamma)
+
+
+def du_of_v(v, dv, gamma):
+    """Directional derivative A0(v) dv of u(v) along dv, written out by the chain rule
+    on the inverse map (A0 = du/dv is the metric tensor of Sec. 4.1)."""
+    g1 = gamma - 1.0
+    rho, vel, p = primitives_of_v(v, gamma)
+    w, vm = v[..., 1:-1], v[..., -1]
+    dv1, dw, dvm = dv[..., 0], dv[..., 1:-1], dv[..., -1]
+    ww = np.sum(w * w, axis=-1)
+    ds = -dv1 + np.sum(w * dw, axis=-1) / vm - ww * dvm / (2.0 * vm * vm)
+    dlnrho = (-dvm / vm - ds) / g1
+    drho = rho * dlnrho
+    dvel = -dw / vm[..., None] + w * (dvm / (vm * vm))[..., None]
+    dp = p * (dlnrho - dvm / vm)
+    dmom = drho[..., None] * vel + rho[..., None] * dvel
+    dE = dp / g1 + 0.5 * drho * np.sum(vel * vel, axis=-1) + rho * np.sum(vel * dvel, axis=-1)
+    return np.concatenate([drho[..., None], dmom, dE[..., None]], axis=-1)
+
+
+def A0_of_v(v, gamma):
+    """A0 = du/dv as a matrix [..., m, m] (row = u component)."""
+    m = v.shape[-1]
+    cols = [du_of_v(v, np.broadcast_to(np.eye(m)[l], v.shape), gamma) for l in range(m)]
+    return np.stack(cols, axis=-1)
+
+
+# -- fluxes (Eqs. flux, viscFlux, closuresNS) ------------------------------------------
+def inviscid_flux_prim(rho, vel, p, gamma):
+    """F(u) [..., m, d]: rows (rho V_j, rho V_i V_j + delta_ij p, V_j (rho E + p))."""
+    d = vel.shape[-1]
+    rhoE = p / (gamma - 1.0) + 0.5 * rho * np.sum(vel * vel, axis=-1)
+    rows = [rho[..., None] * vel]
+    for i in range(d):
+        r = rho[..., None] * vel[..., i:i + 1] * vel
+        r = r + p[..., None] * np.eye(d)[i]
+        rows.append(r)
+    rows.append(vel * (rhoE + p)[..., None])
+    return np.stack(rows, axis=-2)
+
+
+def inviscid_flux_v(v, gamma):
+    rho, vel, p = primitives_of_v(v, gamma)
+    return inviscid_flux_prim(rho, vel, p, gamma)
+
+
+def inviscid_flux_u(u, gamma):
+    rho, vel, p = primitives_of_u(u, gamma)
+    return inviscid_flux_prim(rho, vel, p, gamma)
+
+
+def viscous_flux(v, q, phys: Physics):
+    """G(v, q) [..., m, d] of Eq. viscFlux with q ~ grad v (Sec. 3.3).
+
+    The matrices K_jk are not printed; G is evaluated through the primitive gradients
+    grad V_i = -grad w_i / v_m + w_i grad v_m / v_m^2 and T = 1/(c_v (-v_m)),
+    grad T = grad v_m / (c_v v_m^2), which equals -K_jk (du/dv) q."""
+    gamma = phys.gamma
+    d = v.shape[-1] - 2
+    w, vm = v[..., 1:-1], v[..., -1]
+    vel = -w / vm[..., None]
+    qw, qm = q[..., 1:-1, :], q[..., -1, :]                       # [..., d, d], [..., d]
+    gradV = -qw / vm[..., None, None] + w[..., :, None] * (qm / (vm * vm)[..., None])[..., None, :]
+    gradT = qm / (phys.cv * (vm * vm)[..., None])
+    div = np.trace(gradV, axis1=-2, axis2=-1)
+    tau = phys.mu * (gradV + np.swapaxes(gradV, -1, -2)
+                     - (2.0 / 3.0) * div[..., None, None] * np.eye(d))
+    f = -phys.kappa * gradT
+    zero = np.zeros(v.shape[:-1] + (1, d), dtype=tau.dtype)
+    energy = np.einsum("...i,...ij->...j", vel, tau) - f
+    return -np.concatenate([zero, tau, energy[..., None, :]], axis=-2)
+
+
+# -- entropy pair and stabilization -------------------------------------------------------
+def entropy_H(u, gamma):
+    rho, _vel, p = primitives_of_u(u, gamma)
+    return -rho * thermo_entropy(rho, p, gamma)
+
+
+def entropy_flux(u, gamma):
+    rho, vel, p = primitives_of_u(u, gamma)
+    return (-rho * thermo_entropy(rho, p, gamma))[..., None] * vel
+
+
+def lambda_max(v, n, gamma):
+    """Largest-magnitude eigenvalue of A_n = (dF/du) n: |V.n| + c (Eq. sLxF)."""
+    rho, vel, p = primitives_of_v(v, gamma)
+    c = np.sqrt(gamma * p / rho)
+    return cabs(np.sum(vel * n, axis=-1)) + c
+
+
+def numerical_flux_inviscid(vhat, v, n, gamma):
+    """Eq. numericalFlux with sigma_SLF(v*) = lambda_max(v*) A0(v*), v* = vhat (Sec. 5)."""
+    Fn = 0.5 * np.einsum("...ij,...j->...i", inviscid_flux_v(vhat, gamma) + inviscid_flux_v(v, gamma), n)
+    lam = lambda_max(vhat, n, gamma)
+    return Fn + 0.5 * lam[..., None] * du_of_v(vhat, v - vhat, gamma)
