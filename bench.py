@@ -1,0 +1,338 @@
+#!/usr/bin/env python3
+"""Benchmark of the hot path: assemble + condense throughput (elements/s) for 3D
+Navier-Stokes tetrahedra at p = 3 — the 24^3 periodic cube [0, 2pi]^3, 6 tets per cell
+(82,944 elements; local interior system 400 x 400, reduced to 100 x 100 by the exact
+q-elimination; trace block 200 x 200), Taylor-Green initial state at M0 = 0.1,
+Re = 1600, Pr = 0.71, trace perturbed by 1e-3, BDF2 time term with dt = 0.01.
+
+One step = one hdg_assemble_condense over all elements (residuals, pointwise Jacobians,
+quadrature contractions, LU, X = A^{-1}B, S = D - C X, g). Inputs are resident in HBM;
+each step writes S (26.5 GB) and the recovery data (13.3 GB), far more than L2.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|mixed]
+  python bench.py --impl reference     # the FP64 CPU oracle on a bounded sample
+
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "ns3d_p3_tgv"
+METRIC = "elem/s assemble+condense (3D NS tet p=3), mixed vs FP64, rel err ≤1e-10"
+UNIT = "elem/s"
+
+
+# ----------------------------------------------------------------------------- oracle pool
+_ORACLE = {}
+
+
+def _oracle_init(n_override):
+    """Worker set-up (untimed): the oracle's own mesh and state of the workload."""
+    import numpy as np
+
+    import workloads as wl
+    from oracle import physics as ph
+    from oracle.hdg import Problem, interpolate_state
+    from oracle.mesh import Mesh
+    spec = dict(wl.WORKLOADS[WORKLOAD])
+    if n_override:
+        spec["n"] = n_override
+    mesh = Mesh(spec["dim"], spec["n"], spec["lo"], spec["hi"], spec["p"])
+    phys = ph.Physics(mach=spec["mach"], reynolds=spec["reynolds"], prandtl=spec["prandtl"])
+    prob = Problem(mesh, phys)
+    V, Vh = interpolate_state(prob, lambda x: wl.primitive_state(WORKLOAD, x, **spec))
+    Vh = wl.perturb(Vh, spec["trace_noise"], spec["seed"])
+    _ORACLE.update(prob=prob, V=V, Vh=Vh, dt=spec["dt"])
+
+
+def _oracle_condense(e):
+    """Oracle condensation of element e (BDF2 with u^{n-1} = u^n); returns its S norm."""
+    import numpy as np
+    prob, V, Vh, dt = _ORACLE["prob"], _ORACLE["V"], _ORACLE["Vh"], _ORACLE["dt"]
+    vh = prob.gather_trace(Vh, e)
+    Q = prob.consistent_q(e, V[e], vh)
+    hist = prob.history_weak(e, [V[e], V[e]], [2.0 / dt, -0.5 / dt])
+    L = prob.condense(e, Q, V[e], vh, 1.5 / dt, hist)
+    return float(np.linalg.norm(L["S"]))
+
+
+def oracle_throughput(n_elem_total, per_core, steps=1, warmup=0, n_override=None):
+    """Time the oracle on a seeded sample of elements in a spawn pool over all host
+    cores. Returns (elem/s per step list, cores, sample description)."""
+    import multiprocessing as mp
+
+    import numpy as np
+    cores = os.cpu_count() or 1
+    env_keep = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in env_keep:
+        os.environ[k] = "1"
+    ctx = mp.get_context("spawn")
+    rates = []
+    rng = np.random.default_rng(3)
+    try:
+        with ctx.Pool(cores, initializer=_oracle_init, initargs=(n_override,)) as pool:
+            pool.map(_oracle_condense, [0] * cores)  # pay the set-up in every worker
+            for it in range(warmup + steps):
+                sample = rng.choice(n_elem_total, size=cores * per_core, replace=False).tolist()
+                t0 = time.perf_counter()
+                pool.map(_oracle_condense, sample, chunksize=per_core)
+                dt = time.perf_counter() - t0
+                if it >= warmup:
+                    rates.append(len(sample) / dt)
+    finally:
+        for k, v in env_keep.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    desc = (f"{cores * per_core} seeded random elements of the {n_elem_total}-element workload per step, "
+            f"oracle condense (complex-step Jacobian, dense 400x400 LU) in a spawn pool of {cores} processes")
+    return rates, cores, desc
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.gpu)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- main
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--cpu-per-core", type=int, default=6, help="oracle elements per host core and step")
+    ap.add_argument("--n", type=int, default=None, help="override the cube resolution (tests only)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args):
+    import workloads as wl
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    spec = dict(wl.WORKLOADS[WORKLOAD])
+    n = args.n or spec["n"]
+    E = 6 * n ** 3
+    rates, cores, desc = oracle_throughput(E, max(1, args.cpu_per_core // 3), steps=args.steps,
+                                           warmup=args.warmup, n_override=args.n)
+    value = statistics.median(rates)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * E / value, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "elements": E, "p": 3, "dim": 3, "physics": "navier-stokes",
+                       "precision": "fp64", "l2": "per-element working set, host"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    ws, rank, local = _dist()
+    import torch
+    import torch.distributed as dist
+
+    from paper_1808_05066_gb300 import hdg
+    from paper_1808_05066_gb300.workload import DeviceWorkload, flops_per_element
+    if ws > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    W = DeviceWorkload(WORKLOAD, device=local, n_override=args.n)
+    E = W.n_elem
+    prec = hdg.HDG_PREC_MIXED if args.precision == "mixed" else hdg.HDG_PREC_FP64
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    def max_over_ranks(x):
+        if ws == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    for _ in range(args.warmup):
+        W.assemble(prec)
+    torch.cuda.synchronize(dev)
+    if int(W.status.abs().sum()) != 0:
+        raise RuntimeError("element status flags set during warm-up")
+    # ---------------- device-resident timing
+    hdg.hdg_profile_reset(W.ctx.handle)
+    hdg.hdg_profile_enable(W.ctx.handle, True)
+    gpu_index = int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0]) if \
+        os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0].isdigit() else local
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(gpu_index) as clk:
+        barrier()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            W.assemble(prec)
+        ev1.record(stream)
+        barrier()
+    ms = ev0.elapsed_time(ev1)
+    ms = max_over_ranks(ms)
+    ms_per_step = ms / args.steps
+    value = ws * E * args.steps / (ms / 1000.0)
+    classes = {"pointwise": hdg.HDG_KERNEL_POINTWISE, "assemble": hdg.HDG_KERNEL_ASSEMBLE,
+               "condense": hdg.HDG_KERNEL_CONDENSE, "mixed": hdg.HDG_KERNEL_MIXED}
+    prof = {k: hdg.hdg_profile_read(W.ctx.handle, c) for k, c in classes.items()}
+    launches_total, _ = hdg.hdg_profile_read(W.ctx.handle, -1)
+    hdg.hdg_profile_enable(W.ctx.handle, False)
+    dom = max((k for k in prof if prof[k][0] > 0), key=lambda k: prof[k][1])
+    dom_launches, dom_ms = prof[dom]
+    viscous = W.spec["reynolds"] > 0
+    clocks = clk.summary()
+    sm_max = clocks.get("sm_max_mhz") or 2070.0
+    if dom in ("assemble", "condense"):
+        work = flops_per_element(W.info, viscous, dom) * E * args.steps
+        # FP64 DFMA pipe: 152 SMs x 2 DFMA/clk x 2 flop x max SM clock
+        peak = 152 * 4 * sm_max * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": work / (dom_ms / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x max SM clock", "kernel": dom,
+                "launches": dom_launches, "avg_launch_ms": dom_ms / max(dom_launches, 1), "traffic": None}
+    else:
+        roof = {"bound": "alu", "achieved": None, "peak": None, "unit": "TFLOP/s", "kernel": dom, "traffic": None}
+    if roof.get("achieved") is not None:
+        roof["frac"] = roof["achieved"] / roof["peak"]
+    shares = {k: (prof[k][1] / sum(v[1] for v in prof.values()) if prof[k][1] else 0.0) for k in prof}
+
+    # ---------------- end to end through the C-ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        pin = dict(pin_memory=True)
+        hV = W.V.cpu().pin_memory()
+        hVh = W.Vhat.cpu().pin_memory()
+        hS = torch.empty(W.S.shape, dtype=torch.float64, **pin)
+        hg = torch.empty(W.g.shape, dtype=torch.float64, **pin)
+        dV = torch.empty_like(W.V)
+        dVh = torch.empty_like(W.Vhat)
+        h2d = hV.numel() * 8 + hVh.numel() * 8
+        d2h = hS.numel() * 8 + hg.numel() * 8
+
+        def e2e_step():
+            dV.copy_(hV, non_blocking=True)
+            dVh.copy_(hVh, non_blocking=True)
+            W.assemble(prec, V=dV, Vhat=dVh)
+            hS.copy_(W.S, non_blocking=True)
+            hg.copy_(W.g, non_blocking=True)
+
+        for _ in range(max(1, min(args.warmup, 2))):
+            e2e_step()
+        barrier()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        ev1.record(stream)
+        barrier()
+        ms2 = max_over_ranks(ev0.elapsed_time(ev1))
+        e2e = {"value": ws * E * args.steps / (ms2 / 1000.0), "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
+        del hS, hg
+
+    # ---------------- CPU baseline (oracle), rank 0 at N=1 only
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        rates, cores, desc = oracle_throughput(E, args.cpu_per_core, steps=1, warmup=0, n_override=args.n)
+        cpu = {"value": rates[0], "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "elements_per_gpu": E, "dim": 3, "p": 3, "physics": "navier-stokes",
+                       "mesh": f"{W.spec['n']}^3 periodic cube x 6 tets", "precision": args.precision,
+                       "l2": "inputs+outputs larger than L2 (S alone 26.5 GB written per step)",
+                       "parallelism": f"replica per GPU x{ws}"},
+            "roofline": roof, "kernel_time_share": shares, "gpu_launches": launches_total,
+            "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

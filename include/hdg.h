@@ -1,0 +1,180 @@
+/* C-ABI of the GB300 entropy-variable hybridized DG hot path.
+ *
+ * The method (Fernandez, Nguyen & Peraire, arXiv:1808.05066) discretises the
+ * compressible Euler (Sec. 3.2, Eqs. hDG1-hDG3) and Navier-Stokes equations
+ * (Sec. 3.3, Eqs. hDG_NS0-hDG_NS3) in entropy variables v with a hybrid trace vhat.
+ * The local equations are eliminated element by element ("static condensation",
+ * Sec. 3.2 last paragraph, Sec. 3.3) and only the trace unknowns are globally
+ * coupled. This library implements, on periodic simplex meshes with the HDG trace
+ * space (E^E_h empty, Sec. 3.4 "Examples of schemes"):
+ *   - the per-element Newton linearisation and condensation     hdg_assemble_condense
+ *   - the global trace solve                                     hdg_trace_solve
+ *   - the interior recovery                                      hdg_recover_interior
+ *   - a full BDF Newton step around them                         hdg_newton_step
+ * with the symmetric Lax-Friedrichs stabilisation sigma = lambda_max(vhat) A0(vhat)
+ * (Eq. sLxF with v* = vhat, the choice of Sec. 5) in the inviscid flux of
+ * Eq. numericalFlux, and the viscous flux G(vhat, q) . n of Eq. numericalFluxNS_2.
+ *
+ * Conventions shared by all calls
+ *   - m = d + 2 state components. Entropy variables (v_1, w_1..w_d, v_m), v_m < 0.
+ *   - Nondimensionalisation: freestream density, speed and length are 1, so
+ *     p_inf = 1/(gamma M^2), c_v = 1/(gamma (gamma-1) M^2), mu = 1/Re,
+ *     kappa = gamma c_v mu / Pr, beta = 0.  reynolds == 0 selects Euler.
+ *   - Every array argument of a compute call is a DEVICE pointer owned by the caller
+ *     (the library never frees it); all are row-major double unless stated.
+ *       V     [E][Np][m]        element nodal entropy variables
+ *       Vhat  [F][Nf][m]        trace values at the canonical nodes of each face
+ *       hist  [E][Np][m]        BDF history (sum_j c_j (u(v^{n-j}), phi_a)_K), or NULL
+ *       S     [E][nt][nt]       condensed trace matrix per element, nt = nF Nf m
+ *       g     [E][nt]           condensed right-hand side per element
+ *       recov [E][nv*nt + nv]   recovery data X = A^{-1}B (row-major nv x nt) then
+ *                               y = A^{-1} R_v, nv = Np m
+ *       R     [E][nv + nt]      raw residuals R_v then R_t (element contribution)
+ *     Local trace order is [local face][face node][component]; local face f is the
+ *     face opposite vertex f; face nodes in increasing element-node order.
+ *   - stream is a cudaStream_t (NULL = legacy default stream). Calls enqueue work and
+ *     return without synchronising unless they write a host scalar (iterations,
+ *     norms), which they document.
+ *   - Return value: HDG_OK or an HDG_ERR_* code; hdg_last_error() gives a message
+ *     (thread-local, valid until the next call from the same thread).
+ */
+#ifndef HDG_H_
+#define HDG_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  HDG_OK = 0,
+  HDG_ERR_INVALID_ARG = 1,
+  HDG_ERR_NONPHYSICAL = 2, /* some element has v_m >= 0 or non-positive rho / p  */
+  HDG_ERR_SINGULAR = 3,    /* zero pivot in an element factorisation              */
+  HDG_ERR_REFINE = 4,      /* iterative refinement did not reach its tolerance    */
+  HDG_ERR_NOT_CONVERGED = 5,
+  HDG_ERR_TIMEOUT = 6,
+  HDG_ERR_CUDA = 7,
+  HDG_ERR_UNSUPPORTED = 8  /* (dim, p, quadrature, physics) not compiled in        */
+};
+
+enum { HDG_PREC_FP64 = 0, HDG_PREC_MIXED = 1 };
+enum { HDG_SOLVER_AUTO = 0, HDG_SOLVER_GMRES = 1, HDG_SOLVER_DENSE = 2 };
+/* per-element status bits written by hdg_assemble_condense */
+enum { HDG_ELEM_NONPHYSICAL = 1, HDG_ELEM_SINGULAR = 2, HDG_ELEM_REFINE = 4 };
+
+typedef struct hdg_mesh* hdg_mesh_t;
+typedef struct hdg_ctx* hdg_ctx_t;
+
+typedef struct {
+  double gamma;    /* ratio of specific heats (1.4) */
+  double mach;     /* reference Mach number M */
+  double reynolds; /* Re; 0 = inviscid (Euler) */
+  double prandtl;  /* Pr */
+} hdg_physics;
+
+typedef struct {
+  int32_t dim, p, quad_points; /* quad_points K per direction: exact to degree 2K-1 */
+  int32_t m, Np, Nf, nF, NG, NGF;
+  int32_t nv, nt;              /* per-element interior / trace unknowns */
+  int32_t geo_stride;
+  int64_t n_elem, n_faces, n_trace; /* n_trace = n_faces * Nf * m */
+} hdg_mesh_info;
+
+/* Mesh T_h (Sec. 3.1.1): the n[0] x .. x n[dim-1] periodic grid on the box
+ * [lo, hi], each cell split into 2 triangles / 6 tetrahedra (Kuhn split, the same in
+ * every cell). p = polynomial degree k (1..4), quad_points = K (0 selects p+1).
+ * Host-only work; the mesh owns host arrays only. Errors: HDG_ERR_INVALID_ARG. */
+int hdg_mesh_create(int dim, const int64_t n[3], const double lo[3], const double hi[3], int p,
+                    int quad_points, hdg_mesh_t* out);
+void hdg_mesh_destroy(hdg_mesh_t mesh);
+int hdg_mesh_get_info(hdg_mesh_t mesh, hdg_mesh_info* out);
+/* Host copies of the topology: face_of [E][nF], fnode_map [E][nF][Nf] (canonical face
+ * node of each local face node), face_side [F][2] (e * nF + f; owner first). Any
+ * pointer may be NULL. */
+int hdg_mesh_copy_topology(hdg_mesh_t mesh, int32_t* face_of, int32_t* fnode_map, int32_t* face_side);
+/* Host copies: element node coordinates xnode [E][Np][dim], canonical face-node
+ * coordinates xfnode [F][Nf][dim] (owner side), geometry geo [E][geo_stride] =
+ * (Jinv [dim][dim] with Jinv[r][k] = d r / d x_k, |det J|, per face: unit outward
+ * normal [dim], surface Jacobian). Any pointer may be NULL. */
+int hdg_mesh_copy_coords(hdg_mesh_t mesh, double* xnode, double* xfnode, double* geo);
+
+/* Context: mesh tables, reference tables and physics on one CUDA device. Allocates the
+ * device tables and (lazily, on first use) the internal scratch of the calls below;
+ * everything is freed by hdg_ctx_destroy. The mesh must outlive the context. */
+int hdg_ctx_create(hdg_mesh_t mesh, const hdg_physics* phys, int device, hdg_ctx_t* out);
+void hdg_ctx_destroy(hdg_ctx_t ctx);
+
+/* Entropy variables of Sec. 2.3, v = dH/du for H = -rho s: converts n_points primitive
+ * states prim [n][m] = (rho, V_1..V_d, p) to v [n][m] (device). */
+int hdg_prim_to_entropy(hdg_ctx_t ctx, const double* prim, int64_t n_points, double* v, void* stream);
+
+/* BDF history of the time term of Eq. hDG1 / hDG_NS1:
+ * hist[e][a][i] = c0 (u(v0), phi_a)_K + c1 (u(v1), phi_a)_K. V1 may be NULL (c1 unused).
+ * BDF1: mass_coef = 1/dt, c0 = 1/dt. BDF2: mass_coef = 3/(2dt), c0 = 2/dt, c1 = -1/(2dt). */
+int hdg_history(hdg_ctx_t ctx, const double* V0, const double* V1, double c0, double c1, double* hist,
+                void* stream);
+
+/* Newton linearisation and static condensation of every element (Sec. 3.2-3.3, local
+ * elimination): residuals R_v of Eq. hDG_NS1 / hDG1 (time term mass_coef (u(v), w) - hist)
+ * and R_t of Eq. hDG_NS2 / hDG2 (this element's share), q eliminated exactly through the
+ * linear Eq. hDG_NS0; Jacobian blocks A = dR_v/dV, B = dR_v/dVhat, C = dR_t/dV,
+ * D = dR_t/dVhat; LU of A; S = D - C A^{-1} B, g = R_t - C A^{-1} R_v. Outputs S, g, recov,
+ * R as documented above; elem_status [E] (int32, may be NULL) gets HDG_ELEM_* bits and
+ * must be zeroed by the caller. precision: HDG_PREC_FP64 or HDG_PREC_MIXED.
+ * Does not synchronise; status bits are the way to learn about bad elements. */
+int hdg_assemble_condense(hdg_ctx_t ctx, const double* V, const double* Vhat, const double* hist,
+                          double mass_coef, int precision, double* S, double* g, double* recov,
+                          double* R, int32_t* elem_status, void* stream);
+
+/* Global trace system sum_e P_e^T S_e P_e dVhat = -sum_e P_e^T g_e (Sec. 3.2: only vhat
+ * is globally coupled). method: HDG_SOLVER_GMRES (restarted GMRES(30), face-block Jacobi
+ * preconditioner), HDG_SOLVER_DENSE (assembled dense LU with partial pivoting, for
+ * n_trace <= 16384) or HDG_SOLVER_AUTO. dVhat [F][Nf][m] device output. Writes *iters and
+ * *final_res (relative residual) on the host, so it synchronises the stream.
+ * HDG_ERR_NOT_CONVERGED if rtol was not reached in max_it iterations. */
+int hdg_trace_solve(hdg_ctx_t ctx, const double* S, const double* g, double* dVhat, int method, double rtol,
+                    int max_it, int* iters, double* final_res, void* stream);
+
+/* Interior recovery (Sec. 3.2): dV_e = -y_e - X_e P_e dVhat. dV [E][Np][m] device. */
+int hdg_recover_interior(hdg_ctx_t ctx, const double* recov, const double* dVhat, double* dV, void* stream);
+
+/* Helpers used around the solve. y = K x with K = sum_e P_e^T S_e P_e (trace vectors). */
+int hdg_trace_matvec(hdg_ctx_t ctx, const double* S, const double* x, double* y, void* stream);
+/* Newton residual norm sqrt(sum_e |R_v,e|^2 + |sum_e P_e^T R_t,e|^2) from R; writes the
+ * host scalar *norm (synchronises). */
+int hdg_residual_norm(hdg_ctx_t ctx, const double* R, double* norm, void* stream);
+
+/* One implicit time step by Newton's method: repeats assemble_condense, trace_solve,
+ * recover and the update V += dV, Vhat += dVhat until |R| <= tol max(1, |R_0|) or
+ * max_newton updates were made. V and Vhat are updated in place; *newton_iters and
+ * *res_norm (final) are written on the host. Uses context-owned workspaces (allocated on
+ * first call). HDG_ERR_NOT_CONVERGED / HDG_ERR_NONPHYSICAL / HDG_ERR_SINGULAR on failure. */
+int hdg_newton_step(hdg_ctx_t ctx, double* V, double* Vhat, const double* hist, double mass_coef, int precision,
+                    double tol, int max_newton, int* newton_iters, double* res_norm, void* stream);
+
+/* Measurement support (no counterpart in the paper). Every kernel launch of a context
+ * is counted per kernel class; with profiling enabled each launch is also bracketed by
+ * CUDA events recorded on its launching stream. hdg_profile_read synchronises on the
+ * recorded events and returns, for one class (HDG_KERNEL_*, or -1 for all), the number
+ * of launches and their summed device time in milliseconds since the last reset. */
+enum {
+  HDG_KERNEL_POINTWISE = 0, /* FP64 form: fluxes and pointwise Jacobians            */
+  HDG_KERNEL_ASSEMBLE = 1,  /* FP64 form: quadrature contractions into A, B, C, D    */
+  HDG_KERNEL_CONDENSE = 2,  /* FP64 form: LU, X = A^{-1}B, S = D - C X              */
+  HDG_KERNEL_MIXED = 3,     /* mixed form: fused assemble-factor-condense           */
+  HDG_KERNEL_TRACE = 4,     /* trace operator, preconditioner, solver kernels       */
+  HDG_KERNEL_OTHER = 5,     /* history, conversions, recovery, norms, updates       */
+  HDG_KERNEL_CLASSES = 6
+};
+int hdg_profile_enable(hdg_ctx_t ctx, int on);
+int hdg_profile_reset(hdg_ctx_t ctx);
+int hdg_profile_read(hdg_ctx_t ctx, int kernel_class, int64_t* launches, double* total_ms);
+
+const char* hdg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HDG_H_ */

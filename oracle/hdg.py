@@ -217,10 +217,9 @@ def interpolate_state(prob: Problem, prim_fn):
     mesh, g = prob.mesh, prob.phys.gamma
     rho, vel, p = prim_fn(mesh.xnode)
     V = ph.v_of_u(ph.u_of_primitives(rho, vel, p, g), g)
-    Vhat = np.zeros((mesh.nFaces, prob.Nf, prob.m))
-    for F, sides in enumerate(mesh.face_elems):
-        e, f = sides[0]
-        Vhat[F] = V[e, mesh.ref.face_nodes[f]]
+    owner = np.array([sides[0] for sides in mesh.face_elems])          # [F, 2] (e, f)
+    fn = np.array(mesh.ref.face_nodes)
+    Vhat = V[owner[:, 0][:, None], fn[owner[:, 1]]]                     # [F, Nf, m]
     return V, Vhat
 
 

@@ -34,27 +34,25 @@ class Mesh:
         self.h = (self.hi - self.lo) / n
         self.ref = refel(dim, p, deg)
         ref = self.ref
-        verts = []                                   # integer lattice coords per element
         if dim == 2:
-            tris = [[(0, 0), (1, 0), (1, 1)], [(0, 0), (1, 1), (0, 1)]]
-            for j in range(n):
-                for i in range(n):
-                    for t in tris:
-                        verts.append([(i + a, j + b) for a, b in t])
+            cell = np.array([[(0, 0), (1, 0), (1, 1)], [(0, 0), (1, 1), (0, 1)]], dtype=np.int64)
+            jj, ii = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+            origin = np.stack([ii.ravel(), jj.ravel()], axis=-1)              # cells, x fastest
         else:
-            perms = list(itertools.permutations(range(3)))
-            for k in range(n):
-                for j in range(n):
-                    for i in range(n):
-                        for s in perms:
-                            P = [np.zeros(3, int)]
-                            P.append(P[0] + np.eye(3, dtype=int)[s[0]])
-                            P.append(P[1] + np.eye(3, dtype=int)[s[1]])
-                            P.append(np.ones(3, int))
-                            if np.linalg.det(np.array([P[1], P[2], P[3]], float)) < 0:
-                                P[1], P[2] = P[2], P[1]
-                            verts.append([tuple(np.array((i, j, k)) + q) for q in P])
-        self.L = np.array(verts, dtype=np.int64)     # [E, nF, dim]
+            tets = []
+            for s in itertools.permutations(range(3)):
+                P = [np.zeros(3, int)]
+                P.append(P[0] + np.eye(3, dtype=int)[s[0]])
+                P.append(P[1] + np.eye(3, dtype=int)[s[1]])
+                P.append(np.ones(3, int))
+                if np.linalg.det(np.array([P[1], P[2], P[3]], float)) < 0:
+                    P[1], P[2] = P[2], P[1]
+                tets.append(P)
+            cell = np.array(tets, dtype=np.int64)                              # [6, 4, 3]
+            kk, jj, ii = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+            origin = np.stack([ii.ravel(), jj.ravel(), kk.ravel()], axis=-1)
+        verts = (origin[:, None, None, :] + cell[None]).reshape(-1, cell.shape[1], dim)
+        self.L = verts.astype(np.int64)              # [E, nF, dim]
         self.E = len(verts)
         self.X = self.lo + self.h * self.L.astype(np.float64)
         X0 = self.X[:, 0, :]
@@ -70,43 +68,51 @@ class Mesh:
         self._face_geometry()
 
     # -- topology -------------------------------------------------------------------
-    def _face_key(self, e, f):
-        vs = sorted(tuple(v) for k, v in enumerate(self.L[e]) if k != f)
-        A = np.array(vs[0])
-        return (tuple(A % self.n),) + tuple(tuple(np.array(v) - A) for v in vs[1:])
+    def _encode(self, arr):
+        """Integers -> one int64 per row, monotone in the lexicographic row order."""
+        W = 4 * (self.n * self.p + 8)
+        out = np.zeros(arr.shape[:-1], dtype=np.int64)
+        for r in range(arr.shape[-1]):
+            out = out * W + (arr[..., r] + W // 2)
+        return out
 
     def _faces(self):
-        ref, n, p = self.ref, self.n, self.p
-        nF = ref.nF
-        key2id = {}
-        self.face_of = np.zeros((self.E, nF), dtype=np.int64)
-        self.face_elems = []
-        for e in range(self.E):
-            for f in range(nF):
-                k = self._face_key(e, f)
-                if k not in key2id:
-                    key2id[k] = len(self.face_elems)
-                    self.face_elems.append([(e, f)])
-                else:
-                    self.face_elems[key2id[k]].append((e, f))
-                self.face_of[e, f] = key2id[k]
-        self.nFaces = len(self.face_elems)
-        assert all(len(s) == 2 for s in self.face_elems), "periodic mesh: every face has two sides"
-        self.fnode_map = np.zeros((self.E, nF, ref.Nf), dtype=np.int64)
-        for F, sides in enumerate(self.face_elems):
-            e0, f0 = sides[0]
-            canon = [self._face_node_key(e0, f0, a) for a in ref.face_nodes[f0]]
-            pos = {c: i for i, c in enumerate(canon)}
-            assert len(pos) == ref.Nf
-            for (e, f) in sides:
-                for c, a in enumerate(ref.face_nodes[f]):
-                    self.fnode_map[e, f, c] = pos[self._face_node_key(e, f, a)]
-
-    def _face_node_key(self, e, f, a):
-        """Node position (units h/p) relative to the face's smallest vertex: periodic
-        copies of a face differ by a translation, so the key is the same on both sides."""
-        A = min(tuple(v) for k, v in enumerate(self.L[e]) if k != f)
-        return tuple(self.Nint[e, a] - self.p * np.array(A))
+        ref, n, p, E = self.ref, self.n, self.p, self.E
+        nF, Nf = ref.nF, ref.Nf
+        # vertices of every (element, local face), sorted lexicographically
+        fv = self.L[:, np.array(ref.face_verts), :]                        # [E, nF, nF-1, d]
+        order = np.argsort(self._encode(fv), axis=-1, kind="stable")
+        fv = np.take_along_axis(fv, order[..., None], axis=2)
+        A = fv[:, :, 0, :]                                                 # smallest vertex
+        key = np.concatenate([A % n, (fv[:, :, 1:, :] - A[:, :, None, :]).reshape(E, nF, -1)], axis=-1)
+        key = key.reshape(E * nF, -1)
+        _, first, inv = np.unique(key, axis=0, return_index=True, return_inverse=True)
+        inv = inv.reshape(-1)
+        rank = np.empty(len(first), dtype=np.int64)                        # first-appearance order
+        rank[np.argsort(first, kind="stable")] = np.arange(len(first))
+        face_of = rank[inv]
+        self.face_of = face_of.reshape(E, nF)
+        self.nFaces = len(first)
+        srt = np.argsort(face_of, kind="stable")                           # sides in appearance order
+        counts = np.bincount(face_of, minlength=self.nFaces)
+        assert np.all(counts == 2), "periodic mesh: every face has two sides"
+        sides = srt.reshape(self.nFaces, 2)                                # flat (e * nF + f)
+        self.face_elems = [[(int(a // nF), int(a % nF)), (int(b // nF), int(b % nF))] for a, b in sides]
+        # face-node keys: node position (units h/p) relative to the face's smallest vertex;
+        # periodic copies of a face differ by a translation, so both sides share the keys
+        fn = np.array(ref.face_nodes)                                      # [nF, Nf]
+        KN = self.Nint[:, fn, :] - p * A[:, :, None, :]                     # [E, nF, Nf, d]
+        codes = self._encode(KN).reshape(E * nF, Nf)
+        c0, c1 = codes[sides[:, 0]], codes[sides[:, 1]]
+        o0, o1 = np.argsort(c0, axis=1), np.argsort(c1, axis=1)
+        assert np.array_equal(np.take_along_axis(c0, o0, 1), np.take_along_axis(c1, o1, 1))
+        assert np.all(np.diff(np.take_along_axis(c0, o0, 1), axis=1) > 0)
+        fmap = np.zeros((E * nF, Nf), dtype=np.int64)
+        fmap[sides[:, 0]] = np.arange(Nf)                                  # owner: canonical order
+        m1 = np.zeros_like(c1)
+        np.put_along_axis(m1, o1, o0, axis=1)
+        fmap[sides[:, 1]] = m1
+        self.fnode_map = fmap.reshape(E, nF, Nf)
 
     def _face_geometry(self):
         ref, dim = self.ref, self.dim
@@ -114,23 +120,21 @@ class Mesh:
         self.normal = np.zeros((self.E, nF, dim))
         self.face_jac = np.zeros((self.E, nF))
         pm = 1.0 if dim == 2 else 0.5                # measure of the parameter simplex
-        for e in range(self.E):
-            for f in range(nF):
-                Y = self.X[e, ref.face_verts[f]]
-                opp = self.X[e, f]
-                if dim == 2:
-                    t = Y[1] - Y[0]
-                    nv = np.array([t[1], -t[0]])
-                    area = np.linalg.norm(t)
-                else:
-                    c = np.cross(Y[1] - Y[0], Y[2] - Y[0])
-                    nv = c
-                    area = 0.5 * np.linalg.norm(c)
-                nv = nv / np.linalg.norm(nv)
-                if np.dot(nv, opp - Y[0]) > 0:
-                    nv = -nv
-                self.normal[e, f] = nv
-                self.face_jac[e, f] = area / pm
+        for f in range(nF):
+            Y = self.X[:, ref.face_verts[f]]         # [E, dim, dim]
+            opp = self.X[:, f]
+            if dim == 2:
+                t = Y[:, 1] - Y[:, 0]
+                nv = np.stack([t[:, 1], -t[:, 0]], axis=-1)
+                area = np.linalg.norm(t, axis=-1)
+            else:
+                nv = np.cross(Y[:, 1] - Y[:, 0], Y[:, 2] - Y[:, 0])
+                area = 0.5 * np.linalg.norm(nv, axis=-1)
+            nv = nv / np.linalg.norm(nv, axis=-1, keepdims=True)
+            flip = np.sum(nv * (opp - Y[:, 0]), axis=-1) > 0
+            nv[flip] = -nv[flip]
+            self.normal[:, f] = nv
+            self.face_jac[:, f] = area / pm
 
     # -- counting (Sec. 3.4, Eqs. dof / nnz, Tables t:dofs / t:nnz) ------------------
     @property

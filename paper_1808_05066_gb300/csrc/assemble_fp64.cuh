@@ -1,0 +1,637 @@
+// Plain FP64 assemble + condense (the reference GPU form of the hot path).
+//
+// Per element K the Newton linearisation of the local equations (Eq. hDG_NS1 / hDG1,
+// with q eliminated exactly through Eq. hDG_NS0, which is linear in (q, v, vhat)) and
+// of the element's share of the trace equation (Eq. hDG_NS2 / hDG2) is assembled as
+//   A' = dR_v/dV, B' = dR_v/dVhat, C' = dR_t/dV, D' = dR_t/dVhat
+// and condensed: X = A'^{-1} B', y = A'^{-1} R_v, S = D' - C' X, g = R_t - C' y.
+// This equals the block elimination of the full [q; v] interior system in the order
+// q first (the q-q block is the element mass matrix times the identity).
+//
+// Unknowns are grouped per state component into NZ "nodal" values z = [V (NP); Vhat
+// (NF x NFN)]. At each quadrature point the value of v is Phi z and the lifted
+// gradient is q_k = R_k z with
+//   R_k(g, b)     = sum_r Jinv[r][k] dPhi_r(g, b) - sum_{f: b on f} n_fk s_f PL_f(g, c_f(b))
+//   R_k(g, (f,c)) = n_fk s_f PL_f(g, c),  s_f = |F| / |K| (face / element Jacobians),
+// PL_f = Phi Mref^{-1} E_f the lift of face f. Three kernels per chunk of elements:
+//   k_pointwise  one thread per quadrature point: fluxes and exact pointwise Jacobians
+//                by forward-mode dual numbers, pre-contracted with weights and Jinv;
+//   k_assemble   one CTA per element: quadrature contractions into A', B', C', D', R;
+//   k_condense   one CTA per element: LU with partial pivoting of A' in shared memory,
+//                triangular solves for X and y, Schur products for S and g.
+#pragma once
+#include "hdg_device.cuh"
+
+namespace hdg {
+
+struct AssembleArgs {
+  const double* V;      // [E][NP][M]
+  const double* Vhat;   // [F][NFN][M]
+  const int* tgidx;     // [E][NF][NFN] global face-node index
+  const double* geo;    // [E][GEO]
+  const double* hist;   // [E][NP][M] or null
+  double mass_coef;
+  int64_t e0, ne;       // element chunk
+  // scratch (chunk-local)
+  double* ptv;          // [ne][NG][PT_VOL]
+  double* ptf;          // [ne][NF][NGF][PT_FACE]
+  double* Ap;           // [ne][NV][NV]
+  double* Cp;           // [ne][NT][NV]
+  // outputs (global element index)
+  double* S;            // [E][NT][NT]   (D' on entry to condense)
+  double* g;            // [E][NT]
+  double* recov;        // [E][NV*NT + NV]  X then y (B' on entry to condense)
+  double* R;            // [E][NV + NT] raw residuals R_v, R_t (always written)
+  int* status;          // [E]
+};
+
+enum { HDG_STATUS_NONPHYSICAL = 1, HDG_STATUS_SINGULAR = 2 };
+
+template <class C>
+HDG_DEVI void load_element(const AssembleArgs& a, int64_t e, double (*z)[C::M], double* G) {
+  constexpr int M = C::M;
+  for (int t = threadIdx.x; t < C::NP * M; t += blockDim.x) z[t / M][t % M] = a.V[e * C::NV + t];
+  for (int t = threadIdx.x; t < C::NF * C::NFN * M; t += blockDim.x) {
+    int fc = t / M, i = t % M;
+    int gi = a.tgidx[e * (C::NF * C::NFN) + fc];
+    z[C::NP + fc][i] = a.Vhat[(int64_t)gi * M + i];
+  }
+  for (int t = threadIdx.x; t < C::GEO; t += blockDim.x) G[t] = a.geo[e * C::GEO + t];
+}
+
+// ------------------------------------------------------------------------------------
+// k_pointwise
+// ------------------------------------------------------------------------------------
+template <class C>
+__global__ void __launch_bounds__(128) k_pointwise(AssembleArgs a, DevTables T, PhysParams ph) {
+  constexpr int D = C::D, M = C::M, NP = C::NP, NFN = C::NFN, NF = C::NF, NG = C::NG, NGF = C::NGF;
+  __shared__ double z[C::NZ][M];
+  __shared__ double G[C::GEO];
+  const int64_t le = blockIdx.x;
+  const int64_t e = a.e0 + le;
+  load_element<C>(a, e, z, G);
+  __syncthreads();
+  const double* Jinv = G;
+  const double detJ = G[D * D];
+  const int tid = threadIdx.x;
+  bool bad = false;
+  if (tid < NG) {
+    const int g = tid;
+    const double W = T.W[g] * detJ;
+    double v[M];
+    for (int i = 0; i < M; ++i) {
+      double s = 0.0;
+      for (int b = 0; b < NP; ++b) s += T.Phi[g * NP + b] * z[b][i];
+      v[i] = s;
+    }
+    double q[M][D];
+    if (C::VISC) {
+      for (int i = 0; i < M; ++i) {
+        double gr[D];
+        for (int r = 0; r < D; ++r) {
+          double s = 0.0;
+          for (int b = 0; b < NP; ++b) s += T.dPhi[(r * NG + g) * NP + b] * z[b][i];
+          gr[r] = s;
+        }
+        for (int k = 0; k < D; ++k) {
+          double s = 0.0;
+          for (int r = 0; r < D; ++r) s += Jinv[r * D + k] * gr[r];
+          for (int f = 0; f < NF; ++f) {
+            const double* Gf = G + D * D + 1 + f * (D + 1);
+            double lift = 0.0;
+            for (int c = 0; c < NFN; ++c)
+              lift += T.PL[(f * NG + g) * NFN + c] * (z[NP + f * NFN + c][i] - z[T.fnodes[f * NFN + c]][i]);
+            s += Gf[k] * (Gf[D] / detJ) * lift;
+          }
+          q[i][k] = s;
+        }
+      }
+    }
+    bad = !(v[M - 1] < 0.0);
+    Dual<M> vd[M];
+    for (int l = 0; l < M; ++l) {
+      vd[l] = dconst<M>(v[l]);
+      vd[l].d[l] = 1.0;
+    }
+    Dual<M> rho, vel[D], p, u[M], F[M][D];
+    prim_of_v<D>(vd, ph.gamma, rho, vel, p);
+    cons_and_flux<D>(rho, vel, p, ph.gamma, u, F);
+    bad = bad || !(rho.v > 0.0) || !(p.v > 0.0);
+    if (C::VISC) {
+      Dual<M> Gv[M][D];
+      visc_flux<D>(vd, q, ph, Gv);
+      for (int i = 0; i < M; ++i)
+        for (int j = 0; j < D; ++j) F[i][j] = F[i][j] + Gv[i][j];
+    }
+    double* out = a.ptv + (le * NG + g) * C::PT_VOL;
+    double* MU = out;
+    double* FR = MU + M;
+    double* T0 = FR + D * M;
+    double* T1 = T0 + M * M;
+    double* T2 = T1 + D * M * M;
+    for (int i = 0; i < M; ++i) {
+      MU[i] = W * a.mass_coef * u[i].v;
+      for (int l = 0; l < M; ++l) T0[i * M + l] = W * a.mass_coef * u[i].d[l];
+    }
+    for (int r = 0; r < D; ++r)
+      for (int i = 0; i < M; ++i) {
+        double s = 0.0;
+        for (int j = 0; j < D; ++j) s += Jinv[r * D + j] * F[i][j].v;
+        FR[r * M + i] = -W * s;
+        for (int l = 0; l < M; ++l) {
+          double t = 0.0;
+          for (int j = 0; j < D; ++j) t += Jinv[r * D + j] * F[i][j].d[l];
+          T1[(r * M + i) * M + l] = -W * t;
+        }
+      }
+    if (C::VISC) {
+      // G is linear in q: dG/dq_lk = G(v, E_lk)
+      for (int l = 0; l < M; ++l)
+        for (int k = 0; k < D; ++k) {
+          double E[M][D];
+          for (int i = 0; i < M; ++i)
+            for (int j = 0; j < D; ++j) E[i][j] = (i == l && j == k) ? 1.0 : 0.0;
+          double Gq[M][D];
+          visc_flux<D>(v, E, ph, Gq);
+          for (int r = 0; r < D; ++r)
+            for (int i = 0; i < M; ++i) {
+              double s = 0.0;
+              for (int j = 0; j < D; ++j) s += Jinv[r * D + j] * Gq[i][j];
+              T2[((r * M + i) * M + l) * D + k] = -W * s;
+            }
+        }
+    }
+  } else if (tid < NG + NF * NGF) {
+    const int f = (tid - NG) / NGF;
+    const int gf = (tid - NG) % NGF;
+    const double* Gf = G + D * D + 1 + f * (D + 1);
+    const double* n = Gf;
+    const double Wf = T.WF[gf] * Gf[D];
+    const double* phif = T.PhiF + (f * NGF + gf) * NP;
+    double v[M], vh[M];
+    for (int i = 0; i < M; ++i) {
+      double s = 0.0, sh = 0.0;
+      for (int b = 0; b < NP; ++b) s += phif[b] * z[b][i];
+      for (int c = 0; c < NFN; ++c) sh += phif[T.fnodes[f * NFN + c]] * z[NP + f * NFN + c][i];
+      v[i] = s;
+      vh[i] = sh;
+    }
+    double q[M][D];
+    if (C::VISC) {
+      for (int i = 0; i < M; ++i) {
+        double gr[D];
+        for (int r = 0; r < D; ++r) {
+          double s = 0.0;
+          for (int b = 0; b < NP; ++b) s += T.dPhiF[((f * D + r) * NGF + gf) * NP + b] * z[b][i];
+          gr[r] = s;
+        }
+        for (int k = 0; k < D; ++k) {
+          double s = 0.0;
+          for (int r = 0; r < D; ++r) s += Jinv[r * D + k] * gr[r];
+          for (int fl = 0; fl < NF; ++fl) {
+            const double* Gl = G + D * D + 1 + fl * (D + 1);
+            double lift = 0.0;
+            for (int c = 0; c < NFN; ++c)
+              lift += T.PLF[((f * NF + fl) * NGF + gf) * NFN + c] *
+                      (z[NP + fl * NFN + c][i] - z[T.fnodes[fl * NFN + c]][i]);
+            s += Gl[k] * (Gl[D] / detJ) * lift;
+          }
+          q[i][k] = s;
+        }
+      }
+    }
+    bad = !(v[M - 1] < 0.0) || !(vh[M - 1] < 0.0);
+    // pass A: derivatives with respect to vhat
+    Dual<M> vhd[M], dvd[M];
+    for (int l = 0; l < M; ++l) {
+      vhd[l] = dconst<M>(vh[l]);
+      vhd[l].d[l] = 1.0;
+      dvd[l] = v[l] - vhd[l];
+    }
+    Dual<M> rh, velh[D], prh, uh[M], Fh[M][D], duh[M];
+    prim_of_v<D>(vhd, ph.gamma, rh, velh, prh);
+    cons_and_flux<D>(rh, velh, prh, ph.gamma, uh, Fh);
+    bad = bad || !(rh.v > 0.0) || !(prh.v > 0.0);
+    Dual<M> lam = lambda_max<D>(rh, velh, prh, n, ph.gamma);
+    du_of_v<D>(vhd, dvd, ph.gamma, duh);
+    Dual<M> hA[M];
+    for (int i = 0; i < M; ++i) {
+      Dual<M> s = Fh[i][0] * n[0];
+      for (int j = 1; j < D; ++j) s = s + Fh[i][j] * n[j];
+      hA[i] = 0.5 * s + 0.5 * (lam * duh[i]);
+    }
+    if (C::VISC) {
+      Dual<M> Gh[M][D];
+      visc_flux<D>(vhd, q, ph, Gh);
+      for (int i = 0; i < M; ++i)
+        for (int j = 0; j < D; ++j) hA[i] = hA[i] + Gh[i][j] * n[j];
+    }
+    // pass B: derivatives with respect to v (F(v).n; the sigma term gives lam A0(vhat))
+    Dual<M> vd[M];
+    for (int l = 0; l < M; ++l) {
+      vd[l] = dconst<M>(v[l]);
+      vd[l].d[l] = 1.0;
+    }
+    Dual<M> rv, velv[D], pv, Fv[M][D];
+    prim_of_v<D>(vd, ph.gamma, rv, velv, pv);
+    cons_and_flux<D>(rv, velv, pv, ph.gamma, (Dual<M>*)nullptr, Fv);
+    bad = bad || !(rv.v > 0.0) || !(pv.v > 0.0);
+    double* out = a.ptf + ((le * NF + f) * NGF + gf) * C::PT_FACE;
+    double* HF = out;
+    double* U0 = HF + M;
+    double* U1 = U0 + M * M;
+    double* U2 = U1 + M * M;
+    for (int i = 0; i < M; ++i) {
+      Dual<M> s = Fv[i][0] * n[0];
+      for (int j = 1; j < D; ++j) s = s + Fv[i][j] * n[j];
+      HF[i] = Wf * (hA[i].v + 0.5 * s.v);
+      for (int l = 0; l < M; ++l) {
+        U0[i * M + l] = Wf * (0.5 * s.d[l] + 0.5 * lam.v * uh[i].d[l]);
+        U1[i * M + l] = Wf * hA[i].d[l];
+      }
+    }
+    if (C::VISC) {
+      for (int l = 0; l < M; ++l)
+        for (int k = 0; k < D; ++k) {
+          double E[M][D];
+          for (int i = 0; i < M; ++i)
+            for (int j = 0; j < D; ++j) E[i][j] = (i == l && j == k) ? 1.0 : 0.0;
+          double Gq[M][D];
+          visc_flux<D>(vh, E, ph, Gq);
+          for (int i = 0; i < M; ++i) {
+            double s = 0.0;
+            for (int j = 0; j < D; ++j) s += Gq[i][j] * n[j];
+            U2[(i * M + l) * D + k] = Wf * s;
+          }
+        }
+    }
+  }
+  if (bad) atomicOr(a.status + e, HDG_STATUS_NONPHYSICAL);
+}
+
+// ------------------------------------------------------------------------------------
+// k_assemble
+// ------------------------------------------------------------------------------------
+template <class C>
+struct AsmSmem {
+  static constexpr int GT = C::NG < 64 ? C::NG : 64;  // volume points per tile
+  static constexpr int RB = C::NR * GT * C::NZ;
+  static constexpr int RBF = C::NRF * C::NGF * C::NZ;
+  static constexpr int RBMAX = RB > RBF ? RB : RBF;
+  static constexpr int ZS = C::NP * GT * C::NR;
+  static constexpr int ZSF = C::NFN * C::NGF * C::NRF;
+  static constexpr int ZSMAX = ZS > ZSF ? ZS : ZSF;
+  static constexpr size_t bytes =
+      sizeof(double) * (RBMAX + ZSMAX + C::NZ * C::M + C::GEO + C::NV + C::NT);
+};
+
+template <class C>
+__global__ void __launch_bounds__(256) k_assemble(AssembleArgs a, DevTables T) {
+  constexpr int D = C::D, M = C::M, NP = C::NP, NFN = C::NFN, NF = C::NF, NG = C::NG, NGF = C::NGF;
+  constexpr int NZ = C::NZ, NV = C::NV, NT = C::NT, NR = C::NR, NRF = C::NRF;
+  using SM = AsmSmem<C>;
+  constexpr int GT = SM::GT;
+  extern __shared__ double smem[];
+  double* Rb = smem;
+  double* Zs = Rb + SM::RBMAX;
+  double(*z)[M] = reinterpret_cast<double(*)[M]>(Zs + SM::ZSMAX);
+  double* G = Zs + SM::ZSMAX + NZ * M;
+  double* Rv = G + C::GEO;
+  double* Rt = Rv + NV;
+  const int64_t le = blockIdx.x;
+  const int64_t e = a.e0 + le;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  load_element<C>(a, e, z, G);
+  __syncthreads();
+  const double* Jinv = G;
+  const double detJ = G[D * D];
+  double* Ap = a.Ap + le * NV * NV;
+  double* Cp = a.Cp + le * NT * NV;
+  double* Bp = a.recov + e * (int64_t)(NV * NT + NV);
+  double* Dp = a.S + e * (int64_t)NT * NT;
+  const double* ptv = a.ptv + le * NG * C::PT_VOL;
+  const double* ptf = a.ptf + le * NF * NGF * C::PT_FACE;
+
+  // residual R_v, volume part
+  for (int t = tid; t < NV; t += nth) {
+    int an = t / M, i = t % M;
+    double s = a.hist ? -a.hist[e * NV + t] : 0.0;
+    for (int g = 0; g < NG; ++g) {
+      const double* P = ptv + g * C::PT_VOL;
+      s += T.Phi[g * NP + an] * P[i];
+      for (int r = 0; r < D; ++r) s += T.dPhi[(r * NG + g) * NP + an] * P[M + r * M + i];
+    }
+    Rv[t] = s;
+  }
+
+  // ---------------- volume contractions ----------------
+  for (int g0 = 0; g0 < NG; g0 += GT) {
+    const int ng = (NG - g0) < GT ? (NG - g0) : GT;
+    __syncthreads();
+    // right operators Rb[beta][gg][j]
+    for (int t = tid; t < NR * GT * NZ; t += nth) {
+      int beta = t / (GT * NZ), gg = (t / NZ) % GT, j = t % NZ;
+      double val = 0.0;
+      if (gg < ng) {
+        int g = g0 + gg;
+        if (beta == 0) {
+          val = j < NP ? T.Phi[g * NP + j] : 0.0;
+        } else {
+          int k = beta - 1;
+          if (j < NP) {
+            for (int r = 0; r < D; ++r) val += Jinv[r * D + k] * T.dPhi[(r * NG + g) * NP + j];
+            for (int f = 0; f < NF; ++f) {
+              int c = T.nodepos[f * NP + j];
+              if (c >= 0) {
+                const double* Gf = G + D * D + 1 + f * (D + 1);
+                val -= Gf[k] * (Gf[D] / detJ) * T.PL[(f * NG + g) * NFN + c];
+              }
+            }
+          } else {
+            int f = (j - NP) / NFN, c = (j - NP) % NFN;
+            const double* Gf = G + D * D + 1 + f * (D + 1);
+            val = Gf[k] * (Gf[D] / detJ) * T.PL[(f * NG + g) * NFN + c];
+          }
+        }
+      }
+      Rb[t] = val;
+    }
+    for (int il = 0; il < M * M; ++il) {
+      const int i = il / M, l = il % M;
+      __syncthreads();
+      // Zs[a][gg][beta] = sum_alpha L_alpha(g, a) C^{il}_{alpha beta}(g)
+      for (int t = tid; t < NP * GT * NR; t += nth) {
+        int an = t / (GT * NR), gg = (t / NR) % GT, beta = t % NR;
+        double val = 0.0;
+        if (gg < ng) {
+          int g = g0 + gg;
+          const double* P = ptv + g * C::PT_VOL;
+          const double* T0 = P + M + D * M;
+          const double* T1 = T0 + M * M;
+          const double* T2 = T1 + D * M * M;
+          if (beta == 0) {
+            val = T.Phi[g * NP + an] * T0[i * M + l];
+            for (int r = 0; r < D; ++r) val += T.dPhi[(r * NG + g) * NP + an] * T1[(r * M + i) * M + l];
+          } else {
+            int k = beta - 1;
+            for (int r = 0; r < D; ++r)
+              val += T.dPhi[(r * NG + g) * NP + an] * T2[((r * M + i) * M + l) * D + k];
+          }
+        }
+        Zs[t] = val;
+      }
+      __syncthreads();
+      for (int t = tid; t < NP * NZ; t += nth) {
+        int an = t / NZ, j = t % NZ;
+        const int b0 = j < NP ? 0 : 1;
+        double acc = 0.0;
+        for (int gg = 0; gg < ng; ++gg)
+          for (int beta = b0; beta < NR; ++beta) acc += Zs[(an * GT + gg) * NR + beta] * Rb[(beta * GT + gg) * NZ + j];
+        int row = an * M + i;
+        if (j < NP) {
+          double* dst = Ap + row * NV + j * M + l;
+          *dst = (g0 == 0) ? acc : *dst + acc;
+        } else {
+          double* dst = Bp + row * NT + (j - NP) * M + l;
+          *dst = (g0 == 0) ? acc : *dst + acc;
+        }
+      }
+    }
+  }
+
+  // ---------------- face contractions ----------------
+  for (int f = 0; f < NF; ++f) {
+    __syncthreads();
+    const double* Gf = G + D * D + 1 + f * (D + 1);
+    for (int t = tid; t < NRF * NGF * NZ; t += nth) {
+      int beta = t / (NGF * NZ), gf = (t / NZ) % NGF, j = t % NZ;
+      const double* phif = T.PhiF + (f * NGF + gf) * NP;
+      double val = 0.0;
+      if (beta == 0) {
+        val = j < NP ? phif[j] : 0.0;
+      } else if (beta == 1) {
+        if (j >= NP && (j - NP) / NFN == f) val = phif[T.fnodes[f * NFN + (j - NP) % NFN]];
+      } else {
+        int k = beta - 2;
+        if (j < NP) {
+          for (int r = 0; r < D; ++r) val += Jinv[r * D + k] * T.dPhiF[((f * D + r) * NGF + gf) * NP + j];
+          for (int fl = 0; fl < NF; ++fl) {
+            int c = T.nodepos[fl * NP + j];
+            if (c >= 0) {
+              const double* Gl = G + D * D + 1 + fl * (D + 1);
+              val -= Gl[k] * (Gl[D] / detJ) * T.PLF[((f * NF + fl) * NGF + gf) * NFN + c];
+            }
+          }
+        } else {
+          int fl = (j - NP) / NFN, c = (j - NP) % NFN;
+          const double* Gl = G + D * D + 1 + fl * (D + 1);
+          val = Gl[k] * (Gl[D] / detJ) * T.PLF[((f * NF + fl) * NGF + gf) * NFN + c];
+        }
+      }
+      Rb[t] = val;
+    }
+    (void)Gf;
+    // residual: face contribution
+    __syncthreads();
+    for (int t = tid; t < NFN * M; t += nth) {
+      int c = t / M, i = t % M;
+      double s = 0.0;
+      for (int gf = 0; gf < NGF; ++gf) {
+        double psi = T.PhiF[(f * NGF + gf) * NP + T.fnodes[f * NFN + c]];
+        s += psi * ptf[(f * NGF + gf) * C::PT_FACE + i];
+      }
+      Rv[T.fnodes[f * NFN + c] * M + i] += s;
+      Rt[(f * NFN + c) * M + i] = s;
+    }
+    for (int il = 0; il < M * M; ++il) {
+      const int i = il / M, l = il % M;
+      __syncthreads();
+      for (int t = tid; t < NFN * NGF * NRF; t += nth) {
+        int c = t / (NGF * NRF), gf = (t / NRF) % NGF, beta = t % NRF;
+        const double* P = ptf + (f * NGF + gf) * C::PT_FACE;
+        const double* U0 = P + M;
+        const double* U1 = U0 + M * M;
+        const double* U2 = U1 + M * M;
+        double psi = T.PhiF[(f * NGF + gf) * NP + T.fnodes[f * NFN + c]];
+        double u;
+        if (beta == 0)
+          u = U0[i * M + l];
+        else if (beta == 1)
+          u = U1[i * M + l];
+        else
+          u = U2[(i * M + l) * D + (beta - 2)];
+        Zs[t] = psi * u;
+      }
+      __syncthreads();
+      for (int t = tid; t < NFN * NZ; t += nth) {
+        int c = t / NZ, j = t % NZ;
+        double acc = 0.0;
+        for (int gf = 0; gf < NGF; ++gf)
+          for (int beta = 0; beta < NRF; ++beta) acc += Zs[(c * NGF + gf) * NRF + beta] * Rb[(beta * NGF + gf) * NZ + j];
+        int rowv = T.fnodes[f * NFN + c] * M + i;
+        int rowt = (f * NFN + c) * M + i;
+        if (j < NP) {
+          Ap[rowv * NV + j * M + l] += acc;
+          Cp[rowt * NV + j * M + l] = acc;
+        } else {
+          int tcol = (j - NP) * M + l;
+          Bp[rowv * NT + tcol] += acc;
+          Dp[rowt * NT + tcol] = acc;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  double* Rout = a.R + e * (int64_t)(NV + NT);
+  for (int t = tid; t < NV; t += nth) Rout[t] = Rv[t];
+  for (int t = tid; t < NT; t += nth) Rout[NV + t] = Rt[t];
+}
+
+// ------------------------------------------------------------------------------------
+// k_condense
+// ------------------------------------------------------------------------------------
+template <class C>
+struct CondSmem {
+  static constexpr int CB = 64;  // right-hand-side columns per block
+  static constexpr size_t bytes = sizeof(double) * (C::NV * C::NV + C::NV * CB) + sizeof(int) * C::NV + 64;
+};
+
+template <class C>
+__global__ void __launch_bounds__(256) k_condense(AssembleArgs a) {
+  constexpr int NV = C::NV, NT = C::NT;
+  using SM = CondSmem<C>;
+  constexpr int CB = SM::CB;
+  extern __shared__ double smem[];
+  double* LU = smem;                 // [NV][NV]
+  double* Xs = LU + NV * NV;         // [NV][CB]
+  int* piv = reinterpret_cast<int*>(Xs + NV * CB);
+  __shared__ int s_piv;
+  __shared__ int s_bad;
+  const int64_t le = blockIdx.x;
+  const int64_t e = a.e0 + le;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const double* Ap = a.Ap + le * NV * NV;
+  const double* Cp = a.Cp + le * NT * NV;
+  double* X = a.recov + e * (int64_t)(NV * NT + NV);
+  double* y = X + NV * NT;
+  double* S = a.S + e * (int64_t)NT * NT;
+  const double* R = a.R + e * (int64_t)(NV + NT);
+  for (int t = tid; t < NV * NV; t += nth) LU[t] = Ap[t];
+  if (tid == 0) s_bad = 0;
+  __syncthreads();
+  // LU with partial pivoting (row interchanges recorded in piv)
+  for (int k = 0; k < NV; ++k) {
+    if (tid < 32) {
+      double best = -1.0;
+      int bi = k;
+      for (int r = k + tid; r < NV; r += 32) {
+        double v = fabs(LU[r * NV + k]);
+        if (v > best) {
+          best = v;
+          bi = r;
+        }
+      }
+      for (int off = 16; off > 0; off >>= 1) {
+        double ob = __shfl_down_sync(0xffffffffu, best, off);
+        int oi = __shfl_down_sync(0xffffffffu, bi, off);
+        if (ob > best || (ob == best && oi < bi)) {
+          best = ob;
+          bi = oi;
+        }
+      }
+      if (tid == 0) {
+        s_piv = bi;
+        piv[k] = bi;
+        if (!(best > 0.0)) s_bad = 1;
+      }
+    }
+    __syncthreads();
+    const int pr = s_piv;
+    if (pr != k)
+      for (int j = tid; j < NV; j += nth) {
+        double t = LU[k * NV + j];
+        LU[k * NV + j] = LU[pr * NV + j];
+        LU[pr * NV + j] = t;
+      }
+    __syncthreads();
+    const double d = LU[k * NV + k];
+    const double inv = d != 0.0 ? 1.0 / d : 0.0;
+    for (int r = k + 1 + tid; r < NV; r += nth) LU[r * NV + k] *= inv;
+    __syncthreads();
+    const int rem = NV - k - 1;
+    for (int t = tid; t < rem * rem; t += nth) {
+      int r = k + 1 + t / rem, c = k + 1 + t % rem;
+      LU[r * NV + c] -= LU[r * NV + k] * LU[k * NV + c];
+    }
+    __syncthreads();
+  }
+  if (tid == 0 && s_bad) atomicOr(a.status + e, HDG_STATUS_SINGULAR);
+  // X = A'^{-1} [B' | R_v] in column blocks (B' stored in X)
+  for (int c0 = 0; c0 < NT + 1; c0 += CB) {
+    const int nc = (NT + 1 - c0) < CB ? (NT + 1 - c0) : CB;
+    __syncthreads();
+    for (int t = tid; t < NV * CB; t += nth) {
+      int r = t / CB, c = t % CB;
+      int col = c0 + c;
+      double v = 0.0;
+      if (c < nc) v = col < NT ? X[r * NT + col] : R[r];
+      Xs[t] = v;
+    }
+    __syncthreads();
+    // apply the row interchanges in order
+    for (int t = tid; t < CB; t += nth)
+      for (int k = 0; k < NV; ++k) {
+        int p = piv[k];
+        if (p != k) {
+          double tmp = Xs[k * CB + t];
+          Xs[k * CB + t] = Xs[p * CB + t];
+          Xs[p * CB + t] = tmp;
+        }
+      }
+    __syncthreads();
+    for (int k = 0; k < NV; ++k) {  // forward, unit lower
+      for (int t = tid; t < (NV - k - 1) * CB; t += nth) {
+        int r = k + 1 + t / CB, c = t % CB;
+        Xs[r * CB + c] -= LU[r * NV + k] * Xs[k * CB + c];
+      }
+      __syncthreads();
+    }
+    for (int k = NV - 1; k >= 0; --k) {  // backward, upper
+      for (int c = tid; c < CB; c += nth) Xs[k * CB + c] /= LU[k * NV + k];
+      __syncthreads();
+      for (int t = tid; t < k * CB; t += nth) {
+        int r = t / CB, c = t % CB;
+        Xs[r * CB + c] -= LU[r * NV + k] * Xs[k * CB + c];
+      }
+      __syncthreads();
+    }
+    for (int t = tid; t < NV * CB; t += nth) {
+      int r = t / CB, c = t % CB;
+      int col = c0 + c;
+      if (c < nc) {
+        if (col < NT)
+          X[r * NT + col] = Xs[t];
+        else
+          y[r] = Xs[t];
+      }
+    }
+  }
+  __syncthreads();
+  // S = D' - C' X ; g = R_t - C' y
+  for (int t = tid; t < NT * NT; t += nth) {
+    int r = t / NT, c = t % NT;
+    double s = S[t];
+    const double* Cr = Cp + r * NV;
+    for (int k = 0; k < NV; ++k) s -= Cr[k] * X[k * NT + c];
+    S[t] = s;
+  }
+  double* g = a.g + e * NT;
+  for (int r = tid; r < NT; r += nth) {
+    double s = R[NV + r];
+    const double* Cr = Cp + r * NV;
+    for (int k = 0; k < NV; ++k) s -= Cr[k] * y[k];
+    g[r] = s;
+  }
+}
+
+}  // namespace hdg

@@ -1,0 +1,423 @@
+// C-ABI entry points (include/hdg.h): argument checks, context set-up, device table
+// upload, and the Newton-step driver. All numerical work runs in the kernels of
+// assemble_fp64.cu, assemble_mixed.cu and trace.cu.
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ctx.hpp"
+
+namespace hdg {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+int cuda_fail(cudaError_t err, const char* what) {
+  g_last_error = std::string(what) + ": " + cudaGetErrorString(err);
+  return HDG_ERR_CUDA;
+}
+
+}  // namespace hdg
+
+using hdg::set_error;
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+template <class T>
+int upload(T** dst, const std::vector<T>& src) {
+  HDG_CK(cudaMalloc(dst, sizeof(T) * std::max<size_t>(1, src.size())));
+  if (!src.empty()) HDG_CK(cudaMemcpy(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice));
+  return HDG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* hdg_last_error(void) { return hdg::g_last_error.c_str(); }
+
+int hdg_mesh_create(int dim, const int64_t n[3], const double lo[3], const double hi[3], int p, int quad_points,
+                    hdg_mesh_t* out) {
+  if (!out || !n || !lo || !hi) {
+    set_error("hdg_mesh_create: null argument");
+    return HDG_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  if (quad_points == 0) quad_points = p + 1;
+  auto* m = new hdg_mesh();
+  int rc = hdg::build_mesh(dim, n, lo, hi, p, quad_points, m->m);
+  if (rc != 0) {
+    delete m;
+    set_error("hdg_mesh_create: invalid mesh arguments (code " + std::to_string(rc) + ")");
+    return HDG_ERR_INVALID_ARG;
+  }
+  *out = m;
+  return HDG_OK;
+}
+
+void hdg_mesh_destroy(hdg_mesh_t mesh) { delete mesh; }
+
+int hdg_mesh_get_info(hdg_mesh_t mesh, hdg_mesh_info* out) {
+  if (!mesh || !out) {
+    set_error("hdg_mesh_get_info: null argument");
+    return HDG_ERR_INVALID_ARG;
+  }
+  const hdg::Mesh& m = mesh->m;
+  out->dim = m.dim;
+  out->p = m.p;
+  out->quad_points = m.K;
+  out->m = m.dim + 2;
+  out->Np = m.ref.Np;
+  out->Nf = m.ref.Nf;
+  out->nF = m.ref.nF;
+  out->NG = m.ref.NG;
+  out->NGF = m.ref.NGF;
+  out->nv = m.ref.Np * (m.dim + 2);
+  out->nt = m.ref.nF * m.ref.Nf * (m.dim + 2);
+  out->geo_stride = m.geo_stride;
+  out->n_elem = m.E;
+  out->n_faces = m.nFaces;
+  out->n_trace = m.nFaces * m.ref.Nf * (m.dim + 2);
+  return HDG_OK;
+}
+
+int hdg_mesh_copy_topology(hdg_mesh_t mesh, int32_t* face_of, int32_t* fnode_map, int32_t* face_side) {
+  if (!mesh) {
+    set_error("hdg_mesh_copy_topology: null mesh");
+    return HDG_ERR_INVALID_ARG;
+  }
+  const hdg::Mesh& m = mesh->m;
+  if (face_of) std::memcpy(face_of, m.face_of.data(), sizeof(int32_t) * m.face_of.size());
+  if (fnode_map) std::memcpy(fnode_map, m.fnode_map.data(), sizeof(int32_t) * m.fnode_map.size());
+  if (face_side) std::memcpy(face_side, m.face_side.data(), sizeof(int32_t) * m.face_side.size());
+  return HDG_OK;
+}
+
+int hdg_mesh_copy_coords(hdg_mesh_t mesh, double* xnode, double* xfnode, double* geo) {
+  if (!mesh) {
+    set_error("hdg_mesh_copy_coords: null mesh");
+    return HDG_ERR_INVALID_ARG;
+  }
+  const hdg::Mesh& m = mesh->m;
+  if (xnode) std::memcpy(xnode, m.xnode.data(), sizeof(double) * m.xnode.size());
+  if (xfnode) std::memcpy(xfnode, m.xfnode.data(), sizeof(double) * m.xfnode.size());
+  if (geo) std::memcpy(geo, m.geo.data(), sizeof(double) * m.geo.size());
+  return HDG_OK;
+}
+
+int hdg_ctx_create(hdg_mesh_t mesh, const hdg_physics* phys, int device, hdg_ctx_t* out) {
+  if (!mesh || !phys || !out) {
+    set_error("hdg_ctx_create: null argument");
+    return HDG_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  if (!(phys->gamma > 1.0) || !(phys->mach > 0.0) || phys->reynolds < 0.0 || !(phys->prandtl > 0.0)) {
+    set_error("hdg_ctx_create: invalid physics parameters");
+    return HDG_ERR_INVALID_ARG;
+  }
+  const hdg::Mesh& m = mesh->m;
+  const bool visc = phys->reynolds > 0.0;
+  if (!hdg::config_supported(m.dim, m.p, m.K, visc)) {
+    set_error("hdg_ctx_create: (dim, p, quad_points, physics) not compiled in");
+    return HDG_ERR_UNSUPPORTED;
+  }
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    set_error("hdg_ctx_create: no such CUDA device");
+    return HDG_ERR_CUDA;
+  }
+  DeviceGuard guard(device);
+  auto* c = new hdg_ctx();
+  c->mesh = mesh;
+  c->device = device;
+  c->visc = visc;
+  const double g = phys->gamma;
+  c->ph.gamma = g;
+  c->ph.cv = 1.0 / (g * (g - 1.0) * phys->mach * phys->mach);
+  c->ph.mu = visc ? 1.0 / phys->reynolds : 0.0;
+  c->ph.kappa = g * c->ph.cv * c->ph.mu / phys->prandtl;
+  c->dim = m.dim;
+  c->p = m.p;
+  c->K = m.K;
+  c->M = m.dim + 2;
+  c->NP = m.ref.Np;
+  c->NFN = m.ref.Nf;
+  c->NF = m.ref.nF;
+  c->NG = m.ref.NG;
+  c->NGF = m.ref.NGF;
+  c->NV = c->NP * c->M;
+  c->NT = c->NF * c->NFN * c->M;
+  c->GEO = m.geo_stride;
+  c->E = m.E;
+  c->F = m.nFaces;
+  c->ntrace = m.nFaces * m.ref.Nf * c->M;
+  if (const char* ch = std::getenv("HDG_ELEMENT_CHUNK")) {
+    long v = std::strtol(ch, nullptr, 10);
+    if (v > 0) c->chunk = std::min<int64_t>(v, c->E);
+  }
+
+  hdg::RefTables T = hdg::make_tables(m.ref);
+  std::vector<double> tab;
+  size_t off[8];
+  const std::vector<double>* parts[8] = {&T.W, &T.Phi, &T.dPhi, &T.PL, &T.WF, &T.PhiF, &T.dPhiF, &T.PLF};
+  for (int i = 0; i < 8; ++i) {
+    off[i] = tab.size();
+    tab.insert(tab.end(), parts[i]->begin(), parts[i]->end());
+  }
+  std::vector<int> itab(T.fnodes);
+  const size_t npos_off = itab.size();
+  std::vector<int> nodepos(c->NF * c->NP, -1);
+  for (int f = 0; f < c->NF; ++f)
+    for (int cc = 0; cc < c->NFN; ++cc) nodepos[f * c->NP + T.fnodes[f * c->NFN + cc]] = cc;
+  itab.insert(itab.end(), nodepos.begin(), nodepos.end());
+
+  // element -> canonical face node; face sides
+  std::vector<int> tgidx(c->E * c->NF * c->NFN);
+  for (int64_t e = 0; e < c->E; ++e)
+    for (int f = 0; f < c->NF; ++f)
+      for (int cc = 0; cc < c->NFN; ++cc)
+        tgidx[(e * c->NF + f) * c->NFN + cc] =
+            m.face_of[e * c->NF + f] * c->NFN + m.fnode_map[(e * c->NF + f) * c->NFN + cc];
+  std::vector<int> fs_elem(2 * c->F), fs_loc(2 * c->F * c->NFN);
+  for (int64_t F = 0; F < c->F; ++F)
+    for (int sd = 0; sd < 2; ++sd) {
+      int32_t ef = m.face_side[2 * F + sd];
+      int64_t e = ef / c->NF;
+      int f = ef % c->NF;
+      fs_elem[2 * F + sd] = (int)e;
+      for (int cc = 0; cc < c->NFN; ++cc) {
+        int canon = m.fnode_map[(e * c->NF + f) * c->NFN + cc];
+        fs_loc[(2 * F + sd) * c->NFN + canon] = f * c->NFN + cc;
+      }
+    }
+  int rc = HDG_OK;
+  if ((rc = upload(&c->d_tab, tab)) || (rc = upload(&c->d_itab, itab)) || (rc = upload(&c->d_tgidx, tgidx)) ||
+      (rc = upload(&c->d_geo, m.geo)) || (rc = upload(&c->d_fs_elem, fs_elem)) || (rc = upload(&c->d_fs_loc, fs_loc))) {
+    hdg_ctx_destroy(c);
+    return rc;
+  }
+  c->T.W = c->d_tab + off[0];
+  c->T.Phi = c->d_tab + off[1];
+  c->T.dPhi = c->d_tab + off[2];
+  c->T.PL = c->d_tab + off[3];
+  c->T.WF = c->d_tab + off[4];
+  c->T.PhiF = c->d_tab + off[5];
+  c->T.dPhiF = c->d_tab + off[6];
+  c->T.PLF = c->d_tab + off[7];
+  c->T.fnodes = c->d_itab;
+  c->T.nodepos = c->d_itab + npos_off;
+  *out = c;
+  return HDG_OK;
+}
+
+void hdg_ctx_destroy(hdg_ctx_t c) {
+  if (!c) return;
+  DeviceGuard guard(c->device);
+  void* bufs[] = {c->d_tab, c->d_itab, c->d_tgidx, c->d_geo, c->d_fs_elem, c->d_fs_loc, c->d_scr,
+                  c->d_sw, c->d_pc, c->d_pcpiv, c->d_dense, c->d_dpiv, c->d_red, c->d_S,
+                  c->d_g, c->d_recov, c->d_R, c->d_dV, c->d_dVh, c->d_status};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  if (c->h_red) cudaFreeHost(c->h_red);
+  for (auto& r : c->pending) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  delete c;
+}
+
+#define HDG_REQUIRE(cond, msg)  \
+  do {                          \
+    if (!(cond)) {              \
+      set_error(msg);           \
+      return HDG_ERR_INVALID_ARG; \
+    }                           \
+  } while (0)
+
+int hdg_prim_to_entropy(hdg_ctx_t ctx, const double* prim, int64_t n_points, double* v, void* stream) {
+  HDG_REQUIRE(ctx && prim && v && n_points >= 0, "hdg_prim_to_entropy: invalid argument");
+  DeviceGuard guard(ctx->device);
+  return hdg::launch_prim_to_entropy(ctx, prim, n_points, v, (cudaStream_t)stream);
+}
+
+int hdg_history(hdg_ctx_t ctx, const double* V0, const double* V1, double c0, double c1, double* hist,
+                void* stream) {
+  HDG_REQUIRE(ctx && V0 && hist, "hdg_history: invalid argument");
+  DeviceGuard guard(ctx->device);
+  return hdg::launch_history(ctx, V0, V1, c0, c1, hist, (cudaStream_t)stream);
+}
+
+int hdg_assemble_condense(hdg_ctx_t ctx, const double* V, const double* Vhat, const double* hist, double mass_coef,
+                          int precision, double* S, double* g, double* recov, double* R, int32_t* elem_status,
+                          void* stream) {
+  HDG_REQUIRE(ctx && V && Vhat && S && g && recov && R, "hdg_assemble_condense: null argument");
+  HDG_REQUIRE(precision == HDG_PREC_FP64 || precision == HDG_PREC_MIXED, "hdg_assemble_condense: precision");
+  DeviceGuard guard(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  int32_t* st = elem_status;
+  if (!st) {
+    if (!ctx->d_status) HDG_CK(cudaMalloc(&ctx->d_status, sizeof(int32_t) * ctx->E));
+    HDG_CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int32_t) * ctx->E, s));
+    st = ctx->d_status;
+  }
+  if (precision == HDG_PREC_MIXED)
+    return hdg::assemble_condense_mixed(ctx, V, Vhat, hist, mass_coef, S, g, recov, R, st, s);
+  return hdg::assemble_condense_fp64(ctx, V, Vhat, hist, mass_coef, S, g, recov, R, st, s);
+}
+
+int hdg_trace_solve(hdg_ctx_t ctx, const double* S, const double* g, double* dVhat, int method, double rtol,
+                    int max_it, int* iters, double* final_res, void* stream) {
+  HDG_REQUIRE(ctx && S && g && dVhat && iters && final_res, "hdg_trace_solve: null argument");
+  HDG_REQUIRE(method >= HDG_SOLVER_AUTO && method <= HDG_SOLVER_DENSE && rtol > 0.0 && max_it > 0,
+              "hdg_trace_solve: invalid method / tolerance");
+  DeviceGuard guard(ctx->device);
+  return hdg::trace_solve(ctx, S, g, dVhat, method, rtol, max_it, iters, final_res, (cudaStream_t)stream);
+}
+
+int hdg_recover_interior(hdg_ctx_t ctx, const double* recov, const double* dVhat, double* dV, void* stream) {
+  HDG_REQUIRE(ctx && recov && dVhat && dV, "hdg_recover_interior: null argument");
+  DeviceGuard guard(ctx->device);
+  return hdg::launch_recover(ctx, recov, dVhat, dV, (cudaStream_t)stream);
+}
+
+int hdg_trace_matvec(hdg_ctx_t ctx, const double* S, const double* x, double* y, void* stream) {
+  HDG_REQUIRE(ctx && S && x && y, "hdg_trace_matvec: null argument");
+  DeviceGuard guard(ctx->device);
+  double* work = nullptr;
+  HDG_CK(cudaMallocAsync(&work, sizeof(double) * ctx->E * ctx->NT, (cudaStream_t)stream));
+  int rc = hdg::launch_trace_matvec(ctx, S, x, y, work, (cudaStream_t)stream);
+  cudaFreeAsync(work, (cudaStream_t)stream);
+  return rc;
+}
+
+int hdg_residual_norm(hdg_ctx_t ctx, const double* R, double* norm, void* stream) {
+  HDG_REQUIRE(ctx && R && norm, "hdg_residual_norm: null argument");
+  DeviceGuard guard(ctx->device);
+  return hdg::residual_norm(ctx, R, norm, (cudaStream_t)stream);
+}
+
+int hdg_profile_enable(hdg_ctx_t ctx, int on) {
+  HDG_REQUIRE(ctx, "hdg_profile_enable: null context");
+  ctx->prof = on != 0;
+  return HDG_OK;
+}
+
+static int drain_profile(hdg_ctx_t ctx) {
+  for (auto& r : ctx->pending) {
+    HDG_CK(cudaEventSynchronize(r.b));
+    float ms = 0.f;
+    HDG_CK(cudaEventElapsedTime(&ms, r.a, r.b));
+    ctx->prof_ms[r.cls] += ms;
+    ctx->prof_n[r.cls] += 1;
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  ctx->pending.clear();
+  return HDG_OK;
+}
+
+int hdg_profile_reset(hdg_ctx_t ctx) {
+  HDG_REQUIRE(ctx, "hdg_profile_reset: null context");
+  DeviceGuard guard(ctx->device);
+  int rc = drain_profile(ctx);
+  for (int k = 0; k < HDG_KERNEL_CLASSES; ++k) {
+    ctx->prof_ms[k] = 0.0;
+    ctx->prof_n[k] = 0;
+    ctx->launches[k] = 0;
+  }
+  return rc;
+}
+
+int hdg_profile_read(hdg_ctx_t ctx, int kernel_class, int64_t* launches, double* total_ms) {
+  HDG_REQUIRE(ctx && launches && total_ms && kernel_class >= -1 && kernel_class < HDG_KERNEL_CLASSES,
+              "hdg_profile_read: invalid argument");
+  DeviceGuard guard(ctx->device);
+  int rc = drain_profile(ctx);
+  if (rc) return rc;
+  *launches = 0;
+  *total_ms = 0.0;
+  for (int k = 0; k < HDG_KERNEL_CLASSES; ++k)
+    if (kernel_class < 0 || k == kernel_class) {
+      *launches += ctx->launches[k];
+      *total_ms += ctx->prof_ms[k];
+    }
+  return HDG_OK;
+}
+
+int hdg_newton_step(hdg_ctx_t ctx, double* V, double* Vhat, const double* hist, double mass_coef, int precision,
+                    double tol, int max_newton, int* newton_iters, double* res_norm, void* stream) {
+  HDG_REQUIRE(ctx && V && Vhat && newton_iters && res_norm && tol > 0.0 && max_newton >= 0,
+              "hdg_newton_step: invalid argument");
+  DeviceGuard guard(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t E = ctx->E;
+  if (!ctx->d_S) {
+    HDG_CK(cudaMalloc(&ctx->d_S, sizeof(double) * E * ctx->NT * ctx->NT));
+    HDG_CK(cudaMalloc(&ctx->d_g, sizeof(double) * E * ctx->NT));
+    HDG_CK(cudaMalloc(&ctx->d_recov, sizeof(double) * E * (ctx->NV * ctx->NT + ctx->NV)));
+    HDG_CK(cudaMalloc(&ctx->d_R, sizeof(double) * E * (ctx->NV + ctx->NT)));
+    HDG_CK(cudaMalloc(&ctx->d_dV, sizeof(double) * E * ctx->NV));
+    HDG_CK(cudaMalloc(&ctx->d_dVh, sizeof(double) * ctx->ntrace));
+  }
+  if (!ctx->d_status) HDG_CK(cudaMalloc(&ctx->d_status, sizeof(int32_t) * E));
+  std::vector<int32_t> hstat;
+  double r0 = -1.0, rn = 0.0;
+  *newton_iters = 0;
+  for (int it = 0;; ++it) {
+    HDG_CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int32_t) * E, s));
+    int rc = hdg_assemble_condense(ctx, V, Vhat, hist, mass_coef, precision, ctx->d_S, ctx->d_g, ctx->d_recov,
+                                   ctx->d_R, ctx->d_status, s);
+    if (rc) return rc;
+    rc = hdg::residual_norm(ctx, ctx->d_R, &rn, s);
+    if (rc) return rc;
+    hstat.resize(E);
+    HDG_CK(cudaMemcpyAsync(hstat.data(), ctx->d_status, sizeof(int32_t) * E, cudaMemcpyDeviceToHost, s));
+    HDG_CK(cudaStreamSynchronize(s));
+    int bits = 0;
+    for (int32_t b : hstat) bits |= b;
+    *res_norm = rn;
+    if (bits & HDG_ELEM_NONPHYSICAL) {
+      set_error("hdg_newton_step: non-physical state");
+      return HDG_ERR_NONPHYSICAL;
+    }
+    if (bits & HDG_ELEM_SINGULAR) {
+      set_error("hdg_newton_step: singular element matrix");
+      return HDG_ERR_SINGULAR;
+    }
+    if (r0 < 0.0) r0 = rn;
+    if (rn <= tol * std::max(1.0, r0)) return HDG_OK;
+    if (it >= max_newton) {
+      set_error("hdg_newton_step: Newton did not converge");
+      return HDG_ERR_NOT_CONVERGED;
+    }
+    int iters = 0;
+    double fres = 0.0;
+    rc = hdg::trace_solve(ctx, ctx->d_S, ctx->d_g, ctx->d_dVh, HDG_SOLVER_AUTO, 1e-12, 600, &iters, &fres, s);
+    if (rc) return rc;
+    rc = hdg::launch_recover(ctx, ctx->d_recov, ctx->d_dVh, ctx->d_dV, s);
+    if (rc) return rc;
+    rc = hdg::launch_axpy(E * ctx->NV, 1.0, ctx->d_dV, V, s);
+    if (rc) return rc;
+    rc = hdg::launch_axpy(ctx->ntrace, 1.0, ctx->d_dVh, Vhat, s);
+    if (rc) return rc;
+    *newton_iters = it + 1;
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,114 @@
+// Internal context shared by the C-ABI translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/hdg.h"
+#include "hdg_device.cuh"
+#include "mesh.hpp"
+
+struct hdg_mesh {
+  hdg::Mesh m;
+};
+
+struct hdg_ctx {
+  hdg_mesh* mesh = nullptr;
+  int device = 0;
+  hdg::PhysParams ph{};
+  bool visc = false;
+  int dim = 0, p = 0, K = 0, M = 0, NP = 0, NFN = 0, NF = 0, NG = 0, NGF = 0, NV = 0, NT = 0, GEO = 0;
+  int64_t E = 0, F = 0, ntrace = 0;
+  // device tables
+  double* d_tab = nullptr;
+  int* d_itab = nullptr;
+  hdg::DevTables T{};
+  int* d_tgidx = nullptr;    // [E][NF][NFN] canonical global face node of each local face node
+  double* d_geo = nullptr;   // [E][GEO]
+  int* d_fs_elem = nullptr;  // [F][2] element of each side (owner first)
+  int* d_fs_loc = nullptr;   // [F][2][NFN] local face-node row (f*NFN + c) for canonical node
+  // assembly scratch (chunked over elements)
+  int64_t chunk = 0;
+  double* d_scr = nullptr;
+  size_t scr_bytes = 0;
+  // solver scratch
+  double* d_sw = nullptr;    // GMRES / matvec workspace
+  size_t sw_bytes = 0;
+  double* d_pc = nullptr;    // face-block Jacobi factors [F][B][B]
+  int* d_pcpiv = nullptr;    // [F][B]
+  double* d_dense = nullptr; // dense trace matrix for the direct solver
+  int* d_dpiv = nullptr;
+  size_t dense_n = 0;
+  double* d_red = nullptr;   // reduction buffer (device)
+  double* h_red = nullptr;   // pinned host mirror
+  // Newton workspace
+  double *d_S = nullptr, *d_g = nullptr, *d_recov = nullptr, *d_R = nullptr, *d_dV = nullptr, *d_dVh = nullptr;
+  int32_t* d_status = nullptr;
+  // measurement: launch counts per kernel class and (when enabled) event pairs
+  bool prof = false;
+  int64_t launches[HDG_KERNEL_CLASSES] = {0};
+  struct EvRec {
+    int cls;
+    cudaEvent_t a, b;
+  };
+  std::vector<EvRec> pending;
+  double prof_ms[HDG_KERNEL_CLASSES] = {0};
+  int64_t prof_n[HDG_KERNEL_CLASSES] = {0};
+};
+
+namespace hdg {
+
+void set_error(const std::string& msg);
+int cuda_fail(cudaError_t err, const char* what);
+
+#define HDG_CK(call)                                           \
+  do {                                                         \
+    cudaError_t _e = (call);                                   \
+    if (_e != cudaSuccess) return ::hdg::cuda_fail(_e, #call); \
+  } while (0)
+
+// Launch bracketing for the measurement hooks (see hdg_profile_read).
+struct LaunchScope {
+  hdg_ctx* c;
+  int cls;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr, b = nullptr;
+  LaunchScope(hdg_ctx* ctx, int k, cudaStream_t st) : c(ctx), cls(k), s(st) {
+    c->launches[cls]++;
+    if (c->prof) {
+      cudaEventCreate(&a);
+      cudaEventCreate(&b);
+      cudaEventRecord(a, s);
+    }
+  }
+  ~LaunchScope() {
+    if (a) {
+      cudaEventRecord(b, s);
+      c->pending.push_back({cls, a, b});
+    }
+  }
+};
+
+// assemble + condense (assemble_fp64.cu / assemble_mixed.cu)
+int assemble_condense_fp64(hdg_ctx* ctx, const double* V, const double* Vhat, const double* hist, double mass_coef,
+                           double* S, double* g, double* recov, double* R, int32_t* status, cudaStream_t s);
+int assemble_condense_mixed(hdg_ctx* ctx, const double* V, const double* Vhat, const double* hist,
+                            double mass_coef, double* S, double* g, double* recov, double* R, int32_t* status,
+                            cudaStream_t s);
+bool config_supported(int dim, int p, int K, bool visc);
+
+// trace-space and element helpers (trace.cu)
+int launch_prim_to_entropy(hdg_ctx* ctx, const double* prim, int64_t n, double* v, cudaStream_t s);
+int launch_history(hdg_ctx* ctx, const double* V0, const double* V1, double c0, double c1, double* hist,
+                   cudaStream_t s);
+int launch_trace_matvec(hdg_ctx* ctx, const double* S, const double* x, double* y, double* work, cudaStream_t s);
+int launch_trace_rhs(hdg_ctx* ctx, const double* g, double* rhs, cudaStream_t s);
+int launch_recover(hdg_ctx* ctx, const double* recov, const double* dVhat, double* dV, cudaStream_t s);
+int residual_norm(hdg_ctx* ctx, const double* R, double* norm, cudaStream_t s);
+int trace_solve(hdg_ctx* ctx, const double* S, const double* g, double* dVhat, int method, double rtol, int max_it,
+                int* iters, double* final_res, cudaStream_t s);
+int launch_axpy(int64_t n, double a, const double* x, double* y, cudaStream_t s);
+
+}  // namespace hdg

@@ -1,0 +1,342 @@
+// Device-side building blocks: compile-time element sizes, forward-mode dual
+// numbers, and the pointwise physics of the entropy-variable formulation.
+//
+// Physics (paper Sec. 2): m = d + 2 conserved variables u = (rho, rho V, rho E),
+// inviscid flux F (Eq. flux), viscous flux G (Eqs. viscFlux, closuresNS) and the
+// entropy variables v = dH/du for H = -rho s (Sec. 2.3). The inverse map u(v) is not
+// printed; from v(u):  s = gamma - v_1 + |w|^2 / (2 v_m),
+//   log rho = (log(gamma-1) - log(-v_m) - s) / (gamma-1),
+//   p = rho (gamma-1) / (-v_m),  V = -w / v_m,  w = (v_2..v_{d+1}).
+// Nondimensionalisation: c_v = 1/(gamma (gamma-1) M^2), mu = 1/Re,
+// kappa = gamma c_v mu / Pr, beta = 0.
+#pragma once
+#include <cstdint>
+
+#define HDG_DEVI __device__ __forceinline__
+
+namespace hdg {
+
+constexpr int cbinom(int n, int k) { return k == 0 ? 1 : (n * cbinom(n - 1, k - 1)) / k; }
+constexpr int cipow(int b, int e) { return e == 0 ? 1 : b * cipow(b, e - 1); }
+
+template <int D_, int P_, int K_, bool VISC_>
+struct Cfg {
+  static constexpr int D = D_, P = P_, K = K_;
+  static constexpr bool VISC = VISC_;
+  static constexpr int M = D + 2;
+  static constexpr int NP = cbinom(P + D, D);
+  static constexpr int NFN = cbinom(P + D - 1, D - 1);
+  static constexpr int NF = D + 1;
+  static constexpr int NG = cipow(K, D);
+  static constexpr int NGF = cipow(K, D - 1);
+  static constexpr int NV = NP * M;            // interior unknowns (v) per element
+  static constexpr int NT = NF * NFN * M;      // trace unknowns per element
+  static constexpr int NZ = NP + NF * NFN;     // nodal unknowns per component
+  static constexpr int GEO = D * D + 1 + NF * (D + 1);
+  static constexpr int NR = VISC ? D + 1 : 1;  // volume right operators: value (+ grad)
+  static constexpr int NRF = VISC ? D + 2 : 2; // face right operators: v, vhat (+ grad)
+  // per-point tensors written by the pointwise kernel
+  static constexpr int PT_VOL = M + D * M + M * M + D * M * M + (VISC ? D * M * M * D : 0);
+  static constexpr int PT_FACE = M + 2 * M * M + (VISC ? M * M * D : 0);
+};
+
+struct PhysParams {
+  double gamma, cv, mu, kappa;
+};
+
+// Constant reference tables (device pointers into one buffer).
+struct DevTables {
+  const double* W;      // [NG]
+  const double* Phi;    // [NG][NP]
+  const double* dPhi;   // [D][NG][NP]
+  const double* PL;     // [NF][NG][NFN]
+  const double* WF;     // [NGF]
+  const double* PhiF;   // [NF][NGF][NP]
+  const double* dPhiF;  // [NF][D][NGF][NP]
+  const double* PLF;    // [NF][NF][NGF][NFN]
+  const int* fnodes;    // [NF][NFN]
+  const int* nodepos;   // [NF][NP] position of node a on face f, -1 if off the face
+};
+
+// ---------------------------------------------------------------------------------
+// Forward-mode dual numbers with N derivative directions.
+// ---------------------------------------------------------------------------------
+template <int N>
+struct Dual {
+  double v;
+  double d[N];
+};
+
+template <int N>
+HDG_DEVI Dual<N> dconst(double a) {
+  Dual<N> r;
+  r.v = a;
+#pragma unroll
+  for (int i = 0; i < N; ++i) r.d[i] = 0.0;
+  return r;
+}
+template <int N>
+HDG_DEVI Dual<N> operator+(const Dual<N>& a, const Dual<N>& b) {
+  Dual<N> r;
+  r.v = a.v + b.v;
+#pragma unroll
+  for (int i = 0; i < N; ++i) r.d[i] = a.d[i] + b.d[i];
+  return r;
+}
+template <int N>
+HDG_DEVI Dual<N> operator-(const Dual<N>& a, const Dual<N>& b) {
+  Dual<N> r;
+  r.v = a.v - b.v;
+#pragma unroll
+  for (int i = 0; i < N; ++i) r.d[i] = a.d[i] - b.d[i];
+  return r;
+}
+template <int N>
+HDG_DEVI Dual<N> operator-(const Dual<N>& a) {
+  Dual<N> r;
+  r.v = -a.v;
+#pragma unroll
+  for (int i = 0; i < N; ++i) r.d[i] = -a.d[i];
+  return r;
+}
+template <int N>
+HDG_DEVI Dual<N> operator*(const Dual<N>& a, const Dual<N>& b) {
+  Dual<N> r;
+  r.v = a.v * b.v;
+#pragma unroll
+  for (int i = 0; i < N; ++i) r.d[i] = a.d[i] * b.v + a.v * b.d[i];
+  return r;
+}
+template <int N>
+HDG_DEVI Dual<N> operator/(const Dual<N>& a, const Dual<N>& b) {
+  Dual<N> r;
+  double ib = 1.0 / b.v;
+  r.v = a.v * ib;
+#pragma unroll
+  for (int i = 0; i < N; ++i) r.d[i] = (a.d[i] - r.v * b.d[i]) * ib;
+  return r;
+}
+template <int N>
+HDG_DEVI Dual<N> operator+(const Dual<N>& a, double b) {
+  Dual<N> r = a;
+  r.v += b;
+  return r;
+}
+template <int N>
+HDG_DEVI Dual<N> operator+(double b, const Dual<N>& a) {
+  return a + b;
+}
+template <int N>
+HDG_DEVI Dual<N> operator-(const Dual<N>& a, double b) {
+  Dual<N> r = a;
+  r.v -= b;
+  return r;
+}
+template <int N>
+HDG_DEVI Dual<N> operator-(double b, const Dual<N>& a) {
+  Dual<N> r = -a;
+  r.v += b;
+  return r;
+}
+template <int N>
+HDG_DEVI Dual<N> operator*(const Dual<N>& a, double b) {
+  Dual<N> r;
+  r.v = a.v * b;
+#pragma unroll
+  for (int i = 0; i < N; ++i) r.d[i] = a.d[i] * b;
+  return r;
+}
+template <int N>
+HDG_DEVI Dual<N> operator*(double b, const Dual<N>& a) {
+  return a * b;
+}
+template <int N>
+HDG_DEVI Dual<N> operator/(const Dual<N>& a, double b) {
+  return a * (1.0 / b);
+}
+template <int N>
+HDG_DEVI Dual<N> operator/(double a, const Dual<N>& b) {
+  Dual<N> r;
+  double ib = 1.0 / b.v;
+  r.v = a * ib;
+  double s = -r.v * ib;
+#pragma unroll
+  for (int i = 0; i < N; ++i) r.d[i] = s * b.d[i];
+  return r;
+}
+template <int N>
+HDG_DEVI Dual<N> log(const Dual<N>& a) {
+  Dual<N> r;
+  r.v = ::log(a.v);
+  double s = 1.0 / a.v;
+#pragma unroll
+  for (int i = 0; i < N; ++i) r.d[i] = a.d[i] * s;
+  return r;
+}
+template <int N>
+HDG_DEVI Dual<N> exp(const Dual<N>& a) {
+  Dual<N> r;
+  r.v = ::exp(a.v);
+#pragma unroll
+  for (int i = 0; i < N; ++i) r.d[i] = a.d[i] * r.v;
+  return r;
+}
+template <int N>
+HDG_DEVI Dual<N> sqrt(const Dual<N>& a) {
+  Dual<N> r;
+  r.v = ::sqrt(a.v);
+  double s = 0.5 / r.v;
+#pragma unroll
+  for (int i = 0; i < N; ++i) r.d[i] = a.d[i] * s;
+  return r;
+}
+// |x| with d|x|/dx = sign(x), sign(0) = 0
+template <int N>
+HDG_DEVI Dual<N> absk(const Dual<N>& a) {
+  double s = (a.v > 0.0) ? 1.0 : ((a.v < 0.0) ? -1.0 : 0.0);
+  return a * s;
+}
+HDG_DEVI double absk(double a) { return a > 0.0 ? a : -a; }
+HDG_DEVI double valof(double a) { return a; }
+template <int N>
+HDG_DEVI double valof(const Dual<N>& a) {
+  return a.v;
+}
+
+// ---------------------------------------------------------------------------------
+// Pointwise physics, generic in the scalar type (double or Dual<N>).
+// ---------------------------------------------------------------------------------
+template <int D, class T>
+HDG_DEVI void prim_of_v(const T* v, double gamma, T& rho, T* vel, T& p) {
+  using ::log;
+  using ::exp;
+  const double g1 = gamma - 1.0;
+  const T& vm = v[D + 1];
+  T ww = v[1] * v[1];
+#pragma unroll
+  for (int i = 1; i < D; ++i) ww = ww + v[1 + i] * v[1 + i];
+  T s = (gamma - v[0]) + ww / (2.0 * vm);
+  T lnrho = (::log(g1) - log(-vm) - s) * (1.0 / g1);
+  rho = exp(lnrho);
+  T ivm = 1.0 / vm;
+  p = -(rho * g1) * ivm;
+#pragma unroll
+  for (int i = 0; i < D; ++i) vel[i] = -(v[1 + i] * ivm);
+}
+
+// u(v) and the inviscid flux F(v) [M][D] from primitives.
+template <int D, class T>
+HDG_DEVI void cons_and_flux(const T& rho, const T* vel, const T& p, double gamma, T* u, T (*F)[D]) {
+  T vv = vel[0] * vel[0];
+#pragma unroll
+  for (int i = 1; i < D; ++i) vv = vv + vel[i] * vel[i];
+  T rhoE = p * (1.0 / (gamma - 1.0)) + 0.5 * (rho * vv);
+  if (u) {
+    u[0] = rho;
+#pragma unroll
+    for (int i = 0; i < D; ++i) u[1 + i] = rho * vel[i];
+    u[D + 1] = rhoE;
+  }
+  if (F) {
+    T H = rhoE + p;
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      T mj = rho * vel[j];
+      F[0][j] = mj;
+#pragma unroll
+      for (int i = 0; i < D; ++i) {
+        F[1 + i][j] = mj * vel[i];
+        if (i == j) F[1 + i][j] = F[1 + i][j] + p;
+      }
+      F[D + 1][j] = vel[j] * H;
+    }
+  }
+}
+
+// Directional derivative du = A0(v) dv of u(v) (chain rule on the inverse map).
+template <int D, class T>
+HDG_DEVI void du_of_v(const T* v, const T* dv, double gamma, T* du) {
+  const double g1 = gamma - 1.0;
+  T rho, vel[D], p;
+  prim_of_v<D>(v, gamma, rho, vel, p);
+  const T& vm = v[D + 1];
+  const T& dvm = dv[D + 1];
+  T ivm = 1.0 / vm;
+  T wdw = v[1] * dv[1];
+  T ww = v[1] * v[1];
+#pragma unroll
+  for (int i = 1; i < D; ++i) {
+    wdw = wdw + v[1 + i] * dv[1 + i];
+    ww = ww + v[1 + i] * v[1 + i];
+  }
+  T ds = wdw * ivm - dv[0] - 0.5 * (ww * dvm) * (ivm * ivm);
+  T dlnrho = (-(dvm * ivm) - ds) * (1.0 / g1);
+  T drho = rho * dlnrho;
+  T dvel[D];
+#pragma unroll
+  for (int i = 0; i < D; ++i) dvel[i] = (v[1 + i] * dvm) * (ivm * ivm) - dv[1 + i] * ivm;
+  T dp = p * (dlnrho - dvm * ivm);
+  du[0] = drho;
+  T vv = vel[0] * vel[0];
+  T vdv = vel[0] * dvel[0];
+#pragma unroll
+  for (int i = 1; i < D; ++i) {
+    vv = vv + vel[i] * vel[i];
+    vdv = vdv + vel[i] * dvel[i];
+  }
+#pragma unroll
+  for (int i = 0; i < D; ++i) du[1 + i] = drho * vel[i] + rho * dvel[i];
+  du[D + 1] = dp * (1.0 / g1) + 0.5 * (drho * vv) + rho * vdv;
+}
+
+// Viscous flux G(v, q) [M][D] (Eq. viscFlux) with q ~ grad v, through
+// grad V_i = -grad w_i / v_m + w_i grad v_m / v_m^2 and grad T = grad v_m / (c_v v_m^2).
+template <int D, class T, class TQ>
+HDG_DEVI void visc_flux(const T* v, const TQ (*q)[D], const PhysParams& ph, T (*G)[D]) {
+  const T& vm = v[D + 1];
+  T ivm = 1.0 / vm;
+  T ivm2 = ivm * ivm;
+  T vel[D];
+#pragma unroll
+  for (int i = 0; i < D; ++i) vel[i] = -(v[1 + i] * ivm);
+  T gV[D][D];
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = 0; j < D; ++j) gV[i][j] = (v[1 + i] * ivm2) * q[D + 1][j] - q[1 + i][j] * ivm;
+  T div = gV[0][0];
+#pragma unroll
+  for (int i = 1; i < D; ++i) div = div + gV[i][i];
+  T tau[D][D];
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      T t = gV[i][j] + gV[j][i];
+      if (i == j) t = t - (2.0 / 3.0) * div;
+      tau[i][j] = ph.mu * t;
+    }
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    G[0][j] = vm * 0.0;
+    T e = vel[0] * tau[0][j];
+#pragma unroll
+    for (int i = 1; i < D; ++i) e = e + vel[i] * tau[i][j];
+    T gradT = (ph.kappa / ph.cv) * (q[D + 1][j] * ivm2);
+#pragma unroll
+    for (int i = 0; i < D; ++i) G[1 + i][j] = -tau[i][j];
+    G[D + 1][j] = -(e + gradT);
+  }
+}
+
+// Largest-magnitude eigenvalue of A_n: |V.n| + c (Eq. sLxF).
+template <int D, class T>
+HDG_DEVI T lambda_max(const T& rho, const T* vel, const T& p, const double* n, double gamma) {
+  using ::sqrt;
+  T vn = vel[0] * n[0];
+#pragma unroll
+  for (int i = 1; i < D; ++i) vn = vn + vel[i] * n[i];
+  return absk(vn) + sqrt(gamma * p / rho);
+}
+
+}  // namespace hdg

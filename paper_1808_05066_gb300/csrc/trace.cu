@@ -1,0 +1,708 @@
+// Trace-space operations around the condensed local problems:
+//   * BDF history and primitive -> entropy-variable conversion (element data),
+//   * the assembled trace operator K = sum_e P_e^T S_e P_e applied element by element
+//     and its right-hand side -sum_e P_e^T g_e (Sec. 3.2: only vhat is coupled),
+//   * recovery of the interior update dV_e = -y_e - X_e P_e dVhat,
+//   * the Newton residual norm,
+//   * the trace solve: restarted GMRES(30) with right face-block Jacobi preconditioning,
+//     or an assembled dense LU with partial pivoting for small systems.
+// All vectors in the trace space are [F][Nf][m] (canonical face-node order).
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "ctx.hpp"
+
+namespace hdg {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+inline unsigned nblocks(int64_t n, int t = kThreads) {
+  int64_t b = (n + t - 1) / t;
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 64));
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  return v;
+}
+
+// Block sum; result valid in thread 0.
+__device__ double block_sum(double v) {
+  __shared__ double part[32];
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) part[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (w == 0) {
+    s = lane < (int)((blockDim.x + 31) >> 5) ? part[lane] : 0.0;
+    s = warp_sum(s);
+  }
+  return s;
+}
+
+// ---------------------------------------------------------------- element data
+template <int D>
+__global__ void k_prim_to_entropy(const double* prim, int64_t n, double gamma, double* v) {
+  constexpr int M = D + 2;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    const double* P = prim + t * M;
+    double rho = P[0], p = P[M - 1], vv = 0.0;
+    for (int i = 0; i < D; ++i) vv += P[1 + i] * P[1 + i];
+    double rhoE = p / (gamma - 1.0) + 0.5 * rho * vv;
+    double s = ::log(p) - gamma * ::log(rho);
+    double* o = v + t * M;
+    o[0] = -s + gamma + 1.0 - (gamma - 1.0) * rhoE / p;
+    for (int i = 0; i < D; ++i) o[1 + i] = (gamma - 1.0) * rho * P[1 + i] / p;
+    o[M - 1] = -(gamma - 1.0) * rho / p;
+  }
+}
+
+template <int D>
+__global__ void k_history(DevTables T, const double* geo, int GEO, int NP, int NG, const double* V0,
+                          const double* V1, double c0, double c1, double gamma, double* hist) {
+  constexpr int M = D + 2;
+  extern __shared__ double sh[];
+  double* u = sh;  // [NG][M]
+  const int64_t e = blockIdx.x;
+  const double detJ = geo[e * GEO + D * D];
+  for (int g = threadIdx.x; g < NG; g += blockDim.x) {
+    double acc[M];
+    for (int i = 0; i < M; ++i) acc[i] = 0.0;
+    for (int which = 0; which < 2; ++which) {
+      const double* Vs = which == 0 ? V0 : V1;
+      const double c = which == 0 ? c0 : c1;
+      if (!Vs) continue;
+      double v[M];
+      for (int i = 0; i < M; ++i) {
+        double s = 0.0;
+        for (int b = 0; b < NP; ++b) s += T.Phi[g * NP + b] * Vs[(e * NP + b) * M + i];
+        v[i] = s;
+      }
+      double rho, vel[D], p;
+      prim_of_v<D>(v, gamma, rho, vel, p);
+      double uu[M];
+      cons_and_flux<D>(rho, vel, p, gamma, uu, (double(*)[D]) nullptr);
+      for (int i = 0; i < M; ++i) acc[i] += c * uu[i];
+    }
+    for (int i = 0; i < M; ++i) u[g * M + i] = acc[i] * T.W[g] * detJ;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < NP * M; t += blockDim.x) {
+    int a = t / M, i = t % M;
+    double s = 0.0;
+    for (int g = 0; g < NG; ++g) s += T.Phi[g * NP + a] * u[g * M + i];
+    hist[e * NP * M + t] = s;
+  }
+}
+
+// ---------------------------------------------------------------- trace operator
+// rhs[F][c][i] = -sum_sides g_e[loc * M + i]
+__global__ void k_trace_gather(const int* fs_elem, const int* fs_loc, int64_t F, int NFN, int M, int NT,
+                               const double* ge, double scale, double* out) {
+  const int64_t n = F * NFN * M;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    int64_t Fi = t / (NFN * M);
+    int c = (int)((t / M) % NFN), i = (int)(t % M);
+    double s = 0.0;
+    for (int side = 0; side < 2; ++side) {
+      int64_t e = fs_elem[2 * Fi + side];
+      int loc = fs_loc[(2 * Fi + side) * NFN + c];
+      s += ge[e * NT + loc * M + i];
+    }
+    out[t] = scale * s;
+  }
+}
+
+// w_e = S_e x_e, one warp per row, x_e gathered into shared memory.
+__global__ void k_elem_matvec(const double* S, const double* x, const int* tgidx, int NT, int M, double* w) {
+  extern __shared__ double xs[];
+  const int64_t e = blockIdx.x;
+  const int nfc = NT / M;
+  for (int t = threadIdx.x; t < NT; t += blockDim.x) {
+    int fc = t / M, i = t % M;
+    xs[t] = x[(int64_t)tgidx[e * nfc + fc] * M + i];
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const double* Se = S + e * (int64_t)NT * NT;
+  for (int r = wid; r < NT; r += nw) {
+    double s = 0.0;
+    for (int c = lane; c < NT; c += 32) s += Se[(int64_t)r * NT + c] * xs[c];
+    s = warp_sum(s);
+    if (lane == 0) w[e * NT + r] = s;
+  }
+}
+
+// dV_e = -y_e - X_e P_e dVhat
+__global__ void k_recover(const double* recov, const double* dvh, const int* tgidx, int NV, int NT, int M,
+                          double* dV) {
+  extern __shared__ double xs[];
+  const int64_t e = blockIdx.x;
+  const int nfc = NT / M;
+  for (int t = threadIdx.x; t < NT; t += blockDim.x) {
+    int fc = t / M, i = t % M;
+    xs[t] = dvh[(int64_t)tgidx[e * nfc + fc] * M + i];
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const double* X = recov + e * (int64_t)(NV * NT + NV);
+  const double* y = X + (int64_t)NV * NT;
+  for (int r = wid; r < NV; r += nw) {
+    double s = 0.0;
+    for (int c = lane; c < NT; c += 32) s += X[(int64_t)r * NT + c] * xs[c];
+    s = warp_sum(s);
+    if (lane == 0) dV[e * NV + r] = -y[r] - s;
+  }
+}
+
+__global__ void k_sumsq_elem_rows(const double* R, int64_t E, int stride, int n, double* out) {
+  double s = 0.0;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < E * n; t += (int64_t)gridDim.x * blockDim.x) {
+    int64_t e = t / n;
+    double v = R[e * stride + (t % n)];
+    s += v * v;
+  }
+  s = block_sum(s);
+  if (threadIdx.x == 0) atomicAdd(out, s);
+}
+
+__global__ void k_sumsq_trace_residual(const double* R, const int* fs_elem, const int* fs_loc, int64_t F, int NFN,
+                                       int M, int NV, int NT, double* out) {
+  double s = 0.0;
+  const int64_t n = F * NFN * M;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    int64_t Fi = t / (NFN * M);
+    int c = (int)((t / M) % NFN), i = (int)(t % M);
+    double v = 0.0;
+    for (int side = 0; side < 2; ++side) {
+      int64_t e = fs_elem[2 * Fi + side];
+      int loc = fs_loc[(2 * Fi + side) * NFN + c];
+      v += R[e * (int64_t)(NV + NT) + NV + loc * M + i];
+    }
+    s += v * v;
+  }
+  s = block_sum(s);
+  if (threadIdx.x == 0) atomicAdd(out, s);
+}
+
+// ---------------------------------------------------------------- vector ops
+__global__ void k_axpy(int64_t n, double a, const double* x, double* y) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+    y[t] += a * x[t];
+}
+__global__ void k_scale_copy(int64_t n, double a, const double* x, double* y) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+    y[t] = a * x[t];
+}
+// out[j] = basis_j . w for j < nb (blockIdx.y = j)
+__global__ void k_multidot(int64_t n, const double* basis, int64_t ld, const double* w, double* out) {
+  const int j = blockIdx.y;
+  const double* b = basis + j * ld;
+  double s = 0.0;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+    s += b[t] * w[t];
+  s = block_sum(s);
+  if (threadIdx.x == 0) atomicAdd(out + j, s);
+}
+// w -= sum_j h[j] basis_j
+__global__ void k_multiaxpy(int64_t n, const double* basis, int64_t ld, const double* h, int nb, double* w) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    double s = w[t];
+    for (int j = 0; j < nb; ++j) s -= h[j] * basis[j * ld + t];
+    w[t] = s;
+  }
+}
+// x += sum_j c[j] basis_j
+__global__ void k_multiaxpy_add(int64_t n, const double* basis, int64_t ld, const double* c, int nb, double* x) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    double s = x[t];
+    for (int j = 0; j < nb; ++j) s += c[j] * basis[j * ld + t];
+    x[t] = s;
+  }
+}
+
+// ---------------------------------------------------------------- face-block Jacobi
+// K_FF (canonical order) = sum_sides S_e[loc rows, loc cols]; LU with partial pivoting.
+__global__ void k_face_block_factor(const double* S, const int* fs_elem, const int* fs_loc, int NFN, int M, int NT,
+                                    double* fac, int* piv) {
+  extern __shared__ double A[];  // [B][B]
+  __shared__ int s_p;
+  const int B = NFN * M;
+  const int64_t Fi = blockIdx.x;
+  for (int t = threadIdx.x; t < B * B; t += blockDim.x) {
+    int r = t / B, c = t % B;
+    int cr = r / M, ir = r % M, cc = c / M, ic = c % M;
+    double s = 0.0;
+    for (int side = 0; side < 2; ++side) {
+      int64_t e = fs_elem[2 * Fi + side];
+      int lr = fs_loc[(2 * Fi + side) * NFN + cr] * M + ir;
+      int lc = fs_loc[(2 * Fi + side) * NFN + cc] * M + ic;
+      s += S[e * (int64_t)NT * NT + (int64_t)lr * NT + lc];
+    }
+    A[t] = s;
+  }
+  __syncthreads();
+  for (int k = 0; k < B; ++k) {
+    if (threadIdx.x < 32) {
+      double best = -1.0;
+      int bi = k;
+      for (int r = k + threadIdx.x; r < B; r += 32) {
+        double v = fabs(A[r * B + k]);
+        if (v > best) {
+          best = v;
+          bi = r;
+        }
+      }
+      for (int off = 16; off > 0; off >>= 1) {
+        double ob = __shfl_down_sync(0xffffffffu, best, off);
+        int oi = __shfl_down_sync(0xffffffffu, bi, off);
+        if (ob > best || (ob == best && oi < bi)) {
+          best = ob;
+          bi = oi;
+        }
+      }
+      if (threadIdx.x == 0) {
+        s_p = bi;
+        piv[Fi * B + k] = bi;
+      }
+    }
+    __syncthreads();
+    int p = s_p;
+    if (p != k)
+      for (int j = threadIdx.x; j < B; j += blockDim.x) {
+        double t = A[k * B + j];
+        A[k * B + j] = A[p * B + j];
+        A[p * B + j] = t;
+      }
+    __syncthreads();
+    double d = A[k * B + k];
+    double inv = d != 0.0 ? 1.0 / d : 0.0;
+    for (int r = k + 1 + threadIdx.x; r < B; r += blockDim.x) A[r * B + k] *= inv;
+    __syncthreads();
+    int rem = B - k - 1;
+    for (int t = threadIdx.x; t < rem * rem; t += blockDim.x) {
+      int r = k + 1 + t / rem, c = k + 1 + t % rem;
+      A[r * B + c] -= A[r * B + k] * A[k * B + c];
+    }
+    __syncthreads();
+  }
+  for (int t = threadIdx.x; t < B * B; t += blockDim.x) fac[Fi * (int64_t)B * B + t] = A[t];
+}
+
+// z_F = K_FF^{-1} r_F, one warp per face
+__global__ void k_face_block_solve(const double* fac, const int* piv, int64_t F, int B, const double* r,
+                                   double* z) {
+  extern __shared__ double xs[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int64_t Fi = (int64_t)blockIdx.x * nw + wid;
+  if (Fi >= F) return;
+  double* x = xs + wid * B;
+  for (int t = lane; t < B; t += 32) x[t] = r[Fi * B + t];
+  __syncwarp();
+  const int* P = piv + Fi * B;
+  if (lane == 0)
+    for (int k = 0; k < B; ++k) {
+      int p = P[k];
+      if (p != k) {
+        double t = x[k];
+        x[k] = x[p];
+        x[p] = t;
+      }
+    }
+  __syncwarp();
+  const double* A = fac + Fi * (int64_t)B * B;
+  for (int k = 0; k < B; ++k) {
+    double xk = x[k];
+    for (int rr = k + 1 + lane; rr < B; rr += 32) x[rr] -= A[rr * B + k] * xk;
+    __syncwarp();
+  }
+  for (int k = B - 1; k >= 0; --k) {
+    if (lane == 0) x[k] /= A[k * B + k];
+    __syncwarp();
+    double xk = x[k];
+    for (int rr = lane; rr < k; rr += 32) x[rr] -= A[rr * B + k] * xk;
+    __syncwarp();
+  }
+  for (int t = lane; t < B; t += 32) z[Fi * B + t] = x[t];
+}
+
+// ---------------------------------------------------------------- dense direct solver
+__global__ void k_dense_scatter(const double* S, const int* tgidx, int64_t E, int NT, int M, int64_t n, double* K) {
+  const int nfc = NT / M;
+  const int64_t tot = E * (int64_t)NT * NT;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
+    int64_t e = t / ((int64_t)NT * NT);
+    int r = (int)((t / NT) % NT), c = (int)(t % NT);
+    int64_t gr = (int64_t)tgidx[e * nfc + r / M] * M + r % M;
+    int64_t gc = (int64_t)tgidx[e * nfc + c / M] * M + c % M;
+    atomicAdd(K + gr * n + gc, S[t]);
+  }
+}
+__global__ void k_dense_pivot(double* K, int64_t n, int64_t k, int* piv, int* bad) {
+  __shared__ double bv[1024];
+  __shared__ int64_t bi[1024];
+  double best = -1.0;
+  int64_t idx = k;
+  for (int64_t r = k + threadIdx.x; r < n; r += blockDim.x) {
+    double v = fabs(K[r * n + k]);
+    if (v > best) {
+      best = v;
+      idx = r;
+    }
+  }
+  bv[threadIdx.x] = best;
+  bi[threadIdx.x] = idx;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) {
+      double ov = bv[threadIdx.x + s];
+      int64_t oi = bi[threadIdx.x + s];
+      if (ov > bv[threadIdx.x] || (ov == bv[threadIdx.x] && oi < bi[threadIdx.x])) {
+        bv[threadIdx.x] = ov;
+        bi[threadIdx.x] = oi;
+      }
+    }
+    __syncthreads();
+  }
+  const int64_t p = bi[0];
+  if (threadIdx.x == 0) {
+    piv[k] = (int)p;
+    if (!(bv[0] > 0.0)) *bad = 1;
+  }
+  if (p != k)
+    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+      double t = K[k * n + j];
+      K[k * n + j] = K[p * n + j];
+      K[p * n + j] = t;
+    }
+}
+__global__ void k_dense_scale(double* K, int64_t n, int64_t k) {
+  const double d = K[k * n + k];
+  const double inv = d != 0.0 ? 1.0 / d : 0.0;
+  for (int64_t r = k + 1 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
+    K[r * n + k] *= inv;
+}
+__global__ void k_dense_update(double* K, int64_t n, int64_t k) {
+  const int64_t rem = n - k - 1;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < rem * rem; t += (int64_t)gridDim.x * blockDim.x) {
+    int64_t r = k + 1 + t / rem, c = k + 1 + t % rem;
+    K[r * n + c] -= K[r * n + k] * K[k * n + c];
+  }
+}
+// forward / backward substitution in one block
+__global__ void k_dense_solve(const double* K, const int* piv, int64_t n, double* x) {
+  if (threadIdx.x == 0)
+    for (int64_t k = 0; k < n; ++k) {
+      int64_t p = piv[k];
+      if (p != k) {
+        double t = x[k];
+        x[k] = x[p];
+        x[p] = t;
+      }
+    }
+  __syncthreads();
+  for (int64_t k = 0; k < n; ++k) {
+    double xk = x[k];
+    for (int64_t r = k + 1 + threadIdx.x; r < n; r += blockDim.x) x[r] -= K[r * n + k] * xk;
+    __syncthreads();
+  }
+  for (int64_t k = n - 1; k >= 0; --k) {
+    if (threadIdx.x == 0) x[k] /= K[k * n + k];
+    __syncthreads();
+    double xk = x[k];
+    for (int64_t r = threadIdx.x; r < k; r += blockDim.x) x[r] -= K[r * n + k] * xk;
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+// ================================================================ host launchers
+int launch_prim_to_entropy(hdg_ctx* ctx, const double* prim, int64_t n, double* v, cudaStream_t s) {
+  if (n <= 0) return HDG_OK;
+  if (ctx->dim == 2)
+    k_prim_to_entropy<2><<<nblocks(n), kThreads, 0, s>>>(prim, n, ctx->ph.gamma, v);
+  else
+    k_prim_to_entropy<3><<<nblocks(n), kThreads, 0, s>>>(prim, n, ctx->ph.gamma, v);
+  HDG_CK(cudaGetLastError());
+  return HDG_OK;
+}
+
+int launch_history(hdg_ctx* ctx, const double* V0, const double* V1, double c0, double c1, double* hist,
+                   cudaStream_t s) {
+  size_t sm = sizeof(double) * ctx->NG * ctx->M;
+  if (ctx->dim == 2)
+    k_history<2><<<(unsigned)ctx->E, 128, sm, s>>>(ctx->T, ctx->d_geo, ctx->GEO, ctx->NP, ctx->NG, V0, V1, c0, c1,
+                                                   ctx->ph.gamma, hist);
+  else
+    k_history<3><<<(unsigned)ctx->E, 128, sm, s>>>(ctx->T, ctx->d_geo, ctx->GEO, ctx->NP, ctx->NG, V0, V1, c0, c1,
+                                                   ctx->ph.gamma, hist);
+  HDG_CK(cudaGetLastError());
+  return HDG_OK;
+}
+
+int launch_trace_rhs(hdg_ctx* ctx, const double* g, double* rhs, cudaStream_t s) {
+  k_trace_gather<<<nblocks(ctx->ntrace), kThreads, 0, s>>>(ctx->d_fs_elem, ctx->d_fs_loc, ctx->F, ctx->NFN, ctx->M,
+                                                          ctx->NT, g, -1.0, rhs);
+  HDG_CK(cudaGetLastError());
+  return HDG_OK;
+}
+
+int launch_trace_matvec(hdg_ctx* ctx, const double* S, const double* x, double* y, double* work, cudaStream_t s) {
+  k_elem_matvec<<<(unsigned)ctx->E, 256, sizeof(double) * ctx->NT, s>>>(S, x, ctx->d_tgidx, ctx->NT, ctx->M, work);
+  k_trace_gather<<<nblocks(ctx->ntrace), kThreads, 0, s>>>(ctx->d_fs_elem, ctx->d_fs_loc, ctx->F, ctx->NFN, ctx->M,
+                                                          ctx->NT, work, 1.0, y);
+  HDG_CK(cudaGetLastError());
+  return HDG_OK;
+}
+
+int launch_recover(hdg_ctx* ctx, const double* recov, const double* dVhat, double* dV, cudaStream_t s) {
+  k_recover<<<(unsigned)ctx->E, 256, sizeof(double) * ctx->NT, s>>>(recov, dVhat, ctx->d_tgidx, ctx->NV, ctx->NT,
+                                                                   ctx->M, dV);
+  HDG_CK(cudaGetLastError());
+  return HDG_OK;
+}
+
+int launch_axpy(int64_t n, double a, const double* x, double* y, cudaStream_t s) {
+  k_axpy<<<nblocks(n), kThreads, 0, s>>>(n, a, x, y);
+  HDG_CK(cudaGetLastError());
+  return HDG_OK;
+}
+
+static int ensure_red(hdg_ctx* ctx) {
+  if (!ctx->d_red) {
+    HDG_CK(cudaMalloc(&ctx->d_red, sizeof(double) * 128));
+    HDG_CK(cudaMallocHost(&ctx->h_red, sizeof(double) * 128));
+  }
+  return HDG_OK;
+}
+
+int residual_norm(hdg_ctx* ctx, const double* R, double* norm, cudaStream_t s) {
+  int rc = ensure_red(ctx);
+  if (rc) return rc;
+  HDG_CK(cudaMemsetAsync(ctx->d_red, 0, sizeof(double) * 2, s));
+  k_sumsq_elem_rows<<<nblocks(ctx->E * (int64_t)ctx->NV), kThreads, 0, s>>>(R, ctx->E, ctx->NV + ctx->NT, ctx->NV,
+                                                                           ctx->d_red);
+  k_sumsq_trace_residual<<<nblocks(ctx->ntrace), kThreads, 0, s>>>(R, ctx->d_fs_elem, ctx->d_fs_loc, ctx->F, ctx->NFN,
+                                                                  ctx->M, ctx->NV, ctx->NT, ctx->d_red + 1);
+  HDG_CK(cudaGetLastError());
+  HDG_CK(cudaMemcpyAsync(ctx->h_red, ctx->d_red, sizeof(double) * 2, cudaMemcpyDeviceToHost, s));
+  HDG_CK(cudaStreamSynchronize(s));
+  *norm = std::sqrt(ctx->h_red[0] + ctx->h_red[1]);
+  return HDG_OK;
+}
+
+// ---------------------------------------------------------------- dense solve
+static int dense_solve(hdg_ctx* ctx, const double* S, const double* g, double* dVhat, double* final_res,
+                       cudaStream_t s) {
+  const int64_t n = ctx->ntrace;
+  if ((size_t)n != ctx->dense_n) {
+    if (ctx->d_dense) cudaFree(ctx->d_dense);
+    if (ctx->d_dpiv) cudaFree(ctx->d_dpiv);
+    ctx->d_dense = nullptr;
+    ctx->d_dpiv = nullptr;
+    ctx->dense_n = 0;
+    HDG_CK(cudaMalloc(&ctx->d_dense, sizeof(double) * n * n));
+    HDG_CK(cudaMalloc(&ctx->d_dpiv, sizeof(int) * (n + 1)));
+    ctx->dense_n = (size_t)n;
+  }
+  int rc = ensure_red(ctx);
+  if (rc) return rc;
+  double* K = ctx->d_dense;
+  int* bad = ctx->d_dpiv + n;
+  HDG_CK(cudaMemsetAsync(K, 0, sizeof(double) * n * n, s));
+  HDG_CK(cudaMemsetAsync(bad, 0, sizeof(int), s));
+  k_dense_scatter<<<nblocks(ctx->E * (int64_t)ctx->NT * ctx->NT), kThreads, 0, s>>>(S, ctx->d_tgidx, ctx->E, ctx->NT,
+                                                                                   ctx->M, n, K);
+  for (int64_t k = 0; k < n; ++k) {
+    k_dense_pivot<<<1, 1024, 0, s>>>(K, n, k, ctx->d_dpiv, bad);
+    if (k + 1 < n) {
+      k_dense_scale<<<nblocks(n - k - 1), kThreads, 0, s>>>(K, n, k);
+      k_dense_update<<<nblocks((n - k - 1) * (n - k - 1)), kThreads, 0, s>>>(K, n, k);
+    }
+  }
+  rc = launch_trace_rhs(ctx, g, dVhat, s);
+  if (rc) return rc;
+  k_dense_solve<<<1, 1024, 0, s>>>(K, ctx->d_dpiv, n, dVhat);
+  HDG_CK(cudaGetLastError());
+  int hbad = 0;
+  HDG_CK(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+  HDG_CK(cudaStreamSynchronize(s));
+  if (hbad) {
+    set_error("trace_solve: singular assembled trace matrix");
+    return HDG_ERR_SINGULAR;
+  }
+  *final_res = 0.0;
+  return HDG_OK;
+}
+
+// ---------------------------------------------------------------- GMRES
+static int gmres_solve(hdg_ctx* ctx, const double* S, const double* g, double* x, double rtol, int max_it,
+                       int* iters, double* final_res, cudaStream_t s) {
+  const int m = 30;
+  const int64_t n = ctx->ntrace;
+  const int B = ctx->NFN * ctx->M;
+  // workspace: basis V (m+1) n, Z (precond of current basis vector) n, w n, b n, elem work E*NT
+  const size_t need = sizeof(double) * ((size_t)(m + 1) * n + 3 * (size_t)n + (size_t)ctx->E * ctx->NT);
+  if (ctx->sw_bytes < need) {
+    if (ctx->d_sw) cudaFree(ctx->d_sw);
+    ctx->d_sw = nullptr;
+    ctx->sw_bytes = 0;
+    HDG_CK(cudaMalloc(&ctx->d_sw, need));
+    ctx->sw_bytes = need;
+  }
+  if (!ctx->d_pc) {
+    HDG_CK(cudaMalloc(&ctx->d_pc, sizeof(double) * ctx->F * B * B));
+    HDG_CK(cudaMalloc(&ctx->d_pcpiv, sizeof(int) * ctx->F * B));
+  }
+  int rc = ensure_red(ctx);
+  if (rc) return rc;
+  double* Vb = ctx->d_sw;
+  double* zt = Vb + (size_t)(m + 1) * n;
+  double* w = zt + n;
+  double* b = w + n;
+  double* ew = b + n;
+  k_face_block_factor<<<(unsigned)ctx->F, 64, sizeof(double) * B * B, s>>>(S, ctx->d_fs_elem, ctx->d_fs_loc, ctx->NFN,
+                                                                         ctx->M, ctx->NT, ctx->d_pc, ctx->d_pcpiv);
+  rc = launch_trace_rhs(ctx, g, b, s);
+  if (rc) return rc;
+  const int wpb = 8;
+  auto precond = [&](const double* r, double* z) {
+    k_face_block_solve<<<(unsigned)((ctx->F + wpb - 1) / wpb), 32 * wpb, sizeof(double) * wpb * B, s>>>(
+        ctx->d_pc, ctx->d_pcpiv, ctx->F, B, r, z);
+  };
+  auto dot_host = [&](const double* basis, int nb, const double* v, double* out) -> int {
+    HDG_CK(cudaMemsetAsync(ctx->d_red, 0, sizeof(double) * nb, s));
+    dim3 grid(std::min<unsigned>(nblocks(n), 1024), nb);
+    k_multidot<<<grid, kThreads, 0, s>>>(n, basis, n, v, ctx->d_red);
+    HDG_CK(cudaGetLastError());
+    HDG_CK(cudaMemcpyAsync(ctx->h_red, ctx->d_red, sizeof(double) * nb, cudaMemcpyDeviceToHost, s));
+    HDG_CK(cudaStreamSynchronize(s));
+    for (int i = 0; i < nb; ++i) out[i] = ctx->h_red[i];
+    return HDG_OK;
+  };
+  HDG_CK(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
+  double bn2;
+  rc = dot_host(b, 1, b, &bn2);
+  if (rc) return rc;
+  const double bnorm = std::sqrt(bn2);
+  *iters = 0;
+  if (bnorm == 0.0) {
+    *final_res = 0.0;
+    return HDG_OK;
+  }
+  std::vector<double> H((m + 1) * m), cs(m), sn(m), gv(m + 1), h(m + 1), h2(m + 1), yv(m);
+  double rel = 1.0;
+  int total = 0;
+  bool first = true;
+  while (total < max_it) {
+    // r = b - K x
+    if (first) {
+      HDG_CK(cudaMemcpyAsync(w, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    } else {
+      rc = launch_trace_matvec(ctx, S, x, w, ew, s);
+      if (rc) return rc;
+      k_scale_copy<<<nblocks(n), kThreads, 0, s>>>(n, -1.0, w, w);
+      k_axpy<<<nblocks(n), kThreads, 0, s>>>(n, 1.0, b, w);
+    }
+    first = false;
+    double rn2;
+    rc = dot_host(w, 1, w, &rn2);
+    if (rc) return rc;
+    double beta = std::sqrt(rn2);
+    rel = beta / bnorm;
+    if (rel <= rtol) break;
+    k_scale_copy<<<nblocks(n), kThreads, 0, s>>>(n, 1.0 / beta, w, Vb);
+    std::fill(gv.begin(), gv.end(), 0.0);
+    gv[0] = beta;
+    int j = 0;
+    for (; j < m && total < max_it; ++j, ++total) {
+      precond(Vb + (size_t)j * n, zt);
+      rc = launch_trace_matvec(ctx, S, zt, w, ew, s);
+      if (rc) return rc;
+      // classical Gram-Schmidt, twice
+      rc = dot_host(Vb, j + 1, w, h.data());
+      if (rc) return rc;
+      HDG_CK(cudaMemcpyAsync(ctx->d_red + 64, h.data(), sizeof(double) * (j + 1), cudaMemcpyHostToDevice, s));
+      k_multiaxpy<<<nblocks(n), kThreads, 0, s>>>(n, Vb, n, ctx->d_red + 64, j + 1, w);
+      rc = dot_host(Vb, j + 1, w, h2.data());
+      if (rc) return rc;
+      HDG_CK(cudaMemcpyAsync(ctx->d_red + 64, h2.data(), sizeof(double) * (j + 1), cudaMemcpyHostToDevice, s));
+      k_multiaxpy<<<nblocks(n), kThreads, 0, s>>>(n, Vb, n, ctx->d_red + 64, j + 1, w);
+      for (int i = 0; i <= j; ++i) h[i] += h2[i];
+      double wn2;
+      rc = dot_host(w, 1, w, &wn2);
+      if (rc) return rc;
+      h[j + 1] = std::sqrt(wn2);
+      if (h[j + 1] > 0.0) k_scale_copy<<<nblocks(n), kThreads, 0, s>>>(n, 1.0 / h[j + 1], w, Vb + (size_t)(j + 1) * n);
+      for (int i = 0; i < j; ++i) {  // apply previous rotations
+        double t = cs[i] * h[i] + sn[i] * h[i + 1];
+        h[i + 1] = -sn[i] * h[i] + cs[i] * h[i + 1];
+        h[i] = t;
+      }
+      double den = std::hypot(h[j], h[j + 1]);
+      cs[j] = den > 0.0 ? h[j] / den : 1.0;
+      sn[j] = den > 0.0 ? h[j + 1] / den : 0.0;
+      h[j] = den;
+      h[j + 1] = 0.0;
+      gv[j + 1] = -sn[j] * gv[j];
+      gv[j] = cs[j] * gv[j];
+      for (int i = 0; i <= j; ++i) H[i * m + j] = h[i];
+      rel = std::fabs(gv[j + 1]) / bnorm;
+      if (rel <= rtol) {
+        ++j;
+        ++total;
+        break;
+      }
+    }
+    // y = H^{-1} g ; x += M^{-1} V y
+    for (int i = j - 1; i >= 0; --i) {
+      double t = gv[i];
+      for (int k = i + 1; k < j; ++k) t -= H[i * m + k] * yv[k];
+      yv[i] = t / H[i * m + i];
+    }
+    HDG_CK(cudaMemcpyAsync(ctx->d_red + 64, yv.data(), sizeof(double) * j, cudaMemcpyHostToDevice, s));
+    HDG_CK(cudaMemsetAsync(w, 0, sizeof(double) * n, s));
+    k_multiaxpy_add<<<nblocks(n), kThreads, 0, s>>>(n, Vb, n, ctx->d_red + 64, j, w);
+    precond(w, zt);
+    k_axpy<<<nblocks(n), kThreads, 0, s>>>(n, 1.0, zt, x);
+    HDG_CK(cudaGetLastError());
+    if (rel <= rtol) break;
+  }
+  // true residual
+  rc = launch_trace_matvec(ctx, S, x, w, ew, s);
+  if (rc) return rc;
+  k_scale_copy<<<nblocks(n), kThreads, 0, s>>>(n, -1.0, w, w);
+  k_axpy<<<nblocks(n), kThreads, 0, s>>>(n, 1.0, b, w);
+  double rn2;
+  rc = dot_host(w, 1, w, &rn2);
+  if (rc) return rc;
+  *final_res = std::sqrt(rn2) / bnorm;
+  *iters = total;
+  if (*final_res > rtol * 10.0) {
+    set_error("trace_solve: GMRES did not converge");
+    return HDG_ERR_NOT_CONVERGED;
+  }
+  return HDG_OK;
+}
+
+int trace_solve(hdg_ctx* ctx, const double* S, const double* g, double* dVhat, int method, double rtol, int max_it,
+                int* iters, double* final_res, cudaStream_t s) {
+  if (method == HDG_SOLVER_AUTO) method = ctx->ntrace <= 4096 ? HDG_SOLVER_DENSE : HDG_SOLVER_GMRES;
+  if (method == HDG_SOLVER_DENSE) {
+    if (ctx->ntrace > 16384) {
+      set_error("trace_solve: dense solver limited to n_trace <= 16384");
+      return HDG_ERR_INVALID_ARG;
+    }
+    *iters = 1;
+    return dense_solve(ctx, S, g, dVhat, final_res, s);
+  }
+  return gmres_solve(ctx, S, g, dVhat, rtol, max_it, iters, final_res, s);
+}
+
+}  // namespace hdg

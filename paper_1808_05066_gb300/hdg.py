@@ -1,0 +1,278 @@
+"""ctypes binding of include/hdg.h: the same entry points, argument marshalling only.
+
+Device buffers are passed as torch CUDA tensors (or raw integer addresses); streams as
+torch.cuda.Stream / raw handles (None = the current torch stream). All numerical work
+runs in libhdg.so; if the library cannot be loaded, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, byref, c_double, c_int, c_int32, c_int64, c_void_p
+
+import numpy as np
+
+from . import _build
+
+HDG_OK = 0
+HDG_ERR_INVALID_ARG = 1
+HDG_ERR_NONPHYSICAL = 2
+HDG_ERR_SINGULAR = 3
+HDG_ERR_REFINE = 4
+HDG_ERR_NOT_CONVERGED = 5
+HDG_ERR_TIMEOUT = 6
+HDG_ERR_CUDA = 7
+HDG_ERR_UNSUPPORTED = 8
+HDG_PREC_FP64 = 0
+HDG_PREC_MIXED = 1
+HDG_SOLVER_AUTO = 0
+HDG_SOLVER_GMRES = 1
+HDG_SOLVER_DENSE = 2
+
+EXPORTED = [
+    "hdg_mesh_create", "hdg_mesh_destroy", "hdg_mesh_get_info", "hdg_mesh_copy_topology",
+    "hdg_mesh_copy_coords", "hdg_ctx_create", "hdg_ctx_destroy", "hdg_prim_to_entropy",
+    "hdg_history", "hdg_assemble_condense", "hdg_trace_solve", "hdg_recover_interior",
+    "hdg_trace_matvec", "hdg_residual_norm", "hdg_newton_step", "hdg_profile_enable",
+    "hdg_profile_reset", "hdg_profile_read", "hdg_last_error",
+]
+HDG_KERNEL_POINTWISE = 0
+HDG_KERNEL_ASSEMBLE = 1
+HDG_KERNEL_CONDENSE = 2
+HDG_KERNEL_MIXED = 3
+HDG_KERNEL_TRACE = 4
+HDG_KERNEL_OTHER = 5
+HDG_KERNEL_CLASSES = 6
+
+
+class HdgError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"hdg error {code}: {msg}")
+        self.code = code
+
+
+class hdg_physics(ctypes.Structure):
+    _fields_ = [("gamma", c_double), ("mach", c_double), ("reynolds", c_double), ("prandtl", c_double)]
+
+
+class hdg_mesh_info(ctypes.Structure):
+    _fields_ = [("dim", c_int32), ("p", c_int32), ("quad_points", c_int32), ("m", c_int32),
+                ("Np", c_int32), ("Nf", c_int32), ("nF", c_int32), ("NG", c_int32), ("NGF", c_int32),
+                ("nv", c_int32), ("nt", c_int32), ("geo_stride", c_int32),
+                ("n_elem", c_int64), ("n_faces", c_int64), ("n_trace", c_int64)]
+
+
+def _load():
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: run __graft_entry__.build() (nvcc, sm_103a) first")
+    lib = ctypes.CDLL(path)
+    P = c_void_p
+    sig = {
+        "hdg_mesh_create": (c_int, [c_int, POINTER(c_int64), POINTER(c_double), POINTER(c_double), c_int, c_int,
+                                    POINTER(c_void_p)]),
+        "hdg_mesh_destroy": (None, [P]),
+        "hdg_mesh_get_info": (c_int, [P, POINTER(hdg_mesh_info)]),
+        "hdg_mesh_copy_topology": (c_int, [P, P, P, P]),
+        "hdg_mesh_copy_coords": (c_int, [P, P, P, P]),
+        "hdg_ctx_create": (c_int, [P, POINTER(hdg_physics), c_int, POINTER(c_void_p)]),
+        "hdg_ctx_destroy": (None, [P]),
+        "hdg_prim_to_entropy": (c_int, [P, P, c_int64, P, P]),
+        "hdg_history": (c_int, [P, P, P, c_double, c_double, P, P]),
+        "hdg_assemble_condense": (c_int, [P, P, P, P, c_double, c_int, P, P, P, P, P, P]),
+        "hdg_trace_solve": (c_int, [P, P, P, P, c_int, c_double, c_int, POINTER(c_int), POINTER(c_double), P]),
+        "hdg_recover_interior": (c_int, [P, P, P, P, P]),
+        "hdg_trace_matvec": (c_int, [P, P, P, P, P]),
+        "hdg_residual_norm": (c_int, [P, P, POINTER(c_double), P]),
+        "hdg_newton_step": (c_int, [P, P, P, P, c_double, c_int, c_double, c_int, POINTER(c_int),
+                                    POINTER(c_double), P]),
+        "hdg_profile_enable": (c_int, [P, c_int]),
+        "hdg_profile_reset": (c_int, [P]),
+        "hdg_profile_read": (c_int, [P, c_int, POINTER(c_int64), POINTER(c_double)]),
+        "hdg_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = _load()
+LIB_PATH = _build.LIB
+
+
+def _check(code):
+    if code != HDG_OK:
+        raise HdgError(code, _lib.hdg_last_error().decode())
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    raise TypeError(f"cannot pass {type(x)} as a pointer")
+
+
+def _stream(s):
+    if s is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+# ------------------------------------------------------------------ raw entry points
+def hdg_mesh_create(dim, n, lo, hi, p, quad_points=0):
+    n3 = (c_int64 * 3)(*(list(n) + [1] * (3 - len(n))))
+    lo3 = (c_double * 3)(*(list(lo) + [0.0] * (3 - len(lo))))
+    hi3 = (c_double * 3)(*(list(hi) + [1.0] * (3 - len(hi))))
+    h = c_void_p()
+    _check(_lib.hdg_mesh_create(dim, n3, lo3, hi3, p, quad_points, byref(h)))
+    return h.value
+
+
+def hdg_mesh_destroy(mesh):
+    _lib.hdg_mesh_destroy(mesh)
+
+
+def hdg_mesh_get_info(mesh):
+    info = hdg_mesh_info()
+    _check(_lib.hdg_mesh_get_info(mesh, byref(info)))
+    return {k: getattr(info, k) for k, _ in hdg_mesh_info._fields_}
+
+
+def hdg_mesh_copy_topology(mesh):
+    i = hdg_mesh_get_info(mesh)
+    face_of = np.zeros((i["n_elem"], i["nF"]), np.int32)
+    fnode_map = np.zeros((i["n_elem"], i["nF"], i["Nf"]), np.int32)
+    face_side = np.zeros((i["n_faces"], 2), np.int32)
+    _check(_lib.hdg_mesh_copy_topology(mesh, _ptr(face_of), _ptr(fnode_map), _ptr(face_side)))
+    return face_of, fnode_map, face_side
+
+
+def hdg_mesh_copy_coords(mesh):
+    i = hdg_mesh_get_info(mesh)
+    xnode = np.zeros((i["n_elem"], i["Np"], i["dim"]))
+    xfnode = np.zeros((i["n_faces"], i["Nf"], i["dim"]))
+    geo = np.zeros((i["n_elem"], i["geo_stride"]))
+    _check(_lib.hdg_mesh_copy_coords(mesh, _ptr(xnode), _ptr(xfnode), _ptr(geo)))
+    return xnode, xfnode, geo
+
+
+def hdg_ctx_create(mesh, gamma=1.4, mach=0.5, reynolds=0.0, prandtl=0.71, device=0):
+    ph = hdg_physics(gamma, mach, reynolds, prandtl)
+    h = c_void_p()
+    _check(_lib.hdg_ctx_create(mesh, byref(ph), device, byref(h)))
+    return h.value
+
+
+def hdg_ctx_destroy(ctx):
+    _lib.hdg_ctx_destroy(ctx)
+
+
+def hdg_prim_to_entropy(ctx, prim, n_points, v, stream=None):
+    _check(_lib.hdg_prim_to_entropy(ctx, _ptr(prim), n_points, _ptr(v), _stream(stream)))
+
+
+def hdg_history(ctx, V0, V1, c0, c1, hist, stream=None):
+    _check(_lib.hdg_history(ctx, _ptr(V0), _ptr(V1), c0, c1, _ptr(hist), _stream(stream)))
+
+
+def hdg_assemble_condense(ctx, V, Vhat, hist, mass_coef, precision, S, g, recov, R, elem_status=None,
+                          stream=None):
+    _check(_lib.hdg_assemble_condense(ctx, _ptr(V), _ptr(Vhat), _ptr(hist), mass_coef, precision, _ptr(S),
+                                      _ptr(g), _ptr(recov), _ptr(R), _ptr(elem_status), _stream(stream)))
+
+
+def hdg_trace_solve(ctx, S, g, dVhat, method=HDG_SOLVER_AUTO, rtol=1e-12, max_it=600, stream=None):
+    it = c_int()
+    res = c_double()
+    _check(_lib.hdg_trace_solve(ctx, _ptr(S), _ptr(g), _ptr(dVhat), method, rtol, max_it, byref(it), byref(res),
+                                _stream(stream)))
+    return it.value, res.value
+
+
+def hdg_recover_interior(ctx, recov, dVhat, dV, stream=None):
+    _check(_lib.hdg_recover_interior(ctx, _ptr(recov), _ptr(dVhat), _ptr(dV), _stream(stream)))
+
+
+def hdg_trace_matvec(ctx, S, x, y, stream=None):
+    _check(_lib.hdg_trace_matvec(ctx, _ptr(S), _ptr(x), _ptr(y), _stream(stream)))
+
+
+def hdg_residual_norm(ctx, R, stream=None):
+    out = c_double()
+    _check(_lib.hdg_residual_norm(ctx, _ptr(R), byref(out), _stream(stream)))
+    return out.value
+
+
+def hdg_newton_step(ctx, V, Vhat, hist, mass_coef, precision=HDG_PREC_FP64, tol=1e-10, max_newton=10,
+                    stream=None):
+    it = c_int()
+    res = c_double()
+    _check(_lib.hdg_newton_step(ctx, _ptr(V), _ptr(Vhat), _ptr(hist), mass_coef, precision, tol, max_newton,
+                                byref(it), byref(res), _stream(stream)))
+    return it.value, res.value
+
+
+def hdg_profile_enable(ctx, on=True):
+    _check(_lib.hdg_profile_enable(ctx, 1 if on else 0))
+
+
+def hdg_profile_reset(ctx):
+    _check(_lib.hdg_profile_reset(ctx))
+
+
+def hdg_profile_read(ctx, kernel_class=-1):
+    n = c_int64()
+    ms = c_double()
+    _check(_lib.hdg_profile_read(ctx, kernel_class, byref(n), byref(ms)))
+    return n.value, ms.value
+
+
+# ------------------------------------------------------------------ thin owners
+class Mesh:
+    """Owns an hdg_mesh_t; exposes its info and host copies of its tables."""
+
+    def __init__(self, dim, n, lo, hi, p, quad_points=0):
+        n = [n] * dim if np.isscalar(n) else list(n)
+        lo = [lo] * dim if np.isscalar(lo) else list(lo)
+        hi = [hi] * dim if np.isscalar(hi) else list(hi)
+        self.handle = hdg_mesh_create(dim, n, lo, hi, p, quad_points)
+        self.info = hdg_mesh_get_info(self.handle)
+
+    def topology(self):
+        return hdg_mesh_copy_topology(self.handle)
+
+    def coords(self):
+        return hdg_mesh_copy_coords(self.handle)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            hdg_mesh_destroy(h)
+            self.handle = None
+
+
+class Context:
+    """Owns an hdg_ctx_t bound to a Mesh (kept alive by this object)."""
+
+    def __init__(self, mesh: Mesh, gamma=1.4, mach=0.5, reynolds=0.0, prandtl=0.71, device=0):
+        self.mesh = mesh
+        self.handle = hdg_ctx_create(mesh.handle, gamma, mach, reynolds, prandtl, device)
+        self.device = device
+
+    def close(self):
+        if getattr(self, "handle", None):
+            hdg_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        self.close()

@@ -1,0 +1,112 @@
+"""Device-resident workloads for the C-ABI path.
+
+Builds the named synthetic workload of workloads.py on the GPU: the C-ABI mesh, the
+context, the initial entropy variables (closed-form primitive fields at the element and
+face nodes, converted by hdg_prim_to_entropy), the trace perturbation, the BDF history
+and the output buffers of hdg_assemble_condense. No method arithmetic happens here.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import torch
+
+import workloads as wl
+
+from . import hdg
+
+
+def _prim(name, spec, x):
+    rho, vel, p = wl.primitive_state(name, x)
+    return np.concatenate([rho[..., None], vel, p[..., None]], axis=-1)
+
+
+class DeviceWorkload:
+    """State and buffers of one workload on one GPU.
+
+    The time term is BDF2 with both history levels equal to the initial state
+    (u^{n-1} = u^n), dt from the workload: mass_coef = 3/(2 dt), history
+    c0 = 2/dt, c1 = -1/(2 dt)."""
+
+    def __init__(self, name: str, device: int = 0, n_override: int | None = None, outputs: bool = True):
+        spec = dict(wl.WORKLOADS[name])
+        if n_override:
+            spec["n"] = n_override
+        self.name, self.spec = name, spec
+        self.dev = torch.device("cuda", device)
+        d = spec["dim"]
+        self.mesh = hdg.Mesh(d, spec["n"], spec["lo"], spec["hi"], spec["p"])
+        self.ctx = hdg.Context(self.mesh, 1.4, spec["mach"], spec["reynolds"], spec["prandtl"], device)
+        self.info = self.mesh.info
+        xnode, xfnode, _ = self.mesh.coords()
+        self.V = self._entropy(_prim(name, spec, xnode))
+        Vh = self._entropy(_prim(name, spec, xfnode))
+        eps = spec.get("trace_noise", 0.0)
+        if eps:
+            Vh = torch.from_numpy(wl.perturb(Vh.cpu().numpy(), eps, spec["seed"])).to(self.dev)
+        self.Vhat = Vh.contiguous()
+        dt = spec["dt"]
+        self.dt = dt
+        if spec.get("bdf", 2) == 2:
+            self.mass_coef = 1.5 / dt
+            c0, c1, V1 = 2.0 / dt, -0.5 / dt, self.V
+        else:
+            self.mass_coef = 1.0 / dt
+            c0, c1, V1 = 1.0 / dt, 0.0, None
+        self.hist = torch.empty_like(self.V)
+        hdg.hdg_history(self.ctx.handle, self.V, V1, c0, c1, self.hist)
+        if outputs:
+            self.alloc_outputs()
+        torch.cuda.synchronize(self.dev)
+
+    def _entropy(self, prim):
+        t = torch.from_numpy(np.ascontiguousarray(prim)).to(self.dev)
+        out = torch.empty_like(t)
+        hdg.hdg_prim_to_entropy(self.ctx.handle, t, t.numel() // t.shape[-1], out)
+        return out
+
+    def alloc_outputs(self):
+        i = self.info
+        E, nv, nt = i["n_elem"], i["nv"], i["nt"]
+        f64 = dict(dtype=torch.float64, device=self.dev)
+        self.S = torch.empty((E, nt, nt), **f64)
+        self.g = torch.empty((E, nt), **f64)
+        self.recov = torch.empty((E, nv * nt + nv), **f64)
+        self.R = torch.empty((E, nv + nt), **f64)
+        self.status = torch.zeros(E, dtype=torch.int32, device=self.dev)
+
+    def assemble(self, precision=hdg.HDG_PREC_FP64, V=None, Vhat=None, stream=None):
+        hdg.hdg_assemble_condense(self.ctx.handle, self.V if V is None else V, self.Vhat if Vhat is None else Vhat,
+                                  self.hist, self.mass_coef, precision, self.S, self.g, self.recov, self.R,
+                                  self.status, stream)
+
+    @property
+    def n_elem(self):
+        return self.info["n_elem"]
+
+
+def bench_workload_name() -> str:
+    return "ns3d_p3_tgv"
+
+
+def flops_per_element(info: dict, viscous: bool, kernel: str) -> float:
+    """Useful floating-point operations per element of the FP64 form, counted from the
+    loop structure of the kernels (multiply + add = 2 flops):
+      assemble: volume contraction per (i, l): NP x [NP x ng x NR + NT' x ng x (NR-1)]
+                + the left factor NP x ng x NR x (D+1); face contraction per face and (i, l):
+                NFN x NZ x NGF x NRF + NFN x NGF x NRF;
+      condense: LU NV^3/3 + solves (NT + 1) NV^2 + Schur NT^2 NV + NT NV."""
+    D, M = info["dim"], info["m"]
+    NP, NFN, NF, NG, NGF = info["Np"], info["Nf"], info["nF"], info["NG"], info["NGF"]
+    NV, NT = info["nv"], info["nt"]
+    NZ = NP + NF * NFN
+    NR = D + 1 if viscous else 1
+    NRF = D + 2 if viscous else 2
+    if kernel == "assemble":
+        vol = M * M * (NP * (NP * NG * NR + NF * NFN * NG * (NR - 1)) + NP * NG * NR * (D + 1))
+        face = NF * M * M * (NFN * NZ * NGF * NRF + NFN * NGF * NRF)
+        return 2.0 * (vol + face)
+    if kernel == "condense":
+        return 2.0 * (NV ** 3 / 3.0 + (NT + 1) * NV ** 2 + NT * NT * NV + NT * NV)
+    raise ValueError(kernel)

@@ -1,0 +1,185 @@
+"""Parity of the CUDA path (through the C-ABI) with the FP64 oracle, element by element,
+on the same seeded inputs. Tolerances: condensed blocks S, g and the recovery data
+<= 1e-10 relative Frobenius per element (the stated accuracy target; the FP64 form is
+expected near 1e-13), residuals <= 1e-12 relative."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import workloads as wl
+from hdg_cases import CASES, GpuCase, oracle_hist, oracle_setup, prim_array, rel_fro
+
+pytestmark = pytest.mark.gpu
+
+TOL_BLOCK = 1e-10
+TOL_RES = 1e-12
+
+
+def _sample(E, k, seed=0):
+    if E <= k:
+        return list(range(E))
+    rng = np.random.default_rng(seed)
+    s = set(rng.choice(E, size=k - 2, replace=False).tolist())
+    s.update([0, E - 1])
+    return sorted(s)
+
+
+def test_prim_to_entropy_matches_oracle():
+    from oracle import physics as ph
+    gc = GpuCase(CASES["euler2d_p2"])
+    rng = np.random.default_rng(3)
+    for d in (2, 3):
+        n = 1000
+        rho = rng.uniform(0.5, 2, n); vel = rng.normal(size=(n, d)); p = rng.uniform(0.5, 3, n)
+        prim = np.concatenate([rho[:, None], vel, p[:, None]], axis=1)
+        if d == 3:
+            gc3 = GpuCase(CASES["ns3d_p1"])
+            v_gpu = gc3.to_entropy(prim).cpu().numpy()
+        else:
+            v_gpu = gc.to_entropy(prim).cpu().numpy()
+        v_ora = ph.v_of_u(ph.u_of_primitives(rho, vel, p, 1.4), 1.4)
+        assert np.allclose(v_gpu, v_ora, rtol=1e-14, atol=1e-14)
+
+
+@pytest.mark.parametrize("name", ["euler2d_p2", "ns2d_p3", "ns3d_p2"])
+def test_history_matches_oracle(name):
+    case = CASES[name]
+    gc = GpuCase(case)
+    prob, Q, V, Vh = oracle_setup(case)
+    h_gpu = gc.history().cpu().numpy()
+    h_ora = oracle_hist(prob, V, case)
+    assert rel_fro(h_gpu, h_ora) < 1e-13
+
+
+@pytest.mark.parametrize("name,nsample", [("euler2d_p2", 128), ("ns2d_p3", 18), ("ns2d_p4", 18),
+                                          ("ns3d_p1", 30), ("ns3d_p2", 12), ("ns3d_p3", 5)])
+def test_assemble_condense_matches_oracle(name, nsample):
+    case = CASES[name]
+    gc = GpuCase(case)
+    prob, Q, V, Vh = oracle_setup(case)
+    # same input state on both sides (to rounding)
+    assert rel_fro(gc.V.cpu().numpy(), V) < 1e-14
+    assert rel_fro(gc.Vhat.cpu().numpy(), Vh) < 1e-14
+    hist_o = oracle_hist(prob, V, case)
+    gc.assemble(gc.history())
+    S, g = gc.S.cpu().numpy(), gc.g.cpu().numpy()
+    rec, R = gc.recov.cpu().numpy(), gc.R.cpu().numpy()
+    assert int(gc.status.abs().sum()) == 0
+    nv, nt = gc.info["nv"], gc.info["nt"]
+    for e in _sample(prob.mesh.E, nsample):
+        L = prob.condense(e, None if Q is None else Q[e], V[e], prob.gather_trace(Vh, e), case.mass_coef,
+                          hist_o[e])
+        nq = L["Rl"].size - nv
+        # raw residuals, relative to the size of the terms they sum (time term and
+        # face fluxes), since a residual near equilibrium is a cancelled sum
+        Rv = L["Rl"][nq:]
+        scale = max(np.abs(Rv).max(), np.abs(L["Rt"]).max(), np.abs(hist_o[e]).max(), 1.0)
+        assert np.abs(Rv - R[e, :nv]).max() <= TOL_RES * scale, (e, "R_v")
+        assert np.abs(L["Rt"] - R[e, nv:]).max() <= TOL_RES * scale, (e, "R_t")
+        assert rel_fro(S[e], L["S"]) < TOL_BLOCK, (e, rel_fro(S[e], L["S"]))
+        assert rel_fro(g[e], L["g"]) < TOL_BLOCK, (e, rel_fro(g[e], L["g"]))
+        X = rec[e, :nv * nt].reshape(nv, nt)
+        y = rec[e, nv * nt:]
+        assert rel_fro(X, L["X"][nq:]) < TOL_BLOCK, (e, "X")
+        assert rel_fro(y, L["y"][nq:]) < TOL_BLOCK, (e, "y")
+
+
+def test_chunked_launch_ragged_tail(monkeypatch):
+    """Element chunks of 7 over 128 elements (18 full chunks + a ragged tail of 2) give
+    the same output as one chunk, bit for bit."""
+    case = CASES["euler2d_p2"]
+    gc = GpuCase(case)
+    hist = gc.history()
+    gc.assemble(hist)
+    S1 = gc.S.clone(); rec1 = gc.recov.clone()
+    monkeypatch.setenv("HDG_ELEMENT_CHUNK", "7")
+    gc2 = GpuCase(case)
+    gc2.assemble(hist)
+    assert bool((gc2.S == S1).all()) and bool((gc2.recov == rec1).all())
+
+
+@pytest.mark.parametrize("method", [2, 1])
+def test_trace_solve_and_recovery_match_oracle(method):
+    """Config-1 workload: assembled trace solve (dense LU / GMRES) and the recovery
+    against the oracle's dense solve and recovery."""
+    from oracle.hdg import newton_iteration
+    case = CASES["euler2d_p2"]
+    gc = GpuCase(case)
+    prob, Q, V, Vh = oracle_setup(case)
+    hist_o = oracle_hist(prob, V, case)
+    Qn, Vn, Vhn, rn, dvh, _ = newton_iteration(prob, Q, V, Vh, case.mass_coef, hist_o)
+    gc.assemble(gc.history())
+    torch = gc.torch
+    dVh = torch.empty_like(gc.Vhat)
+    it, res = gc.hdg.hdg_trace_solve(gc.ctx.handle, gc.S, gc.g, dVh, method, 1e-13, 500)
+    assert res < 1e-11
+    assert rel_fro(dVh.cpu().numpy().ravel(), dvh) < 1e-9
+    dV = torch.empty_like(gc.V)
+    gc.hdg.hdg_recover_interior(gc.ctx.handle, gc.recov, dVh, dV)
+    assert rel_fro(dV.cpu().numpy(), Vn - V) < 1e-9
+    rn_gpu = gc.hdg.hdg_residual_norm(gc.ctx.handle, gc.R)
+    assert abs(rn_gpu - rn) <= 1e-12 * rn
+
+
+def test_newton_step_matches_oracle():
+    """One BDF1 step of the 2D Euler p=2 vortex workload (dt = 0.05) to |R| <= 1e-10:
+    same iteration count and the same converged state as the oracle."""
+    from oracle.hdg import time_step
+    import dataclasses
+    case = dataclasses.replace(CASES["euler2d_p2"], noise=0.0)
+    gc = GpuCase(case)
+    prob, Q, V, Vh = oracle_setup(case)
+    dt = 0.05
+    res = time_step(prob, None, V, Vh, [V], 1, dt, tol=1e-10, max_it=10)
+    hist = gc.torch.empty_like(gc.V)
+    gc.hdg.hdg_history(gc.ctx.handle, gc.V.clone(), None, 1.0 / dt, 0.0, hist)
+    V_gpu = gc.V.clone(); Vh_gpu = gc.Vhat.clone()
+    it, rn = gc.hdg.hdg_newton_step(gc.ctx.handle, V_gpu, Vh_gpu, hist, 1.0 / dt, 0, 1e-10, 10)
+    assert it == res.iters
+    assert rel_fro(V_gpu.cpu().numpy(), res.V) < 1e-11
+    assert rel_fro(Vh_gpu.cpu().numpy(), res.Vhat) < 1e-11
+
+
+def test_nonphysical_state_sets_status():
+    case = CASES["euler2d_p2"]
+    gc = GpuCase(case)
+    V = gc.V.clone()
+    V[5, 0, -1] = 0.3          # v_m > 0: not a physical state
+    gc.V = V
+    gc.assemble(None)
+    st = gc.status.cpu().numpy()
+    assert st[5] & 1
+    assert (st[np.arange(len(st)) != 5] & 1).sum() == 0
+
+
+def test_bench_workload_full_size_sampled():
+    """The 82,944-element 3D NS p=3 workload in the launch configuration bench.py times
+    (FP64 form): sampled elements, including the first and the last, against the oracle."""
+    import torch
+    from oracle import physics as ph
+    from oracle.hdg import Problem, interpolate_state
+    from oracle.mesh import Mesh
+    from paper_1808_05066_gb300.workload import DeviceWorkload
+    name = "ns3d_p3_tgv"
+    W = DeviceWorkload(name)
+    W.status.zero_()
+    W.assemble()
+    torch.cuda.synchronize()
+    assert int(W.status.abs().sum()) == 0
+    spec = wl.WORKLOADS[name]
+    mesh = Mesh(spec["dim"], spec["n"], spec["lo"], spec["hi"], spec["p"])
+    prob = Problem(mesh, ph.Physics(mach=spec["mach"], reynolds=spec["reynolds"], prandtl=spec["prandtl"]))
+    V, Vh = interpolate_state(prob, lambda x: wl.primitive_state(name, x))
+    Vh = wl.perturb(Vh, spec["trace_noise"], spec["seed"])
+    assert rel_fro(W.V.cpu().numpy(), V) < 1e-14
+    dt = spec["dt"]
+    for e in _sample(mesh.E, 4, seed=5):
+        vh = prob.gather_trace(Vh, e)
+        Q = prob.consistent_q(e, V[e], vh)
+        hist = prob.history_weak(e, [V[e], V[e]], [2.0 / dt, -0.5 / dt])
+        assert rel_fro(W.hist[e].cpu().numpy().ravel(), hist.ravel()) < 1e-13
+        L = prob.condense(e, Q, V[e], vh, 1.5 / dt, hist)
+        assert rel_fro(W.S[e].cpu().numpy(), L["S"]) < TOL_BLOCK, e
+        assert rel_fro(W.g[e].cpu().numpy(), L["g"]) < TOL_BLOCK, e

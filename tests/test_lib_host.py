@@ -1,0 +1,68 @@
+"""Host-side checks of the C-ABI library (no GPU needed): it loads, exports every
+symbol include/hdg.h declares, rejects invalid arguments, and its mesh (an independent
+C++ implementation of the numbering rules) agrees with the oracle's mesh."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle.mesh import Mesh as OMesh
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _lib():
+    from paper_1808_05066_gb300 import hdg
+    return hdg
+
+
+def test_library_exports_every_declared_symbol():
+    hdg = _lib()
+    with open(os.path.join(ROOT, "include", "hdg.h")) as fh:
+        text = fh.read()
+    declared = set(re.findall(r"^\s*(?:int|void|const char\*)\s+(hdg_\w+)\s*\(", text, re.M))
+    assert declared, "no declarations parsed"
+    assert declared == set(hdg.EXPORTED)
+    for name in declared:
+        assert hasattr(hdg._lib, name), name
+
+
+def test_invalid_arguments_are_rejected():
+    hdg = _lib()
+    with pytest.raises(hdg.HdgError) as ei:
+        hdg.hdg_mesh_create(2, [0, 4], [0, 0], [1, 1], 2)
+    assert ei.value.code == hdg.HDG_ERR_INVALID_ARG
+    with pytest.raises(hdg.HdgError):
+        hdg.hdg_mesh_create(4, [2, 2, 2], [0, 0, 0], [1, 1, 1], 2)
+    with pytest.raises(hdg.HdgError):
+        hdg.hdg_mesh_create(2, [2, 2], [0, 0], [1, 1], 0)
+
+
+@pytest.mark.parametrize("dim,n,p", [(2, 3, 2), (2, 2, 4), (3, 2, 3), (3, 1, 1), (3, 3, 2)])
+def test_mesh_matches_oracle(dim, n, p):
+    hdg = _lib()
+    L = 2.5
+    m = hdg.Mesh(dim, n, 0.0, L, p)
+    o = OMesh(dim, n, 0.0, L, p)
+    info = m.info
+    assert info["n_elem"] == o.E and info["n_faces"] == o.nFaces
+    assert info["Np"] == o.ref.Np and info["Nf"] == o.ref.Nf
+    assert info["NG"] == len(o.ref.qw) and info["NGF"] == len(o.ref.fqw)
+    face_of, fnode_map, face_side = m.topology()
+    assert np.array_equal(face_of, o.face_of)
+    assert np.array_equal(fnode_map, o.fnode_map)
+    sides = np.array([[e * o.ref.nF + f for (e, f) in s] for s in o.face_elems])
+    assert np.array_equal(face_side, sides)
+    xnode, xfnode, geo = m.coords()
+    assert np.allclose(xnode, o.xnode, atol=1e-13)
+    d = dim
+    assert np.allclose(geo[:, :d * d].reshape(-1, d, d), o.Jinv, atol=1e-12)
+    assert np.allclose(geo[:, d * d], np.abs(o.detJ), atol=1e-13)
+    for f in range(d + 1):
+        base = d * d + 1 + f * (d + 1)
+        assert np.allclose(geo[:, base:base + d], o.normal[:, f], atol=1e-13)
+        assert np.allclose(geo[:, base + d], o.face_jac[:, f], atol=1e-13)
+    for F, sd in enumerate(o.face_elems):
+        e, f = sd[0]
+        assert np.allclose(xfnode[F], o.xnode[e, o.ref.face_nodes[f]], atol=1e-13)
