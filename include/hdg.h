@@ -160,13 +160,14 @@ int hdg_newton_step(hdg_ctx_t ctx, double* V, double* Vhat, const double* hist, 
  * recorded events and returns, for one class (HDG_KERNEL_*, or -1 for all), the number
  * of launches and their summed device time in milliseconds since the last reset. */
 enum {
-  HDG_KERNEL_POINTWISE = 0, /* FP64 form: fluxes and pointwise Jacobians            */
-  HDG_KERNEL_ASSEMBLE = 1,  /* FP64 form: quadrature contractions into A, B, C, D    */
-  HDG_KERNEL_CONDENSE = 2,  /* FP64 form: LU, X = A^{-1}B, S = D - C X              */
-  HDG_KERNEL_MIXED = 3,     /* mixed form: fused assemble-factor-condense           */
-  HDG_KERNEL_TRACE = 4,     /* trace operator, preconditioner, solver kernels       */
-  HDG_KERNEL_OTHER = 5,     /* history, conversions, recovery, norms, updates       */
-  HDG_KERNEL_CLASSES = 6
+  HDG_KERNEL_POINTWISE = 0,        /* fluxes and pointwise Jacobians (both forms)          */
+  HDG_KERNEL_ASSEMBLE = 1,         /* FP64 form: quadrature contractions into A, B, C, D    */
+  HDG_KERNEL_CONDENSE = 2,         /* FP64 form: LU, X = A^{-1}B, S = D - C X              */
+  HDG_KERNEL_MIXED_ASSEMBLE = 3,   /* mixed form: double-float contractions               */
+  HDG_KERNEL_MIXED_CONDENSE = 4,   /* mixed form: FP32 LU, refinement, double-float Schur  */
+  HDG_KERNEL_TRACE = 5,            /* trace operator, preconditioner, solver kernels       */
+  HDG_KERNEL_OTHER = 6,            /* history, conversions, recovery, norms, updates       */
+  HDG_KERNEL_CLASSES = 7
 };
 int hdg_profile_enable(hdg_ctx_t ctx, int on);
 int hdg_profile_reset(hdg_ctx_t ctx);

@@ -20,6 +20,7 @@
 //   k_condense   one CTA per element: LU with partial pivoting of A' in shared memory,
 //                triangular solves for X and y, Schur products for S and g.
 #pragma once
+#include "dfloat.cuh"
 #include "hdg_device.cuh"
 
 namespace hdg {
@@ -62,7 +63,11 @@ HDG_DEVI void load_element(const AssembleArgs& a, int64_t e, double (*z)[C::M], 
 // ------------------------------------------------------------------------------------
 // k_pointwise
 // ------------------------------------------------------------------------------------
-template <class C>
+HDG_DEVI void put(double* p, int i, double v) { p[i] = v; }
+HDG_DEVI void put(df2* p, int i, double v) { p[i] = df_from(v); }
+
+// OutT = double (FP64 form) or df2 (mixed form: per-point tensors as double-floats)
+template <class C, class OutT = double>
 __global__ void __launch_bounds__(128) k_pointwise(AssembleArgs a, DevTables T, PhysParams ph) {
   constexpr int D = C::D, M = C::M, NP = C::NP, NFN = C::NFN, NF = C::NF, NG = C::NG, NGF = C::NGF;
   __shared__ double z[C::NZ][M];
@@ -123,25 +128,25 @@ __global__ void __launch_bounds__(128) k_pointwise(AssembleArgs a, DevTables T, 
       for (int i = 0; i < M; ++i)
         for (int j = 0; j < D; ++j) F[i][j] = F[i][j] + Gv[i][j];
     }
-    double* out = a.ptv + (le * NG + g) * C::PT_VOL;
-    double* MU = out;
-    double* FR = MU + M;
-    double* T0 = FR + D * M;
-    double* T1 = T0 + M * M;
-    double* T2 = T1 + D * M * M;
+    OutT* out = reinterpret_cast<OutT*>(a.ptv) + (le * NG + g) * C::PT_VOL;
+    OutT* MU = out;
+    OutT* FR = MU + M;
+    OutT* T0 = FR + D * M;
+    OutT* T1 = T0 + M * M;
+    OutT* T2 = T1 + D * M * M;
     for (int i = 0; i < M; ++i) {
-      MU[i] = W * a.mass_coef * u[i].v;
-      for (int l = 0; l < M; ++l) T0[i * M + l] = W * a.mass_coef * u[i].d[l];
+      put(MU, i, W * a.mass_coef * u[i].v);
+      for (int l = 0; l < M; ++l) put(T0, i * M + l, W * a.mass_coef * u[i].d[l]);
     }
     for (int r = 0; r < D; ++r)
       for (int i = 0; i < M; ++i) {
         double s = 0.0;
         for (int j = 0; j < D; ++j) s += Jinv[r * D + j] * F[i][j].v;
-        FR[r * M + i] = -W * s;
+        put(FR, r * M + i, -W * s);
         for (int l = 0; l < M; ++l) {
           double t = 0.0;
           for (int j = 0; j < D; ++j) t += Jinv[r * D + j] * F[i][j].d[l];
-          T1[(r * M + i) * M + l] = -W * t;
+          put(T1, (r * M + i) * M + l, -W * t);
         }
       }
     if (C::VISC) {
@@ -157,7 +162,7 @@ __global__ void __launch_bounds__(128) k_pointwise(AssembleArgs a, DevTables T, 
             for (int i = 0; i < M; ++i) {
               double s = 0.0;
               for (int j = 0; j < D; ++j) s += Jinv[r * D + j] * Gq[i][j];
-              T2[((r * M + i) * M + l) * D + k] = -W * s;
+              put(T2, ((r * M + i) * M + l) * D + k, -W * s);
             }
         }
     }
@@ -236,18 +241,18 @@ __global__ void __launch_bounds__(128) k_pointwise(AssembleArgs a, DevTables T, 
     prim_of_v<D>(vd, ph.gamma, rv, velv, pv);
     cons_and_flux<D>(rv, velv, pv, ph.gamma, (Dual<M>*)nullptr, Fv);
     bad = bad || !(rv.v > 0.0) || !(pv.v > 0.0);
-    double* out = a.ptf + ((le * NF + f) * NGF + gf) * C::PT_FACE;
-    double* HF = out;
-    double* U0 = HF + M;
-    double* U1 = U0 + M * M;
-    double* U2 = U1 + M * M;
+    OutT* out = reinterpret_cast<OutT*>(a.ptf) + ((le * NF + f) * NGF + gf) * C::PT_FACE;
+    OutT* HF = out;
+    OutT* U0 = HF + M;
+    OutT* U1 = U0 + M * M;
+    OutT* U2 = U1 + M * M;
     for (int i = 0; i < M; ++i) {
       Dual<M> s = Fv[i][0] * n[0];
       for (int j = 1; j < D; ++j) s = s + Fv[i][j] * n[j];
-      HF[i] = Wf * (hA[i].v + 0.5 * s.v);
+      put(HF, i, Wf * (hA[i].v + 0.5 * s.v));
       for (int l = 0; l < M; ++l) {
-        U0[i * M + l] = Wf * (0.5 * s.d[l] + 0.5 * lam.v * uh[i].d[l]);
-        U1[i * M + l] = Wf * hA[i].d[l];
+        put(U0, i * M + l, Wf * (0.5 * s.d[l] + 0.5 * lam.v * uh[i].d[l]));
+        put(U1, i * M + l, Wf * hA[i].d[l]);
       }
     }
     if (C::VISC) {
@@ -261,7 +266,7 @@ __global__ void __launch_bounds__(128) k_pointwise(AssembleArgs a, DevTables T, 
           for (int i = 0; i < M; ++i) {
             double s = 0.0;
             for (int j = 0; j < D; ++j) s += Gq[i][j] * n[j];
-            U2[(i * M + l) * D + k] = Wf * s;
+            put(U2, (i * M + l) * D + k, Wf * s);
           }
         }
     }

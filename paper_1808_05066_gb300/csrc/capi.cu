@@ -212,6 +212,7 @@ int hdg_ctx_create(hdg_mesh_t mesh, const hdg_physics* phys, int device, hdg_ctx
     hdg_ctx_destroy(c);
     return rc;
   }
+  c->tab_size = tab.size();
   c->T.W = c->d_tab + off[0];
   c->T.Phi = c->d_tab + off[1];
   c->T.dPhi = c->d_tab + off[2];
@@ -229,7 +230,7 @@ int hdg_ctx_create(hdg_mesh_t mesh, const hdg_physics* phys, int device, hdg_ctx
 void hdg_ctx_destroy(hdg_ctx_t c) {
   if (!c) return;
   DeviceGuard guard(c->device);
-  void* bufs[] = {c->d_tab, c->d_itab, c->d_tgidx, c->d_geo, c->d_fs_elem, c->d_fs_loc, c->d_scr,
+  void* bufs[] = {c->d_tab, c->d_tab_df, c->d_itab, c->d_tgidx, c->d_geo, c->d_fs_elem, c->d_fs_loc, c->d_scr,
                   c->d_sw, c->d_pc, c->d_pcpiv, c->d_dense, c->d_dpiv, c->d_red, c->d_S,
                   c->d_g, c->d_recov, c->d_R, c->d_dV, c->d_dVh, c->d_status};
   for (void* b : bufs)

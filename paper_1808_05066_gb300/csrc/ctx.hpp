@@ -23,6 +23,8 @@ struct hdg_ctx {
   int64_t E = 0, F = 0, ntrace = 0;
   // device tables
   double* d_tab = nullptr;
+  size_t tab_size = 0;       // doubles in d_tab
+  float* d_tab_df = nullptr; // the same tables as double-float pairs (mixed form)
   int* d_itab = nullptr;
   hdg::DevTables T{};
   int* d_tgidx = nullptr;    // [E][NF][NFN] canonical global face node of each local face node

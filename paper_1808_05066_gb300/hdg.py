@@ -39,10 +39,11 @@ EXPORTED = [
 HDG_KERNEL_POINTWISE = 0
 HDG_KERNEL_ASSEMBLE = 1
 HDG_KERNEL_CONDENSE = 2
-HDG_KERNEL_MIXED = 3
-HDG_KERNEL_TRACE = 4
-HDG_KERNEL_OTHER = 5
-HDG_KERNEL_CLASSES = 6
+HDG_KERNEL_MIXED_ASSEMBLE = 3
+HDG_KERNEL_MIXED_CONDENSE = 4
+HDG_KERNEL_TRACE = 5
+HDG_KERNEL_OTHER = 6
+HDG_KERNEL_CLASSES = 7
 
 
 class HdgError(RuntimeError):
