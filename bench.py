@@ -164,7 +164,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="mixed")
+    ap.add_argument("--fp64-steps", type=int, default=2, help="timed steps of the FP64 comparison form")
     ap.add_argument("--cpu-per-core", type=int, default=6, help="oracle elements per host core and step")
     ap.add_argument("--n", type=int, default=None, help="override the cube resolution (tests only)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -173,10 +174,8 @@ def parse():
 
 
 def _dist():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
+    from paper_1808_05066_gb300.multirank import world
+    return world()
 
 
 def run_reference(args):
@@ -225,12 +224,10 @@ def main():
             dist.barrier()
         torch.cuda.synchronize(dev)
 
+    from paper_1808_05066_gb300.multirank import max_over_ranks as _mor
+
     def max_over_ranks(x):
-        if ws == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return _mor(x, device=dev)
 
     for _ in range(args.warmup):
         W.assemble(prec)
@@ -273,10 +270,43 @@ def main():
                 "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x max SM clock", "kernel": dom,
                 "launches": dom_launches, "avg_launch_ms": dom_ms / max(dom_launches, 1), "traffic": None}
     else:
-        roof = {"bound": "alu", "achieved": None, "peak": None, "unit": "TFLOP/s", "kernel": dom, "traffic": None}
+        # double-float multiply-accumulate = 12 FP32 operations for 2 useful flops:
+        # peak useful rate = 152 SMs x 128 FP32 lanes x max SM clock x 2 / 12
+        kind = "assemble" if dom == "mixed_assemble" else "condense_df"
+        work = flops_per_element(W.info, viscous, kind) * E * args.steps
+        peak = 152 * 128 * sm_max * 1e6 * 2 / 12 / 1e12
+        roof = {"bound": "alu", "achieved": work / (dom_ms / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x max SM clock, 12 FP32 ops per "
+                               "double-float multiply-accumulate", "kernel": dom,
+                "launches": dom_launches, "avg_launch_ms": dom_ms / max(dom_launches, 1), "traffic": None}
     if roof.get("achieved") is not None:
         roof["frac"] = roof["achieved"] / roof["peak"]
     shares = {k: (prof[k][1] / sum(v[1] for v in prof.values()) if prof[k][1] else 0.0) for k in prof}
+
+    # ---------------- the plain FP64 GPU form on the same workload, and the accuracy of
+    # the headline form against it on every element (relative Frobenius norm of S)
+    fp64_form = None
+    if prec != hdg.HDG_PREC_FP64 and args.fp64_steps > 0:
+        S_head = W.S.clone() if W.S.numel() * 8 < 0.3 * torch.cuda.get_device_properties(dev).total_memory else None
+        W.assemble(hdg.HDG_PREC_FP64)
+        barrier()
+        ev0.record(stream)
+        for _ in range(args.fp64_steps):
+            W.assemble(hdg.HDG_PREC_FP64)
+        ev1.record(stream)
+        barrier()
+        ms64 = max_over_ranks(ev0.elapsed_time(ev1))
+        fp64_form = {"value": ws * E * args.fp64_steps / (ms64 / 1000.0), "unit": UNIT,
+                     "ms_per_step": ms64 / args.fp64_steps, "steps": args.fp64_steps}
+        if S_head is not None:
+            err = 0.0
+            for e0 in range(0, E, 4096):
+                d = (S_head[e0:e0 + 4096] - W.S[e0:e0 + 4096]).flatten(1).norm(dim=1)
+                n = W.S[e0:e0 + 4096].flatten(1).norm(dim=1)
+                err = max(err, float((d / n).max()))
+            fp64_form["max_rel_err_S_vs_fp64"] = err
+            del S_head
+        fp64_form["speedup_of_headline"] = value / fp64_form["value"]
 
     # ---------------- end to end through the C-ABI with host buffers
     e2e = None
@@ -321,12 +351,14 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f32x2+f32" if prec == hdg.HDG_PREC_MIXED else "f64",
+            "data": "synthetic",
             "config": {"workload": WORKLOAD, "elements_per_gpu": E, "dim": 3, "p": 3, "physics": "navier-stokes",
                        "mesh": f"{W.spec['n']}^3 periodic cube x 6 tets", "precision": args.precision,
                        "l2": "inputs+outputs larger than L2 (S alone 26.5 GB written per step)",
                        "parallelism": f"replica per GPU x{ws}"},
             "roofline": roof, "kernel_time_share": shares, "gpu_launches": launches_total,
+            "fp64_form": fp64_form,
             "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)

@@ -9,7 +9,7 @@
 
 namespace hdg {
 
-struct df2 {
+struct __align__(8) df2 {
   float hi, lo;
 };
 

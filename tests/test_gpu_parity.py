@@ -86,6 +86,35 @@ def test_assemble_condense_matches_oracle(name, nsample):
         assert rel_fro(y, L["y"][nq:]) < TOL_BLOCK, (e, "y")
 
 
+@pytest.mark.parametrize("name,nsample", [("euler2d_p2", 32), ("ns2d_p3", 18), ("ns2d_p4", 18),
+                                          ("ns3d_p1", 20), ("ns3d_p2", 10), ("ns3d_p3", 5)])
+def test_mixed_precision_matches_oracle(name, nsample):
+    """Mixed form (double-float contractions, FP32 LU with refinement): same outputs as
+    the oracle within the condensed-block tolerance."""
+    case = CASES[name]
+    gc = GpuCase(case)
+    prob, Q, V, Vh = oracle_setup(case)
+    hist_o = oracle_hist(prob, V, case)
+    gc.assemble(gc.history(), precision=1)
+    S, g = gc.S.cpu().numpy(), gc.g.cpu().numpy()
+    rec, R = gc.recov.cpu().numpy(), gc.R.cpu().numpy()
+    assert int(gc.status.abs().sum()) == 0
+    nv, nt = gc.info["nv"], gc.info["nt"]
+    for e in _sample(prob.mesh.E, nsample, seed=1):
+        L = prob.condense(e, None if Q is None else Q[e], V[e], prob.gather_trace(Vh, e), case.mass_coef,
+                          hist_o[e])
+        nq = L["Rl"].size - nv
+        Rv = L["Rl"][nq:]
+        scale = max(np.abs(Rv).max(), np.abs(L["Rt"]).max(), np.abs(hist_o[e]).max(), 1.0)
+        assert np.abs(Rv - R[e, :nv]).max() <= TOL_RES * scale, (e, "R_v")
+        assert np.abs(L["Rt"] - R[e, nv:]).max() <= TOL_RES * scale, (e, "R_t")
+        assert rel_fro(S[e], L["S"]) < TOL_BLOCK, (e, rel_fro(S[e], L["S"]))
+        assert rel_fro(g[e], L["g"]) < TOL_BLOCK, (e, rel_fro(g[e], L["g"]))
+        X = rec[e, :nv * nt].reshape(nv, nt)
+        assert rel_fro(X, L["X"][nq:]) < TOL_BLOCK, (e, "X")
+        assert rel_fro(rec[e, nv * nt:], L["y"][nq:]) < TOL_BLOCK, (e, "y")
+
+
 def test_chunked_launch_ragged_tail(monkeypatch):
     """Element chunks of 7 over 128 elements (18 full chunks + a ragged tail of 2) give
     the same output as one chunk, bit for bit."""

@@ -191,3 +191,35 @@ def test_entropy_non_increasing_and_bounded():
         assert b <= a + 1e-12 * abs(a)
     assert Hs[-1] < Hs[0]
     assert min(Hs) >= Hstar - 1e-12 * abs(Hstar)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_history_weak_closed_form(dim):
+    """For p = 1 and a uniform state, (u, phi_a)_K = u |K| / (d + 1) for every vertex
+    basis function (the integral of a barycentric coordinate)."""
+    mesh = Mesh(dim, 2, 0.0, 3.0, 1)
+    prob = Problem(mesh, NS)
+    u0 = ph.u_of_primitives(np.array(1.2), np.array([0.3, -0.2, 0.1][:dim]), np.array(9.0), 1.4)
+    v0 = ph.v_of_u(u0, 1.4)
+    Vc = np.broadcast_to(v0, (prob.Np, prob.m))
+    for e in (0, mesh.E - 1):
+        h = prob.history_weak(e, [Vc], [2.5])
+        vol = abs(mesh.detJ[e]) / math.factorial(dim)
+        assert np.allclose(h, 2.5 * u0[None, :] * vol / (dim + 1), rtol=1e-13)
+
+
+@pytest.mark.parametrize("dim,p", [(2, 2), (3, 2)])
+def test_consistent_q_is_exact_gradient(dim, p):
+    """With v linear in x and vhat its exact trace, Eq. hDG_NS0 gives q = grad v."""
+    mesh = Mesh(dim, 2, 0.0, 3.0, p)
+    prob = Problem(mesh, NS)
+    rng = np.random.default_rng(9)
+    m = dim + 2
+    a0 = np.array([-5.0] + [0.1] * dim + [-0.2])
+    Gr = 0.01 * rng.normal(size=(m, dim))
+    for e in (0, 5, mesh.E - 1):
+        x = mesh.xnode[e]                                   # element nodes (unreduced)
+        V = a0 + x @ Gr.T
+        Vh = V[np.array(mesh.ref.face_nodes)]               # exact trace in local order
+        Q = prob.consistent_q(e, V, Vh)
+        assert np.allclose(Q, np.broadcast_to(Gr, Q.shape), atol=1e-12)
