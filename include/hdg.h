@@ -128,6 +128,24 @@ int hdg_assemble_condense(hdg_ctx_t ctx, const double* V, const double* Vhat, co
                           double mass_coef, int precision, double* S, double* g, double* recov,
                           double* R, int32_t* elem_status, void* stream);
 
+/* The same FP64 assemble + condense for callers that must not allocate device memory
+ * during the call (the paper has no counterpart: this is a deployment variant). Such
+ * callers include code running while a stream is captured into a CUDA graph (cudaMalloc
+ * cannot be captured), runtimes that give the library a fixed memory arena, and loops
+ * where cudaMalloc/cudaFree and their implicit synchronisation are not acceptable.
+ * The call allocates nothing: its scratch is a 64 MiB static device array, present on every
+ * GPU that loads the library until the process exits; elements are processed in chunks
+ * that fit it. A configuration whose single-element scratch exceeds 64 MiB is rejected with
+ * HDG_ERR_INVALID_ARG. The first call on a device resolves the array's device address
+ * (cudaGetSymbolAddress) with that device current: make it before any stream capture.
+ * All calls share the array, so calls whose kernels overlap on the GPU race; order them
+ * on one stream (or synchronise). Nothing in the array needs clearing between calls.
+ * Arguments as for hdg_assemble_condense with precision FP64; elem_status is required
+ * (zeroed by the caller). The context itself is created beforehand by hdg_ctx_create. */
+int hdg_assemble_condense_noalloc(hdg_ctx_t ctx, const double* V, const double* Vhat, const double* hist,
+                                  double mass_coef, double* S, double* g, double* recov, double* R,
+                                  int32_t* elem_status, void* stream);
+
 /* Global trace system sum_e P_e^T S_e P_e dVhat = -sum_e P_e^T g_e (Sec. 3.2: only vhat
  * is globally coupled). method: HDG_SOLVER_GMRES (restarted GMRES(30), face-block Jacobi
  * preconditioner), HDG_SOLVER_DENSE (assembled dense LU with partial pivoting, for

@@ -34,7 +34,7 @@ EXPORTED = [
     "hdg_mesh_copy_coords", "hdg_ctx_create", "hdg_ctx_destroy", "hdg_prim_to_entropy",
     "hdg_history", "hdg_assemble_condense", "hdg_trace_solve", "hdg_recover_interior",
     "hdg_trace_matvec", "hdg_residual_norm", "hdg_newton_step", "hdg_profile_enable",
-    "hdg_profile_reset", "hdg_profile_read", "hdg_last_error",
+    "hdg_profile_reset", "hdg_profile_read", "hdg_last_error", "hdg_assemble_condense_noalloc",
 ]
 HDG_KERNEL_POINTWISE = 0
 HDG_KERNEL_ASSEMBLE = 1
@@ -91,6 +91,7 @@ def _load():
         "hdg_profile_reset": (c_int, [P]),
         "hdg_profile_read": (c_int, [P, c_int, POINTER(c_int64), POINTER(c_double)]),
         "hdg_last_error": (ctypes.c_char_p, []),
+        "hdg_assemble_condense_noalloc": (c_int, [P, P, P, P, c_double, P, P, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -190,6 +191,13 @@ def hdg_assemble_condense(ctx, V, Vhat, hist, mass_coef, precision, S, g, recov,
                           stream=None):
     _check(_lib.hdg_assemble_condense(ctx, _ptr(V), _ptr(Vhat), _ptr(hist), mass_coef, precision, _ptr(S),
                                       _ptr(g), _ptr(recov), _ptr(R), _ptr(elem_status), _stream(stream)))
+
+
+def hdg_assemble_condense_noalloc(ctx, V, Vhat, hist, mass_coef, S, g, recov, R, elem_status, stream=None):
+    """FP64 assemble + condense that allocates no device memory (scratch in a static
+    64 MiB device array); for callers that cannot allocate during the call."""
+    _check(_lib.hdg_assemble_condense_noalloc(ctx, _ptr(V), _ptr(Vhat), _ptr(hist), mass_coef, _ptr(S), _ptr(g),
+                                              _ptr(recov), _ptr(R), _ptr(elem_status), _stream(stream)))
 
 
 def hdg_trace_solve(ctx, S, g, dVhat, method=HDG_SOLVER_AUTO, rtol=1e-12, max_it=600, stream=None):
