@@ -167,10 +167,43 @@ int hdg_residual_norm(hdg_ctx_t ctx, const double* R, double* norm, void* stream
 /* One implicit time step by Newton's method: repeats assemble_condense, trace_solve,
  * recover and the update V += dV, Vhat += dVhat until |R| <= tol max(1, |R_0|) or
  * max_newton updates were made. V and Vhat are updated in place; *newton_iters and
- * *res_norm (final) are written on the host. Uses context-owned workspaces (allocated on
- * first call). HDG_ERR_NOT_CONVERGED / HDG_ERR_NONPHYSICAL / HDG_ERR_SINGULAR on failure. */
+ * *res_norm (final) are written on the host; res_history (host, nullable, max_newton + 1
+ * entries) receives the residual norm before each update, trace_iters (host, nullable) the
+ * total trace-solver iterations. Uses context-owned workspaces (allocated on first call).
+ * HDG_ERR_NOT_CONVERGED / HDG_ERR_NONPHYSICAL / HDG_ERR_SINGULAR on failure. */
 int hdg_newton_step(hdg_ctx_t ctx, double* V, double* Vhat, const double* hist, double mass_coef, int precision,
-                    double tol, int max_newton, int* newton_iters, double* res_norm, void* stream);
+                    double tol, int max_newton, int* newton_iters, double* res_norm, double* res_history,
+                    int* trace_iters, void* stream);
+
+/* Learned warm start of the implicit step (no counterpart in the paper: it only supplies
+ * the initial guess of the Newton solve above, which still decides the converged answer).
+ * A per-face MLP x (nin) -> tanh (nh) -> tanh (nh) -> linear (nout) predicts the correction
+ * to the extrapolated trace update dvhat^{n+1} - dvhat^n of one face from the face-node
+ * features [V_side0 - vhat^n | V_side1 - vhat^n | dvhat^n | dvhat^{n-1}] (nin = 4 Nf m,
+ * nout = Nf m). Weights are applied in BF16 with FP32 accumulation; training keeps FP32
+ * master weights and Adam moments. The parameter buffer (device) holds, for
+ * P = hdg_mlp_param_count(): P float master weights (W1 [nh][nin], b1, W2 [nh][nh], b2,
+ * W3 [nout][nh], b3), P floats Adam m, P floats Adam v, then P bf16 weights: 14 P bytes.
+ * Compiled sizes: (nin, nh, nout) = (64, 64, 16) and (48, 32, 12). */
+int64_t hdg_mlp_param_count(int nin, int nh, int nout);
+/* Glorot-uniform weights from a SplitMix64 counter stream of seed; zero biases and moments. */
+int hdg_mlp_init(float* params, int nin, int nh, int nout, uint64_t seed, void* stream);
+/* Standardised features feat [F][nin] (float) of every face; mean, scale [nin] (device). */
+int hdg_mlp_features(hdg_ctx_t ctx, const double* V, const double* Vhat, const double* dvhat1,
+                     const double* dvhat2, const float* mean, const float* scale, float* feat, void* stream);
+/* y [B][nout] = MLP(x [B][nin]) with the BF16 weights of params. */
+int hdg_mlp_forward(const float* params, int nin, int nh, int nout, const float* x, int64_t B, float* y,
+                    void* stream);
+/* Mean-squared-error gradient grad [P] (float, device) and loss [1] (device) of a batch. */
+int hdg_mlp_gradient(const float* params, float* grad, int nin, int nh, int nout, const float* x,
+                     const float* target, int64_t B, float* loss, void* stream);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, step = 1, 2, ...) on a batch. */
+int hdg_mlp_train_step(float* params, float* grad, int nin, int nh, int nout, const float* x,
+                       const float* target, int64_t B, float lr, int step, float* loss, void* stream);
+/* Warm start of the trace: Vhat_out = Vhat + dvhat1 + (pred * tscale + tmean) componentwise,
+ * pred [F][nout] from hdg_mlp_forward, tmean / tscale [nout] the target de-standardisation. */
+int hdg_mlp_apply_trace(hdg_ctx_t ctx, const double* Vhat, const double* dvhat1, const float* pred,
+                        const float* tmean, const float* tscale, double* Vhat_out, void* stream);
 
 /* Measurement support (no counterpart in the paper). Every kernel launch of a context
  * is counted per kernel class; with profiling enabled each launch is also bracketed by

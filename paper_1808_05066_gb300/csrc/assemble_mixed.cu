@@ -10,7 +10,7 @@ namespace hdg {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kRefine = 3;
+constexpr int kRefine = 2;
 
 int ensure_df_tables(hdg_ctx* ctx) {
   if (ctx->d_tab_df) return HDG_OK;
@@ -56,7 +56,7 @@ int run_mixed(hdg_ctx* ctx, const double* V, const double* Vhat, const double* h
     HDG_CK(cudaFuncSetAttribute(k_assemble_df<C, kThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)X::asm_bytes));
     HDG_CK(cudaFuncSetAttribute(k_condense_df<C, kThreads, kRefine>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)X::cond_bytes));
+                                (int)CondCfg<C, kThreads>::bytes));
     attr_done = true;
   }
   const df2* td = reinterpret_cast<const df2*>(ctx->d_tab_df);
@@ -98,7 +98,7 @@ int run_mixed(hdg_ctx* ctx, const double* V, const double* Vhat, const double* h
     }
     {
       LaunchScope ls(ctx, HDG_KERNEL_MIXED_CONDENSE, s);
-      k_condense_df<C, kThreads, kRefine><<<(unsigned)a.ne, kThreads, X::cond_bytes, s>>>(a);
+      k_condense_df<C, kThreads, kRefine><<<(unsigned)a.ne, kThreads, CondCfg<C, kThreads>::bytes, s>>>(a);
     }
   }
   HDG_CK(cudaGetLastError());

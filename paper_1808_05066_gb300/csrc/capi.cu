@@ -362,7 +362,8 @@ int hdg_profile_read(hdg_ctx_t ctx, int kernel_class, int64_t* launches, double*
 }
 
 int hdg_newton_step(hdg_ctx_t ctx, double* V, double* Vhat, const double* hist, double mass_coef, int precision,
-                    double tol, int max_newton, int* newton_iters, double* res_norm, void* stream) {
+                    double tol, int max_newton, int* newton_iters, double* res_norm, double* res_history,
+                    int* trace_iters, void* stream) {
   HDG_REQUIRE(ctx && V && Vhat && newton_iters && res_norm && tol > 0.0 && max_newton >= 0,
               "hdg_newton_step: invalid argument");
   DeviceGuard guard(ctx->device);
@@ -380,6 +381,7 @@ int hdg_newton_step(hdg_ctx_t ctx, double* V, double* Vhat, const double* hist, 
   std::vector<int32_t> hstat;
   double r0 = -1.0, rn = 0.0;
   *newton_iters = 0;
+  if (trace_iters) *trace_iters = 0;
   for (int it = 0;; ++it) {
     HDG_CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int32_t) * E, s));
     int rc = hdg_assemble_condense(ctx, V, Vhat, hist, mass_coef, precision, ctx->d_S, ctx->d_g, ctx->d_recov,
@@ -393,6 +395,7 @@ int hdg_newton_step(hdg_ctx_t ctx, double* V, double* Vhat, const double* hist, 
     int bits = 0;
     for (int32_t b : hstat) bits |= b;
     *res_norm = rn;
+    if (res_history) res_history[it] = rn;
     if (bits & HDG_ELEM_NONPHYSICAL) {
       set_error("hdg_newton_step: non-physical state");
       return HDG_ERR_NONPHYSICAL;
@@ -410,6 +413,7 @@ int hdg_newton_step(hdg_ctx_t ctx, double* V, double* Vhat, const double* hist, 
     int iters = 0;
     double fres = 0.0;
     rc = hdg::trace_solve(ctx, ctx->d_S, ctx->d_g, ctx->d_dVh, HDG_SOLVER_AUTO, 1e-12, 600, &iters, &fres, s);
+    if (trace_iters) *trace_iters += iters;
     if (rc) return rc;
     rc = hdg::launch_recover(ctx, ctx->d_recov, ctx->d_dVh, ctx->d_dV, s);
     if (rc) return rc;

@@ -35,6 +35,8 @@ EXPORTED = [
     "hdg_history", "hdg_assemble_condense", "hdg_trace_solve", "hdg_recover_interior",
     "hdg_trace_matvec", "hdg_residual_norm", "hdg_newton_step", "hdg_profile_enable",
     "hdg_profile_reset", "hdg_profile_read", "hdg_last_error", "hdg_assemble_condense_noalloc",
+    "hdg_mlp_param_count", "hdg_mlp_init", "hdg_mlp_features", "hdg_mlp_forward", "hdg_mlp_gradient",
+    "hdg_mlp_train_step", "hdg_mlp_apply_trace",
 ]
 HDG_KERNEL_POINTWISE = 0
 HDG_KERNEL_ASSEMBLE = 1
@@ -86,7 +88,14 @@ def _load():
         "hdg_trace_matvec": (c_int, [P, P, P, P, P]),
         "hdg_residual_norm": (c_int, [P, P, POINTER(c_double), P]),
         "hdg_newton_step": (c_int, [P, P, P, P, c_double, c_int, c_double, c_int, POINTER(c_int),
-                                    POINTER(c_double), P]),
+                                    POINTER(c_double), POINTER(c_double), POINTER(c_int), P]),
+        "hdg_mlp_param_count": (c_int64, [c_int, c_int, c_int]),
+        "hdg_mlp_init": (c_int, [P, c_int, c_int, c_int, ctypes.c_uint64, P]),
+        "hdg_mlp_features": (c_int, [P, P, P, P, P, P, P, P, P]),
+        "hdg_mlp_forward": (c_int, [P, c_int, c_int, c_int, P, c_int64, P, P]),
+        "hdg_mlp_gradient": (c_int, [P, P, c_int, c_int, c_int, P, P, c_int64, P, P]),
+        "hdg_mlp_train_step": (c_int, [P, P, c_int, c_int, c_int, P, P, c_int64, ctypes.c_float, c_int, P, P]),
+        "hdg_mlp_apply_trace": (c_int, [P, P, P, P, P, P, P, P]),
         "hdg_profile_enable": (c_int, [P, c_int]),
         "hdg_profile_reset": (c_int, [P]),
         "hdg_profile_read": (c_int, [P, c_int, POINTER(c_int64), POINTER(c_double)]),
@@ -223,12 +232,50 @@ def hdg_residual_norm(ctx, R, stream=None):
 
 
 def hdg_newton_step(ctx, V, Vhat, hist, mass_coef, precision=HDG_PREC_FP64, tol=1e-10, max_newton=10,
-                    stream=None):
+                    stream=None, history=False):
+    """Returns (updates, final residual norm) or, with history=True,
+    (updates, final norm, residual norms before each update, trace-solver iterations)."""
     it = c_int()
     res = c_double()
+    hist_buf = (c_double * (max_newton + 1))()
+    tr = c_int()
     _check(_lib.hdg_newton_step(ctx, _ptr(V), _ptr(Vhat), _ptr(hist), mass_coef, precision, tol, max_newton,
-                                byref(it), byref(res), _stream(stream)))
+                                byref(it), byref(res), hist_buf, byref(tr), _stream(stream)))
+    if history:
+        return it.value, res.value, list(hist_buf)[:it.value + 1], tr.value
     return it.value, res.value
+
+
+def hdg_mlp_param_count(nin, nh, nout):
+    return int(_lib.hdg_mlp_param_count(nin, nh, nout))
+
+
+def hdg_mlp_init(params, nin, nh, nout, seed, stream=None):
+    _check(_lib.hdg_mlp_init(_ptr(params), nin, nh, nout, seed, _stream(stream)))
+
+
+def hdg_mlp_features(ctx, V, Vhat, dvhat1, dvhat2, mean, scale, feat, stream=None):
+    _check(_lib.hdg_mlp_features(ctx, _ptr(V), _ptr(Vhat), _ptr(dvhat1), _ptr(dvhat2), _ptr(mean), _ptr(scale),
+                                 _ptr(feat), _stream(stream)))
+
+
+def hdg_mlp_forward(params, nin, nh, nout, x, B, y, stream=None):
+    _check(_lib.hdg_mlp_forward(_ptr(params), nin, nh, nout, _ptr(x), B, _ptr(y), _stream(stream)))
+
+
+def hdg_mlp_gradient(params, grad, nin, nh, nout, x, target, B, loss, stream=None):
+    _check(_lib.hdg_mlp_gradient(_ptr(params), _ptr(grad), nin, nh, nout, _ptr(x), _ptr(target), B, _ptr(loss),
+                                 _stream(stream)))
+
+
+def hdg_mlp_train_step(params, grad, nin, nh, nout, x, target, B, lr, step, loss, stream=None):
+    _check(_lib.hdg_mlp_train_step(_ptr(params), _ptr(grad), nin, nh, nout, _ptr(x), _ptr(target), B, lr, step,
+                                   _ptr(loss), _stream(stream)))
+
+
+def hdg_mlp_apply_trace(ctx, Vhat, dvhat1, pred, tmean, tscale, Vhat_out, stream=None):
+    _check(_lib.hdg_mlp_apply_trace(ctx, _ptr(Vhat), _ptr(dvhat1), _ptr(pred), _ptr(tmean), _ptr(tscale),
+                                    _ptr(Vhat_out), _stream(stream)))
 
 
 def hdg_profile_enable(ctx, on=True):

@@ -21,7 +21,7 @@ def test_library_exports_every_declared_symbol():
     hdg = _lib()
     with open(os.path.join(ROOT, "include", "hdg.h")) as fh:
         text = fh.read()
-    declared = set(re.findall(r"^\s*(?:int|void|const char\*)\s+(hdg_\w+)\s*\(", text, re.M))
+    declared = set(re.findall(r"^\s*(?:int64_t|int|void|const char\*)\s+(hdg_\w+)\s*\(", text, re.M))
     assert declared, "no declarations parsed"
     assert declared == set(hdg.EXPORTED)
     for name in declared:
