@@ -158,6 +158,10 @@ int hdg_trace_solve(hdg_ctx_t ctx, const double* S, const double* g, double* dVh
 /* Interior recovery (Sec. 3.2): dV_e = -y_e - X_e P_e dVhat. dV [E][Np][m] device. */
 int hdg_recover_interior(hdg_ctx_t ctx, const double* recov, const double* dVhat, double* dV, void* stream);
 
+/* out = a x + b y elementwise over n doubles (device; out may alias x or y). Used for
+ * state extrapolation and Newton updates around the calls above. */
+int hdg_axpby(int64_t n, double a, const double* x, double b, const double* y, double* out, void* stream);
+
 /* Helpers used around the solve. y = K x with K = sum_e P_e^T S_e P_e (trace vectors). */
 int hdg_trace_matvec(hdg_ctx_t ctx, const double* S, const double* x, double* y, void* stream);
 /* Newton residual norm sqrt(sum_e |R_v,e|^2 + |sum_e P_e^T R_t,e|^2) from R; writes the
@@ -188,9 +192,17 @@ int hdg_newton_step(hdg_ctx_t ctx, double* V, double* Vhat, const double* hist, 
 int64_t hdg_mlp_param_count(int nin, int nh, int nout);
 /* Glorot-uniform weights from a SplitMix64 counter stream of seed; zero biases and moments. */
 int hdg_mlp_init(float* params, int nin, int nh, int nout, uint64_t seed, void* stream);
-/* Standardised features feat [F][nin] (float) of every face; mean, scale [nin] (device). */
+/* Standardised features feat [F][nin] (float) of every face: (raw - mean) / std, with
+ * mean, std [nin] (device; zeros and ones give the raw features). */
 int hdg_mlp_features(hdg_ctx_t ctx, const double* V, const double* Vhat, const double* dvhat1,
-                     const double* dvhat2, const float* mean, const float* scale, float* feat, void* stream);
+                     const double* dvhat2, const float* mean, const float* std, float* feat, void* stream);
+/* Column mean and standard deviation of x [B][n] (float, device). */
+int hdg_mlp_stats(const float* x, int64_t B, int n, float* mean, float* std, void* stream);
+/* In place x = (x - mean) / std, columnwise. */
+int hdg_mlp_standardize(float* x, int64_t B, int n, const float* mean, const float* std, void* stream);
+/* Raw training target of each trace entry: (vhat_next - vhat) - dvhat1, as float. */
+int hdg_mlp_target(int64_t n, const double* vhat_next, const double* vhat, const double* dvhat1, float* out,
+                   void* stream);
 /* y [B][nout] = MLP(x [B][nin]) with the BF16 weights of params. */
 int hdg_mlp_forward(const float* params, int nin, int nh, int nout, const float* x, int64_t B, float* y,
                     void* stream);

@@ -12,6 +12,7 @@ Everything here is plain and slow on purpose:
                matching, affine geometry, DOF / NNZ counting (Tables t:dofs, t:nnz).
   * physics.py entropy variables (Sec. 2.3), inverse map, fluxes (Eqs. flux,
                viscFlux, closuresNS), stabilization (Eq. sLxF); complex-safe.
+  * mlp.py     the per-face warm-start MLP in FP64 (forward, loss, chain-rule gradient).
   * hdg.py     local residuals of Eqs. hDG1-2 / hDG_NS0-2 with the numerical
                fluxes of Eqs. numericalFlux and numericalFluxNS_2; Jacobians by
                complex step; dense static condensation; global trace solve;

@@ -30,10 +30,21 @@ int ensure_df_tables(hdg_ctx* ctx) {
   return HDG_OK;
 }
 
+// One compiled tile shape of the mixed assembly kernel.
+struct AsmVariant {
+  int threads, gt;
+  size_t smem;
+  void (*kernel)(AssembleArgs, DevTables, DevTablesDF);
+};
+
+template <class C, int NTH, int GTM>
+AsmVariant make_variant() {
+  return AsmVariant{NTH, GTM, MixCfg<C, NTH, GTM>::asm_bytes, &k_assemble_df<C, NTH, GTM>};
+}
+
 template <class C>
 int run_mixed(hdg_ctx* ctx, const double* V, const double* Vhat, const double* hist, double mass_coef, double* S,
               double* g, double* recov, double* R, int32_t* status, cudaStream_t s) {
-  using X = MixCfg<C, kThreads>;
   int rc = ensure_df_tables(ctx);
   if (rc) return rc;
   const size_t per = sizeof(double) * ((size_t)C::NG * C::PT_VOL + (size_t)C::NF * C::NGF * C::PT_FACE +
@@ -51,10 +62,14 @@ int run_mixed(hdg_ctx* ctx, const double* V, const double* Vhat, const double* h
     HDG_CK(cudaMalloc(&ctx->d_scr, need));
     ctx->scr_bytes = need;
   }
+  // compiled tile shapes of the assembly kernel (threads, volume points per tile)
+  const AsmVariant variants[] = {make_variant<C, 256, 64>(), make_variant<C, 256, 32>(),
+                                 make_variant<C, 512, 64>(), make_variant<C, 128, 16>()};
+  constexpr int NVAR = 4;
   static bool attr_done = false;
   if (!attr_done) {
-    HDG_CK(cudaFuncSetAttribute(k_assemble_df<C, kThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)X::asm_bytes));
+    for (const AsmVariant& v : variants)
+      HDG_CK(cudaFuncSetAttribute(v.kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem));
     HDG_CK(cudaFuncSetAttribute(k_condense_df<C, kThreads, kRefine>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)CondCfg<C, kThreads>::bytes));
     attr_done = true;
@@ -92,9 +107,36 @@ int run_mixed(hdg_ctx* ctx, const double* V, const double* Vhat, const double* h
       LaunchScope ls(ctx, HDG_KERNEL_POINTWISE, s);
       k_pointwise<C, df2><<<(unsigned)a.ne, pw_threads, 0, s>>>(a, ctx->T, ctx->ph);
     }
+    if (ctx->asm_variant < 0 && a.ne >= 512) {
+      // autotune on this chunk: time every compiled shape (each writes the same outputs)
+      float best = 1e30f;
+      int best_i = 0;
+      cudaEvent_t t0, t1;
+      HDG_CK(cudaEventCreate(&t0));
+      HDG_CK(cudaEventCreate(&t1));
+      for (int i = 0; i < NVAR; ++i) {
+        HDG_CK(cudaEventRecord(t0, s));
+        variants[i].kernel<<<(unsigned)a.ne, variants[i].threads, variants[i].smem, s>>>(a, ctx->T, TD);
+        HDG_CK(cudaEventRecord(t1, s));
+        HDG_CK(cudaEventSynchronize(t1));
+        HDG_CK(cudaGetLastError());
+        float ms = 0.f;
+        HDG_CK(cudaEventElapsedTime(&ms, t0, t1));
+        if (ms < best) {
+          best = ms;
+          best_i = i;
+        }
+      }
+      cudaEventDestroy(t0);
+      cudaEventDestroy(t1);
+      ctx->asm_variant = best_i;
+      ctx->asm_variant_threads = variants[best_i].threads;
+      ctx->asm_variant_gt = variants[best_i].gt;
+    }
+    const AsmVariant& v = variants[ctx->asm_variant < 0 ? 0 : ctx->asm_variant];
     {
       LaunchScope ls(ctx, HDG_KERNEL_MIXED_ASSEMBLE, s);
-      k_assemble_df<C, kThreads><<<(unsigned)a.ne, kThreads, X::asm_bytes, s>>>(a, ctx->T, TD);
+      v.kernel<<<(unsigned)a.ne, v.threads, v.smem, s>>>(a, ctx->T, TD);
     }
     {
       LaunchScope ls(ctx, HDG_KERNEL_MIXED_CONDENSE, s);

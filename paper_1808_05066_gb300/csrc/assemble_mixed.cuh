@@ -28,9 +28,12 @@ struct DevTablesDF {
   const df2* PLF;    // [NF][NF][NGF][NFN]
 };
 
-template <class C, int NTHREADS>
+// Tile shape of the mixed assembly: NTHREADS threads per element CTA and GTMAX volume
+// quadrature points per shared-memory tile (smaller tiles: less shared memory, more CTAs
+// per SM). The library times the compiled shapes on the first chunk and keeps the fastest.
+template <class C, int NTHREADS, int GTMAX = 64>
 struct MixCfg {
-  static constexpr int GT = C::NG < 64 ? C::NG : 64;
+  static constexpr int GT = C::NG < GTMAX ? C::NG : GTMAX;
   static constexpr int JW = (C::NP * C::NZ + NTHREADS - 1) / NTHREADS;    // outputs per thread (volume)
   static constexpr int NSV = (C::NZ + JW - 1) / JW;                       // strips per row
   static constexpr int JWF = (C::NFN * C::NZ + NTHREADS - 1) / NTHREADS;  // faces
@@ -41,23 +44,28 @@ struct MixCfg {
   static constexpr int ZS = C::NP * GT * C::NR;
   static constexpr int ZSF = C::NFN * C::NGF * C::NRF;
   static constexpr int ZSMAX = ZS > ZSF ? ZS : ZSF;
-  static constexpr size_t asm_bytes =
-      sizeof(df2) * (RBMAX + ZSMAX + C::D * C::D + C::NF * C::D) + sizeof(double) * (C::NZ * C::M + C::GEO + C::NV + C::NT);
+  static constexpr int NTS = 1 + C::D + (C::VISC ? C::D * C::D : 0);  // point values one (i, l) needs
+  static constexpr int TSV = GT * NTS;
+  static constexpr int TSF = C::NGF * C::NRF;
+  static constexpr int TSMAX = TSV > TSF ? TSV : TSF;
+  static constexpr size_t asm_bytes = sizeof(df2) * (RBMAX + ZSMAX + TSMAX + C::D * C::D + C::NF * C::D) +
+                                      sizeof(double) * (C::NZ * C::M + C::GEO + C::NV + C::NT);
 };
 
 // ------------------------------------------------------------------------------------
 // k_assemble_df: one CTA per element
 // ------------------------------------------------------------------------------------
-template <class C, int NTHREADS>
+template <class C, int NTHREADS, int GTMAX>
 __global__ void __launch_bounds__(NTHREADS) k_assemble_df(AssembleArgs a, DevTables T, DevTablesDF TD) {
   constexpr int D = C::D, M = C::M, NP = C::NP, NFN = C::NFN, NF = C::NF, NG = C::NG, NGF = C::NGF;
   constexpr int NZ = C::NZ, NV = C::NV, NT = C::NT, NR = C::NR, NRF = C::NRF;
-  using X = MixCfg<C, NTHREADS>;
+  using X = MixCfg<C, NTHREADS, GTMAX>;
   constexpr int GT = X::GT, JW = X::JW, NSV = X::NSV, JWF = X::JWF, NSF = X::NSF;
   extern __shared__ double smem_d[];
   df2* Rb = reinterpret_cast<df2*>(smem_d);
   df2* Zs = Rb + X::RBMAX;
-  df2* JiD = Zs + X::ZSMAX;          // [D][D] Jinv as double-float
+  df2* Ts = Zs + X::ZSMAX;           // per-(i, l) point values staged from the point tensors
+  df2* JiD = Ts + X::TSMAX;          // [D][D] Jinv as double-float
   df2* NsD = JiD + D * D;            // [NF][D] n_f s_f
   double(*z)[M] = reinterpret_cast<double(*)[M]>(NsD + NF * D);
   double* G = reinterpret_cast<double*>(z) + NZ * M;
@@ -129,25 +137,41 @@ __global__ void __launch_bounds__(NTHREADS) k_assemble_df(AssembleArgs a, DevTab
       }
       Rb[t] = val;
     }
+    constexpr int NTS = X::NTS;
     for (int il = 0; il < M * M; ++il) {
       const int i = il / M, l = il % M;
+      __syncthreads();
+      // stage T0[i][l], T1[r][i][l], T2[r][i][l][k] of the tile's points
+      for (int t = tid; t < GT * NTS; t += NTHREADS) {
+        const int gg = t / NTS, q = t % NTS;
+        df2 val = {0.f, 0.f};
+        if (gg < ng) {
+          const df2* P = ptv + (g0 + gg) * C::PT_VOL + M + D * M;  // T0
+          if (q == 0)
+            val = P[i * M + l];
+          else if (q <= D)
+            val = P[M * M + ((q - 1) * M + i) * M + l];
+          else {
+            const int r = (q - 1 - D) / D, k = (q - 1 - D) % D;
+            val = P[M * M + D * M * M + ((r * M + i) * M + l) * D + k];
+          }
+        }
+        Ts[t] = val;
+      }
       __syncthreads();
       for (int t = tid; t < NP * GT * NR; t += NTHREADS) {
         int an = t / (GT * NR), gg = (t / NR) % GT, beta = t % NR;
         df2 val = {0.f, 0.f};
         if (gg < ng) {
           int g = g0 + gg;
-          const df2* P = ptv + g * C::PT_VOL;
-          const df2* T0 = P + M + D * M;
-          const df2* T1 = T0 + M * M;
-          const df2* T2 = T1 + D * M * M;
+          const df2* Tp = Ts + gg * NTS;
           dfacc acc;
           if (beta == 0) {
-            acc.mac(TD.Phi[g * NP + an], T0[i * M + l]);
-            for (int r = 0; r < D; ++r) acc.mac(TD.dPhi[(r * NG + g) * NP + an], T1[(r * M + i) * M + l]);
+            acc.mac(TD.Phi[g * NP + an], Tp[0]);
+            for (int r = 0; r < D; ++r) acc.mac(TD.dPhi[(r * NG + g) * NP + an], Tp[1 + r]);
           } else {
             int k = beta - 1;
-            for (int r = 0; r < D; ++r) acc.mac(TD.dPhi[(r * NG + g) * NP + an], T2[((r * M + i) * M + l) * D + k]);
+            for (int r = 0; r < D; ++r) acc.mac(TD.dPhi[(r * NG + g) * NP + an], Tp[1 + D + r * D + k]);
           }
           val = acc.norm();
         }
@@ -226,16 +250,18 @@ __global__ void __launch_bounds__(NTHREADS) k_assemble_df(AssembleArgs a, DevTab
     for (int il = 0; il < M * M; ++il) {
       const int i = il / M, l = il % M;
       __syncthreads();
+      for (int t = tid; t < NGF * NRF; t += NTHREADS) {  // stage U0, U1, U2[k] of the face points
+        const int gf = t / NRF, beta = t % NRF;
+        const df2* U0 = ptf + (f * NGF + gf) * C::PT_FACE + M;
+        Ts[t] = beta == 0 ? U0[i * M + l]
+                          : (beta == 1 ? U0[M * M + i * M + l] : U0[2 * M * M + (i * M + l) * D + (beta - 2)]);
+      }
+      __syncthreads();
       for (int t = tid; t < NFN * NGF * NRF; t += NTHREADS) {
         int c = t / (NGF * NRF), gf = (t / NRF) % NGF, beta = t % NRF;
-        const df2* P = ptf + (f * NGF + gf) * C::PT_FACE;
-        const df2* U0 = P + M;
-        const df2* U1 = U0 + M * M;
-        const df2* U2 = U1 + M * M;
         df2 psi = TD.PhiF[(f * NGF + gf) * NP + T.fnodes[f * NFN + c]];
-        df2 u = beta == 0 ? U0[i * M + l] : (beta == 1 ? U1[i * M + l] : U2[(i * M + l) * D + (beta - 2)]);
         dfacc acc;
-        acc.mac(psi, u);
+        acc.mac(psi, Ts[gf * NRF + beta]);
         Zs[t] = acc.norm();
       }
       __syncthreads();

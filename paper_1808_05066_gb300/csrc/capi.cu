@@ -167,6 +167,10 @@ int hdg_ctx_create(hdg_mesh_t mesh, const hdg_physics* phys, int device, hdg_ctx
   c->E = m.E;
   c->F = m.nFaces;
   c->ntrace = m.nFaces * m.ref.Nf * c->M;
+  if (const char* av = std::getenv("HDG_ASM_VARIANT")) {  // force a tile shape (tests)
+    long v = std::strtol(av, nullptr, 10);
+    if (v >= 0 && v < 4) c->asm_variant = (int)v;
+  }
   if (const char* ch = std::getenv("HDG_ELEMENT_CHUNK")) {
     long v = std::strtol(ch, nullptr, 10);
     if (v > 0) c->chunk = std::min<int64_t>(v, c->E);
@@ -311,6 +315,11 @@ int hdg_residual_norm(hdg_ctx_t ctx, const double* R, double* norm, void* stream
   HDG_REQUIRE(ctx && R && norm, "hdg_residual_norm: null argument");
   DeviceGuard guard(ctx->device);
   return hdg::residual_norm(ctx, R, norm, (cudaStream_t)stream);
+}
+
+int hdg_axpby(int64_t n, double a, const double* x, double b, const double* y, double* out, void* stream) {
+  HDG_REQUIRE(n >= 0 && x && y && out, "hdg_axpby: invalid argument");
+  return hdg::launch_axpby(n, a, x, b, y, out, (cudaStream_t)stream);
 }
 
 int hdg_profile_enable(hdg_ctx_t ctx, int on) {

@@ -35,6 +35,8 @@ struct hdg_ctx {
   int64_t chunk = 0;
   double* d_scr = nullptr;
   size_t scr_bytes = 0;
+  // autotuned tile shape of the mixed assembly (-1: not chosen yet)
+  int asm_variant = -1, asm_variant_threads = 0, asm_variant_gt = 0;
   // solver scratch
   double* d_sw = nullptr;    // GMRES / matvec workspace
   size_t sw_bytes = 0;
@@ -112,5 +114,6 @@ int residual_norm(hdg_ctx* ctx, const double* R, double* norm, cudaStream_t s);
 int trace_solve(hdg_ctx* ctx, const double* S, const double* g, double* dVhat, int method, double rtol, int max_it,
                 int* iters, double* final_res, cudaStream_t s);
 int launch_axpy(int64_t n, double a, const double* x, double* y, cudaStream_t s);
+int launch_axpby(int64_t n, double a, const double* x, double b, const double* y, double* out, cudaStream_t s);
 
 }  // namespace hdg

@@ -69,10 +69,10 @@ __global__ void k_mlp_init(float* params, int nin, int nh, int nout, uint64_t se
   }
 }
 
-// Face features [F][4][NFN][M] (float), standardised.
+// Face features [F][4][NFN][M] (float), standardised: (raw - mean) / std.
 __global__ void k_mlp_features(const double* V, const double* Vhat, const double* dvh1, const double* dvh2,
                                const int* fs_elem, const int* fs_loc, const int* fnodes, int64_t F, int NFN, int M,
-                               int NP, int NF, const float* mean, const float* scale, float* feat) {
+                               int NP, int NF, const float* mean, const float* stdv, float* feat) {
   const int per = NFN * M;
   const int nin = 4 * per;
   const int64_t n = F * per;
@@ -88,10 +88,10 @@ __global__ void k_mlp_features(const double* V, const double* Vhat, const double
       const int a = fnodes[f * NFN + cl];
       const double v = V[(e * NP + a) * M + i];
       const int k = side * per + r;
-      out[k] = (float)((v - vh - mean[k]) * scale[k]);
+      out[k] = (float)((v - vh - mean[k]) / stdv[k]);
     }
-    out[2 * per + r] = (float)((dvh1[t] - mean[2 * per + r]) * scale[2 * per + r]);
-    out[3 * per + r] = (float)((dvh2[t] - mean[3 * per + r]) * scale[3 * per + r]);
+    out[2 * per + r] = (float)((dvh1[t] - mean[2 * per + r]) / stdv[2 * per + r]);
+    out[3 * per + r] = (float)((dvh2[t] - mean[3 * per + r]) / stdv[3 * per + r]);
   }
 }
 
@@ -282,6 +282,50 @@ int launch_grad(const float* params, const float* x, const float* target, int64_
   return HDG_OK;
 }
 
+// Column statistics of x [B][n]: mean and standard deviation (FP64 accumulation; a
+// deviation below 1e-30 is reported as 1 so that standardising leaves the column as is).
+__global__ void k_mlp_stats(const float* x, int64_t B, int n, float* mean, float* stdv) {
+  const int col = blockIdx.x;
+  double s = 0.0, s2 = 0.0;
+  for (int64_t b = threadIdx.x; b < B; b += blockDim.x) {
+    const double v = x[b * n + col];
+    s += v;
+    s2 += v * v;
+  }
+  __shared__ double ps[256], ps2[256];
+  ps[threadIdx.x] = s;
+  ps2[threadIdx.x] = s2;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) {
+      ps[threadIdx.x] += ps[threadIdx.x + w];
+      ps2[threadIdx.x] += ps2[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double m = ps[0] / (double)B;
+    const double var = ps2[0] / (double)B - m * m;
+    const double sd = var > 1e-60 ? ::sqrt(var) : 1.0;
+    mean[col] = (float)m;
+    stdv[col] = (float)sd;
+  }
+}
+
+__global__ void k_mlp_standardize(float* x, int64_t B, int n, const float* mean, const float* stdv) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < B * n; t += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(t % n);
+    x[t] = (x[t] - mean[c]) / stdv[c];
+  }
+}
+
+// Raw training target: the correction of the extrapolated trace update,
+// (vhat^{n+1} - vhat^n) - dvhat^n.
+__global__ void k_mlp_target(int64_t n, const double* vh_next, const double* vh, const double* dvh1, float* out) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+    out[t] = (float)((vh_next[t] - vh[t]) - dvh1[t]);
+}
+
 inline unsigned nb(int64_t n) {
   int64_t b = (n + 255) / 256;
   return (unsigned)(b < 1 ? 1 : (b > 152 * 32 ? 152 * 32 : b));
@@ -311,14 +355,14 @@ int hdg_mlp_init(float* params, int nin, int nh, int nout, uint64_t seed, void* 
 }
 
 int hdg_mlp_features(hdg_ctx_t ctx, const double* V, const double* Vhat, const double* dvh1, const double* dvh2,
-                     const float* mean, const float* scale, float* feat, void* stream) {
-  if (!ctx || !V || !Vhat || !dvh1 || !dvh2 || !mean || !scale || !feat) {
+                     const float* mean, const float* stdv, float* feat, void* stream) {
+  if (!ctx || !V || !Vhat || !dvh1 || !dvh2 || !mean || !stdv || !feat) {
     set_error("hdg_mlp_features: null argument");
     return HDG_ERR_INVALID_ARG;
   }
   k_mlp_features<<<nb(ctx->ntrace), 256, 0, (cudaStream_t)stream>>>(
       V, Vhat, dvh1, dvh2, ctx->d_fs_elem, ctx->d_fs_loc, ctx->T.fnodes, ctx->F, ctx->NFN, ctx->M, ctx->NP, ctx->NF,
-      mean, scale, feat);
+      mean, stdv, feat);
   HDG_CK(cudaGetLastError());
   return HDG_OK;
 }
@@ -378,6 +422,37 @@ int hdg_mlp_gradient(const float* params, float* grad, int nin, int nh, int nout
   MLP_DISPATCH(48, 32, 12, return launch_grad<48, 32, 12>(params, x, target, B, grad, loss, s))
   set_error("hdg_mlp_gradient: network size not compiled in");
   return HDG_ERR_UNSUPPORTED;
+}
+
+int hdg_mlp_stats(const float* x, int64_t B, int n, float* mean, float* stdv, void* stream) {
+  if (!x || !mean || !stdv || B <= 0 || n <= 0) {
+    set_error("hdg_mlp_stats: invalid argument");
+    return HDG_ERR_INVALID_ARG;
+  }
+  k_mlp_stats<<<n, 256, 0, (cudaStream_t)stream>>>(x, B, n, mean, stdv);
+  HDG_CK(cudaGetLastError());
+  return HDG_OK;
+}
+
+int hdg_mlp_standardize(float* x, int64_t B, int n, const float* mean, const float* stdv, void* stream) {
+  if (!x || !mean || !stdv || B < 0 || n <= 0) {
+    set_error("hdg_mlp_standardize: invalid argument");
+    return HDG_ERR_INVALID_ARG;
+  }
+  k_mlp_standardize<<<nb(B * n), 256, 0, (cudaStream_t)stream>>>(x, B, n, mean, stdv);
+  HDG_CK(cudaGetLastError());
+  return HDG_OK;
+}
+
+int hdg_mlp_target(int64_t n, const double* vhat_next, const double* vhat, const double* dvhat1, float* out,
+                   void* stream) {
+  if (!vhat_next || !vhat || !dvhat1 || !out || n < 0) {
+    set_error("hdg_mlp_target: invalid argument");
+    return HDG_ERR_INVALID_ARG;
+  }
+  k_mlp_target<<<nb(n), 256, 0, (cudaStream_t)stream>>>(n, vhat_next, vhat, dvhat1, out);
+  HDG_CK(cudaGetLastError());
+  return HDG_OK;
 }
 
 int hdg_mlp_apply_trace(hdg_ctx_t ctx, const double* Vhat, const double* dvh1, const float* pred, const float* tmean,

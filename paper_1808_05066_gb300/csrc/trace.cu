@@ -195,6 +195,10 @@ __global__ void k_axpy(int64_t n, double a, const double* x, double* y) {
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
     y[t] += a * x[t];
 }
+__global__ void k_axpby(int64_t n, double a, const double* x, double b, const double* y, double* out) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+    out[t] = a * x[t] + b * y[t];
+}
 __global__ void k_scale_copy(int64_t n, double a, const double* x, double* y) {
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
     y[t] = a * x[t];
@@ -464,6 +468,13 @@ int launch_trace_matvec(hdg_ctx* ctx, const double* S, const double* x, double* 
 int launch_recover(hdg_ctx* ctx, const double* recov, const double* dVhat, double* dV, cudaStream_t s) {
   k_recover<<<(unsigned)ctx->E, 256, sizeof(double) * ctx->NT, s>>>(recov, dVhat, ctx->d_tgidx, ctx->NV, ctx->NT,
                                                                    ctx->M, dV);
+  HDG_CK(cudaGetLastError());
+  return HDG_OK;
+}
+
+int launch_axpby(int64_t n, double a, const double* x, double b, const double* y, double* out, cudaStream_t s) {
+  if (n <= 0) return HDG_OK;
+  k_axpby<<<nblocks(n), kThreads, 0, s>>>(n, a, x, b, y, out);
   HDG_CK(cudaGetLastError());
   return HDG_OK;
 }

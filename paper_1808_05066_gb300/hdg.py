@@ -36,7 +36,8 @@ EXPORTED = [
     "hdg_trace_matvec", "hdg_residual_norm", "hdg_newton_step", "hdg_profile_enable",
     "hdg_profile_reset", "hdg_profile_read", "hdg_last_error", "hdg_assemble_condense_noalloc",
     "hdg_mlp_param_count", "hdg_mlp_init", "hdg_mlp_features", "hdg_mlp_forward", "hdg_mlp_gradient",
-    "hdg_mlp_train_step", "hdg_mlp_apply_trace",
+    "hdg_mlp_train_step", "hdg_mlp_apply_trace", "hdg_mlp_stats", "hdg_mlp_standardize", "hdg_mlp_target",
+    "hdg_axpby",
 ]
 HDG_KERNEL_POINTWISE = 0
 HDG_KERNEL_ASSEMBLE = 1
@@ -96,6 +97,10 @@ def _load():
         "hdg_mlp_gradient": (c_int, [P, P, c_int, c_int, c_int, P, P, c_int64, P, P]),
         "hdg_mlp_train_step": (c_int, [P, P, c_int, c_int, c_int, P, P, c_int64, ctypes.c_float, c_int, P, P]),
         "hdg_mlp_apply_trace": (c_int, [P, P, P, P, P, P, P, P]),
+        "hdg_mlp_stats": (c_int, [P, c_int64, c_int, P, P, P]),
+        "hdg_mlp_standardize": (c_int, [P, c_int64, c_int, P, P, P]),
+        "hdg_mlp_target": (c_int, [c_int64, P, P, P, P, P]),
+        "hdg_axpby": (c_int, [c_int64, c_double, P, c_double, P, P, P]),
         "hdg_profile_enable": (c_int, [P, c_int]),
         "hdg_profile_reset": (c_int, [P]),
         "hdg_profile_read": (c_int, [P, c_int, POINTER(c_int64), POINTER(c_double)]),
@@ -246,6 +251,10 @@ def hdg_newton_step(ctx, V, Vhat, hist, mass_coef, precision=HDG_PREC_FP64, tol=
     return it.value, res.value
 
 
+def hdg_axpby(n, a, x, b, y, out, stream=None):
+    _check(_lib.hdg_axpby(n, a, _ptr(x), b, _ptr(y), _ptr(out), _stream(stream)))
+
+
 def hdg_mlp_param_count(nin, nh, nout):
     return int(_lib.hdg_mlp_param_count(nin, nh, nout))
 
@@ -254,9 +263,21 @@ def hdg_mlp_init(params, nin, nh, nout, seed, stream=None):
     _check(_lib.hdg_mlp_init(_ptr(params), nin, nh, nout, seed, _stream(stream)))
 
 
-def hdg_mlp_features(ctx, V, Vhat, dvhat1, dvhat2, mean, scale, feat, stream=None):
-    _check(_lib.hdg_mlp_features(ctx, _ptr(V), _ptr(Vhat), _ptr(dvhat1), _ptr(dvhat2), _ptr(mean), _ptr(scale),
+def hdg_mlp_features(ctx, V, Vhat, dvhat1, dvhat2, mean, std, feat, stream=None):
+    _check(_lib.hdg_mlp_features(ctx, _ptr(V), _ptr(Vhat), _ptr(dvhat1), _ptr(dvhat2), _ptr(mean), _ptr(std),
                                  _ptr(feat), _stream(stream)))
+
+
+def hdg_mlp_stats(x, B, n, mean, std, stream=None):
+    _check(_lib.hdg_mlp_stats(_ptr(x), B, n, _ptr(mean), _ptr(std), _stream(stream)))
+
+
+def hdg_mlp_standardize(x, B, n, mean, std, stream=None):
+    _check(_lib.hdg_mlp_standardize(_ptr(x), B, n, _ptr(mean), _ptr(std), _stream(stream)))
+
+
+def hdg_mlp_target(n, vhat_next, vhat, dvhat1, out, stream=None):
+    _check(_lib.hdg_mlp_target(n, _ptr(vhat_next), _ptr(vhat), _ptr(dvhat1), _ptr(out), _stream(stream)))
 
 
 def hdg_mlp_forward(params, nin, nh, nout, x, B, y, stream=None):

@@ -115,6 +115,24 @@ def test_mixed_precision_matches_oracle(name, nsample):
         assert rel_fro(rec[e, nv * nt:], L["y"][nq:]) < TOL_BLOCK, (e, "y")
 
 
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+def test_mixed_tile_shapes_match_oracle(variant, monkeypatch):
+    """Every compiled tile shape of the mixed assembly (the autotuner's candidates)
+    gives the oracle's condensed blocks."""
+    monkeypatch.setenv("HDG_ASM_VARIANT", str(variant))
+    case = CASES["ns3d_p3"]
+    gc = GpuCase(case)
+    prob, Q, V, Vh = oracle_setup(case)
+    hist_o = oracle_hist(prob, V, case)
+    gc.assemble(gc.history(), precision=1)
+    assert int(gc.status.abs().sum()) == 0
+    S, g = gc.S.cpu().numpy(), gc.g.cpu().numpy()
+    for e in (3, 40):
+        L = prob.condense(e, Q[e], V[e], prob.gather_trace(Vh, e), case.mass_coef, hist_o[e])
+        assert rel_fro(S[e], L["S"]) < TOL_BLOCK, (variant, e)
+        assert rel_fro(g[e], L["g"]) < TOL_BLOCK, (variant, e)
+
+
 def test_chunked_launch_ragged_tail(monkeypatch):
     """Element chunks of 7 over 128 elements (18 full chunks + a ragged tail of 2) give
     the same output as one chunk, bit for bit."""

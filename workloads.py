@@ -140,6 +140,10 @@ WORKLOADS = {
     "ns2d_p3_vortices": dict(dim=2, n=128, lo=0.0, hi=160.0, p=3, viscous=True,
                              mach=0.5, reynolds=5000.0, prandtl=0.71, dt=0.01, bdf=2,
                              seed=5, n_vortices=32),
+    # the same flow on a 16x16 patch (same h, 4 vortices): the learned-warm-start test case
+    "ns2d_p3_vortices_small": dict(dim=2, n=16, lo=0.0, hi=20.0, p=3, viscous=True,
+                                   mach=0.5, reynolds=5000.0, prandtl=0.71, dt=0.01, bdf=2,
+                                   seed=5, n_vortices=4),
 }
 
 
