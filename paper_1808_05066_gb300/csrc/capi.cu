@@ -240,6 +240,7 @@ void hdg_ctx_destroy(hdg_ctx_t c) {
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (c->h_red) cudaFreeHost(c->h_red);
+  if (c->lu_graph_exec) cudaGraphExecDestroy(c->lu_graph_exec);
   for (auto& r : c->pending) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);

@@ -45,6 +45,7 @@ struct hdg_ctx {
   double* d_dense = nullptr; // dense trace matrix for the direct solver
   int* d_dpiv = nullptr;
   size_t dense_n = 0;
+  cudaGraphExec_t lu_graph_exec = nullptr;  // recorded pivot/scale/update sequence
   double* d_red = nullptr;   // reduction buffer (device)
   double* h_red = nullptr;   // pinned host mirror
   // Newton workspace

@@ -521,6 +521,10 @@ static int dense_solve(hdg_ctx* ctx, const double* S, const double* g, double* d
     HDG_CK(cudaMalloc(&ctx->d_dense, sizeof(double) * n * n));
     HDG_CK(cudaMalloc(&ctx->d_dpiv, sizeof(int) * (n + 1)));
     ctx->dense_n = (size_t)n;
+    if (ctx->lu_graph_exec) {  // the recorded graph refers to the old buffers
+      cudaGraphExecDestroy(ctx->lu_graph_exec);
+      ctx->lu_graph_exec = nullptr;
+    }
   }
   int rc = ensure_red(ctx);
   if (rc) return rc;
@@ -530,12 +534,34 @@ static int dense_solve(hdg_ctx* ctx, const double* S, const double* g, double* d
   HDG_CK(cudaMemsetAsync(bad, 0, sizeof(int), s));
   k_dense_scatter<<<nblocks(ctx->E * (int64_t)ctx->NT * ctx->NT), kThreads, 0, s>>>(S, ctx->d_tgidx, ctx->E, ctx->NT,
                                                                                    ctx->M, n, K);
-  for (int64_t k = 0; k < n; ++k) {
-    k_dense_pivot<<<1, 1024, 0, s>>>(K, n, k, ctx->d_dpiv, bad);
-    if (k + 1 < n) {
-      k_dense_scale<<<nblocks(n - k - 1), kThreads, 0, s>>>(K, n, k);
-      k_dense_update<<<nblocks((n - k - 1) * (n - k - 1)), kThreads, 0, s>>>(K, n, k);
+  // LU with partial pivoting: 3 launches per pivot, recorded once per context into a CUDA
+  // graph (on a context-owned stream, so the caller's stream may be the legacy default
+  // stream) and replayed on the caller's stream.
+  if (!ctx->lu_graph_exec) {
+    cudaStream_t cap = nullptr;
+    HDG_CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    cudaGraph_t graph = nullptr;
+    HDG_CK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+    for (int64_t k = 0; k < n; ++k) {
+      k_dense_pivot<<<1, 1024, 0, cap>>>(K, n, k, ctx->d_dpiv, bad);
+      if (k + 1 < n) {
+        k_dense_scale<<<nblocks(n - k - 1), kThreads, 0, cap>>>(K, n, k);
+        k_dense_update<<<nblocks((n - k - 1) * (n - k - 1)), kThreads, 0, cap>>>(K, n, k);
+      }
     }
+    cudaError_t ce = cudaStreamEndCapture(cap, &graph);
+    cudaStreamDestroy(cap);
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture (dense LU)");
+    ce = cudaGraphInstantiate(&ctx->lu_graph_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) {
+      ctx->lu_graph_exec = nullptr;
+      return cuda_fail(ce, "cudaGraphInstantiate (dense LU)");
+    }
+  }
+  {
+    LaunchScope ls(ctx, HDG_KERNEL_TRACE, s);
+    HDG_CK(cudaGraphLaunch(ctx->lu_graph_exec, s));
   }
   rc = launch_trace_rhs(ctx, g, dVhat, s);
   if (rc) return rc;
