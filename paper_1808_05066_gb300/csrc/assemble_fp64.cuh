@@ -38,6 +38,7 @@ struct AssembleArgs {
   double* ptf;          // [ne][NF][NGF][PT_FACE]
   double* Ap;           // [ne][NV][NV]
   double* Cp;           // [ne][NT][NV]
+  uint4* oz;            // [ne][...] exact-slice operands of the mixed condensation
   // outputs (global element index)
   double* S;            // [E][NT][NT]   (D' on entry to condense)
   double* g;            // [E][NT]

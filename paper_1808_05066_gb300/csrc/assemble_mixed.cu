@@ -1,16 +1,16 @@
-// Dispatch of the mixed-precision assemble + condense (see assemble_mixed.cuh).
+// Dispatch of the mixed-precision assemble + condense (assemble_mixed.cuh, condense_tc.cuh).
 #include <algorithm>
 #include <vector>
 
 #include "assemble_mixed.cuh"
+#include "condense_tc.cuh"
 #include "ctx.hpp"
 
 namespace hdg {
 
 namespace {
 
-constexpr int kThreads = 256;
-constexpr int kRefine = 2;
+constexpr int kSlices = 6;  // exact bf16 slices per operand in the condensation products
 
 int ensure_df_tables(hdg_ctx* ctx) {
   if (ctx->d_tab_df) return HDG_OK;
@@ -42,19 +42,50 @@ AsmVariant make_variant() {
   return AsmVariant{NTH, GTM, MixCfg<C, NTH, GTM>::asm_bytes, &k_assemble_df<C, NTH, GTM>};
 }
 
+// One compiled shape of the condensation kernel.
+struct CondVariant {
+  int threads;
+  size_t smem;
+  void (*kernel)(AssembleArgs);
+};
+
+template <class C, int NTH>
+CondVariant make_cond_variant() {
+  return CondVariant{NTH, CondTC<C, NTH, kSlices>::bytes, &k_condense_tc<C, NTH, kSlices>};
+}
+
+// Times `launch` once on the stream (the chunk's outputs are rewritten each time).
+template <class F>
+int time_launch(cudaStream_t s, F launch, float* ms) {
+  cudaEvent_t t0, t1;
+  HDG_CK(cudaEventCreate(&t0));
+  HDG_CK(cudaEventCreate(&t1));
+  HDG_CK(cudaEventRecord(t0, s));
+  launch();
+  HDG_CK(cudaEventRecord(t1, s));
+  HDG_CK(cudaEventSynchronize(t1));
+  HDG_CK(cudaGetLastError());
+  HDG_CK(cudaEventElapsedTime(ms, t0, t1));
+  cudaEventDestroy(t0);
+  cudaEventDestroy(t1);
+  return HDG_OK;
+}
+
 template <class C>
 int run_mixed(hdg_ctx* ctx, const double* V, const double* Vhat, const double* hist, double mass_coef, double* S,
               double* g, double* recov, double* R, int32_t* status, cudaStream_t s) {
   int rc = ensure_df_tables(ctx);
   if (rc) return rc;
-  const size_t per = sizeof(double) * ((size_t)C::NG * C::PT_VOL + (size_t)C::NF * C::NGF * C::PT_FACE +
-                                       (size_t)C::NV * C::NV + (size_t)C::NT * C::NV);
+  using TC = CondTC<C, 256, kSlices>;
+  const size_t per_pt = sizeof(double) * ((size_t)C::NG * C::PT_VOL + (size_t)C::NF * C::NGF * C::PT_FACE +
+                                          (size_t)C::NV * C::NV + (size_t)C::NT * C::NV);
+  const size_t per = per_pt + sizeof(uint4) * TC::slice_uint4;
   if (ctx->chunk == 0) {
     int64_t ch = std::min<int64_t>(ctx->E, 8192);
-    while (ch > 256 && per * ch > ((size_t)3 << 30)) ch /= 2;
+    while (ch > 256 && per * ch > ((size_t)8 << 30)) ch /= 2;
     ctx->chunk = ch;
   }
-  const size_t need = per * ctx->chunk;
+  const size_t need = per * ctx->chunk + 256;  // + room to align the slice scratch
   if (ctx->scr_bytes < need) {
     if (ctx->d_scr) cudaFree(ctx->d_scr);
     ctx->d_scr = nullptr;
@@ -66,12 +97,14 @@ int run_mixed(hdg_ctx* ctx, const double* V, const double* Vhat, const double* h
   const AsmVariant variants[] = {make_variant<C, 256, 64>(), make_variant<C, 256, 32>(),
                                  make_variant<C, 512, 64>(), make_variant<C, 128, 16>()};
   constexpr int NVAR = 4;
+  const CondVariant cvariants[] = {make_cond_variant<C, 256>(), make_cond_variant<C, 512>()};
+  constexpr int NCVAR = 2;
   static bool attr_done = false;
   if (!attr_done) {
     for (const AsmVariant& v : variants)
       HDG_CK(cudaFuncSetAttribute(v.kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem));
-    HDG_CK(cudaFuncSetAttribute(k_condense_df<C, kThreads, kRefine>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)CondCfg<C, kThreads>::bytes));
+    for (const CondVariant& v : cvariants)
+      HDG_CK(cudaFuncSetAttribute(v.kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem));
     attr_done = true;
   }
   const df2* td = reinterpret_cast<const df2*>(ctx->d_tab_df);
@@ -99,6 +132,10 @@ int run_mixed(hdg_ctx* ctx, const double* V, const double* Vhat, const double* h
   a.ptf = a.ptv + ch * C::NG * C::PT_VOL;
   a.Ap = a.ptf + ch * C::NF * C::NGF * C::PT_FACE;
   a.Cp = a.Ap + ch * C::NV * C::NV;
+  {  // 256-byte aligned start of the slice scratch (chunk sizes may be odd)
+    const uintptr_t p = reinterpret_cast<uintptr_t>(a.Cp + ch * C::NT * C::NV);
+    a.oz = reinterpret_cast<uint4*>((p + 255) & ~(uintptr_t)255);
+  }
   const int pw_threads = ((C::NG + C::NF * C::NGF + 31) / 32) * 32;
   for (int64_t e0 = 0; e0 < ctx->E; e0 += ch) {
     a.e0 = e0;
@@ -107,40 +144,54 @@ int run_mixed(hdg_ctx* ctx, const double* V, const double* Vhat, const double* h
       LaunchScope ls(ctx, HDG_KERNEL_POINTWISE, s);
       k_pointwise<C, df2><<<(unsigned)a.ne, pw_threads, 0, s>>>(a, ctx->T, ctx->ph);
     }
-    if (ctx->asm_variant < 0 && a.ne >= 512) {
-      // autotune on this chunk: time every compiled shape (each writes the same outputs)
-      float best = 1e30f;
-      int best_i = 0;
-      cudaEvent_t t0, t1;
-      HDG_CK(cudaEventCreate(&t0));
-      HDG_CK(cudaEventCreate(&t1));
-      for (int i = 0; i < NVAR; ++i) {
-        HDG_CK(cudaEventRecord(t0, s));
-        variants[i].kernel<<<(unsigned)a.ne, variants[i].threads, variants[i].smem, s>>>(a, ctx->T, TD);
-        HDG_CK(cudaEventRecord(t1, s));
-        HDG_CK(cudaEventSynchronize(t1));
-        HDG_CK(cudaGetLastError());
-        float ms = 0.f;
-        HDG_CK(cudaEventElapsedTime(&ms, t0, t1));
-        if (ms < best) {
-          best = ms;
-          best_i = i;
+    if ((ctx->asm_variant < 0 || ctx->cond_variant < 0) && a.ne >= 512) {
+      // autotune on this chunk: time every compiled shape (each rewrites the same outputs)
+      if (ctx->asm_variant < 0) {
+        float best = 1e30f;
+        int best_i = 0;
+        for (int i = 0; i < NVAR; ++i) {
+          float ms = 0.f;
+          const AsmVariant& v = variants[i];
+          int rc = time_launch(s, [&] { v.kernel<<<(unsigned)a.ne, v.threads, v.smem, s>>>(a, ctx->T, TD); }, &ms);
+          if (rc) return rc;
+          if (ms < best) {
+            best = ms;
+            best_i = i;
+          }
         }
+        ctx->asm_variant = best_i;
+        ctx->asm_variant_threads = variants[best_i].threads;
+        ctx->asm_variant_gt = variants[best_i].gt;
       }
-      cudaEventDestroy(t0);
-      cudaEventDestroy(t1);
-      ctx->asm_variant = best_i;
-      ctx->asm_variant_threads = variants[best_i].threads;
-      ctx->asm_variant_gt = variants[best_i].gt;
+      if (ctx->cond_variant < 0) {
+        const AsmVariant& v = variants[ctx->asm_variant];
+        float best = 1e30f;
+        int best_i = 0;
+        for (int i = 0; i < NCVAR; ++i) {
+          // the condensation overwrites its inputs: assemble again before each trial
+          v.kernel<<<(unsigned)a.ne, v.threads, v.smem, s>>>(a, ctx->T, TD);
+          float ms = 0.f;
+          const CondVariant& cv = cvariants[i];
+          int rc = time_launch(s, [&] { cv.kernel<<<(unsigned)a.ne, cv.threads, cv.smem, s>>>(a); }, &ms);
+          if (rc) return rc;
+          if (ms < best) {
+            best = ms;
+            best_i = i;
+          }
+        }
+        ctx->cond_variant = best_i;
+        ctx->cond_variant_threads = cvariants[best_i].threads;
+      }
     }
     const AsmVariant& v = variants[ctx->asm_variant < 0 ? 0 : ctx->asm_variant];
     {
       LaunchScope ls(ctx, HDG_KERNEL_MIXED_ASSEMBLE, s);
       v.kernel<<<(unsigned)a.ne, v.threads, v.smem, s>>>(a, ctx->T, TD);
     }
+    const CondVariant& cv = cvariants[ctx->cond_variant < 0 ? 0 : ctx->cond_variant];
     {
       LaunchScope ls(ctx, HDG_KERNEL_MIXED_CONDENSE, s);
-      k_condense_df<C, kThreads, kRefine><<<(unsigned)a.ne, kThreads, CondCfg<C, kThreads>::bytes, s>>>(a);
+      cv.kernel<<<(unsigned)a.ne, cv.threads, cv.smem, s>>>(a);
     }
   }
   HDG_CK(cudaGetLastError());

@@ -1,18 +1,12 @@
-// Mixed-precision assemble + condense.
+// Mixed-precision assembly (the condensation that follows it is in condense_tc.cuh).
 //
 // Same mathematics as the FP64 form (assemble_fp64.cuh), arranged for GB300's pipes:
 //   * pointwise fluxes and Jacobians: FP64 (k_pointwise), stored as double-floats;
 //   * quadrature contractions for A', B', C', D': double-float multiply-accumulate on
 //     the FP32 pipe, each thread accumulating a strip of JW outputs in registers;
-//   * FP32 inverse (Gauss-Jordan with row pivoting, shared memory) of the equilibrated
-//     matrix D^{-1/2} A' D^{-1/2}, D = |diag A'|: at low Mach the state components differ
-//     by orders of magnitude and A' has condition numbers ~1e6 (3D, M = 0.1), which the
-//     symmetric diagonal scaling brings to ~1e2, within reach of FP32 refinement;
-//   * X = A'^{-1} [B' | R_v]: FP32 product with the inverse, then NREF sweeps of
-//     iterative refinement  r = B' - A' X (double-float), X += D^{-1/2} Ainv D^{-1/2} r;
-//   * S = D' - C' X and g = R_t - C' y: double-float.
-// The result agrees with the FP64 oracle to ~1e-12 relative (double-float carries
-// ~48 bits; refinement removes the FP32 factorisation error).
+//   * the four blocks leave as double-float pairs (hi, lo) in the 8-byte slots of the
+//     arrays the FP64 form uses, ready for the mixed condensation;
+//   * residuals R_v, R_t: FP64 from the double-float point data.
 #pragma once
 #include "assemble_fp64.cuh"
 #include "dfloat.cuh"
@@ -52,6 +46,12 @@ struct MixCfg {
                                       sizeof(double) * (C::NZ * C::M + C::GEO + C::NV + C::NT);
 };
 
+HDG_DEVI df2 df_add(df2 x, const dfacc& y) {
+  dfacc t = y;
+  t.add(x);
+  return t.norm();
+}
+
 // ------------------------------------------------------------------------------------
 // k_assemble_df: one CTA per element
 // ------------------------------------------------------------------------------------
@@ -83,10 +83,11 @@ __global__ void __launch_bounds__(NTHREADS) k_assemble_df(AssembleArgs a, DevTab
     const double* Gf = G + D * D + 1 + f * (D + 1);
     NsD[tid] = df_from(Gf[k] * (Gf[D] / detJ));
   }
-  double* Ap = a.Ap + le * NV * NV;
+  // A', B', C', D' leave as double-float pairs (8 bytes, in the FP64 arrays' slots)
+  df2* Ad = reinterpret_cast<df2*>(a.Ap) + le * NV * NV;
   df2* Cp = reinterpret_cast<df2*>(a.Cp) + le * NT * NV;
-  double* Bp = a.recov + e * (int64_t)(NV * NT + NV);
-  double* Dp = a.S + e * (int64_t)NT * NT;
+  df2* Bd = reinterpret_cast<df2*>(a.recov + e * (int64_t)(NV * NT + NV));
+  df2* Dd = reinterpret_cast<df2*>(a.S + e * (int64_t)NT * NT);
   const df2* ptv = reinterpret_cast<const df2*>(a.ptv) + le * NG * C::PT_VOL;
   const df2* ptf = reinterpret_cast<const df2*>(a.ptf) + le * NF * NGF * C::PT_FACE;
 
@@ -195,9 +196,8 @@ __global__ void __launch_bounds__(NTHREADS) k_assemble_df(AssembleArgs a, DevTab
         for (int jj = 0; jj < JW; ++jj) {
           const int j = j0 + jj;
           if (j >= NZ) continue;
-          const double v = acc[jj].value();
-          double* dst = j < NP ? Ap + row * NV + j * M + l : Bp + row * NT + (j - NP) * M + l;
-          *dst = (g0 == 0) ? v : *dst + v;
+          df2* dst = j < NP ? Ad + row * NV + j * M + l : Bd + row * NT + (j - NP) * M + l;
+          *dst = (g0 == 0) ? acc[jj].norm() : df_add(*dst, acc[jj]);
         }
       }
     }
@@ -282,14 +282,15 @@ __global__ void __launch_bounds__(NTHREADS) k_assemble_df(AssembleArgs a, DevTab
         for (int jj = 0; jj < JWF; ++jj) {
           const int j = j0 + jj;
           if (j >= NZ) continue;
-          const double v = acc[jj].value();
           if (j < NP) {
-            Ap[rowv * NV + j * M + l] += v;
-            Cp[rowt * NV + j * M + l] = df_from(v);
+            df2& dst = Ad[rowv * NV + j * M + l];
+            dst = df_add(dst, acc[jj]);
+            Cp[rowt * NV + j * M + l] = acc[jj].norm();
           } else {
             const int tcol = (j - NP) * M + l;
-            Bp[rowv * NT + tcol] += v;
-            Dp[rowt * NT + tcol] = v;
+            df2& dst = Bd[rowv * NT + tcol];
+            dst = df_add(dst, acc[jj]);
+            Dd[rowt * NT + tcol] = acc[jj].norm();
           }
         }
       }
@@ -299,284 +300,6 @@ __global__ void __launch_bounds__(NTHREADS) k_assemble_df(AssembleArgs a, DevTab
   double* Rout = a.R + e * (int64_t)(NV + NT);
   for (int t = tid; t < NV; t += NTHREADS) Rout[t] = Rv[t];
   for (int t = tid; t < NT; t += NTHREADS) Rout[NV + t] = Rt[t];
-}
-
-// ------------------------------------------------------------------------------------
-// k_condense_df: one CTA per element
-//
-//  1. Jacobi equilibration sc = |diag A'|^{-1/2}; FP32 Gauss-Jordan inversion with row
-//     pivoting of sc A' sc (Ai, in place): one pass of ~NV^3 FP32 FMAs, 3 barriers per
-//     pivot step, and every later solve is a GEMM without sequential dependencies.
-//  2. Per block of CB right-hand sides (columns of B' and R_v):
-//       X  = sc (Ai (sc B))                         FP32 GEMM
-//       NREF times:  W = sc (B - A' X)              double-float GEMM
-//                    X += sc (Ai W)                 FP32 GEMM, double-float update
-//       S[:, block] -= C' X, g = R_t - C' y        double-float GEMM
-//     GEMMs use RT x CT register tiles per thread.
-// ------------------------------------------------------------------------------------
-template <class C, int NTHREADS>
-struct CondCfg {
-  static constexpr int NV = C::NV, NT = C::NT;
-  static constexpr int CB = 32;
-  static constexpr int RT = 4, CT = 4;
-  static constexpr size_t bytes =
-      sizeof(df2) * (NV * NV + NV * CB) + sizeof(float) * (NV * NV + NV * CB + NV) + sizeof(int) * NV + 64;
-};
-
-template <class C, int NTHREADS, int NREF>
-__global__ void __launch_bounds__(NTHREADS) k_condense_df(AssembleArgs a) {
-  constexpr int NV = C::NV, NT = C::NT;
-  using Q = CondCfg<C, NTHREADS>;
-  constexpr int CB = Q::CB, RT = Q::RT, CT = Q::CT;
-  constexpr int NRT = (NV + RT - 1) / RT;   // row tiles over NV
-  constexpr int NTT = (NT + RT - 1) / RT;   // row tiles over NT
-  constexpr int NCT = CB / CT;              // column tiles
-  extern __shared__ double smem_d[];
-  df2* Ad = reinterpret_cast<df2*>(smem_d);          // [NV][NV]  A' (double-float)
-  df2* Xb = Ad + NV * NV;                            // [NV][CB]  current block of X
-  float* Ai = reinterpret_cast<float*>(Xb + NV * CB);  // [NV][NV]  (sc A' sc)^{-1}
-  float* W = Ai + NV * NV;                           // [NV][CB]
-  float* sc = W + NV * CB;                           // [NV]
-  int* piv = reinterpret_cast<int*>(sc + NV);        // [NV]
-  __shared__ int s_piv, s_bad;
-  __shared__ float s_corr[NREF], s_xmax;
-  const int64_t le = blockIdx.x;
-  const int64_t e = a.e0 + le;
-  const int tid = threadIdx.x;
-  const double* Ap = a.Ap + le * NV * NV;
-  const df2* Cp = reinterpret_cast<const df2*>(a.Cp) + le * NT * NV;
-  double* Xg = a.recov + e * (int64_t)(NV * NT + NV);
-  double* yg = Xg + NV * NT;
-  double* S = a.S + e * (int64_t)NT * NT;
-  const double* R = a.R + e * (int64_t)(NV + NT);
-
-  for (int r = tid; r < NV; r += NTHREADS) {
-    double d = fabs(Ap[r * NV + r]);
-    sc[r] = d > 0.0 ? (float)(1.0 / ::sqrt(d)) : 1.f;
-  }
-  if (tid == 0) s_bad = 0;
-  __syncthreads();
-  for (int t = tid; t < NV * NV; t += NTHREADS) {
-    double v = Ap[t];
-    Ad[t] = df_from(v);
-    Ai[t] = (float)(v * (double)sc[t / NV] * (double)sc[t % NV]);
-  }
-  __syncthreads();
-  // ---- Gauss-Jordan inversion in place with row pivoting
-  for (int k = 0; k < NV; ++k) {
-    if (tid < 32) {
-      float best = -1.f;
-      int bi = k;
-      for (int r = k + tid; r < NV; r += 32) {
-        float v = fabsf(Ai[r * NV + k]);
-        if (v > best) {
-          best = v;
-          bi = r;
-        }
-      }
-      for (int off = 16; off > 0; off >>= 1) {
-        float ob = __shfl_down_sync(0xffffffffu, best, off);
-        int oi = __shfl_down_sync(0xffffffffu, bi, off);
-        if (ob > best || (ob == best && oi < bi)) {
-          best = ob;
-          bi = oi;
-        }
-      }
-      if (tid == 0) {
-        s_piv = bi;
-        piv[k] = bi;
-        if (!(best > 0.f)) s_bad |= HDG_STATUS_SINGULAR;
-      }
-    }
-    __syncthreads();
-    const int pr = s_piv;
-    const float pivv = Ai[pr * NV + k];
-    const float ip = pivv != 0.f ? 1.f / pivv : 0.f;
-    __syncthreads();
-    // swap rows k and pr, scale the pivot row (the pivot column entry becomes 1/pivot)
-    for (int j = tid; j < NV; j += NTHREADS) {
-      float vk = Ai[k * NV + j], vp = Ai[pr * NV + j];
-      if (pr != k) Ai[pr * NV + j] = vk;
-      Ai[k * NV + j] = (j == k) ? ip : vp * ip;
-    }
-    __syncthreads();
-    // eliminate column k from the other rows (multipliers staged first: the pass
-    // overwrites column k)
-    float* fcol = W;
-    for (int r = tid; r < NV; r += NTHREADS) fcol[r] = Ai[r * NV + k];
-    __syncthreads();
-    for (int t = tid; t < NV * NV; t += NTHREADS) {
-      int r = t / NV, j = t % NV;
-      if (r == k) continue;
-      const float f = fcol[r];
-      if (j == k)
-        Ai[t] = -f * ip;
-      else
-        Ai[t] = fmaf(-f, Ai[k * NV + j], Ai[t]);
-    }
-    __syncthreads();
-  }
-  // undo the row interchanges as column interchanges, in reverse order
-  for (int k = NV - 1; k >= 0; --k) {
-    const int p = piv[k];
-    if (p != k)
-      for (int r = tid; r < NV; r += NTHREADS) {
-        float t = Ai[r * NV + k];
-        Ai[r * NV + k] = Ai[r * NV + p];
-        Ai[r * NV + p] = t;
-      }
-    __syncthreads();
-  }
-
-  // ---- blocks of right-hand sides
-  for (int c0 = 0; c0 < NT + 1; c0 += CB) {
-    const int nc = (NT + 1 - c0) < CB ? (NT + 1 - c0) : CB;
-    auto bval = [&](int r, int c) -> double {  // B' (stored in X) or R_v
-      int col = c0 + c;
-      return c < nc ? (col < NT ? Xg[r * NT + col] : R[r]) : 0.0;
-    };
-    for (int t = tid; t < NV * CB; t += NTHREADS) W[t] = (float)(bval(t / CB, t % CB) * (double)sc[t / CB]);
-    __syncthreads();
-    // X = sc (Ai W)
-    for (int tile = tid; tile < NRT * NCT; tile += NTHREADS) {
-      const int r0 = (tile / NCT) * RT, cc0 = (tile % NCT) * CT;
-      float acc[RT][CT] = {};
-      for (int k = 0; k < NV; ++k) {
-        float w[CT];
-#pragma unroll
-        for (int j = 0; j < CT; ++j) w[j] = W[k * CB + cc0 + j];
-#pragma unroll
-        for (int i = 0; i < RT; ++i) {
-          float av = (r0 + i < NV) ? Ai[(r0 + i) * NV + k] : 0.f;
-#pragma unroll
-          for (int j = 0; j < CT; ++j) acc[i][j] = fmaf(av, w[j], acc[i][j]);
-        }
-      }
-#pragma unroll
-      for (int i = 0; i < RT; ++i)
-        if (r0 + i < NV)
-#pragma unroll
-          for (int j = 0; j < CT; ++j) Xb[(r0 + i) * CB + cc0 + j] = df_from((double)acc[i][j] * (double)sc[r0 + i]);
-    }
-    __syncthreads();
-    if (tid < NREF) s_corr[tid] = 0.f;
-    if (tid == 0) s_xmax = 0.f;
-    for (int it = 0; it < NREF; ++it) {
-      // W = sc (B - A' X) in double-float
-      for (int tile = tid; tile < NRT * NCT; tile += NTHREADS) {
-        const int r0 = (tile / NCT) * RT, cc0 = (tile % NCT) * CT;
-        dfacc acc[RT][CT];
-#pragma unroll
-        for (int i = 0; i < RT; ++i)
-#pragma unroll
-          for (int j = 0; j < CT; ++j)
-            if (r0 + i < NV) acc[i][j].add(df_from(bval(r0 + i, cc0 + j)));
-        for (int k = 0; k < NV; ++k) {
-          df2 xv[CT];
-#pragma unroll
-          for (int j = 0; j < CT; ++j) xv[j] = Xb[k * CB + cc0 + j];
-#pragma unroll
-          for (int i = 0; i < RT; ++i) {
-            df2 av = (r0 + i < NV) ? Ad[(r0 + i) * NV + k] : df2{0.f, 0.f};
-            av.hi = -av.hi;
-            av.lo = -av.lo;
-#pragma unroll
-            for (int j = 0; j < CT; ++j) acc[i][j].mac(av, xv[j]);
-          }
-        }
-#pragma unroll
-        for (int i = 0; i < RT; ++i)
-          if (r0 + i < NV)
-#pragma unroll
-            for (int j = 0; j < CT; ++j) W[(r0 + i) * CB + cc0 + j] = (acc[i][j].hi + acc[i][j].lo) * sc[r0 + i];
-      }
-      __syncthreads();
-      // X += sc (Ai W)
-      for (int tile = tid; tile < NRT * NCT; tile += NTHREADS) {
-        const int r0 = (tile / NCT) * RT, cc0 = (tile % NCT) * CT;
-        float acc[RT][CT] = {};
-        for (int k = 0; k < NV; ++k) {
-          float w[CT];
-#pragma unroll
-          for (int j = 0; j < CT; ++j) w[j] = W[k * CB + cc0 + j];
-#pragma unroll
-          for (int i = 0; i < RT; ++i) {
-            float av = (r0 + i < NV) ? Ai[(r0 + i) * NV + k] : 0.f;
-#pragma unroll
-            for (int j = 0; j < CT; ++j) acc[i][j] = fmaf(av, w[j], acc[i][j]);
-          }
-        }
-        float cmax = 0.f, xmax = 0.f;
-#pragma unroll
-        for (int i = 0; i < RT; ++i)
-          if (r0 + i < NV)
-#pragma unroll
-            for (int j = 0; j < CT; ++j) {
-              const float corr = acc[i][j] * sc[r0 + i];
-              dfacc u;
-              u.add(Xb[(r0 + i) * CB + cc0 + j]);
-              u.add(df2{corr, 0.f});
-              const df2 xn = u.norm();
-              Xb[(r0 + i) * CB + cc0 + j] = xn;
-              cmax = fmaxf(cmax, fabsf(corr));
-              xmax = fmaxf(xmax, fabsf(xn.hi));
-            }
-        atomicMax(reinterpret_cast<int*>(&s_corr[it]), __float_as_int(cmax));
-        if (it == NREF - 1) atomicMax(reinterpret_cast<int*>(&s_xmax), __float_as_int(xmax));
-      }
-      __syncthreads();
-    }
-    // Each sweep contracts the error by rho ~ |I - Ainv A'|; the correction of the last
-    // sweep measures the error before it, so the error left is ~ c_last^2 / c_prev.
-    if (tid == 0) {
-      const float cl = s_corr[NREF - 1];
-      const float cp = NREF > 1 ? s_corr[NREF > 1 ? NREF - 2 : 0] : s_xmax;
-      const bool ok = (double)cl * (double)cl <= 1e-10 * (double)s_xmax * (double)cp;
-      if (!ok) s_bad |= 4;  // refinement did not reach 1e-10
-    }
-    // store X (and y) for the recovery
-    for (int t = tid; t < NV * CB; t += NTHREADS) {
-      int r = t / CB, c = t % CB, col = c0 + c;
-      if (c < nc) {
-        if (col < NT)
-          Xg[r * NT + col] = df_val(Xb[t]);
-        else
-          yg[r] = df_val(Xb[t]);
-      }
-    }
-    // Schur products: S[:, block] = D' - C' X ; g = R_t - C' y
-    for (int tile = tid; tile < NTT * NCT; tile += NTHREADS) {
-      const int r0 = (tile / NCT) * RT, cc0 = (tile % NCT) * CT;
-      dfacc acc[RT][CT];
-      for (int k = 0; k < NV; ++k) {
-        df2 xv[CT];
-#pragma unroll
-        for (int j = 0; j < CT; ++j) xv[j] = Xb[k * CB + cc0 + j];
-#pragma unroll
-        for (int i = 0; i < RT; ++i) {
-          const df2 cv = (r0 + i < NT) ? Cp[(r0 + i) * NV + k] : df2{0.f, 0.f};
-#pragma unroll
-          for (int j = 0; j < CT; ++j) acc[i][j].mac(cv, xv[j]);
-        }
-      }
-#pragma unroll
-      for (int i = 0; i < RT; ++i) {
-        const int r = r0 + i;
-        if (r >= NT) continue;
-#pragma unroll
-        for (int j = 0; j < CT; ++j) {
-          const int c = cc0 + j, col = c0 + c;
-          if (c >= nc) continue;
-          if (col < NT)
-            S[r * NT + col] -= acc[i][j].value();
-          else
-            a.g[e * NT + r] = R[NV + r] - acc[i][j].value();
-        }
-      }
-    }
-    __syncthreads();
-  }
-  if (tid == 0 && s_bad) atomicOr(a.status + e, s_bad);
 }
 
 }  // namespace hdg

@@ -133,6 +133,44 @@ def test_mixed_tile_shapes_match_oracle(variant, monkeypatch):
         assert rel_fro(g[e], L["g"]) < TOL_BLOCK, (variant, e)
 
 
+@pytest.mark.parametrize("cvariant", [0, 1])
+@pytest.mark.parametrize("name", ["ns3d_p3", "euler2d_p2", "ns2d_p4"])
+def test_mixed_condensation_shapes_match_oracle(name, cvariant, monkeypatch):
+    """Both compiled shapes of the tensor-core condensation (256 and 512 threads) give the
+    oracle's S, g, X and y, including the ragged last block of right-hand sides."""
+    monkeypatch.setenv("HDG_COND_VARIANT", str(cvariant))
+    case = CASES[name]
+    gc = GpuCase(case)
+    prob, Q, V, Vh = oracle_setup(case)
+    hist_o = oracle_hist(prob, V, case)
+    gc.assemble(gc.history(), precision=1)
+    assert int(gc.status.abs().sum()) == 0
+    S, g, rec = gc.S.cpu().numpy(), gc.g.cpu().numpy(), gc.recov.cpu().numpy()
+    nv, nt = gc.info["nv"], gc.info["nt"]
+    for e in (0, prob.mesh.E - 1):
+        L = prob.condense(e, None if Q is None else Q[e], V[e], prob.gather_trace(Vh, e), case.mass_coef,
+                          hist_o[e])
+        nq = L["Rl"].size - nv
+        assert rel_fro(S[e], L["S"]) < TOL_BLOCK, (cvariant, e, "S")
+        assert rel_fro(g[e], L["g"]) < TOL_BLOCK, (cvariant, e, "g")
+        assert rel_fro(rec[e, :nv * nt].reshape(nv, nt), L["X"][nq:]) < TOL_BLOCK, (cvariant, e, "X")
+        assert rel_fro(rec[e, nv * nt:], L["y"][nq:]) < TOL_BLOCK, (cvariant, e, "y")
+
+
+def test_mixed_chunked_launch_ragged_tail(monkeypatch):
+    """The mixed form in element chunks of 7 (odd-sized scratch offsets, a ragged tail)
+    gives the same output as one chunk, bit for bit."""
+    case = CASES["euler2d_p2"]
+    gc = GpuCase(case)
+    hist = gc.history()
+    gc.assemble(hist, precision=1)
+    S1 = gc.S.clone(); rec1 = gc.recov.clone(); g1 = gc.g.clone()
+    monkeypatch.setenv("HDG_ELEMENT_CHUNK", "7")
+    gc2 = GpuCase(case)
+    gc2.assemble(hist, precision=1)
+    assert bool((gc2.S == S1).all()) and bool((gc2.recov == rec1).all()) and bool((gc2.g == g1).all())
+
+
 def test_chunked_launch_ragged_tail(monkeypatch):
     """Element chunks of 7 over 128 elements (18 full chunks + a ragged tail of 2) give
     the same output as one chunk, bit for bit."""
