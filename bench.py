@@ -254,7 +254,7 @@ def main():
     value = ws * E * args.steps / (ms / 1000.0)
     classes = {"pointwise": hdg.HDG_KERNEL_POINTWISE, "assemble": hdg.HDG_KERNEL_ASSEMBLE,
                "condense": hdg.HDG_KERNEL_CONDENSE, "mixed_assemble": hdg.HDG_KERNEL_MIXED_ASSEMBLE,
-               "mixed_condense": hdg.HDG_KERNEL_MIXED_CONDENSE}
+               "mixed_prep": hdg.HDG_KERNEL_MIXED_PREP, "mixed_condense": hdg.HDG_KERNEL_MIXED_CONDENSE}
     prof = {k: hdg.hdg_profile_read(W.ctx.handle, c) for k, c in classes.items()}
     launches_total, _ = hdg.hdg_profile_read(W.ctx.handle, -1)
     hdg.hdg_profile_enable(W.ctx.handle, False)

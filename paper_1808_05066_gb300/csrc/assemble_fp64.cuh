@@ -39,6 +39,7 @@ struct AssembleArgs {
   double* Ap;           // [ne][NV][NV]
   double* Cp;           // [ne][NT][NV]
   uint4* oz;            // [ne][...] exact-slice operands of the mixed condensation
+  float* prep;          // [ne][...] inverse, FP32 copy and scales for the mixed condensation
   // outputs (global element index)
   double* S;            // [E][NT][NT]   (D' on entry to condense)
   double* g;            // [E][NT]

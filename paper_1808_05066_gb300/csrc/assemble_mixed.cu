@@ -79,13 +79,13 @@ int run_mixed(hdg_ctx* ctx, const double* V, const double* Vhat, const double* h
   using TC = CondTC<C, 256, kSlices>;
   const size_t per_pt = sizeof(double) * ((size_t)C::NG * C::PT_VOL + (size_t)C::NF * C::NGF * C::PT_FACE +
                                           (size_t)C::NV * C::NV + (size_t)C::NT * C::NV);
-  const size_t per = per_pt + sizeof(uint4) * TC::slice_uint4;
+  const size_t per = per_pt + sizeof(uint4) * TC::slice_uint4 + sizeof(float) * TC::prep_floats;
   if (ctx->chunk == 0) {
     int64_t ch = std::min<int64_t>(ctx->E, 8192);
-    while (ch > 256 && per * ch > ((size_t)8 << 30)) ch /= 2;
+    while (ch > 256 && per * ch > ((size_t)12 << 30)) ch /= 2;
     ctx->chunk = ch;
   }
-  const size_t need = per * ctx->chunk + 256;  // + room to align the slice scratch
+  const size_t need = per * ctx->chunk + 512;  // + room to align the slice and prep scratch
   if (ctx->scr_bytes < need) {
     if (ctx->d_scr) cudaFree(ctx->d_scr);
     ctx->d_scr = nullptr;
@@ -105,6 +105,8 @@ int run_mixed(hdg_ctx* ctx, const double* V, const double* Vhat, const double* h
       HDG_CK(cudaFuncSetAttribute(v.kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem));
     for (const CondVariant& v : cvariants)
       HDG_CK(cudaFuncSetAttribute(v.kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem));
+    HDG_CK(cudaFuncSetAttribute(k_condense_prep<C, kSlices>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)TC::prep_bytes));
     attr_done = true;
   }
   const df2* td = reinterpret_cast<const df2*>(ctx->d_tab_df);
@@ -135,6 +137,8 @@ int run_mixed(hdg_ctx* ctx, const double* V, const double* Vhat, const double* h
   {  // 256-byte aligned start of the slice scratch (chunk sizes may be odd)
     const uintptr_t p = reinterpret_cast<uintptr_t>(a.Cp + ch * C::NT * C::NV);
     a.oz = reinterpret_cast<uint4*>((p + 255) & ~(uintptr_t)255);
+    const uintptr_t q = reinterpret_cast<uintptr_t>(a.oz + ch * TC::slice_uint4);
+    a.prep = reinterpret_cast<float*>((q + 255) & ~(uintptr_t)255);
   }
   const int pw_threads = ((C::NG + C::NF * C::NGF + 31) / 32) * 32;
   for (int64_t e0 = 0; e0 < ctx->E; e0 += ch) {
@@ -170,6 +174,7 @@ int run_mixed(hdg_ctx* ctx, const double* V, const double* Vhat, const double* h
         for (int i = 0; i < NCVAR; ++i) {
           // the condensation overwrites its inputs: assemble again before each trial
           v.kernel<<<(unsigned)a.ne, v.threads, v.smem, s>>>(a, ctx->T, TD);
+          k_condense_prep<C, kSlices><<<(unsigned)a.ne, TC::PTH, TC::prep_bytes, s>>>(a);
           float ms = 0.f;
           const CondVariant& cv = cvariants[i];
           int rc = time_launch(s, [&] { cv.kernel<<<(unsigned)a.ne, cv.threads, cv.smem, s>>>(a); }, &ms);
@@ -189,6 +194,10 @@ int run_mixed(hdg_ctx* ctx, const double* V, const double* Vhat, const double* h
       v.kernel<<<(unsigned)a.ne, v.threads, v.smem, s>>>(a, ctx->T, TD);
     }
     const CondVariant& cv = cvariants[ctx->cond_variant < 0 ? 0 : ctx->cond_variant];
+    {
+      LaunchScope ls(ctx, HDG_KERNEL_MIXED_PREP, s);
+      k_condense_prep<C, kSlices><<<(unsigned)a.ne, TC::PTH, TC::prep_bytes, s>>>(a);
+    }
     {
       LaunchScope ls(ctx, HDG_KERNEL_MIXED_CONDENSE, s);
       cv.kernel<<<(unsigned)a.ne, cv.threads, cv.smem, s>>>(a);

@@ -6,11 +6,12 @@
 //   D' [NT][NT] in the S array; R_v, R_t in FP64.
 // Outputs (FP64): S over D', X = A'^{-1} B' over B' and y = A'^{-1} R_v, g.
 //
-// One CTA per element.
-//   1. Jacobi equilibration sc = |diag A'|^{-1/2}; FP32 Gauss-Jordan inverse Ai of
-//      sc A' sc with row pivoting (shared memory). A' and C' are cut into exact bf16
-//      slices (ozaki.cuh), stored fragment-native in a per-element scratch (L2).
-//   2. Per block of CB = 32 right-hand sides (columns of B' and R_v):
+// Two kernels, one CTA per element each:
+//   k_condense_prep (small CTA, several per SM so that elements hide each other's latency):
+//      Jacobi equilibration sc = |diag A'|^{-1/2}; FP32 Gauss-Jordan inverse with row
+//      pivoting of (sc A' sc)^T in shared memory; FP32 copy of A'; row exponents and exact
+//      bf16 slices (ozaki.cuh) of A' and C', fragment-native. All to a per-element scratch.
+//   k_condense_tc, per block of CB = 32 right-hand sides (columns of B' and R_v):
 //        X0 = sc Ai sc B                            FP32
 //        r0 = B - A' X0                             exact slices on the tensor cores
 //        d0 = sc Ai sc r0,  r1 = r0 - A'_hi d0      FP32 (d0 ~ rho |X|, rho ~ 1e-5)
@@ -31,75 +32,188 @@ struct CondTC {
   static constexpr int MTC = (NT + 15) / 16;  // row tiles of C'
   static constexpr int CB = 32, NTB = CB / 8;
   static constexpr int RT = NTHREADS >= 512 ? 2 : 4, CT = 4;  // FP32 register tile
+  static constexpr int LDA = (NV + 3) / 4 * 4;  // leading dimension of the transposed FP32 matrices
   // fragment-native slices per element: [tile][slice][lane] uint4
   static constexpr size_t slice_uint4 = (size_t)(MTA + MTC) * KT * OZS * 32;
   static constexpr size_t xs_bytes = sizeof(uint2) * KT * NTB * OZS * 32;
   static_assert(xs_bytes >= sizeof(float) * 2 * NV * CB, "residual buffers alias the slice buffer");
-  static constexpr size_t bytes = sizeof(float) * (2 * NV * NV + NV * CB + NV) + sizeof(df2) * NV * CB + xs_bytes +
+  static constexpr size_t bytes = sizeof(float) * (2 * NV * LDA + NV * CB + NV) + sizeof(df2) * NV * CB + xs_bytes +
                                   sizeof(int) * (NV + MTA * 16 + MTC * 16 + CB) + 64;
+  // per-element block written by k_condense_prep: Ai^T, A'^T [NV][LDA], sc [LDA], eA, eC
+  static constexpr int PREP_AI = 0, PREP_AH = NV * LDA, PREP_SC = 2 * NV * LDA, PREP_EA = PREP_SC + LDA,
+                       PREP_EC = PREP_EA + MTA * 16;
+  static constexpr size_t prep_floats = (size_t)(PREP_EC + MTC * 16 + 3) / 4 * 4;
+  static constexpr int PTH = 128;  // threads of the prep kernel
+  static constexpr size_t prep_bytes = sizeof(float) * (NV * LDA + NV) + sizeof(int) * (2 * NV + 2 * (PTH / 32)) + 64;
 };
 
-// out = Ai * W for an NV x CB block, RT x CT register tiles; epi(r0, c0, acc) stores.
-template <int NV, int CB, int RT, int CT, int NTHREADS, class Epi>
-HDG_DEVI void cond_gemm_f32(const float* __restrict__ A, const float* __restrict__ Wm, Epi epi) {
+// out = A * W for an NV x CB block with A stored transposed (At[k][r] = A[r][k], leading
+// dimension LDA, zero past NV): RT x CT register tiles, two vector loads per k.
+template <int NV, int LDA, int CB, int RT, int CT, int NTHREADS, class Epi>
+HDG_DEVI void cond_gemm_f32(const float* __restrict__ At, const float* __restrict__ Wm, Epi epi) {
+  static_assert(CT == 4 && (RT == 2 || RT == 4), "vector loads");
   constexpr int NRT = (NV + RT - 1) / RT, NCT = CB / CT;
   for (int tile = threadIdx.x; tile < NRT * NCT; tile += NTHREADS) {
     const int r0 = (tile / NCT) * RT, c0 = (tile % NCT) * CT;
     float acc[RT][CT] = {};
+#pragma unroll 4
     for (int k = 0; k < NV; ++k) {
       const float4 w = *reinterpret_cast<const float4*>(Wm + k * CB + c0);
+      float av[RT];
+      if constexpr (RT == 4) {
+        const float4 v = *reinterpret_cast<const float4*>(At + k * LDA + r0);
+        av[0] = v.x;
+        av[1] = v.y;
+        av[2] = v.z;
+        av[3] = v.w;
+      } else {
+        const float2 v = *reinterpret_cast<const float2*>(At + k * LDA + r0);
+        av[0] = v.x;
+        av[1] = v.y;
+      }
 #pragma unroll
       for (int i = 0; i < RT; ++i) {
-        const float av = (r0 + i < NV) ? A[(r0 + i) * NV + k] : 0.f;
-        acc[i][0] = fmaf(av, w.x, acc[i][0]);
-        acc[i][1] = fmaf(av, w.y, acc[i][1]);
-        acc[i][2] = fmaf(av, w.z, acc[i][2]);
-        acc[i][3] = fmaf(av, w.w, acc[i][3]);
+        acc[i][0] = fmaf(av[i], w.x, acc[i][0]);
+        acc[i][1] = fmaf(av[i], w.y, acc[i][1]);
+        acc[i][2] = fmaf(av[i], w.z, acc[i][2]);
+        acc[i][3] = fmaf(av[i], w.w, acc[i][3]);
       }
     }
     epi(r0, c0, acc);
   }
 }
 
+// In-place Gauss-Jordan inverse with partial (row) pivoting of an n x n FP32 matrix G in
+// shared memory (leading dimension LD), for a small CTA. Warp w eliminates rows w, w+NWARP,
+// ... with lanes over columns and the pivot row in registers; the lane that updates column
+// k+1 proposes the next pivot, so a step takes two barriers. The row interchanges are left
+// as a column permutation: the inverse's column j is G's column sigma(j), sigma = the
+// interchanges (k, piv[k]) applied for k = 0, 1, ... (gj_column). Returns false on a zero pivot.
+template <int N, int LD, int NTHREADS>
+HDG_DEVI bool gj_inverse_smem(float* G, int* piv, float* cval, int* crow) {
+  constexpr int NWARP = NTHREADS / 32, NQ = (N + 31) / 32;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  bool ok = true;
+  if (lane == 0) {  // candidates for column 0
+    float bv = 0.f;
+    int br = -1;
+    for (int r = warp; r < N; r += NWARP) {
+      const float v = G[r * LD];
+      if (br < 0 || fabsf(v) > fabsf(bv)) {
+        bv = v;
+        br = r;
+      }
+    }
+    cval[warp] = bv;
+    crow[warp] = br;
+  }
+  __syncthreads();
+  for (int k = 0; k < N; ++k) {
+    float pv = 0.f;
+    int pr = -1;
+#pragma unroll
+    for (int w = 0; w < NWARP; ++w) {
+      const int r = crow[w];
+      const float v = cval[w];
+      if (r >= 0 && (pr < 0 || fabsf(v) > fabsf(pv) || (fabsf(v) == fabsf(pv) && r < pr))) {
+        pv = v;
+        pr = r;
+      }
+    }
+    if (pr < 0) pr = k;  // no candidate (NaN input): keep the row
+    if (!(fabsf(pv) > 0.f)) ok = false;
+    const float ip = pv != 0.f ? 1.f / pv : 0.f;
+    if (tid == 0) piv[k] = pr;
+    for (int j = tid; j < N; j += NTHREADS) {  // swap rows k and pr, scale the pivot row
+      const float vk = G[k * LD + j], vp = G[pr * LD + j];
+      if (pr != k) G[pr * LD + j] = vk;
+      G[k * LD + j] = (j == k) ? ip : vp * ip;
+    }
+    __syncthreads();
+    float pk[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) pk[q] = (lane + 32 * q < N) ? G[k * LD + lane + 32 * q] : 0.f;
+    const int kn = k + 1, qn = kn >> 5, ln = kn & 31;
+    float bv = 0.f;
+    int br = -1;
+    for (int r = warp; r < N; r += NWARP) {
+      if (r == k) continue;
+      const float f = G[r * LD + k];
+      __syncwarp();
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {
+        const int j = lane + 32 * q;
+        if (j < N) {
+          const float nv = (j == k) ? -f * ip : fmaf(-f, pk[q], G[r * LD + j]);
+          G[r * LD + j] = nv;
+          if (q == qn && lane == ln && r > k && (br < 0 || fabsf(nv) > fabsf(bv))) {
+            bv = nv;
+            br = r;
+          }
+        }
+      }
+    }
+    __syncwarp();
+    if (lane == ln) {
+      cval[warp] = bv;
+      crow[warp] = br;
+    }
+    __syncthreads();
+  }
+  return ok;
+}
+
+// Column of G holding the inverse's column j after gj_inverse_smem.
+template <int N>
+HDG_DEVI int gj_column(const int* piv, int j) {
+  int x = j;
+  for (int k = 0; k < N; ++k) {
+    const int p = piv[k];
+    x = (x == k) ? p : (x == p ? k : x);
+  }
+  return x;
+}
+
 // Exact-slice product of MT row tiles of a sliced left operand (global, fragment-native)
 // with the sliced block Xs (shared memory), nnt column tiles; each warp owns one row tile
-// and up to two column tiles at a time. epi(row, col, value_without_scales) per element.
-template <int KT, int NTB, int OZS, int NWARP, class Epi>
+// and NJ column tiles at a time, with the next k tile's fragments loaded ahead.
+// epi(row, col, value_without_scales) per element.
+template <int KT, int NTB, int OZS, int NWARP, int NJ, class Epi>
 HDG_DEVI void cond_oz_product(const uint4* __restrict__ Lsl, int MT, const uint2* Xs, int nnt, Epi epi) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int NH = (nnt + 1) >> 1;
+  const int NH = (nnt + NJ - 1) / NJ;
   for (int task = warp; task < MT * NH; task += NWARP) {
-    const int mt = task / NH, nt0 = 2 * (task % NH);
-    const bool two = nt0 + 1 < nnt;
-    float acc[2][OZS][4];
+    const int mt = task / NH, nt0 = NJ * (task % NH);
+    float acc[NJ][OZS][4];
 #pragma unroll
-    for (int j = 0; j < 2; ++j)
+    for (int j = 0; j < NJ; ++j)
 #pragma unroll
       for (int d = 0; d < OZS; ++d)
 #pragma unroll
         for (int q = 0; q < 4; ++q) acc[j][d][q] = 0.f;
     const uint4* Lt = Lsl + (size_t)mt * KT * OZS * 32 + lane;
+    uint4 a[OZS], an[OZS];
+#pragma unroll
+    for (int s = 0; s < OZS; ++s) a[s] = Lt[s * 32];
 #pragma unroll 1
     for (int kt = 0; kt < KT; ++kt) {
-      uint4 a[OZS];
+      if (kt + 1 < KT)  // next tile's fragments in flight during this tile's products
 #pragma unroll
-      for (int s = 0; s < OZS; ++s) a[s] = Lt[(kt * OZS + s) * 32];
-      {
-        uint2 b[OZS];
+        for (int s = 0; s < OZS; ++s) an[s] = Lt[((kt + 1) * OZS + s) * 32];
 #pragma unroll
-        for (int s = 0; s < OZS; ++s) b[s] = Xs[((kt * NTB + nt0) * OZS + s) * 32 + lane];
-        oz_mma_tile<OZS>(acc[0], a, b);
-      }
-      if (two) {
-        uint2 b[OZS];
+      for (int j = 0; j < NJ; ++j)
+        if (nt0 + j < nnt) {
+          uint2 b[OZS];
 #pragma unroll
-        for (int s = 0; s < OZS; ++s) b[s] = Xs[((kt * NTB + nt0 + 1) * OZS + s) * 32 + lane];
-        oz_mma_tile<OZS>(acc[1], a, b);
-      }
+          for (int s = 0; s < OZS; ++s) b[s] = Xs[((kt * NTB + nt0 + j) * OZS + s) * 32 + lane];
+          oz_mma_tile<OZS>(acc[j], a, b);
+        }
+#pragma unroll
+      for (int s = 0; s < OZS; ++s) a[s] = an[s];
     }
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      if (j == 1 && !two) break;
+    for (int j = 0; j < NJ; ++j) {
+      if (nt0 + j >= nnt) break;
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int row = mt * 16 + (lane >> 2) + 8 * (q >> 1);
@@ -116,59 +230,40 @@ HDG_DEVI df2 df_scaled(const dfacc& v, int e) {
   return {n.hi * p, n.lo * p};
 }
 
-template <class C, int NTHREADS, int OZS>
-__global__ void __launch_bounds__(NTHREADS) k_condense_tc(AssembleArgs a) {
-  using Q = CondTC<C, NTHREADS, OZS>;
-  constexpr int NV = C::NV, NT = C::NT, KT = Q::KT, MTA = Q::MTA, MTC = Q::MTC, CB = Q::CB, NTB = Q::NTB;
-  constexpr int RT = Q::RT, CT = Q::CT, NWARP = NTHREADS / 32;
+template <class C, int OZS>
+__global__ void __launch_bounds__(CondTC<C, 256, OZS>::PTH) k_condense_prep(AssembleArgs a) {
+  using Q = CondTC<C, 256, OZS>;
+  constexpr int NV = C::NV, NT = C::NT, KT = Q::KT, MTA = Q::MTA, MTC = Q::MTC, LDA = Q::LDA;
+  constexpr int PTH = Q::PTH, NWARP = PTH / 32;
   extern __shared__ double smem_d[];
-  df2* Xb = reinterpret_cast<df2*>(smem_d);                 // [NV][CB] current X block
-  uint2* Xs = reinterpret_cast<uint2*>(Xb + NV * CB);       // [KT][NTB][OZS][32] X slices
-  float* Rk = reinterpret_cast<float*>(Xs);                 // [NV][CB] residual (aliases Xs)
-  float* Dk = Rk + NV * CB;                                 // [NV][CB] correction (aliases Xs)
-  float* Ai = reinterpret_cast<float*>(reinterpret_cast<char*>(Xs) + Q::xs_bytes);  // [NV][NV]
-  float* Ah = Ai + NV * NV;                                 // [NV][NV] A' (FP32)
-  float* W = Ah + NV * NV;                                  // [NV][CB]
-  float* sc = W + NV * CB;                                  // [NV]
-  int* piv = reinterpret_cast<int*>(sc + NV);               // [NV]
-  int* eA = piv + NV;                                       // [MTA*16] row exponents of A'
-  int* eC = eA + MTA * 16;                                  // [MTC*16] row exponents of C'
-  int* eX = eC + MTC * 16;                                  // [CB] column exponents of the X block
-  __shared__ int s_piv, s_bad;
-  __shared__ float s_corr[2], s_xmax;
+  float* G = reinterpret_cast<float*>(smem_d);  // [NV][LDA] A'^T, then (sc A' sc)^-T (permuted)
+  float* sc = G + NV * LDA;                     // [NV]
+  int* piv = reinterpret_cast<int*>(sc + NV);   // [NV]
+  int* sig = piv + NV;                          // [NV]
+  float* cval = reinterpret_cast<float*>(sig + NV);
+  int* crow = reinterpret_cast<int*>(cval + NWARP);
   const int64_t le = blockIdx.x;
   const int64_t e = a.e0 + le;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const df2* Ap = reinterpret_cast<const df2*>(a.Ap) + le * NV * NV;
   const df2* Cp = reinterpret_cast<const df2*>(a.Cp) + le * NT * NV;
+  float* pre = a.prep + le * Q::prep_floats;
+  int* eA = reinterpret_cast<int*>(pre + Q::PREP_EA);
+  int* eC = reinterpret_cast<int*>(pre + Q::PREP_EC);
   uint4* slA = a.oz + le * Q::slice_uint4;
-  uint4* slC = slA + (size_t)MTA * KT * OZS * 32;
-  double* Xg = a.recov + e * (int64_t)(NV * NT + NV);  // B' (double-float) in, X out
-  const df2* Bd = reinterpret_cast<const df2*>(Xg);
-  double* yg = Xg + NV * NT;
-  double* S = a.S + e * (int64_t)NT * NT;  // D' (double-float) in, S out
-  const df2* Dd = reinterpret_cast<const df2*>(S);
-  const double* R = a.R + e * (int64_t)(NV + NT);
 
-  // ---- equilibration, FP32 copies of A', row exponents
-  for (int r = tid; r < NV; r += NTHREADS) {
-    const float d = fabsf(Ap[r * NV + r].hi);
-    sc[r] = d > 0.f ? rsqrtf(d) : 1.f;
-  }
-  if (tid == 0) s_bad = 0;
-  __syncthreads();
-  for (int r = warp; r < MTA * 16; r += NWARP) {
+  // A'^T (FP32) in shared memory, row exponents of A' and C'
+  for (int r = warp; r < LDA; r += NWARP) {
     float mx = 0.f;
-    if (r < NV)
-      for (int k = lane; k < NV; k += 32) {
-        const float v = Ap[r * NV + k].hi;
-        Ah[r * NV + k] = v;
-        Ai[r * NV + k] = v * sc[r] * sc[k];
-        mx = fmaxf(mx, fabsf(v));
-      }
+    for (int k = lane; k < NV; k += 32) {
+      const float v = r < NV ? Ap[r * NV + k].hi : 0.f;
+      G[k * LDA + r] = v;
+      mx = fmaxf(mx, fabsf(v));
+    }
     for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-    if (lane == 0) eA[r] = oz_exponent(mx);
+    if (lane == 0 && r < NV) eA[r] = oz_exponent(mx);
   }
+  for (int r = NV + tid; r < MTA * 16; r += PTH) eA[r] = 0;
   for (int r = warp; r < MTC * 16; r += NWARP) {
     float mx = 0.f;
     if (r < NT)
@@ -177,7 +272,28 @@ __global__ void __launch_bounds__(NTHREADS) k_condense_tc(AssembleArgs a) {
     if (lane == 0) eC[r] = oz_exponent(mx);
   }
   __syncthreads();
-  // ---- slices of A' and C' (one warp per 16 x 16 tile)
+  // A'^T out; equilibration sc = |diag A'|^-1/2 and the scaled transpose for the inverse
+  {
+    const float4* src = reinterpret_cast<const float4*>(G);
+    float4* dst = reinterpret_cast<float4*>(pre + Q::PREP_AH);
+    for (int t = tid; t < NV * LDA / 4; t += PTH) dst[t] = src[t];
+  }
+  for (int r = tid; r < LDA; r += PTH) {
+    float v = 1.f;
+    if (r < NV) {
+      const float d = fabsf(G[r * LDA + r]);
+      v = d > 0.f ? rsqrtf(d) : 1.f;
+      sc[r] = v;
+    }
+    pre[Q::PREP_SC + r] = v;
+  }
+  __syncthreads();
+  for (int t = tid; t < NV * LDA; t += PTH) {
+    const int k = t / LDA, r = t % LDA;
+    G[t] = r < NV ? G[t] * sc[r] * sc[k] : 0.f;
+  }
+  __syncthreads();
+  // slices of A' and C' (one warp per 16 x 16 tile)
   {
     auto getA = [&](int r, int k) { return (r < NV && k < NV) ? Ap[r * NV + k] : df2{0.f, 0.f}; };
     auto getC = [&](int r, int k) { return (r < NT && k < NV) ? Cp[r * NV + k] : df2{0.f, 0.f}; };
@@ -191,63 +307,63 @@ __global__ void __launch_bounds__(NTHREADS) k_condense_tc(AssembleArgs a) {
         oz_slice_left_tile<OZS>(slA + (size_t)u * OZS * 32, 32, (mt - MTA) * 16, kt * 16, lane, getC, sC);
     }
   }
-  // ---- Gauss-Jordan inversion of sc A' sc in place with row pivoting
-  for (int k = 0; k < NV; ++k) {
-    if (tid < 32) {
-      float best = -1.f;
-      int bi = k;
-      for (int r = k + tid; r < NV; r += 32) {
-        const float v = fabsf(Ai[r * NV + k]);
-        if (v > best) {
-          best = v;
-          bi = r;
-        }
-      }
-      for (int off = 16; off > 0; off >>= 1) {
-        const float ob = __shfl_down_sync(0xffffffffu, best, off);
-        const int oi = __shfl_down_sync(0xffffffffu, bi, off);
-        if (ob > best || (ob == best && oi < bi)) {
-          best = ob;
-          bi = oi;
-        }
-      }
-      if (tid == 0) {
-        s_piv = bi;
-        piv[k] = bi;
-        if (!(best > 0.f)) s_bad |= HDG_STATUS_SINGULAR;
-      }
-    }
-    __syncthreads();
-    const int pr = s_piv;
-    const float pivv = Ai[pr * NV + k];
-    const float ip = pivv != 0.f ? 1.f / pivv : 0.f;
-    __syncthreads();
-    for (int j = tid; j < NV; j += NTHREADS) {
-      const float vk = Ai[k * NV + j], vp = Ai[pr * NV + j];
-      if (pr != k) Ai[pr * NV + j] = vk;
-      Ai[k * NV + j] = (j == k) ? ip : vp * ip;
-    }
-    __syncthreads();
-    for (int r = tid; r < NV; r += NTHREADS) W[r] = Ai[r * NV + k];  // multipliers
-    __syncthreads();
-    for (int t = tid; t < NV * NV; t += NTHREADS) {
-      const int r = t / NV, j = t % NV;
-      if (r == k) continue;
-      const float f = W[r];
-      Ai[t] = (j == k) ? -f * ip : fmaf(-f, Ai[k * NV + j], Ai[t]);
-    }
-    __syncthreads();
+  // inverse of the transposed equilibrated matrix, written out with its columns in place
+  const bool ok = gj_inverse_smem<NV, LDA, PTH>(G, piv, cval, crow);
+  for (int j = tid; j < NV; j += PTH) sig[j] = gj_column<NV>(piv, j);
+  __syncthreads();
+  float* ai = pre + Q::PREP_AI;
+  for (int t = tid; t < NV * LDA; t += PTH) {
+    const int k = t / LDA, r = t % LDA;
+    ai[t] = r < NV ? G[k * LDA + sig[r]] : 0.f;
   }
-  for (int k = NV - 1; k >= 0; --k) {  // row interchanges become column interchanges
-    const int p = piv[k];
-    if (p != k)
-      for (int r = tid; r < NV; r += NTHREADS) {
-        const float t = Ai[r * NV + k];
-        Ai[r * NV + k] = Ai[r * NV + p];
-        Ai[r * NV + p] = t;
-      }
-    __syncthreads();
+  if (tid == 0 && !ok) atomicOr(a.status + e, HDG_STATUS_SINGULAR);
+}
+
+template <class C, int NTHREADS, int OZS>
+__global__ void __launch_bounds__(NTHREADS) k_condense_tc(AssembleArgs a) {
+  using Q = CondTC<C, NTHREADS, OZS>;
+  constexpr int NV = C::NV, NT = C::NT, KT = Q::KT, MTA = Q::MTA, MTC = Q::MTC, CB = Q::CB, NTB = Q::NTB;
+  constexpr int RT = Q::RT, CT = Q::CT, LDA = Q::LDA, NWARP = NTHREADS / 32;
+  constexpr int NJ = NTHREADS >= 512 ? 1 : 2;  // column tiles per warp task (register budget)
+  extern __shared__ double smem_d[];
+  df2* Xb = reinterpret_cast<df2*>(smem_d);                 // [NV][CB] current X block
+  uint2* Xs = reinterpret_cast<uint2*>(Xb + NV * CB);       // [KT][NTB][OZS][32] X slices
+  float* Rk = reinterpret_cast<float*>(Xs);                 // [NV][CB] residual (aliases Xs)
+  float* Dk = Rk + NV * CB;                                 // [NV][CB] correction (aliases Xs)
+  // FP32 matrices stored transposed ([k][r], leading dimension LDA, zero past NV)
+  float* Ai = reinterpret_cast<float*>(reinterpret_cast<char*>(Xs) + Q::xs_bytes);  // (sc A' sc)^-T
+  float* Ah = Ai + NV * LDA;                                // A'^T (FP32)
+  float* W = Ah + NV * LDA;                                 // [NV][CB]
+  float* sc = W + NV * CB;                                  // [NV]
+  int* eA = reinterpret_cast<int*>(sc + NV);                // [MTA*16] row exponents of A'
+  int* eC = eA + MTA * 16;                                  // [MTC*16] row exponents of C'
+  int* eX = eC + MTC * 16;                                  // [CB] column exponents of the X block
+  __shared__ int s_bad;
+  __shared__ float s_corr[2], s_xmax;
+  const int64_t le = blockIdx.x;
+  const int64_t e = a.e0 + le;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint4* slA = a.oz + le * Q::slice_uint4;
+  const uint4* slC = slA + (size_t)MTA * KT * OZS * 32;
+  double* Xg = a.recov + e * (int64_t)(NV * NT + NV);  // B' (double-float) in, X out
+  const df2* Bd = reinterpret_cast<const df2*>(Xg);
+  double* yg = Xg + NV * NT;
+  double* S = a.S + e * (int64_t)NT * NT;  // D' (double-float) in, S out
+  const df2* Dd = reinterpret_cast<const df2*>(S);
+  const double* R = a.R + e * (int64_t)(NV + NT);
+
+  // ---- the element's prepared operands: Ai^T, A'^T, sc, row exponents
+  {
+    const float* pre = a.prep + le * Q::prep_floats;
+    const float4* src = reinterpret_cast<const float4*>(pre);
+    float4* dst = reinterpret_cast<float4*>(Ai);  // Ai and Ah are contiguous, as in the block
+    for (int t = tid; t < 2 * NV * LDA / 4; t += NTHREADS) dst[t] = src[t];
+    for (int r = tid; r < NV; r += NTHREADS) sc[r] = pre[Q::PREP_SC + r];
+    const int* ex = reinterpret_cast<const int*>(pre + Q::PREP_EA);
+    for (int r = tid; r < (MTA + MTC) * 16; r += NTHREADS) eA[r] = ex[r];  // eC follows eA
   }
+  if (tid == 0) s_bad = 0;
+  __syncthreads();
 
   auto col_exponents = [&]() {  // eX[c] from the current X block
     for (int c = warp; c < CB; c += NWARP) {
@@ -283,7 +399,7 @@ __global__ void __launch_bounds__(NTHREADS) k_condense_tc(AssembleArgs a) {
     if (tid == 0) s_xmax = 0.f;
     __syncthreads();
     // X0 = sc Ai W
-    cond_gemm_f32<NV, CB, RT, CT, NTHREADS>(Ai, W, [&](int r0, int cc0, float(&acc)[RT][CT]) {
+    cond_gemm_f32<NV, LDA, CB, RT, CT, NTHREADS>(Ai, W, [&](int r0, int cc0, float(&acc)[RT][CT]) {
 #pragma unroll
       for (int i = 0; i < RT; ++i)
         if (r0 + i < NV)
@@ -296,7 +412,7 @@ __global__ void __launch_bounds__(NTHREADS) k_condense_tc(AssembleArgs a) {
     slice_X(nnt);
     __syncthreads();
     // r0 = B - A' X0 (exact slices), staged in W (the products read Xs, which Rk aliases)
-    cond_oz_product<KT, NTB, OZS, NWARP>(slA, MTA, Xs, nnt, [&](int row, int col, const dfacc& v) {
+    cond_oz_product<KT, NTB, OZS, NWARP, NJ>(slA, MTA, Xs, nnt, [&](int row, int col, const dfacc& v) {
       if (row < NV) {
         const df2 p = df_scaled(v, eA[row] + eX[col]);
         dfacc t;
@@ -314,7 +430,7 @@ __global__ void __launch_bounds__(NTHREADS) k_condense_tc(AssembleArgs a) {
     __syncthreads();
     // two corrections: d_it = sc Ai W; X += d_it; between them r1 = r0 - A' d0 (FP32)
     for (int it = 0; it < 2; ++it) {
-      cond_gemm_f32<NV, CB, RT, CT, NTHREADS>(Ai, W, [&](int r0, int cc0, float(&acc)[RT][CT]) {
+      cond_gemm_f32<NV, LDA, CB, RT, CT, NTHREADS>(Ai, W, [&](int r0, int cc0, float(&acc)[RT][CT]) {
         float cmax = 0.f, xmax = 0.f;
 #pragma unroll
         for (int i = 0; i < RT; ++i)
@@ -337,7 +453,7 @@ __global__ void __launch_bounds__(NTHREADS) k_condense_tc(AssembleArgs a) {
       });
       __syncthreads();
       if (it == 1) break;
-      cond_gemm_f32<NV, CB, RT, CT, NTHREADS>(Ah, Dk, [&](int r0, int cc0, float(&acc)[RT][CT]) {
+      cond_gemm_f32<NV, LDA, CB, RT, CT, NTHREADS>(Ah, Dk, [&](int r0, int cc0, float(&acc)[RT][CT]) {
 #pragma unroll
         for (int i = 0; i < RT; ++i)
           if (r0 + i < NV)
@@ -373,7 +489,7 @@ __global__ void __launch_bounds__(NTHREADS) k_condense_tc(AssembleArgs a) {
     slice_X(nnt);
     __syncthreads();
     // S[:, block] = D' - C' X ; g = R_t - C' y
-    cond_oz_product<KT, NTB, OZS, NWARP>(slC, MTC, Xs, nnt, [&](int row, int col, const dfacc& v) {
+    cond_oz_product<KT, NTB, OZS, NWARP, NJ>(slC, MTC, Xs, nnt, [&](int row, int col, const dfacc& v) {
       const int gc = c0 + col;
       if (row >= NT || col >= nc) return;
       const df2 p = df_scaled(v, eC[row] + eX[col]);

@@ -46,7 +46,8 @@ HDG_KERNEL_MIXED_ASSEMBLE = 3
 HDG_KERNEL_MIXED_CONDENSE = 4
 HDG_KERNEL_TRACE = 5
 HDG_KERNEL_OTHER = 6
-HDG_KERNEL_CLASSES = 7
+HDG_KERNEL_MIXED_PREP = 7
+HDG_KERNEL_CLASSES = 8
 
 
 class HdgError(RuntimeError):
