@@ -1,0 +1,609 @@
+// Mixed-precision assembly on the bf16 tensor cores (exact slices, ozaki.cuh).
+//
+// The Jacobian blocks of Eqs. hDG_NS1-2 (after the exact elimination of q) are quadrature
+// contractions. Written as products (rows il = (i, l) pairs of state components, an / c the
+// test node, j the nodal column of the trial unknowns, beta the operator):
+//   volume:  A'|B' [(an,i)][(j,l)] += sum_{beta,g} Z_il[an][beta,g] Rb[beta,g][j]
+//            Z_il[an][0,g]   = Phi[g][an] T0[g][il] + sum_r dPhi_r[g][an] T1[g][r][il]
+//            Z_il[an][1+k,g] = sum_r dPhi_r[g][an] T2[g][r][il][k]
+//   face f:  F_f[(c,i)][(j,l)] = sum_{beta,gf} PhiF_f[gf][c] U[gf][beta][il] RbF_f[beta,gf][j]
+//            C'|D' rows (f,c,i) = F_f;  A'|B' rows (fnode(f,c), i) += F_f
+// T0, T1, T2, U are the pointwise flux Jacobians (double-float, k_pointwise); Rb, RbF are
+// the element's value / lifted-gradient operators at the quadrature points (geometry x
+// reference tables). Every product runs as exact bf16 slices: S slices per operand with a
+// power-of-two scale per row (an FP32 bound of the row's largest entry) and per column,
+// S(S+1)/2 mma.sync per tile, each slice diagonal accumulated exactly in FP32 over at most
+// 128 k entries, combined in double-float.
+//
+// Kernels (per element chunk):
+//   k_asm_rb      the operator slices Rb, RbF (fragment-native) and column exponents
+//   k_asm_vol_tc  grid (element x row block): 16 MTC rows of (il, an) x all columns
+//   k_asm_face_tc grid (element x il group): the faces, after the volume
+//   k_asm_residual R_v, R_t in FP64 from the double-float point data
+#pragma once
+#include "assemble_mixed.cuh"
+#include "ozaki.cuh"
+
+namespace hdg {
+
+template <class C, int S, int MTC>
+struct AsmTC {
+  static constexpr int D = C::D, M = C::M, NP = C::NP, NFN = C::NFN, NF = C::NF, NG = C::NG, NGF = C::NGF;
+  static constexpr int NZ = C::NZ, NV = C::NV, NT = C::NT, NR = C::NR, NRF = C::NRF;
+  static constexpr int NTN = (NZ + 7) / 8;    // n tiles over the nodal columns
+  static constexpr int NGRP = (NTN + 3) / 4;  // groups of up to 4 n tiles (one warp each)
+  static constexpr int KTB = (NG + 15) / 16, KTV = NR * KTB;     // volume k tiles (beta-major)
+  static constexpr int KTBF = (NGF + 15) / 16, KTF = NRF * KTBF;  // face k tiles
+  static constexpr int KFLUSH = 8;            // k tiles per exact accumulation (128 entries)
+  static constexpr int ROWS = 16 * MTC;       // product rows per CTA
+  static constexpr int RV = M * M * NP;       // volume rows (il, an)
+  static constexpr int NPASS = (RV + ROWS - 1) / ROWS;
+  static constexpr int QIL = ROWS / NFN;      // il pairs per face CTA (whole pairs: no races)
+  static constexpr int NFCTA = (M * M + QIL - 1) / QIL;
+  static constexpr int NTH = 32 * MTC * NGRP;
+  static constexpr int NILV = (ROWS + NP - 1) / NP + 1;  // il pairs one volume CTA touches
+  static constexpr int NTS = 1 + D + (C::VISC ? D * D : 0);
+  static_assert(QIL >= 1 && KTF <= KFLUSH, "face block");
+  // operator slices per element (uint2 units): volume [KTV][NTN][S][32], faces [NF][KTF][NTN][S][32],
+  // then the column exponents (int): volume [NTN*8], faces [NF][NTN*8]
+  static constexpr size_t vol_u2 = (size_t)KTV * NTN * S * 32;
+  static constexpr size_t face_u2 = (size_t)KTF * NTN * S * 32;
+  static constexpr int NEXP = NTN * 8 * (1 + NF);
+  static constexpr size_t rb_u2 = (vol_u2 + NF * face_u2 + (NEXP + 1) / 2 + 31) / 32 * 32;
+  static constexpr size_t stripe_u2 = (size_t)NTN * S * 32;  // one k tile of operator slices
+  // shared memory of the product kernels
+  static constexpr size_t zs_u4 = (size_t)MTC * S * 32;       // one k tile of Z slices
+  static constexpr int NPSI = (1 + D) * NG * NP;  // Phi and dPhi of all volume points
+  static constexpr size_t vol_bytes = sizeof(uint4) * 2 * zs_u4 + sizeof(uint2) * 2 * stripe_u2 +
+                                      sizeof(df2) * (NG * NILV * NTS + NPSI) + sizeof(int) * (ROWS + NTN * 8) + 64;
+  static constexpr size_t face_bytes = sizeof(uint4) * 2 * zs_u4 + sizeof(uint2) * 2 * stripe_u2 +
+                                       sizeof(df2) * (NGF * QIL * NRF + NGF * NFN) + sizeof(int) * (ROWS + NTN * 8) + 64;
+};
+
+// Geometry as double-floats: Jinv [D][D] and n_f s_f / |J| [NF][D].
+template <class C>
+HDG_DEVI void load_geo_df(const AssembleArgs& a, int64_t e, df2* JiD, df2* NsD) {
+  constexpr int D = C::D, NF = C::NF;
+  const double* G = a.geo + e * C::GEO;
+  const double detJ = G[D * D];
+  for (int t = threadIdx.x; t < D * D; t += blockDim.x) JiD[t] = df_from(G[t]);
+  for (int t = threadIdx.x; t < NF * D; t += blockDim.x) {
+    const int f = t / D, k = t % D;
+    const double* Gf = G + D * D + 1 + f * (D + 1);
+    NsD[t] = df_from(Gf[k] * (Gf[D] / detJ));
+  }
+}
+
+// Volume operator Rb[beta,g][j]: value (double-float) or an FP32 bound of |value|.
+template <class C, bool BOUND>
+HDG_DEVI auto rb_vol(int beta, int g, int j, const DevTables& T, const DevTablesDF& TD, const df2* JiD,
+                     const df2* NsD) {
+  constexpr int D = C::D, NP = C::NP, NG = C::NG, NFN = C::NFN, NF = C::NF;
+  dfacc acc;
+  float bnd = 0.f;
+  auto term = [&](df2 x, df2 y, bool neg) {
+    if constexpr (BOUND) {
+      bnd = fmaf(fabsf(x.hi), fabsf(y.hi), bnd);
+    } else {
+      if (neg) x = df2{-x.hi, -x.lo};
+      acc.mac(x, y);
+    }
+  };
+  if (g < NG && j < C::NZ) {
+    if (beta == 0) {
+      if (j < NP) term(TD.Phi[g * NP + j], df2{1.f, 0.f}, false);
+    } else {
+      const int k = beta - 1;
+      if (j < NP) {
+        for (int r = 0; r < D; ++r) term(JiD[r * D + k], TD.dPhi[(r * NG + g) * NP + j], false);
+        for (int f = 0; f < NF; ++f) {
+          const int c = T.nodepos[f * NP + j];
+          if (c >= 0) term(NsD[f * D + k], TD.PL[(f * NG + g) * NFN + c], true);
+        }
+      } else {
+        const int f = (j - NP) / NFN, c = (j - NP) % NFN;
+        term(NsD[f * D + k], TD.PL[(f * NG + g) * NFN + c], false);
+      }
+    }
+  }
+  if constexpr (BOUND)
+    return bnd;
+  else
+    return acc.norm();
+}
+
+// Face operator RbF_f[beta,gf][j].
+template <class C, bool BOUND>
+HDG_DEVI auto rb_face(int f, int beta, int gf, int j, const DevTables& T, const DevTablesDF& TD, const df2* JiD,
+                      const df2* NsD) {
+  constexpr int D = C::D, NP = C::NP, NGF = C::NGF, NFN = C::NFN, NF = C::NF;
+  dfacc acc;
+  float bnd = 0.f;
+  auto term = [&](df2 x, df2 y, bool neg) {
+    if constexpr (BOUND) {
+      bnd = fmaf(fabsf(x.hi), fabsf(y.hi), bnd);
+    } else {
+      if (neg) x = df2{-x.hi, -x.lo};
+      acc.mac(x, y);
+    }
+  };
+  if (gf < NGF && j < C::NZ) {
+    const df2* phif = TD.PhiF + (f * NGF + gf) * NP;
+    if (beta == 0) {
+      if (j < NP) term(phif[j], df2{1.f, 0.f}, false);
+    } else if (beta == 1) {
+      if (j >= NP && (j - NP) / NFN == f) term(phif[T.fnodes[f * NFN + (j - NP) % NFN]], df2{1.f, 0.f}, false);
+    } else {
+      const int k = beta - 2;
+      if (j < NP) {
+        for (int r = 0; r < D; ++r) term(JiD[r * D + k], TD.dPhiF[((f * D + r) * NGF + gf) * NP + j], false);
+        for (int fl = 0; fl < NF; ++fl) {
+          const int c = T.nodepos[fl * NP + j];
+          if (c >= 0) term(NsD[fl * D + k], TD.PLF[((f * NF + fl) * NGF + gf) * NFN + c], true);
+        }
+      } else {
+        const int fl = (j - NP) / NFN, c = (j - NP) % NFN;
+        term(NsD[fl * D + k], TD.PLF[((f * NF + fl) * NGF + gf) * NFN + c], false);
+      }
+    }
+  }
+  if constexpr (BOUND)
+    return bnd;
+  else
+    return acc.norm();
+}
+
+// ------------------------------------------------------------------------------------
+// k_asm_rb: operator slices and column exponents of one element
+// ------------------------------------------------------------------------------------
+template <class C, int S, int MTC>
+__global__ void __launch_bounds__(256) k_asm_rb(AssembleArgs a, DevTables T, DevTablesDF TD) {
+  using Q = AsmTC<C, S, MTC>;
+  constexpr int D = C::D, NF = C::NF, NTN = Q::NTN, KTV = Q::KTV, KTF = Q::KTF, KTB = Q::KTB, KTBF = Q::KTBF;
+  constexpr int NC = NTN * 8;
+  __shared__ df2 JiD[D * D], NsD[NF * D];
+  __shared__ int ex[Q::NEXP];
+  __shared__ float bmax[Q::NEXP];
+  const int64_t le = blockIdx.x;
+  const int64_t e = a.e0 + le;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  load_geo_df<C>(a, e, JiD, NsD);
+  for (int t = tid; t < Q::NEXP; t += blockDim.x) bmax[t] = 0.f;
+  __syncthreads();
+  // column bounds: volume (over beta, g) and per face (over beta, gf)
+  for (int t = tid; t < NC * KTV * 16; t += blockDim.x) {
+    const int j = t % NC, kk = t / NC, beta = kk / (KTB * 16), g = kk % (KTB * 16);
+    const float b = rb_vol<C, true>(beta, g, j, T, TD, JiD, NsD);
+    if (b > 0.f) atomicMax(reinterpret_cast<int*>(&bmax[j]), __float_as_int(b));
+  }
+  for (int t = tid; t < NF * NC * KTF * 16; t += blockDim.x) {
+    const int j = t % NC, kk = (t / NC) % (KTF * 16), f = t / (NC * KTF * 16);
+    const int beta = kk / (KTBF * 16), gf = kk % (KTBF * 16);
+    const float b = rb_face<C, true>(f, beta, gf, j, T, TD, JiD, NsD);
+    if (b > 0.f) atomicMax(reinterpret_cast<int*>(&bmax[NC * (1 + f) + j]), __float_as_int(b));
+  }
+  __syncthreads();
+  uint2* out = reinterpret_cast<uint2*>(a.rb) + le * Q::rb_u2;
+  int* exg = reinterpret_cast<int*>(out + Q::vol_u2 + NF * Q::face_u2);
+  for (int t = tid; t < Q::NEXP; t += blockDim.x) {
+    ex[t] = oz_exponent(bmax[t] * 1.0001f);  // margin for the bound's own rounding
+    exg[t] = ex[t];
+  }
+  __syncthreads();
+  // slices, one warp per 16 x 8 tile
+  for (int u = warp; u < KTV * NTN; u += nw) {
+    const int kt = u / NTN, nt = u % NTN;
+    auto get = [&](int K, int j) { return rb_vol<C, false>(K / (KTB * 16), K % (KTB * 16), j, T, TD, JiD, NsD); };
+    auto sc = [&](int j) { return oz_scale(ex[j]); };
+    oz_slice_right_tile<S>(out + (size_t)u * S * 32, 32, kt * 16, nt * 8, lane, get, sc);
+  }
+  for (int u = warp; u < NF * KTF * NTN; u += nw) {
+    const int f = u / (KTF * NTN), kt = (u / NTN) % KTF, nt = u % NTN;
+    auto get = [&](int kk, int j) { return rb_face<C, false>(f, kk / (KTBF * 16), kk % (KTBF * 16), j, T, TD, JiD, NsD); };
+    auto sc = [&](int j) { return oz_scale(ex[NC * (1 + f) + j]); };
+    oz_slice_right_tile<S>(out + Q::vol_u2 + (size_t)u * S * 32, 32, kt * 16, nt * 8, lane, get, sc);
+  }
+}
+
+// Shared pieces of the two product kernels.
+template <int S>
+HDG_DEVI void put_left_half(uint4* zs, int s_stride, int lane, int h, const float (&v)[4][S]) {
+  // v: (row a, k0), (row a, k0+1), (row b, k0), (row b, k0+1) of the lane's half h
+  uint2* z2 = reinterpret_cast<uint2*>(zs);
+#pragma unroll
+  for (int s = 0; s < S; ++s) z2[(s * s_stride + lane) * 2 + h] = make_uint2(oz_pack2(v[0][s], v[1][s]), oz_pack2(v[2][s], v[3][s]));
+}
+
+// One warp's products for one k tile: m tile mt, n tiles [nt0, nt0 + 4), tiles whose
+// operator block is zero skipped (live(nt) false).
+template <int S, int NTN, class Live>
+HDG_DEVI void tile_products(float (&acc)[4][S][4], const uint4* zs, const uint2* rbs, int mt, int nt0, int lane,
+                            Live live) {
+  uint4 a[S];
+#pragma unroll
+  for (int s = 0; s < S; ++s) a[s] = zs[(mt * S + s) * 32 + lane];
+#pragma unroll
+  for (int jj = 0; jj < 4; ++jj) {
+    const int nt = nt0 + jj;
+    if (nt >= NTN || !live(nt)) continue;
+    uint2 b[S];
+#pragma unroll
+    for (int s = 0; s < S; ++s) b[s] = rbs[(nt * S + s) * 32 + lane];
+    oz_mma_tile<S>(acc[jj], a, b);
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// k_asm_vol_tc: rows [ROWS*blockIdx.y, +ROWS) of (il, an), all nodal columns
+// ------------------------------------------------------------------------------------
+template <class C, int S, int MTC>
+__global__ void __launch_bounds__(AsmTC<C, S, MTC>::NTH) k_asm_vol_tc(AssembleArgs a, DevTablesDF TD) {
+  using Q = AsmTC<C, S, MTC>;
+  constexpr int D = C::D, M = C::M, NP = C::NP, NG = C::NG, NV = C::NV, NT = C::NT;
+  constexpr int NTN = Q::NTN, NGRP = Q::NGRP, KTB = Q::KTB, KTV = Q::KTV, ROWS = Q::ROWS, NILV = Q::NILV,
+                NTS = Q::NTS, NTH = Q::NTH, NC = NTN * 8;
+  extern __shared__ double smem_d[];
+  uint4* Zs = reinterpret_cast<uint4*>(smem_d);                       // [2][MTC][S][32]
+  uint2* Rs = reinterpret_cast<uint2*>(Zs + 2 * Q::zs_u4);            // [2][NTN][S][32]
+  df2* Ts = reinterpret_cast<df2*>(Rs + 2 * Q::stripe_u2);            // [NG][NILV][NTS]
+  df2* Ps = Ts + NG * NILV * NTS;                                     // Phi [NG][NP], dPhi [D][NG][NP]
+  int* eR = reinterpret_cast<int*>(Ps + Q::NPSI);                     // [ROWS]
+  int* eC = eR + ROWS;                                                // [NC]
+  const int64_t le = blockIdx.y;  // the element's row blocks are neighbours in launch order
+  const int64_t e = a.e0 + le;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int row0 = blockIdx.x * ROWS;
+  const int il_lo = row0 / NP;
+  const df2* ptv = reinterpret_cast<const df2*>(a.ptv) + le * NG * C::PT_VOL;
+  const uint2* rbg = reinterpret_cast<const uint2*>(a.rb) + le * Q::rb_u2;
+  const int* exg = reinterpret_cast<const int*>(rbg + Q::vol_u2 + C::NF * Q::face_u2);
+
+  // stage T0, T1, T2 of the il pairs this block touches; row exponents from FP32 bounds
+  for (int t = tid; t < NG * NILV * NTS; t += NTH) {
+    const int q = t % NTS, ilr = (t / NTS) % NILV, g = t / (NTS * NILV);
+    const int il = il_lo + ilr;
+    df2 v{0.f, 0.f};
+    if (il < M * M) {
+      const int i = il / M, l = il % M;
+      const df2* P = ptv + g * C::PT_VOL + M + D * M;
+      if (q == 0)
+        v = P[i * M + l];
+      else if (q <= D)
+        v = P[M * M + ((q - 1) * M + i) * M + l];
+      else {
+        const int r = (q - 1 - D) / D, k = (q - 1 - D) % D;
+        v = P[M * M + D * M * M + ((r * M + i) * M + l) * D + k];
+      }
+    }
+    Ts[t] = v;
+  }
+  for (int t = tid; t < NG * NP; t += NTH) Ps[t] = TD.Phi[t];
+  for (int t = tid; t < D * NG * NP; t += NTH) Ps[NG * NP + t] = TD.dPhi[t];
+  for (int t = tid; t < ROWS; t += NTH) eR[t] = 0;
+  for (int t = tid; t < NC; t += NTH) eC[t] = exg[t];
+  __syncthreads();
+  const df2* Phi = Ps;
+  const df2* dPhi = Ps + NG * NP;
+  {
+    float* bR = reinterpret_cast<float*>(eR);  // bounds first, exponents after
+    for (int t = tid; t < ROWS * NG; t += NTH) {
+      const int rl = t % ROWS, g = t / ROWS, row = row0 + rl;
+      if (row >= Q::RV) continue;
+      const int an = row % NP, ilr = row / NP - il_lo;
+      const df2* Tp = Ts + (g * NILV + ilr) * NTS;
+      float b = fabsf(Phi[g * NP + an].hi) * fabsf(Tp[0].hi);
+      for (int r = 0; r < D; ++r) b = fmaf(fabsf(dPhi[(r * NG + g) * NP + an].hi), fabsf(Tp[1 + r].hi), b);
+      if constexpr (C::VISC)
+        for (int k = 0; k < D; ++k) {
+          float bk = 0.f;
+          for (int r = 0; r < D; ++r)
+            bk = fmaf(fabsf(dPhi[(r * NG + g) * NP + an].hi), fabsf(Tp[1 + D + r * D + k].hi), bk);
+          b = fmaxf(b, bk);
+        }
+      if (b > 0.f) atomicMax(reinterpret_cast<int*>(&bR[rl]), __float_as_int(b));
+    }
+    __syncthreads();
+    for (int t = tid; t < ROWS; t += NTH) eR[t] = oz_exponent(bR[t] * 1.0001f);
+    __syncthreads();
+  }
+
+  // Z slices of k tile kt into buffer b
+  auto produce = [&](int kt, int b) {
+    const int beta = kt / KTB, g0 = (kt % KTB) * 16;
+    for (int u = tid; u < MTC * 64; u += NTH) {
+      const int mt = u >> 6, ln = (u >> 1) & 31, h = u & 1;
+      const int rl0 = mt * 16 + (ln >> 2);
+      const int kk0 = 2 * (ln & 3) + 8 * h;
+      float v[4][S];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int rl = rl0 + 8 * (q >> 1), g = g0 + kk0 + (q & 1), row = row0 + rl;
+        df2 z{0.f, 0.f};
+        if (row < Q::RV && g < NG) {
+          const int an = row % NP, ilr = row / NP - il_lo;
+          const df2* Tp = Ts + (g * NILV + ilr) * NTS;
+          dfacc acc;
+          if (beta == 0) {
+            acc.mac(Phi[g * NP + an], Tp[0]);
+            for (int r = 0; r < D; ++r) acc.mac(dPhi[(r * NG + g) * NP + an], Tp[1 + r]);
+          } else {
+            const int k = beta - 1;
+            for (int r = 0; r < D; ++r) acc.mac(dPhi[(r * NG + g) * NP + an], Tp[1 + D + r * D + k]);
+          }
+          z = acc.norm();
+        }
+        oz_split<S>(z, oz_scale(eR[rl]), v[q]);
+      }
+      put_left_half<S>(Zs + (size_t)(b * MTC + mt) * S * 32, 32, ln, h, v);
+    }
+  };
+  // operator stripe kt into buffer b (asynchronous; completed before the next barrier)
+  auto fetch = [&](int kt, int b) {
+    const uint4* src = reinterpret_cast<const uint4*>(rbg + (size_t)kt * Q::stripe_u2);
+    uint4* dst = reinterpret_cast<uint4*>(Rs + (size_t)b * Q::stripe_u2);
+    for (int t = tid; t < (int)(Q::stripe_u2 / 2); t += NTH) cp_async16(dst + t, src + t);
+    cp_async_commit();
+  };
+
+  const int mt = warp / NGRP, nt0 = 4 * (warp % NGRP);
+  float acc[4][S][4];
+  auto zero = [&]() {
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj)
+#pragma unroll
+      for (int d = 0; d < S; ++d)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[jj][d][q] = 0.f;
+  };
+  // flush: the exact diagonals into the double-float output (store first, then add)
+  auto flush = [&](bool first) {
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) {
+      const int nt = nt0 + jj;
+      if (nt >= NTN) continue;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int rl = mt * 16 + (lane >> 2) + 8 * (q >> 1), row = row0 + rl;
+        const int j = nt * 8 + 2 * (lane & 3) + (q & 1);
+        if (row >= Q::RV || j >= C::NZ) continue;
+        const dfacc v = oz_combine<S>(acc[jj], q);
+        const df2 p = oz_scaled(v, eR[rl] + eC[j]);
+        const int an = row % NP, il = row / NP, i = il / M, l = il % M;
+        df2* dst = j < NP ? reinterpret_cast<df2*>(a.Ap) + le * NV * NV + (an * M + i) * NV + j * M + l
+                          : reinterpret_cast<df2*>(a.recov + e * (int64_t)(NV * NT + NV)) + (an * M + i) * NT +
+                                (j - NP) * M + l;
+        if (first) {
+          *dst = p;
+        } else {
+          dfacc t;
+          t.add(*dst);
+          t.add(p);
+          *dst = t.norm();
+        }
+      }
+    }
+  };
+  zero();
+  fetch(0, 0);
+  produce(0, 0);
+  cp_async_wait_all();
+  __syncthreads();
+  for (int kt = 0; kt < KTV; ++kt) {
+    if (kt + 1 < KTV) {
+      fetch(kt + 1, (kt + 1) & 1);
+      produce(kt + 1, (kt + 1) & 1);
+    }
+    const bool beta0 = kt < KTB;
+    tile_products<S, NTN>(acc, Zs + (size_t)(kt & 1) * Q::zs_u4, Rs + (size_t)(kt & 1) * Q::stripe_u2, mt, nt0, lane,
+                          [&](int nt) { return !beta0 || nt * 8 < NP; });
+    if ((kt + 1) % Q::KFLUSH == 0 || kt + 1 == KTV) {
+      flush(kt + 1 <= Q::KFLUSH);
+      zero();
+    }
+    cp_async_wait_all();
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// k_asm_face_tc: the face blocks of il pairs [QIL*blockIdx.x, +QIL), all faces in turn
+// ------------------------------------------------------------------------------------
+template <class C, int S, int MTC>
+__global__ void __launch_bounds__(AsmTC<C, S, MTC>::NTH) k_asm_face_tc(AssembleArgs a, DevTables T, DevTablesDF TD) {
+  using Q = AsmTC<C, S, MTC>;
+  constexpr int D = C::D, M = C::M, NP = C::NP, NFN = C::NFN, NF = C::NF, NGF = C::NGF, NV = C::NV, NT = C::NT;
+  constexpr int NRF = C::NRF, NTN = Q::NTN, NGRP = Q::NGRP, KTBF = Q::KTBF, KTF = Q::KTF, ROWS = Q::ROWS,
+                QIL = Q::QIL, NTH = Q::NTH, NC = NTN * 8;
+  extern __shared__ double smem_d[];
+  uint4* Zs = reinterpret_cast<uint4*>(smem_d);             // [2][MTC][S][32]
+  uint2* Rs = reinterpret_cast<uint2*>(Zs + 2 * Q::zs_u4);  // [2][NTN][S][32]
+  df2* Us = reinterpret_cast<df2*>(Rs + 2 * Q::stripe_u2);  // [NGF][QIL][NRF]
+  df2* Psi = Us + NGF * QIL * NRF;                          // [NGF][NFN] face basis at the face nodes
+  int* eR = reinterpret_cast<int*>(Psi + NGF * NFN);        // [ROWS]
+  int* eC = eR + ROWS;                                      // [NC]
+  const int64_t le = blockIdx.y;
+  const int64_t e = a.e0 + le;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int il0 = blockIdx.x * QIL;
+  const df2* ptf = reinterpret_cast<const df2*>(a.ptf) + le * NF * NGF * C::PT_FACE;
+  const uint2* rbg = reinterpret_cast<const uint2*>(a.rb) + le * Q::rb_u2;
+  const int* exg = reinterpret_cast<const int*>(rbg + Q::vol_u2 + NF * Q::face_u2);
+  df2* Ad = reinterpret_cast<df2*>(a.Ap) + le * NV * NV;
+  df2* Cd = reinterpret_cast<df2*>(a.Cp) + le * NT * NV;
+  df2* Bd = reinterpret_cast<df2*>(a.recov + e * (int64_t)(NV * NT + NV));
+  df2* Dd = reinterpret_cast<df2*>(a.S + e * (int64_t)NT * NT);
+  const int mt = warp / NGRP, nt0 = 4 * (warp % NGRP);
+  auto rowinfo = [&](int rl, int& il, int& c) {  // false past the block's pairs
+    il = il0 + rl / NFN;
+    c = rl % NFN;
+    return rl < QIL * NFN && il < M * M;
+  };
+
+  for (int f = 0; f < NF; ++f) {
+    // U of the block's il pairs at the face's points; row and column exponents
+    for (int t = tid; t < NGF * QIL * NRF; t += NTH) {
+      const int beta = t % NRF, ilr = (t / NRF) % QIL, gf = t / (NRF * QIL);
+      const int il = il0 + ilr;
+      df2 v{0.f, 0.f};
+      if (il < M * M) {
+        const int i = il / M, l = il % M;
+        const df2* U0 = ptf + (f * NGF + gf) * C::PT_FACE + M;
+        v = beta == 0 ? U0[i * M + l]
+                      : (beta == 1 ? U0[M * M + i * M + l] : U0[2 * M * M + (i * M + l) * D + (beta - 2)]);
+      }
+      Us[t] = v;
+    }
+    for (int t = tid; t < NGF * NFN; t += NTH) {
+      const int gf = t / NFN, c = t % NFN;
+      Psi[t] = TD.PhiF[(f * NGF + gf) * NP + T.fnodes[f * NFN + c]];
+    }
+    for (int t = tid; t < ROWS; t += NTH) eR[t] = 0;
+    for (int t = tid; t < NC; t += NTH) eC[t] = exg[NC * (1 + f) + t];
+    __syncthreads();
+    {
+      float* bR = reinterpret_cast<float*>(eR);
+      for (int t = tid; t < ROWS * NGF; t += NTH) {
+        const int rl = t % ROWS, gf = t / ROWS;
+        int il, c;
+        if (!rowinfo(rl, il, c)) continue;
+        const float psi = fabsf(Psi[gf * NFN + c].hi);
+        float um = 0.f;
+        for (int beta = 0; beta < NRF; ++beta) um = fmaxf(um, fabsf(Us[(gf * QIL + (il - il0)) * NRF + beta].hi));
+        const float b = psi * um;
+        if (b > 0.f) atomicMax(reinterpret_cast<int*>(&bR[rl]), __float_as_int(b));
+      }
+      __syncthreads();
+      for (int t = tid; t < ROWS; t += NTH) eR[t] = oz_exponent(bR[t] * 1.0001f);
+      __syncthreads();
+    }
+    auto produce = [&](int kt, int b) {
+      const int beta = kt / KTBF, g0 = (kt % KTBF) * 16;
+      for (int u = tid; u < MTC * 64; u += NTH) {
+        const int m = u >> 6, ln = (u >> 1) & 31, h = u & 1;
+        const int rl0 = m * 16 + (ln >> 2);
+        const int kk0 = 2 * (ln & 3) + 8 * h;
+        float v[4][S];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int rl = rl0 + 8 * (q >> 1), gf = g0 + kk0 + (q & 1);
+          int il, c;
+          df2 z{0.f, 0.f};
+          if (rowinfo(rl, il, c) && gf < NGF) {
+            dfacc acc;
+            acc.mac(Psi[gf * NFN + c], Us[(gf * QIL + (il - il0)) * NRF + beta]);
+            z = acc.norm();
+          }
+          oz_split<S>(z, oz_scale(eR[rl]), v[q]);
+        }
+        put_left_half<S>(Zs + (size_t)(b * MTC + m) * S * 32, 32, ln, h, v);
+      }
+    };
+    auto fetch = [&](int kt, int b) {
+      const uint4* src = reinterpret_cast<const uint4*>(rbg + Q::vol_u2 + (size_t)(f * KTF + kt) * Q::stripe_u2);
+      uint4* dst = reinterpret_cast<uint4*>(Rs + (size_t)b * Q::stripe_u2);
+      for (int t = tid; t < (int)(Q::stripe_u2 / 2); t += NTH) cp_async16(dst + t, src + t);
+      cp_async_commit();
+    };
+    float acc[4][S][4];
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj)
+#pragma unroll
+      for (int d = 0; d < S; ++d)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[jj][d][q] = 0.f;
+    fetch(0, 0);
+    produce(0, 0);
+    cp_async_wait_all();
+    __syncthreads();
+    const int jlo = NP + f * NFN, jhi = NP + (f + 1) * NFN;  // the face's own trace columns
+    for (int kt = 0; kt < KTF; ++kt) {
+      if (kt + 1 < KTF) {
+        fetch(kt + 1, (kt + 1) & 1);
+        produce(kt + 1, (kt + 1) & 1);
+      }
+      const int beta = kt / KTBF;
+      tile_products<S, NTN>(acc, Zs + (size_t)(kt & 1) * Q::zs_u4, Rs + (size_t)(kt & 1) * Q::stripe_u2, mt, nt0, lane,
+                            [&](int nt) {
+                              if (beta == 0) return nt * 8 < NP;
+                              if (beta == 1) return nt * 8 < jhi && nt * 8 + 8 > jlo;
+                              return true;
+                            });
+      cp_async_wait_all();
+      __syncthreads();
+    }
+    // C', D' rows of the face; A', B' rows of its nodes (this block owns these il pairs)
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) {
+      const int nt = nt0 + jj;
+      if (nt >= NTN) continue;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int rl = mt * 16 + (lane >> 2) + 8 * (q >> 1);
+        const int j = nt * 8 + 2 * (lane & 3) + (q & 1);
+        int il, c;
+        if (!rowinfo(rl, il, c) || j >= C::NZ) continue;
+        const df2 p = oz_scaled(oz_combine<S>(acc[jj], q), eR[rl] + eC[j]);
+        const int i = il / M, l = il % M;
+        const int rowt = (f * NFN + c) * M + i, rowv = T.fnodes[f * NFN + c] * M + i;
+        if (j < NP) {
+          Cd[rowt * NV + j * M + l] = p;
+          df2& dst = Ad[rowv * NV + j * M + l];
+          dfacc t;
+          t.add(dst);
+          t.add(p);
+          dst = t.norm();
+        } else {
+          const int tcol = (j - NP) * M + l;
+          Dd[rowt * NT + tcol] = p;
+          df2& dst = Bd[rowv * NT + tcol];
+          dfacc t;
+          t.add(dst);
+          t.add(p);
+          dst = t.norm();
+        }
+      }
+    }
+    __syncthreads();  // the next face adds to the same node rows
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// k_asm_residual: R_v and R_t (FP64 from the double-float point data)
+// ------------------------------------------------------------------------------------
+template <class C>
+__global__ void __launch_bounds__(128) k_asm_residual(AssembleArgs a, DevTables T) {
+  constexpr int D = C::D, M = C::M, NP = C::NP, NFN = C::NFN, NF = C::NF, NG = C::NG, NGF = C::NGF;
+  constexpr int NV = C::NV, NT = C::NT;
+  __shared__ double Rv[NV];
+  const int64_t le = blockIdx.x;
+  const int64_t e = a.e0 + le;
+  const int tid = threadIdx.x;
+  const df2* ptv = reinterpret_cast<const df2*>(a.ptv) + le * NG * C::PT_VOL;
+  const df2* ptf = reinterpret_cast<const df2*>(a.ptf) + le * NF * NGF * C::PT_FACE;
+  double* Rout = a.R + e * (int64_t)(NV + NT);
+  for (int t = tid; t < NV; t += blockDim.x) {
+    const int an = t / M, i = t % M;
+    double s = a.hist ? -a.hist[e * NV + t] : 0.0;
+    for (int g = 0; g < NG; ++g) {
+      const df2* P = ptv + g * C::PT_VOL;
+      s += T.Phi[g * NP + an] * df_val(P[i]);
+      for (int r = 0; r < D; ++r) s += T.dPhi[(r * NG + g) * NP + an] * df_val(P[M + r * M + i]);
+    }
+    Rv[t] = s;
+  }
+  __syncthreads();
+  for (int f = 0; f < NF; ++f) {
+    for (int t = tid; t < NFN * M; t += blockDim.x) {
+      const int c = t / M, i = t % M;
+      double s = 0.0;
+      for (int gf = 0; gf < NGF; ++gf)
+        s += T.PhiF[(f * NGF + gf) * NP + T.fnodes[f * NFN + c]] * df_val(ptf[(f * NGF + gf) * C::PT_FACE + i]);
+      Rv[T.fnodes[f * NFN + c] * M + i] += s;
+      Rout[NV + (f * NFN + c) * M + i] = s;
+    }
+    __syncthreads();
+  }
+  for (int t = tid; t < NV; t += blockDim.x) Rout[t] = Rv[t];
+}
+
+}  // namespace hdg

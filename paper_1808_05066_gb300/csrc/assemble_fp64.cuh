@@ -40,6 +40,7 @@ struct AssembleArgs {
   double* Cp;           // [ne][NT][NV]
   uint4* oz;            // [ne][...] exact-slice operands of the mixed condensation
   float* prep;          // [ne][...] inverse, FP32 copy and scales for the mixed condensation
+  uint2* rb;            // [ne][...] operator slices of the mixed assembly
   // outputs (global element index)
   double* S;            // [E][NT][NT]   (D' on entry to condense)
   double* g;            // [E][NT]

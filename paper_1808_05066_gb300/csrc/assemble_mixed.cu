@@ -1,8 +1,8 @@
-// Dispatch of the mixed-precision assemble + condense (assemble_mixed.cuh, condense_tc.cuh).
+// Dispatch of the mixed-precision assemble + condense (asm_tc.cuh, condense_tc.cuh).
 #include <algorithm>
 #include <vector>
 
-#include "assemble_mixed.cuh"
+#include "asm_tc.cuh"
 #include "condense_tc.cuh"
 #include "ctx.hpp"
 
@@ -10,7 +10,7 @@ namespace hdg {
 
 namespace {
 
-constexpr int kSlices = 6;  // exact bf16 slices per operand in the condensation products
+constexpr int kSlices = 6;  // exact bf16 slices per operand in every tensor-core product
 
 int ensure_df_tables(hdg_ctx* ctx) {
   if (ctx->d_tab_df) return HDG_OK;
@@ -30,16 +30,33 @@ int ensure_df_tables(hdg_ctx* ctx) {
   return HDG_OK;
 }
 
-// One compiled tile shape of the mixed assembly kernel.
+// One compiled shape of the assembly products: MTC row tiles (16 MTC rows) per CTA.
 struct AsmVariant {
-  int threads, gt;
-  size_t smem;
-  void (*kernel)(AssembleArgs, DevTables, DevTablesDF);
+  int mtc, threads;
+  void (*run)(const AssembleArgs&, const DevTables&, const DevTablesDF&, cudaStream_t);
+  int (*set_attr)();
 };
 
-template <class C, int NTH, int GTM>
+template <class C, int MTC>
+void run_products(const AssembleArgs& a, const DevTables& T, const DevTablesDF& TD, cudaStream_t s) {
+  using Q = AsmTC<C, kSlices, MTC>;
+  k_asm_vol_tc<C, kSlices, MTC><<<dim3(Q::NPASS, (unsigned)a.ne), Q::NTH, Q::vol_bytes, s>>>(a, TD);
+  k_asm_face_tc<C, kSlices, MTC><<<dim3(Q::NFCTA, (unsigned)a.ne), Q::NTH, Q::face_bytes, s>>>(a, T, TD);
+}
+
+template <class C, int MTC>
+int set_products_attr() {
+  using Q = AsmTC<C, kSlices, MTC>;
+  HDG_CK(cudaFuncSetAttribute(k_asm_vol_tc<C, kSlices, MTC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)Q::vol_bytes));
+  HDG_CK(cudaFuncSetAttribute(k_asm_face_tc<C, kSlices, MTC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)Q::face_bytes));
+  return HDG_OK;
+}
+
+template <class C, int MTC>
 AsmVariant make_variant() {
-  return AsmVariant{NTH, GTM, MixCfg<C, NTH, GTM>::asm_bytes, &k_assemble_df<C, NTH, GTM>};
+  return AsmVariant{MTC, AsmTC<C, kSlices, MTC>::NTH, &run_products<C, MTC>, &set_products_attr<C, MTC>};
 }
 
 // One compiled shape of the condensation kernel.
@@ -77,15 +94,17 @@ int run_mixed(hdg_ctx* ctx, const double* V, const double* Vhat, const double* h
   int rc = ensure_df_tables(ctx);
   if (rc) return rc;
   using TC = CondTC<C, 256, kSlices>;
+  using AQ = AsmTC<C, kSlices, 2>;  // the operator slices do not depend on the row tiling
   const size_t per_pt = sizeof(double) * ((size_t)C::NG * C::PT_VOL + (size_t)C::NF * C::NGF * C::PT_FACE +
                                           (size_t)C::NV * C::NV + (size_t)C::NT * C::NV);
-  const size_t per = per_pt + sizeof(uint4) * TC::slice_uint4 + sizeof(float) * TC::prep_floats;
+  const size_t per =
+      per_pt + sizeof(uint4) * TC::slice_uint4 + sizeof(float) * TC::prep_floats + sizeof(uint2) * AQ::rb_u2;
   if (ctx->chunk == 0) {
     int64_t ch = std::min<int64_t>(ctx->E, 8192);
-    while (ch > 256 && per * ch > ((size_t)12 << 30)) ch /= 2;
+    while (ch > 256 && per * ch > ((size_t)16 << 30)) ch /= 2;
     ctx->chunk = ch;
   }
-  const size_t need = per * ctx->chunk + 512;  // + room to align the slice and prep scratch
+  const size_t need = per * ctx->chunk + 1024;  // + room to align the slice, prep and operator scratch
   if (ctx->scr_bytes < need) {
     if (ctx->d_scr) cudaFree(ctx->d_scr);
     ctx->d_scr = nullptr;
@@ -94,15 +113,14 @@ int run_mixed(hdg_ctx* ctx, const double* V, const double* Vhat, const double* h
     ctx->scr_bytes = need;
   }
   // compiled tile shapes of the assembly kernel (threads, volume points per tile)
-  const AsmVariant variants[] = {make_variant<C, 256, 64>(), make_variant<C, 256, 32>(),
-                                 make_variant<C, 512, 64>(), make_variant<C, 128, 16>()};
-  constexpr int NVAR = 4;
+  const AsmVariant variants[] = {make_variant<C, 2>(), make_variant<C, 4>()};
+  constexpr int NVAR = 2;
   const CondVariant cvariants[] = {make_cond_variant<C, 256>(), make_cond_variant<C, 512>()};
   constexpr int NCVAR = 2;
   static bool attr_done = false;
   if (!attr_done) {
     for (const AsmVariant& v : variants)
-      HDG_CK(cudaFuncSetAttribute(v.kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem));
+      if (int rc2 = v.set_attr()) return rc2;
     for (const CondVariant& v : cvariants)
       HDG_CK(cudaFuncSetAttribute(v.kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem));
     HDG_CK(cudaFuncSetAttribute(k_condense_prep<C, kSlices>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -139,6 +157,8 @@ int run_mixed(hdg_ctx* ctx, const double* V, const double* Vhat, const double* h
     a.oz = reinterpret_cast<uint4*>((p + 255) & ~(uintptr_t)255);
     const uintptr_t q = reinterpret_cast<uintptr_t>(a.oz + ch * TC::slice_uint4);
     a.prep = reinterpret_cast<float*>((q + 255) & ~(uintptr_t)255);
+    const uintptr_t r = reinterpret_cast<uintptr_t>(a.prep + ch * TC::prep_floats);
+    a.rb = reinterpret_cast<uint2*>((r + 255) & ~(uintptr_t)255);
   }
   const int pw_threads = ((C::NG + C::NF * C::NGF + 31) / 32) * 32;
   for (int64_t e0 = 0; e0 < ctx->E; e0 += ch) {
@@ -148,6 +168,14 @@ int run_mixed(hdg_ctx* ctx, const double* V, const double* Vhat, const double* h
       LaunchScope ls(ctx, HDG_KERNEL_POINTWISE, s);
       k_pointwise<C, df2><<<(unsigned)a.ne, pw_threads, 0, s>>>(a, ctx->T, ctx->ph);
     }
+    {
+      LaunchScope ls(ctx, HDG_KERNEL_MIXED_ASSEMBLE, s);
+      k_asm_rb<C, kSlices, 2><<<(unsigned)a.ne, 256, 0, s>>>(a, ctx->T, TD);
+    }
+    {
+      LaunchScope ls(ctx, HDG_KERNEL_MIXED_ASSEMBLE, s);
+      k_asm_residual<C><<<(unsigned)a.ne, 128, 0, s>>>(a, ctx->T);
+    }
     if ((ctx->asm_variant < 0 || ctx->cond_variant < 0) && a.ne >= 512) {
       // autotune on this chunk: time every compiled shape (each rewrites the same outputs)
       if (ctx->asm_variant < 0) {
@@ -156,7 +184,7 @@ int run_mixed(hdg_ctx* ctx, const double* V, const double* Vhat, const double* h
         for (int i = 0; i < NVAR; ++i) {
           float ms = 0.f;
           const AsmVariant& v = variants[i];
-          int rc = time_launch(s, [&] { v.kernel<<<(unsigned)a.ne, v.threads, v.smem, s>>>(a, ctx->T, TD); }, &ms);
+          int rc = time_launch(s, [&] { v.run(a, ctx->T, TD, s); }, &ms);
           if (rc) return rc;
           if (ms < best) {
             best = ms;
@@ -165,7 +193,7 @@ int run_mixed(hdg_ctx* ctx, const double* V, const double* Vhat, const double* h
         }
         ctx->asm_variant = best_i;
         ctx->asm_variant_threads = variants[best_i].threads;
-        ctx->asm_variant_gt = variants[best_i].gt;
+        ctx->asm_variant_gt = 16 * variants[best_i].mtc;
       }
       if (ctx->cond_variant < 0) {
         const AsmVariant& v = variants[ctx->asm_variant];
@@ -173,7 +201,7 @@ int run_mixed(hdg_ctx* ctx, const double* V, const double* Vhat, const double* h
         int best_i = 0;
         for (int i = 0; i < NCVAR; ++i) {
           // the condensation overwrites its inputs: assemble again before each trial
-          v.kernel<<<(unsigned)a.ne, v.threads, v.smem, s>>>(a, ctx->T, TD);
+          v.run(a, ctx->T, TD, s);
           k_condense_prep<C, kSlices><<<(unsigned)a.ne, TC::PTH, TC::prep_bytes, s>>>(a);
           float ms = 0.f;
           const CondVariant& cv = cvariants[i];
@@ -191,7 +219,7 @@ int run_mixed(hdg_ctx* ctx, const double* V, const double* Vhat, const double* h
     const AsmVariant& v = variants[ctx->asm_variant < 0 ? 0 : ctx->asm_variant];
     {
       LaunchScope ls(ctx, HDG_KERNEL_MIXED_ASSEMBLE, s);
-      v.kernel<<<(unsigned)a.ne, v.threads, v.smem, s>>>(a, ctx->T, TD);
+      v.run(a, ctx->T, TD, s);
     }
     const CondVariant& cv = cvariants[ctx->cond_variant < 0 ? 0 : ctx->cond_variant];
     {

@@ -224,11 +224,6 @@ HDG_DEVI void cond_oz_product(const uint4* __restrict__ Lsl, int MT, const uint2
   }
 }
 
-HDG_DEVI df2 df_scaled(const dfacc& v, int e) {
-  const float p = ldexpf(1.f, e);
-  const df2 n = v.norm();
-  return {n.hi * p, n.lo * p};
-}
 
 template <class C, int OZS>
 __global__ void __launch_bounds__(CondTC<C, 256, OZS>::PTH) k_condense_prep(AssembleArgs a) {
@@ -414,7 +409,7 @@ __global__ void __launch_bounds__(NTHREADS) k_condense_tc(AssembleArgs a) {
     // r0 = B - A' X0 (exact slices), staged in W (the products read Xs, which Rk aliases)
     cond_oz_product<KT, NTB, OZS, NWARP, NJ>(slA, MTA, Xs, nnt, [&](int row, int col, const dfacc& v) {
       if (row < NV) {
-        const df2 p = df_scaled(v, eA[row] + eX[col]);
+        const df2 p = oz_scaled(v, eA[row] + eX[col]);
         dfacc t;
         t.add(bval(row, col));
         t.add(df2{-p.hi, -p.lo});
@@ -492,7 +487,7 @@ __global__ void __launch_bounds__(NTHREADS) k_condense_tc(AssembleArgs a) {
     cond_oz_product<KT, NTB, OZS, NWARP, NJ>(slC, MTC, Xs, nnt, [&](int row, int col, const dfacc& v) {
       const int gc = c0 + col;
       if (row >= NT || col >= nc) return;
-      const df2 p = df_scaled(v, eC[row] + eX[col]);
+      const df2 p = oz_scaled(v, eC[row] + eX[col]);
       dfacc t;
       if (gc < NT)
         t.add(Dd[row * NT + gc]);

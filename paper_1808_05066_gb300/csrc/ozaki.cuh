@@ -128,4 +128,19 @@ HDG_DEVI dfacc oz_combine(const float (&acc)[S][4], int q) {
   return r;
 }
 
+// v * 2^e as a double-float (the row and column scales of a slice product).
+HDG_DEVI df2 oz_scaled(const dfacc& v, int e) {
+  const float p = ldexpf(1.f, e);
+  const df2 n = v.norm();
+  return {n.hi * p, n.lo * p};
+}
+
+// Asynchronous 16-byte copies global -> shared (cp.async, L2 only) and their completion.
+HDG_DEVI void cp_async16(void* smem_dst, const void* gmem_src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
+HDG_DEVI void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+HDG_DEVI void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 }  // namespace hdg
