@@ -26,12 +26,12 @@
 
 namespace hdg {
 
-template <class C, int S, int MTC>
+template <class C, int S, int MTC, int NJW = 4>
 struct AsmTC {
   static constexpr int D = C::D, M = C::M, NP = C::NP, NFN = C::NFN, NF = C::NF, NG = C::NG, NGF = C::NGF;
   static constexpr int NZ = C::NZ, NV = C::NV, NT = C::NT, NR = C::NR, NRF = C::NRF;
   static constexpr int NTN = (NZ + 7) / 8;    // n tiles over the nodal columns
-  static constexpr int NGRP = (NTN + 3) / 4;  // groups of up to 4 n tiles (one warp each)
+  static constexpr int NGRP = (NTN + NJW - 1) / NJW;  // groups of NJW n tiles (one warp each)
   static constexpr int KTB = (NG + 15) / 16, KTV = NR * KTB;     // volume k tiles (beta-major)
   static constexpr int KTBF = (NGF + 15) / 16, KTF = NRF * KTBF;  // face k tiles
   static constexpr int KFLUSH = 8;            // k tiles per exact accumulation (128 entries)
@@ -41,6 +41,8 @@ struct AsmTC {
   static constexpr int QIL = ROWS / NFN;      // il pairs per face CTA (whole pairs: no races)
   static constexpr int NFCTA = (M * M + QIL - 1) / QIL;
   static constexpr int NTH = 32 * MTC * NGRP;
+  // NJW = 2 keeps a thread within 128 registers (two 256-thread CTAs or one 512-thread CTA per SM)
+  static constexpr int MINB = NJW == 2 ? (512 / NTH > 0 ? 512 / NTH : 1) : 1;
   static constexpr int NILV = (ROWS + NP - 1) / NP + 1;  // il pairs one volume CTA touches
   static constexpr int NTS = 1 + D + (C::VISC ? D * D : 0);
   static_assert(QIL >= 1 && KTF <= KFLUSH, "face block");
@@ -206,24 +208,24 @@ __global__ void __launch_bounds__(256) k_asm_rb(AssembleArgs a, DevTables T, Dev
 }
 
 // Shared pieces of the two product kernels.
+// Word w of lane ln of a left-operand tile holds rows (ln/4) + 8 (w%2), k (2 (ln%4) + 8 (w/2)) + {0, 1}.
 template <int S>
-HDG_DEVI void put_left_half(uint4* zs, int s_stride, int lane, int h, const float (&v)[4][S]) {
-  // v: (row a, k0), (row a, k0+1), (row b, k0), (row b, k0+1) of the lane's half h
-  uint2* z2 = reinterpret_cast<uint2*>(zs);
+HDG_DEVI void put_left_word(uint4* zs, int lane, int w, const float (&v0)[S], const float (&v1)[S]) {
+  unsigned* z32 = reinterpret_cast<unsigned*>(zs);
 #pragma unroll
-  for (int s = 0; s < S; ++s) z2[(s * s_stride + lane) * 2 + h] = make_uint2(oz_pack2(v[0][s], v[1][s]), oz_pack2(v[2][s], v[3][s]));
+  for (int s = 0; s < S; ++s) z32[(s * 32 + lane) * 4 + w] = oz_pack2(v0[s], v1[s]);
 }
 
-// One warp's products for one k tile: m tile mt, n tiles [nt0, nt0 + 4), tiles whose
+// One warp's products for one k tile: m tile mt, n tiles [nt0, nt0 + NJW), tiles whose
 // operator block is zero skipped (live(nt) false).
-template <int S, int NTN, class Live>
-HDG_DEVI void tile_products(float (&acc)[4][S][4], const uint4* zs, const uint2* rbs, int mt, int nt0, int lane,
+template <int S, int NTN, int NJW, class Live>
+HDG_DEVI void tile_products(float (&acc)[NJW][S][4], const uint4* zs, const uint2* rbs, int mt, int nt0, int lane,
                             Live live) {
   uint4 a[S];
 #pragma unroll
   for (int s = 0; s < S; ++s) a[s] = zs[(mt * S + s) * 32 + lane];
 #pragma unroll
-  for (int jj = 0; jj < 4; ++jj) {
+  for (int jj = 0; jj < NJW; ++jj) {
     const int nt = nt0 + jj;
     if (nt >= NTN || !live(nt)) continue;
     uint2 b[S];
@@ -236,9 +238,10 @@ HDG_DEVI void tile_products(float (&acc)[4][S][4], const uint4* zs, const uint2*
 // ------------------------------------------------------------------------------------
 // k_asm_vol_tc: rows [ROWS*blockIdx.y, +ROWS) of (il, an), all nodal columns
 // ------------------------------------------------------------------------------------
-template <class C, int S, int MTC>
-__global__ void __launch_bounds__(AsmTC<C, S, MTC>::NTH) k_asm_vol_tc(AssembleArgs a, DevTablesDF TD) {
-  using Q = AsmTC<C, S, MTC>;
+template <class C, int S, int MTC, int NJW>
+__global__ void __launch_bounds__(AsmTC<C, S, MTC, NJW>::NTH, AsmTC<C, S, MTC, NJW>::MINB)
+    k_asm_vol_tc(AssembleArgs a, DevTablesDF TD) {
+  using Q = AsmTC<C, S, MTC, NJW>;
   constexpr int D = C::D, M = C::M, NP = C::NP, NG = C::NG, NV = C::NV, NT = C::NT;
   constexpr int NTN = Q::NTN, NGRP = Q::NGRP, KTB = Q::KTB, KTV = Q::KTV, ROWS = Q::ROWS, NILV = Q::NILV,
                 NTS = Q::NTS, NTH = Q::NTH, NC = NTN * 8;
@@ -310,14 +313,15 @@ __global__ void __launch_bounds__(AsmTC<C, S, MTC>::NTH) k_asm_vol_tc(AssembleAr
   // Z slices of k tile kt into buffer b
   auto produce = [&](int kt, int b) {
     const int beta = kt / KTB, g0 = (kt % KTB) * 16;
-    for (int u = tid; u < MTC * 64; u += NTH) {
-      const int mt = u >> 6, ln = (u >> 1) & 31, h = u & 1;
-      const int rl0 = mt * 16 + (ln >> 2);
-      const int kk0 = 2 * (ln & 3) + 8 * h;
-      float v[4][S];
+    for (int u = tid; u < MTC * 128; u += NTH) {
+      const int mt = u >> 7, ln = (u >> 2) & 31, w = u & 3;
+      const int rl = mt * 16 + (ln >> 2) + 8 * (w & 1), row = row0 + rl;
+      const int kk0 = 2 * (ln & 3) + 8 * (w >> 1);
+      const float sc = oz_scale(eR[rl]);
+      float v[2][S];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int rl = rl0 + 8 * (q >> 1), g = g0 + kk0 + (q & 1), row = row0 + rl;
+      for (int q = 0; q < 2; ++q) {
+        const int g = g0 + kk0 + q;
         df2 z{0.f, 0.f};
         if (row < Q::RV && g < NG) {
           const int an = row % NP, ilr = row / NP - il_lo;
@@ -332,9 +336,9 @@ __global__ void __launch_bounds__(AsmTC<C, S, MTC>::NTH) k_asm_vol_tc(AssembleAr
           }
           z = acc.norm();
         }
-        oz_split<S>(z, oz_scale(eR[rl]), v[q]);
+        oz_split<S>(z, sc, v[q]);
       }
-      put_left_half<S>(Zs + (size_t)(b * MTC + mt) * S * 32, 32, ln, h, v);
+      put_left_word<S>(Zs + (size_t)(b * MTC + mt) * S * 32, ln, w, v[0], v[1]);
     }
   };
   // operator stripe kt into buffer b (asynchronous; completed before the next barrier)
@@ -345,11 +349,11 @@ __global__ void __launch_bounds__(AsmTC<C, S, MTC>::NTH) k_asm_vol_tc(AssembleAr
     cp_async_commit();
   };
 
-  const int mt = warp / NGRP, nt0 = 4 * (warp % NGRP);
-  float acc[4][S][4];
+  const int mt = warp / NGRP, nt0 = NJW * (warp % NGRP);
+  float acc[NJW][S][4];
   auto zero = [&]() {
 #pragma unroll
-    for (int jj = 0; jj < 4; ++jj)
+    for (int jj = 0; jj < NJW; ++jj)
 #pragma unroll
       for (int d = 0; d < S; ++d)
 #pragma unroll
@@ -358,7 +362,7 @@ __global__ void __launch_bounds__(AsmTC<C, S, MTC>::NTH) k_asm_vol_tc(AssembleAr
   // flush: the exact diagonals into the double-float output (store first, then add)
   auto flush = [&](bool first) {
 #pragma unroll
-    for (int jj = 0; jj < 4; ++jj) {
+    for (int jj = 0; jj < NJW; ++jj) {
       const int nt = nt0 + jj;
       if (nt >= NTN) continue;
 #pragma unroll
@@ -394,7 +398,7 @@ __global__ void __launch_bounds__(AsmTC<C, S, MTC>::NTH) k_asm_vol_tc(AssembleAr
       produce(kt + 1, (kt + 1) & 1);
     }
     const bool beta0 = kt < KTB;
-    tile_products<S, NTN>(acc, Zs + (size_t)(kt & 1) * Q::zs_u4, Rs + (size_t)(kt & 1) * Q::stripe_u2, mt, nt0, lane,
+    tile_products<S, NTN, NJW>(acc, Zs + (size_t)(kt & 1) * Q::zs_u4, Rs + (size_t)(kt & 1) * Q::stripe_u2, mt, nt0, lane,
                           [&](int nt) { return !beta0 || nt * 8 < NP; });
     if ((kt + 1) % Q::KFLUSH == 0 || kt + 1 == KTV) {
       flush(kt + 1 <= Q::KFLUSH);
@@ -408,9 +412,10 @@ __global__ void __launch_bounds__(AsmTC<C, S, MTC>::NTH) k_asm_vol_tc(AssembleAr
 // ------------------------------------------------------------------------------------
 // k_asm_face_tc: the face blocks of il pairs [QIL*blockIdx.x, +QIL), all faces in turn
 // ------------------------------------------------------------------------------------
-template <class C, int S, int MTC>
-__global__ void __launch_bounds__(AsmTC<C, S, MTC>::NTH) k_asm_face_tc(AssembleArgs a, DevTables T, DevTablesDF TD) {
-  using Q = AsmTC<C, S, MTC>;
+template <class C, int S, int MTC, int NJW>
+__global__ void __launch_bounds__(AsmTC<C, S, MTC, NJW>::NTH, AsmTC<C, S, MTC, NJW>::MINB)
+    k_asm_face_tc(AssembleArgs a, DevTables T, DevTablesDF TD) {
+  using Q = AsmTC<C, S, MTC, NJW>;
   constexpr int D = C::D, M = C::M, NP = C::NP, NFN = C::NFN, NF = C::NF, NGF = C::NGF, NV = C::NV, NT = C::NT;
   constexpr int NRF = C::NRF, NTN = Q::NTN, NGRP = Q::NGRP, KTBF = Q::KTBF, KTF = Q::KTF, ROWS = Q::ROWS,
                 QIL = Q::QIL, NTH = Q::NTH, NC = NTN * 8;
@@ -432,7 +437,7 @@ __global__ void __launch_bounds__(AsmTC<C, S, MTC>::NTH) k_asm_face_tc(AssembleA
   df2* Cd = reinterpret_cast<df2*>(a.Cp) + le * NT * NV;
   df2* Bd = reinterpret_cast<df2*>(a.recov + e * (int64_t)(NV * NT + NV));
   df2* Dd = reinterpret_cast<df2*>(a.S + e * (int64_t)NT * NT);
-  const int mt = warp / NGRP, nt0 = 4 * (warp % NGRP);
+  const int mt = warp / NGRP, nt0 = NJW * (warp % NGRP);
   auto rowinfo = [&](int rl, int& il, int& c) {  // false past the block's pairs
     il = il0 + rl / NFN;
     c = rl % NFN;
@@ -478,24 +483,26 @@ __global__ void __launch_bounds__(AsmTC<C, S, MTC>::NTH) k_asm_face_tc(AssembleA
     }
     auto produce = [&](int kt, int b) {
       const int beta = kt / KTBF, g0 = (kt % KTBF) * 16;
-      for (int u = tid; u < MTC * 64; u += NTH) {
-        const int m = u >> 6, ln = (u >> 1) & 31, h = u & 1;
-        const int rl0 = m * 16 + (ln >> 2);
-        const int kk0 = 2 * (ln & 3) + 8 * h;
-        float v[4][S];
+      for (int u = tid; u < MTC * 128; u += NTH) {
+        const int m = u >> 7, ln = (u >> 2) & 31, w = u & 3;
+        const int rl = m * 16 + (ln >> 2) + 8 * (w & 1);
+        const int kk0 = 2 * (ln & 3) + 8 * (w >> 1);
+        const float sc = oz_scale(eR[rl]);
+        int il, c;
+        const bool rv = rowinfo(rl, il, c);
+        float v[2][S];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int rl = rl0 + 8 * (q >> 1), gf = g0 + kk0 + (q & 1);
-          int il, c;
+        for (int q = 0; q < 2; ++q) {
+          const int gf = g0 + kk0 + q;
           df2 z{0.f, 0.f};
-          if (rowinfo(rl, il, c) && gf < NGF) {
+          if (rv && gf < NGF) {
             dfacc acc;
             acc.mac(Psi[gf * NFN + c], Us[(gf * QIL + (il - il0)) * NRF + beta]);
             z = acc.norm();
           }
-          oz_split<S>(z, oz_scale(eR[rl]), v[q]);
+          oz_split<S>(z, sc, v[q]);
         }
-        put_left_half<S>(Zs + (size_t)(b * MTC + m) * S * 32, 32, ln, h, v);
+        put_left_word<S>(Zs + (size_t)(b * MTC + m) * S * 32, ln, w, v[0], v[1]);
       }
     };
     auto fetch = [&](int kt, int b) {
@@ -504,9 +511,9 @@ __global__ void __launch_bounds__(AsmTC<C, S, MTC>::NTH) k_asm_face_tc(AssembleA
       for (int t = tid; t < (int)(Q::stripe_u2 / 2); t += NTH) cp_async16(dst + t, src + t);
       cp_async_commit();
     };
-    float acc[4][S][4];
+    float acc[NJW][S][4];
 #pragma unroll
-    for (int jj = 0; jj < 4; ++jj)
+    for (int jj = 0; jj < NJW; ++jj)
 #pragma unroll
       for (int d = 0; d < S; ++d)
 #pragma unroll
@@ -522,7 +529,7 @@ __global__ void __launch_bounds__(AsmTC<C, S, MTC>::NTH) k_asm_face_tc(AssembleA
         produce(kt + 1, (kt + 1) & 1);
       }
       const int beta = kt / KTBF;
-      tile_products<S, NTN>(acc, Zs + (size_t)(kt & 1) * Q::zs_u4, Rs + (size_t)(kt & 1) * Q::stripe_u2, mt, nt0, lane,
+      tile_products<S, NTN, NJW>(acc, Zs + (size_t)(kt & 1) * Q::zs_u4, Rs + (size_t)(kt & 1) * Q::stripe_u2, mt, nt0, lane,
                             [&](int nt) {
                               if (beta == 0) return nt * 8 < NP;
                               if (beta == 1) return nt * 8 < jhi && nt * 8 + 8 > jlo;
@@ -533,7 +540,7 @@ __global__ void __launch_bounds__(AsmTC<C, S, MTC>::NTH) k_asm_face_tc(AssembleA
     }
     // C', D' rows of the face; A', B' rows of its nodes (this block owns these il pairs)
 #pragma unroll
-    for (int jj = 0; jj < 4; ++jj) {
+    for (int jj = 0; jj < NJW; ++jj) {
       const int nt = nt0 + jj;
       if (nt >= NTN) continue;
 #pragma unroll

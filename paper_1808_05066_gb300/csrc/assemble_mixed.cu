@@ -30,33 +30,35 @@ int ensure_df_tables(hdg_ctx* ctx) {
   return HDG_OK;
 }
 
-// One compiled shape of the assembly products: MTC row tiles (16 MTC rows) per CTA.
+// One compiled shape of the assembly products: MTC row tiles (16 MTC rows) per CTA, NJW
+// column tiles per warp.
 struct AsmVariant {
-  int mtc, threads;
+  int mtc, njw, threads;
   void (*run)(const AssembleArgs&, const DevTables&, const DevTablesDF&, cudaStream_t);
   int (*set_attr)();
 };
 
-template <class C, int MTC>
+template <class C, int MTC, int NJW>
 void run_products(const AssembleArgs& a, const DevTables& T, const DevTablesDF& TD, cudaStream_t s) {
-  using Q = AsmTC<C, kSlices, MTC>;
-  k_asm_vol_tc<C, kSlices, MTC><<<dim3(Q::NPASS, (unsigned)a.ne), Q::NTH, Q::vol_bytes, s>>>(a, TD);
-  k_asm_face_tc<C, kSlices, MTC><<<dim3(Q::NFCTA, (unsigned)a.ne), Q::NTH, Q::face_bytes, s>>>(a, T, TD);
+  using Q = AsmTC<C, kSlices, MTC, NJW>;
+  k_asm_vol_tc<C, kSlices, MTC, NJW><<<dim3(Q::NPASS, (unsigned)a.ne), Q::NTH, Q::vol_bytes, s>>>(a, TD);
+  k_asm_face_tc<C, kSlices, MTC, NJW><<<dim3(Q::NFCTA, (unsigned)a.ne), Q::NTH, Q::face_bytes, s>>>(a, T, TD);
 }
 
-template <class C, int MTC>
+template <class C, int MTC, int NJW>
 int set_products_attr() {
-  using Q = AsmTC<C, kSlices, MTC>;
-  HDG_CK(cudaFuncSetAttribute(k_asm_vol_tc<C, kSlices, MTC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  using Q = AsmTC<C, kSlices, MTC, NJW>;
+  HDG_CK(cudaFuncSetAttribute(k_asm_vol_tc<C, kSlices, MTC, NJW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)Q::vol_bytes));
-  HDG_CK(cudaFuncSetAttribute(k_asm_face_tc<C, kSlices, MTC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  HDG_CK(cudaFuncSetAttribute(k_asm_face_tc<C, kSlices, MTC, NJW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)Q::face_bytes));
   return HDG_OK;
 }
 
-template <class C, int MTC>
+template <class C, int MTC, int NJW>
 AsmVariant make_variant() {
-  return AsmVariant{MTC, AsmTC<C, kSlices, MTC>::NTH, &run_products<C, MTC>, &set_products_attr<C, MTC>};
+  return AsmVariant{MTC, NJW, AsmTC<C, kSlices, MTC, NJW>::NTH, &run_products<C, MTC, NJW>,
+                    &set_products_attr<C, MTC, NJW>};
 }
 
 // One compiled shape of the condensation kernel.
@@ -113,8 +115,9 @@ int run_mixed(hdg_ctx* ctx, const double* V, const double* Vhat, const double* h
     ctx->scr_bytes = need;
   }
   // compiled tile shapes of the assembly kernel (threads, volume points per tile)
-  const AsmVariant variants[] = {make_variant<C, 2>(), make_variant<C, 4>()};
-  constexpr int NVAR = 2;
+  const AsmVariant variants[] = {make_variant<C, 2, 4>(), make_variant<C, 4, 4>(), make_variant<C, 2, 2>(),
+                                 make_variant<C, 4, 2>()};
+  constexpr int NVAR = 4;
   const CondVariant cvariants[] = {make_cond_variant<C, 256>(), make_cond_variant<C, 512>()};
   constexpr int NCVAR = 2;
   static bool attr_done = false;

@@ -115,7 +115,7 @@ def test_mixed_precision_matches_oracle(name, nsample):
         assert rel_fro(rec[e, nv * nt:], L["y"][nq:]) < TOL_BLOCK, (e, "y")
 
 
-@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
 def test_mixed_tile_shapes_match_oracle(variant, monkeypatch):
     """Every compiled tile shape of the mixed assembly (the autotuner's candidates)
     gives the oracle's condensed blocks."""
