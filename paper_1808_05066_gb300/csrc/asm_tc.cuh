@@ -58,8 +58,9 @@ struct AsmTC {
   static constexpr int NPSI = (1 + D) * NG * NP;  // Phi and dPhi of all volume points
   static constexpr size_t vol_bytes = sizeof(uint4) * 2 * zs_u4 + sizeof(uint2) * 2 * stripe_u2 +
                                       sizeof(df2) * (NG * NILV * NTS + NPSI) + sizeof(int) * (ROWS + NTN * 8) + 64;
-  static constexpr size_t face_bytes = sizeof(uint4) * 2 * zs_u4 + sizeof(uint2) * 2 * stripe_u2 +
-                                       sizeof(df2) * (NGF * QIL * NRF + NGF * NFN) + sizeof(int) * (ROWS + NTN * 8) + 64;
+  static constexpr size_t face_bytes =
+      sizeof(uint4) * 2 * zs_u4 + sizeof(uint2) * 2 * stripe_u2 +
+      sizeof(df2) * (NF * NGF * QIL * NRF + NF * NGF * NFN + QIL * NP * NZ) + sizeof(int) * NF * (ROWS + NTN * 8) + 64;
 };
 
 // Geometry as double-floats: Jinv [D][D] and n_f s_f / |J| [NF][D].
@@ -410,22 +411,26 @@ __global__ void __launch_bounds__(AsmTC<C, S, MTC, NJW>::NTH, AsmTC<C, S, MTC, N
 }
 
 // ------------------------------------------------------------------------------------
-// k_asm_face_tc: the face blocks of il pairs [QIL*blockIdx.x, +QIL), all faces in turn
+// k_asm_face_tc: the face blocks of il pairs [QIL*blockIdx.x, +QIL). The four faces run as
+// one pipeline of NF*KTF k tiles; each face's block goes to C', D' and is added, in shared
+// memory, to the A', B' rows of its nodes, which are added to the volume part once at the end
+// (this block owns these il pairs, so no other block touches those entries).
 // ------------------------------------------------------------------------------------
 template <class C, int S, int MTC, int NJW>
 __global__ void __launch_bounds__(AsmTC<C, S, MTC, NJW>::NTH, AsmTC<C, S, MTC, NJW>::MINB)
     k_asm_face_tc(AssembleArgs a, DevTables T, DevTablesDF TD) {
   using Q = AsmTC<C, S, MTC, NJW>;
   constexpr int D = C::D, M = C::M, NP = C::NP, NFN = C::NFN, NF = C::NF, NGF = C::NGF, NV = C::NV, NT = C::NT;
-  constexpr int NRF = C::NRF, NTN = Q::NTN, NGRP = Q::NGRP, KTBF = Q::KTBF, KTF = Q::KTF, ROWS = Q::ROWS,
-                QIL = Q::QIL, NTH = Q::NTH, NC = NTN * 8;
+  constexpr int NZ = C::NZ, NRF = C::NRF, NTN = Q::NTN, NGRP = Q::NGRP, KTBF = Q::KTBF, KTF = Q::KTF,
+                ROWS = Q::ROWS, QIL = Q::QIL, NTH = Q::NTH, NC = NTN * 8, NK = NF * KTF;
   extern __shared__ double smem_d[];
   uint4* Zs = reinterpret_cast<uint4*>(smem_d);             // [2][MTC][S][32]
   uint2* Rs = reinterpret_cast<uint2*>(Zs + 2 * Q::zs_u4);  // [2][NTN][S][32]
-  df2* Us = reinterpret_cast<df2*>(Rs + 2 * Q::stripe_u2);  // [NGF][QIL][NRF]
-  df2* Psi = Us + NGF * QIL * NRF;                          // [NGF][NFN] face basis at the face nodes
-  int* eR = reinterpret_cast<int*>(Psi + NGF * NFN);        // [ROWS]
-  int* eC = eR + ROWS;                                      // [NC]
+  df2* Us = reinterpret_cast<df2*>(Rs + 2 * Q::stripe_u2);  // [NF][NGF][QIL][NRF]
+  df2* Psi = Us + NF * NGF * QIL * NRF;                     // [NF][NGF][NFN] face basis at the face nodes
+  df2* Acc = Psi + NF * NGF * NFN;                          // [QIL][NP][NZ] face part of A', B'
+  int* eR = reinterpret_cast<int*>(Acc + QIL * NP * NZ);    // [NF][ROWS]
+  int* eC = eR + NF * ROWS;                                 // [NF][NC]
   const int64_t le = blockIdx.y;
   const int64_t e = a.e0 + le;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -444,101 +449,86 @@ __global__ void __launch_bounds__(AsmTC<C, S, MTC, NJW>::NTH, AsmTC<C, S, MTC, N
     return rl < QIL * NFN && il < M * M;
   };
 
-  for (int f = 0; f < NF; ++f) {
-    // U of the block's il pairs at the face's points; row and column exponents
-    for (int t = tid; t < NGF * QIL * NRF; t += NTH) {
-      const int beta = t % NRF, ilr = (t / NRF) % QIL, gf = t / (NRF * QIL);
-      const int il = il0 + ilr;
-      df2 v{0.f, 0.f};
-      if (il < M * M) {
-        const int i = il / M, l = il % M;
-        const df2* U0 = ptf + (f * NGF + gf) * C::PT_FACE + M;
-        v = beta == 0 ? U0[i * M + l]
-                      : (beta == 1 ? U0[M * M + i * M + l] : U0[2 * M * M + (i * M + l) * D + (beta - 2)]);
-      }
-      Us[t] = v;
+  // U and the face basis of every face, the A', B' accumulator, row and column exponents
+  for (int t = tid; t < NF * NGF * QIL * NRF; t += NTH) {
+    const int beta = t % NRF, ilr = (t / NRF) % QIL, gf = (t / (NRF * QIL)) % NGF, f = t / (NRF * QIL * NGF);
+    const int il = il0 + ilr;
+    df2 v{0.f, 0.f};
+    if (il < M * M) {
+      const int i = il / M, l = il % M;
+      const df2* U0 = ptf + (f * NGF + gf) * C::PT_FACE + M;
+      v = beta == 0 ? U0[i * M + l] : (beta == 1 ? U0[M * M + i * M + l] : U0[2 * M * M + (i * M + l) * D + (beta - 2)]);
     }
-    for (int t = tid; t < NGF * NFN; t += NTH) {
-      const int gf = t / NFN, c = t % NFN;
-      Psi[t] = TD.PhiF[(f * NGF + gf) * NP + T.fnodes[f * NFN + c]];
+    Us[t] = v;
+  }
+  for (int t = tid; t < NF * NGF * NFN; t += NTH) {
+    const int c = t % NFN, gf = (t / NFN) % NGF, f = t / (NFN * NGF);
+    Psi[t] = TD.PhiF[(f * NGF + gf) * NP + T.fnodes[f * NFN + c]];
+  }
+  for (int t = tid; t < QIL * NP * NZ; t += NTH) Acc[t] = df2{0.f, 0.f};
+  for (int t = tid; t < NF * ROWS; t += NTH) eR[t] = 0;
+  for (int t = tid; t < NF * NC; t += NTH) eC[t] = exg[NC + t];
+  __syncthreads();
+  {
+    float* bR = reinterpret_cast<float*>(eR);
+    for (int t = tid; t < NF * ROWS * NGF; t += NTH) {
+      const int rl = t % ROWS, gf = (t / ROWS) % NGF, f = t / (ROWS * NGF);
+      int il, c;
+      if (!rowinfo(rl, il, c)) continue;
+      const float psi = fabsf(Psi[(f * NGF + gf) * NFN + c].hi);
+      float um = 0.f;
+      for (int beta = 0; beta < NRF; ++beta)
+        um = fmaxf(um, fabsf(Us[((f * NGF + gf) * QIL + (il - il0)) * NRF + beta].hi));
+      const float b = psi * um;
+      if (b > 0.f) atomicMax(reinterpret_cast<int*>(&bR[f * ROWS + rl]), __float_as_int(b));
     }
-    for (int t = tid; t < ROWS; t += NTH) eR[t] = 0;
-    for (int t = tid; t < NC; t += NTH) eC[t] = exg[NC * (1 + f) + t];
     __syncthreads();
-    {
-      float* bR = reinterpret_cast<float*>(eR);
-      for (int t = tid; t < ROWS * NGF; t += NTH) {
-        const int rl = t % ROWS, gf = t / ROWS;
-        int il, c;
-        if (!rowinfo(rl, il, c)) continue;
-        const float psi = fabsf(Psi[gf * NFN + c].hi);
-        float um = 0.f;
-        for (int beta = 0; beta < NRF; ++beta) um = fmaxf(um, fabsf(Us[(gf * QIL + (il - il0)) * NRF + beta].hi));
-        const float b = psi * um;
-        if (b > 0.f) atomicMax(reinterpret_cast<int*>(&bR[rl]), __float_as_int(b));
-      }
-      __syncthreads();
-      for (int t = tid; t < ROWS; t += NTH) eR[t] = oz_exponent(bR[t] * 1.0001f);
-      __syncthreads();
-    }
-    auto produce = [&](int kt, int b) {
-      const int beta = kt / KTBF, g0 = (kt % KTBF) * 16;
-      for (int u = tid; u < MTC * 128; u += NTH) {
-        const int m = u >> 7, ln = (u >> 2) & 31, w = u & 3;
-        const int rl = m * 16 + (ln >> 2) + 8 * (w & 1);
-        const int kk0 = 2 * (ln & 3) + 8 * (w >> 1);
-        const float sc = oz_scale(eR[rl]);
-        int il, c;
-        const bool rv = rowinfo(rl, il, c);
-        float v[2][S];
+    for (int t = tid; t < NF * ROWS; t += NTH) eR[t] = oz_exponent(bR[t] * 1.0001f);
+    __syncthreads();
+  }
+  // k tile kk of the chained sequence: face kk / KTF, tile kk % KTF
+  auto produce = [&](int kk, int b) {
+    const int f = kk / KTF, kt = kk % KTF;
+    const int beta = kt / KTBF, g0 = (kt % KTBF) * 16;
+    for (int u = tid; u < MTC * 128; u += NTH) {
+      const int m = u >> 7, ln = (u >> 2) & 31, w = u & 3;
+      const int rl = m * 16 + (ln >> 2) + 8 * (w & 1);
+      const int kk0 = 2 * (ln & 3) + 8 * (w >> 1);
+      const float sc = oz_scale(eR[f * ROWS + rl]);
+      int il, c;
+      const bool rv = rowinfo(rl, il, c);
+      float v[2][S];
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
-          const int gf = g0 + kk0 + q;
-          df2 z{0.f, 0.f};
-          if (rv && gf < NGF) {
-            dfacc acc;
-            acc.mac(Psi[gf * NFN + c], Us[(gf * QIL + (il - il0)) * NRF + beta]);
-            z = acc.norm();
-          }
-          oz_split<S>(z, sc, v[q]);
+      for (int q = 0; q < 2; ++q) {
+        const int gf = g0 + kk0 + q;
+        df2 z{0.f, 0.f};
+        if (rv && gf < NGF) {
+          dfacc acc;
+          acc.mac(Psi[(f * NGF + gf) * NFN + c], Us[((f * NGF + gf) * QIL + (il - il0)) * NRF + beta]);
+          z = acc.norm();
         }
-        put_left_word<S>(Zs + (size_t)(b * MTC + m) * S * 32, ln, w, v[0], v[1]);
+        oz_split<S>(z, sc, v[q]);
       }
-    };
-    auto fetch = [&](int kt, int b) {
-      const uint4* src = reinterpret_cast<const uint4*>(rbg + Q::vol_u2 + (size_t)(f * KTF + kt) * Q::stripe_u2);
-      uint4* dst = reinterpret_cast<uint4*>(Rs + (size_t)b * Q::stripe_u2);
-      for (int t = tid; t < (int)(Q::stripe_u2 / 2); t += NTH) cp_async16(dst + t, src + t);
-      cp_async_commit();
-    };
-    float acc[NJW][S][4];
+      put_left_word<S>(Zs + (size_t)(b * MTC + m) * S * 32, ln, w, v[0], v[1]);
+    }
+  };
+  auto fetch = [&](int kk, int b) {
+    const uint4* src = reinterpret_cast<const uint4*>(rbg + Q::vol_u2 + (size_t)kk * Q::stripe_u2);
+    uint4* dst = reinterpret_cast<uint4*>(Rs + (size_t)b * Q::stripe_u2);
+    for (int t = tid; t < (int)(Q::stripe_u2 / 2); t += NTH) cp_async16(dst + t, src + t);
+    cp_async_commit();
+  };
+  float acc[NJW][S][4];
+  auto zero = [&]() {
 #pragma unroll
     for (int jj = 0; jj < NJW; ++jj)
 #pragma unroll
       for (int d = 0; d < S; ++d)
 #pragma unroll
         for (int q = 0; q < 4; ++q) acc[jj][d][q] = 0.f;
-    fetch(0, 0);
-    produce(0, 0);
-    cp_async_wait_all();
-    __syncthreads();
-    const int jlo = NP + f * NFN, jhi = NP + (f + 1) * NFN;  // the face's own trace columns
-    for (int kt = 0; kt < KTF; ++kt) {
-      if (kt + 1 < KTF) {
-        fetch(kt + 1, (kt + 1) & 1);
-        produce(kt + 1, (kt + 1) & 1);
-      }
-      const int beta = kt / KTBF;
-      tile_products<S, NTN, NJW>(acc, Zs + (size_t)(kt & 1) * Q::zs_u4, Rs + (size_t)(kt & 1) * Q::stripe_u2, mt, nt0, lane,
-                            [&](int nt) {
-                              if (beta == 0) return nt * 8 < NP;
-                              if (beta == 1) return nt * 8 < jhi && nt * 8 + 8 > jlo;
-                              return true;
-                            });
-      cp_async_wait_all();
-      __syncthreads();
-    }
-    // C', D' rows of the face; A', B' rows of its nodes (this block owns these il pairs)
+  };
+  // the face's block: C', D' rows (global) and the A', B' rows of its nodes (shared)
+  auto emit = [&](int f) {
 #pragma unroll
     for (int jj = 0; jj < NJW; ++jj) {
       const int nt = nt0 + jj;
@@ -548,29 +538,50 @@ __global__ void __launch_bounds__(AsmTC<C, S, MTC, NJW>::NTH, AsmTC<C, S, MTC, N
         const int rl = mt * 16 + (lane >> 2) + 8 * (q >> 1);
         const int j = nt * 8 + 2 * (lane & 3) + (q & 1);
         int il, c;
-        if (!rowinfo(rl, il, c) || j >= C::NZ) continue;
-        const df2 p = oz_scaled(oz_combine<S>(acc[jj], q), eR[rl] + eC[j]);
-        const int i = il / M, l = il % M;
-        const int rowt = (f * NFN + c) * M + i, rowv = T.fnodes[f * NFN + c] * M + i;
-        if (j < NP) {
+        if (!rowinfo(rl, il, c) || j >= NZ) continue;
+        const df2 p = oz_scaled(oz_combine<S>(acc[jj], q), eR[f * ROWS + rl] + eC[f * NC + j]);
+        const int i = il / M, l = il % M, rowt = (f * NFN + c) * M + i;
+        if (j < NP)
           Cd[rowt * NV + j * M + l] = p;
-          df2& dst = Ad[rowv * NV + j * M + l];
-          dfacc t;
-          t.add(dst);
-          t.add(p);
-          dst = t.norm();
-        } else {
-          const int tcol = (j - NP) * M + l;
-          Dd[rowt * NT + tcol] = p;
-          df2& dst = Bd[rowv * NT + tcol];
-          dfacc t;
-          t.add(dst);
-          t.add(p);
-          dst = t.norm();
-        }
+        else
+          Dd[rowt * NT + (j - NP) * M + l] = p;
+        df2& dst = Acc[((il - il0) * NP + T.fnodes[f * NFN + c]) * NZ + j];
+        dst = df_add(dst, dfacc_of(p));
       }
     }
-    __syncthreads();  // the next face adds to the same node rows
+  };
+  zero();
+  fetch(0, 0);
+  produce(0, 0);
+  cp_async_wait_all();
+  __syncthreads();
+  for (int kk = 0; kk < NK; ++kk) {
+    if (kk + 1 < NK) {
+      fetch(kk + 1, (kk + 1) & 1);
+      produce(kk + 1, (kk + 1) & 1);
+    }
+    const int f = kk / KTF, beta = (kk % KTF) / KTBF;
+    const int jlo = NP + f * NFN, jhi = NP + (f + 1) * NFN;  // the face's own trace columns
+    tile_products<S, NTN, NJW>(acc, Zs + (size_t)(kk & 1) * Q::zs_u4, Rs + (size_t)(kk & 1) * Q::stripe_u2, mt, nt0,
+                               lane, [&](int nt) {
+                                 if (beta == 0) return nt * 8 < NP;
+                                 if (beta == 1) return nt * 8 < jhi && nt * 8 + 8 > jlo;
+                                 return true;
+                               });
+    if (kk % KTF == KTF - 1) {
+      emit(f);
+      zero();
+    }
+    cp_async_wait_all();
+    __syncthreads();
+  }
+  // add the faces' part to the A', B' rows of this block's il pairs
+  for (int t = tid; t < QIL * NP * NZ; t += NTH) {
+    const int j = t % NZ, an = (t / NZ) % NP, ilr = t / (NZ * NP), il = il0 + ilr;
+    if (il >= M * M) continue;
+    const int i = il / M, l = il % M;
+    df2& dst = j < NP ? Ad[(an * M + i) * NV + j * M + l] : Bd[(an * M + i) * NT + (j - NP) * M + l];
+    dst = df_add(dst, dfacc_of(Acc[t]));
   }
 }
 

@@ -17,6 +17,13 @@ struct DevTablesDF {
   const df2* PLF;    // [NF][NF][NGF][NFN]
 };
 
+HDG_DEVI dfacc dfacc_of(df2 x) {
+  dfacc t;
+  t.hi = x.hi;
+  t.lo = x.lo;
+  return t;
+}
+
 HDG_DEVI df2 df_add(df2 x, const dfacc& y) {
   dfacc t = y;
   t.add(x);
