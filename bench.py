@@ -158,6 +158,21 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- main
+def measured_peaks() -> dict:
+    """HBM copy bandwidth and sustained dense bf16 rate measured on this GPU type
+    (MEASURED_PEAKS.json beside this file), else the earlier single measurement."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return {"hbm": float(d["hbm_gbs"]), "bf16": float(d["bf16_tflops_sustained"]),
+                "hbm_source": "measured: STREAM-style copy (MEASURED_PEAKS.json)",
+                "bf16_source": "measured: cuBLAS bf16 GEMM, sustained (MEASURED_PEAKS.json)"}
+    except (OSError, KeyError, ValueError):
+        return {"hbm": 6800.0, "bf16": 1700.0, "hbm_source": "fallback: earlier GB300 measurement",
+                "bf16_source": "fallback: earlier GB300 measurement, sustained"}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -210,7 +225,8 @@ def main():
     import torch.distributed as dist
 
     from paper_1808_05066_gb300 import hdg
-    from paper_1808_05066_gb300.workload import DeviceWorkload, flops_per_element
+    from paper_1808_05066_gb300.workload import (DeviceWorkload, algorithmic_bytes_per_element, flops_per_element,
+                                                 slice_mma_per_element)
     if ws > 1:
         dist.init_process_group("nccl", init_method="env://")
     torch.cuda.set_device(local)
@@ -253,7 +269,8 @@ def main():
     ms_per_step = ms / args.steps
     value = ws * E * args.steps / (ms / 1000.0)
     classes = {"pointwise": hdg.HDG_KERNEL_POINTWISE, "assemble": hdg.HDG_KERNEL_ASSEMBLE,
-               "condense": hdg.HDG_KERNEL_CONDENSE, "mixed_assemble": hdg.HDG_KERNEL_MIXED_ASSEMBLE,
+               "condense": hdg.HDG_KERNEL_CONDENSE, "mixed_operators": hdg.HDG_KERNEL_MIXED_OPERATORS,
+               "mixed_assemble": hdg.HDG_KERNEL_MIXED_ASSEMBLE, "mixed_face": hdg.HDG_KERNEL_MIXED_FACE,
                "mixed_prep": hdg.HDG_KERNEL_MIXED_PREP, "mixed_condense": hdg.HDG_KERNEL_MIXED_CONDENSE}
     prof = {k: hdg.hdg_profile_read(W.ctx.handle, c) for k, c in classes.items()}
     launches_total, _ = hdg.hdg_profile_read(W.ctx.handle, -1)
@@ -271,15 +288,24 @@ def main():
                 "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x max SM clock", "kernel": dom,
                 "launches": dom_launches, "avg_launch_ms": dom_ms / max(dom_launches, 1), "traffic": None}
     else:
-        # double-float multiply-accumulate = 12 FP32 operations for 2 useful flops:
-        # peak useful rate = 152 SMs x 128 FP32 lanes x max SM clock x 2 / 12
-        kind = "assemble" if dom == "mixed_assemble" else "condense_df"
-        work = flops_per_element(W.info, viscous, kind) * E * args.steps
-        peak = 152 * 128 * sm_max * 1e6 * 2 / 12 / 1e12
-        roof = {"bound": "alu", "achieved": work / (dom_ms / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x max SM clock, 12 FP32 ops per "
-                               "double-float multiply-accumulate", "kernel": dom,
-                "launches": dom_launches, "avg_launch_ms": dom_ms / max(dom_launches, 1), "traffic": None}
+        # tensor-core kernels of the mixed form: executed bf16 slice-product flops (mma.sync
+        # m16n8k16 = 4096 flops) against the measured sustained bf16 rate (the kernel runs
+        # inside a long step); the HBM side from the kernel's algorithmic bytes
+        pk = measured_peaks()
+        kind = dom if dom in ("mixed_assemble", "mixed_face", "mixed_condense") else "mixed_condense"
+        dom_ms_k = prof[kind][1]
+        flops = slice_mma_per_element(W.info, viscous, kind) * 4096.0 * E * args.steps
+        tensor = flops / (dom_ms_k / 1e3) / 1e12
+        hbm = algorithmic_bytes_per_element(W.info, kind) * E * args.steps / (dom_ms_k / 1e3) / 1e9
+        roof = {"bound": "tensor", "achieved": tensor, "peak": pk["bf16"], "unit": "TFLOP/s",
+                "peak_source": pk["bf16_source"], "kernel": kind, "launches": prof[kind][0],
+                "avg_launch_ms": dom_ms_k / max(prof[kind][0], 1), "traffic": None,
+                "hbm": {"achieved": hbm, "peak": pk["hbm"], "unit": "GB/s", "frac": hbm / pk["hbm"],
+                        "bytes_per_element": algorithmic_bytes_per_element(W.info, kind)}}
+        if roof["hbm"]["frac"] > tensor / pk["bf16"]:
+            roof["bound"] = "hbm"
+            roof["achieved"], roof["peak"], roof["unit"] = hbm, pk["hbm"], "GB/s"
+            roof["peak_source"] = pk["hbm_source"]
     if roof.get("achieved") is not None:
         roof["frac"] = roof["achieved"] / roof["peak"]
     shares = {k: (prof[k][1] / sum(v[1] for v in prof.values()) if prof[k][1] else 0.0) for k in prof}

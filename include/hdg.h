@@ -226,12 +226,14 @@ enum {
   HDG_KERNEL_POINTWISE = 0,        /* fluxes and pointwise Jacobians (both forms)          */
   HDG_KERNEL_ASSEMBLE = 1,         /* FP64 form: quadrature contractions into A, B, C, D    */
   HDG_KERNEL_CONDENSE = 2,         /* FP64 form: LU, X = A^{-1}B, S = D - C X              */
-  HDG_KERNEL_MIXED_ASSEMBLE = 3,   /* mixed form: double-float contractions               */
+  HDG_KERNEL_MIXED_ASSEMBLE = 3,   /* mixed form: volume contractions (tensor-core slices) */
   HDG_KERNEL_MIXED_CONDENSE = 4,   /* mixed form: refinement, tensor-core slice products   */
   HDG_KERNEL_TRACE = 5,            /* trace operator, preconditioner, solver kernels       */
   HDG_KERNEL_OTHER = 6,            /* history, conversions, recovery, norms, updates       */
   HDG_KERNEL_MIXED_PREP = 7,       /* mixed form: FP32 inverse, scales, operand slices      */
-  HDG_KERNEL_CLASSES = 8
+  HDG_KERNEL_MIXED_FACE = 8,       /* mixed form: face contractions (tensor-core slices)    */
+  HDG_KERNEL_MIXED_OPERATORS = 9,  /* mixed form: operator slices, FP64 residuals           */
+  HDG_KERNEL_CLASSES = 10
 };
 int hdg_profile_enable(hdg_ctx_t ctx, int on);
 int hdg_profile_reset(hdg_ctx_t ctx);

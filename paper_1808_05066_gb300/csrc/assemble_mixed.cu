@@ -34,14 +34,24 @@ int ensure_df_tables(hdg_ctx* ctx) {
 // column tiles per warp.
 struct AsmVariant {
   int mtc, njw, threads;
-  void (*run)(const AssembleArgs&, const DevTables&, const DevTablesDF&, cudaStream_t);
+  void (*run_vol)(const AssembleArgs&, const DevTablesDF&, cudaStream_t);
+  void (*run_face)(const AssembleArgs&, const DevTables&, const DevTablesDF&, cudaStream_t);
   int (*set_attr)();
+  void run(const AssembleArgs& a, const DevTables& T, const DevTablesDF& TD, cudaStream_t s) const {
+    run_vol(a, TD, s);
+    run_face(a, T, TD, s);
+  }
 };
 
 template <class C, int MTC, int NJW>
-void run_products(const AssembleArgs& a, const DevTables& T, const DevTablesDF& TD, cudaStream_t s) {
+void run_vol(const AssembleArgs& a, const DevTablesDF& TD, cudaStream_t s) {
   using Q = AsmTC<C, kSlices, MTC, NJW>;
   k_asm_vol_tc<C, kSlices, MTC, NJW><<<dim3(Q::NPASS, (unsigned)a.ne), Q::NTH, Q::vol_bytes, s>>>(a, TD);
+}
+
+template <class C, int MTC, int NJW>
+void run_face(const AssembleArgs& a, const DevTables& T, const DevTablesDF& TD, cudaStream_t s) {
+  using Q = AsmTC<C, kSlices, MTC, NJW>;
   k_asm_face_tc<C, kSlices, MTC, NJW><<<dim3(Q::NFCTA, (unsigned)a.ne), Q::NTH, Q::face_bytes, s>>>(a, T, TD);
 }
 
@@ -57,7 +67,7 @@ int set_products_attr() {
 
 template <class C, int MTC, int NJW>
 AsmVariant make_variant() {
-  return AsmVariant{MTC, NJW, AsmTC<C, kSlices, MTC, NJW>::NTH, &run_products<C, MTC, NJW>,
+  return AsmVariant{MTC, NJW, AsmTC<C, kSlices, MTC, NJW>::NTH, &run_vol<C, MTC, NJW>, &run_face<C, MTC, NJW>,
                     &set_products_attr<C, MTC, NJW>};
 }
 
@@ -172,11 +182,11 @@ int run_mixed(hdg_ctx* ctx, const double* V, const double* Vhat, const double* h
       k_pointwise<C, df2><<<(unsigned)a.ne, pw_threads, 0, s>>>(a, ctx->T, ctx->ph);
     }
     {
-      LaunchScope ls(ctx, HDG_KERNEL_MIXED_ASSEMBLE, s);
+      LaunchScope ls(ctx, HDG_KERNEL_MIXED_OPERATORS, s);
       k_asm_rb<C, kSlices, 2><<<(unsigned)a.ne, 256, 0, s>>>(a, ctx->T, TD);
     }
     {
-      LaunchScope ls(ctx, HDG_KERNEL_MIXED_ASSEMBLE, s);
+      LaunchScope ls(ctx, HDG_KERNEL_MIXED_OPERATORS, s);
       k_asm_residual<C><<<(unsigned)a.ne, 128, 0, s>>>(a, ctx->T);
     }
     if ((ctx->asm_variant < 0 || ctx->cond_variant < 0) && a.ne >= 512) {
@@ -222,7 +232,11 @@ int run_mixed(hdg_ctx* ctx, const double* V, const double* Vhat, const double* h
     const AsmVariant& v = variants[ctx->asm_variant < 0 ? 0 : ctx->asm_variant];
     {
       LaunchScope ls(ctx, HDG_KERNEL_MIXED_ASSEMBLE, s);
-      v.run(a, ctx->T, TD, s);
+      v.run_vol(a, TD, s);
+    }
+    {
+      LaunchScope ls(ctx, HDG_KERNEL_MIXED_FACE, s);
+      v.run_face(a, ctx->T, TD, s);
     }
     const CondVariant& cv = cvariants[ctx->cond_variant < 0 ? 0 : ctx->cond_variant];
     {

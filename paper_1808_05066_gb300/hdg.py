@@ -47,7 +47,9 @@ HDG_KERNEL_MIXED_CONDENSE = 4
 HDG_KERNEL_TRACE = 5
 HDG_KERNEL_OTHER = 6
 HDG_KERNEL_MIXED_PREP = 7
-HDG_KERNEL_CLASSES = 8
+HDG_KERNEL_MIXED_FACE = 8
+HDG_KERNEL_MIXED_OPERATORS = 9
+HDG_KERNEL_CLASSES = 10
 
 
 class HdgError(RuntimeError):

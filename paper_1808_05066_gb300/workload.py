@@ -115,3 +115,66 @@ def flops_per_element(info: dict, viscous: bool, kernel: str) -> float:
         # the Schur products; the FP32 LU and triangular solves are not counted
         return 2.0 * (3 * (NT + 1) * NV ** 2 + NT * NT * NV + NT * NV)
     raise ValueError(kernel)
+
+
+SLICES = 6  # exact bf16 slices per operand in the mixed form's tensor-core products
+
+
+def slice_mma_per_element(info: dict, viscous: bool, kernel: str) -> int:
+    """mma.sync m16n8k16 instructions per element of one mixed-form kernel (4096 bf16 flops
+    each), counted over the 16x8 output tiles that cover real rows and the k tiles whose
+    operator block is nonzero (S(S+1)/2 slice products per tile and k tile):
+      mixed_assemble: rows (i, l, node) = m^2 NP; k tiles per operator ceil(NG/16); the value
+                      operator reaches only the first ceil(NP/8) column tiles;
+      mixed_face:     per face rows (i, l, face node) = m^2 NFN; k tiles per operator
+                      ceil(NGF/16); value operator ceil(NP/8) column tiles, trace operator the
+                      tiles of the face's own trace columns, gradient operators all;
+      mixed_condense: r0 = B - A' X0 (A' rows) and S = D - C' X (C' rows), k = NV, the NT + 1
+                      right-hand sides in blocks of 32."""
+    D, M = info["dim"], info["m"]
+    NP, NFN, NF, NG, NGF = info["Np"], info["Nf"], info["nF"], info["NG"], info["NGF"]
+    NV, NT = info["nv"], info["nt"]
+    NZ = NP + NF * NFN
+    NR = D + 1 if viscous else 1
+    NRF = D + 2 if viscous else 2
+    prod = SLICES * (SLICES + 1) // 2
+    ntn = -(-NZ // 8)
+    nt_val = -(-NP // 8)
+    if kernel == "mixed_assemble":
+        kt = -(-NG // 16)
+        return -(-(M * M * NP) // 16) * kt * (nt_val + (NR - 1) * ntn) * prod
+    if kernel == "mixed_face":
+        kt = -(-NGF // 16)
+        total = 0
+        for f in range(NF):
+            lo, hi = NP + f * NFN, NP + (f + 1) * NFN
+            own = (hi - 1) // 8 - lo // 8 + 1
+            total += -(-(M * M * NFN) // 16) * kt * (nt_val + own + (NRF - 2) * ntn)
+        return total * prod
+    if kernel == "mixed_condense":
+        ntiles = 0
+        for c0 in range(0, NT + 1, 32):
+            ntiles += -(-min(32, NT + 1 - c0) // 8)
+        kt = -(-NV // 16)
+        return (-(-NV // 16) + -(-NT // 16)) * ntiles * kt * prod
+    raise ValueError(kernel)
+
+
+def algorithmic_bytes_per_element(info: dict, kernel: str) -> int:
+    """HBM bytes one element needs moved by a mixed-form kernel (8-byte values):
+      mixed_assemble: read the volume point tensors, write A' and B';
+      mixed_face:     read the face point tensors, write C' and D', add into A' and B';
+      mixed_condense: read D', B', R, the FP32 inverse and A'; write S, X, y and g."""
+    D, M = info["dim"], info["m"]
+    NP, NFN, NF, NG, NGF = info["Np"], info["Nf"], info["nF"], info["NG"], info["NGF"]
+    NV, NT = info["nv"], info["nt"]
+    pt_vol = M + D * M + M * M + D * M * M + D * M * M * D
+    pt_face = M + 2 * M * M + M * M * D
+    if kernel == "mixed_assemble":
+        return 8 * (NG * pt_vol + NV * (NV + NT))
+    if kernel == "mixed_face":
+        return 8 * (NF * NGF * pt_face + NT * (NV + NT) + 2 * NV * (NV + NT))
+    if kernel == "mixed_condense":
+        return 8 * (NT * NT + NV * NT + NV + NT) + 4 * 2 * NV * NV + 8 * (NT * NT + NV * NT + NV + NT)
+    raise ValueError(kernel)
+
