@@ -55,7 +55,8 @@ struct AsmTC {
   static constexpr size_t stripe_u2 = (size_t)NTN * S * 32;  // one k tile of operator slices
   // shared memory of the product kernels
   static constexpr size_t zs_u4 = (size_t)MTC * S * 32;       // one k tile of Z slices
-  static constexpr int NPSI = (1 + D) * NG * NP;  // Phi and dPhi of all volume points
+  static constexpr int NPP = NP | 1;                // odd row stride of the staged basis (banks)
+  static constexpr int NPSI = (1 + D) * NG * NPP;  // Phi and dPhi of all volume points
   static constexpr size_t vol_bytes = sizeof(uint4) * 2 * zs_u4 + sizeof(uint2) * 2 * stripe_u2 +
                                       sizeof(df2) * (NG * NILV * NTS + NPSI) + sizeof(int) * (ROWS + NTN * 8) + 64;
   static constexpr size_t face_bytes =
@@ -281,13 +282,16 @@ __global__ void __launch_bounds__(AsmTC<C, S, MTC, NJW>::NTH, AsmTC<C, S, MTC, N
     }
     Ts[t] = v;
   }
-  for (int t = tid; t < NG * NP; t += NTH) Ps[t] = TD.Phi[t];
-  for (int t = tid; t < D * NG * NP; t += NTH) Ps[NG * NP + t] = TD.dPhi[t];
+  for (int t = tid; t < (1 + D) * NG * NP; t += NTH) {
+    const int gr = t / NP, an = t % NP;  // gr = r * NG + g over Phi, then dPhi_r
+    Ps[gr * Q::NPP + an] = gr < NG ? TD.Phi[t] : TD.dPhi[t - NG * NP];
+  }
   for (int t = tid; t < ROWS; t += NTH) eR[t] = 0;
   for (int t = tid; t < NC; t += NTH) eC[t] = exg[t];
   __syncthreads();
-  const df2* Phi = Ps;
-  const df2* dPhi = Ps + NG * NP;
+  constexpr int NPP = Q::NPP;
+  const df2* Phi = Ps;              // [NG][NPP]
+  const df2* dPhi = Ps + NG * NPP;  // [D][NG][NPP]
   {
     float* bR = reinterpret_cast<float*>(eR);  // bounds first, exponents after
     for (int t = tid; t < ROWS * NG; t += NTH) {
@@ -295,13 +299,13 @@ __global__ void __launch_bounds__(AsmTC<C, S, MTC, NJW>::NTH, AsmTC<C, S, MTC, N
       if (row >= Q::RV) continue;
       const int an = row % NP, ilr = row / NP - il_lo;
       const df2* Tp = Ts + (g * NILV + ilr) * NTS;
-      float b = fabsf(Phi[g * NP + an].hi) * fabsf(Tp[0].hi);
-      for (int r = 0; r < D; ++r) b = fmaf(fabsf(dPhi[(r * NG + g) * NP + an].hi), fabsf(Tp[1 + r].hi), b);
+      float b = fabsf(Phi[g * NPP + an].hi) * fabsf(Tp[0].hi);
+      for (int r = 0; r < D; ++r) b = fmaf(fabsf(dPhi[(r * NG + g) * NPP + an].hi), fabsf(Tp[1 + r].hi), b);
       if constexpr (C::VISC)
         for (int k = 0; k < D; ++k) {
           float bk = 0.f;
           for (int r = 0; r < D; ++r)
-            bk = fmaf(fabsf(dPhi[(r * NG + g) * NP + an].hi), fabsf(Tp[1 + D + r * D + k].hi), bk);
+            bk = fmaf(fabsf(dPhi[(r * NG + g) * NPP + an].hi), fabsf(Tp[1 + D + r * D + k].hi), bk);
           b = fmaxf(b, bk);
         }
       if (b > 0.f) atomicMax(reinterpret_cast<int*>(&bR[rl]), __float_as_int(b));
@@ -311,37 +315,58 @@ __global__ void __launch_bounds__(AsmTC<C, S, MTC, NJW>::NTH, AsmTC<C, S, MTC, N
     __syncthreads();
   }
 
-  // Z slices of k tile kt into buffer b
+  // Z slices of k tile kt into buffer b. Unit u = (m tile, lane, word) of the fragment-native
+  // tile; each thread's units, rows and scales are fixed over the k loop.
+  constexpr int NU = (MTC * 128 + NTH - 1) / NTH;
+  int u_rl[NU], u_an[NU], u_tb[NU], u_kk[NU], u_dst[NU];
+  float u_sc[NU];
+  bool u_ok[NU];
+#pragma unroll
+  for (int x = 0; x < NU; ++x) {
+    const int u = tid + x * NTH;
+    const int mt = u >> 7, ln = (u >> 2) & 31, w = u & 3;
+    const int rl = mt * 16 + (ln >> 2) + 8 * (w & 1), row = row0 + rl;
+    u_ok[x] = u < MTC * 128 && row < Q::RV;
+    u_rl[x] = rl;
+    u_an[x] = row % NP;
+    u_tb[x] = (row / NP - il_lo) * NTS;
+    u_kk[x] = 2 * (ln & 3) + 8 * (w >> 1);
+    u_dst[x] = (mt * S * 32 + ln) * 4 + w;  // word index within one buffer, slice 0
+    u_sc[x] = u < MTC * 128 ? oz_scale(eR[rl]) : 1.f;
+  }
   auto produce = [&](int kt, int b) {
     const int beta = kt / KTB, g0 = (kt % KTB) * 16;
-    for (int u = tid; u < MTC * 128; u += NTH) {
-      const int mt = u >> 7, ln = (u >> 2) & 31, w = u & 3;
-      const int rl = mt * 16 + (ln >> 2) + 8 * (w & 1), row = row0 + rl;
-      const int kk0 = 2 * (ln & 3) + 8 * (w >> 1);
-      const float sc = oz_scale(eR[rl]);
+    unsigned* z32 = reinterpret_cast<unsigned*>(Zs + (size_t)b * Q::zs_u4);
+#pragma unroll
+    for (int x = 0; x < NU; ++x) {
+      if (tid + x * NTH >= MTC * 128) break;
       float v[2][S];
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
-        const int g = g0 + kk0 + q;
+        const int g = g0 + u_kk[x] + q;
         df2 z{0.f, 0.f};
-        if (row < Q::RV && g < NG) {
-          const int an = row % NP, ilr = row / NP - il_lo;
-          const df2* Tp = Ts + (g * NILV + ilr) * NTS;
+        if (u_ok[x] && g < NG) {
+          const df2* Tp = Ts + g * (NILV * NTS) + u_tb[x];
+          const int an = u_an[x];
           dfacc acc;
           if (beta == 0) {
-            acc.mac(Phi[g * NP + an], Tp[0]);
-            for (int r = 0; r < D; ++r) acc.mac(dPhi[(r * NG + g) * NP + an], Tp[1 + r]);
+            acc.mac(Phi[g * NPP + an], Tp[0]);
+#pragma unroll
+            for (int r = 0; r < D; ++r) acc.mac(dPhi[(r * NG + g) * NPP + an], Tp[1 + r]);
           } else {
             const int k = beta - 1;
-            for (int r = 0; r < D; ++r) acc.mac(dPhi[(r * NG + g) * NP + an], Tp[1 + D + r * D + k]);
+#pragma unroll
+            for (int r = 0; r < D; ++r) acc.mac(dPhi[(r * NG + g) * NPP + an], Tp[1 + D + r * D + k]);
           }
           z = acc.norm();
         }
-        oz_split<S>(z, sc, v[q]);
+        oz_split<S>(z, u_sc[x], v[q]);
       }
-      put_left_word<S>(Zs + (size_t)(b * MTC + mt) * S * 32, ln, w, v[0], v[1]);
+#pragma unroll
+      for (int s2 = 0; s2 < S; ++s2) z32[u_dst[x] + s2 * 128] = oz_pack2(v[0][s2], v[1][s2]);
     }
   };
+
   // operator stripe kt into buffer b (asynchronous; completed before the next barrier)
   auto fetch = [&](int kt, int b) {
     const uint4* src = reinterpret_cast<const uint4*>(rbg + (size_t)kt * Q::stripe_u2);

@@ -35,22 +35,32 @@ HDG_DEVI int oz_exponent(float amax) {
   if (amax > 0.f) frexpf(amax, &E);
   return E;
 }
-HDG_DEVI float oz_scale(int E) { return ldexpf(1.f, 8 - E); }
+HDG_DEVI float oz_scale(int E) { return ldexpf(1.f, 8 - E); }  // per row / column, not per entry
 
-// Slices of one double-float value, scaled by a power of two.
+// Slices of one double-float value, scaled by a power of two (|v| scale <= 256).
+// Slice 0 is the nearest integer to the high word h; the low word l joins the remainder
+// (|r| <= 1/2) in one exact two-sum (t, e). Slices 1 and 2 peel t exactly (scale by 2^8,
+// subtract the nearest integer); the two-sum's error e, scaled to the unit of slice 3, is
+// added there (|e| <= 1/2 at that unit, so the slice stays within 128; the rounding of that
+// addition is below 2^-49 of 2^E); slices 3.. peel what is left. Every slice after the first
+// lies in [-128, 128] and the represented value differs from v by less than 2^(E-48).
 template <int S>
 HDG_DEVI void oz_split(df2 v, float scale, float (&out)[S]) {
-  float h = v.hi * scale, l = v.lo * scale;
+  const float h = v.hi * scale, l = v.lo * scale;
+  const float q0 = rintf(h);
+  out[0] = q0;
+  const float r = h - q0;  // exact
+  float t = r + l;         // two-sum: t + e = r + l exactly
+  const float bb = t - r;
+  float e = (r - (t - bb)) + (l - bb);
 #pragma unroll
-  for (int i = 0; i < S; ++i) {
-    const float q = rintf(h);
+  for (int i = 1; i < S; ++i) {
+    t *= 256.f;
+    if (i <= 3) e *= 256.f;
+    if (i == 3) t += e;
+    const float q = rintf(t);
     out[i] = q;
-    const float r = h - q;  // exact: |r| <= 1/2
-    const float t = r + l;  // renormalise (r, l) with a two-sum
-    const float bb = t - r;
-    const float err = (r - (t - bb)) + (l - bb);
-    h = t * 256.f;
-    l = err * 256.f;
+    t -= q;  // exact: |t - q| <= 1/2
   }
 }
 
@@ -128,11 +138,19 @@ HDG_DEVI dfacc oz_combine(const float (&acc)[S][4], int q) {
   return r;
 }
 
-// v * 2^e as a double-float (the row and column scales of a slice product).
+// 2^e as a float for |e| <= 126 (built from the exponent field).
+HDG_DEVI float oz_pow2(int e) {
+  e = e < -126 ? -126 : (e > 127 ? 127 : e);
+  return __int_as_float((e + 127) << 23);
+}
+
+// v * 2^e as a double-float (the row and column scales of a slice product). Two factors
+// keep e over the whole float range.
 HDG_DEVI df2 oz_scaled(const dfacc& v, int e) {
-  const float p = ldexpf(1.f, e);
+  const int e1 = e / 2, e2 = e - e1;
+  const float p1 = oz_pow2(e1), p2 = oz_pow2(e2);
   const df2 n = v.norm();
-  return {n.hi * p, n.lo * p};
+  return {n.hi * p1 * p2, n.lo * p1 * p2};
 }
 
 // Asynchronous 16-byte copies global -> shared (cp.async, L2 only) and their completion.
