@@ -33,9 +33,12 @@ struct CondTC {
   static constexpr int CB = 32, NTB = CB / 8;
   static constexpr int RT = NTHREADS >= 512 ? 2 : 4, CT = 4;  // FP32 register tile
   static constexpr int LDA = (NV + 3) / 4 * 4;  // leading dimension of the transposed FP32 matrices
-  // fragment-native slices per element: [tile][slice][lane] uint4
-  static constexpr size_t slice_uint4 = (size_t)(MTA + MTC) * KT * OZS * 32;
-  static constexpr size_t xs_bytes = sizeof(uint2) * KT * NTB * OZS * 32;
+  // A' and C' rows as the right operand (n tiles of 8 rows), X^T as the left operand
+  // (row tiles of 16 block columns); fragment-native slices, [n tile][k tile][slice][lane]
+  static constexpr int NTA = (NV + 7) / 8, NTC = (NT + 7) / 8, NMB = CB / 16;
+  static constexpr size_t slice_u2 = (size_t)(NTA + NTC) * KT * OZS * 32;
+  static constexpr size_t slice_uint4 = slice_u2 / 2;
+  static constexpr size_t xs_bytes = sizeof(uint4) * KT * NMB * OZS * 32;
   static_assert(xs_bytes >= sizeof(float) * 2 * NV * CB, "residual buffers alias the slice buffer");
   static constexpr size_t bytes = sizeof(float) * (2 * NV * LDA + NV * CB + NV) + sizeof(df2) * NV * CB + xs_bytes +
                                   sizeof(int) * (NV + MTA * 16 + MTC * 16 + CB) + 64;
@@ -174,56 +177,55 @@ HDG_DEVI int gj_column(const int* piv, int j) {
   return x;
 }
 
-// Exact-slice product of MT row tiles of a sliced left operand (global, fragment-native)
-// with the sliced block Xs (shared memory), nnt column tiles; each warp owns one row tile
-// and NJ column tiles at a time, with the next k tile's fragments loaded ahead.
-// epi(row, col, value_without_scales) per element.
-template <int KT, int NTB, int OZS, int NWARP, int NJ, class Epi>
-HDG_DEVI void cond_oz_product(const uint4* __restrict__ Lsl, int MT, const uint2* Xs, int nnt, Epi epi) {
+// Exact-slice product of the rows of A' or C' (right operand, NTL tiles of 8 rows, sliced in
+// global memory [NTL][KT][OZS][32]) with the block's X^T (left operand, nmt tiles of 16
+// block columns, sliced in shared memory [KT][NMB][OZS][32]). Each warp owns one tile of 8
+// rows across all the block's columns, so every right-operand fragment is read from L2 once
+// per block; the next k tile's fragments load during this tile's products.
+// epi(row, col, value_without_scales) per element (row of A' or C', block column).
+template <int KT, int NMB, int OZS, int NWARP, class Epi>
+HDG_DEVI void cond_oz_product(const uint2* __restrict__ Rsl, int NTL, const uint4* Xs, int nmt, Epi epi) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int NH = (nnt + NJ - 1) / NJ;
-  for (int task = warp; task < MT * NH; task += NWARP) {
-    const int mt = task / NH, nt0 = NJ * (task % NH);
-    float acc[NJ][OZS][4];
+  for (int task = warp; task < NTL; task += NWARP) {
+    float acc[NMB][OZS][4];
 #pragma unroll
-    for (int j = 0; j < NJ; ++j)
+    for (int m = 0; m < NMB; ++m)
 #pragma unroll
       for (int d = 0; d < OZS; ++d)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) acc[j][d][q] = 0.f;
-    const uint4* Lt = Lsl + (size_t)mt * KT * OZS * 32 + lane;
-    uint4 a[OZS], an[OZS];
+        for (int q = 0; q < 4; ++q) acc[m][d][q] = 0.f;
+    const uint2* Bt = Rsl + (size_t)task * KT * OZS * 32 + lane;
+    uint2 b[OZS], bn[OZS];
 #pragma unroll
-    for (int s = 0; s < OZS; ++s) a[s] = Lt[s * 32];
+    for (int s = 0; s < OZS; ++s) b[s] = Bt[s * 32];
 #pragma unroll 1
     for (int kt = 0; kt < KT; ++kt) {
       if (kt + 1 < KT)  // next tile's fragments in flight during this tile's products
 #pragma unroll
-        for (int s = 0; s < OZS; ++s) an[s] = Lt[((kt + 1) * OZS + s) * 32];
+        for (int s = 0; s < OZS; ++s) bn[s] = Bt[((kt + 1) * OZS + s) * 32];
 #pragma unroll
-      for (int j = 0; j < NJ; ++j)
-        if (nt0 + j < nnt) {
-          uint2 b[OZS];
+      for (int m = 0; m < NMB; ++m)
+        if (m < nmt) {
+          uint4 a[OZS];
 #pragma unroll
-          for (int s = 0; s < OZS; ++s) b[s] = Xs[((kt * NTB + nt0 + j) * OZS + s) * 32 + lane];
-          oz_mma_tile<OZS>(acc[j], a, b);
+          for (int s = 0; s < OZS; ++s) a[s] = Xs[((kt * NMB + m) * OZS + s) * 32 + lane];
+          oz_mma_tile<OZS>(acc[m], a, b);
         }
 #pragma unroll
-      for (int s = 0; s < OZS; ++s) a[s] = an[s];
+      for (int s = 0; s < OZS; ++s) b[s] = bn[s];
     }
 #pragma unroll
-    for (int j = 0; j < NJ; ++j) {
-      if (nt0 + j >= nnt) break;
+    for (int m = 0; m < NMB; ++m) {
+      if (m >= nmt) break;
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const int row = mt * 16 + (lane >> 2) + 8 * (q >> 1);
-        const int col = (nt0 + j) * 8 + 2 * (lane & 3) + (q & 1);
-        epi(row, col, oz_combine<OZS>(acc[j], q));
+        const int col = m * 16 + (lane >> 2) + 8 * (q >> 1);
+        const int row = task * 8 + 2 * (lane & 3) + (q & 1);
+        epi(row, col, oz_combine<OZS>(acc[m], q));
       }
     }
   }
 }
-
 
 template <class C, int OZS>
 __global__ void __launch_bounds__(CondTC<C, 256, OZS>::PTH) k_condense_prep(AssembleArgs a) {
@@ -245,7 +247,6 @@ __global__ void __launch_bounds__(CondTC<C, 256, OZS>::PTH) k_condense_prep(Asse
   float* pre = a.prep + le * Q::prep_floats;
   int* eA = reinterpret_cast<int*>(pre + Q::PREP_EA);
   int* eC = reinterpret_cast<int*>(pre + Q::PREP_EC);
-  uint4* slA = a.oz + le * Q::slice_uint4;
 
   // A'^T (FP32) in shared memory, row exponents of A' and C'
   for (int r = warp; r < LDA; r += NWARP) {
@@ -288,18 +289,20 @@ __global__ void __launch_bounds__(CondTC<C, 256, OZS>::PTH) k_condense_prep(Asse
     G[t] = r < NV ? G[t] * sc[r] * sc[k] : 0.f;
   }
   __syncthreads();
-  // slices of A' and C' (one warp per 16 x 16 tile)
+  // slices of the rows of A' and C' as the right operand (one warp per 16 x 8 tile)
   {
-    auto getA = [&](int r, int k) { return (r < NV && k < NV) ? Ap[r * NV + k] : df2{0.f, 0.f}; };
-    auto getC = [&](int r, int k) { return (r < NT && k < NV) ? Cp[r * NV + k] : df2{0.f, 0.f}; };
-    auto sA = [&](int r) { return oz_scale(eA[r]); };
-    auto sC = [&](int r) { return oz_scale(eC[r]); };
-    for (int u = warp; u < (MTA + MTC) * KT; u += NWARP) {
-      const int mt = u / KT, kt = u % KT;
-      if (mt < MTA)
-        oz_slice_left_tile<OZS>(slA + (size_t)u * OZS * 32, 32, mt * 16, kt * 16, lane, getA, sA);
+    constexpr int NTA = Q::NTA, NTC = Q::NTC;
+    uint2* sl = reinterpret_cast<uint2*>(a.oz) + le * Q::slice_u2;
+    auto getA = [&](int k, int n) { return (n < NV && k < NV) ? Ap[n * NV + k] : df2{0.f, 0.f}; };
+    auto getC = [&](int k, int n) { return (n < NT && k < NV) ? Cp[n * NV + k] : df2{0.f, 0.f}; };
+    auto sA = [&](int n) { return oz_scale(eA[n]); };
+    auto sC = [&](int n) { return oz_scale(eC[n]); };
+    for (int u = warp; u < (NTA + NTC) * KT; u += NWARP) {
+      const int nt = u / KT, kt = u % KT;
+      if (nt < NTA)
+        oz_slice_right_tile<OZS>(sl + (size_t)u * OZS * 32, 32, kt * 16, nt * 8, lane, getA, sA);
       else
-        oz_slice_left_tile<OZS>(slA + (size_t)u * OZS * 32, 32, (mt - MTA) * 16, kt * 16, lane, getC, sC);
+        oz_slice_right_tile<OZS>(sl + (size_t)u * OZS * 32, 32, kt * 16, (nt - NTA) * 8, lane, getC, sC);
     }
   }
   // inverse of the transposed equilibrated matrix, written out with its columns in place
@@ -317,12 +320,11 @@ __global__ void __launch_bounds__(CondTC<C, 256, OZS>::PTH) k_condense_prep(Asse
 template <class C, int NTHREADS, int OZS>
 __global__ void __launch_bounds__(NTHREADS) k_condense_tc(AssembleArgs a) {
   using Q = CondTC<C, NTHREADS, OZS>;
-  constexpr int NV = C::NV, NT = C::NT, KT = Q::KT, MTA = Q::MTA, MTC = Q::MTC, CB = Q::CB, NTB = Q::NTB;
+  constexpr int NV = C::NV, NT = C::NT, KT = Q::KT, MTA = Q::MTA, MTC = Q::MTC, CB = Q::CB;
   constexpr int RT = Q::RT, CT = Q::CT, LDA = Q::LDA, NWARP = NTHREADS / 32;
-  constexpr int NJ = NTHREADS >= 512 ? 1 : 2;  // column tiles per warp task (register budget)
   extern __shared__ double smem_d[];
   df2* Xb = reinterpret_cast<df2*>(smem_d);                 // [NV][CB] current X block
-  uint2* Xs = reinterpret_cast<uint2*>(Xb + NV * CB);       // [KT][NTB][OZS][32] X slices
+  uint4* Xs = reinterpret_cast<uint4*>(Xb + NV * CB);       // [KT][NMB][OZS][32] slices of X^T
   float* Rk = reinterpret_cast<float*>(Xs);                 // [NV][CB] residual (aliases Xs)
   float* Dk = Rk + NV * CB;                                 // [NV][CB] correction (aliases Xs)
   // FP32 matrices stored transposed ([k][r], leading dimension LDA, zero past NV)
@@ -338,8 +340,8 @@ __global__ void __launch_bounds__(NTHREADS) k_condense_tc(AssembleArgs a) {
   const int64_t le = blockIdx.x;
   const int64_t e = a.e0 + le;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const uint4* slA = a.oz + le * Q::slice_uint4;
-  const uint4* slC = slA + (size_t)MTA * KT * OZS * 32;
+  const uint2* slA = reinterpret_cast<const uint2*>(a.oz) + le * Q::slice_u2;
+  const uint2* slC = slA + (size_t)Q::NTA * KT * OZS * 32;
   double* Xg = a.recov + e * (int64_t)(NV * NT + NV);  // B' (double-float) in, X out
   const df2* Bd = reinterpret_cast<const df2*>(Xg);
   double* yg = Xg + NV * NT;
@@ -368,19 +370,19 @@ __global__ void __launch_bounds__(NTHREADS) k_condense_tc(AssembleArgs a) {
       if (lane == 0) eX[c] = oz_exponent(mx);
     }
   };
-  auto slice_X = [&](int nnt) {
-    auto getX = [&](int k, int n) { return k < NV ? Xb[k * CB + n] : df2{0.f, 0.f}; };
-    auto sX = [&](int n) { return oz_scale(eX[n]); };
-    for (int u = warp; u < KT * nnt; u += NWARP) {
-      const int kt = u / nnt, nt = u % nnt;
-      oz_slice_right_tile<OZS>(Xs + (kt * NTB + nt) * OZS * 32, 32, kt * 16, nt * 8, lane, getX, sX);
+  auto slice_X = [&](int nmt) {  // X^T of the block as the left operand
+    auto getX = [&](int c, int k) { return k < NV ? Xb[k * CB + c] : df2{0.f, 0.f}; };
+    auto sX = [&](int c) { return oz_scale(eX[c]); };
+    for (int u = warp; u < KT * nmt; u += NWARP) {
+      const int kt = u / nmt, m = u % nmt;
+      oz_slice_left_tile<OZS>(Xs + (kt * Q::NMB + m) * OZS * 32, 32, m * 16, kt * 16, lane, getX, sX);
     }
   };
 
   // ---- blocks of right-hand sides
   for (int c0 = 0; c0 < NT + 1; c0 += CB) {
     const int nc = (NT + 1 - c0) < CB ? (NT + 1 - c0) : CB;
-    const int nnt = (nc + 7) / 8;
+    const int nmt = (nc + 15) / 16;
     auto bval = [&](int r, int c) -> df2 {  // B' column or R_v, zero past the block
       const int col = c0 + c;
       if (c >= nc) return df2{0.f, 0.f};
@@ -404,10 +406,10 @@ __global__ void __launch_bounds__(NTHREADS) k_condense_tc(AssembleArgs a) {
     __syncthreads();
     col_exponents();
     __syncthreads();
-    slice_X(nnt);
+    slice_X(nmt);
     __syncthreads();
     // r0 = B - A' X0 (exact slices), staged in W (the products read Xs, which Rk aliases)
-    cond_oz_product<KT, NTB, OZS, NWARP, NJ>(slA, MTA, Xs, nnt, [&](int row, int col, const dfacc& v) {
+    cond_oz_product<KT, Q::NMB, OZS, NWARP>(slA, Q::NTA, Xs, nmt, [&](int row, int col, const dfacc& v) {
       if (row < NV) {
         const df2 p = oz_scaled(v, eA[row] + eX[col]);
         dfacc t;
@@ -472,7 +474,7 @@ __global__ void __launch_bounds__(NTHREADS) k_condense_tc(AssembleArgs a) {
     for (int t = tid; t < NV * CB; t += NTHREADS) {
       const int r = t / CB, c = t % CB, col = c0 + c;
       if (c < nc) {
-        const double xv = df_val(Xb[t]);
+        const double xv = df_to_f64(Xb[t].hi, Xb[t].lo);
         if (col < NT)
           Xg[r * NT + col] = xv;
         else
@@ -481,10 +483,10 @@ __global__ void __launch_bounds__(NTHREADS) k_condense_tc(AssembleArgs a) {
     }
     col_exponents();
     __syncthreads();
-    slice_X(nnt);
+    slice_X(nmt);
     __syncthreads();
     // S[:, block] = D' - C' X ; g = R_t - C' y
-    cond_oz_product<KT, NTB, OZS, NWARP, NJ>(slC, MTC, Xs, nnt, [&](int row, int col, const dfacc& v) {
+    cond_oz_product<KT, Q::NMB, OZS, NWARP>(slC, Q::NTC, Xs, nmt, [&](int row, int col, const dfacc& v) {
       const int gc = c0 + col;
       if (row >= NT || col >= nc) return;
       const df2 p = oz_scaled(v, eC[row] + eX[col]);
@@ -495,9 +497,9 @@ __global__ void __launch_bounds__(NTHREADS) k_condense_tc(AssembleArgs a) {
         t.add(df_from(R[NV + row]));
       t.add(df2{-p.hi, -p.lo});
       if (gc < NT)
-        S[row * NT + gc] = t.value();
+        S[row * NT + gc] = df_to_f64(t.hi, t.lo);
       else
-        a.g[e * NT + row] = t.value();
+        a.g[e * NT + row] = df_to_f64(t.hi, t.lo);
     });
     __syncthreads();
   }

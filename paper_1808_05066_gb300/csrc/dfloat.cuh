@@ -49,4 +49,21 @@ struct dfacc {
   }
 };
 
+// Exact double of a float built from its bit fields on the integer pipe (the FP64 pipe of
+// GB300 runs at 1/64 of the FP32 rate); zero and normal numbers; other classes take the
+// conversion instruction.
+HDG_DEVI double f32_to_f64_bits(float x) {
+  const unsigned u = __float_as_uint(x);
+  const unsigned ex = (u >> 23) & 0xffu;
+  const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
+  if (ex == 0u && (u << 1) == 0u) return __longlong_as_double((long long)sign);
+  if (ex == 0u || ex == 0xffu) return (double)x;
+  const unsigned long long bits = sign | ((unsigned long long)(ex + 896u) << 52) |  // 1023 - 127
+                                  ((unsigned long long)(u & 0x7fffffu) << 29);
+  return __longlong_as_double((long long)bits);
+}
+
+// hi + lo of a double-float in FP64: one FP64 addition.
+HDG_DEVI double df_to_f64(float hi, float lo) { return f32_to_f64_bits(hi) + f32_to_f64_bits(lo); }
+
 }  // namespace hdg
