@@ -263,55 +263,66 @@ __global__ void __launch_bounds__(AsmTC<C, S, MTC, NJW>::NTH, AsmTC<C, S, MTC, N
   const uint2* rbg = reinterpret_cast<const uint2*>(a.rb) + le * Q::rb_u2;
   const int* exg = reinterpret_cast<const int*>(rbg + Q::vol_u2 + C::NF * Q::face_u2);
 
-  // stage T0, T1, T2 of the il pairs this block touches; row exponents from FP32 bounds
+  // stage T0, T1, T2 of the il pairs this block touches and the basis tables (asynchronous
+  // copies, all in flight together); row exponents from FP32 bounds
   for (int t = tid; t < NG * NILV * NTS; t += NTH) {
     const int q = t % NTS, ilr = (t / NTS) % NILV, g = t / (NTS * NILV);
     const int il = il_lo + ilr;
-    df2 v{0.f, 0.f};
     if (il < M * M) {
       const int i = il / M, l = il % M;
       const df2* P = ptv + g * C::PT_VOL + M + D * M;
+      int off;
       if (q == 0)
-        v = P[i * M + l];
+        off = i * M + l;
       else if (q <= D)
-        v = P[M * M + ((q - 1) * M + i) * M + l];
+        off = M * M + ((q - 1) * M + i) * M + l;
       else {
         const int r = (q - 1 - D) / D, k = (q - 1 - D) % D;
-        v = P[M * M + D * M * M + ((r * M + i) * M + l) * D + k];
+        off = M * M + D * M * M + ((r * M + i) * M + l) * D + k;
       }
+      cp_async8(Ts + t, P + off);
+    } else {
+      Ts[t] = df2{0.f, 0.f};
     }
-    Ts[t] = v;
   }
   for (int t = tid; t < (1 + D) * NG * NP; t += NTH) {
     const int gr = t / NP, an = t % NP;  // gr = r * NG + g over Phi, then dPhi_r
-    Ps[gr * Q::NPP + an] = gr < NG ? TD.Phi[t] : TD.dPhi[t - NG * NP];
+    cp_async8(Ps + gr * Q::NPP + an, gr < NG ? TD.Phi + t : TD.dPhi + (t - NG * NP));
   }
-  for (int t = tid; t < ROWS; t += NTH) eR[t] = 0;
+  cp_async_commit();
   for (int t = tid; t < NC; t += NTH) eC[t] = exg[t];
+  cp_async_wait_all();
   __syncthreads();
   constexpr int NPP = Q::NPP;
   const df2* Phi = Ps;              // [NG][NPP]
   const df2* dPhi = Ps + NG * NPP;  // [D][NG][NPP]
   {
-    float* bR = reinterpret_cast<float*>(eR);  // bounds first, exponents after
-    for (int t = tid; t < ROWS * NG; t += NTH) {
-      const int rl = t % ROWS, g = t / ROWS, row = row0 + rl;
-      if (row >= Q::RV) continue;
+    // threads per row: the largest power of two in NTH / ROWS (consecutive lanes of one warp)
+    constexpr int TPR = (NTH / ROWS) >= 8 ? 8 : ((NTH / ROWS) >= 4 ? 4 : ((NTH / ROWS) >= 2 ? 2 : 1));
+    const int rl = tid / TPR, part = tid % TPR, row = row0 + rl;
+    float b = 0.f;
+    if (rl < ROWS && row < Q::RV) {
       const int an = row % NP, ilr = row / NP - il_lo;
-      const df2* Tp = Ts + (g * NILV + ilr) * NTS;
-      float b = fabsf(Phi[g * NPP + an].hi) * fabsf(Tp[0].hi);
-      for (int r = 0; r < D; ++r) b = fmaf(fabsf(dPhi[(r * NG + g) * NPP + an].hi), fabsf(Tp[1 + r].hi), b);
-      if constexpr (C::VISC)
-        for (int k = 0; k < D; ++k) {
-          float bk = 0.f;
-          for (int r = 0; r < D; ++r)
-            bk = fmaf(fabsf(dPhi[(r * NG + g) * NPP + an].hi), fabsf(Tp[1 + D + r * D + k].hi), bk);
-          b = fmaxf(b, bk);
-        }
-      if (b > 0.f) atomicMax(reinterpret_cast<int*>(&bR[rl]), __float_as_int(b));
+      for (int g = part; g < NG; g += TPR) {
+        const df2* Tp = Ts + (g * NILV + ilr) * NTS;
+        float b0 = fabsf(Phi[g * NPP + an].hi) * fabsf(Tp[0].hi);
+#pragma unroll
+        for (int r = 0; r < D; ++r) b0 = fmaf(fabsf(dPhi[(r * NG + g) * NPP + an].hi), fabsf(Tp[1 + r].hi), b0);
+        b = fmaxf(b, b0);
+        if constexpr (C::VISC)
+#pragma unroll
+          for (int k = 0; k < D; ++k) {
+            float bk = 0.f;
+#pragma unroll
+            for (int r = 0; r < D; ++r)
+              bk = fmaf(fabsf(dPhi[(r * NG + g) * NPP + an].hi), fabsf(Tp[1 + D + r * D + k].hi), bk);
+            b = fmaxf(b, bk);
+          }
+      }
     }
-    __syncthreads();
-    for (int t = tid; t < ROWS; t += NTH) eR[t] = oz_exponent(bR[t] * 1.0001f);
+#pragma unroll
+    for (int off = 1; off < TPR; off <<= 1) b = fmaxf(b, __shfl_xor_sync(0xffffffffu, b, off));
+    if (part == 0 && rl < ROWS) eR[rl] = oz_exponent(b * 1.0001f);
     __syncthreads();
   }
 
@@ -385,7 +396,19 @@ __global__ void __launch_bounds__(AsmTC<C, S, MTC, NJW>::NTH, AsmTC<C, S, MTC, N
 #pragma unroll
         for (int q = 0; q < 4; ++q) acc[jj][d][q] = 0.f;
   };
-  // flush: the exact diagonals into the double-float output (store first, then add)
+  // flush: the exact diagonals into the double-float output (store first, then add). A lane's
+  // two output rows (an, i) and component l are fixed: computed once.
+  df2* const Aout = reinterpret_cast<df2*>(a.Ap) + le * NV * NV;
+  df2* const Bout = reinterpret_cast<df2*>(a.recov + e * (int64_t)(NV * NT + NV));
+  int f_row[2], f_l[2], f_rl[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int rl = mt * 16 + (lane >> 2) + 8 * h, row = row0 + rl;
+    const int an = row % NP, il = row / NP;
+    f_rl[h] = rl;
+    f_row[h] = row < Q::RV ? an * M + il / M : -1;
+    f_l[h] = il % M;
+  }
   auto flush = [&](bool first) {
 #pragma unroll
     for (int jj = 0; jj < NJW; ++jj) {
@@ -393,15 +416,12 @@ __global__ void __launch_bounds__(AsmTC<C, S, MTC, NJW>::NTH, AsmTC<C, S, MTC, N
       if (nt >= NTN) continue;
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const int rl = mt * 16 + (lane >> 2) + 8 * (q >> 1), row = row0 + rl;
+        const int h = q >> 1, rl = f_rl[h];
         const int j = nt * 8 + 2 * (lane & 3) + (q & 1);
-        if (row >= Q::RV || j >= C::NZ) continue;
+        if (f_row[h] < 0 || j >= C::NZ) continue;
         const dfacc v = oz_combine<S>(acc[jj], q);
         const df2 p = oz_scaled(v, eR[rl] + eC[j]);
-        const int an = row % NP, il = row / NP, i = il / M, l = il % M;
-        df2* dst = j < NP ? reinterpret_cast<df2*>(a.Ap) + le * NV * NV + (an * M + i) * NV + j * M + l
-                          : reinterpret_cast<df2*>(a.recov + e * (int64_t)(NV * NT + NV)) + (an * M + i) * NT +
-                                (j - NP) * M + l;
+        df2* dst = j < NP ? Aout + f_row[h] * NV + j * M + f_l[h] : Bout + f_row[h] * NT + (j - NP) * M + f_l[h];
         if (first) {
           *dst = p;
         } else {
@@ -475,24 +495,26 @@ __global__ void __launch_bounds__(AsmTC<C, S, MTC, NJW>::NTH, AsmTC<C, S, MTC, N
   };
 
   // U and the face basis of every face, the A', B' accumulator, row and column exponents
-  for (int t = tid; t < NF * NGF * QIL * NRF; t += NTH) {
+  for (int t = tid; t < NF * NGF * QIL * NRF; t += NTH) {  // asynchronous copies, all in flight
     const int beta = t % NRF, ilr = (t / NRF) % QIL, gf = (t / (NRF * QIL)) % NGF, f = t / (NRF * QIL * NGF);
     const int il = il0 + ilr;
-    df2 v{0.f, 0.f};
     if (il < M * M) {
       const int i = il / M, l = il % M;
       const df2* U0 = ptf + (f * NGF + gf) * C::PT_FACE + M;
-      v = beta == 0 ? U0[i * M + l] : (beta == 1 ? U0[M * M + i * M + l] : U0[2 * M * M + (i * M + l) * D + (beta - 2)]);
+      cp_async8(Us + t, U0 + (beta == 0 ? i * M + l : (beta == 1 ? M * M + i * M + l : 2 * M * M + (i * M + l) * D + (beta - 2))));
+    } else {
+      Us[t] = df2{0.f, 0.f};
     }
-    Us[t] = v;
   }
   for (int t = tid; t < NF * NGF * NFN; t += NTH) {
     const int c = t % NFN, gf = (t / NFN) % NGF, f = t / (NFN * NGF);
-    Psi[t] = TD.PhiF[(f * NGF + gf) * NP + T.fnodes[f * NFN + c]];
+    cp_async8(Psi + t, TD.PhiF + (f * NGF + gf) * NP + T.fnodes[f * NFN + c]);
   }
+  cp_async_commit();
   for (int t = tid; t < QIL * NP * NZ; t += NTH) Acc[t] = df2{0.f, 0.f};
   for (int t = tid; t < NF * ROWS; t += NTH) eR[t] = 0;
   for (int t = tid; t < NF * NC; t += NTH) eC[t] = exg[NC + t];
+  cp_async_wait_all();
   __syncthreads();
   {
     float* bR = reinterpret_cast<float*>(eR);
