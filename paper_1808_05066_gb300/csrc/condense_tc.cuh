@@ -40,8 +40,8 @@ struct CondTC {
   static constexpr size_t slice_uint4 = slice_u2 / 2;
   static constexpr size_t xs_bytes = sizeof(uint4) * KT * NMB * OZS * 32;
   static_assert(xs_bytes >= sizeof(float) * 2 * NV * CB, "residual buffers alias the slice buffer");
-  static constexpr size_t bytes = sizeof(float) * (2 * NV * LDA + NV * CB + NV) + sizeof(df2) * NV * CB + xs_bytes +
-                                  sizeof(int) * (NV + MTA * 16 + MTC * 16 + CB) + 64;
+  static constexpr size_t bytes = sizeof(float) * (2 * NV * LDA + NV * CB + NV) + sizeof(df2) * (NV + NT) * CB +
+                                  xs_bytes + sizeof(int) * (NV + MTA * 16 + MTC * 16 + CB) + 64;
   // per-element block written by k_condense_prep: Ai^T, A'^T [NV][LDA], sc [LDA], eA, eC
   static constexpr int PREP_AI = 0, PREP_AH = NV * LDA, PREP_SC = 2 * NV * LDA, PREP_EA = PREP_SC + LDA,
                        PREP_EC = PREP_EA + MTA * 16;
@@ -323,7 +323,8 @@ __global__ void __launch_bounds__(NTHREADS) k_condense_tc(AssembleArgs a) {
   constexpr int NV = C::NV, NT = C::NT, KT = Q::KT, MTA = Q::MTA, MTC = Q::MTC, CB = Q::CB;
   constexpr int RT = Q::RT, CT = Q::CT, LDA = Q::LDA, NWARP = NTHREADS / 32;
   extern __shared__ double smem_d[];
-  df2* Xb = reinterpret_cast<df2*>(smem_d);                 // [NV][CB] current X block
+  df2* Ds = reinterpret_cast<df2*>(smem_d);                 // [NT][CB] D' columns of the block
+  df2* Xb = Ds + NT * CB;                                   // [NV][CB] current X block
   uint4* Xs = reinterpret_cast<uint4*>(Xb + NV * CB);       // [KT][NMB][OZS][32] slices of X^T
   float* Rk = reinterpret_cast<float*>(Xs);                 // [NV][CB] residual (aliases Xs)
   float* Dk = Rk + NV * CB;                                 // [NV][CB] correction (aliases Xs)
@@ -383,6 +384,12 @@ __global__ void __launch_bounds__(NTHREADS) k_condense_tc(AssembleArgs a) {
   for (int c0 = 0; c0 < NT + 1; c0 += CB) {
     const int nc = (NT + 1 - c0) < CB ? (NT + 1 - c0) : CB;
     const int nmt = (nc + 15) / 16;
+    // the block's D' columns, read by the Schur epilogue, copied in the background meanwhile
+    for (int t = tid; t < NT * CB; t += NTHREADS) {
+      const int r = t / CB, c = t % CB;
+      if (c < nc && c0 + c < NT) cp_async8(Ds + t, Dd + (size_t)r * NT + c0 + c);
+    }
+    cp_async_commit();
     auto bval = [&](int r, int c) -> df2 {  // B' column or R_v, zero past the block
       const int col = c0 + c;
       if (c >= nc) return df2{0.f, 0.f};
@@ -484,6 +491,7 @@ __global__ void __launch_bounds__(NTHREADS) k_condense_tc(AssembleArgs a) {
     col_exponents();
     __syncthreads();
     slice_X(nmt);
+    cp_async_wait_all();
     __syncthreads();
     // S[:, block] = D' - C' X ; g = R_t - C' y
     cond_oz_product<KT, Q::NMB, OZS, NWARP>(slC, Q::NTC, Xs, nmt, [&](int row, int col, const dfacc& v) {
@@ -492,7 +500,7 @@ __global__ void __launch_bounds__(NTHREADS) k_condense_tc(AssembleArgs a) {
       const df2 p = oz_scaled(v, eC[row] + eX[col]);
       dfacc t;
       if (gc < NT)
-        t.add(Dd[row * NT + gc]);
+        t.add(Ds[row * CB + col]);
       else
         t.add(df_from(R[NV + row]));
       t.add(df2{-p.hi, -p.lo});
