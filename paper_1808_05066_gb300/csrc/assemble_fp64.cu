@@ -60,6 +60,11 @@ int run_fp64(hdg_ctx* ctx, const double* V, const double* Vhat, const double* hi
     a.e0 = e0;
     a.ne = std::min<int64_t>(ch, ctx->E - e0);
     {
+      int rc_s = HDG_OK;
+      a.S = chunk_S(ctx, S, e0, s, &rc_s);
+      if (rc_s) return rc_s;
+    }
+    {
       LaunchScope ls(ctx, HDG_KERNEL_POINTWISE, s);
       k_pointwise<C><<<(unsigned)a.ne, pw_threads, 0, s>>>(a, ctx->T, ctx->ph);
     }
@@ -71,6 +76,7 @@ int run_fp64(hdg_ctx* ctx, const double* V, const double* Vhat, const double* hi
       LaunchScope ls(ctx, HDG_KERNEL_CONDENSE, s);
       k_condense<C><<<(unsigned)a.ne, 256, CondSmem<C>::bytes, s>>>(a);
     }
+    if (int rc_d = chunk_done(ctx, e0, a.ne, s)) return rc_d;
   }
   HDG_CK(cudaGetLastError());
   return HDG_OK;

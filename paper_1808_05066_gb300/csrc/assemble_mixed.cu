@@ -178,6 +178,11 @@ int run_mixed(hdg_ctx* ctx, const double* V, const double* Vhat, const double* h
     a.e0 = e0;
     a.ne = std::min<int64_t>(ch, ctx->E - e0);
     {
+      int rc_s = HDG_OK;
+      a.S = chunk_S(ctx, S, e0, s, &rc_s);
+      if (rc_s) return rc_s;
+    }
+    {
       LaunchScope ls(ctx, HDG_KERNEL_POINTWISE, s);
       k_pointwise<C, df2><<<(unsigned)a.ne, pw_threads, 0, s>>>(a, ctx->T, ctx->ph);
     }
@@ -247,6 +252,7 @@ int run_mixed(hdg_ctx* ctx, const double* V, const double* Vhat, const double* h
       LaunchScope ls(ctx, HDG_KERNEL_MIXED_CONDENSE, s);
       cv.kernel<<<(unsigned)a.ne, cv.threads, cv.smem, s>>>(a);
     }
+    if (int rc_d = chunk_done(ctx, e0, a.ne, s)) return rc_d;
   }
   HDG_CK(cudaGetLastError());
   return HDG_OK;

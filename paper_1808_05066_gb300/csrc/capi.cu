@@ -48,6 +48,52 @@ int upload(T** dst, const std::vector<T>& src) {
 
 }  // namespace
 
+namespace hdg {
+
+double* chunk_S(hdg_ctx* c, double* S, int64_t e0, cudaStream_t s, int* rc) {
+  *rc = HDG_OK;
+  if (!c->sink_host) return S;
+  const size_t per = (size_t)c->NT * c->NT;
+  if (c->Sbuf_chunk < c->chunk) {  // first use, or a larger chunk: (re)allocate both buffers
+    cudaStreamSynchronize(c->copy_stream);
+    for (double*& b : c->d_Sbuf) {
+      if (b) cudaFree(b);
+      b = nullptr;
+    }
+    c->Sbuf_chunk = 0;
+    for (double*& b : c->d_Sbuf) {
+      if (cudaMalloc(&b, sizeof(double) * per * c->chunk) != cudaSuccess) {
+        set_error("hdg_assemble_condense_host: cannot allocate the chunk buffers of S");
+        *rc = HDG_ERR_CUDA;
+        return nullptr;
+      }
+    }
+    c->Sbuf_chunk = c->chunk;
+  }
+  const int b = c->sink_idx & 1;
+  if (c->sink_idx >= 2 && cudaStreamWaitEvent(s, c->ev_copied[b], 0) != cudaSuccess) {  // buffer copied out
+    *rc = HDG_ERR_CUDA;
+    return nullptr;
+  }
+  // the kernels index S by the global element: shift the buffer's address by e0 elements
+  return reinterpret_cast<double*>(reinterpret_cast<uintptr_t>(c->d_Sbuf[b]) - (uintptr_t)(e0 * per * sizeof(double)));
+}
+
+int chunk_done(hdg_ctx* c, int64_t e0, int64_t ne, cudaStream_t s) {
+  if (!c->sink_host) return HDG_OK;
+  const int b = c->sink_idx & 1;
+  const size_t per = (size_t)c->NT * c->NT;
+  HDG_CK(cudaEventRecord(c->ev_done[b], s));
+  HDG_CK(cudaStreamWaitEvent(c->copy_stream, c->ev_done[b], 0));
+  HDG_CK(cudaMemcpyAsync(c->sink_host + e0 * per, c->d_Sbuf[b], sizeof(double) * per * ne, cudaMemcpyDeviceToHost,
+                         c->copy_stream));
+  HDG_CK(cudaEventRecord(c->ev_copied[b], c->copy_stream));
+  ++c->sink_idx;
+  return HDG_OK;
+}
+
+}  // namespace hdg
+
 extern "C" {
 
 const char* hdg_last_error(void) { return hdg::g_last_error.c_str(); }
@@ -245,6 +291,15 @@ void hdg_ctx_destroy(hdg_ctx_t c) {
     if (b) cudaFree(b);
   if (c->h_red) cudaFreeHost(c->h_red);
   if (c->lu_graph_exec) cudaGraphExecDestroy(c->lu_graph_exec);
+  if (c->copy_stream) {
+    cudaStreamSynchronize(c->copy_stream);
+    cudaStreamDestroy(c->copy_stream);
+    for (int b = 0; b < 2; ++b) {
+      cudaEventDestroy(c->ev_done[b]);
+      cudaEventDestroy(c->ev_copied[b]);
+      if (c->d_Sbuf[b]) cudaFree(c->d_Sbuf[b]);
+    }
+  }
   for (auto& r : c->pending) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
@@ -289,6 +344,41 @@ int hdg_assemble_condense(hdg_ctx_t ctx, const double* V, const double* Vhat, co
   if (precision == HDG_PREC_MIXED)
     return hdg::assemble_condense_mixed(ctx, V, Vhat, hist, mass_coef, S, g, recov, R, st, s);
   return hdg::assemble_condense_fp64(ctx, V, Vhat, hist, mass_coef, S, g, recov, R, st, s);
+}
+
+
+int hdg_assemble_condense_host(hdg_ctx_t ctx, const double* V, const double* Vhat, const double* hist,
+                               double mass_coef, int precision, double* S_host, double* g_host, double* recov,
+                               double* R, int32_t* elem_status, void* stream) {
+  HDG_REQUIRE(ctx && V && Vhat && S_host && g_host && recov && R, "hdg_assemble_condense_host: null argument");
+  HDG_REQUIRE(precision == HDG_PREC_FP64 || precision == HDG_PREC_MIXED, "hdg_assemble_condense_host: precision");
+  DeviceGuard guard(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!ctx->copy_stream) {
+    HDG_CK(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+    for (int b = 0; b < 2; ++b) {
+      HDG_CK(cudaEventCreateWithFlags(&ctx->ev_done[b], cudaEventDisableTiming));
+      HDG_CK(cudaEventCreateWithFlags(&ctx->ev_copied[b], cudaEventDisableTiming));
+    }
+  }
+  if (!ctx->d_g) HDG_CK(cudaMalloc(&ctx->d_g, sizeof(double) * ctx->E * ctx->NT));
+  int32_t* st = elem_status;
+  if (!st) {
+    if (!ctx->d_status) HDG_CK(cudaMalloc(&ctx->d_status, sizeof(int32_t) * ctx->E));
+    HDG_CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int32_t) * ctx->E, s));
+    st = ctx->d_status;
+  }
+  ctx->sink_host = S_host;
+  ctx->sink_idx = 0;
+  int rc = precision == HDG_PREC_MIXED
+               ? hdg::assemble_condense_mixed(ctx, V, Vhat, hist, mass_coef, nullptr, ctx->d_g, recov, R, st, s)
+               : hdg::assemble_condense_fp64(ctx, V, Vhat, hist, mass_coef, nullptr, ctx->d_g, recov, R, st, s);
+  const int used = ctx->sink_idx;
+  ctx->sink_host = nullptr;
+  if (rc) return rc;
+  HDG_CK(cudaMemcpyAsync(g_host, ctx->d_g, sizeof(double) * ctx->E * ctx->NT, cudaMemcpyDeviceToHost, s));
+  for (int b = 0; b < 2 && b < used; ++b) HDG_CK(cudaStreamWaitEvent(s, ctx->ev_copied[b], 0));
+  return HDG_OK;
 }
 
 int hdg_trace_solve(hdg_ctx_t ctx, const double* S, const double* g, double* dVhat, int method, double rtol,
@@ -385,7 +475,7 @@ int hdg_newton_step(hdg_ctx_t ctx, double* V, double* Vhat, const double* hist, 
   const int64_t E = ctx->E;
   if (!ctx->d_S) {
     HDG_CK(cudaMalloc(&ctx->d_S, sizeof(double) * E * ctx->NT * ctx->NT));
-    HDG_CK(cudaMalloc(&ctx->d_g, sizeof(double) * E * ctx->NT));
+    if (!ctx->d_g) HDG_CK(cudaMalloc(&ctx->d_g, sizeof(double) * E * ctx->NT));
     HDG_CK(cudaMalloc(&ctx->d_recov, sizeof(double) * E * (ctx->NV * ctx->NT + ctx->NV)));
     HDG_CK(cudaMalloc(&ctx->d_R, sizeof(double) * E * (ctx->NV + ctx->NT)));
     HDG_CK(cudaMalloc(&ctx->d_dV, sizeof(double) * E * ctx->NV));

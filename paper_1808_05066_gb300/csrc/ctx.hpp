@@ -49,6 +49,15 @@ struct hdg_ctx {
   cudaGraphExec_t lu_graph_exec = nullptr;  // recorded pivot/scale/update sequence
   double* d_red = nullptr;   // reduction buffer (device)
   double* h_red = nullptr;   // pinned host mirror
+  // streaming of S to host memory (hdg_assemble_condense_host): while `sink_host` is set, the
+  // element chunks write S into two device buffers in turn and each chunk's S is copied to the
+  // host on `copy_stream` while the next chunk computes
+  double* sink_host = nullptr;
+  int sink_idx = 0;
+  double* d_Sbuf[2] = {nullptr, nullptr};
+  int64_t Sbuf_chunk = 0;  // elements per buffer
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_done[2] = {nullptr, nullptr}, ev_copied[2] = {nullptr, nullptr};
   // Newton workspace
   double *d_S = nullptr, *d_g = nullptr, *d_recov = nullptr, *d_R = nullptr, *d_dV = nullptr, *d_dVh = nullptr;
   int32_t* d_status = nullptr;
@@ -96,6 +105,11 @@ struct LaunchScope {
     }
   }
 };
+
+// Chunk loops of assemble + condense: the S array a chunk [e0, e0 + ne) writes (indexed by the
+// global element, as the kernels do), and the end of the chunk's launches (capi.cu).
+double* chunk_S(hdg_ctx* ctx, double* S, int64_t e0, cudaStream_t s, int* rc);
+int chunk_done(hdg_ctx* ctx, int64_t e0, int64_t ne, cudaStream_t s);
 
 // assemble + condense (assemble_fp64.cu / assemble_mixed.cu)
 int assemble_condense_fp64(hdg_ctx* ctx, const double* V, const double* Vhat, const double* hist, double mass_coef,

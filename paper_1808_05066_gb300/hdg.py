@@ -37,7 +37,7 @@ EXPORTED = [
     "hdg_profile_reset", "hdg_profile_read", "hdg_last_error", "hdg_assemble_condense_noalloc",
     "hdg_mlp_param_count", "hdg_mlp_init", "hdg_mlp_features", "hdg_mlp_forward", "hdg_mlp_gradient",
     "hdg_mlp_train_step", "hdg_mlp_apply_trace", "hdg_mlp_stats", "hdg_mlp_standardize", "hdg_mlp_target",
-    "hdg_axpby",
+    "hdg_axpby", "hdg_assemble_condense_host",
 ]
 HDG_KERNEL_POINTWISE = 0
 HDG_KERNEL_ASSEMBLE = 1
@@ -109,6 +109,7 @@ def _load():
         "hdg_profile_read": (c_int, [P, c_int, POINTER(c_int64), POINTER(c_double)]),
         "hdg_last_error": (ctypes.c_char_p, []),
         "hdg_assemble_condense_noalloc": (c_int, [P, P, P, P, c_double, P, P, P, P, P, P]),
+        "hdg_assemble_condense_host": (c_int, [P, P, P, P, c_double, c_int, P, P, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -208,6 +209,15 @@ def hdg_assemble_condense(ctx, V, Vhat, hist, mass_coef, precision, S, g, recov,
                           stream=None):
     _check(_lib.hdg_assemble_condense(ctx, _ptr(V), _ptr(Vhat), _ptr(hist), mass_coef, precision, _ptr(S),
                                       _ptr(g), _ptr(recov), _ptr(R), _ptr(elem_status), _stream(stream)))
+
+
+def hdg_assemble_condense_host(ctx, V, Vhat, hist, mass_coef, precision, S_host, g_host, recov, R,
+                               elem_status=None, stream=None):
+    """hdg_assemble_condense with S and g written to host memory (S_host, g_host: CPU tensors,
+    pinned for the copies to overlap the kernels); complete once the stream is synchronised."""
+    _check(_lib.hdg_assemble_condense_host(ctx, _ptr(V), _ptr(Vhat), _ptr(hist), mass_coef, precision,
+                                           _ptr(S_host), _ptr(g_host), _ptr(recov), _ptr(R), _ptr(elem_status),
+                                           _stream(stream)))
 
 
 def hdg_assemble_condense_noalloc(ctx, V, Vhat, hist, mass_coef, S, g, recov, R, elem_status, stream=None):

@@ -81,6 +81,13 @@ class DeviceWorkload:
                                   self.hist, self.mass_coef, precision, self.S, self.g, self.recov, self.R,
                                   self.status, stream)
 
+    def assemble_to_host(self, S_host, g_host, precision=hdg.HDG_PREC_FP64, V=None, Vhat=None, stream=None):
+        """The same call with S and g delivered to (pinned) host memory, copied chunk by chunk
+        while the next chunk computes."""
+        hdg.hdg_assemble_condense_host(self.ctx.handle, self.V if V is None else V,
+                                       self.Vhat if Vhat is None else Vhat, self.hist, self.mass_coef, precision,
+                                       S_host, g_host, self.recov, self.R, self.status, stream)
+
     @property
     def n_elem(self):
         return self.info["n_elem"]

@@ -171,6 +171,32 @@ def test_mixed_chunked_launch_ragged_tail(monkeypatch):
     assert bool((gc2.S == S1).all()) and bool((gc2.recov == rec1).all()) and bool((gc2.g == g1).all())
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_host_output_streaming_equals_device_output(precision, monkeypatch):
+    """hdg_assemble_condense_host (S and g copied to pinned host memory chunk by chunk while the
+    next chunk computes) gives the device entry point's S, g, X and R bit for bit, with chunks of
+    7 elements (18 full chunks and a ragged tail: both device buffers reused many times), on
+    two calls in a row."""
+    monkeypatch.setenv("HDG_ELEMENT_CHUNK", "7")
+    case = CASES["euler2d_p2"]
+    gc = GpuCase(case)
+    hist = gc.history()
+    gc.assemble(hist, precision=precision)
+    S_ref, g_ref, rec_ref, R_ref = gc.S.cpu(), gc.g.cpu(), gc.recov.clone(), gc.R.clone()
+    torch = gc.torch
+    S_host = torch.full(tuple(gc.S.shape), float("nan"), dtype=torch.float64).pin_memory()
+    g_host = torch.full(tuple(gc.g.shape), float("nan"), dtype=torch.float64).pin_memory()
+    for _ in range(2):
+        gc.recov.zero_()
+        gc.R.zero_()
+        gc.hdg.hdg_assemble_condense_host(gc.ctx.handle, gc.V, gc.Vhat, hist, case.mass_coef, precision, S_host,
+                                          g_host, gc.recov, gc.R, gc.status)
+        torch.cuda.synchronize()
+        assert bool((S_host == S_ref).all()) and bool((g_host == g_ref).all())
+        assert bool((gc.recov == rec_ref).all()) and bool((gc.R == R_ref).all())
+        S_host.fill_(float("nan"))
+
+
 def test_chunked_launch_ragged_tail(monkeypatch):
     """Element chunks of 7 over 128 elements (18 full chunks + a ragged tail of 2) give
     the same output as one chunk, bit for bit."""
