@@ -248,17 +248,14 @@ __global__ void __launch_bounds__(CondTC<C, 256, OZS>::PTH) k_condense_prep(Asse
   int* eA = reinterpret_cast<int*>(pre + Q::PREP_EA);
   int* eC = reinterpret_cast<int*>(pre + Q::PREP_EC);
 
-  // A'^T (FP32) in shared memory, row exponents of A' and C'
-  for (int r = warp; r < LDA; r += NWARP) {
-    float mx = 0.f;
-    for (int k = lane; k < NV; k += 32) {
-      const float v = r < NV ? Ap[r * NV + k].hi : 0.f;
-      G[k * LDA + r] = v;
-      mx = fmaxf(mx, fabsf(v));
-    }
-    for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-    if (lane == 0 && r < NV) eA[r] = oz_exponent(mx);
+  // A'^T (FP32 high words) into shared memory by asynchronous copies, all in flight together;
+  // the row exponents of C' meanwhile, then those of A' from shared memory
+  for (int t = tid; t < NV * NV; t += PTH) {
+    const int r = t / NV, k = t % NV;
+    cp_async4(G + k * LDA + r, &Ap[t].hi);
   }
+  cp_async_commit();
+  for (int t = tid; t < NV * (LDA - NV); t += PTH) G[(t / (LDA - NV)) * LDA + NV + t % (LDA - NV)] = 0.f;
   for (int r = NV + tid; r < MTA * 16; r += PTH) eA[r] = 0;
   for (int r = warp; r < MTC * 16; r += NWARP) {
     float mx = 0.f;
@@ -266,6 +263,14 @@ __global__ void __launch_bounds__(CondTC<C, 256, OZS>::PTH) k_condense_prep(Asse
       for (int k = lane; k < NV; k += 32) mx = fmaxf(mx, fabsf(Cp[r * NV + k].hi));
     for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
     if (lane == 0) eC[r] = oz_exponent(mx);
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  for (int r = warp; r < NV; r += NWARP) {
+    float mx = 0.f;
+    for (int k = lane; k < NV; k += 32) mx = fmaxf(mx, fabsf(G[k * LDA + r]));
+    for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    if (lane == 0) eA[r] = oz_exponent(mx);
   }
   __syncthreads();
   // A'^T out; equilibration sc = |diag A'|^-1/2 and the scaled transpose for the inverse

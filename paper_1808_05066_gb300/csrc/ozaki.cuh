@@ -161,6 +161,12 @@ HDG_DEVI void cp_async16(void* smem_dst, const void* gmem_src) {
 HDG_DEVI void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 HDG_DEVI void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+// Asynchronous 4-byte copy global -> shared (cp.async, L1-allocating).
+HDG_DEVI void cp_async4(void* smem_dst, const void* gmem_src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
+
 // Asynchronous 8-byte copy global -> shared (cp.async, L1-allocating).
 HDG_DEVI void cp_async8(void* smem_dst, const void* gmem_src) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
