@@ -57,8 +57,13 @@ struct AsmTC {
   static constexpr size_t zs_u4 = (size_t)MTC * S * 32;       // one k tile of Z slices
   static constexpr int NPP = NP | 1;                // odd row stride of the staged basis (banks)
   static constexpr int NPSI = (1 + D) * NG * NPP;  // Phi and dPhi of all volume points
+  // with one CTA per SM (64-row blocks) the first half-K result waits in shared memory for
+  // the second instead of a global read-modify-write
+  static constexpr bool FLUSH_SMEM = MTC >= 4 && KTV > KFLUSH;
+  static constexpr size_t flush_df2 = FLUSH_SMEM ? (size_t)ROWS * NTN * 8 : 0;
   static constexpr size_t vol_bytes = sizeof(uint4) * 2 * zs_u4 + sizeof(uint2) * 2 * stripe_u2 +
-                                      sizeof(df2) * (NG * NILV * NTS + NPSI) + sizeof(int) * (ROWS + NTN * 8) + 64;
+                                      sizeof(df2) * (NG * NILV * NTS + NPSI + flush_df2) +
+                                      sizeof(int) * (ROWS + NTN * 8) + 64;
   static constexpr size_t face_bytes =
       sizeof(uint4) * 2 * zs_u4 + sizeof(uint2) * 2 * stripe_u2 +
       sizeof(df2) * (NF * NGF * QIL * NRF + NF * NGF * NFN + QIL * NP * NZ) + sizeof(int) * NF * (ROWS + NTN * 8) + 64;
@@ -252,7 +257,8 @@ __global__ void __launch_bounds__(AsmTC<C, S, MTC, NJW>::NTH, AsmTC<C, S, MTC, N
   uint2* Rs = reinterpret_cast<uint2*>(Zs + 2 * Q::zs_u4);            // [2][NTN][S][32]
   df2* Ts = reinterpret_cast<df2*>(Rs + 2 * Q::stripe_u2);            // [NG][NILV][NTS]
   df2* Ps = Ts + NG * NILV * NTS;                                     // Phi [NG][NP], dPhi [D][NG][NP]
-  int* eR = reinterpret_cast<int*>(Ps + Q::NPSI);                     // [ROWS]
+  df2* Fb = Ps + Q::NPSI;                                             // [ROWS][NTN*8] first half-K result
+  int* eR = reinterpret_cast<int*>(Fb + Q::flush_df2);                // [ROWS]
   int* eC = eR + ROWS;                                                // [NC]
   const int64_t le = blockIdx.y;  // the element's row blocks are neighbours in launch order
   const int64_t e = a.e0 + le;
@@ -422,7 +428,17 @@ __global__ void __launch_bounds__(AsmTC<C, S, MTC, NJW>::NTH, AsmTC<C, S, MTC, N
         const dfacc v = oz_combine<S>(acc[jj], q);
         const df2 p = oz_scaled(v, eR[rl] + eC[j]);
         df2* dst = j < NP ? Aout + f_row[h] * NV + j * M + f_l[h] : Bout + f_row[h] * NT + (j - NP) * M + f_l[h];
-        if (first) {
+        if constexpr (Q::FLUSH_SMEM) {
+          df2& fb = Fb[rl * (NTN * 8) + j];  // this lane's own entry in both flushes
+          if (first) {
+            fb = p;
+          } else {
+            dfacc t;
+            t.add(fb);
+            t.add(p);
+            *dst = t.norm();
+          }
+        } else if (first) {
           *dst = p;
         } else {
           dfacc t;

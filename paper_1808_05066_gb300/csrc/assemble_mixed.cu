@@ -194,15 +194,17 @@ int run_mixed(hdg_ctx* ctx, const double* V, const double* Vhat, const double* h
       LaunchScope ls(ctx, HDG_KERNEL_MIXED_OPERATORS, s);
       k_asm_residual<C><<<(unsigned)a.ne, 128, 0, s>>>(a, ctx->T);
     }
-    if ((ctx->asm_variant < 0 || ctx->cond_variant < 0) && a.ne >= 512) {
-      // autotune on this chunk: time every compiled shape (each rewrites the same outputs)
+    if ((ctx->asm_variant < 0 || ctx->face_variant < 0 || ctx->cond_variant < 0) && a.ne >= 512) {
+      // autotune on this chunk: time every compiled shape (each rewrites the same outputs);
+      // the volume and face products are tuned separately (the faces add to the volume's
+      // output, so the volume runs again before each face trial)
       if (ctx->asm_variant < 0) {
         float best = 1e30f;
         int best_i = 0;
         for (int i = 0; i < NVAR; ++i) {
           float ms = 0.f;
           const AsmVariant& v = variants[i];
-          int rc = time_launch(s, [&] { v.run(a, ctx->T, TD, s); }, &ms);
+          int rc = time_launch(s, [&] { v.run_vol(a, TD, s); }, &ms);
           if (rc) return rc;
           if (ms < best) {
             best = ms;
@@ -213,13 +215,31 @@ int run_mixed(hdg_ctx* ctx, const double* V, const double* Vhat, const double* h
         ctx->asm_variant_threads = variants[best_i].threads;
         ctx->asm_variant_gt = 16 * variants[best_i].mtc;
       }
+      if (ctx->face_variant < 0) {
+        float best = 1e30f;
+        int best_i = 0;
+        for (int i = 0; i < NVAR; ++i) {
+          variants[ctx->asm_variant].run_vol(a, TD, s);
+          float ms = 0.f;
+          const AsmVariant& v = variants[i];
+          int rc = time_launch(s, [&] { v.run_face(a, ctx->T, TD, s); }, &ms);
+          if (rc) return rc;
+          if (ms < best) {
+            best = ms;
+            best_i = i;
+          }
+        }
+        ctx->face_variant = best_i;
+      }
       if (ctx->cond_variant < 0) {
-        const AsmVariant& v = variants[ctx->asm_variant];
+        const AsmVariant& vv = variants[ctx->asm_variant];
+        const AsmVariant& vf = variants[ctx->face_variant];
         float best = 1e30f;
         int best_i = 0;
         for (int i = 0; i < NCVAR; ++i) {
           // the condensation overwrites its inputs: assemble again before each trial
-          v.run(a, ctx->T, TD, s);
+          vv.run_vol(a, TD, s);
+          vf.run_face(a, ctx->T, TD, s);
           k_condense_prep<C, kSlices><<<(unsigned)a.ne, TC::PTH, TC::prep_bytes, s>>>(a);
           float ms = 0.f;
           const CondVariant& cv = cvariants[i];
@@ -234,14 +254,13 @@ int run_mixed(hdg_ctx* ctx, const double* V, const double* Vhat, const double* h
         ctx->cond_variant_threads = cvariants[best_i].threads;
       }
     }
-    const AsmVariant& v = variants[ctx->asm_variant < 0 ? 0 : ctx->asm_variant];
     {
       LaunchScope ls(ctx, HDG_KERNEL_MIXED_ASSEMBLE, s);
-      v.run_vol(a, TD, s);
+      variants[ctx->asm_variant < 0 ? 0 : ctx->asm_variant].run_vol(a, TD, s);
     }
     {
       LaunchScope ls(ctx, HDG_KERNEL_MIXED_FACE, s);
-      v.run_face(a, ctx->T, TD, s);
+      variants[ctx->face_variant < 0 ? 0 : ctx->face_variant].run_face(a, ctx->T, TD, s);
     }
     const CondVariant& cv = cvariants[ctx->cond_variant < 0 ? 0 : ctx->cond_variant];
     {

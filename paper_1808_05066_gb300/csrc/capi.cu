@@ -215,7 +215,7 @@ int hdg_ctx_create(hdg_mesh_t mesh, const hdg_physics* phys, int device, hdg_ctx
   c->ntrace = m.nFaces * m.ref.Nf * c->M;
   if (const char* av = std::getenv("HDG_ASM_VARIANT")) {  // force a tile shape (tests)
     long v = std::strtol(av, nullptr, 10);
-    if (v >= 0 && v < 4) c->asm_variant = (int)v;
+    if (v >= 0 && v < 4) c->asm_variant = c->face_variant = (int)v;
   }
   if (const char* cv = std::getenv("HDG_COND_VARIANT")) {  // force a condensation shape (tests)
     long v = std::strtol(cv, nullptr, 10);

@@ -36,7 +36,8 @@ struct hdg_ctx {
   double* d_scr = nullptr;
   size_t scr_bytes = 0;
   // autotuned tile shape of the mixed assembly (-1: not chosen yet)
-  int asm_variant = -1, asm_variant_threads = 0, asm_variant_gt = 0;
+  int asm_variant = -1, asm_variant_threads = 0, asm_variant_gt = 0;  // volume products
+  int face_variant = -1;                                              // face products
   int cond_variant = -1, cond_variant_threads = 0;  // mixed condensation shape
   // solver scratch
   double* d_sw = nullptr;    // GMRES / matvec workspace
