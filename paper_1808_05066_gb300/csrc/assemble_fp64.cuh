@@ -154,13 +154,11 @@ __global__ void __launch_bounds__(128) k_pointwise(AssembleArgs a, DevTables T, 
       }
     if (C::VISC) {
       // G is linear in q: dG/dq_lk = G(v, E_lk)
+      const ViscFactors<D> vf = visc_factors<D>(v);
       for (int l = 0; l < M; ++l)
         for (int k = 0; k < D; ++k) {
-          double E[M][D];
-          for (int i = 0; i < M; ++i)
-            for (int j = 0; j < D; ++j) E[i][j] = (i == l && j == k) ? 1.0 : 0.0;
           double Gq[M][D];
-          visc_flux<D>(v, E, ph, Gq);
+          visc_flux_unit<D>(vf, l, k, ph, Gq);
           for (int r = 0; r < D; ++r)
             for (int i = 0; i < M; ++i) {
               double s = 0.0;
@@ -259,13 +257,11 @@ __global__ void __launch_bounds__(128) k_pointwise(AssembleArgs a, DevTables T, 
       }
     }
     if (C::VISC) {
+      const ViscFactors<D> vf = visc_factors<D>(vh);
       for (int l = 0; l < M; ++l)
         for (int k = 0; k < D; ++k) {
-          double E[M][D];
-          for (int i = 0; i < M; ++i)
-            for (int j = 0; j < D; ++j) E[i][j] = (i == l && j == k) ? 1.0 : 0.0;
           double Gq[M][D];
-          visc_flux<D>(vh, E, ph, Gq);
+          visc_flux_unit<D>(vf, l, k, ph, Gq);
           for (int i = 0; i < M; ++i) {
             double s = 0.0;
             for (int j = 0; j < D; ++j) s += Gq[i][j] * n[j];

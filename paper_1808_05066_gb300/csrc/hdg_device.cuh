@@ -329,6 +329,65 @@ HDG_DEVI void visc_flux(const T* v, const TQ (*q)[D], const PhysParams& ph, T (*
   }
 }
 
+// The state-dependent factors of the viscous flux, shared by every gradient direction.
+template <int D>
+struct ViscFactors {
+  double ivm, ivm2, vel[D], A[D];  // 1/v_m, 1/v_m^2, V_i = -w_i/v_m, w_i/v_m^2
+};
+template <int D>
+HDG_DEVI ViscFactors<D> visc_factors(const double* v) {
+  ViscFactors<D> f;
+  f.ivm = 1.0 / v[D + 1];
+  f.ivm2 = f.ivm * f.ivm;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    f.vel[i] = -(v[1 + i] * f.ivm);
+    f.A[i] = v[1 + i] * f.ivm2;
+  }
+  return f;
+}
+
+// G(v, E_lk) for the unit gradient E_lk (component l, direction k): the same arithmetic as
+// visc_flux with that q, without the terms that vanish (G is linear in q, so these are the
+// columns of dG/dq).
+template <int D>
+HDG_DEVI void visc_flux_unit(const ViscFactors<D>& f, int l, int k, const PhysParams& ph, double (*G)[D]) {
+  double gV[D][D];
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = 0; j < D; ++j) gV[i][j] = 0.0;
+  if (l == D + 1) {
+#pragma unroll
+    for (int i = 0; i < D; ++i) gV[i][k] = f.A[i];
+  } else if (l >= 1) {
+    gV[l - 1][k] = -f.ivm;
+  }
+  double div = gV[0][0];
+#pragma unroll
+  for (int i = 1; i < D; ++i) div = div + gV[i][i];
+  double tau[D][D];
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      double t = gV[i][j] + gV[j][i];
+      if (i == j) t = t - (2.0 / 3.0) * div;
+      tau[i][j] = ph.mu * t;
+    }
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    G[0][j] = 0.0;
+    double e = f.vel[0] * tau[0][j];
+#pragma unroll
+    for (int i = 1; i < D; ++i) e = e + f.vel[i] * tau[i][j];
+    const double gradT = (ph.kappa / ph.cv) * ((l == D + 1 && j == k) ? f.ivm2 : 0.0);
+#pragma unroll
+    for (int i = 0; i < D; ++i) G[1 + i][j] = -tau[i][j];
+    G[D + 1][j] = -(e + gradT);
+  }
+}
+
 // Largest-magnitude eigenvalue of A_n: |V.n| + c (Eq. sLxF).
 template <int D, class T>
 HDG_DEVI T lambda_max(const T& rho, const T* vel, const T& p, const double* n, double gamma) {
