@@ -242,6 +242,10 @@ HDG_DEVI void tile_products(float (&acc)[NJW][S][4], const uint4* zs, const uint
   }
 }
 
+// Warps 4..7, 12..15, ... of a CTA with at least 8 warps: one of every two warps a scheduler
+// holds (warp w runs on scheduler w % 4).
+HDG_DEVI bool stagger_late(int warp, int nthreads) { return nthreads >= 256 && ((warp >> 2) & 1); }
+
 // ------------------------------------------------------------------------------------
 // k_asm_vol_tc: rows [ROWS*blockIdx.y, +ROWS) of (il, an), all nodal columns
 // ------------------------------------------------------------------------------------
@@ -449,19 +453,24 @@ __global__ void __launch_bounds__(AsmTC<C, S, MTC, NJW>::NTH, AsmTC<C, S, MTC, N
       }
     }
   };
+  // staggered roles: on every scheduler half the warps multiply before they produce the next
+  // tile's slices, so that production and products overlap within each k tile
+  const bool late = stagger_late(warp, NTH);
   zero();
   fetch(0, 0);
   produce(0, 0);
   cp_async_wait_all();
   __syncthreads();
   for (int kt = 0; kt < KTV; ++kt) {
-    if (kt + 1 < KTV) {
+    const bool more = kt + 1 < KTV;
+    if (more) {
       fetch(kt + 1, (kt + 1) & 1);
-      produce(kt + 1, (kt + 1) & 1);
+      if (!late) produce(kt + 1, (kt + 1) & 1);
     }
     const bool beta0 = kt < KTB;
     tile_products<S, NTN, NJW>(acc, Zs + (size_t)(kt & 1) * Q::zs_u4, Rs + (size_t)(kt & 1) * Q::stripe_u2, mt, nt0, lane,
                           [&](int nt) { return !beta0 || nt * 8 < NP; });
+    if (more && late) produce(kt + 1, (kt + 1) & 1);
     if ((kt + 1) % Q::KFLUSH == 0 || kt + 1 == KTV) {
       flush(kt + 1 <= Q::KFLUSH);
       zero();
