@@ -22,7 +22,18 @@
 #include "assemble_fp64.cuh"
 #include "ozaki.cuh"
 
+#include <type_traits>
+
 namespace hdg {
+
+template <int N, int LD, int NTHREADS>
+struct GJReg {
+  static constexpr int NWARP = NTHREADS / 32, RW = (N + NWARP - 1) / NWARP, CQ = (N + 31) / 32;
+  static_assert(RW * CQ <= 64, "register tile");
+  // shared scratch (ints): pivot row of each step [N], step of each row [N], candidates [2 NWARP]
+  static constexpr int smem_ints = 2 * N + 2 * NWARP;
+  static constexpr int smem_floats = CQ * 32;  // the scaled pivot row
+};
 
 template <class C, int NTHREADS, int OZS>
 struct CondTC {
@@ -46,8 +57,10 @@ struct CondTC {
   static constexpr int PREP_AI = 0, PREP_AH = NV * LDA, PREP_SC = 2 * NV * LDA, PREP_EA = PREP_SC + LDA,
                        PREP_EC = PREP_EA + MTA * 16;
   static constexpr size_t prep_floats = (size_t)(PREP_EC + MTC * 16 + 3) / 4 * 4;
-  static constexpr int PTH = 128;  // threads of the prep kernel
-  static constexpr size_t prep_bytes = sizeof(float) * (NV * LDA + NV) + sizeof(int) * (2 * NV + 2 * (PTH / 32)) + 64;
+  static constexpr int PTH = 256;  // threads of the prep kernel
+  using GJ = GJReg<NV, LDA, PTH>;
+  static constexpr size_t prep_bytes =
+      sizeof(float) * (NV * LDA + NV + GJ::smem_floats) + sizeof(int) * GJ::smem_ints + 64;
 };
 
 // out = A * W for an NV x CB block with A stored transposed (At[k][r] = A[r][k], leading
@@ -86,32 +99,20 @@ HDG_DEVI void cond_gemm_f32(const float* __restrict__ At, const float* __restric
   }
 }
 
-// In-place Gauss-Jordan inverse with partial (row) pivoting of an n x n FP32 matrix G in
-// shared memory (leading dimension LD), for a small CTA. Warp w eliminates rows w, w+NWARP,
-// ... with lanes over columns and the pivot row in registers; the lane that updates column
-// k+1 proposes the next pivot, so a step takes two barriers. The row interchanges are left
-// as a column permutation: the inverse's column j is G's column sigma(j), sigma = the
-// interchanges (k, piv[k]) applied for k = 0, 1, ... (gj_column). Returns false on a zero pivot.
-template <int N, int LD, int NTHREADS>
-HDG_DEVI bool gj_inverse_smem(float* G, int* piv, float* cval, int* crow) {
-  constexpr int NWARP = NTHREADS / 32, NQ = (N + 31) / 32;
+
+// Steps k = 32 q .. 32 q + 31 of gj_inverse_reg (q: a compile-time register index).
+template <int N, int NTHREADS, int q, int RW, int CQ>
+HDG_DEVI void gj_steps(float (&a)[RW][CQ], unsigned& used, bool& ok, int* si, float* prow) {
+  constexpr int NWARP = NTHREADS / 32;
+  int* pk_of = si;
+  int* k_of = si + N;
+  int* crow = si + 2 * N;
+  float* cval = reinterpret_cast<float*>(crow + NWARP);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  bool ok = true;
-  if (lane == 0) {  // candidates for column 0
-    float bv = 0.f;
-    int br = -1;
-    for (int r = warp; r < N; r += NWARP) {
-      const float v = G[r * LD];
-      if (br < 0 || fabsf(v) > fabsf(bv)) {
-        bv = v;
-        br = r;
-      }
-    }
-    cval[warp] = bv;
-    crow[warp] = br;
-  }
-  __syncthreads();
-  for (int k = 0; k < N; ++k) {
+#pragma unroll 1
+  for (int kk = 0; kk < 32; ++kk) {
+    const int k = 32 * q + kk;
+    if (k >= N) break;
     float pv = 0.f;
     int pr = -1;
 #pragma unroll
@@ -123,58 +124,118 @@ HDG_DEVI bool gj_inverse_smem(float* G, int* piv, float* cval, int* crow) {
         pr = r;
       }
     }
-    if (pr < 0) pr = k;  // no candidate (NaN input): keep the row
     if (!(fabsf(pv) > 0.f)) ok = false;
     const float ip = pv != 0.f ? 1.f / pv : 0.f;
-    if (tid == 0) piv[k] = pr;
-    for (int j = tid; j < N; j += NTHREADS) {  // swap rows k and pr, scale the pivot row
-      const float vk = G[k * LD + j], vp = G[pr * LD + j];
-      if (pr != k) G[pr * LD + j] = vk;
-      G[k * LD + j] = (j == k) ? ip : vp * ip;
+    if (tid == 0) {
+      pk_of[k] = pr;
+      k_of[pr] = k;
+    }
+    if (warp == pr % NWARP) {  // the pivot row, scaled, for every warp
+      const int pi = pr / NWARP;
+      float v[CQ];
+#pragma unroll
+      for (int qq = 0; qq < CQ; ++qq) v[qq] = 0.f;
+#pragma unroll
+      for (int i = 0; i < RW; ++i)  // a select chain keeps a[][] in registers
+#pragma unroll
+        for (int qq = 0; qq < CQ; ++qq) v[qq] = i == pi ? a[i][qq] : v[qq];
+#pragma unroll
+      for (int qq = 0; qq < CQ; ++qq) prow[lane + 32 * qq] = (qq == q && lane == kk) ? ip : v[qq] * ip;
+      used |= 1u << pi;
     }
     __syncthreads();
-    float pk[NQ];
+    float pk[CQ];
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) pk[q] = (lane + 32 * q < N) ? G[k * LD + lane + 32 * q] : 0.f;
-    const int kn = k + 1, qn = kn >> 5, ln = kn & 31;
+    for (int qq = 0; qq < CQ; ++qq) pk[qq] = prow[lane + 32 * qq];
     float bv = 0.f;
     int br = -1;
-    for (int r = warp; r < N; r += NWARP) {
-      if (r == k) continue;
-      const float f = G[r * LD + k];
-      __syncwarp();
 #pragma unroll
-      for (int q = 0; q < NQ; ++q) {
-        const int j = lane + 32 * q;
-        if (j < N) {
-          const float nv = (j == k) ? -f * ip : fmaf(-f, pk[q], G[r * LD + j]);
-          G[r * LD + j] = nv;
-          if (q == qn && lane == ln && r > k && (br < 0 || fabsf(nv) > fabsf(bv))) {
-            bv = nv;
+    for (int i = 0; i < RW; ++i) {
+      const int r = warp + NWARP * i;
+      if (r >= N) continue;
+      const float f = __shfl_sync(0xffffffffu, a[i][q], kk);
+      if (r == pr) {
+#pragma unroll
+        for (int qq = 0; qq < CQ; ++qq) a[i][qq] = pk[qq];
+      } else {
+#pragma unroll
+        for (int qq = 0; qq < CQ; ++qq)
+          a[i][qq] = (qq == q && lane == kk) ? -f * ip : fmaf(-f, pk[qq], a[i][qq]);
+        if (!((used >> i) & 1u)) {  // candidate for column k + 1
+          const float vn = kk < 31 ? a[i][q] : (q + 1 < CQ ? a[i][(q + 1) % CQ] : 0.f);
+          if (br < 0 || fabsf(vn) > fabsf(bv)) {
+            bv = vn;
             br = r;
           }
         }
       }
     }
-    __syncwarp();
-    if (lane == ln) {
+    if (lane == ((kk + 1) & 31)) {
       cval[warp] = bv;
       crow[warp] = br;
     }
     __syncthreads();
   }
-  return ok;
 }
 
-// Column of G holding the inverse's column j after gj_inverse_smem.
-template <int N>
-HDG_DEVI int gj_column(const int* piv, int j) {
-  int x = j;
-  for (int k = 0; k < N; ++k) {
-    const int p = piv[k];
-    x = (x == k) ? p : (x == p ? k : x);
+// Gauss-Jordan inverse with partial pivoting of an N x N FP32 matrix held in registers
+// across the CTA: warp w holds rows w, w + NWARP, ... (RW of them), lane l the columns
+// l, l + 32, ... (CQ). Rows are not moved: step k pivots on the row p_k with the largest
+// |entry| in column k among the rows not yet pivoted (the lowest row on ties), scales it by
+// 1/pivot and eliminates column k from every other row, storing -f/pivot in its place. The
+// tableau's row p_k then holds the inverse's row k with the columns in pivot order:
+// inv[k][p_j] = T[p_k][j]. G (shared memory, leading dimension LD) supplies the matrix and
+// receives the inverse in natural order. The lane that updates column k+1 proposes the next
+// pivot, so a step takes two barriers. Returns false on a zero pivot.
+template <int N, int LD, int NTHREADS>
+HDG_DEVI bool gj_inverse_reg(float* G, int* si, float* prow) {
+  using Q = GJReg<N, LD, NTHREADS>;
+  constexpr int NWARP = Q::NWARP, RW = Q::RW, CQ = Q::CQ;
+  int* pk_of = si;          // [N] pivot row of step k
+  int* k_of = si + N;       // [N] step at which row r pivoted
+  int* crow = si + 2 * N;   // [NWARP] candidate row per warp
+  float* cval = reinterpret_cast<float*>(crow + NWARP);  // [NWARP] its value
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  float a[RW][CQ];
+#pragma unroll
+  for (int i = 0; i < RW; ++i)
+#pragma unroll
+    for (int q = 0; q < CQ; ++q) {
+      const int r = warp + NWARP * i, c = lane + 32 * q;
+      a[i][q] = (r < N && c < N) ? G[r * LD + c] : 0.f;
+    }
+  unsigned used = 0;  // bit i: this warp's row i has pivoted
+  {                   // candidates for column 0 (lane 0)
+    float bv = 0.f;
+    int br = -1;
+#pragma unroll
+    for (int i = 0; i < RW; ++i)
+      if (warp + NWARP * i < N && (br < 0 || fabsf(a[i][0]) > fabsf(bv))) {
+        bv = a[i][0];
+        br = warp + NWARP * i;
+      }
+    if (lane == 0) {
+      cval[warp] = bv;
+      crow[warp] = br;
+    }
   }
-  return x;
+  __syncthreads();
+  bool ok = true;
+  gj_steps<N, NTHREADS, 0>(a, used, ok, si, prow);
+  if constexpr (CQ > 1) gj_steps<N, NTHREADS, 1 % CQ>(a, used, ok, si, prow);
+  if constexpr (CQ > 2) gj_steps<N, NTHREADS, 2 % CQ>(a, used, ok, si, prow);
+  if constexpr (CQ > 3) gj_steps<N, NTHREADS, 3 % CQ>(a, used, ok, si, prow);
+  static_assert(CQ <= 4, "column groups");
+  // inv[k_of[r]][pk_of[c]] = T[r][c]
+#pragma unroll
+  for (int i = 0; i < RW; ++i)
+#pragma unroll
+    for (int q = 0; q < CQ; ++q) {
+      const int r = warp + NWARP * i, c = lane + 32 * q;
+      if (r < N && c < N) G[k_of[r] * LD + pk_of[c]] = a[i][q];
+    }
+  __syncthreads();
+  return ok;
 }
 
 // Exact-slice product of the rows of A' or C' (right operand, NTL tiles of 8 rows, sliced in
@@ -233,12 +294,10 @@ __global__ void __launch_bounds__(CondTC<C, 256, OZS>::PTH) k_condense_prep(Asse
   constexpr int NV = C::NV, NT = C::NT, KT = Q::KT, MTA = Q::MTA, MTC = Q::MTC, LDA = Q::LDA;
   constexpr int PTH = Q::PTH, NWARP = PTH / 32;
   extern __shared__ double smem_d[];
-  float* G = reinterpret_cast<float*>(smem_d);  // [NV][LDA] A'^T, then (sc A' sc)^-T (permuted)
+  float* G = reinterpret_cast<float*>(smem_d);  // [NV][LDA] A'^T, then (sc A' sc)^-T
   float* sc = G + NV * LDA;                     // [NV]
-  int* piv = reinterpret_cast<int*>(sc + NV);   // [NV]
-  int* sig = piv + NV;                          // [NV]
-  float* cval = reinterpret_cast<float*>(sig + NV);
-  int* crow = reinterpret_cast<int*>(cval + NWARP);
+  float* prow = sc + NV;                        // the inverse's pivot row
+  int* gsi = reinterpret_cast<int*>(prow + Q::GJ::smem_floats);
   const int64_t le = blockIdx.x;
   const int64_t e = a.e0 + le;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -255,14 +314,29 @@ __global__ void __launch_bounds__(CondTC<C, 256, OZS>::PTH) k_condense_prep(Asse
     cp_async4(G + k * LDA + r, &Ap[t].hi);
   }
   cp_async_commit();
-  for (int t = tid; t < NV * (LDA - NV); t += PTH) G[(t / (LDA - NV)) * LDA + NV + t % (LDA - NV)] = 0.f;
+  if constexpr (LDA > NV)
+    for (int t = tid; t < NV * (LDA - NV); t += PTH) G[(t / (LDA - NV)) * LDA + NV + t % (LDA - NV)] = 0.f;
   for (int r = NV + tid; r < MTA * 16; r += PTH) eA[r] = 0;
-  for (int r = warp; r < MTC * 16; r += NWARP) {
-    float mx = 0.f;
-    if (r < NT)
-      for (int k = lane; k < NV; k += 32) mx = fmaxf(mx, fabsf(Cp[r * NV + k].hi));
-    for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-    if (lane == 0) eC[r] = oz_exponent(mx);
+  {  // four rows per warp at a time, all their loads in flight together
+    constexpr int RB = 4, KQ = (NV + 31) / 32;
+    for (int r0 = warp * RB; r0 < MTC * 16; r0 += NWARP * RB) {
+      float mx[RB];
+#pragma unroll
+      for (int j = 0; j < RB; ++j) {
+        mx[j] = 0.f;
+        const int r = r0 + j;
+#pragma unroll
+        for (int m = 0; m < KQ; ++m) {
+          const int k = lane + 32 * m;
+          if (r < NT && k < NV) mx[j] = fmaxf(mx[j], fabsf(Cp[r * NV + k].hi));
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < RB; ++j) {
+        for (int off = 16; off > 0; off >>= 1) mx[j] = fmaxf(mx[j], __shfl_xor_sync(0xffffffffu, mx[j], off));
+        if (lane == 0 && r0 + j < MTC * 16) eC[r0 + j] = oz_exponent(mx[j]);
+      }
+    }
   }
   cp_async_wait_all();
   __syncthreads();
@@ -310,15 +384,10 @@ __global__ void __launch_bounds__(CondTC<C, 256, OZS>::PTH) k_condense_prep(Asse
         oz_slice_right_tile<OZS>(sl + (size_t)u * OZS * 32, 32, kt * 16, (nt - NTA) * 8, lane, getC, sC);
     }
   }
-  // inverse of the transposed equilibrated matrix, written out with its columns in place
-  const bool ok = gj_inverse_smem<NV, LDA, PTH>(G, piv, cval, crow);
-  for (int j = tid; j < NV; j += PTH) sig[j] = gj_column<NV>(piv, j);
-  __syncthreads();
+  // inverse of the transposed equilibrated matrix
+  const bool ok = gj_inverse_reg<NV, LDA, PTH>(G, gsi, prow);
   float* ai = pre + Q::PREP_AI;
-  for (int t = tid; t < NV * LDA; t += PTH) {
-    const int k = t / LDA, r = t % LDA;
-    ai[t] = r < NV ? G[k * LDA + sig[r]] : 0.f;
-  }
+  for (int t = tid; t < NV * LDA; t += PTH) ai[t] = (t % LDA) < NV ? G[t] : 0.f;
   if (tid == 0 && !ok) atomicOr(a.status + e, HDG_STATUS_SINGULAR);
 }
 
@@ -400,9 +469,19 @@ __global__ void __launch_bounds__(NTHREADS) k_condense_tc(AssembleArgs a) {
       if (c >= nc) return df2{0.f, 0.f};
       return col < NT ? Bd[r * NT + col] : df_from(R[r]);
     };
-    for (int t = tid; t < NV * CB; t += NTHREADS) {
-      const df2 b = bval(t / CB, t % CB);
-      W[t] = (b.hi + b.lo) * sc[t / CB];
+    {  // all of a thread's B' loads in flight together
+      constexpr int NWI = (NV * CB + NTHREADS - 1) / NTHREADS;
+      df2 bv[NWI];
+#pragma unroll
+      for (int x = 0; x < NWI; ++x) {
+        const int t = tid + x * NTHREADS;
+        bv[x] = t < NV * CB ? bval(t / CB, t % CB) : df2{0.f, 0.f};
+      }
+#pragma unroll
+      for (int x = 0; x < NWI; ++x) {
+        const int t = tid + x * NTHREADS;
+        if (t < NV * CB) W[t] = (bv[x].hi + bv[x].lo) * sc[t / CB];
+      }
     }
     if (tid < 2) s_corr[tid] = 0.f;
     if (tid == 0) s_xmax = 0.f;
