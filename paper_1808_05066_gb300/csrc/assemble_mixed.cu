@@ -83,6 +83,12 @@ CondVariant make_cond_variant() {
   return CondVariant{NTH, CondTC<C, NTH, kSlices>::bytes, &k_condense_tc<C, NTH, kSlices>};
 }
 
+// 16-column blocks, two CTAs per SM
+template <class C>
+CondVariant make_cond_variant2() {
+  return CondVariant{256, CondTC2<C, 256, kSlices>::bytes, &k_condense_tc2<C, 256, kSlices>};
+}
+
 // Times `launch` once on the stream (the chunk's outputs are rewritten each time).
 template <class F>
 int time_launch(cudaStream_t s, F launch, float* ms) {
@@ -128,14 +134,16 @@ int run_mixed(hdg_ctx* ctx, const double* V, const double* Vhat, const double* h
   const AsmVariant variants[] = {make_variant<C, 2, 4>(), make_variant<C, 4, 4>(), make_variant<C, 2, 2>(),
                                  make_variant<C, 4, 2>()};
   constexpr int NVAR = 4;
-  const CondVariant cvariants[] = {make_cond_variant<C, 256>(), make_cond_variant<C, 512>()};
-  constexpr int NCVAR = 2;
+  const CondVariant cvariants[] = {make_cond_variant<C, 256>(), make_cond_variant<C, 512>(), make_cond_variant2<C>()};
+  constexpr int NCVAR = 3;
   static bool attr_done = false;
   if (!attr_done) {
     for (const AsmVariant& v : variants)
       if (int rc2 = v.set_attr()) return rc2;
-    for (const CondVariant& v : cvariants)
+    for (const CondVariant& v : cvariants) {
       HDG_CK(cudaFuncSetAttribute(v.kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem));
+      HDG_CK(cudaFuncSetAttribute(v.kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+    }
     HDG_CK(cudaFuncSetAttribute(k_condense_prep<C, kSlices>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)TC::prep_bytes));
     attr_done = true;

@@ -219,7 +219,7 @@ int hdg_ctx_create(hdg_mesh_t mesh, const hdg_physics* phys, int device, hdg_ctx
   }
   if (const char* cv = std::getenv("HDG_COND_VARIANT")) {  // force a condensation shape (tests)
     long v = std::strtol(cv, nullptr, 10);
-    if (v >= 0 && v < 2) c->cond_variant = (int)v;
+    if (v >= 0 && v < 3) c->cond_variant = (int)v;
   }
   if (const char* ch = std::getenv("HDG_ELEMENT_CHUNK")) {
     long v = std::strtol(ch, nullptr, 10);

@@ -64,16 +64,20 @@ struct CondTC {
 };
 
 // out = A * W for an NV x CB block with A stored transposed (At[k][r] = A[r][k], leading
-// dimension LDA, zero past NV): RT x CT register tiles, two vector loads per k.
-template <int NV, int LDA, int CB, int RT, int CT, int NTHREADS, class Epi>
-HDG_DEVI void cond_gemm_f32(const float* __restrict__ At, const float* __restrict__ Wm, Epi epi) {
+// dimension LDA, zero past NV): RT x CT register tiles, two vector loads per k. With SPLIT
+// (one tile per thread at most) a barrier separates every read of Wm from the epilogues, so
+// that they may overwrite Wm.
+template <int NV, int LDA, int CB, int RT, int CT, int NTHREADS, bool SPLIT = false, class Epi>
+HDG_DEVI void cond_gemm_f32(const float* __restrict__ At, const float* Wm, Epi epi) {
   static_assert(CT == 4 && (RT == 2 || RT == 4), "vector loads");
   constexpr int NRT = (NV + RT - 1) / RT, NCT = CB / CT;
-  for (int tile = threadIdx.x; tile < NRT * NCT; tile += NTHREADS) {
+  static_assert(!SPLIT || NRT * NCT <= NTHREADS, "one tile per thread");
+  for (int tile = threadIdx.x; tile < (SPLIT ? NTHREADS : NRT * NCT); tile += NTHREADS) {
     const int r0 = (tile / NCT) * RT, c0 = (tile % NCT) * CT;
+    const bool live = !SPLIT || tile < NRT * NCT;
     float acc[RT][CT] = {};
 #pragma unroll 4
-    for (int k = 0; k < NV; ++k) {
+    for (int k = 0; k < (live ? NV : 0); ++k) {
       const float4 w = *reinterpret_cast<const float4*>(Wm + k * CB + c0);
       float av[RT];
       if constexpr (RT == 4) {
@@ -95,7 +99,8 @@ HDG_DEVI void cond_gemm_f32(const float* __restrict__ At, const float* __restric
         acc[i][3] = fmaf(av[i], w.w, acc[i][3]);
       }
     }
-    epi(r0, c0, acc);
+    if constexpr (SPLIT) __syncthreads();
+    if (live) epi(r0, c0, acc);
   }
 }
 
@@ -244,7 +249,8 @@ HDG_DEVI bool gj_inverse_reg(float* G, int* si, float* prow) {
 // rows across all the block's columns, so every right-operand fragment is read from L2 once
 // per block; the next k tile's fragments load during this tile's products.
 // epi(row, col, value_without_scales) per element (row of A' or C', block column).
-template <int KT, int NMB, int OZS, int NWARP, class Epi>
+// The right operand is stored with OZG >= OZS slices per tile; the first OZS are used.
+template <int KT, int NMB, int OZS, int NWARP, int OZG = OZS, class Epi>
 HDG_DEVI void cond_oz_product(const uint2* __restrict__ Rsl, int NTL, const uint4* Xs, int nmt, Epi epi) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int task = warp; task < NTL; task += NWARP) {
@@ -255,7 +261,7 @@ HDG_DEVI void cond_oz_product(const uint2* __restrict__ Rsl, int NTL, const uint
       for (int d = 0; d < OZS; ++d)
 #pragma unroll
         for (int q = 0; q < 4; ++q) acc[m][d][q] = 0.f;
-    const uint2* Bt = Rsl + (size_t)task * KT * OZS * 32 + lane;
+    const uint2* Bt = Rsl + (size_t)task * KT * OZG * 32 + lane;
     uint2 b[OZS], bn[OZS];
 #pragma unroll
     for (int s = 0; s < OZS; ++s) b[s] = Bt[s * 32];
@@ -263,7 +269,7 @@ HDG_DEVI void cond_oz_product(const uint2* __restrict__ Rsl, int NTL, const uint
     for (int kt = 0; kt < KT; ++kt) {
       if (kt + 1 < KT)  // next tile's fragments in flight during this tile's products
 #pragma unroll
-        for (int s = 0; s < OZS; ++s) bn[s] = Bt[((kt + 1) * OZS + s) * 32];
+        for (int s = 0; s < OZS; ++s) bn[s] = Bt[((kt + 1) * OZG + s) * 32];
 #pragma unroll
       for (int m = 0; m < NMB; ++m)
         if (m < nmt) {
@@ -579,6 +585,254 @@ __global__ void __launch_bounds__(NTHREADS) k_condense_tc(AssembleArgs a) {
     __syncthreads();
     // S[:, block] = D' - C' X ; g = R_t - C' y
     cond_oz_product<KT, Q::NMB, OZS, NWARP>(slC, Q::NTC, Xs, nmt, [&](int row, int col, const dfacc& v) {
+      const int gc = c0 + col;
+      if (row >= NT || col >= nc) return;
+      const df2 p = oz_scaled(v, eC[row] + eX[col]);
+      dfacc t;
+      if (gc < NT)
+        t.add(Ds[row * CB + col]);
+      else
+        t.add(df_from(R[NV + row]));
+      t.add(df2{-p.hi, -p.lo});
+      if (gc < NT)
+        S[row * NT + gc] = df_to_f64(t.hi, t.lo);
+      else
+        a.g[e * NT + row] = df_to_f64(t.hi, t.lo);
+    });
+    __syncthreads();
+  }
+  if (tid == 0 && s_bad) atomicOr(a.status + e, s_bad);
+}
+
+// ------------------------------------------------------------------------------------
+// k_condense_tc2: the condensation of k_condense_tc in blocks of CB = 16 right-hand sides
+// and without the FP32 copy of A': the second residual r1 = r0 - A' d0 comes from the first
+// OZR = 4 exact slices of A' and of d0 on the tensor cores. Slices hold an entry to a power
+// of two below its row's (column's) largest, not below itself as FP32 does: with three the
+// small entries of A' lose about two digits against FP32 and X misses 1e-10; four give
+// 2^-33 of the largest, as accurate as the FP32 product. About 108 KB of shared memory, so
+// that two elements share an SM and one hides the other's latency.
+// ------------------------------------------------------------------------------------
+template <class C, int NTHREADS, int OZS>
+struct CondTC2 {
+  static constexpr int NV = C::NV, NT = C::NT;
+  static constexpr int KT = (NV + 15) / 16, MTA = KT, MTC = (NT + 15) / 16;
+  static constexpr int CB = 16, NMB = 1;
+  static constexpr int RT = 2, CT = 4;
+  static constexpr int LDA = (NV + 3) / 4 * 4;
+  static constexpr int NTA = (NV + 7) / 8, NTC = (NT + 7) / 8;
+  static constexpr int OZR = 4;
+  static constexpr size_t xs_bytes = sizeof(uint4) * KT * NMB * OZS * 32;
+  static constexpr size_t rk_bytes = sizeof(float) * NV * CB;  // r0, then the slices of d0
+  static_assert(rk_bytes % 16 == 0 && rk_bytes + sizeof(uint4) * KT * NMB * OZR * 32 <= xs_bytes,
+                "r0 and the slices of d0 share the X slice buffer");
+  static constexpr size_t bytes = sizeof(df2) * (NT + NV) * CB + xs_bytes +
+                                  sizeof(float) * (NV * LDA + NV * CB + NV) + sizeof(int) * (MTA * 16 + MTC * 16 + CB) +
+                                  64;
+};
+
+template <class C, int NTHREADS, int OZS>
+__global__ void __launch_bounds__(NTHREADS, 2) k_condense_tc2(AssembleArgs a) {
+  using Q = CondTC2<C, NTHREADS, OZS>;
+  using P = CondTC<C, 256, OZS>;  // the prep block and the slices of A', C'
+  constexpr int NV = C::NV, NT = C::NT, KT = Q::KT, MTA = Q::MTA, MTC = Q::MTC, CB = Q::CB, OZR = Q::OZR;
+  constexpr int RT = Q::RT, CT = Q::CT, LDA = Q::LDA, NWARP = NTHREADS / 32;
+  static_assert(LDA == P::LDA, "prep layout");
+  extern __shared__ double smem_d[];
+  df2* Ds = reinterpret_cast<df2*>(smem_d);                                         // [NT][CB] D' columns
+  df2* Xb = Ds + NT * CB;                                                           // [NV][CB] X block
+  uint4* Xs = reinterpret_cast<uint4*>(Xb + NV * CB);                               // [KT][OZS][32] X^T slices
+  float* Rk = reinterpret_cast<float*>(Xs);                                         // [NV][CB] r0 (aliases Xs)
+  uint4* Xd = reinterpret_cast<uint4*>(reinterpret_cast<char*>(Xs) + Q::rk_bytes);  // [KT][OZR][32] d0^T slices
+  float* Ai = reinterpret_cast<float*>(reinterpret_cast<char*>(Xs) + Q::xs_bytes);  // (sc A' sc)^-T [NV][LDA]
+  float* W = Ai + NV * LDA;                                                         // [NV][CB]
+  float* sc = W + NV * CB;                                                          // [NV]
+  int* eA = reinterpret_cast<int*>(sc + NV);                                        // [MTA*16]
+  int* eC = eA + MTA * 16;                                                          // [MTC*16]
+  int* eX = eC + MTC * 16;                                                          // [CB]
+  __shared__ int s_bad;
+  __shared__ float s_corr[2], s_xmax;
+  const int64_t le = blockIdx.x;
+  const int64_t e = a.e0 + le;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint2* slA = reinterpret_cast<const uint2*>(a.oz) + le * P::slice_u2;
+  const uint2* slC = slA + (size_t)P::NTA * KT * OZS * 32;
+  double* Xg = a.recov + e * (int64_t)(NV * NT + NV);  // B' (double-float) in, X out
+  const df2* Bd = reinterpret_cast<const df2*>(Xg);
+  double* yg = Xg + NV * NT;
+  double* S = a.S + e * (int64_t)NT * NT;  // D' (double-float) in, S out
+  const df2* Dd = reinterpret_cast<const df2*>(S);
+  const double* R = a.R + e * (int64_t)(NV + NT);
+
+  {  // the element's prepared operands: Ai^T, sc, row exponents
+    const float* pre = a.prep + le * P::prep_floats;
+    const float4* src = reinterpret_cast<const float4*>(pre + P::PREP_AI);
+    float4* dst = reinterpret_cast<float4*>(Ai);
+    for (int t = tid; t < NV * LDA / 4; t += NTHREADS) dst[t] = src[t];
+    for (int r = tid; r < NV; r += NTHREADS) sc[r] = pre[P::PREP_SC + r];
+    const int* ex = reinterpret_cast<const int*>(pre + P::PREP_EA);
+    for (int r = tid; r < (MTA + MTC) * 16; r += NTHREADS) eA[r] = ex[r];  // eC follows eA
+  }
+  if (tid == 0) s_bad = 0;
+  __syncthreads();
+
+  auto col_exponents = [&](auto get) {  // eX[c] = exponent of max_r |get(r, c)|
+    for (int c = warp; c < CB; c += NWARP) {
+      float mx = 0.f;
+      for (int r = lane; r < NV; r += 32) mx = fmaxf(mx, fabsf(get(r, c)));
+      for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+      if (lane == 0) eX[c] = oz_exponent(mx);
+    }
+  };
+  auto sX = [&](int c) { return oz_scale(eX[c]); };
+  auto xhi = [&](int r, int c) { return Xb[r * CB + c].hi; };
+
+  for (int c0 = 0; c0 < NT + 1; c0 += CB) {
+    const int nc = (NT + 1 - c0) < CB ? (NT + 1 - c0) : CB;
+    // the block's D' columns, read by the Schur epilogue, copied in the background meanwhile
+    for (int t = tid; t < NT * CB; t += NTHREADS) {
+      const int r = t / CB, c = t % CB;
+      if (c < nc && c0 + c < NT) cp_async8(Ds + t, Dd + (size_t)r * NT + c0 + c);
+    }
+    cp_async_commit();
+    auto bval = [&](int r, int c) -> df2 {  // B' column or R_v, zero past the block
+      const int col = c0 + c;
+      if (c >= nc) return df2{0.f, 0.f};
+      return col < NT ? Bd[r * NT + col] : df_from(R[r]);
+    };
+    {  // W = sc B, all of a thread's loads in flight together
+      constexpr int NWI = (NV * CB + NTHREADS - 1) / NTHREADS;
+      df2 bv[NWI];
+#pragma unroll
+      for (int x = 0; x < NWI; ++x) {
+        const int t = tid + x * NTHREADS;
+        bv[x] = t < NV * CB ? bval(t / CB, t % CB) : df2{0.f, 0.f};
+      }
+#pragma unroll
+      for (int x = 0; x < NWI; ++x) {
+        const int t = tid + x * NTHREADS;
+        if (t < NV * CB) W[t] = (bv[x].hi + bv[x].lo) * sc[t / CB];
+      }
+    }
+    if (tid < 2) s_corr[tid] = 0.f;
+    if (tid == 0) s_xmax = 0.f;
+    __syncthreads();
+    // X0 = sc Ai W
+    cond_gemm_f32<NV, LDA, CB, RT, CT, NTHREADS>(Ai, W, [&](int r0, int cc0, float(&acc)[RT][CT]) {
+#pragma unroll
+      for (int i = 0; i < RT; ++i)
+        if (r0 + i < NV)
+#pragma unroll
+          for (int j = 0; j < CT; ++j) Xb[(r0 + i) * CB + cc0 + j] = df2{acc[i][j] * sc[r0 + i], 0.f};
+    });
+    __syncthreads();
+    col_exponents(xhi);
+    __syncthreads();
+    for (int kt = warp; kt < KT; kt += NWARP) {
+      auto getX = [&](int c, int k) { return k < NV ? Xb[k * CB + c] : df2{0.f, 0.f}; };
+      oz_slice_left_tile<OZS>(Xs + kt * OZS * 32, 32, 0, kt * 16, lane, getX, sX);
+    }
+    __syncthreads();
+    // r0 = B - A' X0 (exact slices) into W
+    cond_oz_product<KT, 1, OZS, NWARP>(slA, Q::NTA, Xs, 1, [&](int row, int col, const dfacc& v) {
+      if (row < NV) {
+        const df2 p = oz_scaled(v, eA[row] + eX[col]);
+        dfacc t;
+        t.add(bval(row, col));
+        t.add(df2{-p.hi, -p.lo});
+        W[row * CB + col] = col < nc ? t.hi + t.lo : 0.f;
+      }
+    });
+    __syncthreads();
+    for (int t = tid; t < NV * CB; t += NTHREADS) {  // Rk = r0 (the X slices are done), W = sc r0
+      const float rv = W[t];
+      Rk[t] = rv;
+      W[t] = rv * sc[t / CB];
+    }
+    __syncthreads();
+    // d0 = sc Ai W, in place in W; X += d0
+    cond_gemm_f32<NV, LDA, CB, RT, CT, NTHREADS, true>(Ai, W, [&](int r0, int cc0, float(&acc)[RT][CT]) {
+      float cmax = 0.f;
+#pragma unroll
+      for (int i = 0; i < RT; ++i)
+        if (r0 + i < NV)
+#pragma unroll
+          for (int j = 0; j < CT; ++j) {
+            const int t = (r0 + i) * CB + cc0 + j;
+            const float corr = acc[i][j] * sc[r0 + i];
+            dfacc u;
+            u.add(Xb[t]);
+            u.add(df2{corr, 0.f});
+            Xb[t] = u.norm();
+            W[t] = corr;
+            cmax = fmaxf(cmax, fabsf(corr));
+          }
+      atomicMax(reinterpret_cast<int*>(&s_corr[0]), __float_as_int(cmax));
+    });
+    __syncthreads();
+    // r1 = r0 - A' d0 from four slices of each, W = sc r1
+    col_exponents([&](int r, int c) { return W[r * CB + c]; });
+    __syncthreads();
+    for (int kt = warp; kt < KT; kt += NWARP) {
+      auto getD = [&](int c, int k) { return df2{k < NV ? W[k * CB + c] : 0.f, 0.f}; };
+      oz_slice_left_tile<OZR>(Xd + kt * OZR * 32, 32, 0, kt * 16, lane, getD, sX);
+    }
+    __syncthreads();
+    cond_oz_product<KT, 1, OZR, NWARP, OZS>(slA, Q::NTA, Xd, 1, [&](int row, int col, const dfacc& v) {
+      if (row < NV) {
+        const df2 p = oz_scaled(v, eA[row] + eX[col]);
+        W[row * CB + col] = col < nc ? ((Rk[row * CB + col] - p.hi) - p.lo) * sc[row] : 0.f;
+      }
+    });
+    __syncthreads();
+    // d1 = sc Ai W; X += d1
+    cond_gemm_f32<NV, LDA, CB, RT, CT, NTHREADS>(Ai, W, [&](int r0, int cc0, float(&acc)[RT][CT]) {
+      float cmax = 0.f, xmax = 0.f;
+#pragma unroll
+      for (int i = 0; i < RT; ++i)
+        if (r0 + i < NV)
+#pragma unroll
+          for (int j = 0; j < CT; ++j) {
+            const int t = (r0 + i) * CB + cc0 + j;
+            const float corr = acc[i][j] * sc[r0 + i];
+            dfacc u;
+            u.add(Xb[t]);
+            u.add(df2{corr, 0.f});
+            const df2 xn = u.norm();
+            Xb[t] = xn;
+            cmax = fmaxf(cmax, fabsf(corr));
+            xmax = fmaxf(xmax, fabsf(xn.hi));
+          }
+      atomicMax(reinterpret_cast<int*>(&s_corr[1]), __float_as_int(cmax));
+      atomicMax(reinterpret_cast<int*>(&s_xmax), __float_as_int(xmax));
+    });
+    __syncthreads();
+    // the error left after the second correction is ~ c_last^2 / c_prev
+    if (tid == 0) {
+      const float cl = s_corr[1], cp = s_corr[0];
+      if (!((double)cl * (double)cl <= 1e-10 * (double)s_xmax * (double)cp)) s_bad |= 4;
+    }
+    // store X and y for the recovery
+    for (int t = tid; t < NV * CB; t += NTHREADS) {
+      const int r = t / CB, c = t % CB, col = c0 + c;
+      if (c < nc) {
+        const double xv = df_to_f64(Xb[t].hi, Xb[t].lo);
+        if (col < NT)
+          Xg[r * NT + col] = xv;
+        else
+          yg[r] = xv;
+      }
+    }
+    col_exponents(xhi);
+    __syncthreads();
+    for (int kt = warp; kt < KT; kt += NWARP) {
+      auto getX = [&](int c, int k) { return k < NV ? Xb[k * CB + c] : df2{0.f, 0.f}; };
+      oz_slice_left_tile<OZS>(Xs + kt * OZS * 32, 32, 0, kt * 16, lane, getX, sX);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    // S[:, block] = D' - C' X ; g = R_t - C' y
+    cond_oz_product<KT, 1, OZS, NWARP>(slC, Q::NTC, Xs, 1, [&](int row, int col, const dfacc& v) {
       const int gc = c0 + col;
       if (row >= NT || col >= nc) return;
       const df2 p = oz_scaled(v, eC[row] + eX[col]);

@@ -133,10 +133,11 @@ def test_mixed_tile_shapes_match_oracle(variant, monkeypatch):
         assert rel_fro(g[e], L["g"]) < TOL_BLOCK, (variant, e)
 
 
-@pytest.mark.parametrize("cvariant", [0, 1])
+@pytest.mark.parametrize("cvariant", [0, 1, 2])
 @pytest.mark.parametrize("name", ["ns3d_p3", "euler2d_p2", "ns2d_p4"])
 def test_mixed_condensation_shapes_match_oracle(name, cvariant, monkeypatch):
-    """Both compiled shapes of the tensor-core condensation (256 and 512 threads) give the
+    """Every compiled shape of the tensor-core condensation (32-column blocks with 256 and
+    512 threads; 16-column blocks with the second residual from slices of A') gives the
     oracle's S, g, X and y, including the ragged last block of right-hand sides."""
     monkeypatch.setenv("HDG_COND_VARIANT", str(cvariant))
     case = CASES[name]
