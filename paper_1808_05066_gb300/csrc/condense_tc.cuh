@@ -249,11 +249,19 @@ HDG_DEVI bool gj_inverse_reg(float* G, int* si, float* prow) {
 // rows across all the block's columns, so every right-operand fragment is read from L2 once
 // per block; the next k tile's fragments load during this tile's products.
 // epi(row, col, value_without_scales) per element (row of A' or C', block column).
-// The right operand is stored with OZG >= OZS slices per tile; the first OZS are used.
-template <int KT, int NMB, int OZS, int NWARP, int OZG = OZS, class Epi>
+// The right operand is stored with OZG >= OZS slices per tile; the first OZS are used. With
+// PF each warp asks L2 for its next task's fragments (one contiguous run) while it works.
+template <int KT, int NMB, int OZS, int NWARP, int OZG = OZS, bool PF = false, class Epi>
 HDG_DEVI void cond_oz_product(const uint2* __restrict__ Rsl, int NTL, const uint4* Xs, int nmt, Epi epi) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int task = warp; task < NTL; task += NWARP) {
+    if constexpr (PF) {
+      if (task + NWARP < NTL) {
+        const char* nx = reinterpret_cast<const char*>(Rsl + (size_t)(task + NWARP) * KT * OZG * 32);
+        constexpr int LINES = (KT * OZG * 32 * (int)sizeof(uint2)) / 128;
+        for (int l = lane; l < LINES; l += 32) asm volatile("prefetch.global.L2 [%0];" ::"l"(nx + l * 128));
+      }
+    }
     float acc[NMB][OZS][4];
 #pragma unroll
     for (int m = 0; m < NMB; ++m)
@@ -633,6 +641,9 @@ struct CondTC2 {
 
 template <class C, int NTHREADS, int OZS>
 __global__ void __launch_bounds__(NTHREADS, 2) k_condense_tc2(AssembleArgs a) {
+  // every block re-reads the slices of A' and C', and two elements per SM keep about as many
+  // of them in flight as L2 holds: each warp asks L2 for its next task's fragments
+  constexpr bool PF = true;
   using Q = CondTC2<C, NTHREADS, OZS>;
   using P = CondTC<C, 256, OZS>;  // the prep block and the slices of A', C'
   constexpr int NV = C::NV, NT = C::NT, KT = Q::KT, MTA = Q::MTA, MTC = Q::MTC, CB = Q::CB, OZR = Q::OZR;
@@ -734,7 +745,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_condense_tc2(AssembleArgs a) {
     }
     __syncthreads();
     // r0 = B - A' X0 (exact slices) into W
-    cond_oz_product<KT, 1, OZS, NWARP>(slA, Q::NTA, Xs, 1, [&](int row, int col, const dfacc& v) {
+    cond_oz_product<KT, 1, OZS, NWARP, OZS, PF>(slA, Q::NTA, Xs, 1, [&](int row, int col, const dfacc& v) {
       if (row < NV) {
         const df2 p = oz_scaled(v, eA[row] + eX[col]);
         dfacc t;
@@ -778,7 +789,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_condense_tc2(AssembleArgs a) {
       oz_slice_left_tile<OZR>(Xd + kt * OZR * 32, 32, 0, kt * 16, lane, getD, sX);
     }
     __syncthreads();
-    cond_oz_product<KT, 1, OZR, NWARP, OZS>(slA, Q::NTA, Xd, 1, [&](int row, int col, const dfacc& v) {
+    cond_oz_product<KT, 1, OZR, NWARP, OZS, PF>(slA, Q::NTA, Xd, 1, [&](int row, int col, const dfacc& v) {
       if (row < NV) {
         const df2 p = oz_scaled(v, eA[row] + eX[col]);
         W[row * CB + col] = col < nc ? ((Rk[row * CB + col] - p.hi) - p.lo) * sc[row] : 0.f;
@@ -832,7 +843,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_condense_tc2(AssembleArgs a) {
     cp_async_wait_all();
     __syncthreads();
     // S[:, block] = D' - C' X ; g = R_t - C' y
-    cond_oz_product<KT, 1, OZS, NWARP>(slC, Q::NTC, Xs, 1, [&](int row, int col, const dfacc& v) {
+    cond_oz_product<KT, 1, OZS, NWARP, OZS, PF>(slC, Q::NTC, Xs, 1, [&](int row, int col, const dfacc& v) {
       const int gc = c0 + col;
       if (row >= NT || col >= nc) return;
       const df2 p = oz_scaled(v, eC[row] + eX[col]);
