@@ -647,13 +647,26 @@ __global__ void __launch_bounds__(AsmTC<C, S, MTC, NJW>::NTH, AsmTC<C, S, MTC, N
     cp_async_wait_all();
     __syncthreads();
   }
-  // add the faces' part to the A', B' rows of this block's il pairs
-  for (int t = tid; t < QIL * NP * NZ; t += NTH) {
-    const int j = t % NZ, an = (t / NZ) % NP, ilr = t / (NZ * NP), il = il0 + ilr;
-    if (il >= M * M) continue;
-    const int i = il / M, l = il % M;
-    df2& dst = j < NP ? Ad[(an * M + i) * NV + j * M + l] : Bd[(an * M + i) * NT + (j - NP) * M + l];
-    dst = df_add(dst, dfacc_of(Acc[t]));
+  // add the faces' part to the A', B' rows of this block's il pairs (all of a thread's loads
+  // in flight together)
+  {
+    constexpr int NADD = (QIL * NP * NZ + NTH - 1) / NTH;
+    df2* dst[NADD];
+    df2 old[NADD];
+#pragma unroll
+    for (int x = 0; x < NADD; ++x) {
+      const int t = tid + x * NTH;
+      const int j = t % NZ, an = (t / NZ) % NP, ilr = t / (NZ * NP), il = il0 + ilr;
+      dst[x] = nullptr;
+      if (t < QIL * NP * NZ && il < M * M) {
+        const int i = il / M, l = il % M;
+        dst[x] = j < NP ? Ad + (an * M + i) * NV + j * M + l : Bd + (an * M + i) * NT + (j - NP) * M + l;
+        old[x] = *dst[x];
+      }
+    }
+#pragma unroll
+    for (int x = 0; x < NADD; ++x)
+      if (dst[x]) *dst[x] = df_add(old[x], dfacc_of(Acc[tid + x * NTH]));
   }
 }
 

@@ -75,9 +75,16 @@ __global__ void __launch_bounds__(128) k_pointwise(AssembleArgs a, DevTables T, 
   constexpr int D = C::D, M = C::M, NP = C::NP, NFN = C::NFN, NF = C::NF, NG = C::NG, NGF = C::NGF;
   __shared__ double z[C::NZ][M];
   __shared__ double G[C::GEO];
+  __shared__ double dz[NF * NFN][M];  // vhat - v at the face nodes (the lifting's jumps)
   const int64_t le = blockIdx.x;
   const int64_t e = a.e0 + le;
   load_element<C>(a, e, z, G);
+  __syncthreads();
+  if (C::VISC)
+    for (int t = threadIdx.x; t < NF * NFN * M; t += blockDim.x) {
+      const int fc = t / M, i = t % M;
+      dz[fc][i] = z[NP + fc][i] - z[T.fnodes[fc]][i];
+    }
   __syncthreads();
   const double* Jinv = G;
   const double detJ = G[D * D];
@@ -95,21 +102,23 @@ __global__ void __launch_bounds__(128) k_pointwise(AssembleArgs a, DevTables T, 
     double q[M][D];
     if (C::VISC) {
       for (int i = 0; i < M; ++i) {
-        double gr[D];
+        double gr[D], lift[NF];
         for (int r = 0; r < D; ++r) {
           double s = 0.0;
           for (int b = 0; b < NP; ++b) s += T.dPhi[(r * NG + g) * NP + b] * z[b][i];
           gr[r] = s;
+        }
+        for (int f = 0; f < NF; ++f) {  // the same for every direction k
+          double l = 0.0;
+          for (int c = 0; c < NFN; ++c) l += T.PL[(f * NG + g) * NFN + c] * dz[f * NFN + c][i];
+          lift[f] = l;
         }
         for (int k = 0; k < D; ++k) {
           double s = 0.0;
           for (int r = 0; r < D; ++r) s += Jinv[r * D + k] * gr[r];
           for (int f = 0; f < NF; ++f) {
             const double* Gf = G + D * D + 1 + f * (D + 1);
-            double lift = 0.0;
-            for (int c = 0; c < NFN; ++c)
-              lift += T.PL[(f * NG + g) * NFN + c] * (z[NP + f * NFN + c][i] - z[T.fnodes[f * NFN + c]][i]);
-            s += Gf[k] * (Gf[D] / detJ) * lift;
+            s += Gf[k] * (Gf[D] / detJ) * lift[f];
           }
           q[i][k] = s;
         }
@@ -185,22 +194,23 @@ __global__ void __launch_bounds__(128) k_pointwise(AssembleArgs a, DevTables T, 
     double q[M][D];
     if (C::VISC) {
       for (int i = 0; i < M; ++i) {
-        double gr[D];
+        double gr[D], lift[NF];
         for (int r = 0; r < D; ++r) {
           double s = 0.0;
           for (int b = 0; b < NP; ++b) s += T.dPhiF[((f * D + r) * NGF + gf) * NP + b] * z[b][i];
           gr[r] = s;
+        }
+        for (int fl = 0; fl < NF; ++fl) {  // the same for every direction k
+          double l = 0.0;
+          for (int c = 0; c < NFN; ++c) l += T.PLF[((f * NF + fl) * NGF + gf) * NFN + c] * dz[fl * NFN + c][i];
+          lift[fl] = l;
         }
         for (int k = 0; k < D; ++k) {
           double s = 0.0;
           for (int r = 0; r < D; ++r) s += Jinv[r * D + k] * gr[r];
           for (int fl = 0; fl < NF; ++fl) {
             const double* Gl = G + D * D + 1 + fl * (D + 1);
-            double lift = 0.0;
-            for (int c = 0; c < NFN; ++c)
-              lift += T.PLF[((f * NF + fl) * NGF + gf) * NFN + c] *
-                      (z[NP + fl * NFN + c][i] - z[T.fnodes[fl * NFN + c]][i]);
-            s += Gl[k] * (Gl[D] / detJ) * lift;
+            s += Gl[k] * (Gl[D] / detJ) * lift[fl];
           }
           q[i][k] = s;
         }
