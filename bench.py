@@ -189,6 +189,34 @@ def parse():
     return ap.parse_args()
 
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per element of the mixed tensor-core
+# kernels from one ncu --set full capture on 3,072 elements; every element is its own CTA (or
+# row blocks of one), so traffic grows with the element count and scales to a launch by its
+# elements. Valid only while the kernel sources hash to the digest they were captured on.
+NCU_TRAFFIC = {
+    "source": "profiles/ncu_mixed_kernels_ns3d_p3_n8.md",
+    "sources_sha256": None,
+    "bytes_per_element": {},
+}
+
+
+def kernel_sources_digest() -> str:
+    import hashlib
+    csrc = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_1808_05066_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".hpp")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(name.encode() + b"\0" + f.read())
+    return h.hexdigest()
+
+
+def ncu_traffic_per_element(kind: str):
+    if NCU_TRAFFIC["sources_sha256"] != kernel_sources_digest():
+        return None
+    return NCU_TRAFFIC["bytes_per_element"].get(kind)
+
+
 def _dist():
     from paper_1808_05066_gb300.multirank import world
     return world()
@@ -226,7 +254,7 @@ def main():
 
     from paper_1808_05066_gb300 import hdg
     from paper_1808_05066_gb300.workload import (DeviceWorkload, algorithmic_bytes_per_element, flops_per_element,
-                                                 slice_mma_per_element)
+                                                 slice_flops_per_element)
     if ws > 1:
         dist.init_process_group("nccl", init_method="env://")
     torch.cuda.set_device(local)
@@ -288,18 +316,22 @@ def main():
                 "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x max SM clock", "kernel": dom,
                 "launches": dom_launches, "avg_launch_ms": dom_ms / max(dom_launches, 1), "traffic": None}
     else:
-        # tensor-core kernels of the mixed form: executed bf16 slice-product flops (mma.sync
-        # m16n8k16 = 4096 flops) against the measured sustained bf16 rate (the kernel runs
-        # inside a long step); the HBM side from the kernel's algorithmic bytes
+        # tensor-core kernels of the mixed form: useful bf16 slice-product flops against the
+        # measured sustained bf16 rate (the kernel runs inside a long step); the HBM side from
+        # the kernel's algorithmic bytes; DRAM traffic from the ncu capture of these sources
         pk = measured_peaks()
         kind = dom if dom in ("mixed_assemble", "mixed_face", "mixed_condense") else "mixed_condense"
         dom_ms_k = prof[kind][1]
-        flops = slice_mma_per_element(W.info, viscous, kind) * 4096.0 * E * args.steps
+        flops = slice_flops_per_element(W.info, viscous, kind) * E * args.steps
         tensor = flops / (dom_ms_k / 1e3) / 1e12
         hbm = algorithmic_bytes_per_element(W.info, kind) * E * args.steps / (dom_ms_k / 1e3) / 1e9
+        launches_k = max(prof[kind][0], 1)
+        tpe = ncu_traffic_per_element(kind)
         roof = {"bound": "tensor", "achieved": tensor, "peak": pk["bf16"], "unit": "TFLOP/s",
                 "peak_source": pk["bf16_source"], "kernel": kind, "launches": prof[kind][0],
-                "avg_launch_ms": dom_ms_k / max(prof[kind][0], 1), "traffic": None,
+                "avg_launch_ms": dom_ms_k / launches_k,
+                "traffic": None if tpe is None else tpe * E * args.steps / launches_k,
+                "traffic_source": NCU_TRAFFIC["source"] if tpe is not None else "kernel sources changed since the capture",
                 "hbm": {"achieved": hbm, "peak": pk["hbm"], "unit": "GB/s", "frac": hbm / pk["hbm"],
                         "bytes_per_element": algorithmic_bytes_per_element(W.info, kind)}}
         if roof["hbm"]["frac"] > tensor / pk["bf16"]:

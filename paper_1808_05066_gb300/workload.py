@@ -127,17 +127,18 @@ def flops_per_element(info: dict, viscous: bool, kernel: str) -> float:
 SLICES = 6  # exact bf16 slices per operand in the mixed form's tensor-core products
 
 
-def slice_mma_per_element(info: dict, viscous: bool, kernel: str) -> int:
-    """mma.sync m16n8k16 instructions per element of one mixed-form kernel (4096 bf16 flops
-    each), counted over the 16x8 output tiles that cover real rows and the k tiles whose
-    operator block is nonzero (S(S+1)/2 slice products per tile and k tile):
-      mixed_assemble: rows (i, l, node) = m^2 NP; k tiles per operator ceil(NG/16); the value
-                      operator reaches only the first ceil(NP/8) column tiles;
-      mixed_face:     per face rows (i, l, face node) = m^2 NFN; k tiles per operator
-                      ceil(NGF/16); value operator ceil(NP/8) column tiles, trace operator the
-                      tiles of the face's own trace columns, gradient operators all;
-      mixed_condense: r0 = B - A' X0 (A' rows) and S = D - C' X (C' rows), k = NV, the NT + 1
-                      right-hand sides in blocks of 32."""
+def slice_flops_per_element(info: dict, viscous: bool, kernel: str) -> float:
+    """Useful bf16 slice-product flops per element of one mixed-form tensor-core kernel:
+    2 x rows x columns x contraction length of every nonzero operator block, times the
+    S(S+1)/2 slice products. Tile padding and products a kernel shape adds are not counted, so
+    this never exceeds what a kernel executes:
+      mixed_assemble: rows (i, l, node) = m^2 NP, contraction NG per operator; the value
+                      operator meets the NP interior columns, each of the NR - 1 gradient
+                      operators all NZ;
+      mixed_face:     per face rows m^2 NFN, contraction NGF; value operator NP columns, trace
+                      operator the face's own NFN, each of the NRF - 2 gradient operators all NZ;
+      mixed_condense: r0 = B - A' X0 and S = D - C' X: NV + NT rows, NT + 1 right-hand sides,
+                      contraction NV."""
     D, M = info["dim"], info["m"]
     NP, NFN, NF, NG, NGF = info["Np"], info["Nf"], info["nF"], info["NG"], info["NGF"]
     NV, NT = info["nv"], info["nt"]
@@ -145,25 +146,12 @@ def slice_mma_per_element(info: dict, viscous: bool, kernel: str) -> int:
     NR = D + 1 if viscous else 1
     NRF = D + 2 if viscous else 2
     prod = SLICES * (SLICES + 1) // 2
-    ntn = -(-NZ // 8)
-    nt_val = -(-NP // 8)
     if kernel == "mixed_assemble":
-        kt = -(-NG // 16)
-        return -(-(M * M * NP) // 16) * kt * (nt_val + (NR - 1) * ntn) * prod
+        return 2.0 * prod * (M * M * NP) * NG * (NP + (NR - 1) * NZ)
     if kernel == "mixed_face":
-        kt = -(-NGF // 16)
-        total = 0
-        for f in range(NF):
-            lo, hi = NP + f * NFN, NP + (f + 1) * NFN
-            own = (hi - 1) // 8 - lo // 8 + 1
-            total += -(-(M * M * NFN) // 16) * kt * (nt_val + own + (NRF - 2) * ntn)
-        return total * prod
+        return 2.0 * prod * NF * (M * M * NFN) * NGF * (NP + NFN + (NRF - 2) * NZ)
     if kernel == "mixed_condense":
-        ntiles = 0
-        for c0 in range(0, NT + 1, 32):
-            ntiles += -(-min(32, NT + 1 - c0) // 8)
-        kt = -(-NV // 16)
-        return (-(-NV // 16) + -(-NT // 16)) * ntiles * kt * prod
+        return 2.0 * prod * (NV + NT) * (NT + 1) * NV
     raise ValueError(kernel)
 
 
