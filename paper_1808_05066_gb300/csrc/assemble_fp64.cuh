@@ -162,19 +162,13 @@ __global__ void __launch_bounds__(128) k_pointwise(AssembleArgs a, DevTables T, 
         }
       }
     if (C::VISC) {
-      // G is linear in q: dG/dq_lk = G(v, E_lk)
+      // dG/dq contracted with the rows of Jinv (G is linear in q)
       const ViscFactors<D> vf = visc_factors<D>(v);
-      for (int l = 0; l < M; ++l)
-        for (int k = 0; k < D; ++k) {
-          double Gq[M][D];
-          visc_flux_unit<D>(vf, l, k, ph, Gq);
-          for (int r = 0; r < D; ++r)
-            for (int i = 0; i < M; ++i) {
-              double s = 0.0;
-              for (int j = 0; j < D; ++j) s += Jinv[r * D + j] * Gq[i][j];
-              put(T2, ((r * M + i) * M + l) * D + k, -W * s);
-            }
-        }
+#pragma unroll 1
+      for (int r = 0; r < D; ++r)
+        visc_jac_dir<D>(vf, Jinv + r * D, ph, [&](int i, int l, int k, double val) {
+          put(T2, ((r * M + i) * M + l) * D + k, -W * val);
+        });
     }
   } else if (tid < NG + NF * NGF) {
     const int f = (tid - NG) / NGF;
@@ -266,18 +260,9 @@ __global__ void __launch_bounds__(128) k_pointwise(AssembleArgs a, DevTables T, 
         put(U1, i * M + l, Wf * hA[i].d[l]);
       }
     }
-    if (C::VISC) {
+    if (C::VISC) {  // dG/dq contracted with the normal
       const ViscFactors<D> vf = visc_factors<D>(vh);
-      for (int l = 0; l < M; ++l)
-        for (int k = 0; k < D; ++k) {
-          double Gq[M][D];
-          visc_flux_unit<D>(vf, l, k, ph, Gq);
-          for (int i = 0; i < M; ++i) {
-            double s = 0.0;
-            for (int j = 0; j < D; ++j) s += Gq[i][j] * n[j];
-            put(U2, (i * M + l) * D + k, Wf * s);
-          }
-        }
+      visc_jac_dir<D>(vf, n, ph, [&](int i, int l, int k, double val) { put(U2, (i * M + l) * D + k, Wf * val); });
     }
   }
   if (bad) atomicOr(a.status + e, HDG_STATUS_NONPHYSICAL);

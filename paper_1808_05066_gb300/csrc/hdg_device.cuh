@@ -347,44 +347,64 @@ HDG_DEVI ViscFactors<D> visc_factors(const double* v) {
   return f;
 }
 
-// G(v, E_lk) for the unit gradient E_lk (component l, direction k): the same arithmetic as
-// visc_flux with that q, without the terms that vanish (G is linear in q, so these are the
-// columns of dG/dq).
-template <int D>
-HDG_DEVI void visc_flux_unit(const ViscFactors<D>& f, int l, int k, const PhysParams& ph, double (*G)[D]) {
-  double gV[D][D];
+// sum_j c_j dG_ij/dq_lk for one vector c: the viscous flux (Eq. viscFlux) is linear in q, and
+// differentiating it by hand gives, with V_a = -w_a/v_m, A_a = w_a/v_m^2 and the Kronecker
+// delta d,
+//   momentum i = 1+a, l = 1+b:    mu/v_m (d_ab c_k + d_ak c_b - 2/3 d_bk c_a)
+//   momentum i = 1+a, l = m-1:   -mu (A_a c_k + d_ak c.A - 2/3 A_k c_a)
+//   energy   i = m-1, l = 1+b:    mu/v_m (V_b c_k + V_k c_b - 2/3 d_bk c.V)
+//   energy   i = m-1, l = m-1:   -mu (V.A c_k + V_k c.A - 2/3 A_k c.V) - kappa/(c_v v_m^2) c_k
+// and zero for i = 0 or l = 0. emit(i, l, k, value) receives every entry; the deltas are
+// branches on unrolled indices, so no arithmetic is spent on the vanishing terms.
+template <int D, class Emit>
+HDG_DEVI void visc_jac_dir(const ViscFactors<D>& f, const double* c, const PhysParams& ph, Emit emit) {
+  constexpr int M = D + 2;
+  constexpr double t3 = 2.0 / 3.0;
+  double cA = c[0] * f.A[0], cV = c[0] * f.vel[0], VA = f.vel[0] * f.A[0];
 #pragma unroll
-  for (int i = 0; i < D; ++i)
-#pragma unroll
-    for (int j = 0; j < D; ++j) gV[i][j] = 0.0;
-  if (l == D + 1) {
-#pragma unroll
-    for (int i = 0; i < D; ++i) gV[i][k] = f.A[i];
-  } else if (l >= 1) {
-    gV[l - 1][k] = -f.ivm;
+  for (int j = 1; j < D; ++j) {
+    cA += c[j] * f.A[j];
+    cV += c[j] * f.vel[j];
+    VA += f.vel[j] * f.A[j];
   }
-  double div = gV[0][0];
+  const double mi = ph.mu * f.ivm, kc = (ph.kappa / ph.cv) * f.ivm2;
 #pragma unroll
-  for (int i = 1; i < D; ++i) div = div + gV[i][i];
-  double tau[D][D];
+  for (int k = 0; k < D; ++k) {
 #pragma unroll
-  for (int i = 0; i < D; ++i)
+    for (int l = 0; l < M; ++l) emit(0, l, k, 0.0);
 #pragma unroll
-    for (int j = 0; j < D; ++j) {
-      double t = gV[i][j] + gV[j][i];
-      if (i == j) t = t - (2.0 / 3.0) * div;
-      tau[i][j] = ph.mu * t;
+    for (int i = 1; i < M; ++i) emit(i, 0, k, 0.0);
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+#pragma unroll
+      for (int b = 0; b < D; ++b) {
+        double s = 0.0;
+        bool any = false;
+        if (a == b) {
+          s = c[k];
+          any = true;
+        }
+        if (a == k) {
+          s = any ? s + c[b] : c[b];
+          any = true;
+        }
+        if (b == k) {
+          s = any ? s - t3 * c[a] : -t3 * c[a];
+          any = true;
+        }
+        emit(1 + a, 1 + b, k, any ? mi * s : 0.0);
+      }
+      double s = f.A[a] * c[k] - t3 * f.A[k] * c[a];
+      if (a == k) s += cA;
+      emit(1 + a, M - 1, k, -ph.mu * s);
     }
 #pragma unroll
-  for (int j = 0; j < D; ++j) {
-    G[0][j] = 0.0;
-    double e = f.vel[0] * tau[0][j];
-#pragma unroll
-    for (int i = 1; i < D; ++i) e = e + f.vel[i] * tau[i][j];
-    const double gradT = (ph.kappa / ph.cv) * ((l == D + 1 && j == k) ? f.ivm2 : 0.0);
-#pragma unroll
-    for (int i = 0; i < D; ++i) G[1 + i][j] = -tau[i][j];
-    G[D + 1][j] = -(e + gradT);
+    for (int b = 0; b < D; ++b) {
+      double s = f.vel[b] * c[k] + f.vel[k] * c[b];
+      if (b == k) s -= t3 * cV;
+      emit(M - 1, 1 + b, k, mi * s);
+    }
+    emit(M - 1, M - 1, k, -ph.mu * (VA * c[k] + f.vel[k] * cA - t3 * f.A[k] * cV) - kc * c[k]);
   }
 }
 
