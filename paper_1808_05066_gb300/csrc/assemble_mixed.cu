@@ -76,17 +76,19 @@ struct CondVariant {
   int threads;
   size_t smem;
   void (*kernel)(AssembleArgs);
+  int ctas_per_element;
+  unsigned grid(int64_t ne) const { return (unsigned)(ne * ctas_per_element); }
 };
 
 template <class C, int NTH>
 CondVariant make_cond_variant() {
-  return CondVariant{NTH, CondTC<C, NTH, kSlices>::bytes, &k_condense_tc<C, NTH, kSlices>};
+  return CondVariant{NTH, CondTC<C, NTH, kSlices>::bytes, &k_condense_tc<C, NTH, kSlices>, 1};
 }
 
 // 16-column blocks, two CTAs per SM
 template <class C>
 CondVariant make_cond_variant2() {
-  return CondVariant{256, CondTC2<C, 256, kSlices>::bytes, &k_condense_tc2<C, 256, kSlices>};
+  return CondVariant{256, CondTC2<C, 256, kSlices>::bytes, &k_condense_tc2<C, 256, kSlices>, 2};
 }
 
 // Times `launch` once on the stream (the chunk's outputs are rewritten each time).
@@ -251,7 +253,7 @@ int run_mixed(hdg_ctx* ctx, const double* V, const double* Vhat, const double* h
           k_condense_prep<C, kSlices><<<(unsigned)a.ne, TC::PTH, TC::prep_bytes, s>>>(a);
           float ms = 0.f;
           const CondVariant& cv = cvariants[i];
-          int rc = time_launch(s, [&] { cv.kernel<<<(unsigned)a.ne, cv.threads, cv.smem, s>>>(a); }, &ms);
+          int rc = time_launch(s, [&] { cv.kernel<<<cv.grid(a.ne), cv.threads, cv.smem, s>>>(a); }, &ms);
           if (rc) return rc;
           if (ms < best) {
             best = ms;
@@ -277,7 +279,7 @@ int run_mixed(hdg_ctx* ctx, const double* V, const double* Vhat, const double* h
     }
     {
       LaunchScope ls(ctx, HDG_KERNEL_MIXED_CONDENSE, s);
-      cv.kernel<<<(unsigned)a.ne, cv.threads, cv.smem, s>>>(a);
+      cv.kernel<<<cv.grid(a.ne), cv.threads, cv.smem, s>>>(a);
     }
     if (int rc_d = chunk_done(ctx, e0, a.ne, s)) return rc_d;
   }

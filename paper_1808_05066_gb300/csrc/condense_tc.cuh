@@ -619,7 +619,8 @@ __global__ void __launch_bounds__(NTHREADS) k_condense_tc(AssembleArgs a) {
 // of two below its row's (column's) largest, not below itself as FP32 does: with three the
 // small entries of A' lose about two digits against FP32 and X misses 1e-10; four give
 // 2^-33 of the largest, as accurate as the FP32 product. About 108 KB of shared memory, so
-// that two elements share an SM and one hides the other's latency.
+// that two CTAs share an SM and one hides the other's latency. Launched with two CTAs per
+// element (grid 2 ne).
 // ------------------------------------------------------------------------------------
 template <class C, int NTHREADS, int OZS>
 struct CondTC2 {
@@ -663,7 +664,10 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_condense_tc2(AssembleArgs a) {
   int* eX = eC + MTC * 16;                                                          // [CB]
   __shared__ int s_bad;
   __shared__ float s_corr[2], s_xmax;
-  const int64_t le = blockIdx.x;
+  // two CTAs per element, on the even and the odd blocks of right-hand sides: the slices of
+  // A' and C' that every block re-reads are then live for half as many elements at a time
+  const int64_t le = blockIdx.x >> 1;
+  const int half = (int)(blockIdx.x & 1);
   const int64_t e = a.e0 + le;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint2* slA = reinterpret_cast<const uint2*>(a.oz) + le * P::slice_u2;
@@ -698,7 +702,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_condense_tc2(AssembleArgs a) {
   auto sX = [&](int c) { return oz_scale(eX[c]); };
   auto xhi = [&](int r, int c) { return Xb[r * CB + c].hi; };
 
-  for (int c0 = 0; c0 < NT + 1; c0 += CB) {
+  for (int c0 = half * CB; c0 < NT + 1; c0 += 2 * CB) {
     const int nc = (NT + 1 - c0) < CB ? (NT + 1 - c0) : CB;
     // the block's D' columns, read by the Schur epilogue, copied in the background meanwhile
     for (int t = tid; t < NT * CB; t += NTHREADS) {
