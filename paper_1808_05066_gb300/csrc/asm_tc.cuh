@@ -677,20 +677,32 @@ template <class C>
 __global__ void __launch_bounds__(128) k_asm_residual(AssembleArgs a, DevTables T) {
   constexpr int D = C::D, M = C::M, NP = C::NP, NFN = C::NFN, NF = C::NF, NG = C::NG, NGF = C::NGF;
   constexpr int NV = C::NV, NT = C::NT;
+  constexpr int PV = M * (1 + D);  // the mass term and the flux rows of a volume point
   __shared__ double Rv[NV];
+  __shared__ double Pv[NG * PV];        // the point values the residual reads, in FP64
+  __shared__ double Pf[NF * NGF * M];   // (each converted once, not once per use)
   const int64_t le = blockIdx.x;
   const int64_t e = a.e0 + le;
   const int tid = threadIdx.x;
   const df2* ptv = reinterpret_cast<const df2*>(a.ptv) + le * NG * C::PT_VOL;
   const df2* ptf = reinterpret_cast<const df2*>(a.ptf) + le * NF * NGF * C::PT_FACE;
   double* Rout = a.R + e * (int64_t)(NV + NT);
+  for (int t = tid; t < NG * PV; t += blockDim.x) {
+    const df2 p = ptv[(t / PV) * C::PT_VOL + t % PV];
+    Pv[t] = df_to_f64(p.hi, p.lo);
+  }
+  for (int t = tid; t < NF * NGF * M; t += blockDim.x) {
+    const df2 p = ptf[(t / M) * C::PT_FACE + t % M];
+    Pf[t] = df_to_f64(p.hi, p.lo);
+  }
+  __syncthreads();
   for (int t = tid; t < NV; t += blockDim.x) {
     const int an = t / M, i = t % M;
     double s = a.hist ? -a.hist[e * NV + t] : 0.0;
     for (int g = 0; g < NG; ++g) {
-      const df2* P = ptv + g * C::PT_VOL;
-      s += T.Phi[g * NP + an] * df_val(P[i]);
-      for (int r = 0; r < D; ++r) s += T.dPhi[(r * NG + g) * NP + an] * df_val(P[M + r * M + i]);
+      const double* P = Pv + g * PV;
+      s += T.Phi[g * NP + an] * P[i];
+      for (int r = 0; r < D; ++r) s += T.dPhi[(r * NG + g) * NP + an] * P[M + r * M + i];
     }
     Rv[t] = s;
   }
@@ -700,7 +712,7 @@ __global__ void __launch_bounds__(128) k_asm_residual(AssembleArgs a, DevTables 
       const int c = t / M, i = t % M;
       double s = 0.0;
       for (int gf = 0; gf < NGF; ++gf)
-        s += T.PhiF[(f * NGF + gf) * NP + T.fnodes[f * NFN + c]] * df_val(ptf[(f * NGF + gf) * C::PT_FACE + i]);
+        s += T.PhiF[(f * NGF + gf) * NP + T.fnodes[f * NFN + c]] * Pf[(f * NGF + gf) * M + i];
       Rv[T.fnodes[f * NFN + c] * M + i] += s;
       Rout[NV + (f * NFN + c) * M + i] = s;
     }
