@@ -195,8 +195,8 @@ def parse():
 # elements. Valid only while the kernel sources hash to the digest they were captured on.
 NCU_TRAFFIC = {
     "source": "profiles/ncu_mixed_kernels_ns3d_p3_n8.md",
-    "sources_sha256": "a294d3f3d85d6a0fb6cec5be8f24c3e5208bc031273aedde28c53a1083c535e4",
-    "bytes_per_element": {"mixed_assemble": 601_344, "mixed_face": 1_256_781, "mixed_condense": 2_596_913},
+    "sources_sha256": "8ba32fe816086478b3f15a9bb66d35afb172852063e4e44965ffe7cd9133a769",
+    "bytes_per_element": {"mixed_assemble": 600_853, "mixed_face": 1_257_236, "mixed_condense": 2_568_499},
 }
 
 
