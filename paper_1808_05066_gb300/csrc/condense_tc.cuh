@@ -702,6 +702,23 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_condense_tc2(AssembleArgs a) {
   auto sX = [&](int c) { return oz_scale(eX[c]); };
   auto xhi = [&](int r, int c) { return Xb[r * CB + c].hi; };
 
+  // W = sc B for the block at column cb: all of a thread's loads in flight together
+  auto w_init = [&](int cb) {
+    const int ncb = (NT + 1 - cb) < CB ? (NT + 1 - cb) : CB;
+    constexpr int NWI = (NV * CB + NTHREADS - 1) / NTHREADS;
+    df2 bv[NWI];
+#pragma unroll
+    for (int x = 0; x < NWI; ++x) {
+      const int t = tid + x * NTHREADS, r = t / CB, c = t % CB, col = cb + c;
+      bv[x] = (t >= NV * CB || c >= ncb) ? df2{0.f, 0.f} : (col < NT ? Bd[r * NT + col] : df_from(R[r]));
+    }
+#pragma unroll
+    for (int x = 0; x < NWI; ++x) {
+      const int t = tid + x * NTHREADS;
+      if (t < NV * CB) W[t] = (bv[x].hi + bv[x].lo) * sc[t / CB];
+    }
+  };
+  if (half * CB < NT + 1) w_init(half * CB);
   for (int c0 = half * CB; c0 < NT + 1; c0 += 2 * CB) {
     const int nc = (NT + 1 - c0) < CB ? (NT + 1 - c0) : CB;
     // the block's D' columns, read by the Schur epilogue, copied in the background meanwhile
@@ -715,20 +732,6 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_condense_tc2(AssembleArgs a) {
       if (c >= nc) return df2{0.f, 0.f};
       return col < NT ? Bd[r * NT + col] : df_from(R[r]);
     };
-    {  // W = sc B, all of a thread's loads in flight together
-      constexpr int NWI = (NV * CB + NTHREADS - 1) / NTHREADS;
-      df2 bv[NWI];
-#pragma unroll
-      for (int x = 0; x < NWI; ++x) {
-        const int t = tid + x * NTHREADS;
-        bv[x] = t < NV * CB ? bval(t / CB, t % CB) : df2{0.f, 0.f};
-      }
-#pragma unroll
-      for (int x = 0; x < NWI; ++x) {
-        const int t = tid + x * NTHREADS;
-        if (t < NV * CB) W[t] = (bv[x].hi + bv[x].lo) * sc[t / CB];
-      }
-    }
     if (tid < 2) s_corr[tid] = 0.f;
     if (tid == 0) s_xmax = 0.f;
     __syncthreads();
@@ -862,6 +865,9 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_condense_tc2(AssembleArgs a) {
       else
         a.g[e * NT + row] = df_to_f64(t.hi, t.lo);
     });
+    // W is free since the last correction: warps done with their Schur tasks fill it for
+    // this CTA's next block while the others finish
+    if (c0 + 2 * CB < NT + 1) w_init(c0 + 2 * CB);
     __syncthreads();
   }
   if (tid == 0 && s_bad) atomicOr(a.status + e, s_bad);
