@@ -195,8 +195,8 @@ def parse():
 # elements. Valid only while the kernel sources hash to the digest they were captured on.
 NCU_TRAFFIC = {
     "source": "profiles/ncu_mixed_kernels_ns3d_p3_n8.md",
-    "sources_sha256": "8ba32fe816086478b3f15a9bb66d35afb172852063e4e44965ffe7cd9133a769",
-    "bytes_per_element": {"mixed_assemble": 600_853, "mixed_face": 1_257_236, "mixed_condense": 2_568_499},
+    "sources_sha256": "20075d4658193ac71f4590ac13b28d664f00857f590874bfc6616ac4ea82f691",
+    "bytes_per_element": {"mixed_assemble": 600_309, "mixed_face": 1_257_285, "mixed_condense": 2_606_220},
 }
 
 
