@@ -103,8 +103,7 @@ def flops_per_element(info: dict, viscous: bool, kernel: str) -> float:
       assemble: volume contraction per (i, l): NP x [NP x ng x NR + NT' x ng x (NR-1)]
                 + the left factor NP x ng x NR x (D+1); face contraction per face and (i, l):
                 NFN x NZ x NGF x NRF + NFN x NGF x NRF;
-      condense: LU NV^3/3 + solves (NT + 1) NV^2 + Schur NT^2 NV + NT NV;
-      condense_df: the double-float work of the mixed condensation."""
+      condense: LU NV^3/3 + solves (NT + 1) NV^2 + Schur NT^2 NV + NT NV."""
     D, M = info["dim"], info["m"]
     NP, NFN, NF, NG, NGF = info["Np"], info["Nf"], info["nF"], info["NG"], info["NGF"]
     NV, NT = info["nv"], info["nt"]
@@ -117,10 +116,6 @@ def flops_per_element(info: dict, viscous: bool, kernel: str) -> float:
         return 2.0 * (vol + face)
     if kernel == "condense":
         return 2.0 * (NV ** 3 / 3.0 + (NT + 1) * NV ** 2 + NT * NT * NV + NT * NV)
-    if kernel == "condense_df":
-        # double-float part of the mixed condensation: refinement residuals (3 sweeps) and
-        # the Schur products; the FP32 LU and triangular solves are not counted
-        return 2.0 * (3 * (NT + 1) * NV ** 2 + NT * NT * NV + NT * NV)
     raise ValueError(kernel)
 
 
