@@ -128,6 +128,21 @@ int hdg_assemble_condense(hdg_ctx_t ctx, const double* V, const double* Vhat, co
                           double mass_coef, int precision, double* S, double* g, double* recov,
                           double* R, int32_t* elem_status, void* stream);
 
+/* hdg_assemble_condense replayed as a CUDA graph (the same local elimination of Sec. 3.2,
+ * the same arguments, results and status bits). An execution mechanism of this library: the
+ * paper has no counterpart. The first call with a given set of arguments runs
+ * hdg_assemble_condense on `stream` (which tunes the kernel shapes and allocates the scratch)
+ * and then captures the same launch sequence, without running it, on a private stream; later
+ * calls with the same pointers, precision, mass_coef and library scratch launch that graph on
+ * `stream`, skipping the per-kernel launches. The graph reads the arrays' current contents, so
+ * new values in the same buffers are used. Any other argument (or a scratch reallocated by a
+ * call of the other precision) captures again. If the capture fails, the call still returns
+ * the ordinary call's results and the context keeps the ordinary path. The graph belongs to
+ * the context (freed by hdg_ctx_destroy); one call at a time per context. */
+int hdg_assemble_condense_graph(hdg_ctx_t ctx, const double* V, const double* Vhat, const double* hist,
+                                double mass_coef, int precision, double* S, double* g, double* recov, double* R,
+                                int32_t* elem_status, void* stream);
+
 /* hdg_assemble_condense with S and g delivered to HOST memory (Sec. 3.2, the same local
  * elimination as hdg_assemble_condense). The elements are processed in chunks; each chunk's S
  * goes to one of two library-owned device buffers and is copied to S_host on an internal copy

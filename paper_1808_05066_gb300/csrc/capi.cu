@@ -291,6 +291,8 @@ void hdg_ctx_destroy(hdg_ctx_t c) {
     if (b) cudaFree(b);
   if (c->h_red) cudaFreeHost(c->h_red);
   if (c->lu_graph_exec) cudaGraphExecDestroy(c->lu_graph_exec);
+  if (c->ac_graph) cudaGraphExecDestroy(c->ac_graph);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   if (c->copy_stream) {
     cudaStreamSynchronize(c->copy_stream);
     cudaStreamDestroy(c->copy_stream);
@@ -346,6 +348,66 @@ int hdg_assemble_condense(hdg_ctx_t ctx, const double* V, const double* Vhat, co
   return hdg::assemble_condense_fp64(ctx, V, Vhat, hist, mass_coef, S, g, recov, R, st, s);
 }
 
+
+int hdg_assemble_condense_graph(hdg_ctx_t ctx, const double* V, const double* Vhat, const double* hist,
+                                double mass_coef, int precision, double* S, double* g, double* recov, double* R,
+                                int32_t* elem_status, void* stream) {
+  HDG_REQUIRE(ctx && V && Vhat && S && g && recov && R, "hdg_assemble_condense_graph: null argument");
+  HDG_REQUIRE(precision == HDG_PREC_FP64 || precision == HDG_PREC_MIXED, "hdg_assemble_condense_graph: precision");
+  DeviceGuard guard(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  using Key = hdg_ctx::GraphKey;
+  Key k;
+  const void* args[9] = {V, Vhat, hist, S, g, recov, R, elem_status, ctx->d_status};
+  for (int i = 0; i < 9; ++i) k.p[i] = args[i];
+  k.mass_coef = mass_coef;
+  k.precision = precision;
+  k.scratch = ctx->d_scr;
+  k.chunk = ctx->chunk;
+  if (ctx->ac_graph && ctx->ac_key == k) {  // replay
+    HDG_CK(cudaGraphLaunch(ctx->ac_graph, s));
+    for (int c = 0; c < HDG_KERNEL_CLASSES; ++c) ctx->launches[c] += ctx->ac_launches[c];
+    return HDG_OK;
+  }
+  // an ordinary call computes this call's result (and tunes and allocates what the sequence
+  // needs); the same sequence is then captured, without running, on a private stream
+  int rc = hdg_assemble_condense(ctx, V, Vhat, hist, mass_coef, precision, S, g, recov, R, elem_status, stream);
+  if (rc != HDG_OK || ctx->ac_graph_failed) return rc;
+  k.p[8] = ctx->d_status;
+  k.scratch = ctx->d_scr;
+  k.chunk = ctx->chunk;
+  if (!ctx->cap_stream) HDG_CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+  int64_t before[HDG_KERNEL_CLASSES];
+  for (int c = 0; c < HDG_KERNEL_CLASSES; ++c) before[c] = ctx->launches[c];
+  const bool prof = ctx->prof;
+  ctx->prof = false;  // no timing events inside the graph
+  cudaGraph_t graph = nullptr;
+  int rc2 = HDG_OK;
+  cudaError_t err = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal);
+  if (err == cudaSuccess) {
+    rc2 = hdg_assemble_condense(ctx, V, Vhat, hist, mass_coef, precision, S, g, recov, R, elem_status,
+                                ctx->cap_stream);
+    err = cudaStreamEndCapture(ctx->cap_stream, &graph);
+  }
+  ctx->prof = prof;
+  for (int c = 0; c < HDG_KERNEL_CLASSES; ++c) {
+    ctx->ac_launches[c] = ctx->launches[c] - before[c];
+    ctx->launches[c] = before[c];
+  }
+  cudaGraphExec_t exec = nullptr;
+  if (err == cudaSuccess && rc2 == HDG_OK && graph) err = cudaGraphInstantiate(&exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  if (err != cudaSuccess || rc2 != HDG_OK || !exec) {  // keep the ordinary path from now on
+    if (exec) cudaGraphExecDestroy(exec);
+    cudaGetLastError();
+    ctx->ac_graph_failed = true;
+    return HDG_OK;
+  }
+  if (ctx->ac_graph) cudaGraphExecDestroy(ctx->ac_graph);
+  ctx->ac_graph = exec;
+  ctx->ac_key = k;
+  return HDG_OK;
+}
 
 int hdg_assemble_condense_host(hdg_ctx_t ctx, const double* V, const double* Vhat, const double* hist,
                                double mass_coef, int precision, double* S_host, double* g_host, double* recov,

@@ -59,6 +59,25 @@ struct hdg_ctx {
   int64_t Sbuf_chunk = 0;  // elements per buffer
   cudaStream_t copy_stream = nullptr;
   cudaEvent_t ev_done[2] = {nullptr, nullptr}, ev_copied[2] = {nullptr, nullptr};
+  // CUDA graph of one assemble + condense (hdg_assemble_condense_graph): the arguments and
+  // library state it was captured with, and the launches it adds per replay
+  struct GraphKey {
+    const void* p[9] = {};
+    double mass_coef = 0.0;
+    int precision = -1;
+    const void* scratch = nullptr;
+    int64_t chunk = 0;
+    bool operator==(const GraphKey& o) const {
+      for (int i = 0; i < 9; ++i)
+        if (p[i] != o.p[i]) return false;
+      return mass_coef == o.mass_coef && precision == o.precision && scratch == o.scratch && chunk == o.chunk;
+    }
+  };
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t ac_graph = nullptr;
+  GraphKey ac_key;
+  int64_t ac_launches[HDG_KERNEL_CLASSES] = {0};
+  bool ac_graph_failed = false;
   // Newton workspace
   double *d_S = nullptr, *d_g = nullptr, *d_recov = nullptr, *d_R = nullptr, *d_dV = nullptr, *d_dVh = nullptr;
   int32_t* d_status = nullptr;

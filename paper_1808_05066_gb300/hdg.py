@@ -37,7 +37,7 @@ EXPORTED = [
     "hdg_profile_reset", "hdg_profile_read", "hdg_last_error", "hdg_assemble_condense_noalloc",
     "hdg_mlp_param_count", "hdg_mlp_init", "hdg_mlp_features", "hdg_mlp_forward", "hdg_mlp_gradient",
     "hdg_mlp_train_step", "hdg_mlp_apply_trace", "hdg_mlp_stats", "hdg_mlp_standardize", "hdg_mlp_target",
-    "hdg_axpby", "hdg_assemble_condense_host",
+    "hdg_axpby", "hdg_assemble_condense_host", "hdg_assemble_condense_graph",
 ]
 HDG_KERNEL_POINTWISE = 0
 HDG_KERNEL_ASSEMBLE = 1
@@ -110,6 +110,7 @@ def _load():
         "hdg_last_error": (ctypes.c_char_p, []),
         "hdg_assemble_condense_noalloc": (c_int, [P, P, P, P, c_double, P, P, P, P, P, P]),
         "hdg_assemble_condense_host": (c_int, [P, P, P, P, c_double, c_int, P, P, P, P, P, P]),
+        "hdg_assemble_condense_graph": (c_int, [P, P, P, P, c_double, c_int, P, P, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -209,6 +210,13 @@ def hdg_assemble_condense(ctx, V, Vhat, hist, mass_coef, precision, S, g, recov,
                           stream=None):
     _check(_lib.hdg_assemble_condense(ctx, _ptr(V), _ptr(Vhat), _ptr(hist), mass_coef, precision, _ptr(S),
                                       _ptr(g), _ptr(recov), _ptr(R), _ptr(elem_status), _stream(stream)))
+
+
+def hdg_assemble_condense_graph(ctx, V, Vhat, hist, mass_coef, precision, S, g, recov, R, elem_status=None,
+                                stream=None):
+    """hdg_assemble_condense replayed as a CUDA graph after its first call with these arguments."""
+    _check(_lib.hdg_assemble_condense_graph(ctx, _ptr(V), _ptr(Vhat), _ptr(hist), mass_coef, precision, _ptr(S),
+                                            _ptr(g), _ptr(recov), _ptr(R), _ptr(elem_status), _stream(stream)))
 
 
 def hdg_assemble_condense_host(ctx, V, Vhat, hist, mass_coef, precision, S_host, g_host, recov, R,
