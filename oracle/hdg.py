@@ -94,6 +94,16 @@ class Problem:
     def n_trace(self):
         return self.mesh.nFaces * self.Nf * self.m
 
+    # -- viscous fluxes (Sec. 3.3) ---------------------------------------------------------
+    def volume_viscous_flux(self, v, q):
+        """G(v_h, q_h) [..., m, d] at volume points, the viscous flux of Eq. hDG_NS1."""
+        return ph.viscous_flux(v, q, self.phys)
+
+    def face_viscous_flux(self, vhat, v, q, n):
+        """Viscous numerical flux ghat_h = G(vhat_h, q_h) . n of Eq. numericalFluxNS_2, the
+        option used in all of Sec. 5; the interior trace v is not used by this option."""
+        return np.einsum("...mj,j->...m", ph.viscous_flux(vhat, q, self.phys), n)
+
     # -- residuals ----------------------------------------------------------------------
     def element_residual(self, e, Q, V, Vh, mass_coef=0.0, hist_w=None):
         """Local residuals for a batch [B, ...] of states of element e.
@@ -108,7 +118,7 @@ class Problem:
         Rq = None
         if self.viscous:
             q = np.einsum("ga,bamk->bgmk", T.phi, Q)
-            flux = flux + ph.viscous_flux(v, q, self.phys)
+            flux = flux + self.volume_viscous_flux(v, q)
             # Eq. hDG_NS0: (q, r) + (v, div r) - <vhat, r.n>
             Rq = (np.einsum("g,ga,bgmk->bamk", T.W, T.phi, q)
                   + np.einsum("g,gak,bgm->bamk", T.W, T.gphi, v))
@@ -126,7 +136,7 @@ class Problem:
             fh = ph.numerical_flux_inviscid(vhf, vf, n, g)
             if self.viscous:
                 qf = np.einsum("ga,bamk->bgmk", T.phif[f], Q)
-                fh = fh + np.einsum("bgmj,j->bgm", ph.viscous_flux(vhf, qf, self.phys), n)
+                fh = fh + self.face_viscous_flux(vhf, vf, qf, n)
                 Rq = Rq - np.einsum("g,ga,bgm,k->bamk", T.Wf[f], T.phif[f], vhf, n)
             Rv = Rv + np.einsum("g,ga,bgm->bam", T.Wf[f], T.phif[f], fh)
             # Eq. hDG2 / hDG_NS2: element contribution <fhat + ghat, mu>
