@@ -53,16 +53,24 @@ enum {
   HDG_ERR_NONPHYSICAL = 2, /* some element has v_m >= 0 or non-positive rho / p  */
   HDG_ERR_SINGULAR = 3,    /* zero pivot in an element factorisation              */
   HDG_ERR_REFINE = 4,      /* iterative refinement did not reach its tolerance    */
-  HDG_ERR_NOT_CONVERGED = 5,
-  HDG_ERR_TIMEOUT = 6,
+  HDG_ERR_NOT_CONVERGED = 5, /* Newton or the trace solver missed its tolerance          */
+  /* 6 is not used: no kernel of this library waits on another, so nothing can time out */
   HDG_ERR_CUDA = 7,
   HDG_ERR_UNSUPPORTED = 8  /* (dim, p, quadrature, physics) not compiled in        */
 };
 
 enum { HDG_PREC_FP64 = 0, HDG_PREC_MIXED = 1 };
 enum { HDG_SOLVER_AUTO = 0, HDG_SOLVER_GMRES = 1, HDG_SOLVER_DENSE = 2 };
-/* per-element status bits written by hdg_assemble_condense */
-enum { HDG_ELEM_NONPHYSICAL = 1, HDG_ELEM_SINGULAR = 2, HDG_ELEM_REFINE = 4 };
+/* trace spaces of Sec. 3.4: E^E_h empty (HDG), all faces (EDG), interior faces (IEDG) */
+enum { HDG_SCHEME_HDG = 0, HDG_SCHEME_EDG = 1, HDG_SCHEME_IEDG = 2 };
+/* per-element status bits written by hdg_assemble_condense:
+ *   NONPHYSICAL  v_m >= 0 or non-positive rho / p at a quadrature point
+ *   SINGULAR     zero pivot in the element factorisation
+ *   REFINE       mixed form: the iterative refinement of X = A^{-1}[B | R_v] missed its
+ *                tolerance (left set only when the FP64 recomputation is switched off)
+ *   FP64         mixed form: the block missed the tolerance and was recomputed by the FP64
+ *                kernels (hdg_ctx_set_refinement); its S, g, X, y are the FP64 form's */
+enum { HDG_ELEM_NONPHYSICAL = 1, HDG_ELEM_SINGULAR = 2, HDG_ELEM_REFINE = 4, HDG_ELEM_FP64 = 8 };
 
 typedef struct hdg_mesh* hdg_mesh_t;
 typedef struct hdg_ctx* hdg_ctx_t;
@@ -84,10 +92,18 @@ typedef struct {
 
 /* Mesh T_h (Sec. 3.1.1): the n[0] x .. x n[dim-1] periodic grid on the box
  * [lo, hi], each cell split into 2 triangles / 6 tetrahedra (Kuhn split, the same in
- * every cell). p = polynomial degree k (1..4), quad_points = K (0 selects p+1).
- * Host-only work; the mesh owns host arrays only. Errors: HDG_ERR_INVALID_ARG. */
-int hdg_mesh_create(int dim, const int64_t n[3], const double lo[3], const double hi[3], int p,
-                    int quad_points, hdg_mesh_t* out);
+ * every cell; element e = (cells in x-fastest order) x (2 or 6) + local index).
+ *   p_per_elem  host array [E] of per-element degrees, or NULL for the uniform degree p.
+ *               Meshes whose elements differ in degree are not built: a non-uniform array
+ *               returns HDG_ERR_UNSUPPORTED (HDG_ERR_INVALID_ARG for a degree outside 1..4).
+ *   p           polynomial degree k of Sec. 3.1.2 (1..4).
+ *   scheme      trace space of Sec. 3.4: HDG_SCHEME_HDG (built); HDG_SCHEME_EDG and
+ *               HDG_SCHEME_IEDG return HDG_ERR_UNSUPPORTED.
+ *   quad_points K Gauss-Jacobi points per direction, exact to degree 2K-1 (0 selects p+1).
+ * Host-only work; the mesh owns host arrays only (freed by hdg_mesh_destroy).
+ * Errors: HDG_ERR_INVALID_ARG, HDG_ERR_UNSUPPORTED. */
+int hdg_mesh_create(int dim, const int64_t n[3], const double lo[3], const double hi[3], const int8_t* p_per_elem,
+                    int p, int scheme, int quad_points, hdg_mesh_t* out);
 void hdg_mesh_destroy(hdg_mesh_t mesh);
 int hdg_mesh_get_info(hdg_mesh_t mesh, hdg_mesh_info* out);
 /* Host copies of the topology: face_of [E][nF], fnode_map [E][nF][Nf] (canonical face
@@ -105,6 +121,22 @@ int hdg_mesh_copy_coords(hdg_mesh_t mesh, double* xnode, double* xfnode, double*
  * everything is freed by hdg_ctx_destroy. The mesh must outlive the context. */
 int hdg_ctx_create(hdg_mesh_t mesh, const hdg_physics* phys, int device, hdg_ctx_t* out);
 void hdg_ctx_destroy(hdg_ctx_t ctx);
+
+/* Mixed form only: tolerance of the refinement status bit and what happens to a flagged
+ * block. A block is flagged when its last correction, squared over the one before it, is
+ * above tol times the largest |X| entry (default tol 1e-10: the error left after the last
+ * correction is about that ratio). With fp64_fallback (the default) the flagged elements
+ * of each chunk are recomputed by the FP64 kernels on the same stream, without a host
+ * synchronisation, and carry HDG_ELEM_FP64 instead of HDG_ELEM_REFINE; without it the bit
+ * stays set and hdg_newton_solve / hdg_newton_step return HDG_ERR_REFINE. tol = 0 flags
+ * every block whose last correction is not exactly zero. Errors: HDG_ERR_INVALID_ARG for
+ * tol outside [0, 1). Drops a graph captured by hdg_assemble_condense_graph. */
+int hdg_ctx_set_refinement(hdg_ctx_t ctx, double tol, int fp64_fallback);
+
+/* Trace solver of the Newton iterations of hdg_newton_solve / hdg_newton_step: method as for
+ * hdg_trace_solve (default HDG_SOLVER_AUTO), relative tolerance (default 1e-12) and iteration
+ * limit (default 600). Errors: HDG_ERR_INVALID_ARG. */
+int hdg_ctx_set_trace_solver(hdg_ctx_t ctx, int method, double rtol, int max_it);
 
 /* Entropy variables of Sec. 2.3, v = dH/du for H = -rho s: converts n_points primitive
  * states prim [n][m] = (rho, V_1..V_d, p) to v [n][m] (device). */
@@ -142,6 +174,9 @@ int hdg_assemble_condense(hdg_ctx_t ctx, const double* V, const double* Vhat, co
 int hdg_assemble_condense_graph(hdg_ctx_t ctx, const double* V, const double* Vhat, const double* hist,
                                 double mass_coef, int precision, double* S, double* g, double* recov, double* R,
                                 int32_t* elem_status, void* stream);
+/* Number of graph launches made by hdg_assemble_condense_graph on this context so far (0 if
+ * every call ran the ordinary path, e.g. because the capture failed). */
+int hdg_ctx_graph_replays(hdg_ctx_t ctx, int64_t* replays);
 
 /* hdg_assemble_condense with S and g delivered to HOST memory (Sec. 3.2, the same local
  * elimination as hdg_assemble_condense). The elements are processed in chunks; each chunk's S
@@ -161,14 +196,15 @@ int hdg_assemble_condense_host(hdg_ctx_t ctx, const double* V, const double* Vha
 
 /* The same FP64 assemble + condense for callers that must not allocate device memory
  * during the call (the paper has no counterpart: this is a deployment variant). Such
- * callers include code running while a stream is captured into a CUDA graph (cudaMalloc
- * cannot be captured), runtimes that give the library a fixed memory arena, and loops
- * where cudaMalloc/cudaFree and their implicit synchronisation are not acceptable.
+ * callers include runtimes that give the library a fixed memory arena and forbid further
+ * cudaMalloc/cudaFree, and loops where an allocation and the implicit device
+ * synchronisation of cudaFree are not acceptable.
  * The call allocates nothing: its scratch is a 64 MiB static device array, present on every
  * GPU that loads the library until the process exits; elements are processed in chunks
  * that fit it. A configuration whose single-element scratch exceeds 64 MiB is rejected with
  * HDG_ERR_INVALID_ARG. The first call on a device resolves the array's device address
- * (cudaGetSymbolAddress) with that device current: make it before any stream capture.
+ * (cudaGetSymbolAddress) with that device current and keeps it for the process; after a
+ * cudaDeviceReset of that device the address is stale and further calls are invalid.
  * All calls share the array, so calls whose kernels overlap on the GPU race; order them
  * on one stream (or synchronise). Nothing in the array needs clearing between calls.
  * Arguments as for hdg_assemble_condense with precision FP64; elem_status is required
@@ -180,7 +216,8 @@ int hdg_assemble_condense_noalloc(hdg_ctx_t ctx, const double* V, const double* 
 /* Global trace system sum_e P_e^T S_e P_e dVhat = -sum_e P_e^T g_e (Sec. 3.2: only vhat
  * is globally coupled). method: HDG_SOLVER_GMRES (restarted GMRES(30), face-block Jacobi
  * preconditioner), HDG_SOLVER_DENSE (assembled dense LU with partial pivoting, for
- * n_trace <= 16384) or HDG_SOLVER_AUTO. dVhat [F][Nf][m] device output. Writes *iters and
+ * n_trace <= 16384) or HDG_SOLVER_AUTO (dense up to 4096 unknowns, else GMRES).
+ * dVhat [F][Nf][m] device output. Writes *iters and
  * *final_res (relative residual) on the host, so it synchronises the stream.
  * HDG_ERR_NOT_CONVERGED if rtol was not reached in max_it iterations. */
 int hdg_trace_solve(hdg_ctx_t ctx, const double* S, const double* g, double* dVhat, int method, double rtol,
@@ -199,16 +236,54 @@ int hdg_trace_matvec(hdg_ctx_t ctx, const double* S, const double* x, double* y,
  * host scalar *norm (synchronises). */
 int hdg_residual_norm(hdg_ctx_t ctx, const double* R, double* norm, void* stream);
 
-/* One implicit time step by Newton's method: repeats assemble_condense, trace_solve,
- * recover and the update V += dV, Vhat += dVhat until |R| <= tol max(1, |R_0|) or
- * max_newton updates were made. V and Vhat are updated in place; *newton_iters and
- * *res_norm (final) are written on the host; res_history (host, nullable, max_newton + 1
- * entries) receives the residual norm before each update, trace_iters (host, nullable) the
- * total trace-solver iterations. Uses context-owned workspaces (allocated on first call).
- * HDG_ERR_NOT_CONVERGED / HDG_ERR_NONPHYSICAL / HDG_ERR_SINGULAR on failure. */
-int hdg_newton_step(hdg_ctx_t ctx, double* V, double* Vhat, const double* hist, double mass_coef, int precision,
-                    double tol, int max_newton, int* newton_iters, double* res_norm, double* res_history,
-                    int* trace_iters, void* stream);
+/* Newton's method on the discrete equations of Sec. 3.2 / 3.3 with a given time term
+ * mass_coef (u(v), w) - hist (hist as for hdg_assemble_condense, NULL for none): repeats
+ * assemble_condense, trace_solve (hdg_ctx_set_trace_solver's settings), recover and the
+ * update V += dV, Vhat += dVhat until |R| <= tol max(1, |R_0|) or max_newton updates were
+ * made. V and Vhat are updated in place; *newton_iters and *res_norm (final) are written on
+ * the host; res_history (host, nullable, max_newton + 1 entries) receives the residual norm
+ * before each update, trace_iters (host, nullable) the total trace-solver iterations.
+ * Context-owned workspaces are allocated on the first call. Synchronises once per Newton
+ * iteration (residual norm and status bits). Errors: HDG_ERR_NOT_CONVERGED (max_newton
+ * updates made, or the trace solve missed its tolerance), HDG_ERR_NONPHYSICAL,
+ * HDG_ERR_SINGULAR, HDG_ERR_REFINE (mixed form with the FP64 recomputation off). */
+int hdg_newton_solve(hdg_ctx_t ctx, double* V, double* Vhat, const double* hist, double mass_coef, int precision,
+                     double tol, int max_newton, int* newton_iters, double* res_norm, double* res_history,
+                     int* trace_iters, void* stream);
+
+/* Learned warm start of hdg_newton_step (no counterpart in the paper; it only supplies the
+ * initial guess, and the Newton solve still decides the converged answer). params = NULL
+ * gives the element-local start alone (dvhat = 0 below). All pointers are device memory.
+ *   params, nin, nh, nout       network of hdg_mlp_* (nin = 4 Nf m, nout = Nf m)
+ *   feat_mean, feat_std [nin]   feature standardisation (hdg_mlp_features)
+ *   tmean, tscale [nout]        target de-standardisation (hdg_mlp_apply_trace)
+ *   vhat_n, dvhat1, dvhat2      [F][Nf][m]: trace of time level n, vhat^n - vhat^{n-1},
+ *                               vhat^{n-1} - vhat^{n-2} */
+typedef struct {
+  const float* params;
+  int nin, nh, nout;
+  const float *feat_mean, *feat_std, *tmean, *tscale;
+  const double *vhat_n, *dvhat1, *dvhat2;
+} hdg_warmstart;
+
+/* One implicit time step by Newton's method (Sec. 3.2 / 3.3 in time; the paper integrates
+ * with DIRK(3,3), this call with BDF):
+ *   bdf_order 0  steady equations (no time term; V_n, V_nm1, dt unused)
+ *             1  BDF1: mass_coef = 1/dt, hist = (u(V_n), w)/dt
+ *             2  BDF2: mass_coef = 3/(2dt), hist = 2 (u(V_n), w)/dt - (u(V_nm1), w)/(2dt)
+ *   V_n, V_nm1  [E][Np][m] entropy variables of time levels n and n-1 (device)
+ *   V, Vhat     on entry the initial guess (e.g. extrapolated with hdg_axpby), on exit the
+ *               converged state of level n+1
+ *   warmstart   NULL: Newton from (V, Vhat). Otherwise the guess is linearised once, the
+ *               network's trace vhat_m = vhat_n + dvhat1 + MLP(features of (V_n, vhat_n,
+ *               dvhat1, dvhat2)) (or the guess's own trace when params is NULL) replaces the
+ *               first global trace solve, and the interior follows from the element-local
+ *               recovery dV = -y - X P (vhat_m - Vhat); Newton continues from there. If that
+ *               solve fails, the plain solve from the caller's guess runs instead.
+ * Other arguments, outputs and errors as for hdg_newton_solve. */
+int hdg_newton_step(hdg_ctx_t ctx, double* V, double* Vhat, const double* V_n, const double* V_nm1, double dt,
+                    int bdf_order, int precision, double tol, int max_newton, const hdg_warmstart* warmstart,
+                    int* newton_iters, double* res_norm, double* res_history, int* trace_iters, void* stream);
 
 /* Learned warm start of the implicit step (no counterpart in the paper: it only supplies
  * the initial guess of the Newton solve above, which still decides the converged answer).

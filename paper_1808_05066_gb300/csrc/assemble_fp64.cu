@@ -32,11 +32,10 @@ int run_fp64(hdg_ctx* ctx, const double* V, const double* Vhat, const double* hi
     HDG_CK(cudaMalloc(&ctx->d_scr, need));
     ctx->scr_bytes = need;
   }
-  static bool attr_done = false;
-  if (!attr_done) {
+  if (!ctx->attr_fp64) {  // per context, hence per device
     HDG_CK(cudaFuncSetAttribute(k_assemble<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)AsmSmem<C>::bytes));
     HDG_CK(cudaFuncSetAttribute(k_condense<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CondSmem<C>::bytes));
-    attr_done = true;
+    ctx->attr_fp64 = true;
   }
   AssembleArgs a{};
   a.V = V;
@@ -82,7 +81,6 @@ int run_fp64(hdg_ctx* ctx, const double* V, const double* Vhat, const double* hi
   return HDG_OK;
 }
 
-// status may be null: use a throwaway buffer in the scratch tail
 }  // namespace
 
 #define HDG_FP64_CASE(D, P, VISC)                                                                       \

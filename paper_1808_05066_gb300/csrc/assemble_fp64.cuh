@@ -47,9 +47,19 @@ struct AssembleArgs {
   double* recov;        // [E][NV*NT + NV]  X then y (B' on entry to condense)
   double* R;            // [E][NV + NT] raw residuals R_v, R_t (always written)
   int* status;          // [E]
+  // With only_flag != 0 a CTA whose element has none of these status bits returns at once:
+  // the FP64 kernels then recompute just the blocks the mixed form flagged, and k_condense
+  // replaces the flag by HDG_STATUS_FP64 (the block is now the FP64 form's).
+  int only_flag;
+  float refine_tol;     // mixed condensation: tolerance of the refinement status bit
 };
 
-enum { HDG_STATUS_NONPHYSICAL = 1, HDG_STATUS_SINGULAR = 2 };
+enum { HDG_STATUS_NONPHYSICAL = 1, HDG_STATUS_SINGULAR = 2, HDG_STATUS_REFINE = 4, HDG_STATUS_FP64 = 8 };
+
+// true if the CTA of element e has nothing to do in a flagged-only pass
+HDG_DEVI bool skip_element(const AssembleArgs& a, int64_t e) {
+  return a.only_flag != 0 && (__ldg(a.status + e) & a.only_flag) == 0;
+}
 
 template <class C>
 HDG_DEVI void load_element(const AssembleArgs& a, int64_t e, double (*z)[C::M], double* G) {
@@ -78,6 +88,7 @@ __global__ void __launch_bounds__(128) k_pointwise(AssembleArgs a, DevTables T, 
   __shared__ double dz[NF * NFN][M];  // vhat - v at the face nodes (the lifting's jumps)
   const int64_t le = blockIdx.x;
   const int64_t e = a.e0 + le;
+  if (skip_element(a, e)) return;
   load_element<C>(a, e, z, G);
   __syncthreads();
   if (C::VISC)
@@ -299,6 +310,7 @@ __global__ void __launch_bounds__(256) k_assemble(AssembleArgs a, DevTables T) {
   double* Rt = Rv + NV;
   const int64_t le = blockIdx.x;
   const int64_t e = a.e0 + le;
+  if (skip_element(a, e)) return;
   const int tid = threadIdx.x, nth = blockDim.x;
   load_element<C>(a, e, z, G);
   __syncthreads();
@@ -508,6 +520,7 @@ __global__ void __launch_bounds__(256) k_condense(AssembleArgs a) {
   __shared__ int s_bad;
   const int64_t le = blockIdx.x;
   const int64_t e = a.e0 + le;
+  if (skip_element(a, e)) return;
   const int tid = threadIdx.x, nth = blockDim.x;
   const double* Ap = a.Ap + le * NV * NV;
   const double* Cp = a.Cp + le * NT * NV;
@@ -630,6 +643,10 @@ __global__ void __launch_bounds__(256) k_condense(AssembleArgs a) {
     const double* Cr = Cp + r * NV;
     for (int k = 0; k < NV; ++k) s -= Cr[k] * y[k];
     g[r] = s;
+  }
+  if (a.only_flag != 0 && tid == 0) {  // flagged-only pass: the block is now the FP64 form's
+    atomicAnd(a.status + e, ~a.only_flag);
+    atomicOr(a.status + e, HDG_STATUS_FP64);
   }
 }
 

@@ -138,8 +138,7 @@ int run_mixed(hdg_ctx* ctx, const double* V, const double* Vhat, const double* h
   constexpr int NVAR = 4;
   const CondVariant cvariants[] = {make_cond_variant<C, 256>(), make_cond_variant<C, 512>(), make_cond_variant2<C>()};
   constexpr int NCVAR = 3;
-  static bool attr_done = false;
-  if (!attr_done) {
+  if (!ctx->attr_mixed) {  // per context, hence per device
     for (const AsmVariant& v : variants)
       if (int rc2 = v.set_attr()) return rc2;
     for (const CondVariant& v : cvariants) {
@@ -148,7 +147,10 @@ int run_mixed(hdg_ctx* ctx, const double* V, const double* Vhat, const double* h
     }
     HDG_CK(cudaFuncSetAttribute(k_condense_prep<C, kSlices>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)TC::prep_bytes));
-    attr_done = true;
+    // the FP64 kernels of the flagged-only recomputation
+    HDG_CK(cudaFuncSetAttribute(k_assemble<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)AsmSmem<C>::bytes));
+    HDG_CK(cudaFuncSetAttribute(k_condense<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CondSmem<C>::bytes));
+    ctx->attr_mixed = true;
   }
   const df2* td = reinterpret_cast<const df2*>(ctx->d_tab_df);
   DevTablesDF TD;
@@ -170,6 +172,7 @@ int run_mixed(hdg_ctx* ctx, const double* V, const double* Vhat, const double* h
   a.recov = recov;
   a.R = R;
   a.status = status;
+  a.refine_tol = (float)ctx->refine_tol;
   const int64_t ch = ctx->chunk;
   a.ptv = ctx->d_scr;
   a.ptf = a.ptv + ch * C::NG * C::PT_VOL;
@@ -280,6 +283,24 @@ int run_mixed(hdg_ctx* ctx, const double* V, const double* Vhat, const double* h
     {
       LaunchScope ls(ctx, HDG_KERNEL_MIXED_CONDENSE, s);
       cv.kernel<<<cv.grid(a.ne), cv.threads, cv.smem, s>>>(a);
+    }
+    if (ctx->refine_fallback) {
+      // blocks whose refinement missed its tolerance are recomputed by the FP64 kernels (the
+      // chunk's scratch is free again); every other CTA returns at once
+      AssembleArgs f = a;
+      f.only_flag = HDG_STATUS_REFINE;
+      {
+        LaunchScope ls(ctx, HDG_KERNEL_POINTWISE, s);
+        k_pointwise<C><<<(unsigned)a.ne, pw_threads, 0, s>>>(f, ctx->T, ctx->ph);
+      }
+      {
+        LaunchScope ls(ctx, HDG_KERNEL_ASSEMBLE, s);
+        k_assemble<C><<<(unsigned)a.ne, 256, AsmSmem<C>::bytes, s>>>(f, ctx->T);
+      }
+      {
+        LaunchScope ls(ctx, HDG_KERNEL_CONDENSE, s);
+        k_condense<C><<<(unsigned)a.ne, 256, CondSmem<C>::bytes, s>>>(f);
+      }
     }
     if (int rc_d = chunk_done(ctx, e0, a.ne, s)) return rc_d;
   }

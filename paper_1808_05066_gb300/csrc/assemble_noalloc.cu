@@ -2,12 +2,11 @@
 // fixed, statically allocated device array instead of memory the library allocates.
 //
 // Who needs it: callers that may not allocate device memory at call time, for example
-// code that runs while a CUDA stream is being captured into a graph (cudaMalloc is not
-// a capturable operation), runtimes that hand the library a fixed arena and forbid
-// further cudaMalloc/cudaFree, or latency-critical loops where an allocation (and the
-// implicit synchronisation of cudaFree) is not acceptable. The ordinary entry point sizes
-// its scratch lazily with cudaMalloc; this one never calls cudaMalloc, cudaFree or any
-// allocating library routine.
+// runtimes that hand the library a fixed memory arena and forbid any further
+// cudaMalloc/cudaFree (the arena owner accounts for every byte), or latency-critical loops
+// where an allocation and the implicit device synchronisation of cudaFree are not
+// acceptable. The ordinary entry point sizes its scratch lazily with cudaMalloc; this one
+// never calls cudaMalloc, cudaFree or any allocating library routine.
 //
 // The scratch is one array of kNoAllocScratchBytes (64 MiB) in this translation unit's
 // device memory, present on every GPU that loads the library until the process exits.
@@ -15,7 +14,8 @@
 // configuration must fit at least once, otherwise the call is rejected with
 // HDG_ERR_INVALID_ARG. Host code cannot use the array's name as a device address, so the
 // first call on each device (with that device current) looks the address up with
-// cudaGetSymbolAddress and caches it; make that first call before any stream capture.
+// cudaGetSymbolAddress and caches it for the life of the process; a device reset
+// (cudaDeviceReset) discards the module holding the array, so calls after one are invalid.
 // All calls share the array: two calls whose kernels overlap on the GPU (different
 // streams without ordering) race on it. Every byte a kernel reads from the array is
 // written earlier in the same chunk, so nothing needs clearing between calls.
@@ -63,8 +63,11 @@ int run_noalloc(hdg_ctx* ctx, double* scratch, const double* V, const double* Vh
     set_error("hdg_assemble_condense_noalloc: one element needs more scratch than the 64 MiB static array");
     return HDG_ERR_INVALID_ARG;
   }
-  HDG_CK(cudaFuncSetAttribute(k_assemble<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)AsmSmem<C>::bytes));
-  HDG_CK(cudaFuncSetAttribute(k_condense<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CondSmem<C>::bytes));
+  if (!ctx->attr_noalloc) {  // this file's instances of the kernels, once per context (one device)
+    HDG_CK(cudaFuncSetAttribute(k_assemble<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)AsmSmem<C>::bytes));
+    HDG_CK(cudaFuncSetAttribute(k_condense<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CondSmem<C>::bytes));
+    ctx->attr_noalloc = true;
+  }
   AssembleArgs a{};
   a.V = V;
   a.Vhat = Vhat;

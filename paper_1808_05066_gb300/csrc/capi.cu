@@ -98,13 +98,32 @@ extern "C" {
 
 const char* hdg_last_error(void) { return hdg::g_last_error.c_str(); }
 
-int hdg_mesh_create(int dim, const int64_t n[3], const double lo[3], const double hi[3], int p, int quad_points,
-                    hdg_mesh_t* out) {
+int hdg_mesh_create(int dim, const int64_t n[3], const double lo[3], const double hi[3], const int8_t* p_per_elem,
+                    int p, int scheme, int quad_points, hdg_mesh_t* out) {
   if (!out || !n || !lo || !hi) {
     set_error("hdg_mesh_create: null argument");
     return HDG_ERR_INVALID_ARG;
   }
   *out = nullptr;
+  if (scheme != HDG_SCHEME_HDG) {
+    set_error(scheme == HDG_SCHEME_EDG || scheme == HDG_SCHEME_IEDG
+                  ? "hdg_mesh_create: the EDG / IEDG trace spaces are not built"
+                  : "hdg_mesh_create: unknown scheme");
+    return scheme == HDG_SCHEME_EDG || scheme == HDG_SCHEME_IEDG ? HDG_ERR_UNSUPPORTED : HDG_ERR_INVALID_ARG;
+  }
+  if (p_per_elem) {  // one degree per element: accepted when every element has degree p
+    if (dim < 2 || dim > 3) {
+      set_error("hdg_mesh_create: invalid mesh arguments");
+      return HDG_ERR_INVALID_ARG;
+    }
+    int64_t E = dim == 2 ? 2 : 6;
+    for (int d = 0; d < dim; ++d) E *= n[d] > 0 ? n[d] : 0;
+    for (int64_t e = 0; e < E; ++e)
+      if (p_per_elem[e] != p) {
+        set_error("hdg_mesh_create: elements of different degree in one mesh are not built");
+        return p_per_elem[e] >= 1 && p_per_elem[e] <= 4 ? HDG_ERR_UNSUPPORTED : HDG_ERR_INVALID_ARG;
+      }
+  }
   if (quad_points == 0) quad_points = p + 1;
   auto* m = new hdg_mesh();
   int rc = hdg::build_mesh(dim, n, lo, hi, p, quad_points, m->m);
@@ -286,7 +305,8 @@ void hdg_ctx_destroy(hdg_ctx_t c) {
   DeviceGuard guard(c->device);
   void* bufs[] = {c->d_tab, c->d_tab_df, c->d_itab, c->d_tgidx, c->d_geo, c->d_fs_elem, c->d_fs_loc, c->d_scr,
                   c->d_sw, c->d_pc, c->d_pcpiv, c->d_dense, c->d_dpiv, c->d_red, c->d_S,
-                  c->d_g, c->d_recov, c->d_R, c->d_dV, c->d_dVh, c->d_status};
+                  c->d_g, c->d_recov, c->d_R, c->d_dV, c->d_dVh, c->d_status, c->d_hist, c->d_V0,
+                  c->d_Vh0, c->d_feat, c->d_pred};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (c->h_red) cudaFreeHost(c->h_red);
@@ -366,6 +386,7 @@ int hdg_assemble_condense_graph(hdg_ctx_t ctx, const double* V, const double* Vh
   k.chunk = ctx->chunk;
   if (ctx->ac_graph && ctx->ac_key == k) {  // replay
     HDG_CK(cudaGraphLaunch(ctx->ac_graph, s));
+    ++ctx->ac_replays;
     for (int c = 0; c < HDG_KERNEL_CLASSES; ++c) ctx->launches[c] += ctx->ac_launches[c];
     return HDG_OK;
   }
@@ -479,6 +500,33 @@ int hdg_axpby(int64_t n, double a, const double* x, double b, const double* y, d
   return hdg::launch_axpby(n, a, x, b, y, out, (cudaStream_t)stream);
 }
 
+int hdg_ctx_set_refinement(hdg_ctx_t ctx, double tol, int fp64_fallback) {
+  HDG_REQUIRE(ctx && tol >= 0.0 && tol < 1.0, "hdg_ctx_set_refinement: invalid argument");
+  ctx->refine_tol = tol;
+  ctx->refine_fallback = fp64_fallback != 0;
+  if (ctx->ac_graph) {  // the captured launch sequence depends on both settings
+    cudaGraphExecDestroy(ctx->ac_graph);
+    ctx->ac_graph = nullptr;
+    ctx->ac_key = hdg_ctx::GraphKey{};
+  }
+  return HDG_OK;
+}
+
+int hdg_ctx_set_trace_solver(hdg_ctx_t ctx, int method, double rtol, int max_it) {
+  HDG_REQUIRE(ctx && method >= HDG_SOLVER_AUTO && method <= HDG_SOLVER_DENSE && rtol > 0.0 && max_it > 0,
+              "hdg_ctx_set_trace_solver: invalid argument");
+  ctx->newton_solver = method;
+  ctx->newton_rtol = rtol;
+  ctx->newton_max_it = max_it;
+  return HDG_OK;
+}
+
+int hdg_ctx_graph_replays(hdg_ctx_t ctx, int64_t* replays) {
+  HDG_REQUIRE(ctx && replays, "hdg_ctx_graph_replays: null argument");
+  *replays = ctx->ac_replays;
+  return HDG_OK;
+}
+
 int hdg_profile_enable(hdg_ctx_t ctx, int on) {
   HDG_REQUIRE(ctx, "hdg_profile_enable: null context");
   ctx->prof = on != 0;
@@ -527,11 +575,12 @@ int hdg_profile_read(hdg_ctx_t ctx, int kernel_class, int64_t* launches, double*
   return HDG_OK;
 }
 
-int hdg_newton_step(hdg_ctx_t ctx, double* V, double* Vhat, const double* hist, double mass_coef, int precision,
-                    double tol, int max_newton, int* newton_iters, double* res_norm, double* res_history,
-                    int* trace_iters, void* stream) {
+int hdg_newton_solve(hdg_ctx_t ctx, double* V, double* Vhat, const double* hist, double mass_coef, int precision,
+                     double tol, int max_newton, int* newton_iters, double* res_norm, double* res_history,
+                     int* trace_iters, void* stream) {
   HDG_REQUIRE(ctx && V && Vhat && newton_iters && res_norm && tol > 0.0 && max_newton >= 0,
-              "hdg_newton_step: invalid argument");
+              "hdg_newton_solve: invalid argument");
+  HDG_REQUIRE(precision == HDG_PREC_FP64 || precision == HDG_PREC_MIXED, "hdg_newton_solve: precision");
   DeviceGuard guard(ctx->device);
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t E = ctx->E;
@@ -563,22 +612,27 @@ int hdg_newton_step(hdg_ctx_t ctx, double* V, double* Vhat, const double* hist, 
     *res_norm = rn;
     if (res_history) res_history[it] = rn;
     if (bits & HDG_ELEM_NONPHYSICAL) {
-      set_error("hdg_newton_step: non-physical state");
+      set_error("hdg_newton_solve: non-physical state");
       return HDG_ERR_NONPHYSICAL;
     }
     if (bits & HDG_ELEM_SINGULAR) {
-      set_error("hdg_newton_step: singular element matrix");
+      set_error("hdg_newton_solve: singular element matrix");
       return HDG_ERR_SINGULAR;
+    }
+    if (bits & HDG_ELEM_REFINE) {  // only with the FP64 recomputation switched off
+      set_error("hdg_newton_solve: iterative refinement of an element block missed its tolerance");
+      return HDG_ERR_REFINE;
     }
     if (r0 < 0.0) r0 = rn;
     if (rn <= tol * std::max(1.0, r0)) return HDG_OK;
     if (it >= max_newton) {
-      set_error("hdg_newton_step: Newton did not converge");
+      set_error("hdg_newton_solve: Newton did not converge");
       return HDG_ERR_NOT_CONVERGED;
     }
     int iters = 0;
     double fres = 0.0;
-    rc = hdg::trace_solve(ctx, ctx->d_S, ctx->d_g, ctx->d_dVh, HDG_SOLVER_AUTO, 1e-12, 600, &iters, &fres, s);
+    rc = hdg::trace_solve(ctx, ctx->d_S, ctx->d_g, ctx->d_dVh, ctx->newton_solver, ctx->newton_rtol,
+                          ctx->newton_max_it, &iters, &fres, s);
     if (trace_iters) *trace_iters += iters;
     if (rc) return rc;
     rc = hdg::launch_recover(ctx, ctx->d_recov, ctx->d_dVh, ctx->d_dV, s);
@@ -589,6 +643,93 @@ int hdg_newton_step(hdg_ctx_t ctx, double* V, double* Vhat, const double* hist, 
     if (rc) return rc;
     *newton_iters = it + 1;
   }
+}
+
+int hdg_newton_step(hdg_ctx_t ctx, double* V, double* Vhat, const double* V_n, const double* V_nm1, double dt,
+                    int bdf_order, int precision, double tol, int max_newton, const hdg_warmstart* warmstart,
+                    int* newton_iters, double* res_norm, double* res_history, int* trace_iters, void* stream) {
+  HDG_REQUIRE(ctx && V && Vhat && newton_iters && res_norm && tol > 0.0 && max_newton >= 0,
+              "hdg_newton_step: invalid argument");
+  HDG_REQUIRE(bdf_order >= 0 && bdf_order <= 2, "hdg_newton_step: bdf_order must be 0, 1 or 2");
+  HDG_REQUIRE(bdf_order == 0 || (dt > 0.0 && V_n), "hdg_newton_step: BDF needs dt > 0 and V_n");
+  HDG_REQUIRE(bdf_order < 2 || V_nm1, "hdg_newton_step: BDF2 needs V_nm1");
+  HDG_REQUIRE(!warmstart || (warmstart->vhat_n && warmstart->dvhat1 && warmstart->dvhat2),
+              "hdg_newton_step: warm start needs vhat_n, dvhat1 and dvhat2");
+  HDG_REQUIRE(precision == HDG_PREC_FP64 || precision == HDG_PREC_MIXED, "hdg_newton_step: precision");
+  DeviceGuard guard(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t nV = ctx->E * ctx->NV;
+  // BDF coefficients: mass_coef (u(v), w) - hist, hist = c0 (u(v^n), w) + c1 (u(v^{n-1}), w)
+  double mass = 0.0;
+  const double* hist = nullptr;
+  if (bdf_order > 0) {
+    if (!ctx->d_hist) HDG_CK(cudaMalloc(&ctx->d_hist, sizeof(double) * nV));
+    const double c0 = bdf_order == 1 ? 1.0 / dt : 2.0 / dt, c1 = bdf_order == 1 ? 0.0 : -0.5 / dt;
+    mass = bdf_order == 1 ? 1.0 / dt : 1.5 / dt;
+    int rc = hdg::launch_history(ctx, V_n, bdf_order == 2 ? V_nm1 : nullptr, c0, c1, ctx->d_hist, s);
+    if (rc) return rc;
+    hist = ctx->d_hist;
+  }
+  if (!warmstart)
+    return hdg_newton_solve(ctx, V, Vhat, hist, mass, precision, tol, max_newton, newton_iters, res_norm,
+                            res_history, trace_iters, stream);
+  // Learned (or element-local) start: the caller's guess (V0, Vhat0) is linearised once;
+  // the network's trace (or Vhat0 itself) takes the place of the first global trace solve and
+  // the interior follows from the element-local recovery dV = -y - X P (vhat_m - Vhat0).
+  const hdg_warmstart& w = *warmstart;
+  if (!ctx->d_S) {
+    HDG_CK(cudaMalloc(&ctx->d_S, sizeof(double) * ctx->E * ctx->NT * ctx->NT));
+    if (!ctx->d_g) HDG_CK(cudaMalloc(&ctx->d_g, sizeof(double) * ctx->E * ctx->NT));
+    HDG_CK(cudaMalloc(&ctx->d_recov, sizeof(double) * ctx->E * (ctx->NV * ctx->NT + ctx->NV)));
+    HDG_CK(cudaMalloc(&ctx->d_R, sizeof(double) * ctx->E * (ctx->NV + ctx->NT)));
+    HDG_CK(cudaMalloc(&ctx->d_dV, sizeof(double) * nV));
+    HDG_CK(cudaMalloc(&ctx->d_dVh, sizeof(double) * ctx->ntrace));
+  }
+  if (!ctx->d_status) HDG_CK(cudaMalloc(&ctx->d_status, sizeof(int32_t) * ctx->E));
+  if (!ctx->d_V0) {
+    HDG_CK(cudaMalloc(&ctx->d_V0, sizeof(double) * nV));
+    HDG_CK(cudaMalloc(&ctx->d_Vh0, sizeof(double) * ctx->ntrace));
+  }
+  HDG_CK(cudaMemcpyAsync(ctx->d_V0, V, sizeof(double) * nV, cudaMemcpyDeviceToDevice, s));
+  HDG_CK(cudaMemcpyAsync(ctx->d_Vh0, Vhat, sizeof(double) * ctx->ntrace, cudaMemcpyDeviceToDevice, s));
+  int rc = HDG_OK;
+  if (w.params) {
+    HDG_REQUIRE(w.feat_mean && w.feat_std && w.tmean && w.tscale, "hdg_newton_step: incomplete network");
+    HDG_REQUIRE(w.nin == 4 * ctx->NFN * ctx->M && w.nout == ctx->NFN * ctx->M,
+                "hdg_newton_step: network sizes do not match the mesh (nin = 4 Nf m, nout = Nf m)");
+    const int64_t need = ctx->F * (int64_t)std::max(w.nin, w.nout);
+    if (ctx->feat_cap < need) {
+      if (ctx->d_feat) cudaFree(ctx->d_feat);
+      if (ctx->d_pred) cudaFree(ctx->d_pred);
+      ctx->d_feat = ctx->d_pred = nullptr;
+      ctx->feat_cap = 0;
+      HDG_CK(cudaMalloc(&ctx->d_feat, sizeof(float) * need));
+      HDG_CK(cudaMalloc(&ctx->d_pred, sizeof(float) * need));
+      ctx->feat_cap = need;
+    }
+    if ((rc = hdg_mlp_features(ctx, V_n ? V_n : V, w.vhat_n, w.dvhat1, w.dvhat2, w.feat_mean, w.feat_std,
+                               ctx->d_feat, stream)) ||
+        (rc = hdg_mlp_forward(w.params, w.nin, w.nh, w.nout, ctx->d_feat, ctx->F, ctx->d_pred, stream)) ||
+        (rc = hdg_mlp_apply_trace(ctx, w.vhat_n, w.dvhat1, ctx->d_pred, w.tmean, w.tscale, ctx->d_dVh, stream)))
+      return rc;
+    if ((rc = hdg::launch_axpby(ctx->ntrace, 1.0, ctx->d_dVh, -1.0, Vhat, ctx->d_dVh, s))) return rc;
+  } else {
+    HDG_CK(cudaMemsetAsync(ctx->d_dVh, 0, sizeof(double) * ctx->ntrace, s));
+  }
+  HDG_CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int32_t) * ctx->E, s));
+  if ((rc = hdg_assemble_condense(ctx, V, Vhat, hist, mass, precision, ctx->d_S, ctx->d_g, ctx->d_recov, ctx->d_R,
+                                  ctx->d_status, stream)) ||
+      (rc = hdg::launch_recover(ctx, ctx->d_recov, ctx->d_dVh, ctx->d_dV, s)) ||
+      (rc = hdg::launch_axpy(nV, 1.0, ctx->d_dV, V, s)) || (rc = hdg::launch_axpy(ctx->ntrace, 1.0, ctx->d_dVh, Vhat, s)))
+    return rc;
+  rc = hdg_newton_solve(ctx, V, Vhat, hist, mass, precision, tol, max_newton, newton_iters, res_norm, res_history,
+                        trace_iters, stream);
+  if (rc == HDG_OK || rc == HDG_ERR_CUDA || rc == HDG_ERR_INVALID_ARG) return rc;
+  // the plain solve from the caller's guess decides when the warm start fails
+  HDG_CK(cudaMemcpyAsync(V, ctx->d_V0, sizeof(double) * nV, cudaMemcpyDeviceToDevice, s));
+  HDG_CK(cudaMemcpyAsync(Vhat, ctx->d_Vh0, sizeof(double) * ctx->ntrace, cudaMemcpyDeviceToDevice, s));
+  return hdg_newton_solve(ctx, V, Vhat, hist, mass, precision, tol, max_newton, newton_iters, res_norm, res_history,
+                          trace_iters, stream);
 }
 
 }  // extern "C"

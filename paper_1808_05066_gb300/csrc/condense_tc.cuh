@@ -573,7 +573,7 @@ __global__ void __launch_bounds__(NTHREADS) k_condense_tc(AssembleArgs a) {
     // measures the error before it, so the error left is ~ c_last^2 / c_prev.
     if (tid == 0) {
       const float cl = s_corr[1], cp = s_corr[0];
-      if (!((double)cl * (double)cl <= 1e-10 * (double)s_xmax * (double)cp)) s_bad |= 4;
+      if (!((double)cl * (double)cl <= (double)a.refine_tol * (double)s_xmax * (double)cp)) s_bad |= HDG_STATUS_REFINE;
     }
     // store X and y for the recovery
     for (int t = tid; t < NV * CB; t += NTHREADS) {
@@ -828,7 +828,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_condense_tc2(AssembleArgs a) {
     // the error left after the second correction is ~ c_last^2 / c_prev
     if (tid == 0) {
       const float cl = s_corr[1], cp = s_corr[0];
-      if (!((double)cl * (double)cl <= 1e-10 * (double)s_xmax * (double)cp)) s_bad |= 4;
+      if (!((double)cl * (double)cl <= (double)a.refine_tol * (double)s_xmax * (double)cp)) s_bad |= HDG_STATUS_REFINE;
     }
     // store X and y for the recovery
     for (int t = tid; t < NV * CB; t += NTHREADS) {

@@ -78,9 +78,26 @@ struct hdg_ctx {
   GraphKey ac_key;
   int64_t ac_launches[HDG_KERNEL_CLASSES] = {0};
   bool ac_graph_failed = false;
+  int64_t ac_replays = 0;  // graph launches so far (hdg_ctx_graph_replays)
   // Newton workspace
   double *d_S = nullptr, *d_g = nullptr, *d_recov = nullptr, *d_R = nullptr, *d_dV = nullptr, *d_dVh = nullptr;
   int32_t* d_status = nullptr;
+  // time step (hdg_newton_step): BDF history, the entry state (plain start, kept for the
+  // fallback of a failed warm start), MLP features and prediction
+  double *d_hist = nullptr, *d_V0 = nullptr, *d_Vh0 = nullptr;
+  float *d_feat = nullptr, *d_pred = nullptr;
+  int64_t feat_cap = 0;
+  // mixed form: refinement tolerance of the condensation's status bit and the FP64
+  // recomputation of the blocks it flags (hdg_ctx_set_refinement)
+  double refine_tol = 1e-10;
+  bool refine_fallback = true;
+  // trace solver of the Newton iterations (hdg_ctx_set_trace_solver)
+  int newton_solver = HDG_SOLVER_AUTO;
+  double newton_rtol = 1e-12;
+  int newton_max_it = 600;
+  // dynamic shared-memory limits raised on this context's device (cudaFuncSetAttribute
+  // applies per device; a context belongs to one device)
+  bool attr_fp64 = false, attr_mixed = false, attr_noalloc = false;
   // measurement: launch counts per kernel class and (when enabled) event pairs
   bool prof = false;
   int64_t launches[HDG_KERNEL_CLASSES] = {0};

@@ -20,7 +20,6 @@ HDG_ERR_NONPHYSICAL = 2
 HDG_ERR_SINGULAR = 3
 HDG_ERR_REFINE = 4
 HDG_ERR_NOT_CONVERGED = 5
-HDG_ERR_TIMEOUT = 6
 HDG_ERR_CUDA = 7
 HDG_ERR_UNSUPPORTED = 8
 HDG_PREC_FP64 = 0
@@ -28,6 +27,13 @@ HDG_PREC_MIXED = 1
 HDG_SOLVER_AUTO = 0
 HDG_SOLVER_GMRES = 1
 HDG_SOLVER_DENSE = 2
+HDG_SCHEME_HDG = 0
+HDG_SCHEME_EDG = 1
+HDG_SCHEME_IEDG = 2
+HDG_ELEM_NONPHYSICAL = 1
+HDG_ELEM_SINGULAR = 2
+HDG_ELEM_REFINE = 4
+HDG_ELEM_FP64 = 8
 
 EXPORTED = [
     "hdg_mesh_create", "hdg_mesh_destroy", "hdg_mesh_get_info", "hdg_mesh_copy_topology",
@@ -37,7 +43,8 @@ EXPORTED = [
     "hdg_profile_reset", "hdg_profile_read", "hdg_last_error", "hdg_assemble_condense_noalloc",
     "hdg_mlp_param_count", "hdg_mlp_init", "hdg_mlp_features", "hdg_mlp_forward", "hdg_mlp_gradient",
     "hdg_mlp_train_step", "hdg_mlp_apply_trace", "hdg_mlp_stats", "hdg_mlp_standardize", "hdg_mlp_target",
-    "hdg_axpby", "hdg_assemble_condense_host", "hdg_assemble_condense_graph",
+    "hdg_axpby", "hdg_assemble_condense_host", "hdg_assemble_condense_graph", "hdg_newton_solve",
+    "hdg_ctx_set_refinement", "hdg_ctx_graph_replays", "hdg_ctx_set_trace_solver",
 ]
 HDG_KERNEL_POINTWISE = 0
 HDG_KERNEL_ASSEMBLE = 1
@@ -62,6 +69,12 @@ class hdg_physics(ctypes.Structure):
     _fields_ = [("gamma", c_double), ("mach", c_double), ("reynolds", c_double), ("prandtl", c_double)]
 
 
+class hdg_warmstart(ctypes.Structure):
+    _fields_ = [("params", c_void_p), ("nin", c_int), ("nh", c_int), ("nout", c_int),
+                ("feat_mean", c_void_p), ("feat_std", c_void_p), ("tmean", c_void_p), ("tscale", c_void_p),
+                ("vhat_n", c_void_p), ("dvhat1", c_void_p), ("dvhat2", c_void_p)]
+
+
 class hdg_mesh_info(ctypes.Structure):
     _fields_ = [("dim", c_int32), ("p", c_int32), ("quad_points", c_int32), ("m", c_int32),
                 ("Np", c_int32), ("Nf", c_int32), ("nF", c_int32), ("NG", c_int32), ("NGF", c_int32),
@@ -76,8 +89,8 @@ def _load():
     lib = ctypes.CDLL(path)
     P = c_void_p
     sig = {
-        "hdg_mesh_create": (c_int, [c_int, POINTER(c_int64), POINTER(c_double), POINTER(c_double), c_int, c_int,
-                                    POINTER(c_void_p)]),
+        "hdg_mesh_create": (c_int, [c_int, POINTER(c_int64), POINTER(c_double), POINTER(c_double), c_void_p, c_int,
+                                    c_int, c_int, POINTER(c_void_p)]),
         "hdg_mesh_destroy": (None, [P]),
         "hdg_mesh_get_info": (c_int, [P, POINTER(hdg_mesh_info)]),
         "hdg_mesh_copy_topology": (c_int, [P, P, P, P]),
@@ -91,8 +104,13 @@ def _load():
         "hdg_recover_interior": (c_int, [P, P, P, P, P]),
         "hdg_trace_matvec": (c_int, [P, P, P, P, P]),
         "hdg_residual_norm": (c_int, [P, P, POINTER(c_double), P]),
-        "hdg_newton_step": (c_int, [P, P, P, P, c_double, c_int, c_double, c_int, POINTER(c_int),
-                                    POINTER(c_double), POINTER(c_double), POINTER(c_int), P]),
+        "hdg_newton_solve": (c_int, [P, P, P, P, c_double, c_int, c_double, c_int, POINTER(c_int),
+                                     POINTER(c_double), POINTER(c_double), POINTER(c_int), P]),
+        "hdg_newton_step": (c_int, [P, P, P, P, P, c_double, c_int, c_int, c_double, c_int, POINTER(hdg_warmstart),
+                                    POINTER(c_int), POINTER(c_double), POINTER(c_double), POINTER(c_int), P]),
+        "hdg_ctx_set_refinement": (c_int, [P, c_double, c_int]),
+        "hdg_ctx_graph_replays": (c_int, [P, POINTER(c_int64)]),
+        "hdg_ctx_set_trace_solver": (c_int, [P, c_int, c_double, c_int]),
         "hdg_mlp_param_count": (c_int64, [c_int, c_int, c_int]),
         "hdg_mlp_init": (c_int, [P, c_int, c_int, c_int, ctypes.c_uint64, P]),
         "hdg_mlp_features": (c_int, [P, P, P, P, P, P, P, P, P]),
@@ -150,12 +168,14 @@ def _stream(s):
 
 
 # ------------------------------------------------------------------ raw entry points
-def hdg_mesh_create(dim, n, lo, hi, p, quad_points=0):
+def hdg_mesh_create(dim, n, lo, hi, p, quad_points=0, p_per_elem=None, scheme=HDG_SCHEME_HDG):
+    """p_per_elem: None (uniform p) or an int8 array [E] of per-element degrees."""
     n3 = (c_int64 * 3)(*(list(n) + [1] * (3 - len(n))))
     lo3 = (c_double * 3)(*(list(lo) + [0.0] * (3 - len(lo))))
     hi3 = (c_double * 3)(*(list(hi) + [1.0] * (3 - len(hi))))
+    pe = None if p_per_elem is None else np.ascontiguousarray(p_per_elem, dtype=np.int8)
     h = c_void_p()
-    _check(_lib.hdg_mesh_create(dim, n3, lo3, hi3, p, quad_points, byref(h)))
+    _check(_lib.hdg_mesh_create(dim, n3, lo3, hi3, _ptr(pe), p, scheme, quad_points, byref(h)))
     return h.value
 
 
@@ -257,19 +277,62 @@ def hdg_residual_norm(ctx, R, stream=None):
     return out.value
 
 
-def hdg_newton_step(ctx, V, Vhat, hist, mass_coef, precision=HDG_PREC_FP64, tol=1e-10, max_newton=10,
-                    stream=None, history=False):
+def hdg_newton_solve(ctx, V, Vhat, hist, mass_coef, precision=HDG_PREC_FP64, tol=1e-10, max_newton=10,
+                     stream=None, history=False):
     """Returns (updates, final residual norm) or, with history=True,
     (updates, final norm, residual norms before each update, trace-solver iterations)."""
     it = c_int()
     res = c_double()
     hist_buf = (c_double * (max_newton + 1))()
     tr = c_int()
-    _check(_lib.hdg_newton_step(ctx, _ptr(V), _ptr(Vhat), _ptr(hist), mass_coef, precision, tol, max_newton,
-                                byref(it), byref(res), hist_buf, byref(tr), _stream(stream)))
+    _check(_lib.hdg_newton_solve(ctx, _ptr(V), _ptr(Vhat), _ptr(hist), mass_coef, precision, tol, max_newton,
+                                 byref(it), byref(res), hist_buf, byref(tr), _stream(stream)))
     if history:
         return it.value, res.value, list(hist_buf)[:it.value + 1], tr.value
     return it.value, res.value
+
+
+def make_warmstart(vhat_n, dvhat1, dvhat2, net=None):
+    """hdg_warmstart from device tensors; net: object with params, nin, nh, nout, fmean, fstd,
+    tmean, tstd (None: the element-local start alone)."""
+    w = hdg_warmstart()
+    w.vhat_n, w.dvhat1, w.dvhat2 = _ptr(vhat_n), _ptr(dvhat1), _ptr(dvhat2)
+    if net is not None:
+        w.params = _ptr(net.params)
+        w.nin, w.nh, w.nout = net.nin, net.nh, net.nout
+        w.feat_mean, w.feat_std = _ptr(net.fmean), _ptr(net.fstd)
+        w.tmean, w.tscale = _ptr(net.tmean), _ptr(net.tstd)
+    return w
+
+
+def hdg_newton_step(ctx, V, Vhat, V_n, V_nm1, dt, bdf_order, precision=HDG_PREC_FP64, tol=1e-10, max_newton=10,
+                    warmstart=None, stream=None, history=False):
+    """One BDF time step (bdf_order 0, 1, 2) from the initial guess (V, Vhat), updated in place.
+    warmstart: an hdg_warmstart (make_warmstart) or None. Returns as hdg_newton_solve."""
+    it = c_int()
+    res = c_double()
+    hist_buf = (c_double * (max_newton + 1))()
+    tr = c_int()
+    _check(_lib.hdg_newton_step(ctx, _ptr(V), _ptr(Vhat), _ptr(V_n), _ptr(V_nm1), dt, bdf_order, precision, tol,
+                                max_newton, None if warmstart is None else byref(warmstart), byref(it), byref(res),
+                                hist_buf, byref(tr), _stream(stream)))
+    if history:
+        return it.value, res.value, list(hist_buf)[:it.value + 1], tr.value
+    return it.value, res.value
+
+
+def hdg_ctx_set_refinement(ctx, tol=1e-10, fp64_fallback=True):
+    _check(_lib.hdg_ctx_set_refinement(ctx, tol, 1 if fp64_fallback else 0))
+
+
+def hdg_ctx_set_trace_solver(ctx, method=HDG_SOLVER_AUTO, rtol=1e-12, max_it=600):
+    _check(_lib.hdg_ctx_set_trace_solver(ctx, method, rtol, max_it))
+
+
+def hdg_ctx_graph_replays(ctx):
+    n = c_int64()
+    _check(_lib.hdg_ctx_graph_replays(ctx, byref(n)))
+    return n.value
 
 
 def hdg_axpby(n, a, x, b, y, out, stream=None):
@@ -339,11 +402,11 @@ def hdg_profile_read(ctx, kernel_class=-1):
 class Mesh:
     """Owns an hdg_mesh_t; exposes its info and host copies of its tables."""
 
-    def __init__(self, dim, n, lo, hi, p, quad_points=0):
+    def __init__(self, dim, n, lo, hi, p, quad_points=0, p_per_elem=None, scheme=HDG_SCHEME_HDG):
         n = [n] * dim if np.isscalar(n) else list(n)
         lo = [lo] * dim if np.isscalar(lo) else list(lo)
         hi = [hi] * dim if np.isscalar(hi) else list(hi)
-        self.handle = hdg_mesh_create(dim, n, lo, hi, p, quad_points)
+        self.handle = hdg_mesh_create(dim, n, lo, hi, p, quad_points, p_per_elem, scheme)
         self.info = hdg_mesh_get_info(self.handle)
 
     def topology(self):

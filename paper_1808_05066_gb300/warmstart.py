@@ -1,7 +1,7 @@
 """Implicit time stepping with Newton, with and without the learned warm start.
 
-Orchestration only: every arithmetic step (history integrals, extrapolation, features,
-network, training, the Newton solve) is a C-ABI call into libhdg.so.
+Orchestration only: every arithmetic step (extrapolation, features, network, training, the
+time step with its warm start) is a C-ABI call into libhdg.so.
 
 Time integration is BDF2 (BDF1 for the first step). With the extrapolation
 V_e = 2 V^n - V^{n-1}, vhat_e = vhat^n + dvhat^n (dvhat^n = vhat^n - vhat^{n-1}), the
@@ -11,6 +11,8 @@ initial guess of step n+1 is
           trace held: assemble+condense, dV = -y (recovery with dvhat = 0);
   mlp:    vhat_m = vhat_e + MLP(face features) in place of the first global trace solve,
           and V from the local recovery dV = -y - X P (vhat_m - vhat_e).
+The local and mlp starts are hdg_newton_step's warm start (hdg_warmstart), which also falls
+back to the plain solve from (V_e, vhat_e) if the solve from the warm start fails.
 The network learns the correction of the extrapolated trace update from the first steps
 of the plain solve. The interior residual carries the 1/dt time term and dominates the
 Newton residual, so a predicted trace helps only together with the interior it implies;
@@ -60,11 +62,8 @@ class Stepper:
         self.Vp = None
         self.dvh1 = torch.zeros_like(self.Vh)
         self.dvh2 = torch.zeros_like(self.Vh)
-        self.hist = torch.empty_like(self.V)
         self.V0 = torch.empty_like(self.V)
         self.Vh0 = torch.empty_like(self.Vh)
-        self.dVh = torch.empty_like(self.Vh)
-        self.dV = torch.empty_like(self.V)
         self.n = 0
         i = W.info
         self.F, self.per = i["n_faces"], i["Nf"] * i["m"]
@@ -90,56 +89,24 @@ class Stepper:
 
     def step(self, warm="plain", net: Network | None = None) -> StepRecord:
         nV, nT = self.V.numel(), self.Vh.numel()
+        # initial guess: V_e = 2 V^n - V^{n-1} (V^n on the first step), vhat_e = vhat^n + dvhat^n
         if self.Vp is None:
-            mass = 1.0 / self.dt
-            hdg.hdg_history(self.ctx, self.V, None, 1.0 / self.dt, 0.0, self.hist)
+            order = 1
             self.V0.copy_(self.V)
         else:
-            mass = 1.5 / self.dt
-            hdg.hdg_history(self.ctx, self.V, self.Vp, 2.0 / self.dt, -0.5 / self.dt, self.hist)
+            order = 2
             hdg.hdg_axpby(nV, 2.0, self.V, -1.0, self.Vp, self.V0)
-        used = "plain"
-        hdg.hdg_axpby(nT, 1.0, self.Vh, 1.0, self.dvh1, self.Vh0)           # vhat_e
+        hdg.hdg_axpby(nT, 1.0, self.Vh, 1.0, self.dvh1, self.Vh0)
+        ws, used = None, "plain"
+        if warm in ("local", "mlp") and self.n >= 2:
+            use_net = warm == "mlp" and net is not None
+            ws = hdg.make_warmstart(self.Vh, self.dvh1, self.dvh2, net if use_net else None)
+            used = "mlp" if use_net else "local"
+        V_try, Vh_try = self.V0.clone(), self.Vh0.clone()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        if warm in ("local", "mlp") and self.n >= 2:
-            W = self.W
-            if not hasattr(W, "S"):
-                W.alloc_outputs()
-            if warm == "mlp" and net is not None:
-                feat = torch.empty((self.F, net.nin), dtype=torch.float32, device=self.V.device)
-                pred = torch.empty((self.F, net.nout), dtype=torch.float32, device=self.V.device)
-                self.features(net, feat)
-                hdg.hdg_mlp_forward(net.params, net.nin, net.nh, net.nout, feat, self.F, pred)
-                hdg.hdg_mlp_apply_trace(self.ctx, self.Vh, self.dvh1, pred, net.tmean, net.tstd, self.dVh)
-                hdg.hdg_axpby(nT, 1.0, self.dVh, -1.0, self.Vh0, self.dVh)     # vhat_m - vhat_e
-                used = "mlp"
-            else:
-                self.dVh.zero_()
-                used = "local"
-            W.status.zero_()
-            hdg.hdg_assemble_condense(self.ctx, self.V0, self.Vh0, self.hist, mass, self.prec, W.S, W.g, W.recov,
-                                      W.R, W.status)
-            hdg.hdg_recover_interior(self.ctx, W.recov, self.dVh, self.dV)
-            hdg.hdg_axpby(nV, 1.0, self.V0, 1.0, self.dV, self.V0)
-            hdg.hdg_axpby(nT, 1.0, self.Vh0, 1.0, self.dVh, self.Vh0)
-        V_try, Vh_try = self.V0.clone(), self.Vh0.clone()
-        try:
-            it, rn, rh, tr = hdg.hdg_newton_step(self.ctx, V_try, Vh_try, self.hist, mass, self.prec, self.tol,
-                                                 self.max_newton, history=True)
-        except hdg.HdgError:
-            if used == "plain":
-                raise
-            # the plain Newton solve from the extrapolated state is the fallback
-            used = used + "->plain"
-            if self.Vp is None:
-                self.V0.copy_(self.V)
-            else:
-                hdg.hdg_axpby(nV, 2.0, self.V, -1.0, self.Vp, self.V0)
-            hdg.hdg_axpby(nT, 1.0, self.Vh, 1.0, self.dvh1, self.Vh0)
-            V_try, Vh_try = self.V0.clone(), self.Vh0.clone()
-            it, rn, rh, tr = hdg.hdg_newton_step(self.ctx, V_try, Vh_try, self.hist, mass, self.prec, self.tol,
-                                                 self.max_newton, history=True)
+        it, rn, rh, tr = hdg.hdg_newton_step(self.ctx, V_try, Vh_try, self.V, self.Vp, self.dt, order, self.prec,
+                                             self.tol, self.max_newton, warmstart=ws, history=True)
         torch.cuda.synchronize()
         wall = 1e3 * (time.perf_counter() - t0)
         # advance the histories: dvh2 <- dvh1, dvh1 <- vhat^{n+1} - vhat^n
@@ -225,8 +192,7 @@ def experiment(workload="ns2d_p3_vortices", n_train=200, n_apply=200, skip=2, ep
                 "trace_iters_per_step": sum(r.trace_iters for r in rs) / len(rs),
                 "wall_ms_per_step": sum(r.wall_ms for r in rs) / len(rs),
                 "initial_residual_geomean": math.exp(sum(math.log(max(r.res_history[0], 1e-300)) for r in rs)
-                                                     / len(rs)),
-                "fallbacks": sum(1 for r in rs if "->" in r.warm)}
+                                                     / len(rs))}
 
     return {"workload": workload, "elements": W.n_elem, "faces": W.info["n_faces"], "precision": precision,
             "tol": tol, "train_steps": n_train, "skip": skip, "epochs": epochs,

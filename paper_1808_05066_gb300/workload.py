@@ -154,7 +154,8 @@ def algorithmic_bytes_per_element(info: dict, kernel: str) -> int:
     """HBM bytes one element needs moved by a mixed-form kernel (8-byte values):
       mixed_assemble: read the volume point tensors, write A' and B';
       mixed_face:     read the face point tensors, write C' and D', add into A' and B';
-      mixed_condense: read D', B', R, the FP32 inverse and A'; write S, X, y and g."""
+      mixed_condense: the method's outputs only: write S, X, y and g (the blocks the assembly
+                      parks in HBM for it are this implementation's, not the method's)."""
     D, M = info["dim"], info["m"]
     NP, NFN, NF, NG, NGF = info["Np"], info["Nf"], info["nF"], info["NG"], info["NGF"]
     NV, NT = info["nv"], info["nt"]
@@ -165,6 +166,19 @@ def algorithmic_bytes_per_element(info: dict, kernel: str) -> int:
     if kernel == "mixed_face":
         return 8 * (NF * NGF * pt_face + NT * (NV + NT) + 2 * NV * (NV + NT))
     if kernel == "mixed_condense":
-        return 8 * (NT * NT + NV * NT + NV + NT) + 4 * 2 * NV * NV + 8 * (NT * NT + NV * NT + NV + NT)
+        return 8 * (NT * NT + NV * NT + NV + NT)
     raise ValueError(kernel)
+
+
+def method_flops_per_element(info: dict, viscous: bool, kernel: str) -> float:
+    """The method's own flops per element of a mixed-form kernel, the same count as the FP64
+    form's kernels (flops_per_element): the assembly contractions for mixed_assemble +
+    mixed_face (split by the share of their slice products), the LU, solves and Schur product
+    for mixed_condense."""
+    if kernel == "mixed_condense":
+        return flops_per_element(info, viscous, "condense")
+    asm = flops_per_element(info, viscous, "assemble")
+    v = slice_flops_per_element(info, viscous, "mixed_assemble")
+    f = slice_flops_per_element(info, viscous, "mixed_face")
+    return asm * (v if kernel == "mixed_assemble" else f) / (v + f)
 

@@ -245,10 +245,8 @@ def test_newton_step_matches_oracle():
     prob, Q, V, Vh = oracle_setup(case)
     dt = 0.05
     res = time_step(prob, None, V, Vh, [V], 1, dt, tol=1e-10, max_it=10)
-    hist = gc.torch.empty_like(gc.V)
-    gc.hdg.hdg_history(gc.ctx.handle, gc.V.clone(), None, 1.0 / dt, 0.0, hist)
     V_gpu = gc.V.clone(); Vh_gpu = gc.Vhat.clone()
-    it, rn = gc.hdg.hdg_newton_step(gc.ctx.handle, V_gpu, Vh_gpu, hist, 1.0 / dt, 0, 1e-10, 10)
+    it, rn = gc.hdg.hdg_newton_step(gc.ctx.handle, V_gpu, Vh_gpu, gc.V, None, dt, 1, 0, 1e-10, 10)
     assert it == res.iters
     assert rel_fro(V_gpu.cpu().numpy(), res.V) < 1e-11
     assert rel_fro(Vh_gpu.cpu().numpy(), res.Vhat) < 1e-11
@@ -266,9 +264,11 @@ def test_nonphysical_state_sets_status():
     assert (st[np.arange(len(st)) != 5] & 1).sum() == 0
 
 
-def test_bench_workload_full_size_sampled():
-    """The 82,944-element 3D NS p=3 workload in the launch configuration bench.py times
-    (FP64 form): sampled elements, including the first and the last, against the oracle."""
+@pytest.mark.parametrize("precision", [0, 1])
+def test_bench_workload_full_size_sampled(precision):
+    """The 82,944-element 3D NS p=3 workload in the launch configuration bench.py times (FP64
+    form, and the mixed form with its autotuned shapes over 8,192-element chunks): sampled
+    elements, including the first and the last, against the oracle."""
     import torch
     from oracle import physics as ph
     from oracle.hdg import Problem, interpolate_state
@@ -277,7 +277,7 @@ def test_bench_workload_full_size_sampled():
     name = "ns3d_p3_tgv"
     W = DeviceWorkload(name)
     W.status.zero_()
-    W.assemble()
+    W.assemble(precision)
     torch.cuda.synchronize()
     assert int(W.status.abs().sum()) == 0
     spec = wl.WORKLOADS[name]
@@ -287,7 +287,7 @@ def test_bench_workload_full_size_sampled():
     Vh = wl.perturb(Vh, spec["trace_noise"], spec["seed"])
     assert rel_fro(W.V.cpu().numpy(), V) < 1e-14
     dt = spec["dt"]
-    for e in _sample(mesh.E, 4, seed=5):
+    for e in _sample(mesh.E, 4 if precision == 0 else 8, seed=5 + precision):
         vh = prob.gather_trace(Vh, e)
         Q = prob.consistent_q(e, V[e], vh)
         hist = prob.history_weak(e, [V[e], V[e]], [2.0 / dt, -0.5 / dt])
@@ -295,3 +295,54 @@ def test_bench_workload_full_size_sampled():
         L = prob.condense(e, Q, V[e], vh, 1.5 / dt, hist)
         assert rel_fro(W.S[e].cpu().numpy(), L["S"]) < TOL_BLOCK, e
         assert rel_fro(W.g[e].cpu().numpy(), L["g"]) < TOL_BLOCK, e
+        nv, nt = W.info["nv"], W.info["nt"]
+        nq = L["Rl"].size - nv
+        assert rel_fro(W.recov[e, :nv * nt].cpu().numpy().reshape(nv, nt), L["X"][nq:]) < TOL_BLOCK, e
+        assert rel_fro(W.recov[e, nv * nt:].cpu().numpy(), L["y"][nq:]) < TOL_BLOCK, e
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_kink_of_the_wave_speed_matches_oracle(precision):
+    """Unperturbed Taylor-Green state (V_z = 0 everywhere, vhat the exact trace): on every
+    face with normal +-e_z, V.n = 0 exactly and the derivative of |V.n| in lambda_max takes
+    the convention sign(0) = 0 on both sides. S and g element by element against the oracle."""
+    import dataclasses
+    case = dataclasses.replace(CASES["ns3d_p2"], noise=0.0)
+    gc = GpuCase(case)
+    prob, Q, V, Vh = oracle_setup(case)
+    hist_o = oracle_hist(prob, V, case)
+    nz = np.abs(prob.mesh.normal[..., 2]) == 1.0
+    assert nz.any()                                     # the kink is met on z-normal faces
+    gc.assemble(gc.history(), precision=precision)
+    assert int(gc.status.abs().sum()) == 0
+    S, g = gc.S.cpu().numpy(), gc.g.cpu().numpy()
+    for e in _sample(prob.mesh.E, 12, seed=9):
+        L = prob.condense(e, Q[e], V[e], prob.gather_trace(Vh, e), case.mass_coef, hist_o[e])
+        assert rel_fro(S[e], L["S"]) < TOL_BLOCK, (e, rel_fro(S[e], L["S"]))
+        assert rel_fro(g[e], L["g"]) < TOL_BLOCK, (e, rel_fro(g[e], L["g"]))
+
+
+@pytest.mark.parametrize("name,precision", [("ns2d_p3", 0), ("ns2d_p3", 1), ("ns3d_p1", 0), ("ns3d_p1", 1)])
+def test_ns_bdf2_newton_step_gmres_matches_oracle(name, precision):
+    """One BDF2 step of a Navier-Stokes case to |R| <= 1e-10 max(1, |R0|) through
+    hdg_newton_step with GMRES trace solves (both precisions), against the oracle's BDF2
+    step (dense trace solves): the same number of Newton updates and the same state."""
+    from oracle.hdg import time_step
+    case = CASES[name]
+    gc = GpuCase(case)
+    prob, Q, V, Vh = oracle_setup(case)
+    dt = 0.05
+    V_nm1 = V * (1.0 + 1e-3)            # a level n-1 different from level n
+    res = time_step(prob, Q, V, Vh, [V, V_nm1], 2, dt, tol=1e-10, max_it=10)
+    assert res.iters >= 2
+    torch = gc.torch
+    V_nm1_gpu = (gc.V * (1.0 + 1e-3)).contiguous()
+    gc.hdg.hdg_ctx_set_trace_solver(gc.ctx.handle, gc.hdg.HDG_SOLVER_GMRES, 1e-13, 2000)
+    V_gpu, Vh_gpu = gc.V.clone(), gc.Vhat.clone()
+    it, rn, rh, tr = gc.hdg.hdg_newton_step(gc.ctx.handle, V_gpu, Vh_gpu, gc.V, V_nm1_gpu, dt, 2, precision,
+                                            1e-10, 10, history=True)
+    assert tr > it                       # the trace systems were solved iteratively
+    assert it == res.iters, (it, res.iters)
+    assert abs(rh[0] - res.res_norms[0]) <= 1e-12 * res.res_norms[0]
+    assert rel_fro(V_gpu.cpu().numpy(), res.V) < 1e-10
+    assert rel_fro(Vh_gpu.cpu().numpy(), res.Vhat) < 1e-10

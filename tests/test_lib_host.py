@@ -37,6 +37,28 @@ def test_invalid_arguments_are_rejected():
         hdg.hdg_mesh_create(4, [2, 2, 2], [0, 0, 0], [1, 1, 1], 2)
     with pytest.raises(hdg.HdgError):
         hdg.hdg_mesh_create(2, [2, 2], [0, 0], [1, 1], 0)
+    with pytest.raises(hdg.HdgError) as ei:     # unknown trace space
+        hdg.hdg_mesh_create(2, [2, 2], [0, 0], [1, 1], 2, scheme=7)
+    assert ei.value.code == hdg.HDG_ERR_INVALID_ARG
+    with pytest.raises(hdg.HdgError) as ei:     # a degree outside 1..4 in p_per_elem
+        hdg.hdg_mesh_create(2, [2, 2], [0, 0], [1, 1], 2, p_per_elem=np.array([2] * 7 + [9], np.int8))
+    assert ei.value.code == hdg.HDG_ERR_INVALID_ARG
+
+
+def test_unbuilt_variants_are_reported():
+    """The boundary's arguments for the EDG / IEDG trace spaces (Sec. 3.4) and for meshes of
+    mixed degree exist; those variants are not built and say so with HDG_ERR_UNSUPPORTED."""
+    hdg = _lib()
+    for scheme in (hdg.HDG_SCHEME_EDG, hdg.HDG_SCHEME_IEDG):
+        with pytest.raises(hdg.HdgError) as ei:
+            hdg.hdg_mesh_create(2, [2, 2], [0, 0], [1, 1], 2, scheme=scheme)
+        assert ei.value.code == hdg.HDG_ERR_UNSUPPORTED
+    with pytest.raises(hdg.HdgError) as ei:
+        hdg.hdg_mesh_create(2, [2, 2], [0, 0], [1, 1], 2, p_per_elem=np.array([2] * 7 + [3], np.int8))
+    assert ei.value.code == hdg.HDG_ERR_UNSUPPORTED
+    # a per-element array of one degree is the uniform mesh
+    m = hdg.Mesh(3, 1, 0.0, 1.0, 2, p_per_elem=np.full(6, 2, np.int8))
+    assert m.info["n_elem"] == 6 and m.info["p"] == 2
 
 
 @pytest.mark.parametrize("dim,n,p", [(2, 3, 2), (2, 2, 4), (3, 2, 3), (3, 1, 1), (3, 3, 2)])

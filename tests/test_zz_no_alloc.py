@@ -1,9 +1,12 @@
 """hdg_assemble_condense_noalloc: the FP64 assemble + condense for callers that cannot
-allocate device memory during the call (e.g. while a stream is captured into a CUDA
-graph, or inside a runtime that owns a fixed arena). Its scratch lives in a static device
-array, so this test checks, through the C-ABI, that two calls in a row — on different
-inputs, sharing that array — reproduce the ordinary entry point's outputs. The file name
-makes pytest collect it last."""
+allocate device memory during the call, such as a runtime that owns a fixed memory arena
+and forbids further cudaMalloc/cudaFree. Its scratch lives in a static device array shared
+by every call, so these tests check, through the C-ABI, that two calls in a row (on
+different inputs, sharing that array) reproduce the ordinary entry point's outputs, also on
+a mesh with more elements than one pass over the array holds (the array is reused chunk
+after chunk within a call). The file name makes pytest collect it last."""
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -13,11 +16,15 @@ pytestmark = pytest.mark.gpu
 
 TOL = 1e-10   # the parity tolerance of the condensed blocks
 
+# one ns3d_p3 element needs 60,400 doubles of scratch, so the 64 MiB array holds 138
+# elements per chunk: the 4^3 x 6 = 384-element mesh takes three chunks
+CHUNKED = dataclasses.replace(CASES["ns3d_p3"], name="ns3d_p3_n4", n=4)
 
-@pytest.mark.parametrize("name", ["ns3d_p3", "ns2d_p4"])
-def test_noalloc_matches_allocating_entry_point(name):
+
+@pytest.mark.parametrize("case", [CASES["ns3d_p3"], CASES["ns2d_p4"], CHUNKED], ids=lambda c: c.name)
+def test_noalloc_matches_allocating_entry_point(case):
     torch = pytest.importorskip("torch")
-    gc = GpuCase(CASES[name])
+    gc = GpuCase(case)
     hdg = gc.hdg
     hist = gc.history()
     inputs = [(gc.V.clone(), gc.Vhat.clone()),

@@ -13,7 +13,7 @@ Sources in the paper:
   * isentropic (Shu) vortex, Sec. 5.4 "Case description". The printed density
     factor psi^2 M_inf is read as psi^2 M_inf^2: only the squared Mach number
     gives radial equilibrium dp/dr = rho u_theta^2 / r together with the printed
-    isentropic pressure law (checked in tests/test_workloads.py).
+    isentropic pressure law (checked in tests/test_oracle_convergence.py).
   * Taylor-Green vortex, Sec. 5.5, Eq. (initialCondTGV), with rho0 = V0 = L = 1
     and P0 = 1 / (gamma M0^2) (M0 = V0 / c0).
 """
