@@ -183,8 +183,8 @@ class Problem:
     def condense(self, e, Q, V, Vh, mass_coef=0.0, hist_w=None):
         Rl, Rt = self.local_residual(e, Q, V, Vh, mass_coef, hist_w)
         A, B, C, D = self.local_jacobian(e, Q, V, Vh, mass_coef, hist_w)
-        X = np.linalg.solve(A, B)
-        y = np.linalg.solve(A, Rl)
+        X = solve_equilibrated(A, B)
+        y = solve_equilibrated(A, Rl)
         S = D - C @ X
         g = Rt - C @ y
         return dict(S=S, g=g, X=X, y=y, Rl=Rl, Rt=Rt, A=A, B=B, C=C, D=D)
@@ -217,6 +217,22 @@ class Problem:
             tot_u += T.W @ u
             tot_H += T.W @ ph.entropy_H(u, self.phys.gamma)
         return tot_u, tot_H
+
+
+def solve_equilibrated(A, B):
+    """A^{-1} B by LU with partial pivoting (numpy.linalg.solve) on the system scaled by powers
+    of two, rows by 1/max|row|, then columns by 1/max|column|: X = c (r A c)^{-1} r B. The
+    scaling is exact in floating point and does not change X; it matters because the local
+    system mixes the q and v unknowns, whose rows differ by orders of magnitude (condition
+    number ~6e9 for 3D NS p = 3 at h = 2 pi / 24, against ~6e5 after scaling), and the plain
+    FP64 solve then loses about 3e-11 of X."""
+    p2 = lambda x: np.exp2(np.round(np.log2(x)))
+    r = p2(1.0 / np.abs(A).max(axis=1))
+    As = r[:, None] * A
+    c = p2(1.0 / np.abs(As).max(axis=0))
+    Bs = r[:, None] * B if B.ndim == 2 else r * B
+    Y = np.linalg.solve(As * c[None, :], Bs)
+    return c[:, None] * Y if Y.ndim == 2 else c * Y
 
 
 # ---------------------------------------------------------------------------------------
@@ -334,6 +350,59 @@ def time_step(prob: Problem, Q, V, Vhat, Vhist, order, dt, tol=1e-10, max_it=10)
     hist = np.stack([prob.history_weak(e, [Vj[e] for Vj in Vhist[:len(coefs)]], coefs)
                      for e in range(prob.mesh.E)])
     return newton_solve(prob, Q, V, Vhat, mass_coef, hist, tol, max_it)
+
+
+def dirk3_tableau():
+    """Butcher tableau (A [3x3], b, c) of the three-stage, third-order, L-stable DIRK(3,3)
+    method of Alexander used in Sec. 5. The diagonal g is the root in (1/6, 1/2) of
+    g^3 - 3 g^2 + 3 g / 2 - 1/6 = 0 (the condition for third order with L-stability);
+    c_2 = (1 + g)/2, b_1 = -(6 g^2 - 16 g + 1)/4, b_2 = (6 g^2 - 20 g + 5)/4, b_3 = g, and the
+    last row of A equals b (stiffly accurate)."""
+    lo, hi = 1.0 / 6.0, 0.5
+    f = lambda x: x ** 3 - 3.0 * x * x + 1.5 * x - 1.0 / 6.0
+    for _ in range(200):                       # bisection: f(1/6) > 0 > f(1/2)
+        mid = 0.5 * (lo + hi)
+        if f(mid) > 0.0:
+            lo = mid
+        else:
+            hi = mid
+    g = 0.5 * (lo + hi)
+    c2 = 0.5 * (1.0 + g)
+    b1 = -(6.0 * g * g - 16.0 * g + 1.0) / 4.0
+    b2 = (6.0 * g * g - 20.0 * g + 5.0) / 4.0
+    A = np.array([[g, 0.0, 0.0], [c2 - g, g, 0.0], [b1, b2, g]])
+    return A, A[2].copy(), np.array([g, c2, 1.0])
+
+
+def dirk3_step(prob: Problem, Q, V, Vhat, dt, tol=1e-10, max_it=10):
+    """One DIRK(3,3) step from level n (V, Vhat) (Sec. 5). Stage i solves the discrete
+    equations with the time term
+        (u_i - u_n, w) / (dt a_ii) - sum_{j<i} (a_ij / a_ii) (k_j, w),
+    i.e. mass_coef = 1 / (dt a_ii) and hist_i = (u_n, w) / (dt a_ii) + sum_{j<i} (a_ij/a_ii) (k_j, w),
+    where the weak stage derivatives follow from the stage equations themselves:
+        (k_j, w) = (u_j - u_n, w) / (dt a_jj) - sum_{l<j} (a_jl / a_jj) (k_l, w).
+    Each stage starts Newton from the previous stage's state; the method is stiffly accurate,
+    so u_{n+1} = u_3. Returns (NewtonResult of the last stage, Newton updates per stage)."""
+    A, _, _ = dirk3_tableau()
+    E = prob.mesh.E
+    Un = np.stack([prob.history_weak(e, [V[e]], [1.0]) for e in range(E)])
+    ks = []
+    cur = NewtonResult(Q, V, Vhat)
+    iters = []
+    for i in range(3):
+        aii = A[i, i]
+        hist = Un / (dt * aii)
+        for j in range(i):
+            hist = hist + (A[i, j] / aii) * ks[j]
+        res = newton_solve(prob, cur.Q, cur.V, cur.Vhat, 1.0 / (dt * aii), hist, tol, max_it)
+        iters.append(res.iters)
+        Ui = np.stack([prob.history_weak(e, [res.V[e]], [1.0]) for e in range(E)])
+        k = (Ui - Un) / (dt * aii)
+        for j in range(i):
+            k = k - (A[i, j] / aii) * ks[j]
+        ks.append(k)
+        cur = res
+    return cur, iters
 
 
 def consistent_Q(prob: Problem, V, Vhat):

@@ -223,3 +223,23 @@ def test_consistent_q_is_exact_gradient(dim, p):
         Vh = V[np.array(mesh.ref.face_nodes)]               # exact trace in local order
         Q = prob.consistent_q(e, V, Vh)
         assert np.allclose(Q, np.broadcast_to(Gr, Q.shape), atol=1e-12)
+
+
+def test_equilibrated_solve_recovers_exact_solution():
+    """The oracle's local solve (power-of-two row and column equilibration, then LU): on a
+    well-conditioned integer matrix with rows and columns scaled by 2^-30..2^30 and an integer
+    solution (so that B = A X is exact), X comes back to rounding."""
+    from oracle.hdg import solve_equilibrated
+    rng = np.random.default_rng(17)
+    n = 60
+    A0 = rng.integers(-9, 10, size=(n, n)).astype(float) + 40.0 * np.eye(n)
+    X = rng.integers(-50, 51, size=(n, 7)).astype(float)
+    r = np.exp2(rng.integers(-30, 31, size=n).astype(float))
+    c = np.exp2(rng.integers(-30, 31, size=n).astype(float))
+    A = r[:, None] * A0 * c[None, :]
+    Xs = X / c[:, None]                       # the solution of the scaled system
+    B = A @ Xs                                # = r (A0 X): exact, the entries are small integers x 2^k
+    assert np.array_equal(B, r[:, None] * (A0 @ X))
+    err = lambda Y, Xt=X: np.abs(Y * c[:, None] - Xt).max() / np.abs(Xt).max()
+    assert err(solve_equilibrated(A, B)) < 1e-13
+    assert err(solve_equilibrated(A, B[:, 0])[:, None], X[:, :1]) < 1e-13
