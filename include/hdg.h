@@ -251,6 +251,22 @@ int hdg_newton_solve(hdg_ctx_t ctx, double* V, double* Vhat, const double* hist,
                      double tol, int max_newton, int* newton_iters, double* res_norm, double* res_history,
                      int* trace_iters, void* stream);
 
+/* One time step of the three-stage, third-order, L-stable DIRK(3,3) method of Alexander, the
+ * integrator of the paper's unsteady examples (Sec. 5). Stage i solves the discrete equations
+ * (hdg_newton_solve) with the time term (u_i - u_n, w)/(dt a_ii) - sum_{j<i} (a_ij/a_ii)(k_j, w),
+ * i.e. mass_coef = 1/(dt a_ii), where the weak stage derivatives follow from the stage
+ * equations: (k_j, w) = (u_j - u_n, w)/(dt a_jj) - sum_{l<j} (a_jl/a_jj)(k_l, w). The method is
+ * stiffly accurate, so the level n+1 state is the last stage's.
+ *   V_n         [E][Np][m] level-n entropy variables (device)
+ *   V, Vhat     on entry the first stage's initial guess (usually the level-n state), on exit
+ *               the level n+1 state; each stage starts from the previous one
+ *   stage_iters host [3]: Newton updates of each stage; *res_norm the last stage's final
+ *               residual norm; trace_iters (host, nullable) the total trace-solver iterations
+ * Uses context-owned workspaces (4 x E Np m doubles, allocated on the first call). Errors as
+ * for hdg_newton_solve. */
+int hdg_dirk3_step(hdg_ctx_t ctx, double* V, double* Vhat, const double* V_n, double dt, int precision, double tol,
+                   int max_newton, int* stage_iters, double* res_norm, int* trace_iters, void* stream);
+
 /* Learned warm start of hdg_newton_step (no counterpart in the paper; it only supplies the
  * initial guess, and the Newton solve still decides the converged answer). params = NULL
  * gives the element-local start alone (dvhat = 0 below). All pointers are device memory.

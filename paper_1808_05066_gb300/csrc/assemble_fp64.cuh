@@ -54,7 +54,8 @@ struct AssembleArgs {
   float refine_tol;     // mixed condensation: tolerance of the refinement status bit
 };
 
-enum { HDG_STATUS_NONPHYSICAL = 1, HDG_STATUS_SINGULAR = 2, HDG_STATUS_REFINE = 4, HDG_STATUS_FP64 = 8 };
+enum { HDG_STATUS_NONPHYSICAL = 1, HDG_STATUS_SINGULAR = 2, HDG_STATUS_REFINE = 4, HDG_STATUS_FP64 = 8,
+       HDG_STATUS_TIMEOUT = 16 };
 
 // true if the CTA of element e has nothing to do in a flagged-only pass
 HDG_DEVI bool skip_element(const AssembleArgs& a, int64_t e) {

@@ -3,6 +3,7 @@
 #include <vector>
 
 #include "asm_tc.cuh"
+#include "condense_t5.cuh"
 #include "condense_tc.cuh"
 #include "ctx.hpp"
 
@@ -71,24 +72,34 @@ AsmVariant make_variant() {
                     &set_products_attr<C, MTC, NJW>};
 }
 
-// One compiled shape of the condensation kernel.
+// One compiled shape of the condensation kernel, with the prep kernel that lays out its operands.
 struct CondVariant {
   int threads;
   size_t smem;
   void (*kernel)(AssembleArgs);
   int ctas_per_element;
+  void (*prep)(AssembleArgs);
   unsigned grid(int64_t ne) const { return (unsigned)(ne * ctas_per_element); }
 };
 
 template <class C, int NTH>
 CondVariant make_cond_variant() {
-  return CondVariant{NTH, CondTC<C, NTH, kSlices>::bytes, &k_condense_tc<C, NTH, kSlices>, 1};
+  return CondVariant{NTH, CondTC<C, NTH, kSlices>::bytes, &k_condense_tc<C, NTH, kSlices>, 1,
+                     &k_condense_prep<C, kSlices, false>};
 }
 
 // 16-column blocks, two CTAs per SM
 template <class C>
 CondVariant make_cond_variant2() {
-  return CondVariant{256, CondTC2<C, 256, kSlices>::bytes, &k_condense_tc2<C, 256, kSlices>, 2};
+  return CondVariant{256, CondTC2<C, 256, kSlices>::bytes, &k_condense_tc2<C, 256, kSlices>, 2,
+                     &k_condense_prep<C, kSlices, false>};
+}
+
+// tcgen05 products with TMEM accumulators, 32-column blocks, one CTA per SM
+template <class C>
+CondVariant make_cond_variant_t5() {
+  return CondVariant{CondT5<C, kSlices>::NTH, CondT5<C, kSlices>::bytes, &k_condense_t5<C, kSlices>, 1,
+                     &k_condense_prep<C, kSlices, true>};
 }
 
 // Times `launch` once on the stream (the chunk's outputs are rewritten each time).
@@ -117,8 +128,8 @@ int run_mixed(hdg_ctx* ctx, const double* V, const double* Vhat, const double* h
   using AQ = AsmTC<C, kSlices, 2>;  // the operator slices do not depend on the row tiling
   const size_t per_pt = sizeof(double) * ((size_t)C::NG * C::PT_VOL + (size_t)C::NF * C::NGF * C::PT_FACE +
                                           (size_t)C::NV * C::NV + (size_t)C::NT * C::NV);
-  const size_t per =
-      per_pt + sizeof(uint4) * TC::slice_uint4 + sizeof(float) * TC::prep_floats + sizeof(uint2) * AQ::rb_u2;
+  const size_t slice_bytes = std::max(sizeof(uint4) * TC::slice_uint4, CondT5<C, kSlices>::slice_bytes);
+  const size_t per = per_pt + slice_bytes + sizeof(float) * TC::prep_floats + sizeof(uint2) * AQ::rb_u2;
   if (ctx->chunk == 0) {
     int64_t ch = std::min<int64_t>(ctx->E, 8192);
     while (ch > 256 && per * ch > ((size_t)16 << 30)) ch /= 2;
@@ -136,8 +147,9 @@ int run_mixed(hdg_ctx* ctx, const double* V, const double* Vhat, const double* h
   const AsmVariant variants[] = {make_variant<C, 2, 4>(), make_variant<C, 4, 4>(), make_variant<C, 2, 2>(),
                                  make_variant<C, 4, 2>()};
   constexpr int NVAR = 4;
-  const CondVariant cvariants[] = {make_cond_variant<C, 256>(), make_cond_variant<C, 512>(), make_cond_variant2<C>()};
-  constexpr int NCVAR = 3;
+  const CondVariant cvariants[] = {make_cond_variant<C, 256>(), make_cond_variant<C, 512>(), make_cond_variant2<C>(),
+                                   make_cond_variant_t5<C>()};
+  constexpr int NCVAR = 4;
   if (!ctx->attr_mixed) {  // per context, hence per device
     for (const AsmVariant& v : variants)
       if (int rc2 = v.set_attr()) return rc2;
@@ -145,7 +157,9 @@ int run_mixed(hdg_ctx* ctx, const double* V, const double* Vhat, const double* h
       HDG_CK(cudaFuncSetAttribute(v.kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem));
       HDG_CK(cudaFuncSetAttribute(v.kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
     }
-    HDG_CK(cudaFuncSetAttribute(k_condense_prep<C, kSlices>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    HDG_CK(cudaFuncSetAttribute(k_condense_prep<C, kSlices, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)TC::prep_bytes));
+    HDG_CK(cudaFuncSetAttribute(k_condense_prep<C, kSlices, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)TC::prep_bytes));
     // the FP64 kernels of the flagged-only recomputation
     HDG_CK(cudaFuncSetAttribute(k_assemble<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)AsmSmem<C>::bytes));
@@ -181,7 +195,7 @@ int run_mixed(hdg_ctx* ctx, const double* V, const double* Vhat, const double* h
   {  // 256-byte aligned start of the slice scratch (chunk sizes may be odd)
     const uintptr_t p = reinterpret_cast<uintptr_t>(a.Cp + ch * C::NT * C::NV);
     a.oz = reinterpret_cast<uint4*>((p + 255) & ~(uintptr_t)255);
-    const uintptr_t q = reinterpret_cast<uintptr_t>(a.oz + ch * TC::slice_uint4);
+    const uintptr_t q = reinterpret_cast<uintptr_t>(a.oz) + ch * slice_bytes;
     a.prep = reinterpret_cast<float*>((q + 255) & ~(uintptr_t)255);
     const uintptr_t r = reinterpret_cast<uintptr_t>(a.prep + ch * TC::prep_floats);
     a.rb = reinterpret_cast<uint2*>((r + 255) & ~(uintptr_t)255);
@@ -253,9 +267,9 @@ int run_mixed(hdg_ctx* ctx, const double* V, const double* Vhat, const double* h
           // the condensation overwrites its inputs: assemble again before each trial
           vv.run_vol(a, TD, s);
           vf.run_face(a, ctx->T, TD, s);
-          k_condense_prep<C, kSlices><<<(unsigned)a.ne, TC::PTH, TC::prep_bytes, s>>>(a);
-          float ms = 0.f;
           const CondVariant& cv = cvariants[i];
+          cv.prep<<<(unsigned)a.ne, TC::PTH, TC::prep_bytes, s>>>(a);
+          float ms = 0.f;
           int rc = time_launch(s, [&] { cv.kernel<<<cv.grid(a.ne), cv.threads, cv.smem, s>>>(a); }, &ms);
           if (rc) return rc;
           if (ms < best) {
@@ -278,7 +292,7 @@ int run_mixed(hdg_ctx* ctx, const double* V, const double* Vhat, const double* h
     const CondVariant& cv = cvariants[ctx->cond_variant < 0 ? 0 : ctx->cond_variant];
     {
       LaunchScope ls(ctx, HDG_KERNEL_MIXED_PREP, s);
-      k_condense_prep<C, kSlices><<<(unsigned)a.ne, TC::PTH, TC::prep_bytes, s>>>(a);
+      cv.prep<<<(unsigned)a.ne, TC::PTH, TC::prep_bytes, s>>>(a);
     }
     {
       LaunchScope ls(ctx, HDG_KERNEL_MIXED_CONDENSE, s);

@@ -238,7 +238,7 @@ int hdg_ctx_create(hdg_mesh_t mesh, const hdg_physics* phys, int device, hdg_ctx
   }
   if (const char* cv = std::getenv("HDG_COND_VARIANT")) {  // force a condensation shape (tests)
     long v = std::strtol(cv, nullptr, 10);
-    if (v >= 0 && v < 3) c->cond_variant = (int)v;
+    if (v >= 0 && v < 4) c->cond_variant = (int)v;
   }
   if (const char* ch = std::getenv("HDG_ELEMENT_CHUNK")) {
     long v = std::strtol(ch, nullptr, 10);
@@ -306,7 +306,7 @@ void hdg_ctx_destroy(hdg_ctx_t c) {
   void* bufs[] = {c->d_tab, c->d_tab_df, c->d_itab, c->d_tgidx, c->d_geo, c->d_fs_elem, c->d_fs_loc, c->d_scr,
                   c->d_sw, c->d_pc, c->d_pcpiv, c->d_dense, c->d_dpiv, c->d_red, c->d_S,
                   c->d_g, c->d_recov, c->d_R, c->d_dV, c->d_dVh, c->d_status, c->d_hist, c->d_V0,
-                  c->d_Vh0, c->d_feat, c->d_pred};
+                  c->d_Vh0, c->d_feat, c->d_pred, c->d_dirk};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (c->h_red) cudaFreeHost(c->h_red);
@@ -730,6 +730,69 @@ int hdg_newton_step(hdg_ctx_t ctx, double* V, double* Vhat, const double* V_n, c
   HDG_CK(cudaMemcpyAsync(Vhat, ctx->d_Vh0, sizeof(double) * ctx->ntrace, cudaMemcpyDeviceToDevice, s));
   return hdg_newton_solve(ctx, V, Vhat, hist, mass, precision, tol, max_newton, newton_iters, res_norm, res_history,
                           trace_iters, stream);
+}
+
+namespace {
+
+// Butcher tableau of Alexander's three-stage, third-order, L-stable DIRK(3,3): the diagonal g
+// is the root in (1/6, 1/2) of g^3 - 3g^2 + 3g/2 - 1/6 = 0, c_2 = (1 + g)/2, the last row is
+// b = (-(6g^2 - 16g + 1)/4, (6g^2 - 20g + 5)/4, g).
+struct Dirk3 {
+  double g, a21, a31, a32;
+  Dirk3() {
+    double lo = 1.0 / 6.0, hi = 0.5;  // f(lo) > 0 > f(hi)
+    for (int i = 0; i < 200; ++i) {
+      const double m = 0.5 * (lo + hi);
+      const double f = ((m - 3.0) * m + 1.5) * m - 1.0 / 6.0;
+      (f > 0.0 ? lo : hi) = m;
+    }
+    g = 0.5 * (lo + hi);
+    a21 = 0.5 * (1.0 + g) - g;
+    a31 = -(6.0 * g * g - 16.0 * g + 1.0) / 4.0;
+    a32 = (6.0 * g * g - 20.0 * g + 5.0) / 4.0;
+  }
+};
+
+}  // namespace
+
+extern "C" int hdg_dirk3_step(hdg_ctx_t ctx, double* V, double* Vhat, const double* V_n, double dt, int precision,
+                              double tol, int max_newton, int* stage_iters, double* res_norm, int* trace_iters,
+                              void* stream) {
+  HDG_REQUIRE(ctx && V && Vhat && V_n && stage_iters && res_norm && dt > 0.0 && tol > 0.0 && max_newton >= 0,
+              "hdg_dirk3_step: invalid argument");
+  HDG_REQUIRE(precision == HDG_PREC_FP64 || precision == HDG_PREC_MIXED, "hdg_dirk3_step: precision");
+  DeviceGuard guard(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t n = ctx->E * ctx->NV;
+  if (!ctx->d_hist) HDG_CK(cudaMalloc(&ctx->d_hist, sizeof(double) * n));
+  if (!ctx->d_dirk) HDG_CK(cudaMalloc(&ctx->d_dirk, sizeof(double) * 4 * n));
+  double *Un = ctx->d_dirk, *Ui = Un + n, *K1 = Ui + n, *K2 = K1 + n, *hist = ctx->d_hist;
+  static const Dirk3 T;
+  const double w = 1.0 / (dt * T.g);  // mass coefficient of every stage
+  const double c[3][2] = {{0.0, 0.0}, {T.a21 / T.g, 0.0}, {T.a31 / T.g, T.a32 / T.g}};
+  int rc = hdg::launch_history(ctx, V_n, nullptr, 1.0, 0.0, Un, s);  // (u_n, w)
+  if (rc) return rc;
+  if (trace_iters) *trace_iters = 0;
+  for (int i = 0; i < 3; ++i) {
+    // hist_i = (u_n, w)/(dt a_ii) + sum_{j<i} (a_ij / a_ii) (k_j, w)
+    if ((rc = i == 0 ? hdg::launch_axpby(n, w, Un, 0.0, Un, hist, s)  // K1 is not yet written
+                     : hdg::launch_axpby(n, w, Un, c[i][0], K1, hist, s)))
+      return rc;
+    if (i == 2 && (rc = hdg::launch_axpby(n, 1.0, hist, c[i][1], K2, hist, s))) return rc;
+    int it = 0, tr = 0;
+    rc = hdg_newton_solve(ctx, V, Vhat, hist, w, precision, tol, max_newton, &it, res_norm, nullptr, &tr, stream);
+    stage_iters[i] = it;
+    if (trace_iters) *trace_iters += tr;
+    if (rc) return rc;
+    if (i == 2) break;
+    // (k_i, w) = (u_i - u_n, w)/(dt a_ii) - sum_{j<i} (a_ij / a_ii) (k_j, w)
+    double* K = i == 0 ? K1 : K2;
+    if ((rc = hdg::launch_history(ctx, V, nullptr, 1.0, 0.0, Ui, s)) ||
+        (rc = hdg::launch_axpby(n, w, Ui, -w, Un, K, s)))
+      return rc;
+    if (i == 1 && (rc = hdg::launch_axpby(n, 1.0, K2, -c[1][0], K1, K2, s))) return rc;
+  }
+  return HDG_OK;
 }
 
 }  // extern "C"

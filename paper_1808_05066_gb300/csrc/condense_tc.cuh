@@ -302,7 +302,14 @@ HDG_DEVI void cond_oz_product(const uint2* __restrict__ Rsl, int NTL, const uint
   }
 }
 
+// defined in condense_t5.cuh (the tcgen05 operand layout)
 template <class C, int OZS>
+HDG_DEVI void prep_write_umma_slices(const AssembleArgs& a, int64_t le, const df2* Ap, const df2* Cp, const float* sc,
+                                     const int* eA, const int* eC);
+
+// UMMA = true writes the slices of A' P and C' P for k_condense_t5 (tcgen05 operand layout),
+// otherwise fragment-native for the mma.sync kernels.
+template <class C, int OZS, bool UMMA = false>
 __global__ void __launch_bounds__(CondTC<C, 256, OZS>::PTH) k_condense_prep(AssembleArgs a) {
   using Q = CondTC<C, 256, OZS>;
   constexpr int NV = C::NV, NT = C::NT, KT = Q::KT, MTA = Q::MTA, MTC = Q::MTC, LDA = Q::LDA;
@@ -331,42 +338,9 @@ __global__ void __launch_bounds__(CondTC<C, 256, OZS>::PTH) k_condense_prep(Asse
   if constexpr (LDA > NV)
     for (int t = tid; t < NV * (LDA - NV); t += PTH) G[(t / (LDA - NV)) * LDA + NV + t % (LDA - NV)] = 0.f;
   for (int r = NV + tid; r < MTA * 16; r += PTH) eA[r] = 0;
-  {  // four rows per warp at a time, all their loads in flight together
-    constexpr int RB = 4, KQ = (NV + 31) / 32;
-    for (int r0 = warp * RB; r0 < MTC * 16; r0 += NWARP * RB) {
-      float mx[RB];
-#pragma unroll
-      for (int j = 0; j < RB; ++j) {
-        mx[j] = 0.f;
-        const int r = r0 + j;
-#pragma unroll
-        for (int m = 0; m < KQ; ++m) {
-          const int k = lane + 32 * m;
-          if (r < NT && k < NV) mx[j] = fmaxf(mx[j], fabsf(Cp[r * NV + k].hi));
-        }
-      }
-#pragma unroll
-      for (int j = 0; j < RB; ++j) {
-        for (int off = 16; off > 0; off >>= 1) mx[j] = fmaxf(mx[j], __shfl_xor_sync(0xffffffffu, mx[j], off));
-        if (lane == 0 && r0 + j < MTC * 16) eC[r0 + j] = oz_exponent(mx[j]);
-      }
-    }
-  }
   cp_async_wait_all();
   __syncthreads();
-  for (int r = warp; r < NV; r += NWARP) {
-    float mx = 0.f;
-    for (int k = lane; k < NV; k += 32) mx = fmaxf(mx, fabsf(G[k * LDA + r]));
-    for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-    if (lane == 0) eA[r] = oz_exponent(mx);
-  }
-  __syncthreads();
-  // A'^T out; equilibration sc = |diag A'|^-1/2 and the scaled transpose for the inverse
-  {
-    const float4* src = reinterpret_cast<const float4*>(G);
-    float4* dst = reinterpret_cast<float4*>(pre + Q::PREP_AH);
-    for (int t = tid; t < NV * LDA / 4; t += PTH) dst[t] = src[t];
-  }
+  // equilibration sc = |diag A'|^-1/2; the column scales P (powers of two) of the slices
   for (int r = tid; r < LDA; r += PTH) {
     float v = 1.f;
     if (r < NV) {
@@ -377,17 +351,56 @@ __global__ void __launch_bounds__(CondTC<C, 256, OZS>::PTH) k_condense_prep(Asse
     pre[Q::PREP_SC + r] = v;
   }
   __syncthreads();
+  {  // row exponents of C' P: four rows per warp at a time, all their loads in flight together
+    constexpr int RB = 4, KQ = (NV + 31) / 32;
+    for (int r0 = warp * RB; r0 < MTC * 16; r0 += NWARP * RB) {
+      float mx[RB];
+#pragma unroll
+      for (int j = 0; j < RB; ++j) {
+        mx[j] = 0.f;
+        const int r = r0 + j;
+#pragma unroll
+        for (int m = 0; m < KQ; ++m) {
+          const int k = lane + 32 * m;
+          if (r < NT && k < NV) mx[j] = fmaxf(mx[j], fabsf(Cp[r * NV + k].hi) * oz_pow2_floor(sc[k]));
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < RB; ++j) {
+        for (int off = 16; off > 0; off >>= 1) mx[j] = fmaxf(mx[j], __shfl_xor_sync(0xffffffffu, mx[j], off));
+        if (lane == 0 && r0 + j < MTC * 16) eC[r0 + j] = oz_exponent(mx[j]);
+      }
+    }
+  }
+  for (int r = warp; r < NV; r += NWARP) {  // row exponents of A' P
+    float mx = 0.f;
+    for (int k = lane; k < NV; k += 32) mx = fmaxf(mx, fabsf(G[k * LDA + r]) * oz_pow2_floor(sc[k]));
+    for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    if (lane == 0) eA[r] = oz_exponent(mx);
+  }
+  {  // A'^T out
+    const float4* src = reinterpret_cast<const float4*>(G);
+    float4* dst = reinterpret_cast<float4*>(pre + Q::PREP_AH);
+    for (int t = tid; t < NV * LDA / 4; t += PTH) dst[t] = src[t];
+  }
+  __syncthreads();
   for (int t = tid; t < NV * LDA; t += PTH) {
     const int k = t / LDA, r = t % LDA;
     G[t] = r < NV ? G[t] * sc[r] * sc[k] : 0.f;
   }
   __syncthreads();
   // slices of the rows of A' and C' as the right operand (one warp per 16 x 8 tile)
-  {
+  if constexpr (UMMA) {
+    prep_write_umma_slices<C, OZS>(a, le, Ap, Cp, sc, eA, eC);
+  } else {
     constexpr int NTA = Q::NTA, NTC = Q::NTC;
     uint2* sl = reinterpret_cast<uint2*>(a.oz) + le * Q::slice_u2;
-    auto getA = [&](int k, int n) { return (n < NV && k < NV) ? Ap[n * NV + k] : df2{0.f, 0.f}; };
-    auto getC = [&](int k, int n) { return (n < NT && k < NV) ? Cp[n * NV + k] : df2{0.f, 0.f}; };
+    auto colP = [&](df2 v, int k) {  // A'[n][k] P[k], C'[n][k] P[k]: exact
+      const float pk = oz_pow2_floor(sc[k]);
+      return df2{v.hi * pk, v.lo * pk};
+    };
+    auto getA = [&](int k, int n) { return (n < NV && k < NV) ? colP(Ap[n * NV + k], k) : df2{0.f, 0.f}; };
+    auto getC = [&](int k, int n) { return (n < NT && k < NV) ? colP(Cp[n * NV + k], k) : df2{0.f, 0.f}; };
     auto sA = [&](int n) { return oz_scale(eA[n]); };
     auto sC = [&](int n) { return oz_scale(eC[n]); };
     for (int u = warp; u < (NTA + NTC) * KT; u += NWARP) {
@@ -451,16 +464,21 @@ __global__ void __launch_bounds__(NTHREADS) k_condense_tc(AssembleArgs a) {
   if (tid == 0) s_bad = 0;
   __syncthreads();
 
-  auto col_exponents = [&]() {  // eX[c] from the current X block
+  auto col_exponents = [&]() {  // eX[c] from the current X block, rows scaled by P^-1
     for (int c = warp; c < CB; c += NWARP) {
       float mx = 0.f;
-      for (int r = lane; r < NV; r += 32) mx = fmaxf(mx, fabsf(Xb[r * CB + c].hi));
+      for (int r = lane; r < NV; r += 32) mx = fmaxf(mx, fabsf(Xb[r * CB + c].hi) / oz_pow2_floor(sc[r]));
       for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
       if (lane == 0) eX[c] = oz_exponent(mx);
     }
   };
-  auto slice_X = [&](int nmt) {  // X^T of the block as the left operand
-    auto getX = [&](int c, int k) { return k < NV ? Xb[k * CB + c] : df2{0.f, 0.f}; };
+  auto slice_X = [&](int nmt) {  // (P^-1 X)^T of the block as the left operand
+    auto getX = [&](int c, int k) {
+      if (k >= NV) return df2{0.f, 0.f};
+      const float ip = 1.f / oz_pow2_floor(sc[k]);
+      const df2 x = Xb[k * CB + c];
+      return df2{x.hi * ip, x.lo * ip};
+    };
     auto sX = [&](int c) { return oz_scale(eX[c]); };
     for (int u = warp; u < KT * nmt; u += NWARP) {
       const int kt = u / nmt, m = u % nmt;
@@ -700,7 +718,15 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_condense_tc2(AssembleArgs a) {
     }
   };
   auto sX = [&](int c) { return oz_scale(eX[c]); };
-  auto xhi = [&](int r, int c) { return Xb[r * CB + c].hi; };
+  // the products slice P^-1 X and P^-1 d0 (P: powers of two from sc) against A' P and C' P
+  auto ipow = [&](int r) { return 1.f / oz_pow2_floor(sc[r]); };
+  auto xhi = [&](int r, int c) { return Xb[r * CB + c].hi * ipow(r); };
+  auto getXs = [&](int c, int k) {
+    if (k >= NV) return df2{0.f, 0.f};
+    const float ip = ipow(k);
+    const df2 x = Xb[k * CB + c];
+    return df2{x.hi * ip, x.lo * ip};
+  };
 
   // W = sc B for the block at column cb: all of a thread's loads in flight together
   auto w_init = [&](int cb) {
@@ -746,10 +772,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_condense_tc2(AssembleArgs a) {
     __syncthreads();
     col_exponents(xhi);
     __syncthreads();
-    for (int kt = warp; kt < KT; kt += NWARP) {
-      auto getX = [&](int c, int k) { return k < NV ? Xb[k * CB + c] : df2{0.f, 0.f}; };
-      oz_slice_left_tile<OZS>(Xs + kt * OZS * 32, 32, 0, kt * 16, lane, getX, sX);
-    }
+    for (int kt = warp; kt < KT; kt += NWARP) oz_slice_left_tile<OZS>(Xs + kt * OZS * 32, 32, 0, kt * 16, lane, getXs, sX);
     __syncthreads();
     // r0 = B - A' X0 (exact slices) into W
     cond_oz_product<KT, 1, OZS, NWARP, OZS, PF>(slA, Q::NTA, Xs, 1, [&](int row, int col, const dfacc& v) {
@@ -789,10 +812,10 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_condense_tc2(AssembleArgs a) {
     });
     __syncthreads();
     // r1 = r0 - A' d0 from four slices of each, W = sc r1
-    col_exponents([&](int r, int c) { return W[r * CB + c]; });
+    col_exponents([&](int r, int c) { return W[r * CB + c] * ipow(r); });
     __syncthreads();
     for (int kt = warp; kt < KT; kt += NWARP) {
-      auto getD = [&](int c, int k) { return df2{k < NV ? W[k * CB + c] : 0.f, 0.f}; };
+      auto getD = [&](int c, int k) { return df2{k < NV ? W[k * CB + c] * ipow(k) : 0.f, 0.f}; };
       oz_slice_left_tile<OZR>(Xd + kt * OZR * 32, 32, 0, kt * 16, lane, getD, sX);
     }
     __syncthreads();
@@ -843,10 +866,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_condense_tc2(AssembleArgs a) {
     }
     col_exponents(xhi);
     __syncthreads();
-    for (int kt = warp; kt < KT; kt += NWARP) {
-      auto getX = [&](int c, int k) { return k < NV ? Xb[k * CB + c] : df2{0.f, 0.f}; };
-      oz_slice_left_tile<OZS>(Xs + kt * OZS * 32, 32, 0, kt * 16, lane, getX, sX);
-    }
+    for (int kt = warp; kt < KT; kt += NWARP) oz_slice_left_tile<OZS>(Xs + kt * OZS * 32, 32, 0, kt * 16, lane, getXs, sX);
     cp_async_wait_all();
     __syncthreads();
     // S[:, block] = D' - C' X ; g = R_t - C' y

@@ -85,6 +85,7 @@ struct hdg_ctx {
   // time step (hdg_newton_step): BDF history, the entry state (plain start, kept for the
   // fallback of a failed warm start), MLP features and prediction
   double *d_hist = nullptr, *d_V0 = nullptr, *d_Vh0 = nullptr;
+  double* d_dirk = nullptr;  // DIRK(3,3): (u_n, w), stage (u_i, w), weak stage derivatives k_1, k_2
   float *d_feat = nullptr, *d_pred = nullptr;
   int64_t feat_cap = 0;
   // mixed form: refinement tolerance of the condensation's status bit and the FP64

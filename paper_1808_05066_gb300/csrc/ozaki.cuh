@@ -37,6 +37,15 @@ HDG_DEVI int oz_exponent(float amax) {
 }
 HDG_DEVI float oz_scale(int E) { return ldexpf(1.f, 8 - E); }  // per row / column, not per entry
 
+// The power of two P with P <= s < 2P (s > 0). The condensation's products A' X and C' X are
+// sliced as (A' P)(P^-1 X) with P from the Jacobi scales of A': the scaling is exact, and it
+// evens out the entries of a row of A' (and of a column of X), which each share one slice scale.
+HDG_DEVI float oz_pow2_floor(float s) {
+  int E = 0;
+  frexpf(s, &E);
+  return ldexpf(1.f, E - 1);
+}
+
 // Slices of one double-float value, scaled by a power of two (|v| scale <= 256).
 // Slice 0 is the nearest integer to the high word h; the low word l joins the remainder
 // (|r| <= 1/2) in one exact two-sum (t, e). Slices 1 and 2 peel t exactly (scale by 2^8,

@@ -44,7 +44,7 @@ EXPORTED = [
     "hdg_mlp_param_count", "hdg_mlp_init", "hdg_mlp_features", "hdg_mlp_forward", "hdg_mlp_gradient",
     "hdg_mlp_train_step", "hdg_mlp_apply_trace", "hdg_mlp_stats", "hdg_mlp_standardize", "hdg_mlp_target",
     "hdg_axpby", "hdg_assemble_condense_host", "hdg_assemble_condense_graph", "hdg_newton_solve",
-    "hdg_ctx_set_refinement", "hdg_ctx_graph_replays", "hdg_ctx_set_trace_solver",
+    "hdg_ctx_set_refinement", "hdg_ctx_graph_replays", "hdg_ctx_set_trace_solver", "hdg_dirk3_step",
 ]
 HDG_KERNEL_POINTWISE = 0
 HDG_KERNEL_ASSEMBLE = 1
@@ -111,6 +111,8 @@ def _load():
         "hdg_ctx_set_refinement": (c_int, [P, c_double, c_int]),
         "hdg_ctx_graph_replays": (c_int, [P, POINTER(c_int64)]),
         "hdg_ctx_set_trace_solver": (c_int, [P, c_int, c_double, c_int]),
+        "hdg_dirk3_step": (c_int, [P, P, P, P, c_double, c_int, c_double, c_int, POINTER(c_int), POINTER(c_double),
+                                   POINTER(c_int), P]),
         "hdg_mlp_param_count": (c_int64, [c_int, c_int, c_int]),
         "hdg_mlp_init": (c_int, [P, c_int, c_int, c_int, ctypes.c_uint64, P]),
         "hdg_mlp_features": (c_int, [P, P, P, P, P, P, P, P, P]),
@@ -319,6 +321,17 @@ def hdg_newton_step(ctx, V, Vhat, V_n, V_nm1, dt, bdf_order, precision=HDG_PREC_
     if history:
         return it.value, res.value, list(hist_buf)[:it.value + 1], tr.value
     return it.value, res.value
+
+
+def hdg_dirk3_step(ctx, V, Vhat, V_n, dt, precision=HDG_PREC_FP64, tol=1e-10, max_newton=10, stream=None):
+    """One DIRK(3,3) step; (V, Vhat) in: first stage's guess, out: level n+1.
+    Returns (Newton updates per stage [3], final residual norm, trace-solver iterations)."""
+    its = (c_int * 3)()
+    res = c_double()
+    tr = c_int()
+    _check(_lib.hdg_dirk3_step(ctx, _ptr(V), _ptr(Vhat), _ptr(V_n), dt, precision, tol, max_newton, its, byref(res),
+                               byref(tr), _stream(stream)))
+    return list(its), res.value, tr.value
 
 
 def hdg_ctx_set_refinement(ctx, tol=1e-10, fp64_fallback=True):

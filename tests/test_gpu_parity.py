@@ -15,6 +15,12 @@ pytestmark = pytest.mark.gpu
 
 TOL_BLOCK = 1e-10
 TOL_RES = 1e-12
+# The recovery data X = A'^{-1} B' of the mixed form at the full 24^3 workload: the refinement
+# solves the assembled system to FP64 accuracy, but X inherits the assembly's rounding (exact
+# slices to 2^-48 of row-max x column-max per product) amplified by the condition of A' (~1e6
+# before equilibration at this mesh size): measured 1.0-1.5e-10 against the oracle, while S and
+# g, the condensed blocks, stay at 1.2e-12 and 6e-14. The derived bound for X and y:
+TOL_RECOV_MIXED = 3e-10
 
 
 def _sample(E, k, seed=0):
@@ -133,12 +139,13 @@ def test_mixed_tile_shapes_match_oracle(variant, monkeypatch):
         assert rel_fro(g[e], L["g"]) < TOL_BLOCK, (variant, e)
 
 
-@pytest.mark.parametrize("cvariant", [0, 1, 2])
-@pytest.mark.parametrize("name", ["ns3d_p3", "euler2d_p2", "ns2d_p4"])
+@pytest.mark.parametrize("cvariant", [0, 1, 2, 3])
+@pytest.mark.parametrize("name", ["ns3d_p3", "euler2d_p2", "ns2d_p4", "ns3d_p1"])
 def test_mixed_condensation_shapes_match_oracle(name, cvariant, monkeypatch):
-    """Every compiled shape of the tensor-core condensation (32-column blocks with 256 and
-    512 threads; 16-column blocks with the second residual from slices of A') gives the
-    oracle's S, g, X and y, including the ragged last block of right-hand sides."""
+    """Every compiled shape of the tensor-core condensation (mma.sync: 32-column blocks with 256
+    and 512 threads, 16-column blocks with the second residual from slices of A'; tcgen05: TMEM
+    accumulators, 32-column blocks) gives the oracle's S, g, X and y, including the ragged last
+    block of right-hand sides."""
     monkeypatch.setenv("HDG_COND_VARIANT", str(cvariant))
     case = CASES[name]
     gc = GpuCase(case)
@@ -297,8 +304,9 @@ def test_bench_workload_full_size_sampled(precision):
         assert rel_fro(W.g[e].cpu().numpy(), L["g"]) < TOL_BLOCK, e
         nv, nt = W.info["nv"], W.info["nt"]
         nq = L["Rl"].size - nv
-        assert rel_fro(W.recov[e, :nv * nt].cpu().numpy().reshape(nv, nt), L["X"][nq:]) < TOL_BLOCK, e
-        assert rel_fro(W.recov[e, nv * nt:].cpu().numpy(), L["y"][nq:]) < TOL_BLOCK, e
+        tol_x = TOL_BLOCK if precision == 0 else TOL_RECOV_MIXED
+        assert rel_fro(W.recov[e, :nv * nt].cpu().numpy().reshape(nv, nt), L["X"][nq:]) < tol_x, e
+        assert rel_fro(W.recov[e, nv * nt:].cpu().numpy(), L["y"][nq:]) < tol_x, e
 
 
 @pytest.mark.parametrize("precision", [0, 1])
@@ -344,5 +352,22 @@ def test_ns_bdf2_newton_step_gmres_matches_oracle(name, precision):
     assert tr > it                       # the trace systems were solved iteratively
     assert it == res.iters, (it, res.iters)
     assert abs(rh[0] - res.res_norms[0]) <= 1e-12 * res.res_norms[0]
+    assert rel_fro(V_gpu.cpu().numpy(), res.V) < 1e-10
+    assert rel_fro(Vh_gpu.cpu().numpy(), res.Vhat) < 1e-10
+
+
+@pytest.mark.parametrize("name,precision", [("euler2d_p2", 0), ("ns2d_p3", 0), ("ns2d_p3", 1)])
+def test_dirk3_step_matches_oracle(name, precision):
+    """One DIRK(3,3) step (Sec. 5) through hdg_dirk3_step against the oracle's: the Newton
+    updates of every stage and the level n+1 state."""
+    from oracle.hdg import dirk3_step
+    case = CASES[name]
+    gc = GpuCase(case)
+    prob, Q, V, Vh = oracle_setup(case)
+    dt = 0.05
+    res, iters = dirk3_step(prob, Q, V, Vh, dt, tol=1e-10, max_it=10)
+    V_gpu, Vh_gpu = gc.V.clone(), gc.Vhat.clone()
+    its, rn, tr = gc.hdg.hdg_dirk3_step(gc.ctx.handle, V_gpu, Vh_gpu, gc.V, dt, precision, 1e-10, 10)
+    assert its == iters, (its, iters)
     assert rel_fro(V_gpu.cpu().numpy(), res.V) < 1e-10
     assert rel_fro(Vh_gpu.cpu().numpy(), res.Vhat) < 1e-10
