@@ -202,8 +202,8 @@ NCU_TRAFFIC = {
 
 # the sources that define the captured kernels and their launch shapes (device code and the
 # dispatch of the mixed form); host-side entry points do not change the kernels
-KERNEL_SOURCES = ("asm_tc.cuh", "condense_tc.cuh", "ozaki.cuh", "dfloat.cuh", "assemble_mixed.cuh",
-                  "assemble_fp64.cuh", "hdg_device.cuh", "assemble_mixed.cu")
+KERNEL_SOURCES = ("asm_tc.cuh", "condense_tc.cuh", "condense_t5.cuh", "ozaki.cuh", "dfloat.cuh",
+                  "assemble_mixed.cuh", "assemble_fp64.cuh", "hdg_device.cuh", "assemble_mixed.cu")
 
 
 def kernel_sources_digest() -> str:

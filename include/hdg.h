@@ -54,7 +54,7 @@ enum {
   HDG_ERR_SINGULAR = 3,    /* zero pivot in an element factorisation              */
   HDG_ERR_REFINE = 4,      /* iterative refinement did not reach its tolerance    */
   HDG_ERR_NOT_CONVERGED = 5, /* Newton or the trace solver missed its tolerance          */
-  /* 6 is not used: no kernel of this library waits on another, so nothing can time out */
+  HDG_ERR_TIMEOUT = 6,       /* a bounded wait inside a kernel gave up (HDG_ELEM_TIMEOUT) */
   HDG_ERR_CUDA = 7,
   HDG_ERR_UNSUPPORTED = 8  /* (dim, p, quadrature, physics) not compiled in        */
 };
@@ -68,9 +68,14 @@ enum { HDG_SCHEME_HDG = 0, HDG_SCHEME_EDG = 1, HDG_SCHEME_IEDG = 2 };
  *   SINGULAR     zero pivot in the element factorisation
  *   REFINE       mixed form: the iterative refinement of X = A^{-1}[B | R_v] missed its
  *                tolerance (left set only when the FP64 recomputation is switched off)
- *   FP64         mixed form: the block missed the tolerance and was recomputed by the FP64
- *                kernels (hdg_ctx_set_refinement); its S, g, X, y are the FP64 form's */
-enum { HDG_ELEM_NONPHYSICAL = 1, HDG_ELEM_SINGULAR = 2, HDG_ELEM_REFINE = 4, HDG_ELEM_FP64 = 8 };
+ *   FP64         mixed form: the block missed the tolerance (or timed out) and was recomputed
+ *                by the FP64 kernels (hdg_ctx_set_refinement); S, g, X, y are the FP64 form's
+ *   TIMEOUT      mixed form, tcgen05 condensation: a bounded wait for its operands or its
+ *                tensor-core products gave up (about a second); the kernel freed its tensor
+ *                memory and returned, the context stays usable, and the block's outputs are
+ *                invalid unless the FP64 recomputation replaced them (then FP64 is set instead) */
+enum { HDG_ELEM_NONPHYSICAL = 1, HDG_ELEM_SINGULAR = 2, HDG_ELEM_REFINE = 4, HDG_ELEM_FP64 = 8,
+       HDG_ELEM_TIMEOUT = 16 };
 
 typedef struct hdg_mesh* hdg_mesh_t;
 typedef struct hdg_ctx* hdg_ctx_t;
@@ -246,7 +251,8 @@ int hdg_residual_norm(hdg_ctx_t ctx, const double* R, double* norm, void* stream
  * Context-owned workspaces are allocated on the first call. Synchronises once per Newton
  * iteration (residual norm and status bits). Errors: HDG_ERR_NOT_CONVERGED (max_newton
  * updates made, or the trace solve missed its tolerance), HDG_ERR_NONPHYSICAL,
- * HDG_ERR_SINGULAR, HDG_ERR_REFINE (mixed form with the FP64 recomputation off). */
+ * HDG_ERR_SINGULAR, HDG_ERR_REFINE / HDG_ERR_TIMEOUT (mixed form with the FP64 recomputation
+ * off). */
 int hdg_newton_solve(hdg_ctx_t ctx, double* V, double* Vhat, const double* hist, double mass_coef, int precision,
                      double tol, int max_newton, int* newton_iters, double* res_norm, double* res_history,
                      int* trace_iters, void* stream);

@@ -52,6 +52,7 @@ struct AssembleArgs {
   // replaces the flag by HDG_STATUS_FP64 (the block is now the FP64 form's).
   int only_flag;
   float refine_tol;     // mixed condensation: tolerance of the refinement status bit
+  int stall_first_copy; // test hook of k_condense_t5: its first operand copy is never issued
 };
 
 enum { HDG_STATUS_NONPHYSICAL = 1, HDG_STATUS_SINGULAR = 2, HDG_STATUS_REFINE = 4, HDG_STATUS_FP64 = 8,

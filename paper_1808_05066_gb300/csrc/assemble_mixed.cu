@@ -95,11 +95,11 @@ CondVariant make_cond_variant2() {
                      &k_condense_prep<C, kSlices, false>};
 }
 
-// tcgen05 products with TMEM accumulators, 32-column blocks, one CTA per SM
-template <class C>
+// tcgen05 products with TMEM accumulators: NB-column blocks, CPS CTAs per SM
+template <class C, int NB, int CPS>
 CondVariant make_cond_variant_t5() {
-  return CondVariant{CondT5<C, kSlices>::NTH, CondT5<C, kSlices>::bytes, &k_condense_t5<C, kSlices>, 1,
-                     &k_condense_prep<C, kSlices, true>};
+  using Q = CondT5<C, kSlices, NB, CPS>;
+  return CondVariant{Q::NTH, Q::bytes, &k_condense_t5<C, kSlices, NB, CPS>, 1, &k_condense_prep<C, kSlices, true>};
 }
 
 // Times `launch` once on the stream (the chunk's outputs are rewritten each time).
@@ -147,9 +147,10 @@ int run_mixed(hdg_ctx* ctx, const double* V, const double* Vhat, const double* h
   const AsmVariant variants[] = {make_variant<C, 2, 4>(), make_variant<C, 4, 4>(), make_variant<C, 2, 2>(),
                                  make_variant<C, 4, 2>()};
   constexpr int NVAR = 4;
-  const CondVariant cvariants[] = {make_cond_variant<C, 256>(), make_cond_variant<C, 512>(), make_cond_variant2<C>(),
-                                   make_cond_variant_t5<C>()};
-  constexpr int NCVAR = 4;
+  const CondVariant cvariants[] = {make_cond_variant<C, 256>(),        make_cond_variant<C, 512>(),
+                                   make_cond_variant2<C>(),             make_cond_variant_t5<C, 32, 1>(),
+                                   make_cond_variant_t5<C, 16, 2>()};
+  constexpr int NCVAR = 5;
   if (!ctx->attr_mixed) {  // per context, hence per device
     for (const AsmVariant& v : variants)
       if (int rc2 = v.set_attr()) return rc2;
@@ -187,6 +188,7 @@ int run_mixed(hdg_ctx* ctx, const double* V, const double* Vhat, const double* h
   a.R = R;
   a.status = status;
   a.refine_tol = (float)ctx->refine_tol;
+  a.stall_first_copy = ctx->t5_stall ? 1 : 0;
   const int64_t ch = ctx->chunk;
   a.ptv = ctx->d_scr;
   a.ptf = a.ptv + ch * C::NG * C::PT_VOL;
@@ -299,10 +301,11 @@ int run_mixed(hdg_ctx* ctx, const double* V, const double* Vhat, const double* h
       cv.kernel<<<cv.grid(a.ne), cv.threads, cv.smem, s>>>(a);
     }
     if (ctx->refine_fallback) {
-      // blocks whose refinement missed its tolerance are recomputed by the FP64 kernels (the
-      // chunk's scratch is free again); every other CTA returns at once
+      // blocks whose refinement missed its tolerance (or whose condensation gave up a wait) are
+      // recomputed by the FP64 kernels (the chunk's scratch is free again); every other CTA
+      // returns at once
       AssembleArgs f = a;
-      f.only_flag = HDG_STATUS_REFINE;
+      f.only_flag = HDG_STATUS_REFINE | HDG_STATUS_TIMEOUT;
       {
         LaunchScope ls(ctx, HDG_KERNEL_POINTWISE, s);
         k_pointwise<C><<<(unsigned)a.ne, pw_threads, 0, s>>>(f, ctx->T, ctx->ph);

@@ -238,8 +238,9 @@ int hdg_ctx_create(hdg_mesh_t mesh, const hdg_physics* phys, int device, hdg_ctx
   }
   if (const char* cv = std::getenv("HDG_COND_VARIANT")) {  // force a condensation shape (tests)
     long v = std::strtol(cv, nullptr, 10);
-    if (v >= 0 && v < 4) c->cond_variant = (int)v;
+    if (v >= 0 && v < 5) c->cond_variant = (int)v;
   }
+  if (const char* st = std::getenv("HDG_T5_STALL_FIRST_COPY")) c->t5_stall = std::strtol(st, nullptr, 10) != 0;
   if (const char* ch = std::getenv("HDG_ELEMENT_CHUNK")) {
     long v = std::strtol(ch, nullptr, 10);
     if (v > 0) c->chunk = std::min<int64_t>(v, c->E);
@@ -618,6 +619,10 @@ int hdg_newton_solve(hdg_ctx_t ctx, double* V, double* Vhat, const double* hist,
     if (bits & HDG_ELEM_SINGULAR) {
       set_error("hdg_newton_solve: singular element matrix");
       return HDG_ERR_SINGULAR;
+    }
+    if (bits & HDG_ELEM_TIMEOUT) {  // only with the FP64 recomputation switched off
+      set_error("hdg_newton_solve: a bounded wait in the element condensation gave up");
+      return HDG_ERR_TIMEOUT;
     }
     if (bits & HDG_ELEM_REFINE) {  // only with the FP64 recomputation switched off
       set_error("hdg_newton_solve: iterative refinement of an element block missed its tolerance");

@@ -92,6 +92,9 @@ struct hdg_ctx {
   // recomputation of the blocks it flags (hdg_ctx_set_refinement)
   double refine_tol = 1e-10;
   bool refine_fallback = true;
+  // test hook (environment HDG_T5_STALL_FIRST_COPY): k_condense_t5 never issues its first operand
+  // copy, so its bounded waits run out and it reports HDG_ELEM_TIMEOUT
+  bool t5_stall = false;
   // trace solver of the Newton iterations (hdg_ctx_set_trace_solver)
   int newton_solver = HDG_SOLVER_AUTO;
   double newton_rtol = 1e-12;

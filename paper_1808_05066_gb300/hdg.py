@@ -20,6 +20,7 @@ HDG_ERR_NONPHYSICAL = 2
 HDG_ERR_SINGULAR = 3
 HDG_ERR_REFINE = 4
 HDG_ERR_NOT_CONVERGED = 5
+HDG_ERR_TIMEOUT = 6
 HDG_ERR_CUDA = 7
 HDG_ERR_UNSUPPORTED = 8
 HDG_PREC_FP64 = 0
@@ -34,6 +35,7 @@ HDG_ELEM_NONPHYSICAL = 1
 HDG_ELEM_SINGULAR = 2
 HDG_ELEM_REFINE = 4
 HDG_ELEM_FP64 = 8
+HDG_ELEM_TIMEOUT = 16
 
 EXPORTED = [
     "hdg_mesh_create", "hdg_mesh_destroy", "hdg_mesh_get_info", "hdg_mesh_copy_topology",

@@ -1,8 +1,9 @@
 """The error contract of the C-ABI on the GPU: every HDG_ERR_* code the header declares for a
 compute call is produced by input data or by a call's own limits, and the per-element status
 bits say which elements caused it. Nothing here faults or hangs a GPU: the failures are a
-non-physical state, a time coefficient that is not a number, iteration limits and a
-refinement tolerance no block can meet."""
+non-physical state, a time coefficient that is not a number, iteration limits, a refinement
+tolerance no block can meet, and a bounded wait that runs out because the host asked the
+kernel not to issue the copy it waits for."""
 import math
 
 import numpy as np
@@ -119,3 +120,30 @@ def test_unsupported_configuration():
     from paper_1808_05066_gb300 import hdg
     mesh = hdg.Mesh(3, 1, 0.0, 1.0, 4)          # 3D p = 4 is not compiled in
     assert _code(lambda: hdg.Context(mesh, 1.4, 0.1, 1600.0, 0.71, 0)) == hdg.HDG_ERR_UNSUPPORTED
+
+
+def test_tcgen05_condensation_wait_timeout(monkeypatch):
+    """Every wait of the tcgen05 condensation is bounded. With the test hook that leaves its first
+    operand copy unissued (a phase that nothing completes), the waits run out after about a
+    second: the kernel sets HDG_ELEM_TIMEOUT, frees its tensor memory and returns, and the
+    context stays usable. The FP64 recomputation then replaces the blocks (HDG_ELEM_FP64, the
+    FP64 form's outputs bit for bit); without it the Newton solve returns HDG_ERR_TIMEOUT."""
+    monkeypatch.setenv("HDG_COND_VARIANT", "3")
+    monkeypatch.setenv("HDG_T5_STALL_FIRST_COPY", "1")
+    gc = GpuCase(CASES["ns2d_p3"])
+    hdg, torch = gc.hdg, gc.torch
+    hist = gc.history()
+    gc.assemble(hist, precision=0)
+    ref = [t.clone() for t in (gc.S, gc.g, gc.recov, gc.R)]
+    gc.assemble(hist, precision=1)
+    assert (gc.status.cpu().numpy() == hdg.HDG_ELEM_FP64).all()
+    for x, y in zip((gc.S, gc.g, gc.recov, gc.R), ref):
+        assert torch.equal(x, y)
+    hdg.hdg_ctx_set_refinement(gc.ctx.handle, 1e-10, False)
+    gc.assemble(hist, precision=1)
+    assert (gc.status.cpu().numpy() & hdg.HDG_ELEM_TIMEOUT).all()
+    V, Vh = gc.V.clone(), gc.Vhat.clone()
+    code = _code(lambda: hdg.hdg_newton_solve(gc.ctx.handle, V, Vh, hist, gc.case.mass_coef, 1, 1e-10, 2))
+    assert code == hdg.HDG_ERR_TIMEOUT
+    gc.assemble(hist, precision=0)             # the context still works
+    assert torch.equal(gc.S, ref[0]) and int(gc.status.abs().sum()) == 0
