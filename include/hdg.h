@@ -81,10 +81,14 @@ typedef struct hdg_mesh* hdg_mesh_t;
 typedef struct hdg_ctx* hdg_ctx_t;
 
 typedef struct {
-  double gamma;    /* ratio of specific heats (1.4) */
-  double mach;     /* reference Mach number M */
-  double reynolds; /* Re; 0 = inviscid (Euler) */
-  double prandtl;  /* Pr */
+  double gamma;       /* ratio of specific heats (1.4) */
+  double mach;        /* reference Mach number M */
+  double reynolds;    /* Re; 0 = inviscid (Euler) */
+  double prandtl;     /* Pr */
+  double mu_exponent; /* power law mu = (1/Re)(T/T_inf)^omega, kappa likewise (Sec. 5.6 uses 3/4;
+                         T_inf = 1 in this nondimensionalisation); 0 = constant viscosity; 0..4 */
+  int32_t visc_flux;  /* viscous numerical flux: 0 or 2 = G(vhat, q) . n (Eq. numericalFluxNS_2, the
+                         choice of Sec. 5), 1 = G(v, q) . n (Eq. numericalFluxNS_1) */
 } hdg_physics;
 
 typedef struct {
@@ -92,7 +96,9 @@ typedef struct {
   int32_t m, Np, Nf, nF, NG, NGF;
   int32_t nv, nt;              /* per-element interior / trace unknowns */
   int32_t geo_stride;
-  int64_t n_elem, n_faces, n_trace; /* n_trace = n_faces * Nf * m */
+  int64_t n_elem, n_faces, n_trace; /* n_trace = n_trace_nodes * m */
+  int32_t scheme;                   /* HDG_SCHEME_* */
+  int64_t n_trace_nodes;            /* HDG: n_faces * Nf (a trace per face); EDG / IEDG: skeleton nodes */
 } hdg_mesh_info;
 
 /* Mesh T_h (Sec. 3.1.1): the n[0] x .. x n[dim-1] periodic grid on the box
@@ -102,8 +108,12 @@ typedef struct {
  *               Meshes whose elements differ in degree are not built: a non-uniform array
  *               returns HDG_ERR_UNSUPPORTED (HDG_ERR_INVALID_ARG for a degree outside 1..4).
  *   p           polynomial degree k of Sec. 3.1.2 (1..4).
- *   scheme      trace space of Sec. 3.4: HDG_SCHEME_HDG (built); HDG_SCHEME_EDG and
- *               HDG_SCHEME_IEDG return HDG_ERR_UNSUPPORTED.
+ *   scheme      trace space of Sec. 3.4: HDG_SCHEME_HDG (one trace per face, Vhat [F][Nf][m]) or
+ *               HDG_SCHEME_EDG (a continuous trace, one unknown per skeleton node, Vhat [N][m],
+ *               nodes numbered in order of first appearance over (element, local face, face
+ *               node)); HDG_SCHEME_IEDG continuous on interior faces only, which on these periodic
+ *               meshes (every face interior) is EDG. The local problem and the condensation are the
+ *               same for all three; only the global trace numbering differs.
  *   quad_points K Gauss-Jacobi points per direction, exact to degree 2K-1 (0 selects p+1).
  * Host-only work; the mesh owns host arrays only (freed by hdg_mesh_destroy).
  * Errors: HDG_ERR_INVALID_ARG, HDG_ERR_UNSUPPORTED. */
@@ -115,8 +125,12 @@ int hdg_mesh_get_info(hdg_mesh_t mesh, hdg_mesh_info* out);
  * node of each local face node), face_side [F][2] (e * nF + f; owner first). Any
  * pointer may be NULL. */
 int hdg_mesh_copy_topology(hdg_mesh_t mesh, int32_t* face_of, int32_t* fnode_map, int32_t* face_side);
-/* Host copies: element node coordinates xnode [E][Np][dim], canonical face-node
- * coordinates xfnode [F][Nf][dim] (owner side), geometry geo [E][geo_stride] =
+/* Global trace node of every local face node, tnode [E][nF][Nf] (host): HDG face * Nf + canonical
+ * face node; EDG the skeleton node. The element's trace unknowns are Vhat[tnode][0..m). */
+int hdg_mesh_copy_trace_map(hdg_mesh_t mesh, int32_t* tnode);
+/* Host copies: element node coordinates xnode [E][Np][dim], trace-node coordinates xfnode
+ * [n_trace_nodes][dim] (HDG: canonical face nodes [F][Nf], owner side; EDG: skeleton nodes),
+ * geometry geo [E][geo_stride] =
  * (Jinv [dim][dim] with Jinv[r][k] = d r / d x_k, |det J|, per face: unit outward
  * normal [dim], surface Jacobian). Any pointer may be NULL. */
 int hdg_mesh_copy_coords(hdg_mesh_t mesh, double* xnode, double* xfnode, double* geo);
@@ -217,6 +231,14 @@ int hdg_assemble_condense_host(hdg_ctx_t ctx, const double* V, const double* Vha
 int hdg_assemble_condense_noalloc(hdg_ctx_t ctx, const double* V, const double* Vhat, const double* hist,
                                   double mass_coef, double* S, double* g, double* recov, double* R,
                                   int32_t* elem_status, void* stream);
+
+/* Entropy diagnostics of Eq. PiS (Sec. 5.6) from (v_h, q_h), q_h the gradient of Eq. hDG_NS0
+ * (element-local, with Vhat): *int_rho_s = int rho s with s = log(p / rho^gamma) (Sec. 2.3), and
+ * *production = (1/c_v) int (Phi / T + kappa |grad T|^2 / T^2), Phi = grad V : tau, the physical
+ * entropy production (0 for Euler). The scheme's own part is Pi_S = d/dt int rho s - production:
+ * callers difference int_rho_s between time levels. Writes host scalars (synchronises). */
+int hdg_entropy_production(hdg_ctx_t ctx, const double* V, const double* Vhat, double* int_rho_s, double* production,
+                           void* stream);
 
 /* Global trace system sum_e P_e^T S_e P_e dVhat = -sum_e P_e^T g_e (Sec. 3.2: only vhat
  * is globally coupled). method: HDG_SOLVER_GMRES (restarted GMRES(30), face-block Jacobi

@@ -48,8 +48,21 @@ class ElementTables:
 class Problem:
     """A mesh + physics + the element tables the residual needs."""
 
-    def __init__(self, mesh: Mesh, phys: ph.Physics):
+    def __init__(self, mesh: Mesh, phys: ph.Physics, viscous_flux_option: int = 2, scheme: str = "hdg"):
+        """viscous_flux_option: 2 = ghat = G(vhat, q) . n (Eq. numericalFluxNS_2, used in all of
+        Sec. 5), 1 = ghat = G(v, q) . n (Eq. numericalFluxNS_1).
+        scheme (Sec. 3.4): "hdg" (E^E_h empty: one trace per face, Vhat [F, Nf, m]) or "edg"
+        (E^E_h = all faces: a continuous trace, one unknown per skeleton node, Vhat [N, m]);
+        on these periodic meshes every face is interior, so IEDG is EDG."""
+        if viscous_flux_option not in (1, 2):
+            raise ValueError(viscous_flux_option)
+        if scheme not in ("hdg", "edg", "iedg"):
+            raise ValueError(scheme)
         self.mesh, self.phys = mesh, phys
+        self.viscous_flux_option = viscous_flux_option
+        self.scheme = "edg" if scheme == "iedg" else scheme
+        if self.scheme == "edg":
+            self.n_edg, self.edg_index = mesh.edg_numbering()
         ref = mesh.ref
         self.d, self.m = mesh.dim, mesh.dim + 2
         self.Np, self.Nf, self.nF = ref.Np, ref.Nf, ref.nF
@@ -82,17 +95,35 @@ class Problem:
     # -- gather / scatter between global trace and element-local trace ------------------
     def gather_trace(self, Vhat, e):
         mesh = self.mesh
+        if self.scheme == "edg":
+            return Vhat[self.edg_index[e]]                                    # [nF, Nf, m]
         return Vhat[mesh.face_of[e][:, None], mesh.fnode_map[e]]          # [nF, Nf, m]
 
-    def trace_index(self, e):
-        """Global flat indices of the element's local trace unknowns (f, c, i)."""
+    def trace_node(self, e):
+        """Global trace node [nF, Nf] of each local face node of element e."""
         mesh = self.mesh
-        base = (mesh.face_of[e][:, None] * self.Nf + mesh.fnode_map[e]) * self.m
+        if self.scheme == "edg":
+            return self.edg_index[e]
+        return mesh.face_of[e][:, None] * self.Nf + mesh.fnode_map[e]
+
+    def trace_index(self, e):
+        """Global flat indices of the element's local trace unknowns (f, c, i); with EDG a
+        node shared by several local faces appears several times (P_e has repeated columns)."""
+        base = self.trace_node(e) * self.m
         return (base[:, :, None] + np.arange(self.m)).ravel()
 
     @property
     def n_trace(self):
+        if self.scheme == "edg":
+            return self.n_edg * self.m
         return self.mesh.nFaces * self.Nf * self.m
+
+    @property
+    def trace_shape(self):
+        """Shape of the global Vhat array."""
+        if self.scheme == "edg":
+            return (self.n_edg, self.m)
+        return (self.mesh.nFaces, self.Nf, self.m)
 
     # -- viscous fluxes (Sec. 3.3) ---------------------------------------------------------
     def volume_viscous_flux(self, v, q):
@@ -100,9 +131,11 @@ class Problem:
         return ph.viscous_flux(v, q, self.phys)
 
     def face_viscous_flux(self, vhat, v, q, n):
-        """Viscous numerical flux ghat_h = G(vhat_h, q_h) . n of Eq. numericalFluxNS_2, the
-        option used in all of Sec. 5; the interior trace v is not used by this option."""
-        return np.einsum("...mj,j->...m", ph.viscous_flux(vhat, q, self.phys), n)
+        """Viscous numerical flux: ghat_h = G(vhat_h, q_h) . n (Eq. numericalFluxNS_2, the option
+        used in all of Sec. 5; the interior trace v is not used) or G(v_h, q_h) . n
+        (Eq. numericalFluxNS_1; vhat is not used)."""
+        state = vhat if self.viscous_flux_option == 2 else v
+        return np.einsum("...mj,j->...m", ph.viscous_flux(state, q, self.phys), n)
 
     # -- residuals ----------------------------------------------------------------------
     def element_residual(self, e, Q, V, Vh, mass_coef=0.0, hist_w=None):
@@ -207,6 +240,32 @@ class Problem:
             out += c * np.einsum("g,ga,gm->am", T.W, T.phi, u)
         return out
 
+    def entropy_production_terms(self, Q, V):
+        """(int rho s, (1/c_v) int (Phi / T + kappa |grad T|^2 / T^2)) of Eq. PiS (Sec. 5.6) with
+        Phi = grad V : tau, both from (v_h, q_h) at the volume quadrature points; s = log(p / rho^gamma)
+        (Sec. 2.3). Pi_S = d/dt int rho s - the second term is the scheme's own entropy production."""
+        phys, g = self.phys, self.phys.gamma
+        d = self.d
+        tot_s = tot_phys = 0.0
+        for e in range(self.mesh.E):
+            T = self.tables(e)
+            v = T.phi @ V[e]                                    # [ng, m]
+            q = np.einsum("ga,amk->gmk", T.phi, Q[e])           # [ng, m, d]
+            rho, vel, p = ph.primitives_of_v(v, g)
+            tot_s += T.W @ (rho * ph.thermo_entropy(rho, p, g))
+            w, vm = v[:, 1:-1], v[:, -1]
+            gradV = -q[:, 1:-1, :] / vm[:, None, None] + w[:, :, None] * (q[:, -1, :] / vm[:, None] ** 2)[:, None, :]
+            gradT = q[:, -1, :] / (phys.cv * vm[:, None] ** 2)
+            Temp = 1.0 / (phys.cv * (-vm))
+            fac = phys.viscosity_factor(vm) * np.ones_like(vm)
+            mu, kappa = phys.mu * fac, phys.kappa * fac
+            div = np.trace(gradV, axis1=1, axis2=2)
+            tau = mu[..., None, None] * (gradV + np.swapaxes(gradV, 1, 2)) \
+                - (2.0 / 3.0) * (mu * div)[:, None, None] * np.eye(d)
+            Phi = np.einsum("gij,gij->g", gradV, tau)
+            tot_phys += T.W @ ((Phi / Temp + kappa * np.sum(gradT ** 2, axis=1) / Temp ** 2) / phys.cv)
+        return tot_s, tot_phys
+
     def integrals(self, V):
         """(total u [m], total generalised entropy int H) over the mesh."""
         tot_u = np.zeros(self.m)
@@ -239,12 +298,17 @@ def solve_equilibrated(A, B):
 # State initialisation from primitive fields (interpolation at nodes)
 # ---------------------------------------------------------------------------------------
 def interpolate_state(prob: Problem, prim_fn):
-    """V at element nodes and Vhat at canonical face nodes from prim_fn(x) -> (rho, vel, p)."""
+    """V at element nodes and Vhat at the trace nodes (canonical face nodes; EDG: skeleton
+    nodes) from prim_fn(x) -> (rho, vel, p)."""
     mesh, g = prob.mesh, prob.phys.gamma
     rho, vel, p = prim_fn(mesh.xnode)
     V = ph.v_of_u(ph.u_of_primitives(rho, vel, p, g), g)
-    owner = np.array([sides[0] for sides in mesh.face_elems])          # [F, 2] (e, f)
     fn = np.array(mesh.ref.face_nodes)
+    if prob.scheme == "edg":
+        Vhat = np.zeros(prob.trace_shape)
+        Vhat[prob.edg_index.reshape(-1)] = V[:, fn, :].reshape(-1, prob.m)   # every copy is the same node
+        return V, Vhat
+    owner = np.array([sides[0] for sides in mesh.face_elems])          # [F, 2] (e, f)
     Vhat = V[owner[:, 0][:, None], fn[owner[:, 1]]]                     # [F, Nf, m]
     return V, Vhat
 

@@ -170,6 +170,17 @@ class Mesh:
             elem_nodes.append(s)
         return ids, elem_nodes
 
+    def edg_numbering(self):
+        """The continuous trace space of EDG (Sec. 3.4, E^E_h = all faces): one unknown per
+        skeleton node, numbered in order of first appearance over (element, local face, face
+        node). Returns (number of nodes, index [E, nF, Nf] of every local face node)."""
+        ids, _ = self._trace_nodes_edg()
+        period = self.n * self.p
+        fn = np.array(self.ref.face_nodes)                                  # [nF, Nf]
+        keys = self.Nint[:, fn, :] % period                                 # [E, nF, Nf, d]
+        index = np.array([ids[tuple(k)] for k in keys.reshape(-1, self.dim)], dtype=np.int64)
+        return len(ids), index.reshape(self.E, self.ref.nF, self.ref.Nf)
+
     def trace_dof_edg(self):
         ids, _ = self._trace_nodes_edg()
         return len(ids)

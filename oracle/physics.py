@@ -21,6 +21,7 @@ class Physics:
     mach: float = 0.5
     reynolds: float = 0.0            # 0 = inviscid (Euler)
     prandtl: float = 0.71
+    mu_exponent: float = 0.0         # power law mu = (1/Re) (T / T_inf)^omega (Sec. 5.6 uses 3/4); 0: constant
 
     @property
     def viscous(self) -> bool:
@@ -37,6 +38,13 @@ class Physics:
     @property
     def kappa(self) -> float:
         return self.gamma * self.cv * self.mu / self.prandtl
+
+    def viscosity_factor(self, vm):
+        """(T / T_inf)^omega at entropy variable v_m, T = 1 / (c_v (-v_m)); the freestream
+        temperature of this nondimensionalisation is T_inf = p_inf / ((gamma - 1) c_v) = 1."""
+        if self.mu_exponent == 0.0:
+            return 1.0
+        return (1.0 / (self.cv * (-vm))) ** self.mu_exponent
 
 
 def cabs(x):
@@ -147,7 +155,8 @@ def viscous_flux(v, q, phys: Physics):
 
     The matrices K_jk are not printed; G is evaluated through the primitive gradients
     grad V_i = -grad w_i / v_m + w_i grad v_m / v_m^2 and T = 1/(c_v (-v_m)),
-    grad T = grad v_m / (c_v v_m^2), which equals -K_jk (du/dv) q."""
+    grad T = grad v_m / (c_v v_m^2), which equals -K_jk (du/dv) q. With a power law
+    (Physics.mu_exponent, Sec. 5.6) mu and kappa are scaled by (T / T_inf)^omega."""
     gamma = phys.gamma
     d = v.shape[-1] - 2
     w, vm = v[..., 1:-1], v[..., -1]
@@ -156,9 +165,14 @@ def viscous_flux(v, q, phys: Physics):
     gradV = -qw / vm[..., None, None] + w[..., :, None] * (qm / (vm * vm)[..., None])[..., None, :]
     gradT = qm / (phys.cv * (vm * vm)[..., None])
     div = np.trace(gradV, axis1=-2, axis2=-1)
-    tau = phys.mu * (gradV + np.swapaxes(gradV, -1, -2)
-                     - (2.0 / 3.0) * div[..., None, None] * np.eye(d))
-    f = -phys.kappa * gradT
+    mu_fac = phys.viscosity_factor(vm)               # mu(T) / mu_ref = kappa(T) / kappa_ref (Pr fixed)
+    mu = phys.mu * mu_fac
+    kappa = phys.kappa * mu_fac
+    if np.ndim(mu_fac):
+        mu, kappa = mu[..., None, None], kappa[..., None]
+    tau = mu * (gradV + np.swapaxes(gradV, -1, -2)
+                - (2.0 / 3.0) * div[..., None, None] * np.eye(d))
+    f = -kappa * gradT
     zero = np.zeros(v.shape[:-1] + (1, d), dtype=tau.dtype)
     energy = np.einsum("...i,...ij->...j", vel, tau) - f
     return -np.concatenate([zero, tau, energy[..., None, :]], axis=-2)

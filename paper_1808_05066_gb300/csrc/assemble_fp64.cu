@@ -81,7 +81,42 @@ int run_fp64(hdg_ctx* ctx, const double* V, const double* Vhat, const double* hi
   return HDG_OK;
 }
 
+template <class C>
+int run_entropy(hdg_ctx* ctx, const double* V, const double* Vhat, double* acc, cudaStream_t s) {
+  AssembleArgs a{};
+  a.V = V;
+  a.Vhat = Vhat;
+  a.tgidx = ctx->d_tgidx;
+  a.geo = ctx->d_geo;
+  a.e0 = 0;
+  a.ne = ctx->E;
+  LaunchScope ls(ctx, HDG_KERNEL_OTHER, s);
+  k_entropy_terms<C><<<(unsigned)ctx->E, 128, 0, s>>>(a, ctx->T, ctx->ph, acc);
+  HDG_CK(cudaGetLastError());
+  return HDG_OK;
+}
+
 }  // namespace
+
+#define HDG_ENTROPY_CASE(D, P, VISC)                                          \
+  if (ctx->dim == D && ctx->p == P && ctx->K == P + 1 && ctx->visc == VISC) \
+    return run_entropy<Cfg<D, P, P + 1, VISC>>(ctx, V, Vhat, acc, s);
+
+int entropy_terms(hdg_ctx* ctx, const double* V, const double* Vhat, double* acc, cudaStream_t s) {
+  HDG_ENTROPY_CASE(2, 1, false)
+  HDG_ENTROPY_CASE(2, 2, false)
+  HDG_ENTROPY_CASE(2, 3, false)
+  HDG_ENTROPY_CASE(2, 4, false)
+  HDG_ENTROPY_CASE(2, 1, true)
+  HDG_ENTROPY_CASE(2, 2, true)
+  HDG_ENTROPY_CASE(2, 3, true)
+  HDG_ENTROPY_CASE(2, 4, true)
+  HDG_ENTROPY_CASE(3, 1, true)
+  HDG_ENTROPY_CASE(3, 2, true)
+  HDG_ENTROPY_CASE(3, 3, true)
+  set_error("entropy_terms: configuration not compiled in");
+  return HDG_ERR_UNSUPPORTED;
+}
 
 #define HDG_FP64_CASE(D, P, VISC)                                                                       \
   if (ctx->dim == D && ctx->p == P && ctx->K == P + 1 && ctx->visc == VISC)                            \

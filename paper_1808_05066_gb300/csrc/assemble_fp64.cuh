@@ -75,6 +75,46 @@ HDG_DEVI void load_element(const AssembleArgs& a, int64_t e, double (*z)[C::M], 
   for (int t = threadIdx.x; t < C::GEO; t += blockDim.x) G[t] = a.geo[e * C::GEO + t];
 }
 
+// v_h and, for Navier-Stokes, the gradient q_h of Eq. hDG_NS0 solved element by element (the
+// gradient of v_h plus the lifting of the face jumps vhat - v) at volume quadrature point g of the
+// element staged in shared memory (z: nodal values, dz: jumps at the face nodes, G: geometry).
+template <class C>
+HDG_DEVI void volume_point_state(int g, const DevTables& T, const double (*z)[C::M], const double (*dz)[C::M],
+                                 const double* G, double* v, double (*q)[C::D]) {
+  constexpr int D = C::D, M = C::M, NP = C::NP, NFN = C::NFN, NF = C::NF, NG = C::NG;
+  const double* Jinv = G;
+  const double detJ = G[D * D];
+  for (int i = 0; i < M; ++i) {
+    double s = 0.0;
+    for (int b = 0; b < NP; ++b) s += T.Phi[g * NP + b] * z[b][i];
+    v[i] = s;
+  }
+  if (C::VISC) {
+    for (int i = 0; i < M; ++i) {
+      double gr[D], lift[NF];
+      for (int r = 0; r < D; ++r) {
+        double s = 0.0;
+        for (int b = 0; b < NP; ++b) s += T.dPhi[(r * NG + g) * NP + b] * z[b][i];
+        gr[r] = s;
+      }
+      for (int f = 0; f < NF; ++f) {  // the same for every direction k
+        double l = 0.0;
+        for (int c = 0; c < NFN; ++c) l += T.PL[(f * NG + g) * NFN + c] * dz[f * NFN + c][i];
+        lift[f] = l;
+      }
+      for (int k = 0; k < D; ++k) {
+        double s = 0.0;
+        for (int r = 0; r < D; ++r) s += Jinv[r * D + k] * gr[r];
+        for (int f = 0; f < NF; ++f) {
+          const double* Gf = G + D * D + 1 + f * (D + 1);
+          s += Gf[k] * (Gf[D] / detJ) * lift[f];
+        }
+        q[i][k] = s;
+      }
+    }
+  }
+}
+
 // ------------------------------------------------------------------------------------
 // k_pointwise
 // ------------------------------------------------------------------------------------
@@ -107,36 +147,8 @@ __global__ void __launch_bounds__(128) k_pointwise(AssembleArgs a, DevTables T, 
     const int g = tid;
     const double W = T.W[g] * detJ;
     double v[M];
-    for (int i = 0; i < M; ++i) {
-      double s = 0.0;
-      for (int b = 0; b < NP; ++b) s += T.Phi[g * NP + b] * z[b][i];
-      v[i] = s;
-    }
     double q[M][D];
-    if (C::VISC) {
-      for (int i = 0; i < M; ++i) {
-        double gr[D], lift[NF];
-        for (int r = 0; r < D; ++r) {
-          double s = 0.0;
-          for (int b = 0; b < NP; ++b) s += T.dPhi[(r * NG + g) * NP + b] * z[b][i];
-          gr[r] = s;
-        }
-        for (int f = 0; f < NF; ++f) {  // the same for every direction k
-          double l = 0.0;
-          for (int c = 0; c < NFN; ++c) l += T.PL[(f * NG + g) * NFN + c] * dz[f * NFN + c][i];
-          lift[f] = l;
-        }
-        for (int k = 0; k < D; ++k) {
-          double s = 0.0;
-          for (int r = 0; r < D; ++r) s += Jinv[r * D + k] * gr[r];
-          for (int f = 0; f < NF; ++f) {
-            const double* Gf = G + D * D + 1 + f * (D + 1);
-            s += Gf[k] * (Gf[D] / detJ) * lift[f];
-          }
-          q[i][k] = s;
-        }
-      }
-    }
+    volume_point_state<C>(g, T, z, dz, G, v, q);
     bad = !(v[M - 1] < 0.0);
     Dual<M> vd[M];
     for (int l = 0; l < M; ++l) {
@@ -177,9 +189,10 @@ __global__ void __launch_bounds__(128) k_pointwise(AssembleArgs a, DevTables T, 
     if (C::VISC) {
       // dG/dq contracted with the rows of Jinv (G is linear in q)
       const ViscFactors<D> vf = visc_factors<D>(v);
+      const PhysParams pv = visc_params_at(ph, v[M - 1]);
 #pragma unroll 1
       for (int r = 0; r < D; ++r)
-        visc_jac_dir<D>(vf, Jinv + r * D, ph, [&](int i, int l, int k, double val) {
+        visc_jac_dir<D>(vf, Jinv + r * D, pv, [&](int i, int l, int k, double val) {
           put(T2, ((r * M + i) * M + l) * D + k, -W * val);
         });
     }
@@ -243,7 +256,7 @@ __global__ void __launch_bounds__(128) k_pointwise(AssembleArgs a, DevTables T, 
       for (int j = 1; j < D; ++j) s = s + Fh[i][j] * n[j];
       hA[i] = 0.5 * s + 0.5 * (lam * duh[i]);
     }
-    if (C::VISC) {
+    if (C::VISC && ph.gflux != 1) {  // ghat = G(vhat, q) . n (Eq. numericalFluxNS_2)
       Dual<M> Gh[M][D];
       visc_flux<D>(vhd, q, ph, Gh);
       for (int i = 0; i < M; ++i)
@@ -264,18 +277,28 @@ __global__ void __launch_bounds__(128) k_pointwise(AssembleArgs a, DevTables T, 
     OutT* U0 = HF + M;
     OutT* U1 = U0 + M * M;
     OutT* U2 = U1 + M * M;
+    Dual<M> gn[M];  // ghat = G(v, q) . n (Eq. numericalFluxNS_1): value and d/dv
+    for (int i = 0; i < M; ++i) gn[i] = vd[0] * 0.0;
+    if (C::VISC && ph.gflux == 1) {
+      Dual<M> Gv[M][D];
+      visc_flux<D>(vd, q, ph, Gv);
+      for (int i = 0; i < M; ++i)
+        for (int j = 0; j < D; ++j) gn[i] = gn[i] + Gv[i][j] * n[j];
+    }
     for (int i = 0; i < M; ++i) {
       Dual<M> s = Fv[i][0] * n[0];
       for (int j = 1; j < D; ++j) s = s + Fv[i][j] * n[j];
-      put(HF, i, Wf * (hA[i].v + 0.5 * s.v));
+      put(HF, i, Wf * (hA[i].v + 0.5 * s.v + gn[i].v));
       for (int l = 0; l < M; ++l) {
-        put(U0, i * M + l, Wf * (0.5 * s.d[l] + 0.5 * lam.v * uh[i].d[l]));
+        put(U0, i * M + l, Wf * (0.5 * s.d[l] + 0.5 * lam.v * uh[i].d[l] + gn[i].d[l]));
         put(U1, i * M + l, Wf * hA[i].d[l]);
       }
     }
-    if (C::VISC) {  // dG/dq contracted with the normal
-      const ViscFactors<D> vf = visc_factors<D>(vh);
-      visc_jac_dir<D>(vf, n, ph, [&](int i, int l, int k, double val) { put(U2, (i * M + l) * D + k, Wf * val); });
+    if (C::VISC) {  // dG/dq contracted with the normal, at the state the viscous flux uses
+      const double* vs = ph.gflux == 1 ? v : vh;
+      const ViscFactors<D> vf = visc_factors<D>(vs);
+      visc_jac_dir<D>(vf, n, visc_params_at(ph, vs[M - 1]),
+                      [&](int i, int l, int k, double val) { put(U2, (i * M + l) * D + k, Wf * val); });
     }
   }
   if (bad) atomicOr(a.status + e, HDG_STATUS_NONPHYSICAL);
@@ -649,6 +672,76 @@ __global__ void __launch_bounds__(256) k_condense(AssembleArgs a) {
   if (a.only_flag != 0 && tid == 0) {  // flagged-only pass: the block is now the FP64 form's
     atomicAnd(a.status + e, ~a.only_flag);
     atomicOr(a.status + e, HDG_STATUS_FP64);
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// k_entropy_terms: the two integrals of Eq. PiS (Sec. 5.6) from (v_h, q_h), one CTA per element:
+//   acc[0] += int_K rho s,  s = log(p / rho^gamma) (Sec. 2.3)
+//   acc[1] += (1/c_v) int_K (Phi / T + kappa |grad T|^2 / T^2),  Phi = grad V : tau
+// ------------------------------------------------------------------------------------
+template <class C>
+__global__ void __launch_bounds__(128) k_entropy_terms(AssembleArgs a, DevTables T, PhysParams ph, double* acc) {
+  constexpr int D = C::D, M = C::M, NP = C::NP, NFN = C::NFN, NF = C::NF, NG = C::NG;
+  __shared__ double z[C::NZ][M];
+  __shared__ double G[C::GEO];
+  __shared__ double dz[NF * NFN][M];
+  __shared__ double red[2][4];
+  const int64_t e = a.e0 + blockIdx.x;
+  load_element<C>(a, e, z, G);
+  __syncthreads();
+  for (int t = threadIdx.x; t < NF * NFN * M; t += blockDim.x) {
+    const int fc = t / M, i = t % M;
+    dz[fc][i] = z[NP + fc][i] - z[T.fnodes[fc]][i];
+  }
+  __syncthreads();
+  double rs = 0.0, pr = 0.0;
+  for (int g = threadIdx.x; g < NG; g += blockDim.x) {
+    const double W = T.W[g] * G[D * D];
+    double v[M], q[M][D];
+    volume_point_state<C>(g, T, z, dz, G, v, q);
+    double rho, vel[D], p;
+    prim_of_v<D>(v, ph.gamma, rho, vel, p);
+    rs += W * rho * (::log(p) - ph.gamma * ::log(rho));
+    if (C::VISC) {
+      const double vm = v[M - 1], ivm = 1.0 / vm, Temp = -ivm / ph.cv;
+      const double fac = ph.mu_exp != 0.0 ? ::exp(-ph.mu_exp * ::log(ph.cv * (-vm))) : 1.0;
+      const double mu = ph.mu * fac, kappa = ph.kappa * fac;
+      double gV[D][D], gT2 = 0.0, div = 0.0;
+      for (int i = 0; i < D; ++i)
+        for (int j = 0; j < D; ++j) gV[i][j] = v[1 + i] * ivm * ivm * q[M - 1][j] - q[1 + i][j] * ivm;
+      for (int j = 0; j < D; ++j) {
+        const double gt = q[M - 1][j] * ivm * ivm / ph.cv;
+        gT2 += gt * gt;
+        div += gV[j][j];
+      }
+      double Phi = 0.0;
+      for (int i = 0; i < D; ++i)
+        for (int j = 0; j < D; ++j) {
+          const double tau = mu * (gV[i][j] + gV[j][i] - (i == j ? (2.0 / 3.0) * div : 0.0));
+          Phi += gV[i][j] * tau;
+        }
+      pr += W * (Phi / Temp + kappa * gT2 / (Temp * Temp)) / ph.cv;
+    }
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    rs += __shfl_xor_sync(0xffffffffu, rs, off);
+    pr += __shfl_xor_sync(0xffffffffu, pr, off);
+  }
+  const int warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    red[0][warp] = rs;
+    red[1][warp] = pr;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s0 = 0.0, s1 = 0.0;
+    for (int w = 0; w < nw; ++w) {
+      s0 += red[0][w];
+      s1 += red[1][w];
+    }
+    atomicAdd(acc, s0);
+    atomicAdd(acc + 1, s1);
   }
 }
 

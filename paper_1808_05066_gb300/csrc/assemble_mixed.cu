@@ -95,11 +95,11 @@ CondVariant make_cond_variant2() {
                      &k_condense_prep<C, kSlices, false>};
 }
 
-// tcgen05 products with TMEM accumulators: NB-column blocks, CPS CTAs per SM
-template <class C, int NB, int CPS>
+// tcgen05 products with TMEM accumulators, 32-column blocks, one CTA per SM
+template <class C>
 CondVariant make_cond_variant_t5() {
-  using Q = CondT5<C, kSlices, NB, CPS>;
-  return CondVariant{Q::NTH, Q::bytes, &k_condense_t5<C, kSlices, NB, CPS>, 1, &k_condense_prep<C, kSlices, true>};
+  using Q = CondT5<C, kSlices>;
+  return CondVariant{Q::NTH, Q::bytes, &k_condense_t5<C, kSlices>, 1, &k_condense_prep<C, kSlices, true>};
 }
 
 // Times `launch` once on the stream (the chunk's outputs are rewritten each time).
@@ -147,10 +147,9 @@ int run_mixed(hdg_ctx* ctx, const double* V, const double* Vhat, const double* h
   const AsmVariant variants[] = {make_variant<C, 2, 4>(), make_variant<C, 4, 4>(), make_variant<C, 2, 2>(),
                                  make_variant<C, 4, 2>()};
   constexpr int NVAR = 4;
-  const CondVariant cvariants[] = {make_cond_variant<C, 256>(),        make_cond_variant<C, 512>(),
-                                   make_cond_variant2<C>(),             make_cond_variant_t5<C, 32, 1>(),
-                                   make_cond_variant_t5<C, 16, 2>()};
-  constexpr int NCVAR = 5;
+  const CondVariant cvariants[] = {make_cond_variant<C, 256>(), make_cond_variant<C, 512>(), make_cond_variant2<C>(),
+                                   make_cond_variant_t5<C>()};
+  constexpr int NCVAR = 4;
   if (!ctx->attr_mixed) {  // per context, hence per device
     for (const AsmVariant& v : variants)
       if (int rc2 = v.set_attr()) return rc2;

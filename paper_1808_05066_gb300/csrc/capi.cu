@@ -105,11 +105,9 @@ int hdg_mesh_create(int dim, const int64_t n[3], const double lo[3], const doubl
     return HDG_ERR_INVALID_ARG;
   }
   *out = nullptr;
-  if (scheme != HDG_SCHEME_HDG) {
-    set_error(scheme == HDG_SCHEME_EDG || scheme == HDG_SCHEME_IEDG
-                  ? "hdg_mesh_create: the EDG / IEDG trace spaces are not built"
-                  : "hdg_mesh_create: unknown scheme");
-    return scheme == HDG_SCHEME_EDG || scheme == HDG_SCHEME_IEDG ? HDG_ERR_UNSUPPORTED : HDG_ERR_INVALID_ARG;
+  if (scheme != HDG_SCHEME_HDG && scheme != HDG_SCHEME_EDG && scheme != HDG_SCHEME_IEDG) {
+    set_error("hdg_mesh_create: unknown scheme");
+    return HDG_ERR_INVALID_ARG;
   }
   if (p_per_elem) {  // one degree per element: accepted when every element has degree p
     if (dim < 2 || dim > 3) {
@@ -132,6 +130,8 @@ int hdg_mesh_create(int dim, const int64_t n[3], const double lo[3], const doubl
     set_error("hdg_mesh_create: invalid mesh arguments (code " + std::to_string(rc) + ")");
     return HDG_ERR_INVALID_ARG;
   }
+  m->m.scheme = scheme;
+  if (scheme != HDG_SCHEME_HDG) hdg::build_edg(m->m);  // every face is interior: IEDG is EDG
   *out = m;
   return HDG_OK;
 }
@@ -158,7 +158,25 @@ int hdg_mesh_get_info(hdg_mesh_t mesh, hdg_mesh_info* out) {
   out->geo_stride = m.geo_stride;
   out->n_elem = m.E;
   out->n_faces = m.nFaces;
-  out->n_trace = m.nFaces * m.ref.Nf * (m.dim + 2);
+  out->scheme = m.scheme;
+  out->n_trace_nodes = m.scheme == HDG_SCHEME_HDG ? m.nFaces * m.ref.Nf : m.n_edg;
+  out->n_trace = out->n_trace_nodes * (m.dim + 2);
+  return HDG_OK;
+}
+
+int hdg_mesh_copy_trace_map(hdg_mesh_t mesh, int32_t* tnode) {
+  if (!mesh || !tnode) {
+    set_error("hdg_mesh_copy_trace_map: null argument");
+    return HDG_ERR_INVALID_ARG;
+  }
+  const hdg::Mesh& m = mesh->m;
+  const int nF = m.ref.nF, Nf = m.ref.Nf;
+  for (int64_t e = 0; e < m.E; ++e)
+    for (int f = 0; f < nF; ++f)
+      for (int c = 0; c < Nf; ++c) {
+        const int64_t i = (e * nF + f) * Nf + c;
+        tnode[i] = m.scheme == HDG_SCHEME_HDG ? m.face_of[e * nF + f] * Nf + m.fnode_map[i] : m.edg_index[i];
+      }
   return HDG_OK;
 }
 
@@ -181,7 +199,10 @@ int hdg_mesh_copy_coords(hdg_mesh_t mesh, double* xnode, double* xfnode, double*
   }
   const hdg::Mesh& m = mesh->m;
   if (xnode) std::memcpy(xnode, m.xnode.data(), sizeof(double) * m.xnode.size());
-  if (xfnode) std::memcpy(xfnode, m.xfnode.data(), sizeof(double) * m.xfnode.size());
+  if (xfnode) {
+    const std::vector<double>& x = m.scheme == HDG_SCHEME_HDG ? m.xfnode : m.xedg;
+    std::memcpy(xfnode, x.data(), sizeof(double) * x.size());
+  }
   if (geo) std::memcpy(geo, m.geo.data(), sizeof(double) * m.geo.size());
   return HDG_OK;
 }
@@ -192,7 +213,8 @@ int hdg_ctx_create(hdg_mesh_t mesh, const hdg_physics* phys, int device, hdg_ctx
     return HDG_ERR_INVALID_ARG;
   }
   *out = nullptr;
-  if (!(phys->gamma > 1.0) || !(phys->mach > 0.0) || phys->reynolds < 0.0 || !(phys->prandtl > 0.0)) {
+  if (!(phys->gamma > 1.0) || !(phys->mach > 0.0) || phys->reynolds < 0.0 || !(phys->prandtl > 0.0) ||
+      !(phys->mu_exponent >= 0.0 && phys->mu_exponent <= 4.0) || phys->visc_flux < 0 || phys->visc_flux > 2) {
     set_error("hdg_ctx_create: invalid physics parameters");
     return HDG_ERR_INVALID_ARG;
   }
@@ -217,6 +239,8 @@ int hdg_ctx_create(hdg_mesh_t mesh, const hdg_physics* phys, int device, hdg_ctx
   c->ph.cv = 1.0 / (g * (g - 1.0) * phys->mach * phys->mach);
   c->ph.mu = visc ? 1.0 / phys->reynolds : 0.0;
   c->ph.kappa = g * c->ph.cv * c->ph.mu / phys->prandtl;
+  c->ph.mu_exp = visc ? phys->mu_exponent : 0.0;
+  c->ph.gflux = phys->visc_flux == 1 ? 1 : 2;
   c->dim = m.dim;
   c->p = m.p;
   c->K = m.K;
@@ -231,14 +255,16 @@ int hdg_ctx_create(hdg_mesh_t mesh, const hdg_physics* phys, int device, hdg_ctx
   c->GEO = m.geo_stride;
   c->E = m.E;
   c->F = m.nFaces;
-  c->ntrace = m.nFaces * m.ref.Nf * c->M;
+  c->scheme = m.scheme == HDG_SCHEME_HDG ? 0 : 1;
+  c->n_tnodes = m.scheme == HDG_SCHEME_HDG ? m.nFaces * m.ref.Nf : m.n_edg;
+  c->ntrace = c->n_tnodes * c->M;
   if (const char* av = std::getenv("HDG_ASM_VARIANT")) {  // force a tile shape (tests)
     long v = std::strtol(av, nullptr, 10);
     if (v >= 0 && v < 4) c->asm_variant = c->face_variant = (int)v;
   }
   if (const char* cv = std::getenv("HDG_COND_VARIANT")) {  // force a condensation shape (tests)
     long v = std::strtol(cv, nullptr, 10);
-    if (v >= 0 && v < 5) c->cond_variant = (int)v;
+    if (v >= 0 && v < 4) c->cond_variant = (int)v;
   }
   if (const char* st = std::getenv("HDG_T5_STALL_FIRST_COPY")) c->t5_stall = std::strtol(st, nullptr, 10) != 0;
   if (const char* ch = std::getenv("HDG_ELEMENT_CHUNK")) {
@@ -265,9 +291,19 @@ int hdg_ctx_create(hdg_mesh_t mesh, const hdg_physics* phys, int device, hdg_ctx
   std::vector<int> tgidx(c->E * c->NF * c->NFN);
   for (int64_t e = 0; e < c->E; ++e)
     for (int f = 0; f < c->NF; ++f)
-      for (int cc = 0; cc < c->NFN; ++cc)
-        tgidx[(e * c->NF + f) * c->NFN + cc] =
-            m.face_of[e * c->NF + f] * c->NFN + m.fnode_map[(e * c->NF + f) * c->NFN + cc];
+      for (int cc = 0; cc < c->NFN; ++cc) {
+        const int64_t i = (e * c->NF + f) * c->NFN + cc;
+        tgidx[i] = c->scheme ? m.edg_index[i] : m.face_of[e * c->NF + f] * c->NFN + m.fnode_map[i];
+      }
+  // every local occurrence (e NF NFN + local face node) of each trace node, grouped by node (the
+  // EDG trace operator and its node-block preconditioner gather through it)
+  std::vector<int> tr_ptr(c->n_tnodes + 1, 0), tr_occ(tgidx.size());
+  for (int t : tgidx) ++tr_ptr[t + 1];
+  for (int64_t t = 0; t < c->n_tnodes; ++t) tr_ptr[t + 1] += tr_ptr[t];
+  {
+    std::vector<int> fill(tr_ptr.begin(), tr_ptr.end() - 1);
+    for (size_t i = 0; i < tgidx.size(); ++i) tr_occ[fill[tgidx[i]]++] = (int)i;
+  }
   std::vector<int> fs_elem(2 * c->F), fs_loc(2 * c->F * c->NFN);
   for (int64_t F = 0; F < c->F; ++F)
     for (int sd = 0; sd < 2; ++sd) {
@@ -282,7 +318,8 @@ int hdg_ctx_create(hdg_mesh_t mesh, const hdg_physics* phys, int device, hdg_ctx
     }
   int rc = HDG_OK;
   if ((rc = upload(&c->d_tab, tab)) || (rc = upload(&c->d_itab, itab)) || (rc = upload(&c->d_tgidx, tgidx)) ||
-      (rc = upload(&c->d_geo, m.geo)) || (rc = upload(&c->d_fs_elem, fs_elem)) || (rc = upload(&c->d_fs_loc, fs_loc))) {
+      (rc = upload(&c->d_geo, m.geo)) || (rc = upload(&c->d_fs_elem, fs_elem)) || (rc = upload(&c->d_fs_loc, fs_loc)) ||
+      (rc = upload(&c->d_tr_ptr, tr_ptr)) || (rc = upload(&c->d_tr_occ, tr_occ))) {
     hdg_ctx_destroy(c);
     return rc;
   }
@@ -307,7 +344,7 @@ void hdg_ctx_destroy(hdg_ctx_t c) {
   void* bufs[] = {c->d_tab, c->d_tab_df, c->d_itab, c->d_tgidx, c->d_geo, c->d_fs_elem, c->d_fs_loc, c->d_scr,
                   c->d_sw, c->d_pc, c->d_pcpiv, c->d_dense, c->d_dpiv, c->d_red, c->d_S,
                   c->d_g, c->d_recov, c->d_R, c->d_dV, c->d_dVh, c->d_status, c->d_hist, c->d_V0,
-                  c->d_Vh0, c->d_feat, c->d_pred, c->d_dirk};
+                  c->d_Vh0, c->d_feat, c->d_pred, c->d_dirk, c->d_ent, c->d_tr_ptr, c->d_tr_occ, c->d_pcn};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (c->h_red) cudaFreeHost(c->h_red);
@@ -462,6 +499,22 @@ int hdg_assemble_condense_host(hdg_ctx_t ctx, const double* V, const double* Vha
   if (rc) return rc;
   HDG_CK(cudaMemcpyAsync(g_host, ctx->d_g, sizeof(double) * ctx->E * ctx->NT, cudaMemcpyDeviceToHost, s));
   for (int b = 0; b < 2 && b < used; ++b) HDG_CK(cudaStreamWaitEvent(s, ctx->ev_copied[b], 0));
+  return HDG_OK;
+}
+
+int hdg_entropy_production(hdg_ctx_t ctx, const double* V, const double* Vhat, double* int_rho_s, double* production,
+                           void* stream) {
+  HDG_REQUIRE(ctx && V && Vhat && int_rho_s && production, "hdg_entropy_production: null argument");
+  DeviceGuard guard(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!ctx->d_ent) HDG_CK(cudaMalloc(&ctx->d_ent, 2 * sizeof(double)));
+  HDG_CK(cudaMemsetAsync(ctx->d_ent, 0, 2 * sizeof(double), s));
+  if (int rc = hdg::entropy_terms(ctx, V, Vhat, ctx->d_ent, s)) return rc;
+  double h[2];
+  HDG_CK(cudaMemcpyAsync(h, ctx->d_ent, sizeof(h), cudaMemcpyDeviceToHost, s));
+  HDG_CK(cudaStreamSynchronize(s));
+  *int_rho_s = h[0];
+  *production = h[1];
   return HDG_OK;
 }
 
@@ -681,6 +734,10 @@ int hdg_newton_step(hdg_ctx_t ctx, double* V, double* Vhat, const double* V_n, c
   // Learned (or element-local) start: the caller's guess (V0, Vhat0) is linearised once;
   // the network's trace (or Vhat0 itself) takes the place of the first global trace solve and
   // the interior follows from the element-local recovery dV = -y - X P (vhat_m - Vhat0).
+  if (ctx->scheme) {
+    set_error("hdg_newton_step: the learned warm start works on face traces (HDG) only");
+    return HDG_ERR_UNSUPPORTED;
+  }
   const hdg_warmstart& w = *warmstart;
   if (!ctx->d_S) {
     HDG_CK(cudaMalloc(&ctx->d_S, sizeof(double) * ctx->E * ctx->NT * ctx->NT));

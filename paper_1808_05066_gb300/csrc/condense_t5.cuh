@@ -27,7 +27,8 @@
 // diagonal d for tile mt at column (mt * OZS + d) * NB.
 //
 // One CTA of 256 threads per element, one CTA per SM (shared memory), 512 TMEM columns. Thread 0
-// issues the bulk copies (a ring of NSLOT stages, up to NSLOT jobs ahead) and the MMAs; all waits
+// issues the bulk copies (a ring of NSLOT stages of one k step x all slices, up to NSLOT - 1 jobs
+// ahead) and the MMAs; the FP32 inverse stays in shared memory for the GEMMs; all waits
 // are bounded: a wait that gives up sets HDG_STATUS_TIMEOUT, the kernel lets its own copies and
 // MMAs drain (with a bounded wait), frees its TMEM and returns.
 #pragma once
@@ -131,36 +132,33 @@ HDG_DEVI void umma_put_pair(unsigned char* blk, uint32_t blk_stride, uint32_t of
 // ---------------------------------------------------------------------------------------------
 // sizes and layout
 // ---------------------------------------------------------------------------------------------
-template <class C, int OZS, int NB_ = 32, int CPS_ = 1>
+template <class C, int OZS>
 struct CondT5 {
   static constexpr int NV = C::NV, NT = C::NT;
   static_assert(NV <= 128 && NT <= 256, "one 128-row tile of A', two of C'");
   static constexpr int KT = (NV + 15) / 16;            // k steps of 16 interior unknowns
   static constexpr int MTC = (NT + 127) / 128;         // 128-row tiles of C'
   static constexpr int NTILE = 1 + MTC;
-  static constexpr int NB = NB_;                       // right-hand sides per block
-  static constexpr int CPS = CPS_;                     // CTAs per SM
+  static constexpr int NB = 32;                        // right-hand sides per block
   static constexpr int OZR = 4;                        // slices of the second residual
-  static constexpr int NSLOT = CPS == 1 ? 18 : 6;      // one-slice stages of the A-operand ring
+  static constexpr int NSLOT = 3;                      // stages of the A-operand ring
   static constexpr int NTH = 256;
-  static constexpr uint32_t TILE = 128 * 16 * 2;      // one slice of one k step of one tile (a job)
+  static constexpr uint32_t TILE = 128 * 16 * 2;      // one slice of one k step of one tile
   static constexpr uint32_t BTILE = NB * 16 * 2;      // one slice of one k step of the X block
-  static constexpr int TMEM_COLS = CPS == 1 ? 512 : 256;
+  static constexpr int TMEM_COLS = 512;
   static_assert(MTC * OZS * NB <= TMEM_COLS, "Schur accumulators fit in TMEM");
   // per element: [tile][k step][slice][TILE]
   static constexpr size_t slice_bytes = (size_t)NTILE * KT * OZS * TILE;
   static constexpr int LDA = (NV + 3) / 4 * 4;
-  // jobs (one slice of one k step of one tile) of one block: r0 (A', KT x OZS), r1 (A', KT x OZR),
-  // S (C' tiles, KT x MTC x OZS)
-  static constexpr int NJOB = KT * (OZS + OZR + MTC * OZS);
+  // jobs of one block: r0 (A', KT steps, OZS slices), r1 (A', KT, OZR), S (C' tiles, KT x MTC, OZS)
+  static constexpr int NJOB = KT * (2 + MTC);
   // shared memory
-  static constexpr size_t a_bytes = (size_t)NSLOT * TILE;
+  static constexpr size_t a_bytes = (size_t)NSLOT * OZS * TILE;
   static constexpr size_t b_bytes = (size_t)KT * OZS * BTILE;
   static constexpr size_t ai_bytes = sizeof(float) * NV * LDA;  // the FP32 inverse, read by every GEMM
   static constexpr size_t bytes = a_bytes + b_bytes + sizeof(df2) * NV * NB + sizeof(float) * 2 * NV * NB +
                                   ai_bytes + sizeof(float) * 128 + sizeof(int) * (128 + 128 * MTC + NB) +
                                   sizeof(uint64_t) * (2 * NSLOT + 1) + 64;
-  static_assert(CPS == 1 || bytes <= 113 * 1024, "two CTAs per SM");
 };
 
 // The prep kernel's slices of A' P (tile 0) and C' P (tiles 1, 2) in the tcgen05 operand layout,
@@ -201,9 +199,9 @@ HDG_DEVI void prep_write_umma_slices(const AssembleArgs& a, int64_t le, const df
 // ---------------------------------------------------------------------------------------------
 // k_condense_t5
 // ---------------------------------------------------------------------------------------------
-template <class C, int OZS, int NB_, int CPS>
-__global__ void __launch_bounds__(256, CPS) k_condense_t5(AssembleArgs a) {
-  using Q = CondT5<C, OZS, NB_, CPS>;
+template <class C, int OZS>
+__global__ void __launch_bounds__(256, 1) k_condense_t5(AssembleArgs a) {
+  using Q = CondT5<C, OZS>;
   using P = CondTC<C, 256, OZS>;  // the prep block (Ai, sc, exponents)
   constexpr int NV = C::NV, NT = C::NT, KT = Q::KT, MTC = Q::MTC, NB = Q::NB, OZR = Q::OZR;
   constexpr int NSLOT = Q::NSLOT, NTH = Q::NTH, NWARP = NTH / 32, LDA = Q::LDA;
@@ -273,20 +271,19 @@ __global__ void __launch_bounds__(256, CPS) k_condense_t5(AssembleArgs a) {
   const int njobs = nblk * Q::NJOB;
   int next_load = 0, issued = 0;  // thread 0 only
   uint32_t acc_phase = 0;         // uniform
-  // job J of the stream: one slice s of one k step kt of one tile (see NJOB)
-  auto job_src = [&](int J) {
+  auto job_src = [&](int J, uint32_t* bytes) {
     const int j = J % Q::NJOB;
-    int tile, kt, sl;
-    if (j < KT * OZS) {
-      tile = 0, kt = j / OZS, sl = j % OZS;
-    } else if (j < KT * (OZS + OZR)) {
-      const int u = j - KT * OZS;
-      tile = 0, kt = u / OZR, sl = u % OZR;
+    int tile, kt, nsl;
+    if (j < KT) {
+      tile = 0, kt = j, nsl = OZS;
+    } else if (j < 2 * KT) {
+      tile = 0, kt = j - KT, nsl = OZR;
     } else {
-      const int u = j - KT * (OZS + OZR);
-      kt = u / (MTC * OZS), tile = 1 + (u / OZS) % MTC, sl = u % OZS;
+      const int u = j - 2 * KT;
+      tile = 1 + u % MTC, kt = u / MTC, nsl = OZS;
     }
-    return slices + ((size_t)(tile * KT + kt) * OZS + sl) * TILE;
+    *bytes = nsl * TILE;
+    return slices + ((size_t)(tile * KT + kt) * OZS) * TILE;
   };
   // thread 0: loads jobs ahead of the MMAs, at most NSLOT - 2 past the last one issued, so that
   // a refill waits only for MMAs queued before the ones the tensor cores are working on
@@ -297,27 +294,28 @@ __global__ void __launch_bounds__(256, CPS) k_condense_t5(AssembleArgs a) {
         s_fail = 1;
         return;
       }
-      const unsigned char* src = job_src(next_load);
-      mbar_arrive_expect_tx(full + slot, TILE);
+      uint32_t bytes;
+      const unsigned char* src = job_src(next_load, &bytes);
+      mbar_arrive_expect_tx(full + slot, bytes);
       if (!(a.stall_first_copy && next_load == 0))  // the test hook leaves this phase incomplete
-        bulk_g2s(As + (size_t)slot * TILE, src, TILE, full + slot);
+        bulk_g2s(As + (size_t)slot * OZS * TILE, src, bytes, full + slot);
       ++next_load;
     }
   };
-  // thread 0: waits for job J (slice sl of the A operand at k step kt) and issues its products
-  // with the B slices t < nsl - sl into the accumulators of the tile (columns acc0 + (sl + t) NB)
-  auto issue = [&](int J, int sl, int nsl, uint32_t acc0, int kt) {
+  // thread 0: waits for job J's operands and issues its slice products into the accumulators
+  // of `tile` (columns acc0 + d NB); npair products with s + t < nsl
+  auto issue = [&](int J, int nsl, uint32_t acc0, int kt) {
     const int slot = J % NSLOT;
     if (s_fail || !mbar_wait(full + slot, (J / NSLOT) & 1, WAIT)) {
       s_fail = 1;
       return;
     }
     tc_fence_after();
-    const uint64_t ad = umma_desc(smem_u32(As + (size_t)slot * TILE), 128, 256);
-    const uint32_t bbase = smem_u32(Bs + (size_t)kt * OZS * BTILE);
-    for (int t = 0; sl + t < nsl; ++t)
-      umma_bf16(tmem + acc0 + (uint32_t)((sl + t) * NB), ad, umma_desc(bbase + t * BTILE, 128, 256), IDESC,
-                (kt > 0 || sl > 0) ? 1u : 0u);
+    const uint32_t abase = smem_u32(As + (size_t)slot * OZS * TILE), bbase = smem_u32(Bs + (size_t)kt * OZS * BTILE);
+    for (int s = 0; s < nsl; ++s)
+      for (int t = 0; s + t < nsl; ++t)
+        umma_bf16(tmem + acc0 + (uint32_t)((s + t) * NB), umma_desc(abase + s * TILE, 128, 256),
+                  umma_desc(bbase + t * BTILE, 128, 256), IDESC, (kt > 0 || s > 0) ? 1u : 0u);
     umma_commit(empty + slot);
     ++issued;
     produce();
@@ -346,14 +344,13 @@ __global__ void __launch_bounds__(256, CPS) k_condense_t5(AssembleArgs a) {
     return r;
   };
   // epilogue over one tile's accumulators: f(row in tile, column, value without scales); warp w
-  // takes TMEM lanes 32 (w % 4).. and columns (NB / 2)(w / 4)..+NB/2 of the block
-  static_assert(NB % 16 == 0, "two column halves of whole 8-column loads");
+  // takes TMEM lanes 32 (w % 4).. and columns 16 (w / 4)..+16 of the block
   auto epilogue = [&](uint32_t acc0, int nacc, auto f) {
     const int q = warp & 3, ch = warp >> 2;
     const int row = 32 * q + lane;
 #pragma unroll 1
-    for (int c8 = 0; c8 < NB / 16; ++c8) {
-      const int col0 = (NB / 2) * ch + 8 * c8;
+    for (int c8 = 0; c8 < 2; ++c8) {
+      const int col0 = 16 * ch + 8 * c8;
       float v[OZS][8];
 #pragma unroll
       for (int d = 0; d < OZS; ++d) {
@@ -430,8 +427,7 @@ __global__ void __launch_bounds__(256, CPS) k_condense_t5(AssembleArgs a) {
     // r0 = B - A' X0
     if (tid == 0) {
       tc_fence_after();
-      for (int kt = 0; kt < KT; ++kt)
-        for (int sl = 0; sl < OZS; ++sl) issue(J0 + kt * OZS + sl, sl, OZS, 0, kt);
+      for (int kt = 0; kt < KT; ++kt) issue(J0 + kt, OZS, 0, kt);
     }
     acc_ready();
     if (s_fail) break;
@@ -478,8 +474,7 @@ __global__ void __launch_bounds__(256, CPS) k_condense_t5(AssembleArgs a) {
     __syncthreads();
     if (tid == 0) {
       tc_fence_after();
-      for (int kt = 0; kt < KT; ++kt)
-        for (int sl = 0; sl < OZR; ++sl) issue(J0 + KT * OZS + kt * OZR + sl, sl, OZR, 0, kt);
+      for (int kt = 0; kt < KT; ++kt) issue(J0 + KT + kt, OZR, 0, kt);
     }
     acc_ready();
     if (s_fail) break;
@@ -537,9 +532,7 @@ __global__ void __launch_bounds__(256, CPS) k_condense_t5(AssembleArgs a) {
     if (tid == 0) {
       tc_fence_after();
       for (int kt = 0; kt < KT; ++kt)
-        for (int mt = 0; mt < MTC; ++mt)
-          for (int sl = 0; sl < OZS; ++sl)
-            issue(J0 + KT * (OZS + OZR) + (kt * MTC + mt) * OZS + sl, sl, OZS, (uint32_t)(mt * OZS * NB), kt);
+        for (int mt = 0; mt < MTC; ++mt) issue(J0 + 2 * KT + kt * MTC + mt, OZS, (uint32_t)(mt * OZS * NB), kt);
     }
     acc_ready();
     if (s_fail) break;

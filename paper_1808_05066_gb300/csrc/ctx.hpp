@@ -21,6 +21,11 @@ struct hdg_ctx {
   bool visc = false;
   int dim = 0, p = 0, K = 0, M = 0, NP = 0, NFN = 0, NF = 0, NG = 0, NGF = 0, NV = 0, NT = 0, GEO = 0;
   int64_t E = 0, F = 0, ntrace = 0;
+  int scheme = 0;            // 0: HDG (trace per face), 1: EDG (continuous trace, Sec. 3.4)
+  int64_t n_tnodes = 0;      // trace nodes: F NFN (HDG) or skeleton nodes (EDG)
+  int* d_tr_ptr = nullptr;   // [n_tnodes + 1] CSR of the local occurrences of each trace node
+  int* d_tr_occ = nullptr;   // [E NF NFN] local occurrence e NF NFN + f NFN + c
+  double* d_pcn = nullptr;   // EDG preconditioner: inverse node blocks [n_tnodes][M][M]
   // device tables
   double* d_tab = nullptr;
   size_t tab_size = 0;       // doubles in d_tab
@@ -86,6 +91,7 @@ struct hdg_ctx {
   // fallback of a failed warm start), MLP features and prediction
   double *d_hist = nullptr, *d_V0 = nullptr, *d_Vh0 = nullptr;
   double* d_dirk = nullptr;  // DIRK(3,3): (u_n, w), stage (u_i, w), weak stage derivatives k_1, k_2
+  double* d_ent = nullptr;   // the two integrals of hdg_entropy_production
   float *d_feat = nullptr, *d_pred = nullptr;
   int64_t feat_cap = 0;
   // mixed form: refinement tolerance of the condensation's status bit and the FP64
@@ -159,6 +165,8 @@ int assemble_condense_mixed(hdg_ctx* ctx, const double* V, const double* Vhat, c
                             double mass_coef, double* S, double* g, double* recov, double* R, int32_t* status,
                             cudaStream_t s);
 bool config_supported(int dim, int p, int K, bool visc);
+// int rho s and the physical entropy production of Eq. PiS added into acc[0], acc[1]
+int entropy_terms(hdg_ctx* ctx, const double* V, const double* Vhat, double* acc, cudaStream_t s);
 
 // trace-space and element helpers (trace.cu)
 int launch_prim_to_entropy(hdg_ctx* ctx, const double* prim, int64_t n, double* v, cudaStream_t s);

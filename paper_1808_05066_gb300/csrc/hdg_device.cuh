@@ -42,6 +42,8 @@ struct Cfg {
 
 struct PhysParams {
   double gamma, cv, mu, kappa;
+  double mu_exp;  // power law mu = mu (T / T_inf)^mu_exp, kappa likewise (T_inf = 1); 0: constant
+  int gflux;      // viscous numerical flux: 2 = G(vhat, q) . n, 1 = G(v, q) . n
 };
 
 // Constant reference tables (device pointers into one buffer).
@@ -293,9 +295,13 @@ HDG_DEVI void du_of_v(const T* v, const T* dv, double gamma, T* du) {
 // grad V_i = -grad w_i / v_m + w_i grad v_m / v_m^2 and grad T = grad v_m / (c_v v_m^2).
 template <int D, class T, class TQ>
 HDG_DEVI void visc_flux(const T* v, const TQ (*q)[D], const PhysParams& ph, T (*G)[D]) {
+  using ::exp;
+  using ::log;
   const T& vm = v[D + 1];
   T ivm = 1.0 / vm;
   T ivm2 = ivm * ivm;
+  // (T / T_inf)^omega with T = 1 / (c_v (-v_m)): scales mu and kappa (Pr fixed)
+  const T fac = ph.mu_exp != 0.0 ? exp(-ph.mu_exp * log(ph.cv * (-vm))) : vm * 0.0 + 1.0;
   T vel[D];
 #pragma unroll
   for (int i = 0; i < D; ++i) vel[i] = -(v[1 + i] * ivm);
@@ -314,7 +320,7 @@ HDG_DEVI void visc_flux(const T* v, const TQ (*q)[D], const PhysParams& ph, T (*
     for (int j = 0; j < D; ++j) {
       T t = gV[i][j] + gV[j][i];
       if (i == j) t = t - (2.0 / 3.0) * div;
-      tau[i][j] = ph.mu * t;
+      tau[i][j] = (ph.mu * fac) * t;
     }
 #pragma unroll
   for (int j = 0; j < D; ++j) {
@@ -322,11 +328,23 @@ HDG_DEVI void visc_flux(const T* v, const TQ (*q)[D], const PhysParams& ph, T (*
     T e = vel[0] * tau[0][j];
 #pragma unroll
     for (int i = 1; i < D; ++i) e = e + vel[i] * tau[i][j];
-    T gradT = (ph.kappa / ph.cv) * (q[D + 1][j] * ivm2);
+    T gradT = ((ph.kappa / ph.cv) * fac) * (q[D + 1][j] * ivm2);
 #pragma unroll
     for (int i = 0; i < D; ++i) G[1 + i][j] = -tau[i][j];
     G[D + 1][j] = -(e + gradT);
   }
+}
+
+// Physical parameters with mu and kappa at the temperature of state v (power law; constant
+// viscosity returns ph unchanged): the coefficients of dG/dq, which is linear in them.
+HDG_DEVI PhysParams visc_params_at(const PhysParams& ph, double vm) {
+  PhysParams p = ph;
+  if (ph.mu_exp != 0.0) {
+    const double fac = ::exp(-ph.mu_exp * ::log(ph.cv * (-vm)));
+    p.mu *= fac;
+    p.kappa *= fac;
+  }
+  return p;
 }
 
 // The state-dependent factors of the viscous flux, shared by every gradient direction.

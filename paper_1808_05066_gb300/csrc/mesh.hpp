@@ -34,9 +34,18 @@ struct Mesh {
   int geo_stride = 0;
   std::vector<double> xnode;       // [E][Np][dim] node coordinates
   std::vector<double> xfnode;      // [F][Nf][dim] canonical face-node coordinates (owner)
+  // EDG trace space (Sec. 3.4, E^E_h = all faces): one unknown per skeleton node, numbered in
+  // order of first appearance over (element, local face, face node); empty for HDG
+  int scheme = 0;                  // HDG_SCHEME_*
+  int64_t n_edg = 0;
+  std::vector<int32_t> edg_index;  // [E][nF][Nf] skeleton node of each local face node
+  std::vector<double> xedg;        // [n_edg][dim] node coordinates (first appearance)
 };
 
 // Returns 0 on success; -1 on invalid arguments.
 int build_mesh(int dim, const int64_t n[3], const double lo[3], const double hi[3], int p, int K, Mesh& m);
+// The continuous (EDG) numbering of the skeleton nodes of a built mesh: identifies the face
+// nodes of all elements by their integer coordinates modulo the period.
+void build_edg(Mesh& m);
 
 }  // namespace hdg

@@ -360,6 +360,10 @@ int hdg_mlp_features(hdg_ctx_t ctx, const double* V, const double* Vhat, const d
     set_error("hdg_mlp_features: null argument");
     return HDG_ERR_INVALID_ARG;
   }
+  if (ctx->scheme) {
+    set_error("hdg_mlp_features: the per-face network works on face traces (HDG) only");
+    return HDG_ERR_UNSUPPORTED;
+  }
   k_mlp_features<<<nb(ctx->ntrace), 256, 0, (cudaStream_t)stream>>>(
       V, Vhat, dvh1, dvh2, ctx->d_fs_elem, ctx->d_fs_loc, ctx->T.fnodes, ctx->F, ctx->NFN, ctx->M, ctx->NP, ctx->NF,
       mean, stdv, feat);
@@ -460,6 +464,10 @@ int hdg_mlp_apply_trace(hdg_ctx_t ctx, const double* Vhat, const double* dvh1, c
   if (!ctx || !Vhat || !dvh1 || !pred || !tmean || !tscale || !Vhat_out) {
     set_error("hdg_mlp_apply_trace: null argument");
     return HDG_ERR_INVALID_ARG;
+  }
+  if (ctx->scheme) {
+    set_error("hdg_mlp_apply_trace: the per-face network works on face traces (HDG) only");
+    return HDG_ERR_UNSUPPORTED;
   }
   k_mlp_apply<<<nb(ctx->ntrace), 256, 0, (cudaStream_t)stream>>>(Vhat, dvh1, pred, tscale, tmean, ctx->F,
                                                                  ctx->NFN * ctx->M, Vhat_out);

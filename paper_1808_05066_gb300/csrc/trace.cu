@@ -118,6 +118,20 @@ __global__ void k_trace_gather(const int* fs_elem, const int* fs_loc, int64_t F,
   }
 }
 
+// EDG (continuous trace): out[t][i] = scale * sum over the local occurrences o of node t of
+// ge[o * M + i], o = e NF NFN + f NFN + c (CSR ptr / occ)
+__global__ void k_node_gather(const int* ptr, const int* occ, int64_t nnode, int M, const double* ge, double scale,
+                              double* out) {
+  const int64_t n = nnode * M;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t node = t / M;
+    const int i = (int)(t % M);
+    double s = 0.0;
+    for (int o = ptr[node]; o < ptr[node + 1]; ++o) s += ge[(int64_t)occ[o] * M + i];
+    out[t] = scale * s;
+  }
+}
+
 // w_e = S_e x_e, one warp per row, x_e gathered into shared memory.
 __global__ void k_elem_matvec(const double* S, const double* x, const int* tgidx, int NT, int M, double* w) {
   extern __shared__ double xs[];
@@ -183,6 +197,27 @@ __global__ void k_sumsq_trace_residual(const double* R, const int* fs_elem, cons
       int64_t e = fs_elem[2 * Fi + side];
       int loc = fs_loc[(2 * Fi + side) * NFN + c];
       v += R[e * (int64_t)(NV + NT) + NV + loc * M + i];
+    }
+    s += v * v;
+  }
+  s = block_sum(s);
+  if (threadIdx.x == 0) atomicAdd(out, s);
+}
+
+// EDG: sum of squares of the assembled trace residual sum_e P_e^T R_t,e
+__global__ void k_sumsq_node_residual(const double* R, const int* ptr, const int* occ, int64_t nnode, int M, int NV,
+                                      int NT, double* out) {
+  const int nfc = NT / M;
+  double s = 0.0;
+  const int64_t n = nnode * M;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t node = t / M;
+    const int i = (int)(t % M);
+    double v = 0.0;
+    for (int o = ptr[node]; o < ptr[node + 1]; ++o) {
+      const int64_t e = occ[o] / nfc;
+      const int fc = occ[o] % nfc;
+      v += R[e * (int64_t)(NV + NT) + NV + fc * M + i];
     }
     s += v * v;
   }
@@ -335,6 +370,64 @@ __global__ void k_face_block_solve(const double* fac, const int* piv, int64_t F,
   for (int t = lane; t < B; t += 32) z[Fi * B + t] = x[t];
 }
 
+// ---------------------------------------------------------------- EDG node-block Jacobi
+// K_tt (M x M) = sum over pairs of local occurrences (e, fc), (e, fc') of node t in the same
+// element of S_e[fc M + i][fc' M + j]; inverted by Gauss-Jordan with partial pivoting. One thread
+// per node (M <= 5).
+__global__ void k_node_block_factor(const double* S, const int* ptr, const int* occ, int64_t nnode, int M, int NT,
+                                    double* binv) {
+  const int nfc = NT / M;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nnode; t += (int64_t)gridDim.x * blockDim.x) {
+    double A[5][10];
+    for (int i = 0; i < M; ++i)
+      for (int j = 0; j < 2 * M; ++j) A[i][j] = (j == M + i) ? 1.0 : 0.0;
+    for (int o1 = ptr[t]; o1 < ptr[t + 1]; ++o1) {
+      const int64_t e = occ[o1] / nfc;
+      const int f1 = occ[o1] % nfc;
+      const double* Se = S + e * (int64_t)NT * NT;
+      for (int o2 = ptr[t]; o2 < ptr[t + 1]; ++o2) {
+        if (occ[o2] / nfc != e) continue;
+        const int f2 = occ[o2] % nfc;
+        for (int i = 0; i < M; ++i)
+          for (int j = 0; j < M; ++j) A[i][j] += Se[(int64_t)(f1 * M + i) * NT + f2 * M + j];
+      }
+    }
+    for (int k = 0; k < M; ++k) {
+      int p = k;
+      for (int r = k + 1; r < M; ++r)
+        if (fabs(A[r][k]) > fabs(A[p][k])) p = r;
+      if (p != k)
+        for (int j = 0; j < 2 * M; ++j) {
+          const double tmp = A[k][j];
+          A[k][j] = A[p][j];
+          A[p][j] = tmp;
+        }
+      const double d = A[k][k];
+      const double inv = d != 0.0 ? 1.0 / d : 0.0;
+      for (int j = 0; j < 2 * M; ++j) A[k][j] *= inv;
+      for (int r = 0; r < M; ++r) {
+        if (r == k) continue;
+        const double f = A[r][k];
+        for (int j = 0; j < 2 * M; ++j) A[r][j] -= f * A[k][j];
+      }
+    }
+    for (int i = 0; i < M; ++i)
+      for (int j = 0; j < M; ++j) binv[(t * M + i) * M + j] = A[i][M + j];
+  }
+}
+
+// z_t = K_tt^{-1} r_t for every node (z and r distinct)
+__global__ void k_node_block_apply(const double* binv, int64_t nnode, int M, const double* r, double* z) {
+  const int64_t n = nnode * M;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t node = t / M;
+    const int i = (int)(t % M);
+    double s = 0.0;
+    for (int j = 0; j < M; ++j) s += binv[(node * M + i) * M + j] * r[node * M + j];
+    z[t] = s;
+  }
+}
+
 // ---------------------------------------------------------------- dense direct solver
 __global__ void k_dense_scatter(const double* S, const int* tgidx, int64_t E, int NT, int M, int64_t n, double* K) {
   const int nfc = NT / M;
@@ -451,16 +544,24 @@ int launch_history(hdg_ctx* ctx, const double* V0, const double* V1, double c0, 
 }
 
 int launch_trace_rhs(hdg_ctx* ctx, const double* g, double* rhs, cudaStream_t s) {
-  k_trace_gather<<<nblocks(ctx->ntrace), kThreads, 0, s>>>(ctx->d_fs_elem, ctx->d_fs_loc, ctx->F, ctx->NFN, ctx->M,
-                                                          ctx->NT, g, -1.0, rhs);
+  if (ctx->scheme)
+    k_node_gather<<<nblocks(ctx->ntrace), kThreads, 0, s>>>(ctx->d_tr_ptr, ctx->d_tr_occ, ctx->n_tnodes, ctx->M, g,
+                                                           -1.0, rhs);
+  else
+    k_trace_gather<<<nblocks(ctx->ntrace), kThreads, 0, s>>>(ctx->d_fs_elem, ctx->d_fs_loc, ctx->F, ctx->NFN, ctx->M,
+                                                            ctx->NT, g, -1.0, rhs);
   HDG_CK(cudaGetLastError());
   return HDG_OK;
 }
 
 int launch_trace_matvec(hdg_ctx* ctx, const double* S, const double* x, double* y, double* work, cudaStream_t s) {
   k_elem_matvec<<<(unsigned)ctx->E, 256, sizeof(double) * ctx->NT, s>>>(S, x, ctx->d_tgidx, ctx->NT, ctx->M, work);
-  k_trace_gather<<<nblocks(ctx->ntrace), kThreads, 0, s>>>(ctx->d_fs_elem, ctx->d_fs_loc, ctx->F, ctx->NFN, ctx->M,
-                                                          ctx->NT, work, 1.0, y);
+  if (ctx->scheme)
+    k_node_gather<<<nblocks(ctx->ntrace), kThreads, 0, s>>>(ctx->d_tr_ptr, ctx->d_tr_occ, ctx->n_tnodes, ctx->M, work,
+                                                           1.0, y);
+  else
+    k_trace_gather<<<nblocks(ctx->ntrace), kThreads, 0, s>>>(ctx->d_fs_elem, ctx->d_fs_loc, ctx->F, ctx->NFN, ctx->M,
+                                                            ctx->NT, work, 1.0, y);
   HDG_CK(cudaGetLastError());
   return HDG_OK;
 }
@@ -499,8 +600,12 @@ int residual_norm(hdg_ctx* ctx, const double* R, double* norm, cudaStream_t s) {
   HDG_CK(cudaMemsetAsync(ctx->d_red, 0, sizeof(double) * 2, s));
   k_sumsq_elem_rows<<<nblocks(ctx->E * (int64_t)ctx->NV), kThreads, 0, s>>>(R, ctx->E, ctx->NV + ctx->NT, ctx->NV,
                                                                            ctx->d_red);
-  k_sumsq_trace_residual<<<nblocks(ctx->ntrace), kThreads, 0, s>>>(R, ctx->d_fs_elem, ctx->d_fs_loc, ctx->F, ctx->NFN,
-                                                                  ctx->M, ctx->NV, ctx->NT, ctx->d_red + 1);
+  if (ctx->scheme)
+    k_sumsq_node_residual<<<nblocks(ctx->ntrace), kThreads, 0, s>>>(R, ctx->d_tr_ptr, ctx->d_tr_occ, ctx->n_tnodes,
+                                                                   ctx->M, ctx->NV, ctx->NT, ctx->d_red + 1);
+  else
+    k_sumsq_trace_residual<<<nblocks(ctx->ntrace), kThreads, 0, s>>>(R, ctx->d_fs_elem, ctx->d_fs_loc, ctx->F,
+                                                                    ctx->NFN, ctx->M, ctx->NV, ctx->NT, ctx->d_red + 1);
   HDG_CK(cudaGetLastError());
   HDG_CK(cudaMemcpyAsync(ctx->h_red, ctx->d_red, sizeof(double) * 2, cudaMemcpyDeviceToHost, s));
   HDG_CK(cudaStreamSynchronize(s));
@@ -593,7 +698,9 @@ static int gmres_solve(hdg_ctx* ctx, const double* S, const double* g, double* x
     HDG_CK(cudaMalloc(&ctx->d_sw, need));
     ctx->sw_bytes = need;
   }
-  if (!ctx->d_pc) {
+  if (ctx->scheme) {
+    if (!ctx->d_pcn) HDG_CK(cudaMalloc(&ctx->d_pcn, sizeof(double) * ctx->n_tnodes * ctx->M * ctx->M));
+  } else if (!ctx->d_pc) {
     HDG_CK(cudaMalloc(&ctx->d_pc, sizeof(double) * ctx->F * B * B));
     HDG_CK(cudaMalloc(&ctx->d_pcpiv, sizeof(int) * ctx->F * B));
   }
@@ -604,14 +711,22 @@ static int gmres_solve(hdg_ctx* ctx, const double* S, const double* g, double* x
   double* w = zt + n;
   double* b = w + n;
   double* ew = b + n;
-  k_face_block_factor<<<(unsigned)ctx->F, 64, sizeof(double) * B * B, s>>>(S, ctx->d_fs_elem, ctx->d_fs_loc, ctx->NFN,
-                                                                         ctx->M, ctx->NT, ctx->d_pc, ctx->d_pcpiv);
+  if (ctx->scheme)  // EDG: node-block Jacobi
+    k_node_block_factor<<<nblocks(ctx->n_tnodes), kThreads, 0, s>>>(S, ctx->d_tr_ptr, ctx->d_tr_occ, ctx->n_tnodes,
+                                                                    ctx->M, ctx->NT, ctx->d_pcn);
+  else  // HDG: face-block Jacobi
+    k_face_block_factor<<<(unsigned)ctx->F, 64, sizeof(double) * B * B, s>>>(S, ctx->d_fs_elem, ctx->d_fs_loc,
+                                                                           ctx->NFN, ctx->M, ctx->NT, ctx->d_pc,
+                                                                           ctx->d_pcpiv);
   rc = launch_trace_rhs(ctx, g, b, s);
   if (rc) return rc;
   const int wpb = 8;
   auto precond = [&](const double* r, double* z) {
-    k_face_block_solve<<<(unsigned)((ctx->F + wpb - 1) / wpb), 32 * wpb, sizeof(double) * wpb * B, s>>>(
-        ctx->d_pc, ctx->d_pcpiv, ctx->F, B, r, z);
+    if (ctx->scheme)
+      k_node_block_apply<<<nblocks(n), kThreads, 0, s>>>(ctx->d_pcn, ctx->n_tnodes, ctx->M, r, z);
+    else
+      k_face_block_solve<<<(unsigned)((ctx->F + wpb - 1) / wpb), 32 * wpb, sizeof(double) * wpb * B, s>>>(
+          ctx->d_pc, ctx->d_pcpiv, ctx->F, B, r, z);
   };
   auto dot_host = [&](const double* basis, int nb, const double* v, double* out) -> int {
     HDG_CK(cudaMemsetAsync(ctx->d_red, 0, sizeof(double) * nb, s));

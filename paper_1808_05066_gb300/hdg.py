@@ -47,6 +47,7 @@ EXPORTED = [
     "hdg_mlp_train_step", "hdg_mlp_apply_trace", "hdg_mlp_stats", "hdg_mlp_standardize", "hdg_mlp_target",
     "hdg_axpby", "hdg_assemble_condense_host", "hdg_assemble_condense_graph", "hdg_newton_solve",
     "hdg_ctx_set_refinement", "hdg_ctx_graph_replays", "hdg_ctx_set_trace_solver", "hdg_dirk3_step",
+    "hdg_entropy_production", "hdg_mesh_copy_trace_map",
 ]
 HDG_KERNEL_POINTWISE = 0
 HDG_KERNEL_ASSEMBLE = 1
@@ -68,7 +69,8 @@ class HdgError(RuntimeError):
 
 
 class hdg_physics(ctypes.Structure):
-    _fields_ = [("gamma", c_double), ("mach", c_double), ("reynolds", c_double), ("prandtl", c_double)]
+    _fields_ = [("gamma", c_double), ("mach", c_double), ("reynolds", c_double), ("prandtl", c_double),
+                ("mu_exponent", c_double), ("visc_flux", c_int32)]
 
 
 class hdg_warmstart(ctypes.Structure):
@@ -81,7 +83,8 @@ class hdg_mesh_info(ctypes.Structure):
     _fields_ = [("dim", c_int32), ("p", c_int32), ("quad_points", c_int32), ("m", c_int32),
                 ("Np", c_int32), ("Nf", c_int32), ("nF", c_int32), ("NG", c_int32), ("NGF", c_int32),
                 ("nv", c_int32), ("nt", c_int32), ("geo_stride", c_int32),
-                ("n_elem", c_int64), ("n_faces", c_int64), ("n_trace", c_int64)]
+                ("n_elem", c_int64), ("n_faces", c_int64), ("n_trace", c_int64),
+                ("scheme", c_int32), ("n_trace_nodes", c_int64)]
 
 
 def _load():
@@ -113,6 +116,8 @@ def _load():
         "hdg_ctx_set_refinement": (c_int, [P, c_double, c_int]),
         "hdg_ctx_graph_replays": (c_int, [P, POINTER(c_int64)]),
         "hdg_ctx_set_trace_solver": (c_int, [P, c_int, c_double, c_int]),
+        "hdg_entropy_production": (c_int, [P, P, P, POINTER(c_double), POINTER(c_double), P]),
+        "hdg_mesh_copy_trace_map": (c_int, [P, P]),
         "hdg_dirk3_step": (c_int, [P, P, P, P, c_double, c_int, c_double, c_int, POINTER(c_int), POINTER(c_double),
                                    POINTER(c_int), P]),
         "hdg_mlp_param_count": (c_int64, [c_int, c_int, c_int]),
@@ -202,17 +207,28 @@ def hdg_mesh_copy_topology(mesh):
     return face_of, fnode_map, face_side
 
 
+def hdg_mesh_copy_trace_map(mesh):
+    i = hdg_mesh_get_info(mesh)
+    tnode = np.zeros((i["n_elem"], i["nF"], i["Nf"]), np.int32)
+    _check(_lib.hdg_mesh_copy_trace_map(mesh, _ptr(tnode)))
+    return tnode
+
+
 def hdg_mesh_copy_coords(mesh):
+    """(xnode [E][Np][dim], trace-node coordinates ([F][Nf][dim] HDG, [N][dim] EDG), geo)."""
     i = hdg_mesh_get_info(mesh)
     xnode = np.zeros((i["n_elem"], i["Np"], i["dim"]))
-    xfnode = np.zeros((i["n_faces"], i["Nf"], i["dim"]))
+    if i["scheme"] == HDG_SCHEME_HDG:
+        xfnode = np.zeros((i["n_faces"], i["Nf"], i["dim"]))
+    else:
+        xfnode = np.zeros((i["n_trace_nodes"], i["dim"]))
     geo = np.zeros((i["n_elem"], i["geo_stride"]))
     _check(_lib.hdg_mesh_copy_coords(mesh, _ptr(xnode), _ptr(xfnode), _ptr(geo)))
     return xnode, xfnode, geo
 
 
-def hdg_ctx_create(mesh, gamma=1.4, mach=0.5, reynolds=0.0, prandtl=0.71, device=0):
-    ph = hdg_physics(gamma, mach, reynolds, prandtl)
+def hdg_ctx_create(mesh, gamma=1.4, mach=0.5, reynolds=0.0, prandtl=0.71, device=0, mu_exponent=0.0, visc_flux=2):
+    ph = hdg_physics(gamma, mach, reynolds, prandtl, mu_exponent, visc_flux)
     h = c_void_p()
     _check(_lib.hdg_ctx_create(mesh, byref(ph), device, byref(h)))
     return h.value
@@ -257,6 +273,13 @@ def hdg_assemble_condense_noalloc(ctx, V, Vhat, hist, mass_coef, S, g, recov, R,
     64 MiB device array); for callers that cannot allocate during the call."""
     _check(_lib.hdg_assemble_condense_noalloc(ctx, _ptr(V), _ptr(Vhat), _ptr(hist), mass_coef, _ptr(S), _ptr(g),
                                               _ptr(recov), _ptr(R), _ptr(elem_status), _stream(stream)))
+
+
+def hdg_entropy_production(ctx, V, Vhat, stream=None):
+    """(int rho s, physical entropy production) of Eq. PiS from (v_h, q_h)."""
+    a, b = c_double(), c_double()
+    _check(_lib.hdg_entropy_production(ctx, _ptr(V), _ptr(Vhat), byref(a), byref(b), _stream(stream)))
+    return a.value, b.value
 
 
 def hdg_trace_solve(ctx, S, g, dVhat, method=HDG_SOLVER_AUTO, rtol=1e-12, max_it=600, stream=None):
@@ -427,6 +450,9 @@ class Mesh:
     def topology(self):
         return hdg_mesh_copy_topology(self.handle)
 
+    def trace_map(self):
+        return hdg_mesh_copy_trace_map(self.handle)
+
     def coords(self):
         return hdg_mesh_copy_coords(self.handle)
 
@@ -440,9 +466,10 @@ class Mesh:
 class Context:
     """Owns an hdg_ctx_t bound to a Mesh (kept alive by this object)."""
 
-    def __init__(self, mesh: Mesh, gamma=1.4, mach=0.5, reynolds=0.0, prandtl=0.71, device=0):
+    def __init__(self, mesh: Mesh, gamma=1.4, mach=0.5, reynolds=0.0, prandtl=0.71, device=0, mu_exponent=0.0,
+                 visc_flux=2):
         self.mesh = mesh
-        self.handle = hdg_ctx_create(mesh.handle, gamma, mach, reynolds, prandtl, device)
+        self.handle = hdg_ctx_create(mesh.handle, gamma, mach, reynolds, prandtl, device, mu_exponent, visc_flux)
         self.device = device
 
     def close(self):

@@ -25,6 +25,9 @@ class Case:
     noise: float = 1e-3
     seed: int = 11
     mass_coef: float = 20.0
+    mu_exponent: float = 0.0   # power-law viscosity exponent (0: constant)
+    visc_flux: int = 2         # viscous numerical flux option (Eq. numericalFluxNS_1 / _2)
+    scheme: str = "hdg"        # trace space (Sec. 3.4): "hdg" or "edg"
 
     @property
     def lo(self):
@@ -50,8 +53,8 @@ def oracle_setup(case: Case):
     from oracle.hdg import Problem, consistent_Q, interpolate_state
     from oracle.mesh import Mesh
     mesh = Mesh(case.dim, case.n, 0.0, case.L, case.p)
-    phys = ph.Physics(mach=case.mach, reynolds=case.reynolds, prandtl=case.prandtl)
-    prob = Problem(mesh, phys)
+    phys = ph.Physics(mach=case.mach, reynolds=case.reynolds, prandtl=case.prandtl, mu_exponent=case.mu_exponent)
+    prob = Problem(mesh, phys, viscous_flux_option=case.visc_flux, scheme=case.scheme)
     V, Vh = interpolate_state(prob, case.prim)
     if case.noise:
         Vh = wl.perturb(Vh, case.noise, case.seed)
@@ -72,8 +75,10 @@ class GpuCase:
         import torch
         from paper_1808_05066_gb300 import hdg
         self.hdg, self.torch, self.case = hdg, torch, case
-        self.mesh = hdg.Mesh(case.dim, case.n, 0.0, case.L, case.p)
-        self.ctx = hdg.Context(self.mesh, 1.4, case.mach, case.reynolds, case.prandtl, device)
+        self.mesh = hdg.Mesh(case.dim, case.n, 0.0, case.L, case.p,
+                             scheme=hdg.HDG_SCHEME_EDG if case.scheme == "edg" else hdg.HDG_SCHEME_HDG)
+        self.ctx = hdg.Context(self.mesh, 1.4, case.mach, case.reynolds, case.prandtl, device,
+                               mu_exponent=case.mu_exponent, visc_flux=case.visc_flux)
         self.info = self.mesh.info
         xnode, xfnode, _ = self.mesh.coords()
         dev = torch.device("cuda", device)

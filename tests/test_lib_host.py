@@ -45,14 +45,31 @@ def test_invalid_arguments_are_rejected():
     assert ei.value.code == hdg.HDG_ERR_INVALID_ARG
 
 
-def test_unbuilt_variants_are_reported():
-    """The boundary's arguments for the EDG / IEDG trace spaces (Sec. 3.4) and for meshes of
-    mixed degree exist; those variants are not built and say so with HDG_ERR_UNSUPPORTED."""
+@pytest.mark.parametrize("dim,n,p", [(2, 3, 2), (2, 2, 4), (3, 2, 3), (3, 1, 2)])
+def test_edg_numbering_matches_oracle(dim, n, p):
+    """The C++ EDG / IEDG numbering of the skeleton nodes (Sec. 3.4) equals the oracle's, node for
+    node, and its size is the oracle's count (Table t:dofs)."""
+    from oracle.hdg import Problem
+    from oracle import physics as ph
     hdg = _lib()
+    o = OMesh(dim, n, 0.0, 2.0, p)
+    prob = Problem(o, ph.Physics(), scheme="edg")
     for scheme in (hdg.HDG_SCHEME_EDG, hdg.HDG_SCHEME_IEDG):
-        with pytest.raises(hdg.HdgError) as ei:
-            hdg.hdg_mesh_create(2, [2, 2], [0, 0], [1, 1], 2, scheme=scheme)
-        assert ei.value.code == hdg.HDG_ERR_UNSUPPORTED
+        m = hdg.Mesh(dim, n, 0.0, 2.0, p, scheme=scheme)
+        assert m.info["scheme"] == scheme and m.info["n_trace_nodes"] == prob.n_edg == o.trace_dof_edg()
+        assert m.info["n_trace"] == prob.n_trace
+        assert np.array_equal(m.trace_map(), prob.edg_index)
+        _, xt, _ = m.coords()
+        assert xt.shape == (prob.n_edg, dim)
+    # the HDG trace map is face * Nf + canonical node
+    h = hdg.Mesh(dim, n, 0.0, 2.0, p)
+    assert np.array_equal(h.trace_map(), o.face_of[:, :, None] * o.ref.Nf + o.fnode_map)
+
+
+def test_unbuilt_variants_are_reported():
+    """The boundary's argument for meshes of mixed degree exists; such meshes are not built and
+    say so with HDG_ERR_UNSUPPORTED."""
+    hdg = _lib()
     with pytest.raises(hdg.HdgError) as ei:
         hdg.hdg_mesh_create(2, [2, 2], [0, 0], [1, 1], 2, p_per_elem=np.array([2] * 7 + [3], np.int8))
     assert ei.value.code == hdg.HDG_ERR_UNSUPPORTED
@@ -88,3 +105,14 @@ def test_mesh_matches_oracle(dim, n, p):
     for F, sd in enumerate(o.face_elems):
         e, f = sd[0]
         assert np.allclose(xfnode[F], o.xnode[e, o.ref.face_nodes[f]], atol=1e-13)
+
+
+def test_physics_arguments_are_checked():
+    """Invalid physics (power-law exponent outside 0..4, unknown viscous-flux option) is rejected
+    before any device is touched."""
+    hdg = _lib()
+    m = hdg.Mesh(2, 2, 0.0, 1.0, 2)
+    for kw in (dict(mu_exponent=-0.5), dict(mu_exponent=9.0), dict(visc_flux=3)):
+        with pytest.raises(hdg.HdgError) as ei:
+            hdg.hdg_ctx_create(m.handle, 1.4, 0.3, 100.0, 0.72, 0, **kw)
+        assert ei.value.code == hdg.HDG_ERR_INVALID_ARG

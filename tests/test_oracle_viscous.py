@@ -28,9 +28,9 @@ from oracle.mesh import Mesh
 GAMMA = 1.4
 
 
-def _shear_problem(n, p, reynolds, mach, patch=None):
-    phys = ph.Physics(mach=mach, reynolds=reynolds, prandtl=0.71)
-    prob = Problem(Mesh(2, n, 0.0, 1.0, p), phys)
+def _shear_problem(n, p, reynolds, mach, patch=None, mu_exponent=0.0, flux_option=2):
+    phys = ph.Physics(mach=mach, reynolds=reynolds, prandtl=0.71, mu_exponent=mu_exponent)
+    prob = Problem(Mesh(2, n, 0.0, 1.0, p), phys, viscous_flux_option=flux_option)
     if patch is not None:
         patch(prob)
     return prob
@@ -43,14 +43,19 @@ def _shear_state(prob, x, t, eps, k, lam, p0):
     return ph.v_of_u(ph.u_of_primitives(rho, vel, np.full(x.shape[:-1], p0), GAMMA), GAMMA)
 
 
-def shear_wave(n, p, steps, order, dt, eps, reynolds=20.0, mach=0.3, patch=None):
-    """March the shear wave; returns (amplitude ratio a(t)/a(0), exp(-lam t), int H(t) - int H(0)
-    per step, closed-form entropy change per step)."""
-    prob = _shear_problem(n, p, reynolds, mach, patch)
+def shear_wave(n, p, steps, order, dt, eps, reynolds=20.0, mach=0.3, patch=None, T0=1.0, mu_exponent=0.0,
+               flux_option=2, prob_out=None):
+    """March the shear wave at uniform temperature T0 (rho = 1, p0 = T0 / (gamma M^2)); returns
+    (amplitude ratio a(t)/a(0), exp(-lam t), int H(t) - int H(0) per step, closed-form entropy
+    change per step), lam = mu(T0) k^2 with mu(T0) = mu_ref T0^omega."""
+    prob = _shear_problem(n, p, reynolds, mach, patch, mu_exponent, flux_option)
+    if prob_out is not None:
+        prob_out.append(prob)
     mesh = prob.mesh
     k = 2.0 * math.pi
-    lam = prob.phys.mu * k * k
-    p0 = 1.0 / (GAMMA * mach ** 2)
+    mu0 = prob.phys.mu * T0 ** mu_exponent
+    lam = mu0 * k * k
+    p0 = T0 / (GAMMA * mach ** 2)
     owner = np.array([s[0] for s in mesh.face_elems])
     fn = np.array(mesh.ref.face_nodes)
     V = _shear_state(prob, mesh.xnode, 0.0, eps, k, lam, p0)
@@ -72,15 +77,17 @@ def shear_wave(n, p, steps, order, dt, eps, reynolds=20.0, mach=0.3, patch=None)
     hist = [V, _shear_state(prob, mesh.xnode, -dt, eps, k, lam, p0)]   # exact V^{-1} for BDF2
     ratio, dH = [], []
     for _ in range(steps):
-        res = time_step(prob, Q, hist[0], Vh, hist, order, dt, tol=1e-12, max_it=8)
-        assert res.res_norms[-1] <= 1e-12 * max(1.0, res.res_norms[0])
+        # the residual's rounding floor grows with the pressure (T0): 5e-12 against entropy
+        # changes of ~1e-7 per step
+        res = time_step(prob, Q, hist[0], Vh, hist, order, dt, tol=5e-12, max_it=8)
+        assert res.res_norms[-1] <= 5e-12 * max(1.0, res.res_norms[0])
         hist = [res.V, hist[0]]
         Vh, Q = res.Vhat, res.Q
         ratio.append(amplitude(res.V) / a0)
         dH.append(prob.integrals(res.V)[1] - H0)
     t = dt * np.arange(1, steps + 1)
     # d/dt int H = -(mu / (c_v T0)) int (du/dy)^2, c_v T0 = p0 / (gamma - 1), int = eps^2 k^2 e^{-2 lam t} / 2
-    rate = prob.phys.mu * (GAMMA - 1.0) / p0 * eps ** 2 * k ** 2 / 2.0
+    rate = mu0 * (GAMMA - 1.0) / p0 * eps ** 2 * k ** 2 / 2.0
     dH_exact = -rate * (1.0 - np.exp(-2.0 * lam * t)) / (2.0 * lam)
     return np.array(ratio), np.exp(-lam * t), np.array(dH), dH_exact
 
