@@ -154,7 +154,10 @@ int hdg_ctx_set_refinement(hdg_ctx_t ctx, double tol, int fp64_fallback);
 
 /* Trace solver of the Newton iterations of hdg_newton_solve / hdg_newton_step: method as for
  * hdg_trace_solve (default HDG_SOLVER_AUTO), relative tolerance (default 1e-12) and iteration
- * limit (default 600). Errors: HDG_ERR_INVALID_ARG. */
+ * limit (default 600). rtol = 0 selects an inexact Newton method: each trace solve stops at the
+ * Eisenstat-Walker forcing term eta_k = 0.9 (|R_k|/|R_{k-1}|)^2 (safeguarded, at most 0.1, never
+ * tighter than the nonlinear tolerance still requires); the converged state meets the same
+ * Newton tolerance. Errors: HDG_ERR_INVALID_ARG (rtol outside [0, 1)). */
 int hdg_ctx_set_trace_solver(hdg_ctx_t ctx, int method, double rtol, int max_it);
 
 /* Entropy variables of Sec. 2.3, v = dH/du for H = -rho s: converts n_points primitive

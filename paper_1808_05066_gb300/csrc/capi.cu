@@ -567,7 +567,8 @@ int hdg_ctx_set_refinement(hdg_ctx_t ctx, double tol, int fp64_fallback) {
 }
 
 int hdg_ctx_set_trace_solver(hdg_ctx_t ctx, int method, double rtol, int max_it) {
-  HDG_REQUIRE(ctx && method >= HDG_SOLVER_AUTO && method <= HDG_SOLVER_DENSE && rtol > 0.0 && max_it > 0,
+  HDG_REQUIRE(ctx && method >= HDG_SOLVER_AUTO && method <= HDG_SOLVER_DENSE && rtol >= 0.0 && rtol < 1.0 &&
+                  max_it > 0,
               "hdg_ctx_set_trace_solver: invalid argument");
   ctx->newton_solver = method;
   ctx->newton_rtol = rtol;
@@ -648,7 +649,7 @@ int hdg_newton_solve(hdg_ctx_t ctx, double* V, double* Vhat, const double* hist,
   }
   if (!ctx->d_status) HDG_CK(cudaMalloc(&ctx->d_status, sizeof(int32_t) * E));
   std::vector<int32_t> hstat;
-  double r0 = -1.0, rn = 0.0;
+  double r0 = -1.0, rn = 0.0, r_prev = -1.0, eta = 0.1;
   *newton_iters = 0;
   if (trace_iters) *trace_iters = 0;
   for (int it = 0;; ++it) {
@@ -687,10 +688,26 @@ int hdg_newton_solve(hdg_ctx_t ctx, double* V, double* Vhat, const double* hist,
       set_error("hdg_newton_solve: Newton did not converge");
       return HDG_ERR_NOT_CONVERGED;
     }
+    // relative tolerance of the trace solve: fixed, or (newton_rtol == 0) the Eisenstat-Walker
+    // forcing term eta_k = 0.9 (|R_k| / |R_{k-1}|)^2, safeguarded by 0.9 eta_{k-1}^2 when that is
+    // above 0.1, at most 0.1, and no tighter than half the tolerance the residual still has to gain
+    double rtol = ctx->newton_rtol;
+    if (rtol == 0.0) {
+      if (r_prev > 0.0) {
+        const double ratio = rn / r_prev, safe = 0.9 * eta * eta;
+        eta = 0.9 * ratio * ratio;
+        if (safe > 0.1) eta = std::max(eta, safe);
+      }
+      eta = std::min(eta, 0.1);
+      eta = std::max(eta, 0.5 * tol * std::max(1.0, r0) / rn);
+      eta = std::max(eta, 1e-13);
+      rtol = eta;
+    }
+    r_prev = rn;
     int iters = 0;
     double fres = 0.0;
-    rc = hdg::trace_solve(ctx, ctx->d_S, ctx->d_g, ctx->d_dVh, ctx->newton_solver, ctx->newton_rtol,
-                          ctx->newton_max_it, &iters, &fres, s);
+    rc = hdg::trace_solve(ctx, ctx->d_S, ctx->d_g, ctx->d_dVh, ctx->newton_solver, rtol, ctx->newton_max_it, &iters,
+                          &fres, s);
     if (trace_iters) *trace_iters += iters;
     if (rc) return rc;
     rc = hdg::launch_recover(ctx, ctx->d_recov, ctx->d_dVh, ctx->d_dV, s);

@@ -364,6 +364,7 @@ def hdg_ctx_set_refinement(ctx, tol=1e-10, fp64_fallback=True):
 
 
 def hdg_ctx_set_trace_solver(ctx, method=HDG_SOLVER_AUTO, rtol=1e-12, max_it=600):
+    """rtol = 0: inexact Newton (Eisenstat-Walker forcing terms)."""
     _check(_lib.hdg_ctx_set_trace_solver(ctx, method, rtol, max_it))
 
 

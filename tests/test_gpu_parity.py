@@ -371,3 +371,28 @@ def test_dirk3_step_matches_oracle(name, precision):
     assert its == iters, (its, iters)
     assert rel_fro(V_gpu.cpu().numpy(), res.V) < 1e-10
     assert rel_fro(Vh_gpu.cpu().numpy(), res.Vhat) < 1e-10
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_inexact_newton_reaches_the_same_state(precision):
+    """The inexact Newton option (trace solves stopped at the Eisenstat-Walker forcing term)
+    reaches the same converged BDF2 state as the oracle's exact Newton solve, within the Newton
+    tolerance's reach, with fewer trace-solver iterations than solves to 1e-13."""
+    from oracle.hdg import time_step
+    case = CASES["ns2d_p3"]
+    gc = GpuCase(case)
+    prob, Q, V, Vh = oracle_setup(case)
+    dt = 0.05
+    res = time_step(prob, Q, V, Vh, [V, V * (1.0 + 1e-3)], 2, dt, tol=1e-12, max_it=12)
+    V_nm1 = (gc.V * (1.0 + 1e-3)).contiguous()
+    iters = {}
+    for rtol in (1e-13, 0.0):
+        gc.hdg.hdg_ctx_set_trace_solver(gc.ctx.handle, gc.hdg.HDG_SOLVER_GMRES, rtol, 3000)
+        V_gpu, Vh_gpu = gc.V.clone(), gc.Vhat.clone()
+        it, rn, rh, tr = gc.hdg.hdg_newton_step(gc.ctx.handle, V_gpu, Vh_gpu, gc.V, V_nm1, dt, 2, precision, 1e-12,
+                                                12, history=True)
+        assert rn <= 1e-12 * max(1.0, rh[0])
+        assert rel_fro(V_gpu.cpu().numpy(), res.V) < 1e-10
+        assert rel_fro(Vh_gpu.cpu().numpy(), res.Vhat) < 1e-10
+        iters[rtol] = tr
+    assert iters[0.0] < iters[1e-13], iters
