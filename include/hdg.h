@@ -89,7 +89,12 @@ typedef struct {
                          T_inf = 1 in this nondimensionalisation); 0 = constant viscosity; 0..4 */
   int32_t visc_flux;  /* viscous numerical flux: 0 or 2 = G(vhat, q) . n (Eq. numericalFluxNS_2, the
                          choice of Sec. 5), 1 = G(v, q) . n (Eq. numericalFluxNS_1) */
+  int32_t stabilization; /* stabilization matrix of Eq. numericalFlux at v* = vhat: HDG_STAB_SLF
+                            (0, lambda_max A0 of Eq. sLxF, the choice of Sec. 5) or HDG_STAB_S (1,
+                            |A_n| A0 of Eq. symStab with the absolute value of Sec. 4.1) */
 } hdg_physics;
+
+enum { HDG_STAB_SLF = 0, HDG_STAB_S = 1 };
 
 typedef struct {
   int32_t dim, p, quad_points; /* quad_points K per direction: exact to degree 2K-1 */

@@ -1,12 +1,22 @@
 """Oracle for the entropy-variable hybridized DG local problem and Newton step.
 
 Follows Sec. 3.2 (Euler, Eqs. hDG1-hDG2) and Sec. 3.3 (Navier-Stokes, Eqs.
-hDG_NS0-hDG_NS2) on periodic meshes (no boundary term), with
+hDG_NS0-hDG_NS2), with
   * inviscid flux Eq. numericalFlux, sigma = sigma_SLF of Eq. sLxF at v* = vhat
-    (the choice of Sec. 5),
+    (the choice of Sec. 5), or sigma_S of Eq. symStab at the same v* (Physics.stabilization),
   * viscous flux Eq. numericalFluxNS_2, G(vhat, q) . n (the choice of Sec. 5),
   * time term (d u(v_h)/dt, w) discretised by BDF: mass_coef (u(v_h), w) - hist,
-    hist = sum_j c_j (u(v_h^{n-j}), w) (BDF1 / BDF2; BDF0 = steady).
+    hist = sum_j c_j (u(v_h^{n-j}), w) (BDF1 / BDF2; BDF0 = steady),
+  * the boundary term <b_h(vhat, v), mu> of Eqs. hDG2 / hDG_NS2 on faces of the boundary
+    (the paper leaves b_h open, Sec. 3.2); two are defined:
+      BC_STATE  b_h = vhat - v_b: the trace takes a given boundary state v_b (the paper's
+                prescribed exact solutions, Secs. 5.1-5.2), v_b given by its values at the
+                face nodes (Problem.boundary_state [F, Nf, m]);
+      BC_SLIP   b_h = fhat(vhat, v; n) + fhat(vhat, R v; -n) (Euler only): the trace residual
+                of an interior face whose other side is the element's mirror image, R
+                reflecting the momentum components, w -> w - 2 (w . n) n; the converged state
+                is the restriction of the mirror-symmetric state on the doubled domain, and
+                no mass or energy crosses the wall.
 
 The local Newton system is the plain definition: the dense Jacobian of the local
 residuals R_l = (R_q, R_v) and of the element's trace residual R_t, taken by
@@ -29,7 +39,7 @@ import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
 from . import physics as ph
-from .mesh import Mesh
+from .mesh import BC_PERIODIC, BC_SLIP, BC_STATE, Mesh
 
 CSTEP = 1e-30
 
@@ -61,6 +71,12 @@ class Problem:
         self.mesh, self.phys = mesh, phys
         self.viscous_flux_option = viscous_flux_option
         self.scheme = "edg" if scheme == "iedg" else scheme
+        bounded = bool(np.any(mesh.face_bc != BC_PERIODIC))
+        if bounded and self.scheme != "hdg":
+            raise ValueError("boundaries are defined for the HDG trace space only")
+        if np.any(mesh.face_bc == BC_SLIP) and phys.viscous:
+            raise ValueError("the slip boundary is defined for the Euler equations only")
+        self.boundary_state = None      # [F, Nf, m] v_b at the canonical face nodes (BC_STATE faces)
         if self.scheme == "edg":
             self.n_edg, self.edg_index = mesh.edg_numbering()
         ref = mesh.ref
@@ -166,14 +182,26 @@ class Problem:
             vf = np.einsum("ga,bam->bgm", T.phif[f], V)
             vhf = np.einsum("gc,bcm->bgm", T.psi[f], Vh[:, f])
             n = T.nrm[f]
-            fh = ph.numerical_flux_inviscid(vhf, vf, n, g)
+            fh = ph.numerical_flux_inviscid(vhf, vf, n, g, self.phys.stabilization)
             if self.viscous:
                 qf = np.einsum("ga,bamk->bgmk", T.phif[f], Q)
                 fh = fh + self.face_viscous_flux(vhf, vf, qf, n)
                 Rq = Rq - np.einsum("g,ga,bgm,k->bamk", T.Wf[f], T.phif[f], vhf, n)
             Rv = Rv + np.einsum("g,ga,bgm->bam", T.Wf[f], T.phif[f], fh)
-            # Eq. hDG2 / hDG_NS2: element contribution <fhat + ghat, mu>
-            Rt[:, f] = np.einsum("g,gc,bgm->bcm", T.Wf[f], T.psi[f], fh)
+            F = self.mesh.face_of[e, f]
+            kind = self.mesh.face_bc[F]
+            if kind == BC_PERIODIC:
+                # Eq. hDG2 / hDG_NS2: element contribution <fhat + ghat, mu>
+                Rt[:, f] = np.einsum("g,gc,bgm->bcm", T.Wf[f], T.psi[f], fh)
+            elif kind == BC_STATE:          # <vhat - v_b, mu>
+                vb = self.boundary_state[F][self.mesh.fnode_map[e, f]]
+                vbf = T.psi[f] @ vb
+                Rt[:, f] = np.einsum("g,gc,bgm->bcm", T.Wf[f], T.psi[f], vhf - vbf)
+            elif kind == BC_SLIP:           # <fhat(vhat, v; n) + fhat(vhat, R v; -n), mu>
+                fm = ph.numerical_flux_inviscid(vhf, reflect(vf, n), -n, g, self.phys.stabilization)
+                Rt[:, f] = np.einsum("g,gc,bgm->bcm", T.Wf[f], T.psi[f], fh + fm)
+            else:
+                raise ValueError(kind)
         return Rq, Rv, Rt
 
     def _pack_l(self, Rq, Rv):
@@ -276,6 +304,14 @@ class Problem:
             tot_u += T.W @ u
             tot_H += T.W @ ph.entropy_H(u, self.phys.gamma)
         return tot_u, tot_H
+
+
+def reflect(v, n):
+    """The mirror image of the state v in the plane with unit normal n: w = (v_2..v_{d+1})
+    -> w - 2 (w . n) n (the velocity V = -w / v_m reflects), v_1 and v_m unchanged."""
+    w = v[..., 1:-1]
+    w = w - 2.0 * np.sum(w * n, axis=-1)[..., None] * n
+    return np.concatenate([v[..., :1], w, v[..., -1:]], axis=-1)
 
 
 def solve_equilibrated(A, B):

@@ -11,8 +11,13 @@ identical in every cell, which is conforming under periodic identification:
   negative vertices 1 and 2 are swapped; e = 6c + t.
 
 A face is the set of element vertices other than local vertex f. Faces are keyed by
-(min vertex mod n, offsets of the other two vertices), so periodic copies coincide
-even for n = 1. Global faces are numbered in order of first appearance over
+(min vertex mod n on periodic axes, offsets of the other two vertices), so periodic
+copies coincide even for n = 1.
+
+Boundaries (the term b_h of Eqs. hDG2 / hDG_NS2, Sec. 3.2): an axis is periodic (the
+default) or bounded on both sides; each side of a bounded axis carries a boundary type
+(BC_STATE or BC_SLIP, see oracle.hdg). A face with one side lies on such a side; it is
+owned by its element. Global faces are numbered in order of first appearance over
 (element, local face); the first element is the owner and its local face-node
 order is the face's canonical node order. Face nodes of the other element are
 matched by integer node coordinates (units h/p) relative to the face's smallest
@@ -26,10 +31,23 @@ import numpy as np
 
 from .refel import refel
 
+BC_PERIODIC, BC_STATE, BC_SLIP = 0, 1, 2
+BC_NAMES = {"periodic": BC_PERIODIC, "state": BC_STATE, "slip": BC_SLIP}
+
 
 class Mesh:
-    def __init__(self, dim: int, n: int, lo: float, hi: float, p: int, deg: int | None = None):
+    def __init__(self, dim: int, n: int, lo: float, hi: float, p: int, deg: int | None = None,
+                 bc=None, verts=None):
+        """bc: per axis a pair (lo side, hi side) of "periodic", "state" or "slip" (default:
+        all periodic); an axis is periodic on both sides or on neither.
+        verts: lattice vertex coordinates [E, d+1, d] of the elements on [0, n]^d, positively
+        oriented (default: the Kuhn split of the n^d grid)."""
         self.dim, self.n, self.p = dim, n, p
+        bc = bc if bc is not None else [("periodic", "periodic")] * dim
+        self.bc = np.array([[BC_NAMES[s] for s in pair] for pair in bc], dtype=np.int64)   # [dim, 2]
+        if self.bc.shape != (dim, 2) or np.any((self.bc[:, 0] == 0) != (self.bc[:, 1] == 0)):
+            raise ValueError("bc: an axis is periodic on both sides or on neither")
+        self.periodic = self.bc[:, 0] == BC_PERIODIC
         self.lo, self.hi = float(lo), float(hi)
         self.h = (self.hi - self.lo) / n
         self.ref = refel(dim, p, deg)
@@ -51,7 +69,9 @@ class Mesh:
             cell = np.array(tets, dtype=np.int64)                              # [6, 4, 3]
             kk, jj, ii = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
             origin = np.stack([ii.ravel(), jj.ravel(), kk.ravel()], axis=-1)
-        verts = (origin[:, None, None, :] + cell[None]).reshape(-1, cell.shape[1], dim)
+        if verts is None:
+            verts = (origin[:, None, None, :] + cell[None]).reshape(-1, cell.shape[1], dim)
+        verts = np.asarray(verts, dtype=np.int64)
         self.L = verts.astype(np.int64)              # [E, nF, dim]
         self.E = len(verts)
         self.X = self.lo + self.h * self.L.astype(np.float64)
@@ -84,7 +104,8 @@ class Mesh:
         order = np.argsort(self._encode(fv), axis=-1, kind="stable")
         fv = np.take_along_axis(fv, order[..., None], axis=2)
         A = fv[:, :, 0, :]                                                 # smallest vertex
-        key = np.concatenate([A % n, (fv[:, :, 1:, :] - A[:, :, None, :]).reshape(E, nF, -1)], axis=-1)
+        Ak = np.where(self.periodic, A % n, A)
+        key = np.concatenate([Ak, (fv[:, :, 1:, :] - A[:, :, None, :]).reshape(E, nF, -1)], axis=-1)
         key = key.reshape(E * nF, -1)
         _, first, inv = np.unique(key, axis=0, return_index=True, return_inverse=True)
         inv = inv.reshape(-1)
@@ -95,9 +116,23 @@ class Mesh:
         self.nFaces = len(first)
         srt = np.argsort(face_of, kind="stable")                           # sides in appearance order
         counts = np.bincount(face_of, minlength=self.nFaces)
-        assert np.all(counts == 2), "periodic mesh: every face has two sides"
-        sides = srt.reshape(self.nFaces, 2)                                # flat (e * nF + f)
-        self.face_elems = [[(int(a // nF), int(a % nF)), (int(b // nF), int(b % nF))] for a, b in sides]
+        assert np.all((counts == 1) | (counts == 2))
+        starts = np.concatenate([[0], np.cumsum(counts)[:-1]])
+        flat = [srt[s:s + c] for s, c in zip(starts, counts)]               # flat (e * nF + f)
+        self.face_elems = [[(int(a // nF), int(a % nF)) for a in fl] for fl in flat]
+        # boundary faces: every vertex on one side of a bounded axis
+        self.face_bc = np.zeros(self.nFaces, dtype=np.int64)
+        self.face_wall = np.full((self.nFaces, 2), -1, dtype=np.int64)    # (axis, side)
+        for F in np.nonzero(counts == 1)[0]:
+            a0 = flat[F][0]
+            v = fv[a0 // nF, a0 % nF]                                      # [nF-1, d]
+            hit = [(r, s) for r in range(self.dim) if not self.periodic[r] for s in (0, 1)
+                   if np.all(v[:, r] == (0 if s == 0 else n))]
+            assert len(hit) == 1, "a face with one side lies on one side of a bounded axis"
+            self.face_wall[F] = hit[0]
+            self.face_bc[F] = self.bc[hit[0]]
+        sides = np.array([fl for fl in flat if len(fl) == 2]).reshape(-1, 2)
+        owners = np.array([fl[0] for fl in flat])
         # face-node keys: node position (units h/p) relative to the face's smallest vertex;
         # periodic copies of a face differ by a translation, so both sides share the keys
         fn = np.array(ref.face_nodes)                                      # [nF, Nf]
@@ -108,7 +143,7 @@ class Mesh:
         assert np.array_equal(np.take_along_axis(c0, o0, 1), np.take_along_axis(c1, o1, 1))
         assert np.all(np.diff(np.take_along_axis(c0, o0, 1), axis=1) > 0)
         fmap = np.zeros((E * nF, Nf), dtype=np.int64)
-        fmap[sides[:, 0]] = np.arange(Nf)                                  # owner: canonical order
+        fmap[owners] = np.arange(Nf)                                       # owner: canonical order
         m1 = np.zeros_like(c1)
         np.put_along_axis(m1, o1, o0, axis=1)
         fmap[sides[:, 1]] = m1
@@ -163,7 +198,7 @@ class Mesh:
             s = set()
             for f in range(ref.nF):
                 for a in ref.face_nodes[f]:
-                    key = tuple(self.Nint[e, a] % period)
+                    key = tuple(np.where(self.periodic, self.Nint[e, a] % period, self.Nint[e, a]))
                     if key not in ids:
                         ids[key] = len(ids)
                     s.add(ids[key])
@@ -177,7 +212,7 @@ class Mesh:
         ids, _ = self._trace_nodes_edg()
         period = self.n * self.p
         fn = np.array(self.ref.face_nodes)                                  # [nF, Nf]
-        keys = self.Nint[:, fn, :] % period                                 # [E, nF, Nf, d]
+        keys = np.where(self.periodic, self.Nint[:, fn, :] % period, self.Nint[:, fn, :])  # [E, nF, Nf, d]
         index = np.array([ids[tuple(k)] for k in keys.reshape(-1, self.dim)], dtype=np.int64)
         return len(ids), index.reshape(self.E, self.ref.nF, self.ref.Nf)
 

@@ -22,6 +22,7 @@ class Physics:
     reynolds: float = 0.0            # 0 = inviscid (Euler)
     prandtl: float = 0.71
     mu_exponent: float = 0.0         # power law mu = (1/Re) (T / T_inf)^omega (Sec. 5.6 uses 3/4); 0: constant
+    stabilization: str = "slf"       # "slf": sigma_SLF of Eq. sLxF (Sec. 5); "s": sigma_S of Eq. symStab
 
     @property
     def viscous(self) -> bool:
@@ -196,8 +197,64 @@ def lambda_max(v, n, gamma):
     return cabs(np.sum(vel * n, axis=-1)) + c
 
 
-def numerical_flux_inviscid(vhat, v, n, gamma):
-    """Eq. numericalFlux with sigma_SLF(v*) = lambda_max(v*) A0(v*), v* = vhat (Sec. 5)."""
+def flux_jacobian_u(v, n, gamma):
+    """A_n = (dF/du) . n at the state v [..., m, m] (row = flux component, column = u
+    component), the textbook Jacobian of the Euler flux in conservation variables written in
+    primitives: with V_n = V . n, k = |V|^2 / 2 and total enthalpy H = (rho E + p) / rho,
+      mass row      (0, n, 0)
+      momentum i    ((gamma-1) k n_i - V_i V_n,  V_i n_j - (gamma-1) n_i V_j + V_n delta_ij,  (gamma-1) n_i)
+      energy row    (V_n ((gamma-1) k - H),  H n_j - (gamma-1) V_n V_j,  gamma V_n)."""
+    g1 = gamma - 1.0
+    rho, vel, p = primitives_of_v(v, gamma)
+    d = vel.shape[-1]
+    m = d + 2
+    n = np.asarray(n, dtype=float)
+    vn = np.sum(vel * n, axis=-1)
+    k = 0.5 * np.sum(vel * vel, axis=-1)
+    H = gamma * p / (g1 * rho) + k
+    A = np.zeros(v.shape[:-1] + (m, m), dtype=np.result_type(v, float))
+    A[..., 0, 1:1 + d] = n
+    for i in range(d):
+        A[..., 1 + i, 0] = g1 * k * n[i] - vel[..., i] * vn
+        for j in range(d):
+            A[..., 1 + i, 1 + j] = vel[..., i] * n[j] - g1 * n[i] * vel[..., j] + (vn if i == j else 0.0)
+        A[..., 1 + i, m - 1] = g1 * n[i]
+    A[..., m - 1, 0] = vn * (g1 * k - H)
+    A[..., m - 1, 1:1 + d] = H[..., None] * n - g1 * vn[..., None] * vel
+    A[..., m - 1, m - 1] = gamma * vn
+    return A
+
+
+def abs_flux_jacobian(v, n, gamma):
+    """|A_n| at the state v: A_n is diagonalisable with the three distinct eigenvalues
+    l_1 = V_n - c, l_2 = V_n (multiplicity d), l_3 = V_n + c (c > 0), so the matrix function
+    is the Lagrange-Sylvester sum  |A_n| = sum_k |l_k| prod_{j != k} (A_n - l_j I) / (l_k - l_j)."""
+    rho, vel, p = primitives_of_v(v, gamma)
+    c = np.sqrt(gamma * p / rho)
+    vn = np.sum(vel * np.asarray(n, dtype=float), axis=-1)
+    A = flux_jacobian_u(v, n, gamma)
+    eye = np.eye(A.shape[-1])
+    lam = [vn - c, vn, vn + c]
+    out = np.zeros_like(A)
+    for kk in range(3):
+        P = np.broadcast_to(eye, A.shape).astype(A.dtype)
+        for j in range(3):
+            if j != kk:
+                P = np.einsum("...ij,...jk->...ik", P, A - lam[j][..., None, None] * eye)
+                P = P / (lam[kk] - lam[j])[..., None, None]
+        out = out + cabs(lam[kk])[..., None, None] * P
+    return out
+
+
+def numerical_flux_inviscid(vhat, v, n, gamma, stabilization="slf"):
+    """Eq. numericalFlux at v* = vhat (Sec. 5) with
+      "slf": sigma_SLF(v*) = lambda_max(v*) A0(v*)            (Eq. sLxF, the choice of Sec. 5)
+      "s":   sigma_S(v*)   = |A_n(v*)|_{A0} = |A_n(v*)| A0(v*)  (Eq. symStab, Sec. 4.1)."""
     Fn = 0.5 * np.einsum("...ij,...j->...i", inviscid_flux_v(vhat, gamma) + inviscid_flux_v(v, gamma), n)
-    lam = lambda_max(vhat, n, gamma)
-    return Fn + 0.5 * lam[..., None] * du_of_v(vhat, v - vhat, gamma)
+    du = du_of_v(vhat, v - vhat, gamma)
+    if stabilization == "slf":
+        lam = lambda_max(vhat, n, gamma)
+        return Fn + 0.5 * lam[..., None] * du
+    if stabilization == "s":
+        return Fn + 0.5 * np.einsum("...ij,...j->...i", abs_flux_jacobian(vhat, n, gamma), du)
+    raise ValueError(stabilization)

@@ -54,7 +54,6 @@ int run_fp64(hdg_ctx* ctx, const double* V, const double* Vhat, const double* hi
   a.ptf = a.ptv + ch * C::NG * C::PT_VOL;
   a.Ap = a.ptf + ch * C::NF * C::NGF * C::PT_FACE;
   a.Cp = a.Ap + ch * C::NV * C::NV;
-  const int pw_threads = ((C::NG + C::NF * C::NGF + 31) / 32) * 32;
   for (int64_t e0 = 0; e0 < ctx->E; e0 += ch) {
     a.e0 = e0;
     a.ne = std::min<int64_t>(ch, ctx->E - e0);
@@ -65,7 +64,7 @@ int run_fp64(hdg_ctx* ctx, const double* V, const double* Vhat, const double* hi
     }
     {
       LaunchScope ls(ctx, HDG_KERNEL_POINTWISE, s);
-      k_pointwise<C><<<(unsigned)a.ne, pw_threads, 0, s>>>(a, ctx->T, ctx->ph);
+      launch_pointwise<C>(a, ctx->T, ctx->ph, s);
     }
     {
       LaunchScope ls(ctx, HDG_KERNEL_ASSEMBLE, s);

@@ -121,8 +121,24 @@ HDG_DEVI void volume_point_state(int g, const DevTables& T, const double (*z)[C:
 HDG_DEVI void put(double* p, int i, double v) { p[i] = v; }
 HDG_DEVI void put(df2* p, int i, double v) { p[i] = df_from(v); }
 
-// OutT = double (FP64 form) or df2 (mixed form: per-point tensors as double-floats)
-template <class C, class OutT = double>
+// The values of sigma(vhat) = d(sigma (v - vhat))/dv at one face point, [row][column]:
+// lambda_max A0 (Eq. sLxF) from the wave speed and u(vhat)'s derivatives, or |A_n| A0 (Eq. symStab)
+// as a table.
+template <int M, bool SYM>
+struct SigmaValues {
+  double lam;
+  const Dual<M>* uh;
+  HDG_DEVI double operator()(int i, int l) const { return lam * uh[i].d[l]; }
+};
+template <int M>
+struct SigmaValues<M, true> {
+  double s[M][M];
+  HDG_DEVI double operator()(int i, int l) const { return s[i][l]; }
+};
+
+// OutT = double (FP64 form) or df2 (mixed form: per-point tensors as double-floats);
+// SYM: sigma_S of Eq. symStab instead of sigma_SLF (launch through launch_pointwise).
+template <class C, class OutT = double, bool SYM = false>
 __global__ void __launch_bounds__(128) k_pointwise(AssembleArgs a, DevTables T, PhysParams ph) {
   constexpr int D = C::D, M = C::M, NP = C::NP, NFN = C::NFN, NF = C::NF, NG = C::NG, NGF = C::NGF;
   __shared__ double z[C::NZ][M];
@@ -248,13 +264,30 @@ __global__ void __launch_bounds__(128) k_pointwise(AssembleArgs a, DevTables T, 
     prim_of_v<D>(vhd, ph.gamma, rh, velh, prh);
     cons_and_flux<D>(rh, velh, prh, ph.gamma, uh, Fh);
     bad = bad || !(rh.v > 0.0) || !(prh.v > 0.0);
-    Dual<M> lam = lambda_max<D>(rh, velh, prh, n, ph.gamma);
-    du_of_v<D>(vhd, dvd, ph.gamma, duh);
+    du_of_v<D>(vhd, dvd, ph.gamma, duh);  // A0(vhat) (v - vhat)
+    Dual<M> sdu[M];                        // sigma(vhat) (v - vhat)
+    SigmaValues<M, SYM> sig;
+    if constexpr (SYM) {  // sigma_S = |A_n| A0 (Eq. symStab)
+      abs_flux_jac_apply<D>(rh, velh, prh, n, ph.gamma, duh, sdu);
+      double vv[D];
+      for (int j = 0; j < D; ++j) vv[j] = velh[j].v;
+      for (int l = 0; l < M; ++l) {
+        double x[M], y[M];
+        for (int k = 0; k < M; ++k) x[k] = uh[k].d[l];
+        abs_flux_jac_apply<D>(rh.v, vv, prh.v, n, ph.gamma, x, y);
+        for (int i = 0; i < M; ++i) sig.s[i][l] = y[i];
+      }
+    } else {  // sigma_SLF = lambda_max A0 (Eq. sLxF)
+      const Dual<M> lam = lambda_max<D>(rh, velh, prh, n, ph.gamma);
+      for (int i = 0; i < M; ++i) sdu[i] = lam * duh[i];
+      sig.lam = lam.v;
+      sig.uh = uh;
+    }
     Dual<M> hA[M];
     for (int i = 0; i < M; ++i) {
       Dual<M> s = Fh[i][0] * n[0];
       for (int j = 1; j < D; ++j) s = s + Fh[i][j] * n[j];
-      hA[i] = 0.5 * s + 0.5 * (lam * duh[i]);
+      hA[i] = 0.5 * s + 0.5 * sdu[i];
     }
     if (C::VISC && ph.gflux != 1) {  // ghat = G(vhat, q) . n (Eq. numericalFluxNS_2)
       Dual<M> Gh[M][D];
@@ -262,7 +295,7 @@ __global__ void __launch_bounds__(128) k_pointwise(AssembleArgs a, DevTables T, 
       for (int i = 0; i < M; ++i)
         for (int j = 0; j < D; ++j) hA[i] = hA[i] + Gh[i][j] * n[j];
     }
-    // pass B: derivatives with respect to v (F(v).n; the sigma term gives lam A0(vhat))
+    // pass B: derivatives with respect to v (F(v).n; the sigma term gives sigma(vhat))
     Dual<M> vd[M];
     for (int l = 0; l < M; ++l) {
       vd[l] = dconst<M>(v[l]);
@@ -290,7 +323,7 @@ __global__ void __launch_bounds__(128) k_pointwise(AssembleArgs a, DevTables T, 
       for (int j = 1; j < D; ++j) s = s + Fv[i][j] * n[j];
       put(HF, i, Wf * (hA[i].v + 0.5 * s.v + gn[i].v));
       for (int l = 0; l < M; ++l) {
-        put(U0, i * M + l, Wf * (0.5 * s.d[l] + 0.5 * lam.v * uh[i].d[l] + gn[i].d[l]));
+        put(U0, i * M + l, Wf * (0.5 * s.d[l] + 0.5 * sig(i, l) + gn[i].d[l]));
         put(U1, i * M + l, Wf * hA[i].d[l]);
       }
     }
@@ -302,6 +335,16 @@ __global__ void __launch_bounds__(128) k_pointwise(AssembleArgs a, DevTables T, 
     }
   }
   if (bad) atomicOr(a.status + e, HDG_STATUS_NONPHYSICAL);
+}
+
+// k_pointwise with the stabilization matrix the physics selects
+template <class C, class OutT = double>
+void launch_pointwise(const AssembleArgs& a, const DevTables& T, const PhysParams& ph, cudaStream_t s) {
+  const int threads = ((C::NG + C::NF * C::NGF + 31) / 32) * 32;
+  if (ph.stab == 1)
+    k_pointwise<C, OutT, true><<<(unsigned)a.ne, threads, 0, s>>>(a, T, ph);
+  else
+    k_pointwise<C, OutT, false><<<(unsigned)a.ne, threads, 0, s>>>(a, T, ph);
 }
 
 // ------------------------------------------------------------------------------------

@@ -201,7 +201,6 @@ int run_mixed(hdg_ctx* ctx, const double* V, const double* Vhat, const double* h
     const uintptr_t r = reinterpret_cast<uintptr_t>(a.prep + ch * TC::prep_floats);
     a.rb = reinterpret_cast<uint2*>((r + 255) & ~(uintptr_t)255);
   }
-  const int pw_threads = ((C::NG + C::NF * C::NGF + 31) / 32) * 32;
   for (int64_t e0 = 0; e0 < ctx->E; e0 += ch) {
     a.e0 = e0;
     a.ne = std::min<int64_t>(ch, ctx->E - e0);
@@ -212,7 +211,7 @@ int run_mixed(hdg_ctx* ctx, const double* V, const double* Vhat, const double* h
     }
     {
       LaunchScope ls(ctx, HDG_KERNEL_POINTWISE, s);
-      k_pointwise<C, df2><<<(unsigned)a.ne, pw_threads, 0, s>>>(a, ctx->T, ctx->ph);
+      launch_pointwise<C, df2>(a, ctx->T, ctx->ph, s);
     }
     {
       LaunchScope ls(ctx, HDG_KERNEL_MIXED_OPERATORS, s);
@@ -307,7 +306,7 @@ int run_mixed(hdg_ctx* ctx, const double* V, const double* Vhat, const double* h
       f.only_flag = HDG_STATUS_REFINE | HDG_STATUS_TIMEOUT;
       {
         LaunchScope ls(ctx, HDG_KERNEL_POINTWISE, s);
-        k_pointwise<C><<<(unsigned)a.ne, pw_threads, 0, s>>>(f, ctx->T, ctx->ph);
+        launch_pointwise<C>(f, ctx->T, ctx->ph, s);
       }
       {
         LaunchScope ls(ctx, HDG_KERNEL_ASSEMBLE, s);

@@ -84,11 +84,10 @@ int run_noalloc(hdg_ctx* ctx, double* scratch, const double* V, const double* Vh
   a.ptf = a.ptv + ch * C::NG * C::PT_VOL;
   a.Ap = a.ptf + ch * C::NF * C::NGF * C::PT_FACE;
   a.Cp = a.Ap + ch * C::NV * C::NV;
-  const int pw_threads = ((C::NG + C::NF * C::NGF + 31) / 32) * 32;
   for (int64_t e0 = 0; e0 < ctx->E; e0 += ch) {
     a.e0 = e0;
     a.ne = std::min<int64_t>(ch, ctx->E - e0);
-    k_pointwise<C><<<(unsigned)a.ne, pw_threads, 0, s>>>(a, ctx->T, ctx->ph);
+    launch_pointwise<C>(a, ctx->T, ctx->ph, s);
     k_assemble<C><<<(unsigned)a.ne, 256, AsmSmem<C>::bytes, s>>>(a, ctx->T);
     k_condense<C><<<(unsigned)a.ne, 256, CondSmem<C>::bytes, s>>>(a);
   }

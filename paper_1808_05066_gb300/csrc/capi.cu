@@ -214,7 +214,8 @@ int hdg_ctx_create(hdg_mesh_t mesh, const hdg_physics* phys, int device, hdg_ctx
   }
   *out = nullptr;
   if (!(phys->gamma > 1.0) || !(phys->mach > 0.0) || phys->reynolds < 0.0 || !(phys->prandtl > 0.0) ||
-      !(phys->mu_exponent >= 0.0 && phys->mu_exponent <= 4.0) || phys->visc_flux < 0 || phys->visc_flux > 2) {
+      !(phys->mu_exponent >= 0.0 && phys->mu_exponent <= 4.0) || phys->visc_flux < 0 || phys->visc_flux > 2 ||
+      (phys->stabilization != HDG_STAB_SLF && phys->stabilization != HDG_STAB_S)) {
     set_error("hdg_ctx_create: invalid physics parameters");
     return HDG_ERR_INVALID_ARG;
   }
@@ -241,6 +242,7 @@ int hdg_ctx_create(hdg_mesh_t mesh, const hdg_physics* phys, int device, hdg_ctx
   c->ph.kappa = g * c->ph.cv * c->ph.mu / phys->prandtl;
   c->ph.mu_exp = visc ? phys->mu_exponent : 0.0;
   c->ph.gflux = phys->visc_flux == 1 ? 1 : 2;
+  c->ph.stab = phys->stabilization;
   c->dim = m.dim;
   c->p = m.p;
   c->K = m.K;

@@ -44,6 +44,7 @@ struct PhysParams {
   double gamma, cv, mu, kappa;
   double mu_exp;  // power law mu = mu (T / T_inf)^mu_exp, kappa likewise (T_inf = 1); 0: constant
   int gflux;      // viscous numerical flux: 2 = G(vhat, q) . n, 1 = G(v, q) . n
+  int stab;       // stabilization matrix: 0 = lambda_max A0 (Eq. sLxF), 1 = |A_n| A0 (Eq. symStab)
 };
 
 // Constant reference tables (device pointers into one buffer).
@@ -434,6 +435,56 @@ HDG_DEVI T lambda_max(const T& rho, const T* vel, const T& p, const double* n, d
 #pragma unroll
   for (int i = 1; i < D; ++i) vn = vn + vel[i] * n[i];
   return absk(vn) + sqrt(gamma * p / rho);
+}
+
+// (B x)_i for B = A_n - V_n I, A_n = (dF/du) . n the Euler flux Jacobian in conservation
+// variables along n; with k = |V|^2 / 2, H = gamma p / ((gamma - 1) rho) + k:
+//   mass      x_V . n - V_n x_0
+//   momentum  ((gamma-1) k n_i - V_i V_n) x_0 + V_i (n . x_V) - (gamma-1) n_i (V . x_V) + (gamma-1) n_i x_E
+//   energy    V_n ((gamma-1) k - H) x_0 + H (n . x_V) - (gamma-1) V_n (V . x_V) + (gamma - 1) V_n x_E
+template <int D, class T, class X, class Y>
+HDG_DEVI void flux_jac_shifted(const T* vel, const T& vn, const T& k, const T& H, const double* n, double gamma,
+                               const X* x, Y* y) {
+  const double g1 = gamma - 1.0;
+  Y nx = x[1] * n[0], Vx = x[1] * vel[0];
+#pragma unroll
+  for (int j = 1; j < D; ++j) {
+    nx = nx + x[1 + j] * n[j];
+    Vx = Vx + x[1 + j] * vel[j];
+  }
+  y[0] = nx - vn * x[0];
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+    y[1 + i] = (g1 * n[i] * k - vel[i] * vn) * x[0] + vel[i] * nx + g1 * n[i] * (x[D + 1] - Vx);
+  y[D + 1] = vn * (g1 * k - H) * x[0] + H * nx + g1 * vn * (x[D + 1] - Vx);
+}
+
+// y = |A_n| x (the absolute value of Sec. 4.1, sigma_S = |A_n| A0 of Eq. symStab): the
+// eigenvalues of A_n are V_n - c, V_n (d-fold), V_n + c, and interpolating |.| on them gives
+//   |A_n| = |V_n| I + a B + b B^2,  B = A_n - V_n I,
+//   a = (|V_n + c| - |V_n - c|) / (2 c),  b = (|V_n - c| + |V_n + c| - 2 |V_n|) / (2 c^2).
+template <int D, class T, class X, class Y>
+HDG_DEVI void abs_flux_jac_apply(const T& rho, const T* vel, const T& p, const double* n, double gamma, const X* x,
+                                 Y* y) {
+  using ::sqrt;
+  constexpr int M = D + 2;
+  T vn = vel[0] * n[0], k = vel[0] * vel[0];
+#pragma unroll
+  for (int i = 1; i < D; ++i) {
+    vn = vn + vel[i] * n[i];
+    k = k + vel[i] * vel[i];
+  }
+  k = 0.5 * k;
+  const T c2 = gamma * p / rho;
+  const T c = sqrt(c2);
+  const T H = c2 / (gamma - 1.0) + k;
+  const T am = absk(vn - c), a0 = absk(vn), ap = absk(vn + c);
+  const T ca = (ap - am) / (2.0 * c), cb = (am + ap - 2.0 * a0) / (2.0 * c2);
+  Y b1[M], b2[M];
+  flux_jac_shifted<D>(vel, vn, k, H, n, gamma, x, b1);
+  flux_jac_shifted<D>(vel, vn, k, H, n, gamma, b1, b2);
+#pragma unroll
+  for (int i = 0; i < M; ++i) y[i] = a0 * x[i] + ca * b1[i] + cb * b2[i];
 }
 
 }  // namespace hdg

@@ -70,7 +70,8 @@ class HdgError(RuntimeError):
 
 class hdg_physics(ctypes.Structure):
     _fields_ = [("gamma", c_double), ("mach", c_double), ("reynolds", c_double), ("prandtl", c_double),
-                ("mu_exponent", c_double), ("visc_flux", c_int32)]
+                ("mu_exponent", c_double), ("visc_flux", c_int32),
+                ("stabilization", c_int32)]
 
 
 class hdg_warmstart(ctypes.Structure):
@@ -227,8 +228,9 @@ def hdg_mesh_copy_coords(mesh):
     return xnode, xfnode, geo
 
 
-def hdg_ctx_create(mesh, gamma=1.4, mach=0.5, reynolds=0.0, prandtl=0.71, device=0, mu_exponent=0.0, visc_flux=2):
-    ph = hdg_physics(gamma, mach, reynolds, prandtl, mu_exponent, visc_flux)
+def hdg_ctx_create(mesh, gamma=1.4, mach=0.5, reynolds=0.0, prandtl=0.71, device=0, mu_exponent=0.0, visc_flux=2,
+                   stabilization=0):
+    ph = hdg_physics(gamma, mach, reynolds, prandtl, mu_exponent, visc_flux, stabilization)
     h = c_void_p()
     _check(_lib.hdg_ctx_create(mesh, byref(ph), device, byref(h)))
     return h.value
@@ -468,9 +470,10 @@ class Context:
     """Owns an hdg_ctx_t bound to a Mesh (kept alive by this object)."""
 
     def __init__(self, mesh: Mesh, gamma=1.4, mach=0.5, reynolds=0.0, prandtl=0.71, device=0, mu_exponent=0.0,
-                 visc_flux=2):
+                 visc_flux=2, stabilization=0):
         self.mesh = mesh
-        self.handle = hdg_ctx_create(mesh.handle, gamma, mach, reynolds, prandtl, device, mu_exponent, visc_flux)
+        self.handle = hdg_ctx_create(mesh.handle, gamma, mach, reynolds, prandtl, device, mu_exponent, visc_flux,
+                                     stabilization)
         self.device = device
 
     def close(self):

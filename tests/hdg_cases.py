@@ -28,6 +28,9 @@ class Case:
     mu_exponent: float = 0.0   # power-law viscosity exponent (0: constant)
     visc_flux: int = 2         # viscous numerical flux option (Eq. numericalFluxNS_1 / _2)
     scheme: str = "hdg"        # trace space (Sec. 3.4): "hdg" or "edg"
+    stabilization: str = "slf"  # "slf" (Eq. sLxF) or "s" (Eq. symStab)
+    vinf: tuple = (1.0, 0.0)    # free stream of the vortex fields
+    psi: float = 5.0            # strength of the single vortex
 
     @property
     def lo(self):
@@ -37,9 +40,11 @@ class Case:
         if self.field == "tgv":
             return wl.tgv_field(x * (2 * math.pi / self.L), self.mach)
         if self.field == "vortex":
-            return wl.vortex_field(x, [wl.Vortex(self.L / 2, self.L / 2, 5.0)], self.mach, period=self.L)
+            return wl.vortex_field(x, [wl.Vortex(self.L / 2, self.L / 2, self.psi)], self.mach, vinf=self.vinf,
+                                   period=self.L)
         nv = int(self.field.replace("vortices", ""))
-        return wl.vortex_field(x, wl.draw_vortices(nv, self.L, self.seed), self.mach, period=self.L)
+        return wl.vortex_field(x, wl.draw_vortices(nv, self.L, self.seed), self.mach, vinf=self.vinf,
+                               period=self.L)
 
 
 def prim_array(case: Case, x):
@@ -53,7 +58,8 @@ def oracle_setup(case: Case):
     from oracle.hdg import Problem, consistent_Q, interpolate_state
     from oracle.mesh import Mesh
     mesh = Mesh(case.dim, case.n, 0.0, case.L, case.p)
-    phys = ph.Physics(mach=case.mach, reynolds=case.reynolds, prandtl=case.prandtl, mu_exponent=case.mu_exponent)
+    phys = ph.Physics(mach=case.mach, reynolds=case.reynolds, prandtl=case.prandtl, mu_exponent=case.mu_exponent,
+                       stabilization=case.stabilization)
     prob = Problem(mesh, phys, viscous_flux_option=case.visc_flux, scheme=case.scheme)
     V, Vh = interpolate_state(prob, case.prim)
     if case.noise:
@@ -78,7 +84,8 @@ class GpuCase:
         self.mesh = hdg.Mesh(case.dim, case.n, 0.0, case.L, case.p,
                              scheme=hdg.HDG_SCHEME_EDG if case.scheme == "edg" else hdg.HDG_SCHEME_HDG)
         self.ctx = hdg.Context(self.mesh, 1.4, case.mach, case.reynolds, case.prandtl, device,
-                               mu_exponent=case.mu_exponent, visc_flux=case.visc_flux)
+                               mu_exponent=case.mu_exponent, visc_flux=case.visc_flux,
+                               stabilization=1 if case.stabilization == "s" else 0)
         self.info = self.mesh.info
         xnode, xfnode, _ = self.mesh.coords()
         dev = torch.device("cuda", device)

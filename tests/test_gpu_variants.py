@@ -1,6 +1,7 @@
 """GPU parity of the variants of the scheme with the oracle, element by element: the viscous
 numerical flux of Eq. numericalFluxNS_1 (ghat = G(v, q) . n), the power-law viscosity of Sec. 5.6
-(mu = mu_ref (T / T_inf)^(3/4)), both together, and the entropy diagnostics of Eq. PiS."""
+(mu = mu_ref (T / T_inf)^(3/4)), both together, the symmetric variable stabilization matrix
+sigma_S = |A_n| A0 of Eq. symStab, and the entropy diagnostics of Eq. PiS."""
 import dataclasses
 
 import numpy as np
@@ -13,13 +14,15 @@ pytestmark = pytest.mark.gpu
 TOL_BLOCK = 1e-10
 TOL_RES = 1e-12
 VARIANTS = {"option1": dict(visc_flux=1), "power_law": dict(mu_exponent=0.75),
-            "both": dict(visc_flux=1, mu_exponent=0.75)}
+            "both": dict(visc_flux=1, mu_exponent=0.75), "sigma_s": dict(stabilization="s")}
 
 
 @pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("variant", list(VARIANTS))
-@pytest.mark.parametrize("name", ["ns2d_p3", "ns3d_p2"])
+@pytest.mark.parametrize("name", ["ns2d_p3", "ns3d_p2", "euler2d_p2"])
 def test_variant_assemble_condense_matches_oracle(name, variant, precision):
+    if CASES[name].reynolds == 0 and variant != "sigma_s":
+        pytest.skip("viscous variant")
     case = dataclasses.replace(CASES[name], **VARIANTS[variant])
     gc = GpuCase(case)
     prob, Q, V, Vh = oracle_setup(case)
@@ -33,7 +36,8 @@ def test_variant_assemble_condense_matches_oracle(name, variant, precision):
     base.assemble(base.history(), precision=precision)
     assert rel_fro(S, base.S.cpu().numpy()) > 1e-8
     for e in sorted({0, 3, prob.mesh.E - 1}):
-        L = prob.condense(e, Q[e], V[e], prob.gather_trace(Vh, e), case.mass_coef, hist_o[e])
+        L = prob.condense(e, None if Q is None else Q[e], V[e], prob.gather_trace(Vh, e), case.mass_coef,
+                          hist_o[e])
         nq = L["Rl"].size - nv
         Rv = L["Rl"][nq:]
         scale = max(np.abs(Rv).max(), np.abs(L["Rt"]).max(), np.abs(hist_o[e]).max(), 1.0)

@@ -108,11 +108,13 @@ def test_mesh_matches_oracle(dim, n, p):
 
 
 def test_physics_arguments_are_checked():
-    """Invalid physics (power-law exponent outside 0..4, unknown viscous-flux option) is rejected
+    """Invalid physics (power-law exponent outside 0..4, unknown viscous-flux option or
+    stabilization matrix) is rejected
     before any device is touched."""
     hdg = _lib()
     m = hdg.Mesh(2, 2, 0.0, 1.0, 2)
-    for kw in (dict(mu_exponent=-0.5), dict(mu_exponent=9.0), dict(visc_flux=3)):
+    for kw in (dict(mu_exponent=-0.5), dict(mu_exponent=9.0), dict(visc_flux=3),
+               dict(stabilization=2)):
         with pytest.raises(hdg.HdgError) as ei:
             hdg.hdg_ctx_create(m.handle, 1.4, 0.3, 100.0, 0.72, 0, **kw)
         assert ei.value.code == hdg.HDG_ERR_INVALID_ARG
