@@ -104,10 +104,21 @@ typedef struct {
   int64_t n_elem, n_faces, n_trace; /* n_trace = n_trace_nodes * m */
   int32_t scheme;                   /* HDG_SCHEME_* */
   int64_t n_trace_nodes;            /* HDG: n_faces * Nf (a trace per face); EDG / IEDG: skeleton nodes */
+  int64_t n_boundary_faces;         /* faces with one side (on the sides of bounded axes) */
 } hdg_mesh_info;
 
-/* Mesh T_h (Sec. 3.1.1): the n[0] x .. x n[dim-1] periodic grid on the box
- * [lo, hi], each cell split into 2 triangles / 6 tetrahedra (Kuhn split, the same in
+/* Boundary types of the sides of the box (the term b_h of Eqs. hDG2 / hDG_NS2, which the paper
+ * leaves open, Sec. 3.2):
+ *   HDG_BC_PERIODIC  the two sides of the axis are identified (no boundary);
+ *   HDG_BC_STATE     b_h = vhat - v_b: the trace takes a given boundary state v_b (the prescribed
+ *                    exact solutions of Secs. 5.1-5.2), set by hdg_ctx_set_boundary_state;
+ *   HDG_BC_SLIP      b_h = fhat(vhat, v; n) + fhat(vhat, R v; -n), R reflecting the momentum
+ *                    components in the wall: the trace residual of an interior face whose other
+ *                    side is the element's mirror image (a slip wall; Euler only). */
+enum { HDG_BC_PERIODIC = 0, HDG_BC_STATE = 1, HDG_BC_SLIP = 2 };
+
+/* Mesh T_h (Sec. 3.1.1): the n[0] x .. x n[dim-1] grid on the box [lo, hi], periodic or
+ * bounded per axis, each cell split into 2 triangles / 6 tetrahedra (Kuhn split, the same in
  * every cell; element e = (cells in x-fastest order) x (2 or 6) + local index).
  *   p_per_elem  host array [E] of per-element degrees, or NULL for the uniform degree p.
  *               Meshes whose elements differ in degree are not built: a non-uniform array
@@ -116,20 +127,25 @@ typedef struct {
  *   scheme      trace space of Sec. 3.4: HDG_SCHEME_HDG (one trace per face, Vhat [F][Nf][m]) or
  *               HDG_SCHEME_EDG (a continuous trace, one unknown per skeleton node, Vhat [N][m],
  *               nodes numbered in order of first appearance over (element, local face, face
- *               node)); HDG_SCHEME_IEDG continuous on interior faces only, which on these periodic
- *               meshes (every face interior) is EDG. The local problem and the condensation are the
+ *               node)); HDG_SCHEME_IEDG continuous on interior faces only, which on periodic meshes
+ *               (every face interior) is EDG. The local problem and the condensation are the
  *               same for all three; only the global trace numbering differs.
  *   quad_points K Gauss-Jacobi points per direction, exact to degree 2K-1 (0 selects p+1).
+ *   bc          host array [2 dim] of HDG_BC_* per axis (lo side, hi side), or NULL for a fully
+ *               periodic mesh; an axis is periodic on both sides or on neither. Bounded meshes
+ *               are built for the HDG scheme only (EDG / IEDG: HDG_ERR_UNSUPPORTED).
  * Host-only work; the mesh owns host arrays only (freed by hdg_mesh_destroy).
  * Errors: HDG_ERR_INVALID_ARG, HDG_ERR_UNSUPPORTED. */
 int hdg_mesh_create(int dim, const int64_t n[3], const double lo[3], const double hi[3], const int8_t* p_per_elem,
-                    int p, int scheme, int quad_points, hdg_mesh_t* out);
+                    int p, int scheme, int quad_points, const int32_t* bc, hdg_mesh_t* out);
 void hdg_mesh_destroy(hdg_mesh_t mesh);
 int hdg_mesh_get_info(hdg_mesh_t mesh, hdg_mesh_info* out);
 /* Host copies of the topology: face_of [E][nF], fnode_map [E][nF][Nf] (canonical face
- * node of each local face node), face_side [F][2] (e * nF + f; owner first). Any
- * pointer may be NULL. */
+ * node of each local face node), face_side [F][2] (e * nF + f; owner first; -1 for the missing
+ * side of a boundary face). Any pointer may be NULL. */
 int hdg_mesh_copy_topology(hdg_mesh_t mesh, int32_t* face_of, int32_t* fnode_map, int32_t* face_side);
+/* Host copy of the boundary type of every face, face_bc [F] (HDG_BC_*; 0 for interior faces). */
+int hdg_mesh_copy_face_bc(hdg_mesh_t mesh, int8_t* face_bc);
 /* Global trace node of every local face node, tnode [E][nF][Nf] (host): HDG face * Nf + canonical
  * face node; EDG the skeleton node. The element's trace unknowns are Vhat[tnode][0..m). */
 int hdg_mesh_copy_trace_map(hdg_mesh_t mesh, int32_t* tnode);
@@ -142,9 +158,19 @@ int hdg_mesh_copy_coords(hdg_mesh_t mesh, double* xnode, double* xfnode, double*
 
 /* Context: mesh tables, reference tables and physics on one CUDA device. Allocates the
  * device tables and (lazily, on first use) the internal scratch of the calls below;
- * everything is freed by hdg_ctx_destroy. The mesh must outlive the context. */
+ * everything is freed by hdg_ctx_destroy. The mesh must outlive the context.
+ * Errors: HDG_ERR_INVALID_ARG (physics), HDG_ERR_UNSUPPORTED (configuration not compiled; slip
+ * walls with viscous physics), HDG_ERR_CUDA. */
 int hdg_ctx_create(hdg_mesh_t mesh, const hdg_physics* phys, int device, hdg_ctx_t* out);
 void hdg_ctx_destroy(hdg_ctx_t ctx);
+
+/* The boundary state v_b of the HDG_BC_STATE faces: Vb is a device array in the trace layout
+ * [n_faces][Nf][m] (entries of other faces are not read), copied on `stream` into the context
+ * (the caller may free or reuse Vb once the stream passes the copy). Every later assembly reads
+ * the copy, so a time-dependent state is set before each step. A mesh with state faces must have
+ * its state set before the first assembly (else HDG_ERR_INVALID_ARG there).
+ * Errors: HDG_ERR_INVALID_ARG (null), HDG_ERR_CUDA. */
+int hdg_ctx_set_boundary_state(hdg_ctx_t ctx, const double* Vb, void* stream);
 
 /* Mixed form only: tolerance of the refinement status bit and what happens to a flagged
  * block. A block is flagged when its last correction, squared over the one before it, is
@@ -382,7 +408,8 @@ int hdg_mlp_apply_trace(hdg_ctx_t ctx, const double* Vhat, const double* dvhat1,
  * of launches and their summed device time in milliseconds since the last reset. */
 enum {
   HDG_KERNEL_POINTWISE = 0,        /* fluxes and pointwise Jacobians (both forms)          */
-  HDG_KERNEL_ASSEMBLE = 1,         /* FP64 form: quadrature contractions into A, B, C, D    */
+  HDG_KERNEL_ASSEMBLE = 1,         /* FP64 form: quadrature contractions into A, B, C, D;
+                                      both forms: the boundary faces' rows                   */
   HDG_KERNEL_CONDENSE = 2,         /* FP64 form: LU, X = A^{-1}B, S = D - C X              */
   HDG_KERNEL_MIXED_ASSEMBLE = 3,   /* mixed form: volume contractions (tensor-core slices) */
   HDG_KERNEL_MIXED_CONDENSE = 4,   /* mixed form: refinement, tensor-core slice products   */

@@ -70,6 +70,7 @@ int run_fp64(hdg_ctx* ctx, const double* V, const double* Vhat, const double* hi
       LaunchScope ls(ctx, HDG_KERNEL_ASSEMBLE, s);
       k_assemble<C><<<(unsigned)a.ne, 256, AsmSmem<C>::bytes, s>>>(a, ctx->T);
     }
+    if (int rc_b = boundary_patch(ctx, a, HDG_PREC_FP64, s)) return rc_b;
     {
       LaunchScope ls(ctx, HDG_KERNEL_CONDENSE, s);
       k_condense<C><<<(unsigned)a.ne, 256, CondSmem<C>::bytes, s>>>(a);

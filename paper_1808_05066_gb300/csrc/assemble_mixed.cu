@@ -289,6 +289,7 @@ int run_mixed(hdg_ctx* ctx, const double* V, const double* Vhat, const double* h
       LaunchScope ls(ctx, HDG_KERNEL_MIXED_FACE, s);
       variants[ctx->face_variant < 0 ? 0 : ctx->face_variant].run_face(a, ctx->T, TD, s);
     }
+    if (int rc_b = boundary_patch(ctx, a, HDG_PREC_MIXED, s)) return rc_b;
     const CondVariant& cv = cvariants[ctx->cond_variant < 0 ? 0 : ctx->cond_variant];
     {
       LaunchScope ls(ctx, HDG_KERNEL_MIXED_PREP, s);
@@ -312,6 +313,7 @@ int run_mixed(hdg_ctx* ctx, const double* V, const double* Vhat, const double* h
         LaunchScope ls(ctx, HDG_KERNEL_ASSEMBLE, s);
         k_assemble<C><<<(unsigned)a.ne, 256, AsmSmem<C>::bytes, s>>>(f, ctx->T);
       }
+      if (int rc_b = boundary_patch(ctx, f, HDG_PREC_FP64, s)) return rc_b;
       {
         LaunchScope ls(ctx, HDG_KERNEL_CONDENSE, s);
         k_condense<C><<<(unsigned)a.ne, 256, CondSmem<C>::bytes, s>>>(f);

@@ -89,6 +89,7 @@ int run_noalloc(hdg_ctx* ctx, double* scratch, const double* V, const double* Vh
     a.ne = std::min<int64_t>(ch, ctx->E - e0);
     launch_pointwise<C>(a, ctx->T, ctx->ph, s);
     k_assemble<C><<<(unsigned)a.ne, 256, AsmSmem<C>::bytes, s>>>(a, ctx->T);
+    if (int rc_b = boundary_patch(ctx, a, HDG_PREC_FP64, s)) return rc_b;
     k_condense<C><<<(unsigned)a.ne, 256, CondSmem<C>::bytes, s>>>(a);
   }
   HDG_CK(cudaGetLastError());

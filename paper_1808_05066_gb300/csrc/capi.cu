@@ -99,7 +99,7 @@ extern "C" {
 const char* hdg_last_error(void) { return hdg::g_last_error.c_str(); }
 
 int hdg_mesh_create(int dim, const int64_t n[3], const double lo[3], const double hi[3], const int8_t* p_per_elem,
-                    int p, int scheme, int quad_points, hdg_mesh_t* out) {
+                    int p, int scheme, int quad_points, const int32_t* bc, hdg_mesh_t* out) {
   if (!out || !n || !lo || !hi) {
     set_error("hdg_mesh_create: null argument");
     return HDG_ERR_INVALID_ARG;
@@ -122,9 +122,15 @@ int hdg_mesh_create(int dim, const int64_t n[3], const double lo[3], const doubl
         return p_per_elem[e] >= 1 && p_per_elem[e] <= 4 ? HDG_ERR_UNSUPPORTED : HDG_ERR_INVALID_ARG;
       }
   }
+  if (bc && scheme != HDG_SCHEME_HDG)
+    for (int d = 0; d < 2 * dim && d < 6; ++d)
+      if (bc[d] != HDG_BC_PERIODIC) {
+        set_error("hdg_mesh_create: bounded meshes are built for the HDG trace space only");
+        return HDG_ERR_UNSUPPORTED;
+      }
   if (quad_points == 0) quad_points = p + 1;
   auto* m = new hdg_mesh();
-  int rc = hdg::build_mesh(dim, n, lo, hi, p, quad_points, m->m);
+  int rc = hdg::build_mesh(dim, n, lo, hi, p, quad_points, m->m, bc);
   if (rc != 0) {
     delete m;
     set_error("hdg_mesh_create: invalid mesh arguments (code " + std::to_string(rc) + ")");
@@ -161,6 +167,16 @@ int hdg_mesh_get_info(hdg_mesh_t mesh, hdg_mesh_info* out) {
   out->scheme = m.scheme;
   out->n_trace_nodes = m.scheme == HDG_SCHEME_HDG ? m.nFaces * m.ref.Nf : m.n_edg;
   out->n_trace = out->n_trace_nodes * (m.dim + 2);
+  out->n_boundary_faces = m.n_boundary;
+  return HDG_OK;
+}
+
+int hdg_mesh_copy_face_bc(hdg_mesh_t mesh, int8_t* face_bc) {
+  if (!mesh || !face_bc) {
+    set_error("hdg_mesh_copy_face_bc: null argument");
+    return HDG_ERR_INVALID_ARG;
+  }
+  std::memcpy(face_bc, mesh->m.face_bc.data(), mesh->m.face_bc.size());
   return HDG_OK;
 }
 
@@ -225,6 +241,12 @@ int hdg_ctx_create(hdg_mesh_t mesh, const hdg_physics* phys, int device, hdg_ctx
     set_error("hdg_ctx_create: (dim, p, quad_points, physics) not compiled in");
     return HDG_ERR_UNSUPPORTED;
   }
+  if (visc)
+    for (int8_t k : m.face_bc)
+      if (k == HDG_BC_SLIP) {
+        set_error("hdg_ctx_create: the slip wall is defined for the Euler equations only");
+        return HDG_ERR_UNSUPPORTED;
+      }
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
     set_error("hdg_ctx_create: no such CUDA device");
@@ -306,10 +328,14 @@ int hdg_ctx_create(hdg_mesh_t mesh, const hdg_physics* phys, int device, hdg_ctx
     std::vector<int> fill(tr_ptr.begin(), tr_ptr.end() - 1);
     for (size_t i = 0; i < tgidx.size(); ++i) tr_occ[fill[tgidx[i]]++] = (int)i;
   }
-  std::vector<int> fs_elem(2 * c->F), fs_loc(2 * c->F * c->NFN);
+  std::vector<int> fs_elem(2 * c->F), fs_loc(2 * c->F * c->NFN, 0);
   for (int64_t F = 0; F < c->F; ++F)
     for (int sd = 0; sd < 2; ++sd) {
       int32_t ef = m.face_side[2 * F + sd];
+      if (ef < 0) {  // the missing side of a boundary face
+        fs_elem[2 * F + sd] = -1;
+        continue;
+      }
       int64_t e = ef / c->NF;
       int f = ef % c->NF;
       fs_elem[2 * F + sd] = (int)e;
@@ -318,7 +344,21 @@ int hdg_ctx_create(hdg_mesh_t mesh, const hdg_physics* phys, int device, hdg_ctx
         fs_loc[(2 * F + sd) * c->NFN + canon] = f * c->NFN + cc;
       }
     }
+  // boundary faces in ascending e NF + f, with their types
+  std::vector<int> bkind;
+  for (int64_t e = 0; e < c->E; ++e)
+    for (int f = 0; f < c->NF; ++f) {
+      const int8_t k = m.face_bc[m.face_of[e * c->NF + f]];
+      if (k == HDG_BC_PERIODIC) continue;
+      c->h_bface.push_back((int)(e * c->NF + f));
+      bkind.push_back(k);
+      if (k == HDG_BC_STATE) c->has_state_bc = true;
+    }
   int rc = HDG_OK;
+  if (!c->h_bface.empty() && ((rc = upload(&c->d_bface, c->h_bface)) || (rc = upload(&c->d_bkind, bkind)))) {
+    hdg_ctx_destroy(c);
+    return rc;
+  }
   if ((rc = upload(&c->d_tab, tab)) || (rc = upload(&c->d_itab, itab)) || (rc = upload(&c->d_tgidx, tgidx)) ||
       (rc = upload(&c->d_geo, m.geo)) || (rc = upload(&c->d_fs_elem, fs_elem)) || (rc = upload(&c->d_fs_loc, fs_loc)) ||
       (rc = upload(&c->d_tr_ptr, tr_ptr)) || (rc = upload(&c->d_tr_occ, tr_occ))) {
@@ -346,7 +386,8 @@ void hdg_ctx_destroy(hdg_ctx_t c) {
   void* bufs[] = {c->d_tab, c->d_tab_df, c->d_itab, c->d_tgidx, c->d_geo, c->d_fs_elem, c->d_fs_loc, c->d_scr,
                   c->d_sw, c->d_pc, c->d_pcpiv, c->d_dense, c->d_dpiv, c->d_red, c->d_S,
                   c->d_g, c->d_recov, c->d_R, c->d_dV, c->d_dVh, c->d_status, c->d_hist, c->d_V0,
-                  c->d_Vh0, c->d_feat, c->d_pred, c->d_dirk, c->d_ent, c->d_tr_ptr, c->d_tr_occ, c->d_pcn};
+                  c->d_Vh0, c->d_feat, c->d_pred, c->d_dirk, c->d_ent, c->d_tr_ptr, c->d_tr_occ, c->d_pcn,
+                  c->d_bface, c->d_bkind, c->d_vb};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (c->h_red) cudaFreeHost(c->h_red);
@@ -376,6 +417,16 @@ void hdg_ctx_destroy(hdg_ctx_t c) {
       return HDG_ERR_INVALID_ARG; \
     }                           \
   } while (0)
+
+int hdg_ctx_set_boundary_state(hdg_ctx_t ctx, const double* Vb, void* stream) {
+  HDG_REQUIRE(ctx && Vb, "hdg_ctx_set_boundary_state: null argument");
+  DeviceGuard guard(ctx->device);
+  if (!ctx->d_vb) HDG_CK(cudaMalloc(&ctx->d_vb, sizeof(double) * ctx->ntrace));
+  HDG_CK(cudaMemcpyAsync(ctx->d_vb, Vb, sizeof(double) * ctx->ntrace, cudaMemcpyDeviceToDevice,
+                         (cudaStream_t)stream));
+  ctx->vb_set = true;
+  return HDG_OK;
+}
 
 int hdg_prim_to_entropy(hdg_ctx_t ctx, const double* prim, int64_t n_points, double* v, void* stream) {
   HDG_REQUIRE(ctx && prim && v && n_points >= 0, "hdg_prim_to_entropy: invalid argument");

@@ -26,6 +26,14 @@ struct hdg_ctx {
   int* d_tr_ptr = nullptr;   // [n_tnodes + 1] CSR of the local occurrences of each trace node
   int* d_tr_occ = nullptr;   // [E NF NFN] local occurrence e NF NFN + f NFN + c
   double* d_pcn = nullptr;   // EDG preconditioner: inverse node blocks [n_tnodes][M][M]
+  // boundary faces (bounded meshes): (e NF + f, type) in ascending e, host and device copies;
+  // the boundary state of the HDG_BC_STATE faces in the trace layout
+  std::vector<int> h_bface;
+  int* d_bface = nullptr;    // [nb] e NF + f
+  int* d_bkind = nullptr;    // [nb] HDG_BC_*
+  bool has_state_bc = false;
+  double* d_vb = nullptr;    // [ntrace] (allocated when the state is first set)
+  bool vb_set = false;
   // device tables
   double* d_tab = nullptr;
   size_t tab_size = 0;       // doubles in d_tab
@@ -34,7 +42,7 @@ struct hdg_ctx {
   hdg::DevTables T{};
   int* d_tgidx = nullptr;    // [E][NF][NFN] canonical global face node of each local face node
   double* d_geo = nullptr;   // [E][GEO]
-  int* d_fs_elem = nullptr;  // [F][2] element of each side (owner first)
+  int* d_fs_elem = nullptr;  // [F][2] element of each side (owner first; -1: boundary face)
   int* d_fs_loc = nullptr;   // [F][2][NFN] local face-node row (f*NFN + c) for canonical node
   // assembly scratch (chunked over elements)
   int64_t chunk = 0;
@@ -165,6 +173,10 @@ int assemble_condense_mixed(hdg_ctx* ctx, const double* V, const double* Vhat, c
                             double mass_coef, double* S, double* g, double* recov, double* R, int32_t* status,
                             cudaStream_t s);
 bool config_supported(int dim, int p, int K, bool visc);
+struct AssembleArgs;  // assemble_fp64.cuh
+// the boundary term of the chunk's boundary faces, written over the interior-face rows the
+// element assembly left in R_t, C and D (boundary.cu); precision selects the output form
+int boundary_patch(hdg_ctx* ctx, const AssembleArgs& a, int precision, cudaStream_t s);
 // int rho s and the physical entropy production of Eq. PiS added into acc[0], acc[1]
 int entropy_terms(hdg_ctx* ctx, const double* V, const double* Vhat, double* acc, cudaStream_t s);
 

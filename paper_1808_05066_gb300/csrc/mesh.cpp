@@ -1,4 +1,4 @@
-// Periodic Kuhn-split simplex meshes; see mesh.hpp for the numbering rules.
+// Kuhn-split simplex meshes, periodic or bounded per axis; see mesh.hpp for the numbering rules.
 #include "mesh.hpp"
 
 #include <algorithm>
@@ -19,12 +19,21 @@ int64_t pmod(int64_t a, int64_t n) {
 
 }  // namespace
 
-int build_mesh(int dim, const int64_t n_[3], const double lo_[3], const double hi_[3], int p, int K, Mesh& m) {
+int build_mesh(int dim, const int64_t n_[3], const double lo_[3], const double hi_[3], int p, int K, Mesh& m,
+               const int32_t* bc) {
   if (dim != 2 && dim != 3) return -1;
   if (p < 1 || p > 6 || K < 1) return -1;
   for (int r = 0; r < dim; ++r)
     if (n_[r] < 1 || !(hi_[r] > lo_[r])) return -1;
   m = Mesh();
+  if (bc)
+    for (int r = 0; r < dim; ++r) {
+      for (int s = 0; s < 2; ++s) {
+        if (bc[2 * r + s] < 0 || bc[2 * r + s] > 2) return -1;
+        m.bc[r][s] = bc[2 * r + s];
+      }
+      if ((m.bc[r][0] == 0) != (m.bc[r][1] == 0)) return -1;
+    }
   m.dim = dim;
   m.p = p;
   m.K = K;
@@ -89,7 +98,7 @@ int build_mesh(int dim, const int64_t n_[3], const double lo_[3], const double h
         if (v != f) fv.push_back(verts[e][v]);
       std::sort(fv.begin(), fv.end());
       std::array<int64_t, 9> key{};
-      for (int r = 0; r < 3; ++r) key[r] = pmod(fv[0][r], m.n[r]);
+      for (int r = 0; r < 3; ++r) key[r] = m.bc[r][0] == 0 ? pmod(fv[0][r], m.n[r]) : fv[0][r];
       for (size_t i = 1; i < fv.size(); ++i)
         for (int r = 0; r < 3; ++r) key[3 * i + r] = fv[i][r] - fv[0][r];
       auto it = key2id.find(key);
@@ -106,10 +115,35 @@ int build_mesh(int dim, const int64_t n_[3], const double lo_[3], const double h
     }
   m.nFaces = (int64_t)sides.size();
   m.face_side.resize(m.nFaces * 2);
+  m.face_bc.assign(m.nFaces, 0);
   for (int64_t F = 0; F < m.nFaces; ++F) {
-    if (sides[F].size() != 2) return -2;
+    if (sides[F].size() == 2) {
+      m.face_side[2 * F] = sides[F][0];
+      m.face_side[2 * F + 1] = sides[F][1];
+      continue;
+    }
+    if (sides[F].size() != 1) return -2;
+    // a face with one side: all its vertices on one side of a bounded axis
+    const int64_t e = sides[F][0] / nF;
+    const int f = sides[F][0] % nF;
+    int kind = -1;
+    for (int r = 0; r < dim; ++r) {
+      if (m.bc[r][0] == 0) continue;
+      for (int s = 0; s < 2; ++s) {
+        bool on = true;
+        for (int v = 0; v < nF; ++v)
+          if (v != f && verts[e][v][r] != (s == 0 ? 0 : m.n[r])) on = false;
+        if (on) {
+          if (kind >= 0) return -2;
+          kind = m.bc[r][s];
+        }
+      }
+    }
+    if (kind <= 0) return -2;
     m.face_side[2 * F] = sides[F][0];
-    m.face_side[2 * F + 1] = sides[F][1];
+    m.face_side[2 * F + 1] = -1;
+    m.face_bc[F] = (int8_t)kind;
+    ++m.n_boundary;
   }
 
   // integer node coordinates (units h/p) and face-node matching relative to the
@@ -143,6 +177,7 @@ int build_mesh(int dim, const int64_t n_[3], const double lo_[3], const double h
     }
     if ((int)pos.size() != Nf) return -3;
     for (int s = 0; s < 2; ++s) {
+      if (m.face_side[2 * F + s] < 0) continue;
       int64_t e = m.face_side[2 * F + s] / nF;
       int f = m.face_side[2 * F + s] % nF;
       V3 A = face_min(e, f);

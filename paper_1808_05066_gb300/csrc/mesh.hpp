@@ -11,6 +11,9 @@
 //       swapped when the determinant is negative; e = 6c + t.
 // Global faces are numbered in order of first appearance over (element, local face);
 // the first element is the owner and its face-node order is the canonical one.
+// An axis is periodic (faces on its two sides identified) or bounded: then the faces on
+// its sides have one side each (face_side[2F+1] = -1) and carry the boundary type of
+// their side (face_bc, HDG_BC_*).
 #pragma once
 #include <cstdint>
 #include <vector>
@@ -28,7 +31,10 @@ struct Mesh {
   std::vector<int64_t> lat;        // [E][nF][dim] integer vertex lattice coordinates
   std::vector<int32_t> face_of;    // [E][nF]
   std::vector<int32_t> fnode_map;  // [E][nF][Nf] canonical face-node index
-  std::vector<int32_t> face_side;  // [F][2] = e * nF + f of the two sides (owner first)
+  std::vector<int32_t> face_side;  // [F][2] = e * nF + f of the two sides (owner first; -1: boundary)
+  int bc[3][2] = {{0, 0}, {0, 0}, {0, 0}};  // per axis, (lo, hi) boundary type; 0 = periodic
+  std::vector<int8_t> face_bc;     // [F] boundary type of the face (0: interior)
+  int64_t n_boundary = 0;          // faces with one side
   std::vector<double> geo;         // [E][geo_stride]: Jinv (dim*dim, [r][k]), |det J|,
                                    //   per face: normal (dim), face_jac (1)
   int geo_stride = 0;
@@ -42,8 +48,10 @@ struct Mesh {
   std::vector<double> xedg;        // [n_edg][dim] node coordinates (first appearance)
 };
 
-// Returns 0 on success; -1 on invalid arguments.
-int build_mesh(int dim, const int64_t n[3], const double lo[3], const double hi[3], int p, int K, Mesh& m);
+// Returns 0 on success; -1 on invalid arguments. bc: per axis (lo, hi) boundary type
+// (HDG_BC_*), or null for all periodic; an axis is periodic on both sides or on neither.
+int build_mesh(int dim, const int64_t n[3], const double lo[3], const double hi[3], int p, int K, Mesh& m,
+               const int32_t* bc = nullptr);
 // The continuous (EDG) numbering of the skeleton nodes of a built mesh: identifies the face
 // nodes of all elements by their integer coordinates modulo the period.
 void build_edg(Mesh& m);

@@ -360,8 +360,8 @@ int hdg_mlp_features(hdg_ctx_t ctx, const double* V, const double* Vhat, const d
     set_error("hdg_mlp_features: null argument");
     return HDG_ERR_INVALID_ARG;
   }
-  if (ctx->scheme) {
-    set_error("hdg_mlp_features: the per-face network works on face traces (HDG) only");
+  if (ctx->scheme || !ctx->h_bface.empty()) {
+    set_error("hdg_mlp_features: the per-face network works on two-sided face traces (periodic HDG) only");
     return HDG_ERR_UNSUPPORTED;
   }
   k_mlp_features<<<nb(ctx->ntrace), 256, 0, (cudaStream_t)stream>>>(
@@ -465,8 +465,8 @@ int hdg_mlp_apply_trace(hdg_ctx_t ctx, const double* Vhat, const double* dvh1, c
     set_error("hdg_mlp_apply_trace: null argument");
     return HDG_ERR_INVALID_ARG;
   }
-  if (ctx->scheme) {
-    set_error("hdg_mlp_apply_trace: the per-face network works on face traces (HDG) only");
+  if (ctx->scheme || !ctx->h_bface.empty()) {
+    set_error("hdg_mlp_apply_trace: the per-face network works on two-sided face traces (periodic HDG) only");
     return HDG_ERR_UNSUPPORTED;
   }
   k_mlp_apply<<<nb(ctx->ntrace), 256, 0, (cudaStream_t)stream>>>(Vhat, dvh1, pred, tscale, tmean, ctx->F,

@@ -111,6 +111,7 @@ __global__ void k_trace_gather(const int* fs_elem, const int* fs_loc, int64_t F,
     double s = 0.0;
     for (int side = 0; side < 2; ++side) {
       int64_t e = fs_elem[2 * Fi + side];
+      if (e < 0) continue;  // a boundary face has one side
       int loc = fs_loc[(2 * Fi + side) * NFN + c];
       s += ge[e * NT + loc * M + i];
     }
@@ -195,6 +196,7 @@ __global__ void k_sumsq_trace_residual(const double* R, const int* fs_elem, cons
     double v = 0.0;
     for (int side = 0; side < 2; ++side) {
       int64_t e = fs_elem[2 * Fi + side];
+      if (e < 0) continue;
       int loc = fs_loc[(2 * Fi + side) * NFN + c];
       v += R[e * (int64_t)(NV + NT) + NV + loc * M + i];
     }
@@ -279,6 +281,7 @@ __global__ void k_face_block_factor(const double* S, const int* fs_elem, const i
     double s = 0.0;
     for (int side = 0; side < 2; ++side) {
       int64_t e = fs_elem[2 * Fi + side];
+      if (e < 0) continue;
       int lr = fs_loc[(2 * Fi + side) * NFN + cr] * M + ir;
       int lc = fs_loc[(2 * Fi + side) * NFN + cc] * M + ic;
       s += S[e * (int64_t)NT * NT + (int64_t)lr * NT + lc];

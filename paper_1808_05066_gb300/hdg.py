@@ -47,8 +47,12 @@ EXPORTED = [
     "hdg_mlp_train_step", "hdg_mlp_apply_trace", "hdg_mlp_stats", "hdg_mlp_standardize", "hdg_mlp_target",
     "hdg_axpby", "hdg_assemble_condense_host", "hdg_assemble_condense_graph", "hdg_newton_solve",
     "hdg_ctx_set_refinement", "hdg_ctx_graph_replays", "hdg_ctx_set_trace_solver", "hdg_dirk3_step",
-    "hdg_entropy_production", "hdg_mesh_copy_trace_map",
+    "hdg_entropy_production", "hdg_mesh_copy_trace_map", "hdg_mesh_copy_face_bc", "hdg_ctx_set_boundary_state",
 ]
+HDG_BC_PERIODIC = 0
+HDG_BC_STATE = 1
+HDG_BC_SLIP = 2
+_BC_NAMES = {"periodic": HDG_BC_PERIODIC, "state": HDG_BC_STATE, "slip": HDG_BC_SLIP}
 HDG_KERNEL_POINTWISE = 0
 HDG_KERNEL_ASSEMBLE = 1
 HDG_KERNEL_CONDENSE = 2
@@ -85,7 +89,7 @@ class hdg_mesh_info(ctypes.Structure):
                 ("Np", c_int32), ("Nf", c_int32), ("nF", c_int32), ("NG", c_int32), ("NGF", c_int32),
                 ("nv", c_int32), ("nt", c_int32), ("geo_stride", c_int32),
                 ("n_elem", c_int64), ("n_faces", c_int64), ("n_trace", c_int64),
-                ("scheme", c_int32), ("n_trace_nodes", c_int64)]
+                ("scheme", c_int32), ("n_trace_nodes", c_int64), ("n_boundary_faces", c_int64)]
 
 
 def _load():
@@ -96,7 +100,9 @@ def _load():
     P = c_void_p
     sig = {
         "hdg_mesh_create": (c_int, [c_int, POINTER(c_int64), POINTER(c_double), POINTER(c_double), c_void_p, c_int,
-                                    c_int, c_int, POINTER(c_void_p)]),
+                                    c_int, c_int, c_void_p, POINTER(c_void_p)]),
+        "hdg_mesh_copy_face_bc": (c_int, [P, P]),
+        "hdg_ctx_set_boundary_state": (c_int, [P, P, P]),
         "hdg_mesh_destroy": (None, [P]),
         "hdg_mesh_get_info": (c_int, [P, POINTER(hdg_mesh_info)]),
         "hdg_mesh_copy_topology": (c_int, [P, P, P, P]),
@@ -178,15 +184,39 @@ def _stream(s):
 
 
 # ------------------------------------------------------------------ raw entry points
-def hdg_mesh_create(dim, n, lo, hi, p, quad_points=0, p_per_elem=None, scheme=HDG_SCHEME_HDG):
-    """p_per_elem: None (uniform p) or an int8 array [E] of per-element degrees."""
+def _bc_array(dim, bc):
+    """None, or per axis a pair (lo, hi) of HDG_BC_* codes or names -> int32 [2 dim]."""
+    if bc is None:
+        return None
+    out = [(_BC_NAMES[s] if isinstance(s, str) else int(s)) for pair in bc for s in pair]
+    if len(out) != 2 * dim:
+        raise ValueError("bc: one (lo, hi) pair per axis")
+    return np.array(out, dtype=np.int32)
+
+
+def hdg_mesh_create(dim, n, lo, hi, p, quad_points=0, p_per_elem=None, scheme=HDG_SCHEME_HDG, bc=None):
+    """p_per_elem: None (uniform p) or an int8 array [E] of per-element degrees; bc: None (periodic)
+    or per axis a (lo, hi) pair of boundary types ("periodic", "state", "slip" or HDG_BC_*)."""
     n3 = (c_int64 * 3)(*(list(n) + [1] * (3 - len(n))))
     lo3 = (c_double * 3)(*(list(lo) + [0.0] * (3 - len(lo))))
     hi3 = (c_double * 3)(*(list(hi) + [1.0] * (3 - len(hi))))
     pe = None if p_per_elem is None else np.ascontiguousarray(p_per_elem, dtype=np.int8)
+    bca = _bc_array(dim, bc)
     h = c_void_p()
-    _check(_lib.hdg_mesh_create(dim, n3, lo3, hi3, _ptr(pe), p, scheme, quad_points, byref(h)))
+    _check(_lib.hdg_mesh_create(dim, n3, lo3, hi3, _ptr(pe), p, scheme, quad_points, _ptr(bca), byref(h)))
     return h.value
+
+
+def hdg_mesh_copy_face_bc(mesh):
+    i = hdg_mesh_get_info(mesh)
+    out = np.zeros(i["n_faces"], np.int8)
+    _check(_lib.hdg_mesh_copy_face_bc(mesh, _ptr(out)))
+    return out
+
+
+def hdg_ctx_set_boundary_state(ctx, Vb, stream=None):
+    """Vb: device tensor in the trace layout [F][Nf][m] (read on the HDG_BC_STATE faces)."""
+    _check(_lib.hdg_ctx_set_boundary_state(ctx, _ptr(Vb), _stream(stream)))
 
 
 def hdg_mesh_destroy(mesh):
@@ -443,15 +473,18 @@ def hdg_profile_read(ctx, kernel_class=-1):
 class Mesh:
     """Owns an hdg_mesh_t; exposes its info and host copies of its tables."""
 
-    def __init__(self, dim, n, lo, hi, p, quad_points=0, p_per_elem=None, scheme=HDG_SCHEME_HDG):
+    def __init__(self, dim, n, lo, hi, p, quad_points=0, p_per_elem=None, scheme=HDG_SCHEME_HDG, bc=None):
         n = [n] * dim if np.isscalar(n) else list(n)
         lo = [lo] * dim if np.isscalar(lo) else list(lo)
         hi = [hi] * dim if np.isscalar(hi) else list(hi)
-        self.handle = hdg_mesh_create(dim, n, lo, hi, p, quad_points, p_per_elem, scheme)
+        self.handle = hdg_mesh_create(dim, n, lo, hi, p, quad_points, p_per_elem, scheme, bc)
         self.info = hdg_mesh_get_info(self.handle)
 
     def topology(self):
         return hdg_mesh_copy_topology(self.handle)
+
+    def face_bc(self):
+        return hdg_mesh_copy_face_bc(self.handle)
 
     def trace_map(self):
         return hdg_mesh_copy_trace_map(self.handle)

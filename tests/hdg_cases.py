@@ -31,6 +31,7 @@ class Case:
     stabilization: str = "slf"  # "slf" (Eq. sLxF) or "s" (Eq. symStab)
     vinf: tuple = (1.0, 0.0)    # free stream of the vortex fields
     psi: float = 5.0            # strength of the single vortex
+    bc: tuple = None            # per axis (lo, hi) boundary types; None: periodic
 
     @property
     def lo(self):
@@ -57,11 +58,13 @@ def oracle_setup(case: Case):
     from oracle import physics as ph
     from oracle.hdg import Problem, consistent_Q, interpolate_state
     from oracle.mesh import Mesh
-    mesh = Mesh(case.dim, case.n, 0.0, case.L, case.p)
+    mesh = Mesh(case.dim, case.n, 0.0, case.L, case.p, bc=case.bc)
     phys = ph.Physics(mach=case.mach, reynolds=case.reynolds, prandtl=case.prandtl, mu_exponent=case.mu_exponent,
                        stabilization=case.stabilization)
     prob = Problem(mesh, phys, viscous_flux_option=case.visc_flux, scheme=case.scheme)
     V, Vh = interpolate_state(prob, case.prim)
+    if case.bc is not None:
+        prob.boundary_state = Vh.copy()     # the unperturbed trace: the state faces' v_b
     if case.noise:
         Vh = wl.perturb(Vh, case.noise, case.seed)
     Q = consistent_Q(prob, V, Vh)
@@ -82,7 +85,7 @@ class GpuCase:
         from paper_1808_05066_gb300 import hdg
         self.hdg, self.torch, self.case = hdg, torch, case
         self.mesh = hdg.Mesh(case.dim, case.n, 0.0, case.L, case.p,
-                             scheme=hdg.HDG_SCHEME_EDG if case.scheme == "edg" else hdg.HDG_SCHEME_HDG)
+                             scheme=hdg.HDG_SCHEME_EDG if case.scheme == "edg" else hdg.HDG_SCHEME_HDG, bc=case.bc)
         self.ctx = hdg.Context(self.mesh, 1.4, case.mach, case.reynolds, case.prandtl, device,
                                mu_exponent=case.mu_exponent, visc_flux=case.visc_flux,
                                stabilization=1 if case.stabilization == "s" else 0)
@@ -93,6 +96,9 @@ class GpuCase:
         i = self.info
         self.V = self.to_entropy(prim_array(case, xnode))
         Vh = self.to_entropy(prim_array(case, xfnode))
+        if case.bc is not None:
+            self.Vb = Vh.clone()
+            hdg.hdg_ctx_set_boundary_state(self.ctx.handle, self.Vb)
         if case.noise:
             Vh = torch.from_numpy(wl.perturb(Vh.cpu().numpy(), case.noise, case.seed)).to(dev)
         self.Vhat = Vh.contiguous()

@@ -43,6 +43,20 @@ def test_invalid_arguments_are_rejected():
     with pytest.raises(hdg.HdgError) as ei:     # a degree outside 1..4 in p_per_elem
         hdg.hdg_mesh_create(2, [2, 2], [0, 0], [1, 1], 2, p_per_elem=np.array([2] * 7 + [9], np.int8))
     assert ei.value.code == hdg.HDG_ERR_INVALID_ARG
+    with pytest.raises(hdg.HdgError) as ei:     # an axis periodic on one side only
+        hdg.hdg_mesh_create(2, [2, 2], [0, 0], [1, 1], 2, bc=[("periodic", "state"), ("periodic", "periodic")])
+    assert ei.value.code == hdg.HDG_ERR_INVALID_ARG
+    with pytest.raises(hdg.HdgError) as ei:     # an unknown boundary type
+        hdg.hdg_mesh_create(2, [2, 2], [0, 0], [1, 1], 2, bc=[(5, 5), (0, 0)])
+    assert ei.value.code == hdg.HDG_ERR_INVALID_ARG
+    with pytest.raises(hdg.HdgError) as ei:     # boundaries are built for the HDG trace space only
+        hdg.hdg_mesh_create(2, [2, 2], [0, 0], [1, 1], 2, scheme=hdg.HDG_SCHEME_EDG,
+                            bc=[("state", "state"), ("periodic", "periodic")])
+    assert ei.value.code == hdg.HDG_ERR_UNSUPPORTED
+    m = hdg.Mesh(2, 2, 0.0, 1.0, 3, bc=[("slip", "slip"), ("periodic", "periodic")])
+    with pytest.raises(hdg.HdgError) as ei:     # the slip wall is defined for the Euler equations only
+        hdg.hdg_ctx_create(m.handle, 1.4, 0.3, 100.0, 0.72, 0)
+    assert ei.value.code == hdg.HDG_ERR_UNSUPPORTED
 
 
 @pytest.mark.parametrize("dim,n,p", [(2, 3, 2), (2, 2, 4), (3, 2, 3), (3, 1, 2)])
@@ -78,21 +92,31 @@ def test_unbuilt_variants_are_reported():
     assert m.info["n_elem"] == 6 and m.info["p"] == 2
 
 
+_BOUNDED = {2: [("state", "slip"), ("periodic", "periodic")],
+            3: [("periodic", "periodic"), ("slip", "slip"), ("state", "state")]}
+
+
+@pytest.mark.parametrize("bounded", [False, True])
 @pytest.mark.parametrize("dim,n,p", [(2, 3, 2), (2, 2, 4), (3, 2, 3), (3, 1, 1), (3, 3, 2)])
-def test_mesh_matches_oracle(dim, n, p):
+def test_mesh_matches_oracle(dim, n, p, bounded):
+    """Topology, face types and geometry of the library's mesh against the oracle's, periodic
+    and with bounded axes (one-sided faces on the walls)."""
     hdg = _lib()
     L = 2.5
-    m = hdg.Mesh(dim, n, 0.0, L, p)
-    o = OMesh(dim, n, 0.0, L, p)
+    bc = _BOUNDED[dim] if bounded else None
+    m = hdg.Mesh(dim, n, 0.0, L, p, bc=bc)
+    o = OMesh(dim, n, 0.0, L, p, bc=bc)
     info = m.info
     assert info["n_elem"] == o.E and info["n_faces"] == o.nFaces
     assert info["Np"] == o.ref.Np and info["Nf"] == o.ref.Nf
     assert info["NG"] == len(o.ref.qw) and info["NGF"] == len(o.ref.fqw)
+    assert info["n_boundary_faces"] == int(np.sum(o.face_bc != 0)) and (info["n_boundary_faces"] > 0) == bounded
     face_of, fnode_map, face_side = m.topology()
     assert np.array_equal(face_of, o.face_of)
     assert np.array_equal(fnode_map, o.fnode_map)
-    sides = np.array([[e * o.ref.nF + f for (e, f) in s] for s in o.face_elems])
+    sides = np.array([[e * o.ref.nF + f for (e, f) in s] + [-1] * (2 - len(s)) for s in o.face_elems])
     assert np.array_equal(face_side, sides)
+    assert np.array_equal(m.face_bc(), o.face_bc)
     xnode, xfnode, geo = m.coords()
     assert np.allclose(xnode, o.xnode, atol=1e-13)
     d = dim
