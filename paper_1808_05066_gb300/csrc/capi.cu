@@ -384,7 +384,7 @@ void hdg_ctx_destroy(hdg_ctx_t c) {
   if (!c) return;
   DeviceGuard guard(c->device);
   void* bufs[] = {c->d_tab, c->d_tab_df, c->d_itab, c->d_tgidx, c->d_geo, c->d_fs_elem, c->d_fs_loc, c->d_scr,
-                  c->d_sw, c->d_pc, c->d_pcpiv, c->d_dense, c->d_dpiv, c->d_red, c->d_S,
+                  c->d_sw, c->d_pc, c->d_dense, c->d_dpiv, c->d_red, c->d_S,
                   c->d_g, c->d_recov, c->d_R, c->d_dV, c->d_dVh, c->d_status, c->d_hist, c->d_V0,
                   c->d_Vh0, c->d_feat, c->d_pred, c->d_dirk, c->d_ent, c->d_tr_ptr, c->d_tr_occ, c->d_pcn,
                   c->d_bface, c->d_bkind, c->d_vb};

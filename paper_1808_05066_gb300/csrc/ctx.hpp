@@ -55,8 +55,7 @@ struct hdg_ctx {
   // solver scratch
   double* d_sw = nullptr;    // GMRES / matvec workspace
   size_t sw_bytes = 0;
-  double* d_pc = nullptr;    // face-block Jacobi factors [F][B][B]
-  int* d_pcpiv = nullptr;    // [F][B]
+  double* d_pc = nullptr;    // face-block Jacobi: inverse face blocks, transposed [F][B][B]
   double* d_dense = nullptr; // dense trace matrix for the direct solver
   int* d_dpiv = nullptr;
   size_t dense_n = 0;

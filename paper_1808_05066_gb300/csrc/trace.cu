@@ -133,8 +133,12 @@ __global__ void k_node_gather(const int* ptr, const int* occ, int64_t nnode, int
   }
 }
 
-// w_e = S_e x_e, one warp per row, x_e gathered into shared memory.
-__global__ void k_elem_matvec(const double* S, const double* x, const int* tgidx, int NT, int M, double* w) {
+// w_e = S_e x_e, x_e gathered into shared memory. S streams through once per product (it is
+// far larger than L2), so each warp keeps kMvRows rows' loads in flight (independent partial
+// sums) and the loads bypass L1 with the streaming hint.
+constexpr int kMvRows = 5;
+__global__ void __launch_bounds__(256) k_elem_matvec(const double* S, const double* x, const int* tgidx, int NT,
+                                                     int M, double* w) {
   extern __shared__ double xs[];
   const int64_t e = blockIdx.x;
   const int nfc = NT / M;
@@ -145,11 +149,23 @@ __global__ void k_elem_matvec(const double* S, const double* x, const int* tgidx
   __syncthreads();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const double* Se = S + e * (int64_t)NT * NT;
-  for (int r = wid; r < NT; r += nw) {
-    double s = 0.0;
-    for (int c = lane; c < NT; c += 32) s += Se[(int64_t)r * NT + c] * xs[c];
-    s = warp_sum(s);
-    if (lane == 0) w[e * NT + r] = s;
+  for (int r0 = wid * kMvRows; r0 < NT; r0 += nw * kMvRows) {
+    double s[kMvRows];
+#pragma unroll
+    for (int u = 0; u < kMvRows; ++u) s[u] = 0.0;
+#pragma unroll 2
+    for (int c = lane; c < NT; c += 32) {
+      const double xc = xs[c];
+#pragma unroll
+      for (int u = 0; u < kMvRows; ++u)
+        if (r0 + u < NT) s[u] += __ldcs(Se + (int64_t)(r0 + u) * NT + c) * xc;
+    }
+#pragma unroll
+    for (int u = 0; u < kMvRows; ++u) s[u] = warp_sum(s[u]);
+    if (lane == 0)
+#pragma unroll
+      for (int u = 0; u < kMvRows; ++u)
+        if (r0 + u < NT) w[e * NT + r0 + u] = s[u];
   }
 }
 
@@ -268,11 +284,15 @@ __global__ void k_multiaxpy_add(int64_t n, const double* basis, int64_t ld, cons
 }
 
 // ---------------------------------------------------------------- face-block Jacobi
-// K_FF (canonical order) = sum_sides S_e[loc rows, loc cols]; LU with partial pivoting.
+// K_FF (canonical order) = sum_sides S_e[loc rows, loc cols]; LU with partial pivoting, then
+// the inverse column by column (thread t: K_FF x = e_t), stored transposed, fac[F][j][i] =
+// K_FF^{-1}[i][j], so that applying it reads whole rows of fac (B <= kMaxFaceBlock).
+constexpr int kMaxFaceBlock = 64;
 __global__ void k_face_block_factor(const double* S, const int* fs_elem, const int* fs_loc, int NFN, int M, int NT,
-                                    double* fac, int* piv) {
-  extern __shared__ double A[];  // [B][B]
+                                    double* fac) {
+  extern __shared__ double A[];  // [B][B], then X [B][B] (column t of the inverse in X[.][t])
   __shared__ int s_p;
+  __shared__ int s_piv[kMaxFaceBlock];
   const int B = NFN * M;
   const int64_t Fi = blockIdx.x;
   for (int t = threadIdx.x; t < B * B; t += blockDim.x) {
@@ -310,7 +330,7 @@ __global__ void k_face_block_factor(const double* S, const int* fs_elem, const i
       }
       if (threadIdx.x == 0) {
         s_p = bi;
-        piv[Fi * B + k] = bi;
+        s_piv[k] = bi;
       }
     }
     __syncthreads();
@@ -333,44 +353,56 @@ __global__ void k_face_block_factor(const double* S, const int* fs_elem, const i
     }
     __syncthreads();
   }
-  for (int t = threadIdx.x; t < B * B; t += blockDim.x) fac[Fi * (int64_t)B * B + t] = A[t];
+  double* X = A + B * B;
+  for (int t = threadIdx.x; t < B; t += blockDim.x) {  // column t of the inverse
+    for (int i = 0; i < B; ++i) X[i * B + t] = i == t ? 1.0 : 0.0;
+    for (int k = 0; k < B; ++k) {  // the row swaps of the factorisation, in order
+      const int p = s_piv[k];
+      if (p != k) {
+        const double tmp = X[k * B + t];
+        X[k * B + t] = X[p * B + t];
+        X[p * B + t] = tmp;
+      }
+    }
+    for (int k = 0; k < B; ++k) {  // unit lower triangle
+      const double xk = X[k * B + t];
+      for (int r = k + 1; r < B; ++r) X[r * B + t] -= A[r * B + k] * xk;
+    }
+    for (int k = B - 1; k >= 0; --k) {  // upper triangle
+      const double d = A[k * B + k];
+      const double xk = d != 0.0 ? X[k * B + t] / d : 0.0;
+      X[k * B + t] = xk;
+      for (int r = 0; r < k; ++r) X[r * B + t] -= A[r * B + k] * xk;
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < B * B; t += blockDim.x) {
+    const int j = t / B, i = t % B;
+    fac[Fi * (int64_t)B * B + t] = X[i * B + j];
+  }
 }
 
-// z_F = K_FF^{-1} r_F, one warp per face
-__global__ void k_face_block_solve(const double* fac, const int* piv, int64_t F, int B, const double* r,
-                                   double* z) {
+// z_F = K_FF^{-1} r_F from the stored inverse (fac[F][j][i] = K_FF^{-1}[i][j]), one warp per face:
+// lane i accumulates row i over j, every load a coalesced run of one stored row
+__global__ void k_face_block_apply(const double* fac, int64_t F, int B, const double* r, double* z) {
   extern __shared__ double xs[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int64_t Fi = (int64_t)blockIdx.x * nw + wid;
   if (Fi >= F) return;
-  double* x = xs + wid * B;
-  for (int t = lane; t < B; t += 32) x[t] = r[Fi * B + t];
-  __syncwarp();
-  const int* P = piv + Fi * B;
-  if (lane == 0)
-    for (int k = 0; k < B; ++k) {
-      int p = P[k];
-      if (p != k) {
-        double t = x[k];
-        x[k] = x[p];
-        x[p] = t;
-      }
-    }
+  double* rs = xs + wid * B;
+  for (int t = lane; t < B; t += 32) rs[t] = r[Fi * B + t];
   __syncwarp();
   const double* A = fac + Fi * (int64_t)B * B;
-  for (int k = 0; k < B; ++k) {
-    double xk = x[k];
-    for (int rr = k + 1 + lane; rr < B; rr += 32) x[rr] -= A[rr * B + k] * xk;
-    __syncwarp();
+  const bool h0 = lane < B, h1 = lane + 32 < B;
+  double a0 = 0.0, a1 = 0.0;
+#pragma unroll 5
+  for (int j = 0; j < B; ++j) {
+    const double rj = rs[j];
+    if (h0) a0 += A[j * B + lane] * rj;
+    if (h1) a1 += A[j * B + 32 + lane] * rj;
   }
-  for (int k = B - 1; k >= 0; --k) {
-    if (lane == 0) x[k] /= A[k * B + k];
-    __syncwarp();
-    double xk = x[k];
-    for (int rr = lane; rr < k; rr += 32) x[rr] -= A[rr * B + k] * xk;
-    __syncwarp();
-  }
-  for (int t = lane; t < B; t += 32) z[Fi * B + t] = x[t];
+  if (h0) z[Fi * B + lane] = a0;
+  if (h1) z[Fi * B + 32 + lane] = a1;
 }
 
 // ---------------------------------------------------------------- EDG node-block Jacobi
@@ -703,9 +735,12 @@ static int gmres_solve(hdg_ctx* ctx, const double* S, const double* g, double* x
   }
   if (ctx->scheme) {
     if (!ctx->d_pcn) HDG_CK(cudaMalloc(&ctx->d_pcn, sizeof(double) * ctx->n_tnodes * ctx->M * ctx->M));
-  } else if (!ctx->d_pc) {
-    HDG_CK(cudaMalloc(&ctx->d_pc, sizeof(double) * ctx->F * B * B));
-    HDG_CK(cudaMalloc(&ctx->d_pcpiv, sizeof(int) * ctx->F * B));
+  } else {
+    if (B > kMaxFaceBlock || 2 * sizeof(double) * B * B > 48 * 1024) {  // factor + inverse in shared memory
+      set_error("trace_solve: face block larger than the preconditioner supports");
+      return HDG_ERR_UNSUPPORTED;
+    }
+    if (!ctx->d_pc) HDG_CK(cudaMalloc(&ctx->d_pc, sizeof(double) * ctx->F * B * B));
   }
   int rc = ensure_red(ctx);
   if (rc) return rc;
@@ -718,9 +753,8 @@ static int gmres_solve(hdg_ctx* ctx, const double* S, const double* g, double* x
     k_node_block_factor<<<nblocks(ctx->n_tnodes), kThreads, 0, s>>>(S, ctx->d_tr_ptr, ctx->d_tr_occ, ctx->n_tnodes,
                                                                     ctx->M, ctx->NT, ctx->d_pcn);
   else  // HDG: face-block Jacobi
-    k_face_block_factor<<<(unsigned)ctx->F, 64, sizeof(double) * B * B, s>>>(S, ctx->d_fs_elem, ctx->d_fs_loc,
-                                                                           ctx->NFN, ctx->M, ctx->NT, ctx->d_pc,
-                                                                           ctx->d_pcpiv);
+    k_face_block_factor<<<(unsigned)ctx->F, 64, 2 * sizeof(double) * B * B, s>>>(S, ctx->d_fs_elem, ctx->d_fs_loc,
+                                                                               ctx->NFN, ctx->M, ctx->NT, ctx->d_pc);
   rc = launch_trace_rhs(ctx, g, b, s);
   if (rc) return rc;
   const int wpb = 8;
@@ -728,8 +762,8 @@ static int gmres_solve(hdg_ctx* ctx, const double* S, const double* g, double* x
     if (ctx->scheme)
       k_node_block_apply<<<nblocks(n), kThreads, 0, s>>>(ctx->d_pcn, ctx->n_tnodes, ctx->M, r, z);
     else
-      k_face_block_solve<<<(unsigned)((ctx->F + wpb - 1) / wpb), 32 * wpb, sizeof(double) * wpb * B, s>>>(
-          ctx->d_pc, ctx->d_pcpiv, ctx->F, B, r, z);
+      k_face_block_apply<<<(unsigned)((ctx->F + wpb - 1) / wpb), 32 * wpb, sizeof(double) * wpb * B, s>>>(
+          ctx->d_pc, ctx->F, B, r, z);
   };
   auto dot_host = [&](const double* basis, int nb, const double* v, double* out) -> int {
     HDG_CK(cudaMemsetAsync(ctx->d_red, 0, sizeof(double) * nb, s));
