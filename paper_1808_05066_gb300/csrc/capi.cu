@@ -387,7 +387,7 @@ void hdg_ctx_destroy(hdg_ctx_t c) {
                   c->d_sw, c->d_pc, c->d_dense, c->d_dpiv, c->d_red, c->d_S,
                   c->d_g, c->d_recov, c->d_R, c->d_dV, c->d_dVh, c->d_status, c->d_hist, c->d_V0,
                   c->d_Vh0, c->d_feat, c->d_pred, c->d_dirk, c->d_ent, c->d_tr_ptr, c->d_tr_occ, c->d_pcn,
-                  c->d_bface, c->d_bkind, c->d_vb};
+                  c->d_bface, c->d_bkind, c->d_vb, c->d_mv_err, c->d_Sdf};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (c->h_red) cudaFreeHost(c->h_red);

@@ -33,48 +33,15 @@
 // MMAs drain (with a bounded wait), frees its TMEM and returns.
 #pragma once
 #include "condense_tc.cuh"
+#include "ptx_async.cuh"
 
 namespace hdg {
 
 // ---------------------------------------------------------------------------------------------
-// PTX wrappers
+// PTX wrappers (the mbarrier and bulk-copy ones are in ptx_async.cuh)
 // ---------------------------------------------------------------------------------------------
-HDG_DEVI uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-HDG_DEVI void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-HDG_DEVI bool mbar_try(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Waits for the phase of the given parity to complete; gives up after `limit` polls.
-HDG_DEVI bool mbar_wait(uint64_t* bar, uint32_t parity, int limit) {
-  for (int i = 0; i < limit; ++i) {
-    if (mbar_try(bar, parity)) return true;
-    if (i > 64) __nanosleep(256);
-  }
-  return false;
-}
-HDG_DEVI void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-// Bulk asynchronous copy global -> shared of `bytes` (multiple of 16, both addresses 16-byte
-// aligned), completing as transaction bytes on `bar`.
-HDG_DEVI void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                   smem_u32(dst)),
-               "l"(src), "r"(bytes), "r"(smem_u32(bar))
-               : "memory");
-}
 HDG_DEVI void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 HDG_DEVI void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-HDG_DEVI void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 // Shared-memory matrix descriptor: start address, leading / stride byte offsets (16-byte units),
 // the fixed version bits 0b001 at [46, 49), no swizzle.

@@ -114,7 +114,12 @@ struct hdg_ctx {
   int newton_max_it = 600;
   // dynamic shared-memory limits raised on this context's device (cudaFuncSetAttribute
   // applies per device; a context belongs to one device)
-  bool attr_fp64 = false, attr_mixed = false, attr_noalloc = false;
+  bool attr_fp64 = false, attr_mixed = false, attr_noalloc = false, attr_matvec = false;
+  int num_sms = 0;               // SMs of the device (persistent grids)
+  int* d_mv_err = nullptr;       // set by the staged trace matvec when a copy wait gave up
+  void* d_Sdf = nullptr;         // double-float copy of S for the GMRES products [E][NT][NT]
+  size_t sdf_bytes = 0;
+  bool sdf_unavailable = false;  // no device memory for it: FP64 products throughout
   // measurement: launch counts per kernel class and (when enabled) event pairs
   bool prof = false;
   int64_t launches[HDG_KERNEL_CLASSES] = {0};

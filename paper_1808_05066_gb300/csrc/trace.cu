@@ -12,6 +12,8 @@
 #include <vector>
 
 #include "ctx.hpp"
+#include "dfloat.cuh"
+#include "ptx_async.cuh"
 
 namespace hdg {
 
@@ -119,6 +121,88 @@ __global__ void k_trace_gather(const int* fs_elem, const int* fs_loc, int64_t F,
   }
 }
 
+// w_e = S_e x_e from the double-float copy of S, in double-float arithmetic on the FP32 pipe
+// (exact products by FMA residuals, two-sum accumulation; ~2^-46 relative per product). S streams
+// through shared memory by bulk asynchronous copies: a persistent CTA walks its elements
+// (e = blockIdx.x, + gridDim.x, ...) in chunks of CR rows (the last one ragged); thread 0 keeps
+// kMvStages chunks in flight on an mbarrier ring and refills a slot once every warp has passed it;
+// the warps read rows from shared memory (row r: lanes over columns, then a warp sum). No thread
+// issues a global load of S, so the copy engine sets the pace. A wait that gives up (about a
+// second) sets *err, writes NaN for the element and ends the CTA once its own copies have drained
+// (bounded as well).
+constexpr int kMvStages = 4;
+constexpr int kMvCtasPerSm = 3;
+constexpr int kMvChunkBytes = 12800;
+constexpr int kMvWaitPolls = 4 * 1000 * 1000;  // ~1 s at 256 ns per poll
+__global__ void __launch_bounds__(256) k_elem_matvec_df(const df2* __restrict__ Sdf, const double* x,
+                                                        const int* tgidx, int64_t E, int NT, int M, int CR,
+                                                        int nchunk, double* w, int* err) {
+  extern __shared__ __align__(128) df2 smf[];
+  __shared__ uint64_t full[kMvStages];
+  __shared__ int s_fail;
+  const size_t chunk_entries = (size_t)CR * NT;
+  df2* xs = smf + kMvStages * chunk_entries;  // [NT]
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+  const int64_t my_elems = blockIdx.x < E ? (E - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int64_t Q = my_elems * nchunk;  // chunks of this CTA, in order
+  if (Q == 0) return;
+  auto chunk_rows = [&](int k) { return k == nchunk - 1 ? NT - (nchunk - 1) * CR : CR; };
+  auto issue = [&](int64_t q) {  // thread 0: chunk q into slot q % kMvStages
+    const int64_t e = blockIdx.x + (q / nchunk) * gridDim.x;
+    const int k = (int)(q % nchunk);
+    const uint32_t bytes = (uint32_t)(sizeof(df2) * chunk_rows(k) * NT);
+    uint64_t* bar = full + (q % kMvStages);
+    mbar_arrive_expect_tx(bar, bytes);
+    bulk_g2s(smf + (q % kMvStages) * chunk_entries, Sdf + (e * NT + (int64_t)k * CR) * NT, bytes, bar);
+  };
+  if (tid == 0) {
+    for (int i = 0; i < kMvStages; ++i) mbar_init(full + i, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  int64_t issued = 0;
+  if (tid == 0)
+    for (; issued < Q && issued < kMvStages; ++issued) issue(issued);
+  for (int64_t q = 0; q < Q; ++q) {
+    const int64_t e = blockIdx.x + (q / nchunk) * gridDim.x;
+    const int k = (int)(q % nchunk);
+    if (tid == 0) s_fail = 0;
+    if (k == 0) {  // the element's x, gathered once (the previous element is done with xs)
+      const int nfc = NT / M;
+      for (int t = tid; t < NT; t += blockDim.x) xs[t] = df_from(x[(int64_t)tgidx[e * nfc + t / M] * M + t % M]);
+    }
+    __syncthreads();
+    if (!mbar_wait(full + (q % kMvStages), (uint32_t)((q / kMvStages) & 1), kMvWaitPolls)) s_fail = 1;
+    __syncthreads();
+    if (s_fail) {  // give up: NaN for the element, let the copies in flight land, leave
+      for (int t = tid; t < NT; t += blockDim.x) w[e * NT + t] = __longlong_as_double(0x7ff8000000000000LL);
+      if (tid == 0) {
+        atomicExch(err, 1);
+        for (int64_t p = q; p < issued; ++p)
+          mbar_wait(full + (p % kMvStages), (uint32_t)((p / kMvStages) & 1), kMvWaitPolls);
+      }
+      return;
+    }
+    const int rows = chunk_rows(k);
+    const df2* chunk = smf + (q % kMvStages) * chunk_entries;
+    for (int r = wid; r < rows; r += nw) {
+      dfacc a;
+      for (int c = lane; c < NT; c += 32) a.mac(chunk[r * NT + c], xs[c]);
+      for (int off = 16; off > 0; off >>= 1) {
+        const float oh = __shfl_down_sync(0xffffffffu, a.hi, off), ol = __shfl_down_sync(0xffffffffu, a.lo, off);
+        a.add(df2{oh, ol});
+      }
+      if (lane == 0) w[e * NT + (int64_t)k * CR + r] = a.value();
+    }
+    __syncthreads();  // every warp is done with the slot (and with xs for the last chunk)
+    if (tid == 0 && issued < Q) {
+      fence_proxy_async();
+      issue(issued);
+      ++issued;
+    }
+  }
+}
+
 // EDG (continuous trace): out[t][i] = scale * sum over the local occurrences o of node t of
 // ge[o * M + i], o = e NF NFN + f NFN + c (CSR ptr / occ)
 __global__ void k_node_gather(const int* ptr, const int* occ, int64_t nnode, int M, const double* ge, double scale,
@@ -133,12 +217,10 @@ __global__ void k_node_gather(const int* ptr, const int* occ, int64_t nnode, int
   }
 }
 
-// w_e = S_e x_e, x_e gathered into shared memory. S streams through once per product (it is
-// far larger than L2), so each warp keeps kMvRows rows' loads in flight (independent partial
-// sums) and the loads bypass L1 with the streaming hint.
-constexpr int kMvRows = 5;
-__global__ void __launch_bounds__(256) k_elem_matvec(const double* S, const double* x, const int* tgidx, int NT,
-                                                     int M, double* w) {
+// w_e = S_e x_e in FP64, one warp per row, x_e gathered into shared memory. On GB300 this is
+// bound by the FP64 pipe (one FMA per 8-byte entry), not by HBM: the GMRES iterations use the
+// double-float copy of S (k_elem_matvec_df) and keep this one for the residuals.
+__global__ void k_elem_matvec(const double* S, const double* x, const int* tgidx, int NT, int M, double* w) {
   extern __shared__ double xs[];
   const int64_t e = blockIdx.x;
   const int nfc = NT / M;
@@ -149,24 +231,19 @@ __global__ void __launch_bounds__(256) k_elem_matvec(const double* S, const doub
   __syncthreads();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const double* Se = S + e * (int64_t)NT * NT;
-  for (int r0 = wid * kMvRows; r0 < NT; r0 += nw * kMvRows) {
-    double s[kMvRows];
-#pragma unroll
-    for (int u = 0; u < kMvRows; ++u) s[u] = 0.0;
-#pragma unroll 2
-    for (int c = lane; c < NT; c += 32) {
-      const double xc = xs[c];
-#pragma unroll
-      for (int u = 0; u < kMvRows; ++u)
-        if (r0 + u < NT) s[u] += __ldcs(Se + (int64_t)(r0 + u) * NT + c) * xc;
-    }
-#pragma unroll
-    for (int u = 0; u < kMvRows; ++u) s[u] = warp_sum(s[u]);
-    if (lane == 0)
-#pragma unroll
-      for (int u = 0; u < kMvRows; ++u)
-        if (r0 + u < NT) w[e * NT + r0 + u] = s[u];
+  for (int r = wid; r < NT; r += nw) {
+    double s = 0.0;
+    for (int c = lane; c < NT; c += 32) s += Se[(int64_t)r * NT + c] * xs[c];
+    s = warp_sum(s);
+    if (lane == 0) w[e * NT + r] = s;
   }
+}
+
+// The double-float copy of S: entry i = hi + lo (hi = S rounded to FP32, lo = the rest rounded),
+// 8 bytes an entry as in FP64, about 48 significant bits.
+__global__ void k_split_df(const double* S, int64_t n, df2* out) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+    out[t] = df_from(S[t]);
 }
 
 // dV_e = -y_e - X_e P_e dVhat
@@ -589,8 +666,7 @@ int launch_trace_rhs(hdg_ctx* ctx, const double* g, double* rhs, cudaStream_t s)
   return HDG_OK;
 }
 
-int launch_trace_matvec(hdg_ctx* ctx, const double* S, const double* x, double* y, double* work, cudaStream_t s) {
-  k_elem_matvec<<<(unsigned)ctx->E, 256, sizeof(double) * ctx->NT, s>>>(S, x, ctx->d_tgidx, ctx->NT, ctx->M, work);
+static int launch_gather(hdg_ctx* ctx, const double* work, double* y, cudaStream_t s) {
   if (ctx->scheme)
     k_node_gather<<<nblocks(ctx->ntrace), kThreads, 0, s>>>(ctx->d_tr_ptr, ctx->d_tr_occ, ctx->n_tnodes, ctx->M, work,
                                                            1.0, y);
@@ -599,6 +675,33 @@ int launch_trace_matvec(hdg_ctx* ctx, const double* S, const double* x, double* 
                                                             ctx->NT, work, 1.0, y);
   HDG_CK(cudaGetLastError());
   return HDG_OK;
+}
+
+int launch_trace_matvec(hdg_ctx* ctx, const double* S, const double* x, double* y, double* work, cudaStream_t s) {
+  k_elem_matvec<<<(unsigned)ctx->E, 256, sizeof(double) * ctx->NT, s>>>(S, x, ctx->d_tgidx, ctx->NT, ctx->M, work);
+  return launch_gather(ctx, work, y, s);
+}
+
+// y = K x from the double-float copy of S (see k_elem_matvec_df)
+static int launch_trace_matvec_df(hdg_ctx* ctx, const df2* Sdf, const double* x, double* y, double* work,
+                                  cudaStream_t s) {
+  const int NT = ctx->NT;
+  const int CR = std::max(1, std::min(NT, kMvChunkBytes / (int)(sizeof(df2) * NT)));
+  const int nchunk = (NT + CR - 1) / CR;
+  const size_t smem = sizeof(df2) * ((size_t)kMvStages * CR * NT + NT);
+  if (!ctx->attr_matvec) {  // per context, hence per device
+    HDG_CK(cudaFuncSetAttribute(k_elem_matvec_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (!ctx->num_sms) HDG_CK(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device));
+    if (!ctx->d_mv_err) {
+      HDG_CK(cudaMalloc(&ctx->d_mv_err, sizeof(int)));
+      HDG_CK(cudaMemset(ctx->d_mv_err, 0, sizeof(int)));
+    }
+    ctx->attr_matvec = true;
+  }
+  const int64_t grid = std::min<int64_t>(ctx->E, (int64_t)kMvCtasPerSm * ctx->num_sms);
+  k_elem_matvec_df<<<(unsigned)grid, 256, smem, s>>>(Sdf, x, ctx->d_tgidx, ctx->E, NT, ctx->M, CR, nchunk, work,
+                                                      ctx->d_mv_err);
+  return launch_gather(ctx, work, y, s);
 }
 
 int launch_recover(hdg_ctx* ctx, const double* recov, const double* dVhat, double* dV, cudaStream_t s) {
@@ -755,6 +858,30 @@ static int gmres_solve(hdg_ctx* ctx, const double* S, const double* g, double* x
   else  // HDG: face-block Jacobi
     k_face_block_factor<<<(unsigned)ctx->F, 64, 2 * sizeof(double) * B * B, s>>>(S, ctx->d_fs_elem, ctx->d_fs_loc,
                                                                                ctx->NFN, ctx->M, ctx->NT, ctx->d_pc);
+  // the double-float copy of S for the Arnoldi products (the restart and final residuals use S
+  // itself); without room for it every product is the FP64 one
+  const size_t sdf_bytes = sizeof(df2) * (size_t)ctx->E * ctx->NT * ctx->NT;
+  if (ctx->sdf_bytes < sdf_bytes && !ctx->sdf_unavailable) {
+    if (ctx->d_Sdf) cudaFree(ctx->d_Sdf);
+    ctx->d_Sdf = nullptr;
+    ctx->sdf_bytes = 0;
+    if (cudaMalloc(&ctx->d_Sdf, sdf_bytes) == cudaSuccess) {
+      ctx->sdf_bytes = sdf_bytes;
+    } else {
+      cudaGetLastError();  // out of memory is not an error here
+      ctx->d_Sdf = nullptr;
+      ctx->sdf_unavailable = true;
+    }
+  }
+  const df2* Sdf = nullptr;
+  if (ctx->d_Sdf) {
+    const int64_t ns = (int64_t)ctx->E * ctx->NT * ctx->NT;
+    k_split_df<<<nblocks(ns), kThreads, 0, s>>>(S, ns, static_cast<df2*>(ctx->d_Sdf));
+    Sdf = static_cast<const df2*>(ctx->d_Sdf);
+  }
+  auto arnoldi_matvec = [&](const double* xin, double* yout) {
+    return Sdf ? launch_trace_matvec_df(ctx, Sdf, xin, yout, ew, s) : launch_trace_matvec(ctx, S, xin, yout, ew, s);
+  };
   rc = launch_trace_rhs(ctx, g, b, s);
   if (rc) return rc;
   const int wpb = 8;
@@ -789,8 +916,9 @@ static int gmres_solve(hdg_ctx* ctx, const double* S, const double* g, double* x
   double rel = 1.0;
   int total = 0;
   bool first = true;
-  while (total < max_it) {
-    // r = b - K x
+  // each cycle starts from the FP64 residual r = b - K x, which also decides convergence (the
+  // Arnoldi products may use the double-float copy of S, whose residual estimate is not trusted)
+  for (;;) {
     if (first) {
       HDG_CK(cudaMemcpyAsync(w, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
     } else {
@@ -805,14 +933,14 @@ static int gmres_solve(hdg_ctx* ctx, const double* S, const double* g, double* x
     if (rc) return rc;
     double beta = std::sqrt(rn2);
     rel = beta / bnorm;
-    if (rel <= rtol) break;
+    if (rel <= rtol || total >= max_it) break;
     k_scale_copy<<<nblocks(n), kThreads, 0, s>>>(n, 1.0 / beta, w, Vb);
     std::fill(gv.begin(), gv.end(), 0.0);
     gv[0] = beta;
     int j = 0;
     for (; j < m && total < max_it; ++j, ++total) {
       precond(Vb + (size_t)j * n, zt);
-      rc = launch_trace_matvec(ctx, S, zt, w, ew, s);
+      rc = arnoldi_matvec(zt, w);
       if (rc) return rc;
       // classical Gram-Schmidt, twice
       rc = dot_host(Vb, j + 1, w, h.data());
@@ -861,18 +989,18 @@ static int gmres_solve(hdg_ctx* ctx, const double* S, const double* g, double* x
     precond(w, zt);
     k_axpy<<<nblocks(n), kThreads, 0, s>>>(n, 1.0, zt, x);
     HDG_CK(cudaGetLastError());
-    if (rel <= rtol) break;
   }
-  // true residual
-  rc = launch_trace_matvec(ctx, S, x, w, ew, s);
-  if (rc) return rc;
-  k_scale_copy<<<nblocks(n), kThreads, 0, s>>>(n, -1.0, w, w);
-  k_axpy<<<nblocks(n), kThreads, 0, s>>>(n, 1.0, b, w);
-  double rn2;
-  rc = dot_host(w, 1, w, &rn2);
-  if (rc) return rc;
-  *final_res = std::sqrt(rn2) / bnorm;
+  *final_res = rel;  // of the last FP64 residual
   *iters = total;
+  if (ctx->d_mv_err) {  // a staged matvec gave up a copy wait
+    int flag = 0;
+    HDG_CK(cudaMemcpy(&flag, ctx->d_mv_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) {
+      HDG_CK(cudaMemset(ctx->d_mv_err, 0, sizeof(int)));
+      set_error("trace_solve: a bulk copy of the trace operator did not complete");
+      return HDG_ERR_TIMEOUT;
+    }
+  }
   if (*final_res > rtol * 10.0) {
     set_error("trace_solve: GMRES did not converge");
     return HDG_ERR_NOT_CONVERGED;
