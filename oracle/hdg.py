@@ -28,6 +28,13 @@ sparse direct solve), and the interior update is dx_e = -A^{-1}(R_l + B P_e dvha
 
 Interior unknown order: [q (node, component, direction); v (node, component)];
 trace order: [local face, face node, component].
+
+Mixed degrees (Mesh(p_elem=...); not in the paper, which uses one degree): element e uses its
+own P_{p_e} with the volume rule exact to degree 2 p_e + 1; its faces carry the trace of degree
+q_F = max(p_L, p_R) and are integrated with the rule exact to degree 2 PT_e + 1, PT_e = the
+largest degree of its faces. V, Q (and the BDF history) are then lists of per-element arrays,
+Vhat is [face nodes, m] with the nodes of face F at fnode_off[F] + canonical index, and the
+element's trace order is [face, its own face nodes, component].
 """
 from __future__ import annotations
 
@@ -40,6 +47,7 @@ import scipy.sparse.linalg as spla
 
 from . import physics as ph
 from .mesh import BC_PERIODIC, BC_SLIP, BC_STATE, Mesh
+from .refel import refel
 
 CSTEP = 1e-30
 
@@ -77,12 +85,17 @@ class Problem:
         if np.any(mesh.face_bc == BC_SLIP) and phys.viscous:
             raise ValueError("the slip boundary is defined for the Euler equations only")
         self.boundary_state = None      # [F, Nf, m] v_b at the canonical face nodes (BC_STATE faces)
+        self.mixed = mesh.p_elem is not None
+        if self.mixed and self.scheme != "hdg":
+            raise ValueError("mixed degrees are built for the HDG trace space")
         if self.scheme == "edg":
             self.n_edg, self.edg_index = mesh.edg_numbering()
         ref = mesh.ref
         self.d, self.m = mesh.dim, mesh.dim + 2
         self.Np, self.Nf, self.nF = ref.Np, ref.Nf, ref.nF
         self.viscous = phys.viscous
+        if self.mixed:
+            self.Nf = mesh.Nf_max
         self.n_i = self.Np * self.m * (1 + (self.d if self.viscous else 0))
         self.n_t = self.nF * self.Nf * self.m
         self._phi = ref.phi(ref.qp)
@@ -90,11 +103,36 @@ class Problem:
         self._phif = [ref.phi(x) for x in ref.fqp_ref]
         self._cache = {}
 
+    # -- element sizes (mixed degrees: per element) ----------------------------------------
+    def np_e(self, e):
+        """Nodes of element e (its own degree)."""
+        if self.mixed:
+            return refel(self.d, int(self.mesh.p_elem[e])).Np
+        return self.Np
+
+    def ni_e(self, e):
+        """Interior unknowns of element e: [q;] v."""
+        return self.np_e(e) * self.m * (1 + (self.d if self.viscous else 0))
+
+    def trace_mask(self, e):
+        """Which entries of the padded local trace [nF, Nf_max, m] are unknowns (mixed degrees:
+        face f of element e has the face nodes of its degree q_{e,f}); all of them otherwise."""
+        if not self.mixed:
+            return np.ones(self.n_t, dtype=bool)
+        cnt = self.mesh.face_nnodes[self.mesh.face_of[e]]                  # [nF]
+        ok = np.arange(self.Nf)[None, :] < cnt[:, None]
+        return np.repeat(ok[:, :, None], self.m, axis=2).ravel()
+
     def tables(self, e: int) -> ElementTables:
         t = self._cache.get(e)
         if t is not None:
             return t
         mesh, ref = self.mesh, self.mesh.ref
+        if self.mixed:
+            t = self._mixed_tables(e)
+            if len(self._cache) < 64:
+                self._cache[e] = t
+            return t
         W = ref.qw * abs(mesh.detJ[e])
         gphi = np.einsum("gar,rj->gaj", self._dphi, mesh.Jinv[e])
         Wf, phif, psi, nrm = [], [], [], []
@@ -108,9 +146,35 @@ class Problem:
             self._cache[e] = t
         return t
 
+    def _mixed_tables(self, e):
+        """Tables of element e of a mixed-degree mesh: the volume rule and basis of its degree
+        p_e (rule exact to degree 2 p_e + 1), on every face the rule exact to degree 2 PT_e + 1
+        (PT_e its trace degree) and the nodal trace basis of that face's degree q_{e,f}, padded
+        with zero columns to Nf_max."""
+        mesh = self.mesh
+        pK, PT = int(mesh.p_elem[e]), int(mesh.elem_trace_deg[e])
+        rK, rT = refel(self.d, pK), refel(self.d, PT)
+        W = rK.qw * abs(mesh.detJ[e])
+        phi = rK.phi(rK.qp)
+        gphi = np.einsum("gar,rj->gaj", rK.dphi(rK.qp), mesh.Jinv[e])
+        Wf, phif, psi, nrm = [], [], [], []
+        for f in range(self.nF):
+            x = rT.fqp_ref[f]
+            rq = refel(self.d, int(mesh.elem_face_deg[e, f]))
+            ps = np.zeros((len(x), self.Nf))
+            ps[:, :rq.Nf] = rq.phi(x)[:, rq.face_nodes[f]]
+            Wf.append(rT.fqw * mesh.face_jac[e, f])
+            phif.append(rK.phi(x))
+            psi.append(ps)
+            nrm.append(mesh.normal[e, f])
+        return ElementTables(W, phi, gphi, Wf, phif, psi, nrm)
+
     # -- gather / scatter between global trace and element-local trace ------------------
     def gather_trace(self, Vhat, e):
         mesh = self.mesh
+        if self.mixed:                                                        # padded [nF, Nf_max, m]
+            tn = self.trace_node(e)
+            return np.where((tn >= 0)[:, :, None], Vhat[np.maximum(tn, 0)], 0.0)
         if self.scheme == "edg":
             return Vhat[self.edg_index[e]]                                    # [nF, Nf, m]
         return Vhat[mesh.face_of[e][:, None], mesh.fnode_map[e]]          # [nF, Nf, m]
@@ -118,6 +182,9 @@ class Problem:
     def trace_node(self, e):
         """Global trace node [nF, Nf] of each local face node of element e."""
         mesh = self.mesh
+        if self.mixed:                                                        # -1: padding
+            fm = mesh.fnode_map_mixed[e]
+            return np.where(fm >= 0, mesh.fnode_off[mesh.face_of[e]][:, None] + fm, -1)
         if self.scheme == "edg":
             return self.edg_index[e]
         return mesh.face_of[e][:, None] * self.Nf + mesh.fnode_map[e]
@@ -126,10 +193,13 @@ class Problem:
         """Global flat indices of the element's local trace unknowns (f, c, i); with EDG a
         node shared by several local faces appears several times (P_e has repeated columns)."""
         base = self.trace_node(e) * self.m
-        return (base[:, :, None] + np.arange(self.m)).ravel()
+        idx = (base[:, :, None] + np.arange(self.m)).ravel()
+        return idx[self.trace_mask(e)] if self.mixed else idx
 
     @property
     def n_trace(self):
+        if self.mixed:
+            return int(self.mesh.fnode_off[-1]) * self.m
         if self.scheme == "edg":
             return self.n_edg * self.m
         return self.mesh.nFaces * self.Nf * self.m
@@ -137,6 +207,8 @@ class Problem:
     @property
     def trace_shape(self):
         """Shape of the global Vhat array."""
+        if self.mixed:
+            return (int(self.mesh.fnode_off[-1]), self.m)
         if self.scheme == "edg":
             return (self.n_edg, self.m)
         return (self.mesh.nFaces, self.Nf, self.m)
@@ -210,23 +282,24 @@ class Problem:
             return np.concatenate([Rq.reshape(B, -1), Rv.reshape(B, -1)], axis=1)
         return Rv.reshape(B, -1)
 
-    def _unpack_x(self, x):
+    def _unpack_x(self, x, Np):
         B = x.shape[0]
         if self.viscous:
-            nq = self.Np * self.m * self.d
-            return (x[:, :nq].reshape(B, self.Np, self.m, self.d),
-                    x[:, nq:].reshape(B, self.Np, self.m))
-        return None, x.reshape(B, self.Np, self.m)
+            nq = Np * self.m * self.d
+            return (x[:, :nq].reshape(B, Np, self.m, self.d),
+                    x[:, nq:].reshape(B, Np, self.m))
+        return None, x.reshape(B, Np, self.m)
 
     def local_residual(self, e, Q, V, Vh, mass_coef=0.0, hist_w=None):
         """Real residuals (R_l [n_i], R_t [n_t]) of element e."""
         Qb = None if Q is None else Q[None]
         Rq, Rv, Rt = self.element_residual(e, Qb, V[None], Vh[None], mass_coef, hist_w)
-        return self._pack_l(Rq, Rv)[0], Rt.reshape(-1)
+        Rt = Rt.reshape(-1)
+        return self._pack_l(Rq, Rv)[0], (Rt[self.trace_mask(e)] if self.mixed else Rt)
 
     def local_jacobian(self, e, Q, V, Vh, mass_coef=0.0, hist_w=None):
         """Dense blocks A, B, C, D of d(R_l, R_t)/d(x, vhat) by complex step."""
-        ni, nt = self.n_i, self.n_t
+        ni, nt = self.ni_e(e), self.n_t
         N = ni + nt
         x0 = V.reshape(-1) if Q is None else np.concatenate([Q.reshape(-1), V.reshape(-1)])
         y0 = Vh.reshape(-1)
@@ -234,11 +307,15 @@ class Problem:
         Y = np.tile(y0.astype(np.complex128), (N, 1))
         X[np.arange(ni), np.arange(ni)] += 1j * CSTEP
         Y[ni + np.arange(nt), np.arange(nt)] += 1j * CSTEP
-        Qb, Vb = self._unpack_x(X)
+        Qb, Vb = self._unpack_x(X, V.shape[0])
         Rq, Rv, Rt = self.element_residual(e, Qb, Vb, Y.reshape((N,) + Vh.shape), mass_coef, hist_w)
         Jl = np.imag(self._pack_l(Rq, Rv)).T / CSTEP          # [ni, N]
         Jt = np.imag(Rt.reshape(N, -1)).T / CSTEP             # [nt, N]
-        return Jl[:, :ni], Jl[:, ni:], Jt[:, :ni], Jt[:, ni:]
+        A, B, C, D = Jl[:, :ni], Jl[:, ni:], Jt[:, :ni], Jt[:, ni:]
+        if self.mixed:                                        # drop the padding of the trace
+            k = self.trace_mask(e)
+            B, C, D = B[:, k], C[k], D[k][:, k]
+        return A, B, C, D
 
     # -- condensation (Sec. 3.2: local elimination of the interior unknowns) -------------
     def condense(self, e, Q, V, Vh, mass_coef=0.0, hist_w=None):
@@ -254,15 +331,16 @@ class Problem:
     def consistent_q(self, e, V, Vh):
         """Q solving Eq. hDG_NS0 exactly for given (v, vhat): M Q = -R_q(Q=0)."""
         T = self.tables(e)
+        Np = T.phi.shape[1]
         M = np.einsum("g,ga,gb->ab", T.W, T.phi, T.phi)
-        Rq, _, _ = self.element_residual(e, np.zeros((1, self.Np, self.m, self.d)),
+        Rq, _, _ = self.element_residual(e, np.zeros((1, Np, self.m, self.d)),
                                          V[None], Vh[None])
-        return -np.linalg.solve(M, Rq[0].reshape(self.Np, -1)).reshape(self.Np, self.m, self.d)
+        return -np.linalg.solve(M, Rq[0].reshape(Np, -1)).reshape(Np, self.m, self.d)
 
     def history_weak(self, e, Vs, coefs):
         """hist_w [Np, m] = sum_j c_j (u(v_h^{n-j}), phi_a)_K."""
         T = self.tables(e)
-        out = np.zeros((self.Np, self.m))
+        out = np.zeros((T.phi.shape[1], self.m))
         for Vj, c in zip(Vs, coefs):
             u = ph.u_of_v(T.phi @ Vj, self.phys.gamma)
             out += c * np.einsum("g,ga,gm->am", T.W, T.phi, u)
@@ -337,6 +415,19 @@ def interpolate_state(prob: Problem, prim_fn):
     """V at element nodes and Vhat at the trace nodes (canonical face nodes; EDG: skeleton
     nodes) from prim_fn(x) -> (rho, vel, p)."""
     mesh, g = prob.mesh, prob.phys.gamma
+    if prob.mixed:                                   # per-element degrees, trace at face degrees
+        V = []
+        for e in range(mesh.E):
+            rho, vel, p = prim_fn(mesh.elem_nodes(e))
+            V.append(ph.v_of_u(ph.u_of_primitives(rho, vel, p, g), g))
+        Vhat = np.zeros(prob.trace_shape)
+        for F, sides in enumerate(mesh.face_elems):
+            e, f = sides[0]
+            r = refel(mesh.dim, int(mesh.face_deg[F]))
+            x = mesh.X[e, 0] + r.nodes[r.face_nodes[f]] @ mesh.J[e].T
+            rho, vel, p = prim_fn(x)
+            Vhat[mesh.fnode_off[F]:mesh.fnode_off[F + 1]] = ph.v_of_u(ph.u_of_primitives(rho, vel, p, g), g)
+        return V, Vhat
     rho, vel, p = prim_fn(mesh.xnode)
     V = ph.v_of_u(ph.u_of_primitives(rho, vel, p, g), g)
     fn = np.array(mesh.ref.face_nodes)
@@ -417,8 +508,9 @@ def newton_iteration(prob: Problem, Q, V, Vhat, mass_coef, hist):
     K, rhs = assemble_trace(prob, locs)
     dvh = solve_trace(K, rhs)
     Vhat_new = Vhat + dvh.reshape(Vhat.shape)
-    Qn = None if Q is None else Q.copy()
-    Vn = V.copy()
+    cp = lambda A: [a.copy() for a in A] if isinstance(A, list) else A.copy()
+    Qn = None if Q is None else cp(Q)
+    Vn = cp(V)
     for e, L in enumerate(locs):
         dx = -(L["y"] + L["X"] @ dvh[prob.trace_index(e)])
         if Q is None:
@@ -450,8 +542,9 @@ def newton_solve(prob: Problem, Q, V, Vhat, mass_coef=0.0, hist=None, tol=1e-10,
 def time_step(prob: Problem, Q, V, Vhat, Vhist, order, dt, tol=1e-10, max_it=10):
     """One BDF step from history states Vhist = [V^n, V^{n-1}, ...]."""
     mass_coef, coefs = bdf_coefficients(order, dt)
-    hist = np.stack([prob.history_weak(e, [Vj[e] for Vj in Vhist[:len(coefs)]], coefs)
-                     for e in range(prob.mesh.E)])
+    hist = [prob.history_weak(e, [Vj[e] for Vj in Vhist[:len(coefs)]], coefs) for e in range(prob.mesh.E)]
+    if not prob.mixed:
+        hist = np.stack(hist)
     return newton_solve(prob, Q, V, Vhat, mass_coef, hist, tol, max_it)
 
 
@@ -511,4 +604,5 @@ def dirk3_step(prob: Problem, Q, V, Vhat, dt, tol=1e-10, max_it=10):
 def consistent_Q(prob: Problem, V, Vhat):
     if not prob.viscous:
         return None
-    return np.stack([prob.consistent_q(e, V[e], prob.gather_trace(Vhat, e)) for e in range(prob.mesh.E)])
+    Q = [prob.consistent_q(e, V[e], prob.gather_trace(Vhat, e)) for e in range(prob.mesh.E)]
+    return Q if prob.mixed else np.stack(Q)

@@ -22,6 +22,14 @@ owned by its element. Global faces are numbered in order of first appearance ove
 order is the face's canonical node order. Face nodes of the other element are
 matched by integer node coordinates (units h/p) relative to the face's smallest
 vertex, which periodic copies share.
+
+Mixed degrees (the paper uses one degree k everywhere; this extension is not in it): with
+p_elem given, element e carries P_{p_e}, and the trace on a face carries the larger degree of
+its two sides, q_F = max(p_L, p_R). Element e then has face degrees q_{e,f} = q_F of its faces
+and a trace degree PT_e = max_f q_{e,f} >= p_e. The trace unknowns are the face nodes of degree
+q_F (the face nodes of the degree-q_F reference element on that face), numbered face by face
+(fnode_off), in the owner's local order; the other side is matched by integer node coordinates
+in units h/q_F. Mixed degrees are built for periodic meshes.
 """
 from __future__ import annotations
 
@@ -37,11 +45,20 @@ BC_NAMES = {"periodic": BC_PERIODIC, "state": BC_STATE, "slip": BC_SLIP}
 
 class Mesh:
     def __init__(self, dim: int, n: int, lo: float, hi: float, p: int, deg: int | None = None,
-                 bc=None, verts=None):
+                 bc=None, verts=None, p_elem=None):
         """bc: per axis a pair (lo side, hi side) of "periodic", "state" or "slip" (default:
         all periodic); an axis is periodic on both sides or on neither.
         verts: lattice vertex coordinates [E, d+1, d] of the elements on [0, n]^d, positively
-        oriented (default: the Kuhn split of the n^d grid)."""
+        oriented (default: the Kuhn split of the n^d grid).
+        p_elem: degree of every element [E] (mixed degrees; p is then ignored and the largest
+        degree takes its place in the uniform arrays)."""
+        if p_elem is not None:
+            p_elem = np.asarray(p_elem, dtype=np.int64)
+            if p_elem.ndim != 1 or p_elem.min() < 1:
+                raise ValueError("p_elem: one degree >= 1 per element")
+            if deg is not None or bc is not None:
+                raise ValueError("mixed degrees: periodic meshes with the default rules only")
+            p = int(p_elem.max())
         self.dim, self.n, self.p = dim, n, p
         bc = bc if bc is not None else [("periodic", "periodic")] * dim
         self.bc = np.array([[BC_NAMES[s] for s in pair] for pair in bc], dtype=np.int64)   # [dim, 2]
@@ -86,6 +103,12 @@ class Mesh:
                      + np.einsum("erc,ac->ear", (self.L[:, 1:, :] - self.L[:, 0:1, :]).transpose(0, 2, 1), idx))
         self._faces()
         self._face_geometry()
+        self.p_elem = None
+        if p_elem is not None:
+            if len(p_elem) != self.E:
+                raise ValueError("p_elem: one degree per element")
+            self.p_elem = p_elem
+            self._mixed_faces()
 
     # -- topology -------------------------------------------------------------------
     def _encode(self, arr):
@@ -148,6 +171,49 @@ class Mesh:
         np.put_along_axis(m1, o1, o0, axis=1)
         fmap[sides[:, 1]] = m1
         self.fnode_map = fmap.reshape(E, nF, Nf)
+
+    def _mixed_faces(self):
+        """Face degrees q_F = max(p_L, p_R), the trace degree of every element and the face-node
+        maps at degree q_F (owner order canonical, the other side matched by node coordinates)."""
+        dim, nF, E = self.dim, self.ref.nF, self.E
+        pe = self.p_elem
+        self.face_deg = np.array([max(int(pe[e]) for e, _f in sides) for sides in self.face_elems],
+                                 dtype=np.int64)
+        self.elem_face_deg = self.face_deg[self.face_of]                  # [E, nF]
+        self.elem_trace_deg = self.elem_face_deg.max(axis=1)              # [E]
+        nf = {q: refel(dim, q).Nf for q in range(1, self.p + 1)}
+        self.face_nnodes = np.array([nf[int(q)] for q in self.face_deg], dtype=np.int64)
+        self.fnode_off = np.concatenate([[0], np.cumsum(self.face_nnodes)]).astype(np.int64)
+        self.Nf_max = max(nf[int(q)] for q in self.face_deg)
+        fmap = np.full((E, nF, self.Nf_max), -1, dtype=np.int64)
+        fv_all = self.ref.face_verts
+        for F, sides in enumerate(self.face_elems):
+            q = int(self.face_deg[F])
+            r = refel(dim, q)
+            idx = np.array(r.idx, dtype=np.int64)
+            codes = []
+            for (e, f) in sides:
+                L = self.L[e]
+                Nq = q * L[0] + idx @ (L[1:] - L[0])                      # degree-q lattice of e
+                fv = L[fv_all[f]]
+                A = fv[np.argmin(self._encode(fv))]                        # smallest face vertex
+                codes.append(self._encode(Nq[r.face_nodes[f]] - q * A))
+            e0, f0 = sides[0]
+            fmap[e0, f0, :r.Nf] = np.arange(r.Nf)
+            if len(sides) == 2:
+                c0, c1 = codes
+                o0, o1 = np.argsort(c0), np.argsort(c1)
+                assert np.array_equal(c0[o0], c1[o1])
+                m1 = np.empty(r.Nf, dtype=np.int64)
+                m1[o1] = o0
+                e1, f1 = sides[1]
+                fmap[e1, f1, :r.Nf] = m1
+        self.fnode_map_mixed = fmap
+
+    def elem_nodes(self, e):
+        """Physical coordinates [Np_e, d] of the nodes of element e at its own degree."""
+        r = refel(self.dim, int(self.p_elem[e])) if self.p_elem is not None else self.ref
+        return self.X[e, 0] + r.nodes @ self.J[e].T
 
     def _face_geometry(self):
         ref, dim = self.ref, self.dim
