@@ -105,6 +105,12 @@ typedef struct {
   int32_t scheme;                   /* HDG_SCHEME_* */
   int64_t n_trace_nodes;            /* HDG: n_faces * Nf (a trace per face); EDG / IEDG: skeleton nodes */
   int64_t n_boundary_faces;         /* faces with one side (on the sides of bounded axes) */
+  /* Elements of different degree (p_per_elem; the paper uses one degree): mixed != 0, p is the
+   * largest degree, Np / Nf / nv / nt are those of degree p (the largest per-element sizes), and
+   * the arrays of the compute calls are packed per element; their total lengths in doubles are
+   * below (for a mesh of one degree they equal the uniform sizes E Np m, E nt, ...). */
+  int32_t mixed, p_min;
+  int64_t len_V, len_g, len_S, len_recov, len_R;
 } hdg_mesh_info;
 
 /* Boundary types of the sides of the box (the term b_h of Eqs. hDG2 / hDG_NS2, which the paper
@@ -120,10 +126,17 @@ enum { HDG_BC_PERIODIC = 0, HDG_BC_STATE = 1, HDG_BC_SLIP = 2 };
 /* Mesh T_h (Sec. 3.1.1): the n[0] x .. x n[dim-1] grid on the box [lo, hi], periodic or
  * bounded per axis, each cell split into 2 triangles / 6 tetrahedra (Kuhn split, the same in
  * every cell; element e = (cells in x-fastest order) x (2 or 6) + local index).
- *   p_per_elem  host array [E] of per-element degrees, or NULL for the uniform degree p.
- *               Meshes whose elements differ in degree are not built: a non-uniform array
- *               returns HDG_ERR_UNSUPPORTED (HDG_ERR_INVALID_ARG for a degree outside 1..4).
- *   p           polynomial degree k of Sec. 3.1.2 (1..4).
+ *   p_per_elem  host array [E] of per-element degrees (1..4), or NULL for the uniform degree p.
+ *               An array whose entries all equal p is the uniform mesh. Elements of different
+ *               degree (an extension: the paper uses one degree k) give each face the larger
+ *               degree of its two sides, q_F = max(p_L, p_R), with the nodes of the degree-q_F
+ *               reference face; the trace unknowns are numbered face by face (face F's canonical
+ *               node c is trace node face_node_off[F] + c, hdg_mesh_copy_layout), so Vhat is
+ *               [trace nodes][m]. Such meshes are built periodic, HDG, with the default rules
+ *               (quad_points 0: element degree + 1 points per direction in the volume, the
+ *               element's largest face degree + 1 on its faces); the compute calls then take
+ *               the packed per-element layout of hdg_mesh_copy_layout.
+ *   p           polynomial degree k of Sec. 3.1.2 (1..4); ignored when p_per_elem is given.
  *   scheme      trace space of Sec. 3.4: HDG_SCHEME_HDG (one trace per face, Vhat [F][Nf][m]) or
  *               HDG_SCHEME_EDG (a continuous trace, one unknown per skeleton node, Vhat [N][m],
  *               nodes numbered in order of first appearance over (element, local face, face
@@ -147,13 +160,25 @@ int hdg_mesh_copy_topology(hdg_mesh_t mesh, int32_t* face_of, int32_t* fnode_map
 /* Host copy of the boundary type of every face, face_bc [F] (HDG_BC_*; 0 for interior faces). */
 int hdg_mesh_copy_face_bc(hdg_mesh_t mesh, int8_t* face_bc);
 /* Global trace node of every local face node, tnode [E][nF][Nf] (host): HDG face * Nf + canonical
- * face node; EDG the skeleton node. The element's trace unknowns are Vhat[tnode][0..m). */
+ * face node; EDG the skeleton node. The element's trace unknowns are Vhat[tnode][0..m).
+ * Mixed degrees: Nf of the largest degree; face_node_off[F] + canonical node, -1 beyond the
+ * nodes of the face's own degree. */
 int hdg_mesh_copy_trace_map(hdg_mesh_t mesh, int32_t* tnode);
+/* Packed per-element layout (host copies; any pointer may be NULL). Offsets [E + 1] in doubles
+ * of element e's block in: V and hist (voff: [Np_e][m]), g (toff: nt_e = sum_f Nf(q_f) m),
+ * S (soff: [nt_e][nt_e]), recov (roff: X [nv_e][nt_e] then y [nv_e]), R (Roff: R_v [nv_e] then
+ * R_t [nt_e]); elem_p [E] element degrees, face_deg [F] face degrees, face_node_off [F + 1] first
+ * trace node of each face. The local trace order is [local face][its own face nodes][component].
+ * For a mesh of one degree the offsets are the uniform strides. Host-only. */
+int hdg_mesh_copy_layout(hdg_mesh_t mesh, int64_t* voff, int64_t* toff, int64_t* soff, int64_t* roff, int64_t* Roff,
+                         int8_t* elem_p, int8_t* face_deg, int64_t* face_node_off);
 /* Host copies: element node coordinates xnode [E][Np][dim], trace-node coordinates xfnode
  * [n_trace_nodes][dim] (HDG: canonical face nodes [F][Nf], owner side; EDG: skeleton nodes),
  * geometry geo [E][geo_stride] =
  * (Jinv [dim][dim] with Jinv[r][k] = d r / d x_k, |det J|, per face: unit outward
- * normal [dim], surface Jacobian). Any pointer may be NULL. */
+ * normal [dim], surface Jacobian). Mixed degrees: xnode is packed [sum_e Np_e][dim] (each element's
+ * nodes at its own degree), xfnode [trace nodes][dim] (each face's nodes at its degree, owner side).
+ * Any pointer may be NULL. */
 int hdg_mesh_copy_coords(hdg_mesh_t mesh, double* xnode, double* xfnode, double* geo);
 
 /* Context: mesh tables, reference tables and physics on one CUDA device. Allocates the
@@ -418,7 +443,8 @@ enum {
   HDG_KERNEL_MIXED_PREP = 7,       /* mixed form: FP32 inverse, scales, operand slices      */
   HDG_KERNEL_MIXED_FACE = 8,       /* mixed form: face contractions (tensor-core slices)    */
   HDG_KERNEL_MIXED_OPERATORS = 9,  /* mixed form: operator slices, FP64 residuals           */
-  HDG_KERNEL_CLASSES = 10
+  HDG_KERNEL_PCLASS = 10,          /* mixed-degree meshes: the persistent fused launch      */
+  HDG_KERNEL_CLASSES = 11
 };
 int hdg_profile_enable(hdg_ctx_t ctx, int on);
 int hdg_profile_reset(hdg_ctx_t ctx);

@@ -110,6 +110,10 @@ extern "C" int hdg_assemble_condense_noalloc(hdg_ctx_t ctx, const double* V, con
     hdg::set_error("hdg_assemble_condense_noalloc: null argument (elem_status is required)");
     return HDG_ERR_INVALID_ARG;
   }
+  if (ctx->pm) {
+    hdg::set_error("hdg_assemble_condense_noalloc: not built for meshes of mixed degree");
+    return HDG_ERR_UNSUPPORTED;
+  }
   int prev = -1;
   if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
   if (prev != ctx->device && cudaSetDevice(ctx->device) != cudaSuccess) {

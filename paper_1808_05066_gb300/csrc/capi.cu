@@ -109,18 +109,33 @@ int hdg_mesh_create(int dim, const int64_t n[3], const double lo[3], const doubl
     set_error("hdg_mesh_create: unknown scheme");
     return HDG_ERR_INVALID_ARG;
   }
-  if (p_per_elem) {  // one degree per element: accepted when every element has degree p
+  bool mixed = false;
+  if (p_per_elem) {  // one degree per element; all equal: the uniform mesh of that degree
     if (dim < 2 || dim > 3) {
       set_error("hdg_mesh_create: invalid mesh arguments");
       return HDG_ERR_INVALID_ARG;
     }
     int64_t E = dim == 2 ? 2 : 6;
     for (int d = 0; d < dim; ++d) E *= n[d] > 0 ? n[d] : 0;
-    for (int64_t e = 0; e < E; ++e)
-      if (p_per_elem[e] != p) {
-        set_error("hdg_mesh_create: elements of different degree in one mesh are not built");
-        return p_per_elem[e] >= 1 && p_per_elem[e] <= 4 ? HDG_ERR_UNSUPPORTED : HDG_ERR_INVALID_ARG;
+    int pmin = 99, pmax = 0;
+    for (int64_t e = 0; e < E; ++e) {
+      if (p_per_elem[e] < 1 || p_per_elem[e] > 4) {
+        set_error("hdg_mesh_create: element degrees must lie in 1..4");
+        return HDG_ERR_INVALID_ARG;
       }
+      pmin = std::min<int>(pmin, p_per_elem[e]);
+      pmax = std::max<int>(pmax, p_per_elem[e]);
+    }
+    if (E > 0) p = pmax;
+    mixed = pmin != pmax;
+    if (mixed) {
+      bool periodic = true;
+      for (int d = 0; bc && d < 2 * dim; ++d) periodic = periodic && bc[d] == HDG_BC_PERIODIC;
+      if (scheme != HDG_SCHEME_HDG || !periodic || (quad_points != 0 && quad_points != p + 1)) {
+        set_error("hdg_mesh_create: meshes of mixed degree are built periodic, HDG, with the default rules");
+        return HDG_ERR_UNSUPPORTED;
+      }
+    }
   }
   if (bc && scheme != HDG_SCHEME_HDG)
     for (int d = 0; d < 2 * dim && d < 6; ++d)
@@ -138,6 +153,11 @@ int hdg_mesh_create(int dim, const int64_t n[3], const double lo[3], const doubl
   }
   m->m.scheme = scheme;
   if (scheme != HDG_SCHEME_HDG) hdg::build_edg(m->m);  // every face is interior: IEDG is EDG
+  if (mixed && (rc = hdg::build_mixed(m->m, p_per_elem)) != 0) {
+    delete m;
+    set_error("hdg_mesh_create: mixed-degree face matching failed (code " + std::to_string(rc) + ")");
+    return HDG_ERR_INVALID_ARG;
+  }
   *out = m;
   return HDG_OK;
 }
@@ -168,6 +188,49 @@ int hdg_mesh_get_info(hdg_mesh_t mesh, hdg_mesh_info* out) {
   out->n_trace_nodes = m.scheme == HDG_SCHEME_HDG ? m.nFaces * m.ref.Nf : m.n_edg;
   out->n_trace = out->n_trace_nodes * (m.dim + 2);
   out->n_boundary_faces = m.n_boundary;
+  out->mixed = m.pe.empty() ? 0 : 1;
+  if (out->mixed) {
+    out->p_min = *std::min_element(m.pe.begin(), m.pe.end());
+    out->n_trace_nodes = m.fnoff.back();
+    out->n_trace = out->n_trace_nodes * (m.dim + 2);
+    out->len_V = m.voff.back();
+    out->len_g = m.toff.back();
+    out->len_S = m.soff.back();
+    out->len_recov = m.roff.back();
+    out->len_R = m.Roff.back();
+  } else {
+    out->p_min = m.p;
+    out->len_V = m.E * out->nv;
+    out->len_g = m.E * out->nt;
+    out->len_S = m.E * (int64_t)out->nt * out->nt;
+    out->len_recov = m.E * ((int64_t)out->nv * out->nt + out->nv);
+    out->len_R = m.E * (int64_t)(out->nv + out->nt);
+  }
+  return HDG_OK;
+}
+
+int hdg_mesh_copy_layout(hdg_mesh_t mesh, int64_t* voff, int64_t* toff, int64_t* soff, int64_t* roff, int64_t* Roff,
+                         int8_t* elem_p, int8_t* face_deg, int64_t* face_node_off) {
+  if (!mesh) {
+    set_error("hdg_mesh_copy_layout: null mesh");
+    return HDG_ERR_INVALID_ARG;
+  }
+  const hdg::Mesh& m = mesh->m;
+  const int M = m.dim + 2;
+  const int64_t nv = (int64_t)m.ref.Np * M, nt = (int64_t)m.ref.nF * m.ref.Nf * M;
+  const bool mx = !m.pe.empty();
+  for (int64_t e = 0; e <= m.E; ++e) {
+    if (voff) voff[e] = mx ? m.voff[e] : e * nv;
+    if (toff) toff[e] = mx ? m.toff[e] : e * nt;
+    if (soff) soff[e] = mx ? m.soff[e] : e * nt * nt;
+    if (roff) roff[e] = mx ? m.roff[e] : e * (nv * nt + nv);
+    if (Roff) Roff[e] = mx ? m.Roff[e] : e * (nv + nt);
+    if (elem_p && e < m.E) elem_p[e] = mx ? m.pe[e] : (int8_t)m.p;
+  }
+  for (int64_t F = 0; F <= m.nFaces; ++F) {
+    if (face_deg && F < m.nFaces) face_deg[F] = mx ? m.fdeg[F] : (int8_t)m.p;
+    if (face_node_off) face_node_off[F] = mx ? m.fnoff[F] : F * m.ref.Nf;
+  }
   return HDG_OK;
 }
 
@@ -191,7 +254,10 @@ int hdg_mesh_copy_trace_map(hdg_mesh_t mesh, int32_t* tnode) {
     for (int f = 0; f < nF; ++f)
       for (int c = 0; c < Nf; ++c) {
         const int64_t i = (e * nF + f) * Nf + c;
-        tnode[i] = m.scheme == HDG_SCHEME_HDG ? m.face_of[e * nF + f] * Nf + m.fnode_map[i] : m.edg_index[i];
+        if (!m.pe.empty())
+          tnode[i] = m.fnode_mix[i] < 0 ? -1 : (int32_t)(m.fnoff[m.face_of[e * nF + f]] + m.fnode_mix[i]);
+        else
+          tnode[i] = m.scheme == HDG_SCHEME_HDG ? m.face_of[e * nF + f] * Nf + m.fnode_map[i] : m.edg_index[i];
       }
   return HDG_OK;
 }
@@ -214,9 +280,13 @@ int hdg_mesh_copy_coords(hdg_mesh_t mesh, double* xnode, double* xfnode, double*
     return HDG_ERR_INVALID_ARG;
   }
   const hdg::Mesh& m = mesh->m;
-  if (xnode) std::memcpy(xnode, m.xnode.data(), sizeof(double) * m.xnode.size());
+  const bool mx = !m.pe.empty();
+  if (xnode) {
+    const std::vector<double>& x = mx ? m.xnode_mix : m.xnode;
+    std::memcpy(xnode, x.data(), sizeof(double) * x.size());
+  }
   if (xfnode) {
-    const std::vector<double>& x = m.scheme == HDG_SCHEME_HDG ? m.xfnode : m.xedg;
+    const std::vector<double>& x = mx ? m.xfnode_mix : m.scheme == HDG_SCHEME_HDG ? m.xfnode : m.xedg;
     std::memcpy(xfnode, x.data(), sizeof(double) * x.size());
   }
   if (geo) std::memcpy(geo, m.geo.data(), sizeof(double) * m.geo.size());
@@ -237,7 +307,7 @@ int hdg_ctx_create(hdg_mesh_t mesh, const hdg_physics* phys, int device, hdg_ctx
   }
   const hdg::Mesh& m = mesh->m;
   const bool visc = phys->reynolds > 0.0;
-  if (!hdg::config_supported(m.dim, m.p, m.K, visc)) {
+  if (m.pe.empty() && !hdg::config_supported(m.dim, m.p, m.K, visc)) {
     set_error("hdg_ctx_create: (dim, p, quad_points, physics) not compiled in");
     return HDG_ERR_UNSUPPORTED;
   }
@@ -294,6 +364,17 @@ int hdg_ctx_create(hdg_mesh_t mesh, const hdg_physics* phys, int device, hdg_ctx
   if (const char* ch = std::getenv("HDG_ELEMENT_CHUNK")) {
     long v = std::strtol(ch, nullptr, 10);
     if (v > 0) c->chunk = std::min<int64_t>(v, c->E);
+  }
+  if (!m.pe.empty()) {  // mixed degrees: class tables, packed layout and work queue only
+    c->n_tnodes = m.fnoff.back();
+    c->ntrace = c->n_tnodes * c->M;
+    int rc = HDG_OK;
+    if ((rc = upload(&c->d_geo, m.geo)) || (rc = hdg::pclass_setup(c))) {
+      hdg_ctx_destroy(c);
+      return rc;
+    }
+    *out = c;
+    return HDG_OK;
   }
 
   hdg::RefTables T = hdg::make_tables(m.ref);
@@ -407,8 +488,18 @@ void hdg_ctx_destroy(hdg_ctx_t c) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
   }
+  hdg::pclass_free(c->pm);
   delete c;
 }
+
+// Calls not built for meshes whose elements differ in degree
+#define HDG_UNIFORM_ONLY(ctx, name)                                                      \
+  do {                                                                                   \
+    if ((ctx)->pm) {                                                                     \
+      set_error(std::string(name) + ": not built for meshes of mixed degree");           \
+      return HDG_ERR_UNSUPPORTED;                                                        \
+    }                                                                                    \
+  } while (0)
 
 #define HDG_REQUIRE(cond, msg)  \
   do {                          \
@@ -420,6 +511,7 @@ void hdg_ctx_destroy(hdg_ctx_t c) {
 
 int hdg_ctx_set_boundary_state(hdg_ctx_t ctx, const double* Vb, void* stream) {
   HDG_REQUIRE(ctx && Vb, "hdg_ctx_set_boundary_state: null argument");
+  HDG_UNIFORM_ONLY(ctx, "hdg_ctx_set_boundary_state");
   DeviceGuard guard(ctx->device);
   if (!ctx->d_vb) HDG_CK(cudaMalloc(&ctx->d_vb, sizeof(double) * ctx->ntrace));
   HDG_CK(cudaMemcpyAsync(ctx->d_vb, Vb, sizeof(double) * ctx->ntrace, cudaMemcpyDeviceToDevice,
@@ -437,6 +529,7 @@ int hdg_prim_to_entropy(hdg_ctx_t ctx, const double* prim, int64_t n_points, dou
 int hdg_history(hdg_ctx_t ctx, const double* V0, const double* V1, double c0, double c1, double* hist,
                 void* stream) {
   HDG_REQUIRE(ctx && V0 && hist, "hdg_history: invalid argument");
+  HDG_UNIFORM_ONLY(ctx, "hdg_history");
   DeviceGuard guard(ctx->device);
   return hdg::launch_history(ctx, V0, V1, c0, c1, hist, (cudaStream_t)stream);
 }
@@ -454,6 +547,13 @@ int hdg_assemble_condense(hdg_ctx_t ctx, const double* V, const double* Vhat, co
     HDG_CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int32_t) * ctx->E, s));
     st = ctx->d_status;
   }
+  if (ctx->pm) {
+    if (precision != HDG_PREC_FP64) {
+      set_error("hdg_assemble_condense: meshes of mixed degree are built for the FP64 form");
+      return HDG_ERR_UNSUPPORTED;
+    }
+    return hdg::assemble_condense_pclass(ctx, V, Vhat, hist, mass_coef, S, g, recov, R, st, s);
+  }
   if (precision == HDG_PREC_MIXED)
     return hdg::assemble_condense_mixed(ctx, V, Vhat, hist, mass_coef, S, g, recov, R, st, s);
   return hdg::assemble_condense_fp64(ctx, V, Vhat, hist, mass_coef, S, g, recov, R, st, s);
@@ -464,6 +564,7 @@ int hdg_assemble_condense_graph(hdg_ctx_t ctx, const double* V, const double* Vh
                                 double mass_coef, int precision, double* S, double* g, double* recov, double* R,
                                 int32_t* elem_status, void* stream) {
   HDG_REQUIRE(ctx && V && Vhat && S && g && recov && R, "hdg_assemble_condense_graph: null argument");
+  HDG_UNIFORM_ONLY(ctx, "hdg_assemble_condense_graph");
   HDG_REQUIRE(precision == HDG_PREC_FP64 || precision == HDG_PREC_MIXED, "hdg_assemble_condense_graph: precision");
   DeviceGuard guard(ctx->device);
   cudaStream_t s = (cudaStream_t)stream;
@@ -525,6 +626,7 @@ int hdg_assemble_condense_host(hdg_ctx_t ctx, const double* V, const double* Vha
                                double mass_coef, int precision, double* S_host, double* g_host, double* recov,
                                double* R, int32_t* elem_status, void* stream) {
   HDG_REQUIRE(ctx && V && Vhat && S_host && g_host && recov && R, "hdg_assemble_condense_host: null argument");
+  HDG_UNIFORM_ONLY(ctx, "hdg_assemble_condense_host");
   HDG_REQUIRE(precision == HDG_PREC_FP64 || precision == HDG_PREC_MIXED, "hdg_assemble_condense_host: precision");
   DeviceGuard guard(ctx->device);
   cudaStream_t s = (cudaStream_t)stream;
@@ -558,6 +660,7 @@ int hdg_assemble_condense_host(hdg_ctx_t ctx, const double* V, const double* Vha
 int hdg_entropy_production(hdg_ctx_t ctx, const double* V, const double* Vhat, double* int_rho_s, double* production,
                            void* stream) {
   HDG_REQUIRE(ctx && V && Vhat && int_rho_s && production, "hdg_entropy_production: null argument");
+  HDG_UNIFORM_ONLY(ctx, "hdg_entropy_production");
   DeviceGuard guard(ctx->device);
   cudaStream_t s = (cudaStream_t)stream;
   if (!ctx->d_ent) HDG_CK(cudaMalloc(&ctx->d_ent, 2 * sizeof(double)));
@@ -574,6 +677,7 @@ int hdg_entropy_production(hdg_ctx_t ctx, const double* V, const double* Vhat, d
 int hdg_trace_solve(hdg_ctx_t ctx, const double* S, const double* g, double* dVhat, int method, double rtol,
                     int max_it, int* iters, double* final_res, void* stream) {
   HDG_REQUIRE(ctx && S && g && dVhat && iters && final_res, "hdg_trace_solve: null argument");
+  HDG_UNIFORM_ONLY(ctx, "hdg_trace_solve");
   HDG_REQUIRE(method >= HDG_SOLVER_AUTO && method <= HDG_SOLVER_DENSE && rtol > 0.0 && max_it > 0,
               "hdg_trace_solve: invalid method / tolerance");
   DeviceGuard guard(ctx->device);
@@ -582,12 +686,14 @@ int hdg_trace_solve(hdg_ctx_t ctx, const double* S, const double* g, double* dVh
 
 int hdg_recover_interior(hdg_ctx_t ctx, const double* recov, const double* dVhat, double* dV, void* stream) {
   HDG_REQUIRE(ctx && recov && dVhat && dV, "hdg_recover_interior: null argument");
+  HDG_UNIFORM_ONLY(ctx, "hdg_recover_interior");
   DeviceGuard guard(ctx->device);
   return hdg::launch_recover(ctx, recov, dVhat, dV, (cudaStream_t)stream);
 }
 
 int hdg_trace_matvec(hdg_ctx_t ctx, const double* S, const double* x, double* y, void* stream) {
   HDG_REQUIRE(ctx && S && x && y, "hdg_trace_matvec: null argument");
+  HDG_UNIFORM_ONLY(ctx, "hdg_trace_matvec");
   DeviceGuard guard(ctx->device);
   double* work = nullptr;
   HDG_CK(cudaMallocAsync(&work, sizeof(double) * ctx->E * ctx->NT, (cudaStream_t)stream));
@@ -598,6 +704,7 @@ int hdg_trace_matvec(hdg_ctx_t ctx, const double* S, const double* x, double* y,
 
 int hdg_residual_norm(hdg_ctx_t ctx, const double* R, double* norm, void* stream) {
   HDG_REQUIRE(ctx && R && norm, "hdg_residual_norm: null argument");
+  HDG_UNIFORM_ONLY(ctx, "hdg_residual_norm");
   DeviceGuard guard(ctx->device);
   return hdg::residual_norm(ctx, R, norm, (cudaStream_t)stream);
 }
@@ -688,6 +795,7 @@ int hdg_newton_solve(hdg_ctx_t ctx, double* V, double* Vhat, const double* hist,
                      int* trace_iters, void* stream) {
   HDG_REQUIRE(ctx && V && Vhat && newton_iters && res_norm && tol > 0.0 && max_newton >= 0,
               "hdg_newton_solve: invalid argument");
+  HDG_UNIFORM_ONLY(ctx, "hdg_newton_solve");
   HDG_REQUIRE(precision == HDG_PREC_FP64 || precision == HDG_PREC_MIXED, "hdg_newton_solve: precision");
   DeviceGuard guard(ctx->device);
   cudaStream_t s = (cudaStream_t)stream;
@@ -778,6 +886,7 @@ int hdg_newton_step(hdg_ctx_t ctx, double* V, double* Vhat, const double* V_n, c
                     int* newton_iters, double* res_norm, double* res_history, int* trace_iters, void* stream) {
   HDG_REQUIRE(ctx && V && Vhat && newton_iters && res_norm && tol > 0.0 && max_newton >= 0,
               "hdg_newton_step: invalid argument");
+  HDG_UNIFORM_ONLY(ctx, "hdg_newton_step");
   HDG_REQUIRE(bdf_order >= 0 && bdf_order <= 2, "hdg_newton_step: bdf_order must be 0, 1 or 2");
   HDG_REQUIRE(bdf_order == 0 || (dt > 0.0 && V_n), "hdg_newton_step: BDF needs dt > 0 and V_n");
   HDG_REQUIRE(bdf_order < 2 || V_nm1, "hdg_newton_step: BDF2 needs V_nm1");
@@ -892,6 +1001,7 @@ extern "C" int hdg_dirk3_step(hdg_ctx_t ctx, double* V, double* Vhat, const doub
                               void* stream) {
   HDG_REQUIRE(ctx && V && Vhat && V_n && stage_iters && res_norm && dt > 0.0 && tol > 0.0 && max_newton >= 0,
               "hdg_dirk3_step: invalid argument");
+  HDG_UNIFORM_ONLY(ctx, "hdg_dirk3_step");
   HDG_REQUIRE(precision == HDG_PREC_FP64 || precision == HDG_PREC_MIXED, "hdg_dirk3_step: precision");
   DeviceGuard guard(ctx->device);
   cudaStream_t s = (cudaStream_t)stream;

@@ -9,6 +9,7 @@
 #include "../../include/hdg.h"
 #include "hdg_device.cuh"
 #include "mesh.hpp"
+#include "pclass.hpp"
 
 struct hdg_mesh {
   hdg::Mesh m;
@@ -116,6 +117,7 @@ struct hdg_ctx {
   // applies per device; a context belongs to one device)
   bool attr_fp64 = false, attr_mixed = false, attr_noalloc = false, attr_matvec = false;
   int num_sms = 0;               // SMs of the device (persistent grids)
+  hdg::PMix* pm = nullptr;       // mixed-degree mesh: class tables, packed layout, work queue
   int* d_mv_err = nullptr;       // set by the staged trace matvec when a copy wait gave up
   void* d_Sdf = nullptr;         // double-float copy of S for the GMRES products [E][NT][NT]
   size_t sdf_bytes = 0;

@@ -317,4 +317,116 @@ void build_edg(Mesh& m) {
   m.n_edg = (int64_t)ids.size();
 }
 
+int build_mixed(Mesh& m, const int8_t* pe_in) {
+  const int dim = m.dim, nF = m.ref.nF, NfMax = m.ref.Nf;
+  const int64_t E = m.E, F = m.nFaces;
+  m.pe.assign(pe_in, pe_in + E);
+  for (int8_t q : m.pe)
+    if (q < 1 || q > m.p) return -1;
+  m.fdeg.assign(F, 0);
+  for (int64_t Fi = 0; Fi < F; ++Fi)
+    for (int s = 0; s < 2; ++s) {
+      const int32_t ef = m.face_side[2 * Fi + s];
+      if (ef >= 0) m.fdeg[Fi] = std::max(m.fdeg[Fi], m.pe[ef / nF]);
+    }
+  m.ptr.assign(E, 0);
+  for (int64_t e = 0; e < E; ++e)
+    for (int f = 0; f < nF; ++f) m.ptr[e] = std::max(m.ptr[e], m.fdeg[m.face_of[e * nF + f]]);
+  std::vector<RefElement> rq(m.p + 1);
+  for (int q = 1; q <= m.p; ++q) rq[q] = make_refel(dim, q, q + 1);
+  m.fnoff.assign(F + 1, 0);
+  for (int64_t Fi = 0; Fi < F; ++Fi) m.fnoff[Fi + 1] = m.fnoff[Fi] + rq[m.fdeg[Fi]].Nf;
+  // lattice vertices of element e (units h)
+  auto vtx = [&](int64_t e, int v, int r) { return m.lat[(e * nF + v) * dim + r]; };
+  // integer coordinates (units h/q) of node a of the degree-q element e, relative to q A
+  auto node_rel = [&](int64_t e, const RefElement& r, int a, const V3& A, V3& out) {
+    const int q = r.p;
+    for (int s = 0; s < dim; ++s) {
+      int64_t x = q * vtx(e, 0, s);
+      for (int t = 0; t < dim; ++t) x += (vtx(e, t + 1, s) - vtx(e, 0, s)) * r.idx[a * dim + t];
+      out[s] = x - q * A[s];
+    }
+    for (int s = dim; s < 3; ++s) out[s] = 0;
+  };
+  auto face_min = [&](int64_t e, int f) {
+    V3 best{};
+    bool first = true;
+    for (int v = 0; v < nF; ++v) {
+      if (v == f) continue;
+      V3 x{};
+      for (int s = 0; s < dim; ++s) x[s] = vtx(e, v, s);
+      if (first || x < best) best = x;
+      first = false;
+    }
+    return best;
+  };
+  m.fnode_mix.assign(E * nF * NfMax, -1);
+  for (int64_t Fi = 0; Fi < F; ++Fi) {
+    const RefElement& r = rq[m.fdeg[Fi]];
+    const int32_t ef0 = m.face_side[2 * Fi];
+    const int64_t e0 = ef0 / nF;
+    const int f0 = ef0 % nF;
+    const V3 A0 = face_min(e0, f0);
+    std::map<V3, int> pos;
+    for (int c = 0; c < r.Nf; ++c) {
+      V3 key{};
+      node_rel(e0, r, r.face_nodes[f0][c], A0, key);
+      pos[key] = c;
+    }
+    if ((int)pos.size() != r.Nf) return -3;
+    for (int s = 0; s < 2; ++s) {
+      const int32_t ef = m.face_side[2 * Fi + s];
+      if (ef < 0) continue;
+      const int64_t e = ef / nF;
+      const int f = ef % nF;
+      const V3 A = face_min(e, f);
+      for (int c = 0; c < r.Nf; ++c) {
+        V3 key{};
+        node_rel(e, r, r.face_nodes[f][c], A, key);
+        auto it = pos.find(key);
+        if (it == pos.end()) return -4;
+        m.fnode_mix[(e * nF + f) * NfMax + c] = it->second;
+      }
+    }
+  }
+  const int M = dim + 2;
+  m.voff.assign(E + 1, 0);
+  m.toff.assign(E + 1, 0);
+  m.soff.assign(E + 1, 0);
+  m.roff.assign(E + 1, 0);
+  m.Roff.assign(E + 1, 0);
+  for (int64_t e = 0; e < E; ++e) {
+    int64_t nt = 0;
+    for (int f = 0; f < nF; ++f) nt += (int64_t)rq[m.fdeg[m.face_of[e * nF + f]]].Nf * M;
+    const int64_t nv = (int64_t)rq[m.pe[e]].Np * M;
+    m.voff[e + 1] = m.voff[e] + nv;
+    m.toff[e + 1] = m.toff[e] + nt;
+    m.soff[e + 1] = m.soff[e] + nt * nt;
+    m.roff[e + 1] = m.roff[e] + nv * nt + nv;
+    m.Roff[e + 1] = m.Roff[e] + nv + nt;
+  }
+  // node coordinates: x = X_0 + J idx / q for the lattice multi-index idx of degree q
+  auto node_x = [&](int64_t e, const RefElement& r, int a, double* x) {
+    for (int s = 0; s < dim; ++s) {
+      const double h = (m.hi[s] - m.lo[s]) / (double)m.n[s];
+      double v = m.lo[s] + h * (double)vtx(e, 0, s);
+      for (int t = 0; t < dim; ++t) v += h * (double)(vtx(e, t + 1, s) - vtx(e, 0, s)) * r.idx[a * dim + t] / r.p;
+      x[s] = v;
+    }
+  };
+  m.xnode_mix.assign(m.voff.back() / M * dim, 0.0);
+  for (int64_t e = 0; e < E; ++e) {
+    const RefElement& r = rq[m.pe[e]];
+    for (int a = 0; a < r.Np; ++a) node_x(e, r, a, &m.xnode_mix[(m.voff[e] / M + a) * dim]);
+  }
+  m.xfnode_mix.assign(m.fnoff.back() * dim, 0.0);
+  for (int64_t Fi = 0; Fi < F; ++Fi) {
+    const RefElement& r = rq[m.fdeg[Fi]];
+    const int64_t e0 = m.face_side[2 * Fi] / nF;
+    const int f0 = m.face_side[2 * Fi] % nF;
+    for (int c = 0; c < r.Nf; ++c) node_x(e0, r, r.face_nodes[f0][c], &m.xfnode_mix[(m.fnoff[Fi] + c) * dim]);
+  }
+  return 0;
+}
+
 }  // namespace hdg

@@ -46,6 +46,21 @@ struct Mesh {
   int64_t n_edg = 0;
   std::vector<int32_t> edg_index;  // [E][nF][Nf] skeleton node of each local face node
   std::vector<double> xedg;        // [n_edg][dim] node coordinates (first appearance)
+  // Mixed degrees (not in the paper, which uses one degree): element e has degree pe[e], the
+  // trace on face F the larger degree of its two sides, fdeg[F] = max(p_L, p_R), with the face
+  // nodes of the degree-fdeg reference element; trace node of canonical face node c of face F:
+  // fnoff[F] + c. Empty for a mesh of one degree (then p is that degree; otherwise the largest).
+  std::vector<int8_t> pe;          // [E]
+  std::vector<int8_t> fdeg;        // [F]
+  std::vector<int8_t> ptr;         // [E] trace degree of the element: the largest of its faces
+  std::vector<int64_t> fnoff;      // [F + 1]
+  std::vector<int32_t> fnode_mix;  // [E][nF][Nf(p)] canonical face node of each local face node
+                                   //   at the face's degree; -1 beyond that face's node count
+  // packed per-element layout of a mixed-degree mesh, offsets [E + 1] in doubles: V and hist
+  // (np_e m), g (nt_e = sum_f Nf(q_f) m), S (nt_e^2), recov (nv_e nt_e + nv_e), R (nv_e + nt_e)
+  std::vector<int64_t> voff, toff, soff, roff, Roff;
+  std::vector<double> xnode_mix;   // [sum_e Np_e][dim] element nodes at the element's degree
+  std::vector<double> xfnode_mix;  // [trace nodes][dim] face nodes at the face's degree (owner side)
 };
 
 // Returns 0 on success; -1 on invalid arguments. bc: per axis (lo, hi) boundary type
@@ -55,5 +70,8 @@ int build_mesh(int dim, const int64_t n[3], const double lo[3], const double hi[
 // The continuous (EDG) numbering of the skeleton nodes of a built mesh: identifies the face
 // nodes of all elements by their integer coordinates modulo the period.
 void build_edg(Mesh& m);
+// The mixed-degree data of a periodic HDG mesh built with p = the largest degree in pe.
+// Returns 0 on success; -1 on invalid degrees.
+int build_mixed(Mesh& m, const int8_t* pe);
 
 }  // namespace hdg

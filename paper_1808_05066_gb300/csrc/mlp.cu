@@ -360,6 +360,10 @@ int hdg_mlp_features(hdg_ctx_t ctx, const double* V, const double* Vhat, const d
     set_error("hdg_mlp_features: null argument");
     return HDG_ERR_INVALID_ARG;
   }
+  if (ctx->pm) {
+    set_error("hdg_mlp_features: not built for meshes of mixed degree");
+    return HDG_ERR_UNSUPPORTED;
+  }
   if (ctx->scheme || !ctx->h_bface.empty()) {
     set_error("hdg_mlp_features: the per-face network works on two-sided face traces (periodic HDG) only");
     return HDG_ERR_UNSUPPORTED;
@@ -464,6 +468,10 @@ int hdg_mlp_apply_trace(hdg_ctx_t ctx, const double* Vhat, const double* dvh1, c
   if (!ctx || !Vhat || !dvh1 || !pred || !tmean || !tscale || !Vhat_out) {
     set_error("hdg_mlp_apply_trace: null argument");
     return HDG_ERR_INVALID_ARG;
+  }
+  if (ctx->pm) {
+    set_error("hdg_mlp_apply_trace: not built for meshes of mixed degree");
+    return HDG_ERR_UNSUPPORTED;
   }
   if (ctx->scheme || !ctx->h_bface.empty()) {
     set_error("hdg_mlp_apply_trace: the per-face network works on two-sided face traces (periodic HDG) only");

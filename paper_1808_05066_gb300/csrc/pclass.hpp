@@ -1,0 +1,56 @@
+// Mixed-degree meshes (elements of different degree in one mesh): the per-class device tables,
+// the packed per-element layout and the work queue of the persistent assemble + condense launch
+// (pclass.cu). The paper uses one degree; this is the library's extension.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+struct hdg_ctx;
+
+namespace hdg {
+
+constexpr int kPClasses = 10;  // (pk, pt) with 1 <= pk <= pt <= 4 (3D Navier-Stokes)
+
+// sizes of one (pk, pt) class: nodes, points, unknowns, tiles, shared memory and per-CTA scratch
+// (doubles) of the fused kernel
+struct PDims {
+  int pk, pt, NP, NFK, NFN, NG, NGF, NV, NT, NZ, GT, RBMAX, ASM, CND, KEEP, SMEM, lu_smem;
+  int64_t SLOT;
+};
+
+// device pointers of the tables of one (pk, pt) class (layouts of ClassTables, refel.hpp) and its sizes
+struct PClassDev {
+  const double *W, *Phi, *dPhi, *WF, *PhiF, *dPhiF, *PsiF, *PhiN, *PL, *PLF, *PLV, *PLFV, *IPro;
+  const int* fnodesK;
+  PDims d;
+};
+
+struct PMix {
+  int pmin = 0, pmax = 0, nfn_max = 0;
+  int64_t n_tnodes = 0;
+  // device copies of the mesh's packed layout offsets (Mesh::voff ..)
+  int64_t *d_voff = nullptr, *d_toff = nullptr, *d_soff = nullptr, *d_roff = nullptr, *d_Roff = nullptr;
+  int* d_tgidx = nullptr;     // [E][NF][nfn_max] trace node of each local face node, -1 beyond
+  int8_t* d_fdeg = nullptr;   // [E][NF]
+  int8_t* d_cls = nullptr;    // [E] class index
+  int* d_queue = nullptr;     // [E] elements, largest class first
+  int* d_counter = nullptr;   // work counter of the persistent launch
+  double* d_tab = nullptr;
+  int* d_itab = nullptr;
+  PClassDev tab[kPClasses] = {};
+  int64_t class_count[kPClasses] = {};
+  size_t smem_bytes = 0;      // dynamic shared memory of the launch: the largest class present
+  int64_t slot_doubles = 0;   // per-CTA scratch: the largest class present
+  bool attr_set = false;
+};
+
+int pclass_index(int pk, int pt);
+// class tables, layout and queue of a mixed-degree mesh; frees with pclass_free
+int pclass_setup(hdg_ctx* c);
+void pclass_free(PMix* pm);
+int assemble_condense_pclass(hdg_ctx* c, const double* V, const double* Vhat, const double* hist, double mass_coef,
+                             double* S, double* g, double* recov, double* R, int32_t* status, cudaStream_t s);
+
+}  // namespace hdg

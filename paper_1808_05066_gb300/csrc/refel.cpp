@@ -294,4 +294,123 @@ RefTables make_tables(const RefElement& r) {
   return T;
 }
 
+ClassTables make_class_tables(int dim, int pk, int pt) {
+  const RefElement rk = make_refel(dim, pk, pk + 1), rt = make_refel(dim, pt, pt + 1);
+  ClassTables T;
+  T.dim = dim;
+  T.pk = pk;
+  T.pt = pt;
+  T.Np = rk.Np;
+  T.Nfk = rk.Nf;
+  T.Nft = rt.Nf;
+  T.nF = rk.nF;
+  T.NG = rk.NG;
+  T.NGF = rt.NGF;
+  const int d = dim, Np = rk.Np, Nft = rt.Nf, nF = rk.nF, NG = rk.NG, NGF = rt.NGF;
+  T.W = rk.vol.w;
+  T.WF = rt.face.w;
+  std::vector<double> dtmp(NG * Np * d);
+  T.Phi.resize(NG * Np);
+  rk.eval(rk.vol.x.data(), NG, T.Phi.data(), dtmp.data());
+  T.dPhi.resize(d * NG * Np);
+  for (int g = 0; g < NG; ++g)
+    for (int a = 0; a < Np; ++a)
+      for (int s = 0; s < d; ++s) T.dPhi[(s * NG + g) * Np + a] = dtmp[(g * Np + a) * d + s];
+  T.PhiF.resize(nF * NGF * Np);
+  T.dPhiF.resize(nF * d * NGF * Np);
+  T.PsiF.resize(nF * NGF * Nft);
+  std::vector<double> dft(NGF * Np * d), pt_all(NGF * rt.Np);
+  for (int f = 0; f < nF; ++f) {
+    rk.eval(rt.fqp[f].data(), NGF, &T.PhiF[f * NGF * Np], dft.data());
+    for (int g = 0; g < NGF; ++g)
+      for (int a = 0; a < Np; ++a)
+        for (int s = 0; s < d; ++s) T.dPhiF[((f * d + s) * NGF + g) * Np + a] = dft[(g * Np + a) * d + s];
+    rt.eval(rt.fqp[f].data(), NGF, pt_all.data(), nullptr);
+    for (int g = 0; g < NGF; ++g)
+      for (int c = 0; c < Nft; ++c) T.PsiF[(f * NGF + g) * Nft + c] = pt_all[g * rt.Np + rt.face_nodes[f][c]];
+  }
+  // reference coordinates of the degree-pt nodes
+  auto node_x = [&](const RefElement& r, int a, double* x) {
+    for (int s = 0; s < d; ++s) x[s] = (double)r.idx[a * d + s] / (double)r.p;
+  };
+  T.PhiN.resize(nF * Nft * Np);
+  {
+    std::vector<double> x(d);
+    for (int f = 0; f < nF; ++f)
+      for (int c = 0; c < Nft; ++c) {
+        node_x(rt, rt.face_nodes[f][c], x.data());
+        rk.eval(x.data(), 1, &T.PhiN[(f * Nft + c) * Np], nullptr);
+      }
+  }
+  T.fnodesK.resize(nF * rk.Nf);
+  for (int f = 0; f < nF; ++f)
+    for (int c = 0; c < rk.Nf; ++c) T.fnodesK[f * rk.Nf + c] = rk.face_nodes[f][c];
+  // lifts L_f = Mref^{-1} E_f with E_f[a][c] = int_f phi_a psi_c (exact: degree pk + pt <= 2 pt + 1)
+  std::vector<double> Mref(Np * Np, 0.0);
+  for (int g = 0; g < NG; ++g)
+    for (int a = 0; a < Np; ++a)
+      for (int b = 0; b < Np; ++b) Mref[a * Np + b] += T.W[g] * T.Phi[g * Np + a] * T.Phi[g * Np + b];
+  std::vector<double> L(nF * Np * Nft);
+  for (int f = 0; f < nF; ++f) {
+    std::vector<double> E(Np * Nft, 0.0);
+    for (int q = 0; q < NGF; ++q)
+      for (int a = 0; a < Np; ++a)
+        for (int c = 0; c < Nft; ++c)
+          E[a * Nft + c] += T.WF[q] * T.PhiF[(f * NGF + q) * Np + a] * T.PsiF[(f * NGF + q) * Nft + c];
+    dense_solve(Mref, E, Np, Nft);
+    for (int i = 0; i < Np * Nft; ++i) L[f * Np * Nft + i] = E[i];
+  }
+  T.PL.assign(nF * NG * Nft, 0.0);
+  for (int f = 0; f < nF; ++f)
+    for (int g = 0; g < NG; ++g)
+      for (int c = 0; c < Nft; ++c) {
+        double s = 0.0;
+        for (int b = 0; b < Np; ++b) s += T.Phi[g * Np + b] * L[(f * Np + b) * Nft + c];
+        T.PL[(f * NG + g) * Nft + c] = s;
+      }
+  T.PLF.assign(nF * nF * NGF * Nft, 0.0);
+  for (int f = 0; f < nF; ++f)
+    for (int fl = 0; fl < nF; ++fl)
+      for (int g = 0; g < NGF; ++g)
+        for (int c = 0; c < Nft; ++c) {
+          double s = 0.0;
+          for (int b = 0; b < Np; ++b) s += T.PhiF[(f * NGF + g) * Np + b] * L[(fl * Np + b) * Nft + c];
+          T.PLF[((f * nF + fl) * NGF + g) * Nft + c] = s;
+        }
+  // the lift of the trace of element function b on face fl: sum_c PL(., c) phi_b(x_c)
+  T.PLV.assign(nF * NG * Np, 0.0);
+  for (int f = 0; f < nF; ++f)
+    for (int g = 0; g < NG; ++g)
+      for (int b = 0; b < Np; ++b) {
+        double s = 0.0;
+        for (int c = 0; c < Nft; ++c) s += T.PL[(f * NG + g) * Nft + c] * T.PhiN[(f * Nft + c) * Np + b];
+        T.PLV[(f * NG + g) * Np + b] = s;
+      }
+  T.PLFV.assign(nF * nF * NGF * Np, 0.0);
+  for (int f = 0; f < nF; ++f)
+    for (int fl = 0; fl < nF; ++fl)
+      for (int g = 0; g < NGF; ++g)
+        for (int b = 0; b < Np; ++b) {
+          double s = 0.0;
+          for (int c = 0; c < Nft; ++c)
+            s += T.PLF[((f * nF + fl) * NGF + g) * Nft + c] * T.PhiN[(fl * Nft + c) * Np + b];
+          T.PLFV[((f * nF + fl) * NGF + g) * Np + b] = s;
+        }
+  // prolongation of the degree-q trace nodes of face f to its degree-pt nodes:
+  // IPro[q-1][f][c][c'] = psi^q_{c'}(x^pt_c) (zero for c' beyond the degree-q face nodes)
+  T.IPro.assign((size_t)pt * nF * Nft * Nft, 0.0);
+  for (int q = 1; q <= pt; ++q) {
+    const RefElement rq = make_refel(dim, q, q + 1);
+    std::vector<double> x(d), vals(rq.Np);
+    for (int f = 0; f < nF; ++f)
+      for (int c = 0; c < Nft; ++c) {
+        node_x(rt, rt.face_nodes[f][c], x.data());
+        rq.eval(x.data(), 1, vals.data(), nullptr);
+        for (int cq = 0; cq < rq.Nf; ++cq)
+          T.IPro[(((size_t)(q - 1) * nF + f) * Nft + c) * Nft + cq] = vals[rq.face_nodes[f][cq]];
+      }
+  }
+  return T;
+}
+
 }  // namespace hdg

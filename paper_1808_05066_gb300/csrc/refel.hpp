@@ -56,4 +56,29 @@ struct RefTables {
 
 RefTables make_tables(const RefElement& r);
 
+// Tables of one element class of a mixed-degree mesh: element degree pk (volume rule with
+// pk + 1 points per direction) and trace degree pt >= pk (face rule with pt + 1 points per
+// direction; the trace space on face f is the nodal space of degree pt on that face, in the
+// face-node order of the degree-pt reference element). With pt = pk the tables equal
+// make_tables(make_refel(dim, pk, pk + 1)) (fnodes aside).
+struct ClassTables {
+  int dim, pk, pt, Np, Nfk, Nft, nF, NG, NGF;
+  std::vector<double> W;      // [NG]
+  std::vector<double> Phi;    // [NG][Np]
+  std::vector<double> dPhi;   // [dim][NG][Np]
+  std::vector<double> WF;     // [NGF]
+  std::vector<double> PhiF;   // [nF][NGF][Np]       element basis at face-f points
+  std::vector<double> dPhiF;  // [nF][dim][NGF][Np]
+  std::vector<double> PsiF;   // [nF][NGF][Nft]      trace basis (degree pt) at face-f points
+  std::vector<double> PhiN;   // [nF][Nft][Np]       element basis at the trace nodes of face f
+  std::vector<double> PL;     // [nF][NG][Nft]       volume values of the lift of trace function c
+  std::vector<double> PLF;    // [nF(points)][nF(lift)][NGF][Nft]
+  std::vector<double> PLV;    // [nF][NG][Np]        lift of the trace of element function b
+  std::vector<double> PLFV;   // [nF(points)][nF(lift)][NGF][Np]
+  std::vector<double> IPro;   // [pt][nF][Nft][Nft]  degree-q trace nodes -> degree-pt nodes (q = 1..pt)
+  std::vector<int> fnodesK;   // [nF][Nfk]           element nodes on face f
+};
+
+ClassTables make_class_tables(int dim, int pk, int pt);
+
 }  // namespace hdg

@@ -48,6 +48,7 @@ EXPORTED = [
     "hdg_axpby", "hdg_assemble_condense_host", "hdg_assemble_condense_graph", "hdg_newton_solve",
     "hdg_ctx_set_refinement", "hdg_ctx_graph_replays", "hdg_ctx_set_trace_solver", "hdg_dirk3_step",
     "hdg_entropy_production", "hdg_mesh_copy_trace_map", "hdg_mesh_copy_face_bc", "hdg_ctx_set_boundary_state",
+    "hdg_mesh_copy_layout",
 ]
 HDG_BC_PERIODIC = 0
 HDG_BC_STATE = 1
@@ -63,7 +64,8 @@ HDG_KERNEL_OTHER = 6
 HDG_KERNEL_MIXED_PREP = 7
 HDG_KERNEL_MIXED_FACE = 8
 HDG_KERNEL_MIXED_OPERATORS = 9
-HDG_KERNEL_CLASSES = 10
+HDG_KERNEL_PCLASS = 10
+HDG_KERNEL_CLASSES = 11
 
 
 class HdgError(RuntimeError):
@@ -89,7 +91,9 @@ class hdg_mesh_info(ctypes.Structure):
                 ("Np", c_int32), ("Nf", c_int32), ("nF", c_int32), ("NG", c_int32), ("NGF", c_int32),
                 ("nv", c_int32), ("nt", c_int32), ("geo_stride", c_int32),
                 ("n_elem", c_int64), ("n_faces", c_int64), ("n_trace", c_int64),
-                ("scheme", c_int32), ("n_trace_nodes", c_int64), ("n_boundary_faces", c_int64)]
+                ("scheme", c_int32), ("n_trace_nodes", c_int64), ("n_boundary_faces", c_int64),
+                ("mixed", c_int32), ("p_min", c_int32), ("len_V", c_int64), ("len_g", c_int64), ("len_S", c_int64),
+                ("len_recov", c_int64), ("len_R", c_int64)]
 
 
 def _load():
@@ -125,6 +129,7 @@ def _load():
         "hdg_ctx_set_trace_solver": (c_int, [P, c_int, c_double, c_int]),
         "hdg_entropy_production": (c_int, [P, P, P, POINTER(c_double), POINTER(c_double), P]),
         "hdg_mesh_copy_trace_map": (c_int, [P, P]),
+        "hdg_mesh_copy_layout": (c_int, [P, P, P, P, P, P, P, P, P]),
         "hdg_dirk3_step": (c_int, [P, P, P, P, c_double, c_int, c_double, c_int, POINTER(c_int), POINTER(c_double),
                                    POINTER(c_int), P]),
         "hdg_mlp_param_count": (c_int64, [c_int, c_int, c_int]),
@@ -245,9 +250,29 @@ def hdg_mesh_copy_trace_map(mesh):
     return tnode
 
 
+def hdg_mesh_copy_layout(mesh):
+    """Packed per-element layout: dict of offsets [E + 1] (voff, toff, soff, roff, Roff), elem_p [E],
+    face_deg [F], face_node_off [F + 1] (host arrays)."""
+    i = hdg_mesh_get_info(mesh)
+    E, F = i["n_elem"], i["n_faces"]
+    out = {k: np.zeros(E + 1, np.int64) for k in ("voff", "toff", "soff", "roff", "Roff")}
+    out["elem_p"] = np.zeros(E, np.int8)
+    out["face_deg"] = np.zeros(F, np.int8)
+    out["face_node_off"] = np.zeros(F + 1, np.int64)
+    _check(_lib.hdg_mesh_copy_layout(mesh, *[_ptr(out[k]) for k in ("voff", "toff", "soff", "roff", "Roff", "elem_p",
+                                                                     "face_deg", "face_node_off")]))
+    return out
+
+
 def hdg_mesh_copy_coords(mesh):
     """(xnode [E][Np][dim], trace-node coordinates ([F][Nf][dim] HDG, [N][dim] EDG), geo)."""
     i = hdg_mesh_get_info(mesh)
+    if i["mixed"]:   # packed: element nodes at each element's degree, trace nodes at each face's
+        xnode = np.zeros((i["len_V"] // i["m"], i["dim"]))
+        xfnode = np.zeros((i["n_trace_nodes"], i["dim"]))
+        geo = np.zeros((i["n_elem"], i["geo_stride"]))
+        _check(_lib.hdg_mesh_copy_coords(mesh, _ptr(xnode), _ptr(xfnode), _ptr(geo)))
+        return xnode, xfnode, geo
     xnode = np.zeros((i["n_elem"], i["Np"], i["dim"]))
     if i["scheme"] == HDG_SCHEME_HDG:
         xfnode = np.zeros((i["n_faces"], i["Nf"], i["dim"]))
@@ -488,6 +513,9 @@ class Mesh:
 
     def trace_map(self):
         return hdg_mesh_copy_trace_map(self.handle)
+
+    def layout(self):
+        return hdg_mesh_copy_layout(self.handle)
 
     def coords(self):
         return hdg_mesh_copy_coords(self.handle)

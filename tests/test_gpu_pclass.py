@@ -1,0 +1,126 @@
+"""GPU parity of the mixed-degree assemble + condense (one persistent launch over the element
+classes (p_e, largest face degree)) against the FP64 oracle, element by element, on 3D
+Navier-Stokes tetrahedra with seeded random degrees 1..4 (face degree max(p_L, p_R)); every class
+present is compared on every element, or on a seeded sample for the larger mesh."""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as wl
+from hdg_cases import rel_fro
+
+pytestmark = pytest.mark.gpu
+
+MACH, RE, PR = 0.1, 1600.0, 0.71
+L = 2 * math.pi
+MASS = 20.0
+
+
+def _prim(x):
+    rho, vel, p = wl.tgv_field(x * (2 * math.pi / L) + 0.3, MACH)
+    return np.concatenate([rho[..., None], vel, p[..., None]], axis=-1)
+
+
+def _setup(n, degs, seed):
+    import torch
+    from oracle import physics as ph
+    from oracle.hdg import Problem, consistent_Q, interpolate_state
+    from oracle.mesh import Mesh as OMesh
+    from paper_1808_05066_gb300 import hdg
+    E = 6 * n ** 3
+    pe = np.random.default_rng(seed).choice(degs, size=E).astype(np.int8)
+    # oracle
+    om = OMesh(3, n, 0.0, L, 0, p_elem=pe)
+    prob = Problem(om, ph.Physics(mach=MACH, reynolds=RE, prandtl=PR))
+    prim_fn = lambda x: wl.tgv_field(x * (2 * math.pi / L) + 0.3, MACH)
+    V, Vh = interpolate_state(prob, prim_fn)
+    Vh = wl.perturb(Vh, 1e-3, seed + 1)
+    hist = [prob.history_weak(e, [V[e] * (1 + 1e-3)], [MASS]) for e in range(om.E)]
+    # GPU: its own mesh, coordinates and state conversion
+    mesh = hdg.Mesh(3, n, 0.0, L, 0, p_per_elem=pe)
+    ctx = hdg.Context(mesh, 1.4, MACH, RE, PR)
+    info, lay = mesh.info, mesh.layout()
+    xnode, xfnode, _ = mesh.coords()
+    dev = torch.device("cuda", 0)
+
+    def to_v(prim):
+        t = torch.from_numpy(np.ascontiguousarray(prim)).to(dev)
+        out = torch.empty_like(t)
+        hdg.hdg_prim_to_entropy(ctx.handle, t, t.numel() // 5, out)
+        return out
+
+    Vg = to_v(_prim(xnode)).reshape(-1)
+    Vhg = to_v(_prim(xfnode))
+    Vhg = torch.from_numpy(wl.perturb(Vhg.cpu().numpy(), 1e-3, seed + 1)).to(dev).contiguous()
+    histg = torch.from_numpy(np.concatenate([h.ravel() for h in hist])).to(dev)
+    return prob, V, Vh, hist, (hdg, mesh, ctx, info, lay, Vg, Vhg, histg, pe)
+
+
+def _run_gpu(g):
+    import torch
+    hdg, mesh, ctx, info, lay, Vg, Vhg, histg, pe = g
+    dev = Vg.device
+    out = dict(S=torch.empty(info["len_S"], dtype=torch.float64, device=dev),
+               g=torch.empty(info["len_g"], dtype=torch.float64, device=dev),
+               recov=torch.empty(info["len_recov"], dtype=torch.float64, device=dev),
+               R=torch.empty(info["len_R"], dtype=torch.float64, device=dev))
+    st = torch.zeros(info["n_elem"], dtype=torch.int32, device=dev)
+    hdg.hdg_assemble_condense(ctx.handle, Vg, Vhg, histg, MASS, hdg.HDG_PREC_FP64, out["S"], out["g"],
+                              out["recov"], out["R"], st)
+    torch.cuda.synchronize()
+    assert int(st.abs().sum()) == 0
+    return {k: v.cpu().numpy() for k, v in out.items()}
+
+
+def _compare(prob, V, Vh, hist, g, res, elems):
+    lay = g[4]
+    worst = {}
+    for e in elems:
+        Q = prob.consistent_q(e, V[e], prob.gather_trace(Vh, e))
+        ref = prob.condense(e, Q, V[e], prob.gather_trace(Vh, e), MASS, hist[e])
+        nt = int(lay["toff"][e + 1] - lay["toff"][e])
+        nv = V[e].size
+        S = res["S"][lay["soff"][e]:lay["soff"][e + 1]].reshape(nt, nt)
+        ge = res["g"][lay["toff"][e]:lay["toff"][e + 1]]
+        rec = res["recov"][lay["roff"][e]:lay["roff"][e + 1]]
+        X, y = rec[:nv * nt].reshape(nv, nt), rec[nv * nt:]
+        R = res["R"][lay["Roff"][e]:lay["Roff"][e + 1]]
+        nq = Q.size                               # the oracle keeps q; compare the v rows
+        errs = dict(S=rel_fro(S, ref["S"]), g=rel_fro(ge, ref["g"]), X=rel_fro(X, ref["X"][nq:]),
+                    y=rel_fro(y, ref["y"][nq:]))
+        # residuals against the oracle's v rows (its q rows vanish at the consistent q), relative to
+        # the largest of the terms they sum
+        Rv = ref["Rl"][nq:]
+        scale = max(np.abs(Rv).max(), np.abs(ref["Rt"]).max(), np.abs(hist[e]).max(), 1.0)
+        errs["Rv"] = float(np.abs(R[:nv] - Rv).max() / scale)
+        errs["Rt"] = float(np.abs(R[nv:] - ref["Rt"]).max() / scale)
+        key = (int(prob.mesh.p_elem[e]), int(prob.mesh.elem_trace_deg[e]))
+        for k, v in errs.items():
+            worst[(key, k)] = max(worst.get((key, k), 0.0), v)
+    return worst
+
+
+# classes covered: (1,4), (4,4) (every element); (1,2) (1,3) (2,2) (2,3) (3,3) ... (three of each);
+# (1,4) (2,4) (3,3) (3,4) (4,4) (one of each: a p = 4 element costs the oracle about 4 s)
+@pytest.mark.parametrize("n,degs,seed,sample", [(1, (1, 2, 3, 4), 3, None), (2, (1, 2, 3), 5, 3),
+                                                (2, (1, 2, 3, 4), 7, 1)])
+def test_mixed_degree_condensation_matches_oracle(n, degs, seed, sample):
+    prob, V, Vh, hist, g = _setup(n, degs, seed)
+    res = _run_gpu(g)
+    E = prob.mesh.E
+    if sample is None:
+        elems = range(E)
+    else:   # up to `sample` elements of every class present
+        rng = np.random.default_rng(seed)
+        cls = [(int(prob.mesh.p_elem[e]), int(prob.mesh.elem_trace_deg[e])) for e in range(E)]
+        elems = []
+        for c in sorted(set(cls)):
+            ids = [e for e in range(E) if cls[e] == c]
+            elems += list(rng.choice(ids, size=min(sample, len(ids)), replace=False))
+    worst = _compare(prob, V, Vh, hist, g, res, elems)
+    classes = sorted({k[0] for k in worst})
+    assert len(classes) >= 2, classes
+    for (cls, k), v in worst.items():
+        tol = 1e-12 if k in ("Rv", "Rt") else 1e-10
+        assert v <= tol, (cls, k, v)

@@ -80,16 +80,65 @@ def test_edg_numbering_matches_oracle(dim, n, p):
     assert np.array_equal(h.trace_map(), o.face_of[:, :, None] * o.ref.Nf + o.fnode_map)
 
 
-def test_unbuilt_variants_are_reported():
-    """The boundary's argument for meshes of mixed degree exists; such meshes are not built and
-    say so with HDG_ERR_UNSUPPORTED."""
+def test_mixed_degree_variants_that_are_not_built():
+    """Meshes of mixed degree are built periodic, HDG, with the default rules; EDG or bounded
+    axes with mixed degrees say so with HDG_ERR_UNSUPPORTED, degrees outside 1..4 are invalid."""
     hdg = _lib()
+    pe = np.array([2] * 7 + [3], np.int8)
+    m = hdg.Mesh(2, 2, 0.0, 1.0, 0, p_per_elem=pe)
+    assert m.info["mixed"] == 1 and m.info["p"] == 3 and m.info["p_min"] == 2
     with pytest.raises(hdg.HdgError) as ei:
-        hdg.hdg_mesh_create(2, [2, 2], [0, 0], [1, 1], 2, p_per_elem=np.array([2] * 7 + [3], np.int8))
+        hdg.hdg_mesh_create(2, [2, 2], [0, 0], [1, 1], 2, p_per_elem=pe, scheme=hdg.HDG_SCHEME_EDG)
     assert ei.value.code == hdg.HDG_ERR_UNSUPPORTED
+    with pytest.raises(hdg.HdgError) as ei:
+        hdg.hdg_mesh_create(2, [2, 2], [0, 0], [1, 1], 2, p_per_elem=pe, bc=[("state", "state"), ("periodic", "periodic")])
+    assert ei.value.code == hdg.HDG_ERR_UNSUPPORTED
+    with pytest.raises(hdg.HdgError) as ei:
+        hdg.hdg_mesh_create(2, [2, 2], [0, 0], [1, 1], 2, p_per_elem=np.array([2] * 7 + [5], np.int8))
+    assert ei.value.code == hdg.HDG_ERR_INVALID_ARG
     # a per-element array of one degree is the uniform mesh
     m = hdg.Mesh(3, 1, 0.0, 1.0, 2, p_per_elem=np.full(6, 2, np.int8))
-    assert m.info["n_elem"] == 6 and m.info["p"] == 2
+    assert m.info["n_elem"] == 6 and m.info["p"] == 2 and m.info["mixed"] == 0
+
+
+@pytest.mark.parametrize("dim,n,degs", [(3, 1, (1, 2, 3, 4)), (3, 2, (1, 2, 3, 4)), (2, 3, (1, 2, 3))])
+def test_mixed_degree_mesh_matches_oracle(dim, n, degs):
+    """Face degrees max(p_L, p_R), trace-node numbering, trace map, packed layout and node
+    coordinates of the library's mixed-degree mesh against the oracle's."""
+    from oracle import physics as ph
+    from oracle.hdg import Problem
+    from oracle.refel import refel
+    hdg = _lib()
+    E = (2 * n * n) if dim == 2 else 6 * n ** 3
+    pe = np.random.default_rng(4 + n).choice(degs, size=E).astype(np.int8)
+    L = 2.5
+    m = hdg.Mesh(dim, n, 0.0, L, 0, p_per_elem=pe)
+    o = OMesh(dim, n, 0.0, L, 0, p_elem=pe)
+    prob = Problem(o, ph.Physics(mach=0.3, reynolds=100.0, prandtl=0.71))
+    lay, tn = m.layout(), m.trace_map()
+    face_of, _, _ = m.topology()
+    assert np.array_equal(face_of, o.face_of)
+    assert np.array_equal(lay["elem_p"], pe)
+    assert np.array_equal(lay["face_deg"], o.face_deg)
+    assert np.array_equal(lay["face_node_off"], o.fnode_off)
+    assert m.info["n_trace_nodes"] == o.fnode_off[-1]
+    xnode, xfnode, _ = m.coords()
+    for e in range(E):
+        t = prob.trace_node(e)
+        assert np.array_equal(tn[e][:, :t.shape[1]], t)
+        assert np.all(tn[e][:, t.shape[1]:] == -1)
+        nv, nt = prob.np_e(e) * (dim + 2), int(prob.trace_mask(e).sum())
+        assert lay["voff"][e + 1] - lay["voff"][e] == nv and lay["toff"][e + 1] - lay["toff"][e] == nt
+        assert lay["soff"][e + 1] - lay["soff"][e] == nt * nt
+        assert lay["roff"][e + 1] - lay["roff"][e] == nv * nt + nv
+        assert lay["Roff"][e + 1] - lay["Roff"][e] == nv + nt
+        a = lay["voff"][e] // (dim + 2)
+        assert np.allclose(xnode[a:a + prob.np_e(e)], o.elem_nodes(e), atol=1e-13)
+    for F, sides in enumerate(o.face_elems):
+        e, f = sides[0]
+        r = refel(dim, int(o.face_deg[F]))
+        x = o.X[e, 0] + r.nodes[r.face_nodes[f]] @ o.J[e].T
+        assert np.allclose(xfnode[o.fnode_off[F]:o.fnode_off[F + 1]], x, atol=1e-13)
 
 
 _BOUNDED = {2: [("state", "slip"), ("periodic", "periodic")],
