@@ -19,7 +19,7 @@ OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libhdg.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["capi.cu", "assemble_fp64.cu", "assemble_mixed.cu", "assemble_noalloc.cu", "boundary.cu", "trace.cu",
-           "mlp.cu", "pclass.cu", "refel.cpp", "mesh.cpp"]
+           "mlp.cu", "pclass.cu", "pclass_trace.cu", "refel.cpp", "mesh.cpp"]
 
 
 def _nvcc() -> str:

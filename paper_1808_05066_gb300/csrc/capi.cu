@@ -492,6 +492,16 @@ void hdg_ctx_destroy(hdg_ctx_t c) {
   delete c;
 }
 
+// Array lengths (doubles) of the compute calls: uniform strides, or the packed per-element layout
+// of a mixed-degree mesh
+static int64_t len_S(const hdg_ctx* c) { return c->pm ? c->mesh->m.soff.back() : c->E * (int64_t)c->NT * c->NT; }
+static int64_t len_g(const hdg_ctx* c) { return c->pm ? c->mesh->m.toff.back() : c->E * (int64_t)c->NT; }
+static int64_t len_recov(const hdg_ctx* c) {
+  return c->pm ? c->mesh->m.roff.back() : c->E * ((int64_t)c->NV * c->NT + c->NV);
+}
+static int64_t len_R(const hdg_ctx* c) { return c->pm ? c->mesh->m.Roff.back() : c->E * (int64_t)(c->NV + c->NT); }
+static int64_t len_V(const hdg_ctx* c) { return c->pm ? c->mesh->m.voff.back() : c->E * (int64_t)c->NV; }
+
 // Calls not built for meshes whose elements differ in degree
 #define HDG_UNIFORM_ONLY(ctx, name)                                                      \
   do {                                                                                   \
@@ -529,7 +539,6 @@ int hdg_prim_to_entropy(hdg_ctx_t ctx, const double* prim, int64_t n_points, dou
 int hdg_history(hdg_ctx_t ctx, const double* V0, const double* V1, double c0, double c1, double* hist,
                 void* stream) {
   HDG_REQUIRE(ctx && V0 && hist, "hdg_history: invalid argument");
-  HDG_UNIFORM_ONLY(ctx, "hdg_history");
   DeviceGuard guard(ctx->device);
   return hdg::launch_history(ctx, V0, V1, c0, c1, hist, (cudaStream_t)stream);
 }
@@ -677,7 +686,6 @@ int hdg_entropy_production(hdg_ctx_t ctx, const double* V, const double* Vhat, d
 int hdg_trace_solve(hdg_ctx_t ctx, const double* S, const double* g, double* dVhat, int method, double rtol,
                     int max_it, int* iters, double* final_res, void* stream) {
   HDG_REQUIRE(ctx && S && g && dVhat && iters && final_res, "hdg_trace_solve: null argument");
-  HDG_UNIFORM_ONLY(ctx, "hdg_trace_solve");
   HDG_REQUIRE(method >= HDG_SOLVER_AUTO && method <= HDG_SOLVER_DENSE && rtol > 0.0 && max_it > 0,
               "hdg_trace_solve: invalid method / tolerance");
   DeviceGuard guard(ctx->device);
@@ -686,17 +694,15 @@ int hdg_trace_solve(hdg_ctx_t ctx, const double* S, const double* g, double* dVh
 
 int hdg_recover_interior(hdg_ctx_t ctx, const double* recov, const double* dVhat, double* dV, void* stream) {
   HDG_REQUIRE(ctx && recov && dVhat && dV, "hdg_recover_interior: null argument");
-  HDG_UNIFORM_ONLY(ctx, "hdg_recover_interior");
   DeviceGuard guard(ctx->device);
   return hdg::launch_recover(ctx, recov, dVhat, dV, (cudaStream_t)stream);
 }
 
 int hdg_trace_matvec(hdg_ctx_t ctx, const double* S, const double* x, double* y, void* stream) {
   HDG_REQUIRE(ctx && S && x && y, "hdg_trace_matvec: null argument");
-  HDG_UNIFORM_ONLY(ctx, "hdg_trace_matvec");
   DeviceGuard guard(ctx->device);
   double* work = nullptr;
-  HDG_CK(cudaMallocAsync(&work, sizeof(double) * ctx->E * ctx->NT, (cudaStream_t)stream));
+  HDG_CK(cudaMallocAsync(&work, sizeof(double) * len_g(ctx), (cudaStream_t)stream));
   int rc = hdg::launch_trace_matvec(ctx, S, x, y, work, (cudaStream_t)stream);
   cudaFreeAsync(work, (cudaStream_t)stream);
   return rc;
@@ -704,7 +710,6 @@ int hdg_trace_matvec(hdg_ctx_t ctx, const double* S, const double* x, double* y,
 
 int hdg_residual_norm(hdg_ctx_t ctx, const double* R, double* norm, void* stream) {
   HDG_REQUIRE(ctx && R && norm, "hdg_residual_norm: null argument");
-  HDG_UNIFORM_ONLY(ctx, "hdg_residual_norm");
   DeviceGuard guard(ctx->device);
   return hdg::residual_norm(ctx, R, norm, (cudaStream_t)stream);
 }
@@ -795,17 +800,16 @@ int hdg_newton_solve(hdg_ctx_t ctx, double* V, double* Vhat, const double* hist,
                      int* trace_iters, void* stream) {
   HDG_REQUIRE(ctx && V && Vhat && newton_iters && res_norm && tol > 0.0 && max_newton >= 0,
               "hdg_newton_solve: invalid argument");
-  HDG_UNIFORM_ONLY(ctx, "hdg_newton_solve");
   HDG_REQUIRE(precision == HDG_PREC_FP64 || precision == HDG_PREC_MIXED, "hdg_newton_solve: precision");
   DeviceGuard guard(ctx->device);
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t E = ctx->E;
   if (!ctx->d_S) {
-    HDG_CK(cudaMalloc(&ctx->d_S, sizeof(double) * E * ctx->NT * ctx->NT));
-    if (!ctx->d_g) HDG_CK(cudaMalloc(&ctx->d_g, sizeof(double) * E * ctx->NT));
-    HDG_CK(cudaMalloc(&ctx->d_recov, sizeof(double) * E * (ctx->NV * ctx->NT + ctx->NV)));
-    HDG_CK(cudaMalloc(&ctx->d_R, sizeof(double) * E * (ctx->NV + ctx->NT)));
-    HDG_CK(cudaMalloc(&ctx->d_dV, sizeof(double) * E * ctx->NV));
+    HDG_CK(cudaMalloc(&ctx->d_S, sizeof(double) * len_S(ctx)));
+    if (!ctx->d_g) HDG_CK(cudaMalloc(&ctx->d_g, sizeof(double) * len_g(ctx)));
+    HDG_CK(cudaMalloc(&ctx->d_recov, sizeof(double) * len_recov(ctx)));
+    HDG_CK(cudaMalloc(&ctx->d_R, sizeof(double) * len_R(ctx)));
+    HDG_CK(cudaMalloc(&ctx->d_dV, sizeof(double) * len_V(ctx)));
     HDG_CK(cudaMalloc(&ctx->d_dVh, sizeof(double) * ctx->ntrace));
   }
   if (!ctx->d_status) HDG_CK(cudaMalloc(&ctx->d_status, sizeof(int32_t) * E));
@@ -873,7 +877,7 @@ int hdg_newton_solve(hdg_ctx_t ctx, double* V, double* Vhat, const double* hist,
     if (rc) return rc;
     rc = hdg::launch_recover(ctx, ctx->d_recov, ctx->d_dVh, ctx->d_dV, s);
     if (rc) return rc;
-    rc = hdg::launch_axpy(E * ctx->NV, 1.0, ctx->d_dV, V, s);
+    rc = hdg::launch_axpy(len_V(ctx), 1.0, ctx->d_dV, V, s);
     if (rc) return rc;
     rc = hdg::launch_axpy(ctx->ntrace, 1.0, ctx->d_dVh, Vhat, s);
     if (rc) return rc;
@@ -886,7 +890,6 @@ int hdg_newton_step(hdg_ctx_t ctx, double* V, double* Vhat, const double* V_n, c
                     int* newton_iters, double* res_norm, double* res_history, int* trace_iters, void* stream) {
   HDG_REQUIRE(ctx && V && Vhat && newton_iters && res_norm && tol > 0.0 && max_newton >= 0,
               "hdg_newton_step: invalid argument");
-  HDG_UNIFORM_ONLY(ctx, "hdg_newton_step");
   HDG_REQUIRE(bdf_order >= 0 && bdf_order <= 2, "hdg_newton_step: bdf_order must be 0, 1 or 2");
   HDG_REQUIRE(bdf_order == 0 || (dt > 0.0 && V_n), "hdg_newton_step: BDF needs dt > 0 and V_n");
   HDG_REQUIRE(bdf_order < 2 || V_nm1, "hdg_newton_step: BDF2 needs V_nm1");
@@ -895,7 +898,7 @@ int hdg_newton_step(hdg_ctx_t ctx, double* V, double* Vhat, const double* V_n, c
   HDG_REQUIRE(precision == HDG_PREC_FP64 || precision == HDG_PREC_MIXED, "hdg_newton_step: precision");
   DeviceGuard guard(ctx->device);
   cudaStream_t s = (cudaStream_t)stream;
-  const int64_t nV = ctx->E * ctx->NV;
+  const int64_t nV = len_V(ctx);
   // BDF coefficients: mass_coef (u(v), w) - hist, hist = c0 (u(v^n), w) + c1 (u(v^{n-1}), w)
   double mass = 0.0;
   const double* hist = nullptr;
@@ -913,8 +916,8 @@ int hdg_newton_step(hdg_ctx_t ctx, double* V, double* Vhat, const double* V_n, c
   // Learned (or element-local) start: the caller's guess (V0, Vhat0) is linearised once;
   // the network's trace (or Vhat0 itself) takes the place of the first global trace solve and
   // the interior follows from the element-local recovery dV = -y - X P (vhat_m - Vhat0).
-  if (ctx->scheme) {
-    set_error("hdg_newton_step: the learned warm start works on face traces (HDG) only");
+  if (ctx->scheme || ctx->pm) {
+    set_error("hdg_newton_step: the learned warm start works on face traces (HDG) of one degree only");
     return HDG_ERR_UNSUPPORTED;
   }
   const hdg_warmstart& w = *warmstart;

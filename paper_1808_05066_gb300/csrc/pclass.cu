@@ -851,6 +851,31 @@ int pclass_setup(hdg_ctx* c) {
     cls[e] = (int8_t)pclass_index(m.pe[e], m.ptr[e]);
     pm->class_count[cls[e]]++;
   }
+  // trace addressing: own face-node counts, the two local occurrences of every trace node,
+  // face-block offsets
+  std::vector<int> fnn(E * NF), occ_e(2 * m.fnoff.back(), -1), occ_l(2 * m.fnoff.back(), -1);
+  std::vector<int64_t> pcoff(c->F + 1, 0);
+  for (int64_t e = 0; e < E; ++e) {
+    int qoff = 0;
+    for (int f = 0; f < NF; ++f) {
+      const int64_t F = m.face_of[e * NF + f];
+      const int nq = nfn(m.fdeg[F]);
+      fnn[e * NF + f] = nq;
+      const int side = m.face_side[2 * F] == (int32_t)(e * NF + f) ? 0 : 1;
+      for (int cl = 0; cl < nq; ++cl) {
+        const int64_t t = m.fnoff[F] + m.fnode_mix[(e * NF + f) * pm->nfn_max + cl];
+        occ_e[2 * t + side] = (int)e;
+        occ_l[2 * t + side] = qoff + cl * 5;
+      }
+      qoff += nq * 5;
+    }
+    pm->nt_max = std::max(pm->nt_max, qoff);
+  }
+  for (int64_t F = 0; F < c->F; ++F) {
+    const int64_t B = (m.fnoff[F + 1] - m.fnoff[F]) * 5;
+    pcoff[F + 1] = pcoff[F] + B * B;
+  }
+  pm->pc_len = pcoff.back();
   // queue: largest class first (interior size, then trace degree), element order within a class
   std::vector<int> queue(E);
   for (int64_t e = 0; e < E; ++e) queue[e] = (int)e;
@@ -862,7 +887,9 @@ int pclass_setup(hdg_ctx* c) {
   if ((rc = up(&pm->d_tab, tab)) || (rc = up(&pm->d_itab, itab)) || (rc = up(&pm->d_voff, m.voff)) ||
       (rc = up(&pm->d_toff, m.toff)) || (rc = up(&pm->d_soff, m.soff)) || (rc = up(&pm->d_roff, m.roff)) ||
       (rc = up(&pm->d_Roff, m.Roff)) || (rc = up(&pm->d_tgidx, tg)) || (rc = up(&pm->d_fdeg, fdeg)) ||
-      (rc = up(&pm->d_cls, cls)) || (rc = up(&pm->d_queue, queue)))
+      (rc = up(&pm->d_cls, cls)) || (rc = up(&pm->d_queue, queue)) || (rc = up(&pm->d_fnn, fnn)) ||
+      (rc = up(&pm->d_occ_e, occ_e)) || (rc = up(&pm->d_occ_l, occ_l)) || (rc = up(&pm->d_fnoff, m.fnoff)) ||
+      (rc = up(&pm->d_pcoff, pcoff)))
     return rc;
   HDG_CK(cudaMalloc(&pm->d_counter, sizeof(int)));
   for (int k = 0; k < kPClasses; ++k) {
@@ -895,8 +922,9 @@ int pclass_setup(hdg_ctx* c) {
 
 void pclass_free(PMix* pm) {
   if (!pm) return;
-  void* bufs[] = {pm->d_voff, pm->d_toff, pm->d_soff, pm->d_roff, pm->d_Roff, pm->d_tgidx, pm->d_fdeg,
-                  pm->d_cls,  pm->d_queue, pm->d_counter, pm->d_tab, pm->d_itab};
+  void* bufs[] = {pm->d_voff, pm->d_toff,  pm->d_soff,    pm->d_roff, pm->d_Roff,  pm->d_tgidx,
+                  pm->d_fdeg, pm->d_cls,   pm->d_queue,   pm->d_counter, pm->d_tab, pm->d_itab,
+                  pm->d_fnn,  pm->d_occ_e, pm->d_occ_l,   pm->d_fnoff, pm->d_pcoff};
   for (void* b : bufs)
     if (b) cudaFree(b);
   delete pm;

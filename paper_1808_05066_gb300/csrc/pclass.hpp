@@ -35,6 +35,14 @@ struct PMix {
   int* d_tgidx = nullptr;     // [E][NF][nfn_max] trace node of each local face node, -1 beyond
   int8_t* d_fdeg = nullptr;   // [E][NF]
   int8_t* d_cls = nullptr;    // [E] class index
+  int* d_fnn = nullptr;       // [E][NF] own face nodes of each face of the element (Nf(q_f))
+  int* d_occ_e = nullptr;     // [trace nodes][2] element of each side of the node's face (-1: none)
+  int* d_occ_l = nullptr;     // [trace nodes][2] first unknown of the node in that element's trace vector
+  int64_t* d_fnoff = nullptr; // [F + 1] first trace node of each face
+  int64_t* d_pcoff = nullptr; // [F + 1] face-block preconditioner offsets (sum of B_F^2)
+  int64_t pc_len = 0;         // doubles of the face-block preconditioner
+  int nt_max = 0;             // largest element trace vector
+  bool attr_face = false;
   int* d_queue = nullptr;     // [E] elements, largest class first
   int* d_counter = nullptr;   // work counter of the persistent launch
   double* d_tab = nullptr;
@@ -46,10 +54,29 @@ struct PMix {
   bool attr_set = false;
 };
 
+// the device addressing of the packed layout, passed to the trace kernels by value
+struct PMixDev {
+  const int64_t *voff, *toff, *soff, *roff, *Roff, *fnoff, *pcoff;
+  const int *tgidx, *fnn, *occ_e, *occ_l;
+  const int8_t* cls;
+  int nfn_max;
+  PClassDev tab[kPClasses];
+};
+
 int pclass_index(int pk, int pt);
 // class tables, layout and queue of a mixed-degree mesh; frees with pclass_free
 int pclass_setup(hdg_ctx* c);
 void pclass_free(PMix* pm);
+PMixDev pmix_dev(const hdg_ctx* c);
+// trace-space operations of pclass_trace.cu (the packed layout's counterparts of trace.cu)
+int pm_history(hdg_ctx* c, const double* V0, const double* V1, double c0, double c1, double* hist, cudaStream_t s);
+int pm_gather(hdg_ctx* c, const double* ge, double scale, double* out, cudaStream_t s);
+int pm_elem_matvec(hdg_ctx* c, const double* S, const double* x, double* w, cudaStream_t s);
+int pm_recover(hdg_ctx* c, const double* recov, const double* dvh, double* dV, cudaStream_t s);
+int pm_sumsq(hdg_ctx* c, const double* R, double* red, cudaStream_t s);
+int pm_face_factor(hdg_ctx* c, const double* S, double* pc, cudaStream_t s);
+int pm_face_apply(hdg_ctx* c, const double* pc, const double* r, double* z, cudaStream_t s);
+int pm_dense_scatter(hdg_ctx* c, const double* S, int64_t n, double* K, cudaStream_t s);
 int assemble_condense_pclass(hdg_ctx* c, const double* V, const double* Vhat, const double* hist, double mass_coef,
                              double* S, double* g, double* recov, double* R, int32_t* status, cudaStream_t s);
 

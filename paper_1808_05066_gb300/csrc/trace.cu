@@ -644,6 +644,7 @@ int launch_prim_to_entropy(hdg_ctx* ctx, const double* prim, int64_t n, double* 
 
 int launch_history(hdg_ctx* ctx, const double* V0, const double* V1, double c0, double c1, double* hist,
                    cudaStream_t s) {
+  if (ctx->pm) return pm_history(ctx, V0, V1, c0, c1, hist, s);
   size_t sm = sizeof(double) * ctx->NG * ctx->M;
   if (ctx->dim == 2)
     k_history<2><<<(unsigned)ctx->E, 128, sm, s>>>(ctx->T, ctx->d_geo, ctx->GEO, ctx->NP, ctx->NG, V0, V1, c0, c1,
@@ -656,6 +657,7 @@ int launch_history(hdg_ctx* ctx, const double* V0, const double* V1, double c0, 
 }
 
 int launch_trace_rhs(hdg_ctx* ctx, const double* g, double* rhs, cudaStream_t s) {
+  if (ctx->pm) return pm_gather(ctx, g, -1.0, rhs, s);
   if (ctx->scheme)
     k_node_gather<<<nblocks(ctx->ntrace), kThreads, 0, s>>>(ctx->d_tr_ptr, ctx->d_tr_occ, ctx->n_tnodes, ctx->M, g,
                                                            -1.0, rhs);
@@ -667,6 +669,7 @@ int launch_trace_rhs(hdg_ctx* ctx, const double* g, double* rhs, cudaStream_t s)
 }
 
 static int launch_gather(hdg_ctx* ctx, const double* work, double* y, cudaStream_t s) {
+  if (ctx->pm) return pm_gather(ctx, work, 1.0, y, s);
   if (ctx->scheme)
     k_node_gather<<<nblocks(ctx->ntrace), kThreads, 0, s>>>(ctx->d_tr_ptr, ctx->d_tr_occ, ctx->n_tnodes, ctx->M, work,
                                                            1.0, y);
@@ -678,6 +681,10 @@ static int launch_gather(hdg_ctx* ctx, const double* work, double* y, cudaStream
 }
 
 int launch_trace_matvec(hdg_ctx* ctx, const double* S, const double* x, double* y, double* work, cudaStream_t s) {
+  if (ctx->pm) {
+    if (int rc = pm_elem_matvec(ctx, S, x, work, s)) return rc;
+    return pm_gather(ctx, work, 1.0, y, s);
+  }
   k_elem_matvec<<<(unsigned)ctx->E, 256, sizeof(double) * ctx->NT, s>>>(S, x, ctx->d_tgidx, ctx->NT, ctx->M, work);
   return launch_gather(ctx, work, y, s);
 }
@@ -705,6 +712,7 @@ static int launch_trace_matvec_df(hdg_ctx* ctx, const df2* Sdf, const double* x,
 }
 
 int launch_recover(hdg_ctx* ctx, const double* recov, const double* dVhat, double* dV, cudaStream_t s) {
+  if (ctx->pm) return pm_recover(ctx, recov, dVhat, dV, s);
   k_recover<<<(unsigned)ctx->E, 256, sizeof(double) * ctx->NT, s>>>(recov, dVhat, ctx->d_tgidx, ctx->NV, ctx->NT,
                                                                    ctx->M, dV);
   HDG_CK(cudaGetLastError());
@@ -736,6 +744,9 @@ int residual_norm(hdg_ctx* ctx, const double* R, double* norm, cudaStream_t s) {
   int rc = ensure_red(ctx);
   if (rc) return rc;
   HDG_CK(cudaMemsetAsync(ctx->d_red, 0, sizeof(double) * 2, s));
+  if (ctx->pm) {
+    if ((rc = pm_sumsq(ctx, R, ctx->d_red, s))) return rc;
+  } else {
   k_sumsq_elem_rows<<<nblocks(ctx->E * (int64_t)ctx->NV), kThreads, 0, s>>>(R, ctx->E, ctx->NV + ctx->NT, ctx->NV,
                                                                            ctx->d_red);
   if (ctx->scheme)
@@ -744,6 +755,7 @@ int residual_norm(hdg_ctx* ctx, const double* R, double* norm, cudaStream_t s) {
   else
     k_sumsq_trace_residual<<<nblocks(ctx->ntrace), kThreads, 0, s>>>(R, ctx->d_fs_elem, ctx->d_fs_loc, ctx->F,
                                                                     ctx->NFN, ctx->M, ctx->NV, ctx->NT, ctx->d_red + 1);
+  }
   HDG_CK(cudaGetLastError());
   HDG_CK(cudaMemcpyAsync(ctx->h_red, ctx->d_red, sizeof(double) * 2, cudaMemcpyDeviceToHost, s));
   HDG_CK(cudaStreamSynchronize(s));
@@ -775,8 +787,12 @@ static int dense_solve(hdg_ctx* ctx, const double* S, const double* g, double* d
   int* bad = ctx->d_dpiv + n;
   HDG_CK(cudaMemsetAsync(K, 0, sizeof(double) * n * n, s));
   HDG_CK(cudaMemsetAsync(bad, 0, sizeof(int), s));
-  k_dense_scatter<<<nblocks(ctx->E * (int64_t)ctx->NT * ctx->NT), kThreads, 0, s>>>(S, ctx->d_tgidx, ctx->E, ctx->NT,
-                                                                                   ctx->M, n, K);
+  if (ctx->pm) {
+    if ((rc = pm_dense_scatter(ctx, S, n, K, s))) return rc;
+  } else {
+    k_dense_scatter<<<nblocks(ctx->E * (int64_t)ctx->NT * ctx->NT), kThreads, 0, s>>>(S, ctx->d_tgidx, ctx->E,
+                                                                                     ctx->NT, ctx->M, n, K);
+  }
   // LU with partial pivoting: 3 launches per pivot, recorded once per context into a CUDA
   // graph (on a context-owned stream, so the caller's stream may be the legacy default
   // stream) and replayed on the caller's stream.
@@ -828,7 +844,8 @@ static int gmres_solve(hdg_ctx* ctx, const double* S, const double* g, double* x
   const int64_t n = ctx->ntrace;
   const int B = ctx->NFN * ctx->M;
   // workspace: basis V (m+1) n, Z (precond of current basis vector) n, w n, b n, elem work E*NT
-  const size_t need = sizeof(double) * ((size_t)(m + 1) * n + 3 * (size_t)n + (size_t)ctx->E * ctx->NT);
+  const size_t elem_work = ctx->pm ? (size_t)ctx->mesh->m.toff.back() : (size_t)ctx->E * ctx->NT;
+  const size_t need = sizeof(double) * ((size_t)(m + 1) * n + 3 * (size_t)n + elem_work);
   if (ctx->sw_bytes < need) {
     if (ctx->d_sw) cudaFree(ctx->d_sw);
     ctx->d_sw = nullptr;
@@ -836,7 +853,9 @@ static int gmres_solve(hdg_ctx* ctx, const double* S, const double* g, double* x
     HDG_CK(cudaMalloc(&ctx->d_sw, need));
     ctx->sw_bytes = need;
   }
-  if (ctx->scheme) {
+  if (ctx->pm) {
+    if (!ctx->d_pc) HDG_CK(cudaMalloc(&ctx->d_pc, sizeof(double) * ctx->pm->pc_len));
+  } else if (ctx->scheme) {
     if (!ctx->d_pcn) HDG_CK(cudaMalloc(&ctx->d_pcn, sizeof(double) * ctx->n_tnodes * ctx->M * ctx->M));
   } else {
     if (B > kMaxFaceBlock || 2 * sizeof(double) * B * B > 48 * 1024) {  // factor + inverse in shared memory
@@ -852,7 +871,9 @@ static int gmres_solve(hdg_ctx* ctx, const double* S, const double* g, double* x
   double* w = zt + n;
   double* b = w + n;
   double* ew = b + n;
-  if (ctx->scheme)  // EDG: node-block Jacobi
+  if (ctx->pm) {  // mixed degrees: face blocks of each face's own size
+    if ((rc = pm_face_factor(ctx, S, ctx->d_pc, s))) return rc;
+  } else if (ctx->scheme)  // EDG: node-block Jacobi
     k_node_block_factor<<<nblocks(ctx->n_tnodes), kThreads, 0, s>>>(S, ctx->d_tr_ptr, ctx->d_tr_occ, ctx->n_tnodes,
                                                                     ctx->M, ctx->NT, ctx->d_pcn);
   else  // HDG: face-block Jacobi
@@ -861,7 +882,7 @@ static int gmres_solve(hdg_ctx* ctx, const double* S, const double* g, double* x
   // the double-float copy of S for the Arnoldi products (the restart and final residuals use S
   // itself); without room for it every product is the FP64 one
   const size_t sdf_bytes = sizeof(df2) * (size_t)ctx->E * ctx->NT * ctx->NT;
-  if (ctx->sdf_bytes < sdf_bytes && !ctx->sdf_unavailable) {
+  if (!ctx->pm && ctx->sdf_bytes < sdf_bytes && !ctx->sdf_unavailable) {
     if (ctx->d_Sdf) cudaFree(ctx->d_Sdf);
     ctx->d_Sdf = nullptr;
     ctx->sdf_bytes = 0;
@@ -874,7 +895,7 @@ static int gmres_solve(hdg_ctx* ctx, const double* S, const double* g, double* x
     }
   }
   const df2* Sdf = nullptr;
-  if (ctx->d_Sdf) {
+  if (ctx->d_Sdf && !ctx->pm) {
     const int64_t ns = (int64_t)ctx->E * ctx->NT * ctx->NT;
     k_split_df<<<nblocks(ns), kThreads, 0, s>>>(S, ns, static_cast<df2*>(ctx->d_Sdf));
     Sdf = static_cast<const df2*>(ctx->d_Sdf);
@@ -886,7 +907,9 @@ static int gmres_solve(hdg_ctx* ctx, const double* S, const double* g, double* x
   if (rc) return rc;
   const int wpb = 8;
   auto precond = [&](const double* r, double* z) {
-    if (ctx->scheme)
+    if (ctx->pm)
+      pm_face_apply(ctx, ctx->d_pc, r, z, s);
+    else if (ctx->scheme)
       k_node_block_apply<<<nblocks(n), kThreads, 0, s>>>(ctx->d_pcn, ctx->n_tnodes, ctx->M, r, z);
     else
       k_face_block_apply<<<(unsigned)((ctx->F + wpb - 1) / wpb), 32 * wpb, sizeof(double) * wpb * B, s>>>(

@@ -2,6 +2,7 @@
 classes (p_e, largest face degree)) against the FP64 oracle, element by element, on 3D
 Navier-Stokes tetrahedra with seeded random degrees 1..4 (face degree max(p_L, p_R)); every class
 present is compared on every element, or on a seeded sample for the larger mesh."""
+import functools
 import math
 
 import numpy as np
@@ -124,3 +125,37 @@ def test_mixed_degree_condensation_matches_oracle(n, degs, seed, sample):
     for (cls, k), v in worst.items():
         tol = 1e-12 if k in ("Rv", "Rt") else 1e-10
         assert v <= tol, (cls, k, v)
+
+
+@functools.lru_cache(maxsize=None)
+def _oracle_bdf2_step(dt):
+    from oracle.hdg import time_step
+    prob, V, Vh, _hist, _g = _setup(2, (1, 2), 9)
+    Q = [prob.consistent_q(e, V[e], prob.gather_trace(Vh, e)) for e in range(prob.mesh.E)]
+    return time_step(prob, Q, V, Vh, [V, [v * (1.0 + 1e-3) for v in V]], 2, dt, tol=1e-12, max_it=12)
+
+
+@pytest.mark.parametrize("solver", ["dense", "gmres"])
+def test_mixed_degree_bdf_newton_step_matches_oracle(solver):
+    """One BDF2 time step on a mixed-degree mesh (3D Navier-Stokes, degrees 1 and 2, 48 tets):
+    hdg_newton_step (condensation in one persistent launch, trace solve with the dense LU or
+    GMRES with face blocks of each face's own size, recovery) against the oracle's time step: the
+    same Newton updates, the same first residual and the same state."""
+    import torch
+    prob, V, Vh, _hist, g = _setup(2, (1, 2), 9)
+    hdg, mesh, ctx, info, lay, Vg, Vhg, _histg, pe = g
+    dt = 0.05
+    res = _oracle_bdf2_step(dt)
+    hdg.hdg_ctx_set_trace_solver(ctx.handle, hdg.HDG_SOLVER_DENSE if solver == "dense" else hdg.HDG_SOLVER_GMRES,
+                                 1e-13, 3000)
+    V_gpu, Vh_gpu = Vg.clone(), Vhg.clone()
+    V_nm1 = (Vg * (1.0 + 1e-3)).contiguous()
+    it, rn, rh, _tr = hdg.hdg_newton_step(ctx.handle, V_gpu, Vh_gpu, Vg, V_nm1, dt, 2, hdg.HDG_PREC_FP64, 1e-12, 12,
+                                          history=True)
+    torch.cuda.synchronize()
+    assert it == res.iters, (it, res.iters)
+    assert abs(rh[0] - res.res_norms[0]) <= 1e-12 * res.res_norms[0]
+    assert rn <= 1e-12 * max(1.0, rh[0])
+    Vo = np.concatenate([v.ravel() for v in res.V])
+    assert rel_fro(V_gpu.cpu().numpy(), Vo) < 1e-10
+    assert rel_fro(Vh_gpu.cpu().numpy().reshape(-1), res.Vhat.reshape(-1)) < 1e-10
