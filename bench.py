@@ -186,6 +186,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-newton", action="store_true", help="skip the Newton-step wall time")
+    ap.add_argument("--no-mixed-degree", action="store_true", help="skip the mixed-degree batch")
+    ap.add_argument("--mixed-degree-steps", type=int, default=2)
+    ap.add_argument("--mixed-degree-newton", action="store_true",
+                    help="also time one BDF2 Newton step of the mixed-degree batch")
     return ap.parse_args()
 
 
@@ -247,6 +251,59 @@ def run_reference(args):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def mixed_degree_leg(args, local, barrier, max_over_ranks, ws):
+    """Elements/s of the FP64 assemble + condense of the mixed-degree workload (one persistent
+    launch per step over the element classes, tile shapes tuned per class on the first call),
+    with the class census and, on request, one BDF2 Newton step."""
+    import torch
+    from paper_1808_05066_gb300 import hdg
+    from paper_1808_05066_gb300.workload import DeviceWorkload
+    name = "ns3d_mixed_tgv"
+    try:
+        W = DeviceWorkload(name, device=local, n_override=args.n)
+        E = W.info["n_elem"]
+        dev = W.dev
+        for _ in range(2):  # the first call tunes the tile shapes
+            W.status.zero_()
+            W.assemble(hdg.HDG_PREC_FP64)
+        torch.cuda.synchronize(dev)
+        hdg.hdg_profile_reset(W.ctx.handle)
+        barrier()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(args.mixed_degree_steps):
+            W.assemble(hdg.HDG_PREC_FP64)
+        b.record()
+        torch.cuda.synchronize(dev)
+        ms = max_over_ranks(a.elapsed_time(b))
+        launches, _ = hdg.hdg_profile_read(W.ctx.handle, hdg.HDG_KERNEL_PCLASS)
+        bad = int((W.status != 0).sum())
+        census = {int(p): int((W.p_elem == p).sum()) for p in (1, 2, 3, 4)}
+        out = {"workload": name, "elements": E, "degrees": census,
+               "face_degree": "max(p_L, p_R)", "value": ws * E * args.mixed_degree_steps / (ms / 1000.0),
+               "unit": "elem/s", "ms_per_step": ms / args.mixed_degree_steps, "steps": args.mixed_degree_steps,
+               "precision": "fp64", "launches_per_step": launches / args.mixed_degree_steps,
+               "elements_flagged": bad,
+               "bytes_written_per_step": 8 * (W.info["len_S"] + W.info["len_g"] + W.info["len_recov"] +
+                                              W.info["len_R"])}
+        if args.mixed_degree_newton:
+            del W.S, W.recov
+            torch.cuda.empty_cache()
+            hdg.hdg_ctx_set_trace_solver(W.ctx.handle, hdg.HDG_SOLVER_GMRES, 1e-12, 600)
+            Vn, Vhn = W.V.clone(), W.Vhat.clone()
+            barrier()
+            t0 = time.perf_counter()
+            it, rn, rh, tr = hdg.hdg_newton_step(W.ctx.handle, Vn, Vhn, W.V, W.V, W.dt, 2, hdg.HDG_PREC_FP64, 1e-10,
+                                                 8, history=True)
+            torch.cuda.synchronize(dev)
+            out["newton_step"] = {"wall_ms": 1e3 * (time.perf_counter() - t0), "newton_updates": it,
+                                  "final_res_norm": rn, "residual_history": rh, "trace_iterations": tr}
+        W.close()
+        return out
+    except Exception as exc:  # recorded, not hidden
+        return {"error": str(exc)}
 
 
 def main():
@@ -442,6 +499,16 @@ def main():
         if prec != hdg.HDG_PREC_FP64:
             newton64 = newton_step(hdg.HDG_PREC_FP64)
 
+    # ---------------- mixed-degree batch: the 32^3 cube (196,608 tets) with degrees 1..4 drawn per
+    # element, FP64, every element in one persistent fused launch per step
+    mixed_degree = None
+    cube_n = W.spec["n"]
+    if not args.no_mixed_degree:
+        W.close()
+        del W
+        torch.cuda.empty_cache()
+        mixed_degree = mixed_degree_leg(args, local, barrier, max_over_ranks, ws)
+
     # ---------------- CPU baseline (oracle), rank 0 at N=1 only
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -457,12 +524,12 @@ def main():
             "dtype": "bf16x6-slice(FP64-accurate)+f32+f64" if prec == hdg.HDG_PREC_MIXED else "f64",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "elements_per_gpu": E, "dim": 3, "p": 3, "physics": "navier-stokes",
-                       "mesh": f"{W.spec['n']}^3 periodic cube x 6 tets", "precision": args.precision,
+                       "mesh": f"{cube_n}^3 periodic cube x 6 tets", "precision": args.precision,
                        "l2": "inputs+outputs larger than L2 (S alone 26.5 GB written per step)",
                        "parallelism": f"replica per GPU x{ws}"},
             "roofline": roof, "kernel_time_share": shares, "gpu_launches": launches_total,
             "fp64_form": fp64_form, "newton_step": newton, "newton_step_inexact": newton_ew,
-            "newton_step_fp64": newton64,
+            "newton_step_fp64": newton64, "mixed_degree": mixed_degree,
             "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)

@@ -45,10 +45,11 @@ constexpr int D3 = 3, M5 = 5, NF4 = 4, GEO3 = D3 * D3 + 1 + NF4 * (D3 + 1);
 constexpr int NR3 = D3 + 1, NRF3 = D3 + 2;  // value (+ gradient) right operators, volume and face
 constexpr int PT_VOL = M5 + D3 * M5 + M5 * M5 + D3 * M5 * M5 + D3 * M5 * M5 * D3;
 constexpr int PT_FACE = M5 + 2 * M5 * M5 + M5 * M5 * D3;
-constexpr int kCB = 32;               // right-hand-side columns per block of the triangular solves
 constexpr int kLuSmemMax = 12000;     // A' (doubles) factored in shared memory up to this size
 
-inline PDims pclass_dims(int pk, int pt) {
+// gt: volume points per contraction tile; cb: right-hand-side columns per block of the
+// triangular solves (both chosen per class by the autotuner, pclass_autotune)
+inline PDims pclass_dims(int pk, int pt, int gt = 32, int cb = 32) {
   PDims d{};
   d.pk = pk;
   d.pt = pt;
@@ -60,13 +61,14 @@ inline PDims pclass_dims(int pk, int pt) {
   d.NV = d.NP * M5;
   d.NT = NF4 * d.NFN * M5;
   d.NZ = d.NP + NF4 * d.NFN;
-  d.GT = d.NG < 32 ? d.NG : 32;
+  d.GT = d.NG < gt ? d.NG : gt;
+  d.CB = cb;
   const int RB = NR3 * d.GT * d.NZ, RBF = NRF3 * d.NGF * d.NZ;
   const int ZS = d.NP * d.GT * NR3, ZSF = (d.NFK + d.NFN) * d.NGF * NRF3;
   d.RBMAX = RB > RBF ? RB : RBF;
   d.ASM = d.RBMAX + (ZS > ZSF ? ZS : ZSF);
   d.lu_smem = d.NV * d.NV <= kLuSmemMax ? 1 : 0;
-  d.CND = (d.lu_smem ? d.NV * d.NV : 0) + d.NV * kCB;
+  d.CND = (d.lu_smem ? d.NV * d.NV : 0) + d.NV * cb;
   d.KEEP = d.NZ * M5 + GEO3 + NF4 * d.NFN * M5 + d.NV + d.NT;
   d.SMEM = d.KEEP + (d.ASM > d.CND ? d.ASM : d.CND) + (d.NV + 1) / 2 + 2;  // + pivots (int)
   d.SLOT = (int64_t)d.NG * PT_VOL + (int64_t)NF4 * d.NGF * PT_FACE + (int64_t)d.NV * d.NV +
@@ -524,9 +526,8 @@ __device__ void pc_factor(double* LU, int NV, int* piv, int* s_misc, int64_t e, 
 }
 
 // X = A'^{-1} [B_q | R_v] in place (B_q in X, row stride nt), y = A'^{-1} R_v.
-__device__ void pc_solve(const double* LU, int NV, const int* piv, double* Xs, double* X, double* y, const double* Rv,
-                         int nt) {
-  constexpr int CB = kCB;
+__device__ void pc_solve(const double* LU, int NV, int CB, const int* piv, double* Xs, double* X, double* y,
+                         const double* Rv, int nt) {
   const int tid = threadIdx.x, nth = blockDim.x;
   for (int c0 = 0; c0 < nt + 1; c0 += CB) {
     const int nc = (nt + 1 - c0) < CB ? (nt + 1 - c0) : CB;
@@ -690,7 +691,7 @@ __device__ void pc_element(const PArgs& a, const PClassDev& T, const PhysParams&
     for (int t = tid; t < NV * NV; t += nth) LU[t] = Ap[t];
   __syncthreads();
   pc_factor(LU, NV, piv, s_misc, e, a);
-  pc_solve(LU, NV, piv, Xs, X, y, Re, ntq);
+  pc_solve(LU, NV, T.d.CB, piv, Xs, X, y, Re, ntq);
   for (int t = tid; t < ntq * ntq; t += nth) {  // S = D_q - C_q X
     const int r = t / ntq, c = t % ntq;
     double s = S[t];
@@ -731,6 +732,92 @@ int pclass_index(int pk, int pt) {
 }
 
 
+namespace {
+
+
+// One launch of the fused kernel over `count` queue entries starting at `queue`.
+int launch_fused(hdg_ctx* c, const PArgs& base, const int* queue, int64_t count, cudaStream_t s) {
+  PMix& pm = *c->pm;
+  PArgs a = base;
+  a.queue = queue;
+  a.E = count;
+  for (int k = 0; k < kPClasses; ++k) a.tab[k] = pm.tab[k];
+  HDG_CK(cudaMemsetAsync(pm.d_counter, 0, sizeof(int), s));
+  const int grid = c->num_sms > 0 ? c->num_sms : 152;
+  k_pclass_fused<<<grid, kThreads, pm.smem_bytes, s>>>(a, c->ph);
+  HDG_CK(cudaGetLastError());
+  return HDG_OK;
+}
+
+// Tile shapes per class: for every class present, every (GT, CB) in {16, 32, 64}^2 that fits the
+// shared memory is timed on up to two waves of that class's elements (CUDA events, one warm-up
+// launch each) and the fastest kept. The sample writes its elements' outputs, which the full
+// launch that follows writes again.
+int pclass_autotune(hdg_ctx* c, const PArgs& base, cudaStream_t s) {
+  PMix& pm = *c->pm;
+  const int grid = c->num_sms > 0 ? c->num_sms : 152;
+  int* d_sample = nullptr;
+  HDG_CK(cudaMalloc(&d_sample, sizeof(int) * 2 * grid));
+  cudaEvent_t ev0, ev1;
+  HDG_CK(cudaEventCreate(&ev0));
+  HDG_CK(cudaEventCreate(&ev1));
+  int rc = HDG_OK;
+  const int cand[3] = {16, 32, 64};
+  for (int k = 0; k < kPClasses && rc == HDG_OK; ++k) {
+    if (pm.class_count[k] == 0) continue;
+    std::vector<int> sample;
+    for (int e : pm.h_queue)
+      if (pm.h_cls[e] == k && (int)sample.size() < 2 * grid) sample.push_back(e);
+    if (cudaMemcpyAsync(d_sample, sample.data(), sizeof(int) * sample.size(), cudaMemcpyHostToDevice, s) != cudaSuccess) {
+      rc = cuda_fail(cudaGetLastError(), "pclass_autotune: sample upload");
+      break;
+    }
+    const PDims keep = pm.tab[k].d;
+    PDims best = keep;
+    float best_ms = -1.0f;
+    for (int gt : cand)
+      for (int cb : cand) {
+        const PDims d = pclass_dims(keep.pk, keep.pt, gt, cb);
+        if (sizeof(double) * (size_t)d.SMEM > pm.smem_limit) continue;
+        if (gt > cand[0] && keep.NG <= gt / 2) continue;  // the smaller tile already held every point
+        pm.tab[k].d = d;
+        const size_t smem_keep = pm.smem_bytes;
+        pm.smem_bytes = std::max(pm.smem_bytes, sizeof(double) * (size_t)d.SMEM);
+        float ms = 0.0f;
+        if ((rc = launch_fused(c, base, d_sample, (int64_t)sample.size(), s)) ||
+            (rc = cudaEventRecord(ev0, s) == cudaSuccess ? HDG_OK : HDG_ERR_CUDA) ||
+            (rc = launch_fused(c, base, d_sample, (int64_t)sample.size(), s)) ||
+            (rc = cudaEventRecord(ev1, s) == cudaSuccess ? HDG_OK : HDG_ERR_CUDA) ||
+            (rc = cudaEventSynchronize(ev1) == cudaSuccess ? HDG_OK : HDG_ERR_CUDA) ||
+            (rc = cudaEventElapsedTime(&ms, ev0, ev1) == cudaSuccess ? HDG_OK : HDG_ERR_CUDA)) {
+          pm.smem_bytes = smem_keep;
+          break;
+        }
+        pm.smem_bytes = smem_keep;
+        if (best_ms < 0.0f || ms < best_ms) {
+          best_ms = ms;
+          best = d;
+        }
+      }
+    pm.tab[k].d = best;
+  }
+  cudaEventDestroy(ev0);
+  cudaEventDestroy(ev1);
+  cudaFree(d_sample);
+  if (rc) return rc == HDG_ERR_CUDA ? cuda_fail(cudaGetLastError(), "pclass_autotune") : rc;
+  pm.smem_bytes = 0;
+  pm.slot_doubles = 0;
+  for (int k = 0; k < kPClasses; ++k)
+    if (pm.class_count[k] > 0) {
+      pm.smem_bytes = std::max(pm.smem_bytes, sizeof(double) * (size_t)pm.tab[k].d.SMEM);
+      pm.slot_doubles = std::max(pm.slot_doubles, pm.tab[k].d.SLOT);
+    }
+  pm.tuned = true;
+  return HDG_OK;
+}
+
+}  // namespace
+
 int assemble_condense_pclass(hdg_ctx* c, const double* V, const double* Vhat, const double* hist, double mass_coef,
                              double* S, double* g, double* recov, double* R, int32_t* status, cudaStream_t s) {
   PMix& pm = *c->pm;
@@ -747,9 +834,17 @@ int assemble_condense_pclass(hdg_ctx* c, const double* V, const double* Vhat, co
     HDG_CK(cudaMalloc(&c->d_scr, need));
     c->scr_bytes = need;
   }
-  if (!pm.attr_set) {  // per context, hence per device
-    HDG_CK(cudaFuncSetAttribute(k_pclass_fused, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)pm.smem_bytes));
+  if (!pm.attr_set) {  // per context, hence per device: all the dynamic shared memory a CTA may have
+    int optin = 0;
+    cudaFuncAttributes fa{};
+    HDG_CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
+    HDG_CK(cudaFuncGetAttributes(&fa, k_pclass_fused));
+    pm.smem_limit = (size_t)optin - fa.sharedSizeBytes;
+    if (pm.smem_bytes > pm.smem_limit) {
+      set_error("assemble_condense: the element classes need more shared memory than the device has");
+      return HDG_ERR_UNSUPPORTED;
+    }
+    HDG_CK(cudaFuncSetAttribute(k_pclass_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pm.smem_limit));
     pm.attr_set = true;
   }
   PArgs a{};
@@ -777,14 +872,11 @@ int assemble_condense_pclass(hdg_ctx* c, const double* V, const double* Vhat, co
   a.recov = recov;
   a.R = R;
   a.status = status;
-  for (int k = 0; k < kPClasses; ++k) a.tab[k] = pm.tab[k];
-  HDG_CK(cudaMemsetAsync(pm.d_counter, 0, sizeof(int), s));
-  {
-    LaunchScope ls(c, HDG_KERNEL_PCLASS, s);
-    k_pclass_fused<<<grid, kThreads, pm.smem_bytes, s>>>(a, c->ph);
+  if (!pm.tuned && c->E >= 4 * (int64_t)grid) {
+    if (int rc = pclass_autotune(c, a, s)) return rc;
   }
-  HDG_CK(cudaGetLastError());
-  return HDG_OK;
+  LaunchScope ls(c, HDG_KERNEL_PCLASS, s);
+  return launch_fused(c, a, pm.d_queue, c->E, s);
 }
 
 namespace {
@@ -883,6 +975,8 @@ int pclass_setup(hdg_ctx* c) {
     const int kx = m.pe[x] * 8 + m.ptr[x], ky = m.pe[y] * 8 + m.ptr[y];
     return kx > ky;
   });
+  pm->h_queue = queue;
+  pm->h_cls = cls;
   int rc = HDG_OK;
   if ((rc = up(&pm->d_tab, tab)) || (rc = up(&pm->d_itab, itab)) || (rc = up(&pm->d_voff, m.voff)) ||
       (rc = up(&pm->d_toff, m.toff)) || (rc = up(&pm->d_soff, m.soff)) || (rc = up(&pm->d_roff, m.roff)) ||

@@ -16,7 +16,7 @@ constexpr int kPClasses = 10;  // (pk, pt) with 1 <= pk <= pt <= 4 (3D Navier-St
 // sizes of one (pk, pt) class: nodes, points, unknowns, tiles, shared memory and per-CTA scratch
 // (doubles) of the fused kernel
 struct PDims {
-  int pk, pt, NP, NFK, NFN, NG, NGF, NV, NT, NZ, GT, RBMAX, ASM, CND, KEEP, SMEM, lu_smem;
+  int pk, pt, NP, NFK, NFN, NG, NGF, NV, NT, NZ, GT, CB, RBMAX, ASM, CND, KEEP, SMEM, lu_smem;
   int64_t SLOT;
 };
 
@@ -50,6 +50,10 @@ struct PMix {
   PClassDev tab[kPClasses] = {};
   int64_t class_count[kPClasses] = {};
   size_t smem_bytes = 0;      // dynamic shared memory of the launch: the largest class present
+  size_t smem_limit = 0;      // dynamic shared memory a CTA of the fused kernel may use on the device
+  bool tuned = false;         // tile shapes (GT, CB) chosen per class by timing (first call)
+  std::vector<int> h_queue;   // host copy of the queue
+  std::vector<int8_t> h_cls;  // host copy of the classes
   int64_t slot_doubles = 0;   // per-CTA scratch: the largest class present
   bool attr_set = false;
 };

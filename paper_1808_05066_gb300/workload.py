@@ -36,7 +36,9 @@ class DeviceWorkload:
         self.name, self.spec = name, spec
         self.dev = torch.device("cuda", device)
         d = spec["dim"]
-        self.mesh = hdg.Mesh(d, spec["n"], spec["lo"], spec["hi"], spec["p"])
+        E = (2 if d == 2 else 6) * spec["n"] ** d
+        self.p_elem = wl.draw_degrees(name, E)
+        self.mesh = hdg.Mesh(d, spec["n"], spec["lo"], spec["hi"], spec["p"], p_per_elem=self.p_elem)
         self.ctx = hdg.Context(self.mesh, 1.4, spec["mach"], spec["reynolds"], spec["prandtl"], device)
         self.info = self.mesh.info
         xnode, xfnode, _ = self.mesh.coords()
@@ -60,6 +62,13 @@ class DeviceWorkload:
             self.alloc_outputs()
         torch.cuda.synchronize(self.dev)
 
+    def close(self):
+        """Release the device buffers and the context (its internal workspaces)."""
+        for k in ("S", "g", "recov", "R", "status", "V", "Vhat", "hist"):
+            if hasattr(self, k):
+                delattr(self, k)
+        self.ctx.close()
+
     def _entropy(self, prim):
         t = torch.from_numpy(np.ascontiguousarray(prim)).to(self.dev)
         out = torch.empty_like(t)
@@ -70,6 +79,13 @@ class DeviceWorkload:
         i = self.info
         E, nv, nt = i["n_elem"], i["nv"], i["nt"]
         f64 = dict(dtype=torch.float64, device=self.dev)
+        if i["mixed"]:   # packed per-element layout
+            self.S = torch.empty(i["len_S"], **f64)
+            self.g = torch.empty(i["len_g"], **f64)
+            self.recov = torch.empty(i["len_recov"], **f64)
+            self.R = torch.empty(i["len_R"], **f64)
+            self.status = torch.zeros(E, dtype=torch.int32, device=self.dev)
+            return
         self.S = torch.empty((E, nt, nt), **f64)
         self.g = torch.empty((E, nt), **f64)
         self.recov = torch.empty((E, nv * nt + nv), **f64)

@@ -136,6 +136,11 @@ WORKLOADS = {
     "ns3d_p3_tgv": dict(dim=3, n=24, lo=0.0, hi=2.0 * math.pi, p=3, viscous=True,
                         mach=0.1, reynolds=1600.0, prandtl=0.71, dt=0.01, bdf=2,
                         seed=3, trace_noise=1e-3),
+    # 3D NS tets of mixed degree, 32^3 periodic cube [0,2pi]^3 (196,608 tets), degree per element
+    # drawn from {1,2,3,4} with weights 0.1/0.3/0.4/0.2 (seed 4), TGV M0=0.1 Re=1600.
+    "ns3d_mixed_tgv": dict(dim=3, n=32, lo=0.0, hi=2.0 * math.pi, p=4, viscous=True,
+                           mach=0.1, reynolds=1600.0, prandtl=0.71, dt=0.01, bdf=2,
+                           seed=3, trace_noise=1e-3, p_draw=((1, 2, 3, 4), (0.1, 0.3, 0.4, 0.2), 4)),
     # 2D NS p=3, 128x128 periodic, 32 vortices, M=0.5, Re=5000 (learned warm start).
     "ns2d_p3_vortices": dict(dim=2, n=128, lo=0.0, hi=160.0, p=3, viscous=True,
                              mach=0.5, reynolds=5000.0, prandtl=0.71, dt=0.01, bdf=2,
@@ -159,3 +164,12 @@ def primitive_state(name: str, x: np.ndarray, **over):
         c = 0.5 * (w["lo"] + w["hi"])
         vs = [Vortex(c, c, 5.0)]
     return vortex_field(x, vs, w["mach"], period=period)
+
+
+def draw_degrees(name: str, n_elem: int):
+    """Per-element degrees of a mixed-degree workload (seeded draw), or None."""
+    w = WORKLOADS[name]
+    if "p_draw" not in w:
+        return None
+    degs, weights, seed = w["p_draw"]
+    return np.random.default_rng(seed).choice(degs, size=n_elem, p=weights).astype(np.int8)
