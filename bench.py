@@ -199,10 +199,9 @@ def parse():
 # elements. Valid only while the kernel sources hash to the digest they were captured on.
 NCU_TRAFFIC = {
     "source": "profiles/ncu_mixed_kernels_ns3d_p3_n8.md",
-    "sources_sha256": "1368eb176dfc421763cce27bfd4f2ea9915e8b0e65dc1dae787aa120b6d22e39",
-    "bytes_per_element": {"mixed_assemble": 600_309, "mixed_face": 1_257_285, "mixed_condense": 2_606_220},
+    "sources_sha256": "4f9eda78a7eadb3a5606341f4b5fa50b2b5a5f71e103193bc010daf658212a7a",
+    "bytes_per_element": {"mixed_assemble": 600_747, "mixed_face": 1_255_572, "mixed_condense": 2_617_894},
 }
-
 
 # the sources that define the captured kernels and their launch shapes (device code and the
 # dispatch of the mixed form); host-side entry points do not change the kernels

@@ -255,6 +255,10 @@ int hdg_assemble_condense_graph(hdg_ctx_t ctx, const double* V, const double* Vh
 /* Number of graph launches made by hdg_assemble_condense_graph on this context so far (0 if
  * every call ran the ordinary path, e.g. because the capture failed). */
 int hdg_ctx_graph_replays(hdg_ctx_t ctx, int64_t* replays);
+/* GMRES restart cycles run by this context's trace solves so far, and how many of them were one
+ * replay of the CUDA graph of a cycle's Arnoldi steps (the rest ran the same kernels launch by
+ * launch, when no graph could be captured). An execution mechanism of this library. */
+int hdg_ctx_trace_cycles(hdg_ctx_t ctx, int64_t* cycles, int64_t* replays);
 
 /* hdg_assemble_condense with S and g delivered to HOST memory (Sec. 3.2, the same local
  * elimination as hdg_assemble_condense). The elements are processed in chunks; each chunk's S
@@ -301,7 +305,8 @@ int hdg_entropy_production(hdg_ctx_t ctx, const double* V, const double* Vhat, d
 
 /* Global trace system sum_e P_e^T S_e P_e dVhat = -sum_e P_e^T g_e (Sec. 3.2: only vhat
  * is globally coupled). method: HDG_SOLVER_GMRES (restarted GMRES(30), face-block Jacobi
- * preconditioner), HDG_SOLVER_DENSE (assembled dense LU with partial pivoting, for
+ * preconditioner; each restart cycle's Arnoldi steps run on the device without a host round
+ * trip, replayed as a CUDA graph, and the host reads the cycle's outcome once per cycle), HDG_SOLVER_DENSE (assembled dense LU with partial pivoting, for
  * n_trace <= 16384) or HDG_SOLVER_AUTO (dense up to 4096 unknowns, else GMRES).
  * dVhat [F][Nf][m] device output. Writes *iters and
  * *final_res (relative residual) on the host, so it synchronises the stream.

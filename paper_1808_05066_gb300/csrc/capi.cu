@@ -472,6 +472,10 @@ void hdg_ctx_destroy(hdg_ctx_t c) {
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (c->h_red) cudaFreeHost(c->h_red);
+  if (c->d_gm) cudaFree(c->d_gm);
+  if (c->h_gm) cudaFreeHost(c->h_gm);
+  if (c->gm_graph) cudaGraphExecDestroy(c->gm_graph);
+  if (c->gm_stream) cudaStreamDestroy(c->gm_stream);
   if (c->lu_graph_exec) cudaGraphExecDestroy(c->lu_graph_exec);
   if (c->ac_graph) cudaGraphExecDestroy(c->ac_graph);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
@@ -738,6 +742,13 @@ int hdg_ctx_set_trace_solver(hdg_ctx_t ctx, int method, double rtol, int max_it)
   ctx->newton_solver = method;
   ctx->newton_rtol = rtol;
   ctx->newton_max_it = max_it;
+  return HDG_OK;
+}
+
+int hdg_ctx_trace_cycles(hdg_ctx_t ctx, int64_t* cycles, int64_t* replays) {
+  HDG_REQUIRE(ctx && cycles && replays, "hdg_ctx_trace_cycles: null argument");
+  *cycles = ctx->gm_cycles;
+  *replays = ctx->gm_replays;
   return HDG_OK;
 }
 

@@ -120,6 +120,15 @@ struct hdg_ctx {
   hdg::PMix* pm = nullptr;       // mixed-degree mesh: class tables, packed layout, work queue
   int* d_mv_err = nullptr;       // set by the staged trace matvec when a copy wait gave up
   void* d_Sdf = nullptr;         // double-float copy of S for the GMRES products [E][NT][NT]
+  // device-resident GMRES: the restart cycle's state (device and pinned host copies) and the CUDA
+  // graph of one cycle's Arnoldi steps, with the pointers it was captured for
+  void* d_gm = nullptr;
+  void* h_gm = nullptr;
+  cudaStream_t gm_stream = nullptr;
+  cudaGraphExec_t gm_graph = nullptr;
+  const void* gm_key[6] = {};
+  bool gm_graph_failed = false;
+  int64_t gm_cycles = 0, gm_replays = 0;  // cycles run, of them by graph replay
   size_t sdf_bytes = 0;
   bool sdf_unavailable = false;  // no device memory for it: FP64 products throughout
   // measurement: launch counts per kernel class and (when enabled) event pairs
@@ -190,7 +199,8 @@ int entropy_terms(hdg_ctx* ctx, const double* V, const double* Vhat, double* acc
 int launch_prim_to_entropy(hdg_ctx* ctx, const double* prim, int64_t n, double* v, cudaStream_t s);
 int launch_history(hdg_ctx* ctx, const double* V0, const double* V1, double c0, double c1, double* hist,
                    cudaStream_t s);
-int launch_trace_matvec(hdg_ctx* ctx, const double* S, const double* x, double* y, double* work, cudaStream_t s);
+int launch_trace_matvec(hdg_ctx* ctx, const double* S, const double* x, double* y, double* work, cudaStream_t s,
+                        const int* skip = nullptr);
 int launch_trace_rhs(hdg_ctx* ctx, const double* g, double* rhs, cudaStream_t s);
 int launch_recover(hdg_ctx* ctx, const double* recov, const double* dVhat, double* dV, cudaStream_t s);
 int residual_norm(hdg_ctx* ctx, const double* R, double* norm, cudaStream_t s);

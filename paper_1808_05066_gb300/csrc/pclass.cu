@@ -18,7 +18,7 @@
 //   4. the blocks in the element's own trace space: B_q = B' P, C_q = P^T C', D_q = P^T D' P,
 //      R_t,q = P^T R_t, P = block-diag(I_f) (the test functions of degree q_f are combinations
 //      of the degree-pt ones with the same coefficients);
-//   5. LU of A' (in shared memory when it fits, else in the CTA's scratch, which stays in L2),
+//   5. LU of A' (in shared memory when it fits, else in the CTA's global-memory scratch),
 //      X = A'^{-1} [B_q | R_v], S = D_q - C_q X, g = R_t,q - C_q y.
 // Outputs are packed per element at the offsets of the mesh layout (hdg_mesh_copy_layout):
 // S [nt_e][nt_e], g [nt_e], recov [nv_e nt_e + nv_e] (X then y), R [nv_e + nt_e], with

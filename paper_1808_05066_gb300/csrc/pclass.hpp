@@ -72,14 +72,17 @@ int pclass_index(int pk, int pt);
 int pclass_setup(hdg_ctx* c);
 void pclass_free(PMix* pm);
 PMixDev pmix_dev(const hdg_ctx* c);
-// trace-space operations of pclass_trace.cu (the packed layout's counterparts of trace.cu)
+// trace-space operations of pclass_trace.cu (the packed layout's counterparts of trace.cu); skip:
+// a device flag that, when set, makes the launch return at once (a finished Krylov cycle)
 int pm_history(hdg_ctx* c, const double* V0, const double* V1, double c0, double c1, double* hist, cudaStream_t s);
-int pm_gather(hdg_ctx* c, const double* ge, double scale, double* out, cudaStream_t s);
-int pm_elem_matvec(hdg_ctx* c, const double* S, const double* x, double* w, cudaStream_t s);
+int pm_gather(hdg_ctx* c, const double* ge, double scale, double* out, cudaStream_t s, const int* skip = nullptr);
+int pm_elem_matvec(hdg_ctx* c, const double* S, const double* x, double* w, cudaStream_t s,
+                   const int* skip = nullptr);
 int pm_recover(hdg_ctx* c, const double* recov, const double* dvh, double* dV, cudaStream_t s);
 int pm_sumsq(hdg_ctx* c, const double* R, double* red, cudaStream_t s);
 int pm_face_factor(hdg_ctx* c, const double* S, double* pc, cudaStream_t s);
-int pm_face_apply(hdg_ctx* c, const double* pc, const double* r, double* z, cudaStream_t s);
+int pm_face_apply(hdg_ctx* c, const double* pc, const double* r, double* z, cudaStream_t s,
+                  const int* skip = nullptr);
 int pm_dense_scatter(hdg_ctx* c, const double* S, int64_t n, double* K, cudaStream_t s);
 int assemble_condense_pclass(hdg_ctx* c, const double* V, const double* Vhat, const double* hist, double mass_coef,
                              double* S, double* g, double* recov, double* R, int32_t* status, cudaStream_t s);

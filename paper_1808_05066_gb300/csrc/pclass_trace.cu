@@ -83,7 +83,8 @@ __global__ void k_pm_history(PMixDev p, const double* geo, const double* V0, con
 }
 
 // w_e = S_e x_e, x_e gathered through the element's trace map (one warp per row)
-__global__ void k_pm_elem_matvec(PMixDev p, const double* S, const double* x, double* w) {
+__global__ void k_pm_elem_matvec(PMixDev p, const double* S, const double* x, double* w, const int* skip) {
+  if (skip && *skip) return;  // a finished Krylov cycle: nothing to do
   extern __shared__ double xs[];
   const int64_t e = blockIdx.x;
   const int nt = (int)(p.toff[e + 1] - p.toff[e]);
@@ -108,7 +109,8 @@ __global__ void k_pm_elem_matvec(PMixDev p, const double* S, const double* x, do
 }
 
 // out[t][i] = scale * sum over the sides of the face of ge[toff[e_s] + loc_s + i]
-__global__ void k_pm_gather(PMixDev p, int64_t ntn, const double* ge, double scale, double* out) {
+__global__ void k_pm_gather(PMixDev p, int64_t ntn, const double* ge, double scale, double* out, const int* skip) {
+  if (skip && *skip) return;  // a finished Krylov cycle: nothing to do
   const int64_t n = ntn * M5;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t node = t / M5;
@@ -282,7 +284,8 @@ __global__ void k_pm_face_factor(PMixDev p, const double* S, double* pc) {
 }
 
 // z_F = K_FF^{-1} r_F, one warp per face (B <= 80: lanes take rows i, i + 32, i + 64)
-__global__ void k_pm_face_apply(PMixDev p, int64_t F, const double* pc, const double* r, double* z) {
+__global__ void k_pm_face_apply(PMixDev p, int64_t F, const double* pc, const double* r, double* z, const int* skip) {
+  if (skip && *skip) return;  // a finished Krylov cycle: nothing to do
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int64_t Fi = (int64_t)blockIdx.x * nw + wid;
   if (Fi >= F) return;
@@ -352,14 +355,14 @@ int pm_history(hdg_ctx* c, const double* V0, const double* V1, double c0, double
   return HDG_OK;
 }
 
-int pm_gather(hdg_ctx* c, const double* ge, double scale, double* out, cudaStream_t s) {
-  k_pm_gather<<<nblk(c->ntrace), kThreads, 0, s>>>(pmix_dev(c), c->n_tnodes, ge, scale, out);
+int pm_gather(hdg_ctx* c, const double* ge, double scale, double* out, cudaStream_t s, const int* skip) {
+  k_pm_gather<<<nblk(c->ntrace), kThreads, 0, s>>>(pmix_dev(c), c->n_tnodes, ge, scale, out, skip);
   HDG_CK(cudaGetLastError());
   return HDG_OK;
 }
 
-int pm_elem_matvec(hdg_ctx* c, const double* S, const double* x, double* w, cudaStream_t s) {
-  k_pm_elem_matvec<<<(unsigned)c->E, 256, sizeof(double) * c->pm->nt_max, s>>>(pmix_dev(c), S, x, w);
+int pm_elem_matvec(hdg_ctx* c, const double* S, const double* x, double* w, cudaStream_t s, const int* skip) {
+  k_pm_elem_matvec<<<(unsigned)c->E, 256, sizeof(double) * c->pm->nt_max, s>>>(pmix_dev(c), S, x, w, skip);
   HDG_CK(cudaGetLastError());
   return HDG_OK;
 }
@@ -389,9 +392,9 @@ int pm_face_factor(hdg_ctx* c, const double* S, double* pc, cudaStream_t s) {
   return HDG_OK;
 }
 
-int pm_face_apply(hdg_ctx* c, const double* pc, const double* r, double* z, cudaStream_t s) {
+int pm_face_apply(hdg_ctx* c, const double* pc, const double* r, double* z, cudaStream_t s, const int* skip) {
   const int wpb = 8;
-  k_pm_face_apply<<<(unsigned)((c->F + wpb - 1) / wpb), 32 * wpb, 0, s>>>(pmix_dev(c), c->F, pc, r, z);
+  k_pm_face_apply<<<(unsigned)((c->F + wpb - 1) / wpb), 32 * wpb, 0, s>>>(pmix_dev(c), c->F, pc, r, z, skip);
   HDG_CK(cudaGetLastError());
   return HDG_OK;
 }

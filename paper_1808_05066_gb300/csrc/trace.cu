@@ -8,6 +8,7 @@
 //     or an assembled dense LU with partial pivoting for small systems.
 // All vectors in the trace space are [F][Nf][m] (canonical face-node order).
 #include <algorithm>
+#include <cstring>
 #include <cmath>
 #include <vector>
 
@@ -105,7 +106,8 @@ __global__ void k_history(DevTables T, const double* geo, int GEO, int NP, int N
 // ---------------------------------------------------------------- trace operator
 // rhs[F][c][i] = -sum_sides g_e[loc * M + i]
 __global__ void k_trace_gather(const int* fs_elem, const int* fs_loc, int64_t F, int NFN, int M, int NT,
-                               const double* ge, double scale, double* out) {
+                               const double* ge, double scale, double* out, const int* skip) {
+  if (skip && *skip) return;  // a finished Krylov cycle: nothing to do
   const int64_t n = F * NFN * M;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
     int64_t Fi = t / (NFN * M);
@@ -136,7 +138,8 @@ constexpr int kMvChunkBytes = 12800;
 constexpr int kMvWaitPolls = 4 * 1000 * 1000;  // ~1 s at 256 ns per poll
 __global__ void __launch_bounds__(256) k_elem_matvec_df(const df2* __restrict__ Sdf, const double* x,
                                                         const int* tgidx, int64_t E, int NT, int M, int CR,
-                                                        int nchunk, double* w, int* err) {
+                                                        int nchunk, double* w, int* err, const int* skip) {
+  if (skip && *skip) return;  // a finished Krylov cycle: nothing to do
   extern __shared__ __align__(128) df2 smf[];
   __shared__ uint64_t full[kMvStages];
   __shared__ int s_fail;
@@ -206,7 +209,8 @@ __global__ void __launch_bounds__(256) k_elem_matvec_df(const df2* __restrict__ 
 // EDG (continuous trace): out[t][i] = scale * sum over the local occurrences o of node t of
 // ge[o * M + i], o = e NF NFN + f NFN + c (CSR ptr / occ)
 __global__ void k_node_gather(const int* ptr, const int* occ, int64_t nnode, int M, const double* ge, double scale,
-                              double* out) {
+                              double* out, const int* skip) {
+  if (skip && *skip) return;  // a finished Krylov cycle: nothing to do
   const int64_t n = nnode * M;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t node = t / M;
@@ -220,7 +224,8 @@ __global__ void k_node_gather(const int* ptr, const int* occ, int64_t nnode, int
 // w_e = S_e x_e in FP64, one warp per row, x_e gathered into shared memory. On GB300 this is
 // bound by the FP64 pipe (one FMA per 8-byte entry), not by HBM: the GMRES iterations use the
 // double-float copy of S (k_elem_matvec_df) and keep this one for the residuals.
-__global__ void k_elem_matvec(const double* S, const double* x, const int* tgidx, int NT, int M, double* w) {
+__global__ void k_elem_matvec(const double* S, const double* x, const int* tgidx, int NT, int M, double* w, const int* skip) {
+  if (skip && *skip) return;  // a finished Krylov cycle: nothing to do
   extern __shared__ double xs[];
   const int64_t e = blockIdx.x;
   const int nfc = NT / M;
@@ -334,7 +339,8 @@ __global__ void k_scale_copy(int64_t n, double a, const double* x, double* y) {
     y[t] = a * x[t];
 }
 // out[j] = basis_j . w for j < nb (blockIdx.y = j)
-__global__ void k_multidot(int64_t n, const double* basis, int64_t ld, const double* w, double* out) {
+__global__ void k_multidot(int64_t n, const double* basis, int64_t ld, const double* w, double* out, const int* skip) {
+  if (skip && *skip) return;  // a finished Krylov cycle: nothing to do
   const int j = blockIdx.y;
   const double* b = basis + j * ld;
   double s = 0.0;
@@ -344,18 +350,90 @@ __global__ void k_multidot(int64_t n, const double* basis, int64_t ld, const dou
   if (threadIdx.x == 0) atomicAdd(out + j, s);
 }
 // w -= sum_j h[j] basis_j
-__global__ void k_multiaxpy(int64_t n, const double* basis, int64_t ld, const double* h, int nb, double* w) {
+__global__ void k_multiaxpy(int64_t n, const double* basis, int64_t ld, const double* h, int nb, double* w, const int* skip) {
+  if (skip && *skip) return;  // a finished Krylov cycle: nothing to do
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
     double s = w[t];
     for (int j = 0; j < nb; ++j) s -= h[j] * basis[j * ld + t];
     w[t] = s;
   }
 }
-// x += sum_j c[j] basis_j
-__global__ void k_multiaxpy_add(int64_t n, const double* basis, int64_t ld, const double* c, int nb, double* x) {
+
+// ---------------------------------------------------------------- device-resident Arnoldi
+// The state of one GMRES(m) restart cycle in device memory: the Hessenberg matrix in its
+// rotated (triangular) form, the Givens rotations, the rotated right-hand side gv, the current
+// column h and its second Gram-Schmidt pass h2, |w|^2, and the cycle's progress. The kernels of
+// the m Arnoldi steps of a cycle are enqueued (or replayed as one CUDA graph) without a host
+// round trip; once a step reaches the tolerance or the iteration limit it sets `done`, and the
+// kernels of the remaining steps return at once.
+constexpr int kGmM = 30;
+struct GmState {
+  double H[(kGmM + 1) * kGmM];  // H[i * m + j]
+  double cs[kGmM], sn[kGmM], gv[kGmM + 1];
+  double h[kGmM + 2], h2[kGmM + 2], y[kGmM];
+  double wn2, hnext, bnorm, rtol, rel;
+  int done, jdone, total, max_it;
+};
+
+__global__ void k_gm_zero(double* a, int n, const int* skip) {
+  if (*skip) return;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) a[i] = 0.0;
+}
+
+// step j: h += h2 (the two Gram-Schmidt passes), h[j+1] = |w|, the previous rotations on h, the
+// new rotation, the rotated right-hand side, column j of H, the residual estimate and the stop test
+__global__ void k_gm_givens(GmState* st, int j, int m) {
+  if (threadIdx.x != 0 || blockIdx.x != 0 || st->done) return;
+  double* h = st->h;
+  for (int i = 0; i <= j; ++i) h[i] += st->h2[i];
+  const double hn = ::sqrt(st->wn2);
+  h[j + 1] = hn;
+  st->hnext = hn;
+  for (int i = 0; i < j; ++i) {
+    const double t = st->cs[i] * h[i] + st->sn[i] * h[i + 1];
+    h[i + 1] = -st->sn[i] * h[i] + st->cs[i] * h[i + 1];
+    h[i] = t;
+  }
+  const double den = ::hypot(h[j], h[j + 1]);
+  st->cs[j] = den > 0.0 ? h[j] / den : 1.0;
+  st->sn[j] = den > 0.0 ? h[j + 1] / den : 0.0;
+  h[j] = den;
+  h[j + 1] = 0.0;
+  st->gv[j + 1] = -st->sn[j] * st->gv[j];
+  st->gv[j] = st->cs[j] * st->gv[j];
+  for (int i = 0; i <= j; ++i) st->H[i * m + j] = h[i];
+  st->rel = ::fabs(st->gv[j + 1]) / st->bnorm;
+  st->total += 1;
+  st->jdone = j + 1;
+  if (st->rel <= st->rtol || st->total >= st->max_it || j + 1 == m) st->done = 1;
+}
+
+// the next basis vector w / h[j+1] (not needed once the cycle is done)
+__global__ void k_gm_scale(const GmState* st, int64_t n, const double* w, double* vnext) {
+  if (st->done || !(st->hnext > 0.0)) return;
+  const double inv = 1.0 / st->hnext;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+    vnext[t] = inv * w[t];
+}
+
+// y = H^{-1} gv on the jdone completed steps (back substitution)
+__global__ void k_gm_solve(GmState* st, int m) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int jd = st->jdone;
+  for (int i = jd - 1; i >= 0; --i) {
+    double t = st->gv[i];
+    for (int k = i + 1; k < jd; ++k) t -= st->H[i * m + k] * st->y[k];
+    st->y[i] = t / st->H[i * m + i];
+  }
+}
+
+// x += sum_{j < *nb} c[j] basis_j (the count read on the device)
+__global__ void k_multiaxpy_add_dev(int64_t n, const double* basis, int64_t ld, const double* c, const int* nb,
+                                    double* x) {
+  const int k = *nb;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
     double s = x[t];
-    for (int j = 0; j < nb; ++j) s += c[j] * basis[j * ld + t];
+    for (int j = 0; j < k; ++j) s += c[j] * basis[j * ld + t];
     x[t] = s;
   }
 }
@@ -461,7 +539,8 @@ __global__ void k_face_block_factor(const double* S, const int* fs_elem, const i
 
 // z_F = K_FF^{-1} r_F from the stored inverse (fac[F][j][i] = K_FF^{-1}[i][j]), one warp per face:
 // lane i accumulates row i over j, every load a coalesced run of one stored row
-__global__ void k_face_block_apply(const double* fac, int64_t F, int B, const double* r, double* z) {
+__global__ void k_face_block_apply(const double* fac, int64_t F, int B, const double* r, double* z, const int* skip) {
+  if (skip && *skip) return;  // a finished Krylov cycle: nothing to do
   extern __shared__ double xs[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int64_t Fi = (int64_t)blockIdx.x * nw + wid;
@@ -529,7 +608,8 @@ __global__ void k_node_block_factor(const double* S, const int* ptr, const int* 
 }
 
 // z_t = K_tt^{-1} r_t for every node (z and r distinct)
-__global__ void k_node_block_apply(const double* binv, int64_t nnode, int M, const double* r, double* z) {
+__global__ void k_node_block_apply(const double* binv, int64_t nnode, int M, const double* r, double* z, const int* skip) {
+  if (skip && *skip) return;  // a finished Krylov cycle: nothing to do
   const int64_t n = nnode * M;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t node = t / M;
@@ -660,42 +740,50 @@ int launch_trace_rhs(hdg_ctx* ctx, const double* g, double* rhs, cudaStream_t s)
   if (ctx->pm) return pm_gather(ctx, g, -1.0, rhs, s);
   if (ctx->scheme)
     k_node_gather<<<nblocks(ctx->ntrace), kThreads, 0, s>>>(ctx->d_tr_ptr, ctx->d_tr_occ, ctx->n_tnodes, ctx->M, g,
-                                                           -1.0, rhs);
+                                                           -1.0, rhs, nullptr);
   else
     k_trace_gather<<<nblocks(ctx->ntrace), kThreads, 0, s>>>(ctx->d_fs_elem, ctx->d_fs_loc, ctx->F, ctx->NFN, ctx->M,
-                                                            ctx->NT, g, -1.0, rhs);
+                                                            ctx->NT, g, -1.0, rhs, nullptr);
   HDG_CK(cudaGetLastError());
   return HDG_OK;
 }
 
-static int launch_gather(hdg_ctx* ctx, const double* work, double* y, cudaStream_t s) {
-  if (ctx->pm) return pm_gather(ctx, work, 1.0, y, s);
+static int launch_gather(hdg_ctx* ctx, const double* work, double* y, cudaStream_t s, const int* skip = nullptr) {
+  if (ctx->pm) return pm_gather(ctx, work, 1.0, y, s, skip);
   if (ctx->scheme)
     k_node_gather<<<nblocks(ctx->ntrace), kThreads, 0, s>>>(ctx->d_tr_ptr, ctx->d_tr_occ, ctx->n_tnodes, ctx->M, work,
-                                                           1.0, y);
+                                                           1.0, y, skip);
   else
     k_trace_gather<<<nblocks(ctx->ntrace), kThreads, 0, s>>>(ctx->d_fs_elem, ctx->d_fs_loc, ctx->F, ctx->NFN, ctx->M,
-                                                            ctx->NT, work, 1.0, y);
+                                                            ctx->NT, work, 1.0, y, skip);
   HDG_CK(cudaGetLastError());
   return HDG_OK;
 }
 
-int launch_trace_matvec(hdg_ctx* ctx, const double* S, const double* x, double* y, double* work, cudaStream_t s) {
+int launch_trace_matvec(hdg_ctx* ctx, const double* S, const double* x, double* y, double* work, cudaStream_t s,
+                        const int* skip) {
   if (ctx->pm) {
-    if (int rc = pm_elem_matvec(ctx, S, x, work, s)) return rc;
-    return pm_gather(ctx, work, 1.0, y, s);
+    if (int rc = pm_elem_matvec(ctx, S, x, work, s, skip)) return rc;
+    return pm_gather(ctx, work, 1.0, y, s, skip);
   }
-  k_elem_matvec<<<(unsigned)ctx->E, 256, sizeof(double) * ctx->NT, s>>>(S, x, ctx->d_tgidx, ctx->NT, ctx->M, work);
-  return launch_gather(ctx, work, y, s);
+  k_elem_matvec<<<(unsigned)ctx->E, 256, sizeof(double) * ctx->NT, s>>>(S, x, ctx->d_tgidx, ctx->NT, ctx->M, work,
+                                                                        skip);
+  return launch_gather(ctx, work, y, s, skip);
 }
 
 // y = K x from the double-float copy of S (see k_elem_matvec_df)
-static int launch_trace_matvec_df(hdg_ctx* ctx, const df2* Sdf, const double* x, double* y, double* work,
-                                  cudaStream_t s) {
+// shared memory of k_elem_matvec_df; its attribute, the SM count and the error flag are set up
+// on first use (before any stream capture: none of these steps may be captured)
+static size_t matvec_df_smem(const hdg_ctx* ctx, int* CR, int* nchunk) {
   const int NT = ctx->NT;
-  const int CR = std::max(1, std::min(NT, kMvChunkBytes / (int)(sizeof(df2) * NT)));
-  const int nchunk = (NT + CR - 1) / CR;
-  const size_t smem = sizeof(df2) * ((size_t)kMvStages * CR * NT + NT);
+  *CR = std::max(1, std::min(NT, kMvChunkBytes / (int)(sizeof(df2) * NT)));
+  *nchunk = (NT + *CR - 1) / *CR;
+  return sizeof(df2) * ((size_t)kMvStages * *CR * NT + NT);
+}
+
+static int prepare_matvec_df(hdg_ctx* ctx) {
+  int CR, nchunk;
+  const size_t smem = matvec_df_smem(ctx, &CR, &nchunk);
   if (!ctx->attr_matvec) {  // per context, hence per device
     HDG_CK(cudaFuncSetAttribute(k_elem_matvec_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     if (!ctx->num_sms) HDG_CK(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device));
@@ -705,10 +793,19 @@ static int launch_trace_matvec_df(hdg_ctx* ctx, const df2* Sdf, const double* x,
     }
     ctx->attr_matvec = true;
   }
+  return HDG_OK;
+}
+
+static int launch_trace_matvec_df(hdg_ctx* ctx, const df2* Sdf, const double* x, double* y, double* work,
+                                  cudaStream_t s, const int* skip = nullptr) {
+  if (int rc = prepare_matvec_df(ctx)) return rc;
+  const int NT = ctx->NT;
+  int CR, nchunk;
+  const size_t smem = matvec_df_smem(ctx, &CR, &nchunk);
   const int64_t grid = std::min<int64_t>(ctx->E, (int64_t)kMvCtasPerSm * ctx->num_sms);
   k_elem_matvec_df<<<(unsigned)grid, 256, smem, s>>>(Sdf, x, ctx->d_tgidx, ctx->E, NT, ctx->M, CR, nchunk, work,
-                                                      ctx->d_mv_err);
-  return launch_gather(ctx, work, y, s);
+                                                      ctx->d_mv_err, skip);
+  return launch_gather(ctx, work, y, s, skip);
 }
 
 int launch_recover(hdg_ctx* ctx, const double* recov, const double* dVhat, double* dV, cudaStream_t s) {
@@ -840,7 +937,7 @@ static int dense_solve(hdg_ctx* ctx, const double* S, const double* g, double* d
 // ---------------------------------------------------------------- GMRES
 static int gmres_solve(hdg_ctx* ctx, const double* S, const double* g, double* x, double rtol, int max_it,
                        int* iters, double* final_res, cudaStream_t s) {
-  const int m = 30;
+  const int m = kGmM;
   const int64_t n = ctx->ntrace;
   const int B = ctx->NFN * ctx->M;
   // workspace: basis V (m+1) n, Z (precond of current basis vector) n, w n, b n, elem work E*NT
@@ -900,30 +997,101 @@ static int gmres_solve(hdg_ctx* ctx, const double* S, const double* g, double* x
     k_split_df<<<nblocks(ns), kThreads, 0, s>>>(S, ns, static_cast<df2*>(ctx->d_Sdf));
     Sdf = static_cast<const df2*>(ctx->d_Sdf);
   }
-  auto arnoldi_matvec = [&](const double* xin, double* yout) {
-    return Sdf ? launch_trace_matvec_df(ctx, Sdf, xin, yout, ew, s) : launch_trace_matvec(ctx, S, xin, yout, ew, s);
+  auto arnoldi_matvec = [&](const double* xin, double* yout, cudaStream_t st, const int* skip) {
+    return Sdf ? launch_trace_matvec_df(ctx, Sdf, xin, yout, ew, st, skip)
+               : launch_trace_matvec(ctx, S, xin, yout, ew, st, skip);
   };
   rc = launch_trace_rhs(ctx, g, b, s);
   if (rc) return rc;
   const int wpb = 8;
-  auto precond = [&](const double* r, double* z) {
+  auto precond = [&](const double* r, double* z, cudaStream_t st, const int* skip) {
     if (ctx->pm)
-      pm_face_apply(ctx, ctx->d_pc, r, z, s);
+      pm_face_apply(ctx, ctx->d_pc, r, z, st, skip);
     else if (ctx->scheme)
-      k_node_block_apply<<<nblocks(n), kThreads, 0, s>>>(ctx->d_pcn, ctx->n_tnodes, ctx->M, r, z);
+      k_node_block_apply<<<nblocks(n), kThreads, 0, st>>>(ctx->d_pcn, ctx->n_tnodes, ctx->M, r, z, skip);
     else
-      k_face_block_apply<<<(unsigned)((ctx->F + wpb - 1) / wpb), 32 * wpb, sizeof(double) * wpb * B, s>>>(
-          ctx->d_pc, ctx->F, B, r, z);
+      k_face_block_apply<<<(unsigned)((ctx->F + wpb - 1) / wpb), 32 * wpb, sizeof(double) * wpb * B, st>>>(
+          ctx->d_pc, ctx->F, B, r, z, skip);
   };
   auto dot_host = [&](const double* basis, int nb, const double* v, double* out) -> int {
     HDG_CK(cudaMemsetAsync(ctx->d_red, 0, sizeof(double) * nb, s));
     dim3 grid(std::min<unsigned>(nblocks(n), 1024), nb);
-    k_multidot<<<grid, kThreads, 0, s>>>(n, basis, n, v, ctx->d_red);
+    k_multidot<<<grid, kThreads, 0, s>>>(n, basis, n, v, ctx->d_red, nullptr);
     HDG_CK(cudaGetLastError());
     HDG_CK(cudaMemcpyAsync(ctx->h_red, ctx->d_red, sizeof(double) * nb, cudaMemcpyDeviceToHost, s));
     HDG_CK(cudaStreamSynchronize(s));
     for (int i = 0; i < nb; ++i) out[i] = ctx->h_red[i];
     return HDG_OK;
+  };
+  // the device state of a cycle and the kernels of one cycle: step j preconditions basis
+  // vector j, applies the operator, orthogonalises twice against the basis (classical
+  // Gram-Schmidt), takes |w|, updates the rotations and the residual estimate, and writes basis
+  // vector j + 1; every step's kernels return at once once `done` is set
+  if (!ctx->d_gm) {
+    HDG_CK(cudaMalloc(&ctx->d_gm, sizeof(GmState)));
+    HDG_CK(cudaMallocHost(&ctx->h_gm, sizeof(GmState)));
+    std::memset(ctx->h_gm, 0, sizeof(GmState));
+  }
+  GmState* gm = static_cast<GmState*>(ctx->d_gm);
+  const int* done = &gm->done;
+  if (Sdf && (rc = prepare_matvec_df(ctx))) return rc;
+  auto enqueue_cycle = [&](cudaStream_t st) -> int {
+    const dim3 dgrid1(std::min<unsigned>(nblocks(n), 1024), 1);
+    for (int j = 0; j < m; ++j) {
+      precond(Vb + (size_t)j * n, zt, st, done);
+      if (int r2 = arnoldi_matvec(zt, w, st, done)) return r2;
+      for (int pass = 0; pass < 2; ++pass) {
+        double* hp = pass == 0 ? gm->h : gm->h2;
+        k_gm_zero<<<1, 64, 0, st>>>(hp, j + 1, done);
+        k_multidot<<<dim3(dgrid1.x, j + 1), kThreads, 0, st>>>(n, Vb, n, w, hp, done);
+        k_multiaxpy<<<nblocks(n), kThreads, 0, st>>>(n, Vb, n, hp, j + 1, w, done);
+      }
+      k_gm_zero<<<1, 64, 0, st>>>(&gm->wn2, 1, done);
+      k_multidot<<<dgrid1, kThreads, 0, st>>>(n, w, n, w, &gm->wn2, done);
+      k_gm_givens<<<1, 32, 0, st>>>(gm, j, m);
+      k_gm_scale<<<nblocks(n), kThreads, 0, st>>>(gm, n, w, Vb + (size_t)(j + 1) * n);
+    }
+    k_gm_solve<<<1, 32, 0, st>>>(gm, m);
+    HDG_CK(cudaMemsetAsync(w, 0, sizeof(double) * n, st));
+    k_multiaxpy_add_dev<<<nblocks(n), kThreads, 0, st>>>(n, Vb, n, gm->y, &gm->jdone, w);
+    precond(w, zt, st, nullptr);
+    k_axpy<<<nblocks(n), kThreads, 0, st>>>(n, 1.0, zt, x);
+    HDG_CK(cudaGetLastError());
+    return HDG_OK;
+  };
+  // the cycle as a CUDA graph, captured once for these buffers and replayed; if the capture
+  // fails the same kernels are launched one by one
+  const void* key[6] = {S, x, ctx->d_sw, Sdf, ctx->d_pc, ctx->d_pcn};
+  if (ctx->gm_graph && !std::equal(key, key + 6, ctx->gm_key)) {
+    cudaGraphExecDestroy(ctx->gm_graph);
+    ctx->gm_graph = nullptr;
+  }
+  if (!ctx->gm_graph && !ctx->gm_graph_failed) {
+    if (!ctx->gm_stream) HDG_CK(cudaStreamCreateWithFlags(&ctx->gm_stream, cudaStreamNonBlocking));
+    cudaGraph_t graph = nullptr;
+    bool ok = cudaStreamBeginCapture(ctx->gm_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    const int rcap = ok ? enqueue_cycle(ctx->gm_stream) : HDG_OK;
+    ok = cudaStreamEndCapture(ctx->gm_stream, &graph) == cudaSuccess && ok && rcap == HDG_OK;
+    if (ok && cudaGraphInstantiate(&ctx->gm_graph, graph, 0) != cudaSuccess) {
+      ctx->gm_graph = nullptr;
+      ok = false;
+    }
+    if (graph) cudaGraphDestroy(graph);
+    if (!ok) {
+      cudaGetLastError();  // a failed capture is not an error of the solve
+      ctx->gm_graph_failed = true;
+    } else {
+      std::copy(key, key + 6, ctx->gm_key);
+    }
+  }
+  auto run_cycle = [&]() -> int {
+    if (ctx->gm_graph) {
+      LaunchScope ls(ctx, HDG_KERNEL_TRACE, s);
+      HDG_CK(cudaGraphLaunch(ctx->gm_graph, s));
+      ++ctx->gm_replays;
+      return HDG_OK;
+    }
+    return enqueue_cycle(s);
   };
   HDG_CK(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
   double bn2;
@@ -935,7 +1103,6 @@ static int gmres_solve(hdg_ctx* ctx, const double* S, const double* g, double* x
     *final_res = 0.0;
     return HDG_OK;
   }
-  std::vector<double> H((m + 1) * m), cs(m), sn(m), gv(m + 1), h(m + 1), h2(m + 1), yv(m);
   double rel = 1.0;
   int total = 0;
   bool first = true;
@@ -958,60 +1125,23 @@ static int gmres_solve(hdg_ctx* ctx, const double* S, const double* g, double* x
     rel = beta / bnorm;
     if (rel <= rtol || total >= max_it) break;
     k_scale_copy<<<nblocks(n), kThreads, 0, s>>>(n, 1.0 / beta, w, Vb);
-    std::fill(gv.begin(), gv.end(), 0.0);
-    gv[0] = beta;
-    int j = 0;
-    for (; j < m && total < max_it; ++j, ++total) {
-      precond(Vb + (size_t)j * n, zt);
-      rc = arnoldi_matvec(zt, w);
-      if (rc) return rc;
-      // classical Gram-Schmidt, twice
-      rc = dot_host(Vb, j + 1, w, h.data());
-      if (rc) return rc;
-      HDG_CK(cudaMemcpyAsync(ctx->d_red + 64, h.data(), sizeof(double) * (j + 1), cudaMemcpyHostToDevice, s));
-      k_multiaxpy<<<nblocks(n), kThreads, 0, s>>>(n, Vb, n, ctx->d_red + 64, j + 1, w);
-      rc = dot_host(Vb, j + 1, w, h2.data());
-      if (rc) return rc;
-      HDG_CK(cudaMemcpyAsync(ctx->d_red + 64, h2.data(), sizeof(double) * (j + 1), cudaMemcpyHostToDevice, s));
-      k_multiaxpy<<<nblocks(n), kThreads, 0, s>>>(n, Vb, n, ctx->d_red + 64, j + 1, w);
-      for (int i = 0; i <= j; ++i) h[i] += h2[i];
-      double wn2;
-      rc = dot_host(w, 1, w, &wn2);
-      if (rc) return rc;
-      h[j + 1] = std::sqrt(wn2);
-      if (h[j + 1] > 0.0) k_scale_copy<<<nblocks(n), kThreads, 0, s>>>(n, 1.0 / h[j + 1], w, Vb + (size_t)(j + 1) * n);
-      for (int i = 0; i < j; ++i) {  // apply previous rotations
-        double t = cs[i] * h[i] + sn[i] * h[i + 1];
-        h[i + 1] = -sn[i] * h[i] + cs[i] * h[i + 1];
-        h[i] = t;
-      }
-      double den = std::hypot(h[j], h[j + 1]);
-      cs[j] = den > 0.0 ? h[j] / den : 1.0;
-      sn[j] = den > 0.0 ? h[j + 1] / den : 0.0;
-      h[j] = den;
-      h[j + 1] = 0.0;
-      gv[j + 1] = -sn[j] * gv[j];
-      gv[j] = cs[j] * gv[j];
-      for (int i = 0; i <= j; ++i) H[i * m + j] = h[i];
-      rel = std::fabs(gv[j + 1]) / bnorm;
-      if (rel <= rtol) {
-        ++j;
-        ++total;
-        break;
-      }
-    }
-    // y = H^{-1} g ; x += M^{-1} V y
-    for (int i = j - 1; i >= 0; --i) {
-      double t = gv[i];
-      for (int k = i + 1; k < j; ++k) t -= H[i * m + k] * yv[k];
-      yv[i] = t / H[i * m + i];
-    }
-    HDG_CK(cudaMemcpyAsync(ctx->d_red + 64, yv.data(), sizeof(double) * j, cudaMemcpyHostToDevice, s));
-    HDG_CK(cudaMemsetAsync(w, 0, sizeof(double) * n, s));
-    k_multiaxpy_add<<<nblocks(n), kThreads, 0, s>>>(n, Vb, n, ctx->d_red + 64, j, w);
-    precond(w, zt);
-    k_axpy<<<nblocks(n), kThreads, 0, s>>>(n, 1.0, zt, x);
-    HDG_CK(cudaGetLastError());
+    // one restart cycle on the device: its starting state, the m Arnoldi steps (replayed as a
+    // graph when one could be captured), the back substitution and x += M^{-1} V y
+    GmState& hs = *static_cast<GmState*>(ctx->h_gm);
+    hs.gv[0] = beta;
+    hs.bnorm = bnorm;
+    hs.rtol = rtol;
+    hs.rel = rel;
+    hs.done = 0;
+    hs.jdone = 0;
+    hs.total = total;
+    hs.max_it = max_it;
+    HDG_CK(cudaMemcpyAsync(gm, &hs, sizeof(GmState), cudaMemcpyHostToDevice, s));
+    if ((rc = run_cycle())) return rc;
+    HDG_CK(cudaMemcpyAsync(&hs, gm, sizeof(GmState), cudaMemcpyDeviceToHost, s));
+    HDG_CK(cudaStreamSynchronize(s));
+    total = hs.total;
+    ++ctx->gm_cycles;
   }
   *final_res = rel;  // of the last FP64 residual
   *iters = total;

@@ -48,7 +48,7 @@ EXPORTED = [
     "hdg_axpby", "hdg_assemble_condense_host", "hdg_assemble_condense_graph", "hdg_newton_solve",
     "hdg_ctx_set_refinement", "hdg_ctx_graph_replays", "hdg_ctx_set_trace_solver", "hdg_dirk3_step",
     "hdg_entropy_production", "hdg_mesh_copy_trace_map", "hdg_mesh_copy_face_bc", "hdg_ctx_set_boundary_state",
-    "hdg_mesh_copy_layout",
+    "hdg_mesh_copy_layout", "hdg_ctx_trace_cycles",
 ]
 HDG_BC_PERIODIC = 0
 HDG_BC_STATE = 1
@@ -126,6 +126,7 @@ def _load():
                                     POINTER(c_int), POINTER(c_double), POINTER(c_double), POINTER(c_int), P]),
         "hdg_ctx_set_refinement": (c_int, [P, c_double, c_int]),
         "hdg_ctx_graph_replays": (c_int, [P, POINTER(c_int64)]),
+        "hdg_ctx_trace_cycles": (c_int, [P, POINTER(c_int64), POINTER(c_int64)]),
         "hdg_ctx_set_trace_solver": (c_int, [P, c_int, c_double, c_int]),
         "hdg_entropy_production": (c_int, [P, P, P, POINTER(c_double), POINTER(c_double), P]),
         "hdg_mesh_copy_trace_map": (c_int, [P, P]),
@@ -429,6 +430,13 @@ def hdg_ctx_graph_replays(ctx):
     n = c_int64()
     _check(_lib.hdg_ctx_graph_replays(ctx, byref(n)))
     return n.value
+
+
+def hdg_ctx_trace_cycles(ctx):
+    """(GMRES restart cycles so far, of them replayed as a CUDA graph)."""
+    c, r = c_int64(), c_int64()
+    _check(_lib.hdg_ctx_trace_cycles(ctx, byref(c), byref(r)))
+    return c.value, r.value
 
 
 def hdg_axpby(n, a, x, b, y, out, stream=None):

@@ -8,6 +8,7 @@ and the output buffers of hdg_assemble_condense. No method arithmetic happens he
 from __future__ import annotations
 
 import math
+import sys
 
 import numpy as np
 import torch
@@ -198,3 +199,34 @@ def method_flops_per_element(info: dict, viscous: bool, kernel: str) -> float:
     f = slice_flops_per_element(info, viscous, "mixed_face")
     return asm * (v if kernel == "mixed_assemble" else f) / (v + f)
 
+
+
+def main(argv=None):
+    """Run a named workload's assemble + condense a few times on cuda:0 and print the time of
+    each call (CUDA events): `python -m paper_1808_05066_gb300.workload ns3d_mixed_tgv --n 4`."""
+    import argparse
+    ap = argparse.ArgumentParser()
+    ap.add_argument("name", choices=sorted(wl.WORKLOADS))
+    ap.add_argument("--n", type=int, default=None, help="cube / square resolution (default: the workload's)")
+    ap.add_argument("--calls", type=int, default=3)
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    args = ap.parse_args(argv)
+    W = DeviceWorkload(args.name, n_override=args.n)
+    prec = hdg.HDG_PREC_MIXED if args.precision == "mixed" else hdg.HDG_PREC_FP64
+    E = W.info["n_elem"]
+    for k in range(args.calls):
+        W.status.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        W.assemble(prec)
+        b.record()
+        torch.cuda.synchronize(W.dev)
+        ms = a.elapsed_time(b)
+        print(f"{args.name} E={E} call {k}: {ms:.2f} ms, {E / ms * 1e3:.0f} elem/s, "
+              f"flagged elements {int((W.status != 0).sum())}", flush=True)
+    W.close()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
