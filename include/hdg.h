@@ -335,7 +335,9 @@ int hdg_residual_norm(hdg_ctx_t ctx, const double* R, double* norm, void* stream
  * the host; res_history (host, nullable, max_newton + 1 entries) receives the residual norm
  * before each update, trace_iters (host, nullable) the total trace-solver iterations.
  * Context-owned workspaces are allocated on the first call. Synchronises once per Newton
- * iteration (residual norm and status bits). Errors: HDG_ERR_NOT_CONVERGED (max_newton
+ * iteration (residual norm and status bits). On meshes of one degree each iteration's
+ * assemble + condense goes through hdg_assemble_condense_graph (captured on the first
+ * iteration, replayed on the others); GMRES cycles are replayed graphs as in hdg_trace_solve. Errors: HDG_ERR_NOT_CONVERGED (max_newton
  * updates made, or the trace solve missed its tolerance), HDG_ERR_NONPHYSICAL,
  * HDG_ERR_SINGULAR, HDG_ERR_REFINE / HDG_ERR_TIMEOUT (mixed form with the FP64 recomputation
  * off). */

@@ -830,8 +830,13 @@ int hdg_newton_solve(hdg_ctx_t ctx, double* V, double* Vhat, const double* hist,
   if (trace_iters) *trace_iters = 0;
   for (int it = 0;; ++it) {
     HDG_CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int32_t) * E, s));
-    int rc = hdg_assemble_condense(ctx, V, Vhat, hist, mass_coef, precision, ctx->d_S, ctx->d_g, ctx->d_recov,
-                                   ctx->d_R, ctx->d_status, s);
+    // one degree: the assemble + condense launch sequence is captured on the first iteration and
+    // replayed on the others (its arguments do not change within the solve); mixed degrees: one
+    // persistent launch
+    int rc = ctx->pm ? hdg_assemble_condense(ctx, V, Vhat, hist, mass_coef, precision, ctx->d_S, ctx->d_g,
+                                             ctx->d_recov, ctx->d_R, ctx->d_status, s)
+                     : hdg_assemble_condense_graph(ctx, V, Vhat, hist, mass_coef, precision, ctx->d_S, ctx->d_g,
+                                                   ctx->d_recov, ctx->d_R, ctx->d_status, s);
     if (rc) return rc;
     rc = hdg::residual_norm(ctx, ctx->d_R, &rn, s);
     if (rc) return rc;
