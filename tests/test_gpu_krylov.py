@@ -37,3 +37,29 @@ def test_gmres_cycles_replay_as_graphs_and_match_oracle(name):
     with pytest.raises(hdg.HdgError) as ei:
         hdg.hdg_trace_solve(gc.ctx.handle, gc.S, gc.g, dVh2, hdg.HDG_SOLVER_GMRES, 1e-13, 7)
     assert ei.value.code == hdg.HDG_ERR_NOT_CONVERGED
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_newton_iterations_replay_graphs(precision):
+    """A BDF1 Newton step with GMRES trace solves: every update after the first replays the
+    captured assemble + condense sequence, every GMRES cycle is a graph replay, and the step
+    reaches the same state as the oracle's time step."""
+    from oracle.hdg import time_step
+    case = CASES["euler2d_p2"]
+    gc = GpuCase(case)
+    prob, Q, V, Vh = oracle_setup(case)
+    dt = 0.05
+    res = time_step(prob, Q, V, Vh, [V], 1, dt, tol=1e-12, max_it=10)
+    hdg = gc.hdg
+    hdg.hdg_ctx_set_trace_solver(gc.ctx.handle, hdg.HDG_SOLVER_GMRES, 1e-13, 2000)
+    g0 = hdg.hdg_ctx_graph_replays(gc.ctx.handle)
+    c0, r0 = hdg.hdg_ctx_trace_cycles(gc.ctx.handle)
+    V_gpu, Vh_gpu = gc.V.clone(), gc.Vhat.clone()
+    it, rn = hdg.hdg_newton_step(gc.ctx.handle, V_gpu, Vh_gpu, gc.V, None, dt, 1, precision, 1e-12, 10)
+    g1 = hdg.hdg_ctx_graph_replays(gc.ctx.handle)
+    c1, r1 = hdg.hdg_ctx_trace_cycles(gc.ctx.handle)
+    assert it == res.iters >= 2
+    assert g1 - g0 == it                    # it + 1 assemblies: the first captures, the rest replay
+    assert c1 - c0 >= it and r1 - r0 == c1 - c0
+    assert rel_fro(V_gpu.cpu().numpy(), res.V) < 1e-10
+    assert rel_fro(Vh_gpu.cpu().numpy(), res.Vhat) < 1e-10
