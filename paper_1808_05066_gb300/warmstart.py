@@ -167,7 +167,7 @@ def collect_and_train(st: Stepper, n_steps: int, skip: int = 2, epochs: int = 30
 
 
 def experiment(workload="ns2d_p3_vortices", n_train=200, n_apply=200, skip=2, epochs=40, lr=2e-3,
-               precision=hdg.HDG_PREC_MIXED, tol=1e-10):
+               precision=hdg.HDG_PREC_MIXED, tol=1e-10, dt=None):
     """The learned warm-start experiment: n_train plain steps (training data), training,
     then n_apply steps from the same state with the plain start and with the network.
     Returns a summary dict (Newton updates, initial residuals, wall time per step)."""
@@ -175,6 +175,8 @@ def experiment(workload="ns2d_p3_vortices", n_train=200, n_apply=200, skip=2, ep
 
     from .workload import DeviceWorkload
     W = DeviceWorkload(workload, outputs=False)
+    if dt is not None:  # a time step other than the workload's (the BDF steps use Stepper.dt)
+        W.dt = dt
     st = Stepper(W, precision=precision, tol=tol)
     t0 = time.perf_counter()
     recs, net = collect_and_train(st, n_train, skip=skip, epochs=epochs, lr=lr)
@@ -210,5 +212,6 @@ if __name__ == "__main__":
     ap.add_argument("--train", type=int, default=200)
     ap.add_argument("--apply", type=int, default=200)
     ap.add_argument("--epochs", type=int, default=40)
+    ap.add_argument("--dt", type=float, default=None, help="time step (default: the workload's)")
     a = ap.parse_args()
-    print(json.dumps(experiment(a.workload, a.train, a.apply, epochs=a.epochs)))
+    print(json.dumps(experiment(a.workload, a.train, a.apply, epochs=a.epochs, dt=a.dt)))
