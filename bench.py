@@ -287,6 +287,21 @@ def mixed_degree_leg(args, local, barrier, max_over_ranks, ws):
                "elements_flagged": bad,
                "bytes_written_per_step": 8 * (W.info["len_S"] + W.info["len_g"] + W.info["len_recov"] +
                                               W.info["len_R"])}
+        # the FP64 pipe roofline of the fused launch: the flops of every element's class and size
+        from paper_1808_05066_gb300.workload import FP64_PIPE_TFLOPS, class_flops_per_element
+        lay = W.mesh.layout()
+        import numpy as _np
+        tdeg = _np.zeros(E, dtype=_np.int64)
+        face_of, _, _ = W.mesh.topology()
+        tdeg = lay["face_deg"][face_of].max(axis=1)
+        ntq = _np.diff(lay["toff"])
+        flops = sum(class_flops_per_element(int(pk), int(pt), int(nt))
+                    for pk, pt, nt in zip(W.p_elem, tdeg, ntq))
+        tf = flops * args.mixed_degree_steps / (ms / 1000.0) / 1e12
+        out["roofline"] = {"bound": "fp64", "achieved": tf, "peak": FP64_PIPE_TFLOPS, "unit": "TFLOP/s",
+                           "frac": tf / FP64_PIPE_TFLOPS, "kernel": "k_pclass_fused",
+                           "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2.07 GHz (a DFMA probe measured 1.20)",
+                           "flops_per_step": flops}
         if args.mixed_degree_newton:
             del W.S, W.recov
             torch.cuda.empty_cache()

@@ -136,7 +136,9 @@ enum { HDG_BC_PERIODIC = 0, HDG_BC_STATE = 1, HDG_BC_SLIP = 2 };
  *               (quad_points 0: element degree + 1 points per direction in the volume, the
  *               element's largest face degree + 1 on its faces); the compute calls then take
  *               the packed per-element layout of hdg_mesh_copy_layout.
- *   p           polynomial degree k of Sec. 3.1.2 (1..4); ignored when p_per_elem is given.
+ *   p           polynomial degree k of Sec. 3.1.2 (1..4); ignored when p_per_elem is given. 3D p = 4
+ *               (Navier-Stokes, FP64 form) runs on the element-class kernels of mixed-degree meshes,
+ *               with the uniform layout.
  *   scheme      trace space of Sec. 3.4: HDG_SCHEME_HDG (one trace per face, Vhat [F][Nf][m]) or
  *               HDG_SCHEME_EDG (a continuous trace, one unknown per skeleton node, Vhat [N][m],
  *               nodes numbered in order of first appearance over (element, local face, face

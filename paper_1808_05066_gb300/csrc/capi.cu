@@ -153,7 +153,18 @@ int hdg_mesh_create(int dim, const int64_t n[3], const double lo[3], const doubl
   }
   m->m.scheme = scheme;
   if (scheme != HDG_SCHEME_HDG) hdg::build_edg(m->m);  // every face is interior: IEDG is EDG
-  if (mixed && (rc = hdg::build_mixed(m->m, p_per_elem)) != 0) {
+  // 3D p = 4 has no uniform kernels: a periodic HDG mesh of that one degree is served by the
+  // element-class kernels too (its packed layout is the uniform one)
+  bool periodic = true;
+  for (int d = 0; bc && d < 2 * dim; ++d) periodic = periodic && bc[d] == HDG_BC_PERIODIC;
+  std::vector<int8_t> all4;
+  const int8_t* pe = p_per_elem;
+  if (!mixed && dim == 3 && p == 4 && scheme == HDG_SCHEME_HDG && periodic && quad_points == p + 1) {
+    all4.assign(m->m.E, (int8_t)4);
+    pe = all4.data();
+    mixed = true;
+  }
+  if (mixed && (rc = hdg::build_mixed(m->m, pe)) != 0) {
     delete m;
     set_error("hdg_mesh_create: mixed-degree face matching failed (code " + std::to_string(rc) + ")");
     return HDG_ERR_INVALID_ARG;
@@ -188,9 +199,10 @@ int hdg_mesh_get_info(hdg_mesh_t mesh, hdg_mesh_info* out) {
   out->n_trace_nodes = m.scheme == HDG_SCHEME_HDG ? m.nFaces * m.ref.Nf : m.n_edg;
   out->n_trace = out->n_trace_nodes * (m.dim + 2);
   out->n_boundary_faces = m.n_boundary;
-  out->mixed = m.pe.empty() ? 0 : 1;
-  if (out->mixed) {
+  out->mixed = 0;
+  if (!m.pe.empty()) {
     out->p_min = *std::min_element(m.pe.begin(), m.pe.end());
+    out->mixed = out->p_min != m.p ? 1 : 0;
     out->n_trace_nodes = m.fnoff.back();
     out->n_trace = out->n_trace_nodes * (m.dim + 2);
     out->len_V = m.voff.back();

@@ -136,6 +136,30 @@ def flops_per_element(info: dict, viscous: bool, kernel: str) -> float:
     raise ValueError(kernel)
 
 
+# FP64 pipe of a GB300: 152 SMs x 2 FP64 FMA per clock x 2 flops x 2.07 GHz (a DFMA probe on the
+# same GPU type measured 1.20 TFLOP/s)
+FP64_PIPE_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def class_flops_per_element(pk: int, pt: int, nt_own: int) -> float:
+    """FP64 flops of one element of the mixed-degree fused kernel (3D Navier-Stokes), counted from
+    its loops like flops_per_element: element degree pk (volume rule pk + 1), trace degree pt on
+    every face (face rule pt + 1), the face contractions over the element's face nodes (degree pk)
+    and the trace nodes (degree pt), and the condensation with the element's own trace size
+    nt_own; the projection onto the faces' own spaces is not counted."""
+    D, M, NF = 3, 5, 4
+    NP = (pk + 1) * (pk + 2) * (pk + 3) // 6
+    NFK = (pk + 1) * (pk + 2) // 2
+    NFN = (pt + 1) * (pt + 2) // 2
+    NG, NGF = (pk + 1) ** 3, (pt + 1) ** 2
+    NZ, NV = NP + NF * NFN, NP * M
+    NR, NRF = D + 1, D + 2
+    vol = M * M * (NP * (NP * NG * NR + NF * NFN * NG * (NR - 1)) + NP * NG * NR * (D + 1))
+    face = NF * M * M * ((NFK + NFN) * NZ * NGF * NRF + (NFK + NFN) * NGF * NRF)
+    cond = NV ** 3 / 3.0 + (nt_own + 1) * NV ** 2 + nt_own * nt_own * NV + nt_own * NV
+    return 2.0 * (vol + face + cond)
+
+
 SLICES = 6  # exact bf16 slices per operand in the mixed form's tensor-core products
 
 

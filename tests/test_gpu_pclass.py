@@ -159,3 +159,17 @@ def test_mixed_degree_bdf_newton_step_matches_oracle(solver):
     Vo = np.concatenate([v.ravel() for v in res.V])
     assert rel_fro(V_gpu.cpu().numpy(), Vo) < 1e-10
     assert rel_fro(Vh_gpu.cpu().numpy().reshape(-1), res.Vhat.reshape(-1)) < 1e-10
+
+
+def test_uniform_3d_p4_runs_on_the_class_kernels():
+    """3D Navier-Stokes at one degree p = 4 (no uniform kernels): the mesh keeps the uniform
+    layout and the element-class launch condenses it; two elements against the oracle."""
+    prob, V, Vh, hist, g = _setup(1, (4,), 13)
+    assert g[3]["mixed"] == 0 and g[3]["p"] == 4 and g[3]["nt"] == 300 and g[3]["nv"] == 175
+    lay = g[4]
+    assert list(lay["soff"][:3]) == [0, 300 * 300, 2 * 300 * 300]
+    res = _run_gpu(g)
+    worst = _compare(prob, V, Vh, hist, g, res, [0, 5])
+    for (cls, k), v in worst.items():
+        assert cls == (4, 4)
+        assert v <= (1e-12 if k in ("Rv", "Rt") else 1e-10), (k, v)
