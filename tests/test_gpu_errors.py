@@ -117,9 +117,19 @@ def test_invalid_arguments_of_compute_calls():
 
 
 def test_unsupported_configuration():
+    """3D p = 4 runs on the element-class kernels for Navier-Stokes in the FP64 form only: Euler
+    physics there, and the mixed form, say HDG_ERR_UNSUPPORTED."""
+    import torch
     from paper_1808_05066_gb300 import hdg
-    mesh = hdg.Mesh(3, 1, 0.0, 1.0, 4)          # 3D p = 4 is not compiled in
-    assert _code(lambda: hdg.Context(mesh, 1.4, 0.1, 1600.0, 0.71, 0)) == hdg.HDG_ERR_UNSUPPORTED
+    mesh = hdg.Mesh(3, 1, 0.0, 1.0, 4)
+    assert _code(lambda: hdg.Context(mesh, 1.4, 0.1, 0.0, 0.71, 0)) == hdg.HDG_ERR_UNSUPPORTED
+    ctx = hdg.Context(mesh, 1.4, 0.1, 1600.0, 0.71, 0)
+    i = mesh.info
+    buf = {k: torch.zeros(i["len_" + k], dtype=torch.float64, device="cuda") for k in ("V", "g", "S", "recov", "R")}
+    Vh = torch.zeros(i["n_trace"], dtype=torch.float64, device="cuda")
+    code = _code(lambda: hdg.hdg_assemble_condense(ctx.handle, buf["V"], Vh, None, 0.0, hdg.HDG_PREC_MIXED, buf["S"],
+                                                   buf["g"], buf["recov"], buf["R"]))
+    assert code == hdg.HDG_ERR_UNSUPPORTED
 
 
 def test_tcgen05_condensation_wait_timeout(monkeypatch):
