@@ -264,15 +264,15 @@ int hdg_ctx_trace_cycles(hdg_ctx_t ctx, int64_t* cycles, int64_t* replays);
 
 /* hdg_assemble_condense with S and g delivered to HOST memory (Sec. 3.2, the same local
  * elimination as hdg_assemble_condense). The elements are processed in chunks; each chunk's S
- * goes to one of two library-owned device buffers and is copied to S_host on an internal copy
- * stream while the next chunk computes, so the copy of S (the bulk of the output) overlaps
- * the kernels. g is copied to g_host at the end.
+ * goes to one of a ring of four library-owned device buffers and is copied to S_host on an
+ * internal copy stream while the next chunks compute, so the copy of S (the bulk of the output)
+ * overlaps the kernels. g is copied to g_host at the end.
  *   V, Vhat, hist, recov, R, elem_status: device pointers as in hdg_assemble_condense.
  *   S_host [E][NT][NT], g_host [E][NT]: host memory; page-locked (cudaHostAlloc) memory is
  *   needed for the copies to overlap the kernels.
  * The call is asynchronous on `stream`: S_host and g_host are complete once the stream has
- * reached the end of the call (cudaStreamSynchronize). The first call allocates the two chunk
- * buffers (2 x chunk x NT x NT doubles) and the context's g. Errors: HDG_ERR_INVALID_ARG for
+ * reached the end of the call (cudaStreamSynchronize). The first call allocates the ring
+ * (4 x chunk x NT x NT doubles) and the context's g. Errors: HDG_ERR_INVALID_ARG for
  * null pointers or an unknown precision, HDG_ERR_CUDA for a failed allocation or launch. */
 int hdg_assemble_condense_host(hdg_ctx_t ctx, const double* V, const double* Vhat, const double* hist,
                                double mass_coef, int precision, double* S_host, double* g_host, double* recov,

@@ -54,14 +54,15 @@ double* chunk_S(hdg_ctx* c, double* S, int64_t e0, cudaStream_t s, int* rc) {
   *rc = HDG_OK;
   if (!c->sink_host) return S;
   const size_t per = (size_t)c->NT * c->NT;
-  if (c->Sbuf_chunk < c->chunk) {  // first use, or a larger chunk: (re)allocate both buffers
+  if (c->Sbuf_chunk < c->chunk) {  // first use, or a larger chunk: (re)allocate the ring
     cudaStreamSynchronize(c->copy_stream);
     for (double*& b : c->d_Sbuf) {
       if (b) cudaFree(b);
       b = nullptr;
     }
     c->Sbuf_chunk = 0;
-    for (double*& b : c->d_Sbuf) {
+    for (int k = 0; k < c->sink_bufs; ++k) {
+      double*& b = c->d_Sbuf[k];
       if (cudaMalloc(&b, sizeof(double) * per * c->chunk) != cudaSuccess) {
         set_error("hdg_assemble_condense_host: cannot allocate the chunk buffers of S");
         *rc = HDG_ERR_CUDA;
@@ -70,8 +71,8 @@ double* chunk_S(hdg_ctx* c, double* S, int64_t e0, cudaStream_t s, int* rc) {
     }
     c->Sbuf_chunk = c->chunk;
   }
-  const int b = c->sink_idx & 1;
-  if (c->sink_idx >= 2 && cudaStreamWaitEvent(s, c->ev_copied[b], 0) != cudaSuccess) {  // buffer copied out
+  const int b = c->sink_idx % c->sink_bufs;
+  if (c->sink_idx >= c->sink_bufs && cudaStreamWaitEvent(s, c->ev_copied[b], 0) != cudaSuccess) {  // copied out
     *rc = HDG_ERR_CUDA;
     return nullptr;
   }
@@ -81,7 +82,7 @@ double* chunk_S(hdg_ctx* c, double* S, int64_t e0, cudaStream_t s, int* rc) {
 
 int chunk_done(hdg_ctx* c, int64_t e0, int64_t ne, cudaStream_t s) {
   if (!c->sink_host) return HDG_OK;
-  const int b = c->sink_idx & 1;
+  const int b = c->sink_idx % c->sink_bufs;
   const size_t per = (size_t)c->NT * c->NT;
   HDG_CK(cudaEventRecord(c->ev_done[b], s));
   HDG_CK(cudaStreamWaitEvent(c->copy_stream, c->ev_done[b], 0));
@@ -373,6 +374,10 @@ int hdg_ctx_create(hdg_mesh_t mesh, const hdg_physics* phys, int device, hdg_ctx
     if (v >= 0 && v < 4) c->cond_variant = (int)v;
   }
   if (const char* st = std::getenv("HDG_T5_STALL_FIRST_COPY")) c->t5_stall = std::strtol(st, nullptr, 10) != 0;
+  if (const char* sb = std::getenv("HDG_SINK_BUFFERS")) {  // device buffers of the host-sink ring
+    long v = std::strtol(sb, nullptr, 10);
+    if (v >= 2 && v <= hdg_ctx::kSinkMax) c->sink_bufs = (int)v;
+  }
   if (const char* ch = std::getenv("HDG_ELEMENT_CHUNK")) {
     long v = std::strtol(ch, nullptr, 10);
     if (v > 0) c->chunk = std::min<int64_t>(v, c->E);
@@ -494,9 +499,9 @@ void hdg_ctx_destroy(hdg_ctx_t c) {
   if (c->copy_stream) {
     cudaStreamSynchronize(c->copy_stream);
     cudaStreamDestroy(c->copy_stream);
-    for (int b = 0; b < 2; ++b) {
-      cudaEventDestroy(c->ev_done[b]);
-      cudaEventDestroy(c->ev_copied[b]);
+    for (int b = 0; b < hdg_ctx::kSinkMax; ++b) {
+      if (c->ev_done[b]) cudaEventDestroy(c->ev_done[b]);
+      if (c->ev_copied[b]) cudaEventDestroy(c->ev_copied[b]);
       if (c->d_Sbuf[b]) cudaFree(c->d_Sbuf[b]);
     }
   }
@@ -657,7 +662,7 @@ int hdg_assemble_condense_host(hdg_ctx_t ctx, const double* V, const double* Vha
   cudaStream_t s = (cudaStream_t)stream;
   if (!ctx->copy_stream) {
     HDG_CK(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < ctx->sink_bufs; ++b) {
       HDG_CK(cudaEventCreateWithFlags(&ctx->ev_done[b], cudaEventDisableTiming));
       HDG_CK(cudaEventCreateWithFlags(&ctx->ev_copied[b], cudaEventDisableTiming));
     }
@@ -678,7 +683,7 @@ int hdg_assemble_condense_host(hdg_ctx_t ctx, const double* V, const double* Vha
   ctx->sink_host = nullptr;
   if (rc) return rc;
   HDG_CK(cudaMemcpyAsync(g_host, ctx->d_g, sizeof(double) * ctx->E * ctx->NT, cudaMemcpyDeviceToHost, s));
-  for (int b = 0; b < 2 && b < used; ++b) HDG_CK(cudaStreamWaitEvent(s, ctx->ev_copied[b], 0));
+  for (int b = 0; b < ctx->sink_bufs && b < used; ++b) HDG_CK(cudaStreamWaitEvent(s, ctx->ev_copied[b], 0));
   return HDG_OK;
 }
 

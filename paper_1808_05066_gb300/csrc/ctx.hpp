@@ -64,14 +64,16 @@ struct hdg_ctx {
   double* d_red = nullptr;   // reduction buffer (device)
   double* h_red = nullptr;   // pinned host mirror
   // streaming of S to host memory (hdg_assemble_condense_host): while `sink_host` is set, the
-  // element chunks write S into two device buffers in turn and each chunk's S is copied to the
-  // host on `copy_stream` while the next chunk computes
+  // element chunks write S into a ring of device buffers in turn and each chunk's S is copied to
+  // the host on `copy_stream` while the next chunks compute
   double* sink_host = nullptr;
   int sink_idx = 0;
-  double* d_Sbuf[2] = {nullptr, nullptr};
+  static constexpr int kSinkMax = 8;
+  int sink_bufs = 4;       // device buffers in the ring (environment HDG_SINK_BUFFERS, 2..8)
+  double* d_Sbuf[kSinkMax] = {};
   int64_t Sbuf_chunk = 0;  // elements per buffer
   cudaStream_t copy_stream = nullptr;
-  cudaEvent_t ev_done[2] = {nullptr, nullptr}, ev_copied[2] = {nullptr, nullptr};
+  cudaEvent_t ev_done[kSinkMax] = {}, ev_copied[kSinkMax] = {};
   // CUDA graph of one assemble + condense (hdg_assemble_condense_graph): the arguments and
   // library state it was captured with, and the launches it adds per replay
   struct GraphKey {
