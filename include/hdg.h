@@ -5,15 +5,19 @@
  * (Sec. 3.3, Eqs. hDG_NS0-hDG_NS3) in entropy variables v with a hybrid trace vhat.
  * The local equations are eliminated element by element ("static condensation",
  * Sec. 3.2 last paragraph, Sec. 3.3) and only the trace unknowns are globally
- * coupled. This library implements, on periodic simplex meshes with the HDG trace
- * space (E^E_h empty, Sec. 3.4 "Examples of schemes"):
+ * coupled. This library implements, on simplex meshes of a Cartesian box (periodic or
+ * bounded per axis; one degree, or elements of different degree) with the HDG trace space
+ * (E^E_h empty) or the continuous EDG / IEDG trace spaces of Sec. 3.4:
  *   - the per-element Newton linearisation and condensation     hdg_assemble_condense
  *   - the global trace solve                                     hdg_trace_solve
  *   - the interior recovery                                      hdg_recover_interior
  *   - a full BDF Newton step around them                         hdg_newton_step
- * with the symmetric Lax-Friedrichs stabilisation sigma = lambda_max(vhat) A0(vhat)
- * (Eq. sLxF with v* = vhat, the choice of Sec. 5) in the inviscid flux of
- * Eq. numericalFlux, and the viscous flux G(vhat, q) . n of Eq. numericalFluxNS_2.
+ *   - a DIRK(3,3) step (Sec. 5's integrator)                     hdg_dirk3_step
+ * with, by default, the symmetric Lax-Friedrichs stabilisation sigma = lambda_max(vhat)
+ * A0(vhat) (Eq. sLxF with v* = vhat, the choice of Sec. 5) in the inviscid flux of
+ * Eq. numericalFlux and the viscous flux G(vhat, q) . n of Eq. numericalFluxNS_2; hdg_physics
+ * selects sigma_S (Eq. symStab), the viscous flux of Eq. numericalFluxNS_1 and a power-law
+ * viscosity (Sec. 5.6).
  *
  * Conventions shared by all calls
  *   - m = d + 2 state components. Entropy variables (v_1, w_1..w_d, v_m), v_m < 0.
