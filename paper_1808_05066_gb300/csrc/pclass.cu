@@ -223,7 +223,7 @@ __device__ void pc_pointwise(const PArgs& a, const PClassDev& T, const PhysParam
     }
     lifted_q(gr, lift, q);
     bad = !(v[M - 1] < 0.0) || !(vh[M - 1] < 0.0);
-    // derivatives with respect to vhat: F(vhat).n, sigma_SLF(vhat) (v - vhat), G(vhat, q).n
+    // derivatives with respect to vhat: F(vhat).n, sigma(vhat) (v - vhat), G(vhat, q).n
     Dual<M> vhd[M], dvd[M];
     for (int l = 0; l < M; ++l) {
       vhd[l] = dconst<M>(vh[l]);
@@ -235,12 +235,32 @@ __device__ void pc_pointwise(const PArgs& a, const PClassDev& T, const PhysParam
     cons_and_flux<D>(rh, velh, prh, ph.gamma, uh, Fh);
     bad = bad || !(rh.v > 0.0) || !(prh.v > 0.0);
     du_of_v<D>(vhd, dvd, ph.gamma, duh);
-    const Dual<M> lam = lambda_max<D>(rh, velh, prh, n, ph.gamma);
+    // sigma(vhat) (v - vhat) and the matrix sigma(vhat) = d(sigma (v - vhat))/dv: sigma_SLF =
+    // lambda_max A0 (Eq. sLxF) or sigma_S = |A_n| A0 (Eq. symStab), as physics selects
+    Dual<M> sdu[M];
+    double sig[M][M];
+    if (ph.stab == 1) {
+      abs_flux_jac_apply<D>(rh, velh, prh, n, ph.gamma, duh, sdu);
+      double vv[D];
+      for (int j = 0; j < D; ++j) vv[j] = velh[j].v;
+      for (int l = 0; l < M; ++l) {
+        double x[M], y[M];
+        for (int k = 0; k < M; ++k) x[k] = uh[k].d[l];
+        abs_flux_jac_apply<D>(rh.v, vv, prh.v, n, ph.gamma, x, y);
+        for (int i = 0; i < M; ++i) sig[i][l] = y[i];
+      }
+    } else {
+      const Dual<M> lam = lambda_max<D>(rh, velh, prh, n, ph.gamma);
+      for (int i = 0; i < M; ++i) {
+        sdu[i] = lam * duh[i];
+        for (int l = 0; l < M; ++l) sig[i][l] = lam.v * uh[i].d[l];
+      }
+    }
     Dual<M> hA[M];
     for (int i = 0; i < M; ++i) {
       Dual<M> s = Fh[i][0] * n[0];
       for (int j = 1; j < D; ++j) s = s + Fh[i][j] * n[j];
-      hA[i] = 0.5 * s + 0.5 * (lam * duh[i]);
+      hA[i] = 0.5 * s + 0.5 * sdu[i];
     }
     if (ph.gflux != 1) {  // ghat = G(vhat, q) . n (Eq. numericalFluxNS_2)
       Dual<M> Gh[M][D];
@@ -275,7 +295,7 @@ __device__ void pc_pointwise(const PArgs& a, const PClassDev& T, const PhysParam
       for (int j = 1; j < D; ++j) s = s + Fv[i][j] * n[j];
       HF[i] = Wf * (hA[i].v + 0.5 * s.v + gn[i].v);
       for (int l = 0; l < M; ++l) {
-        U0[i * M + l] = Wf * (0.5 * s.d[l] + 0.5 * lam.v * uh[i].d[l] + gn[i].d[l]);
+        U0[i * M + l] = Wf * (0.5 * s.d[l] + 0.5 * sig[i][l] + gn[i].d[l]);
         U1[i * M + l] = Wf * hA[i].d[l];
       }
     }
@@ -822,10 +842,6 @@ int pclass_autotune(hdg_ctx* c, const PArgs& base, cudaStream_t s) {
 int assemble_condense_pclass(hdg_ctx* c, const double* V, const double* Vhat, const double* hist, double mass_coef,
                              double* S, double* g, double* recov, double* R, int32_t* status, cudaStream_t s) {
   PMix& pm = *c->pm;
-  if (c->ph.stab != 0) {
-    set_error("assemble_condense: mixed-degree meshes are built with the sigma_SLF stabilization only");
-    return HDG_ERR_UNSUPPORTED;
-  }
   const int grid = c->num_sms > 0 ? c->num_sms : 152;
   const size_t need = sizeof(double) * (size_t)grid * pm.slot_doubles;
   if (c->scr_bytes < need) {

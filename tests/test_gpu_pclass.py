@@ -23,7 +23,7 @@ def _prim(x):
     return np.concatenate([rho[..., None], vel, p[..., None]], axis=-1)
 
 
-def _setup(n, degs, seed):
+def _setup(n, degs, seed, stabilization="slf"):
     import torch
     from oracle import physics as ph
     from oracle.hdg import Problem, consistent_Q, interpolate_state
@@ -33,14 +33,14 @@ def _setup(n, degs, seed):
     pe = np.random.default_rng(seed).choice(degs, size=E).astype(np.int8)
     # oracle
     om = OMesh(3, n, 0.0, L, 0, p_elem=pe)
-    prob = Problem(om, ph.Physics(mach=MACH, reynolds=RE, prandtl=PR))
+    prob = Problem(om, ph.Physics(mach=MACH, reynolds=RE, prandtl=PR, stabilization=stabilization))
     prim_fn = lambda x: wl.tgv_field(x * (2 * math.pi / L) + 0.3, MACH)
     V, Vh = interpolate_state(prob, prim_fn)
     Vh = wl.perturb(Vh, 1e-3, seed + 1)
     hist = [prob.history_weak(e, [V[e] * (1 + 1e-3)], [MASS]) for e in range(om.E)]
     # GPU: its own mesh, coordinates and state conversion
     mesh = hdg.Mesh(3, n, 0.0, L, 0, p_per_elem=pe)
-    ctx = hdg.Context(mesh, 1.4, MACH, RE, PR)
+    ctx = hdg.Context(mesh, 1.4, MACH, RE, PR, stabilization=1 if stabilization == "s" else 0)
     info, lay = mesh.info, mesh.layout()
     xnode, xfnode, _ = mesh.coords()
     dev = torch.device("cuda", 0)
@@ -173,3 +173,13 @@ def test_uniform_3d_p4_runs_on_the_class_kernels():
     for (cls, k), v in worst.items():
         assert cls == (4, 4)
         assert v <= (1e-12 if k in ("Rv", "Rt") else 1e-10), (k, v)
+
+
+def test_mixed_degree_with_symmetric_stabilization():
+    """The fused launch with sigma_S = |A_n| A0 (Eq. symStab) in place of sigma_SLF, every element
+    of a six-tet mesh of degrees 1..3 against the oracle."""
+    prob, V, Vh, hist, g = _setup(1, (1, 2, 3), 17, stabilization="s")
+    res = _run_gpu(g)
+    worst = _compare(prob, V, Vh, hist, g, res, range(prob.mesh.E))
+    for (cls, k), v in worst.items():
+        assert v <= (1e-12 if k in ("Rv", "Rt") else 1e-10), (cls, k, v)
