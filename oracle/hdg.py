@@ -581,21 +581,25 @@ def dirk3_step(prob: Problem, Q, V, Vhat, dt, tol=1e-10, max_it=10):
     so u_{n+1} = u_3. Returns (NewtonResult of the last stage, Newton updates per stage)."""
     A, _, _ = dirk3_tableau()
     E = prob.mesh.E
-    Un = np.stack([prob.history_weak(e, [V[e]], [1.0]) for e in range(E)])
+    # per-element weak forms: one array [E, Np, m], or (mixed degrees) a list of [Np_e, m] arrays
+    weak = lambda Vs: (lambda L: L if prob.mixed else np.stack(L))(
+        [prob.history_weak(e, [Vs[e]], [1.0]) for e in range(E)])
+    lin = lambda a, X, b, Y: ([a * x + b * y for x, y in zip(X, Y)] if prob.mixed else a * X + b * Y)
+    Un = weak(V)
     ks = []
     cur = NewtonResult(Q, V, Vhat)
     iters = []
     for i in range(3):
         aii = A[i, i]
-        hist = Un / (dt * aii)
+        hist = [u / (dt * aii) for u in Un] if prob.mixed else Un / (dt * aii)
         for j in range(i):
-            hist = hist + (A[i, j] / aii) * ks[j]
+            hist = lin(1.0, hist, A[i, j] / aii, ks[j])
         res = newton_solve(prob, cur.Q, cur.V, cur.Vhat, 1.0 / (dt * aii), hist, tol, max_it)
         iters.append(res.iters)
-        Ui = np.stack([prob.history_weak(e, [res.V[e]], [1.0]) for e in range(E)])
-        k = (Ui - Un) / (dt * aii)
+        Ui = weak(res.V)
+        k = [(u - un) / (dt * aii) for u, un in zip(Ui, Un)] if prob.mixed else (Ui - Un) / (dt * aii)
         for j in range(i):
-            k = k - (A[i, j] / aii) * ks[j]
+            k = lin(1.0, k, -(A[i, j] / aii), ks[j])
         ks.append(k)
         cur = res
     return cur, iters

@@ -1037,11 +1037,10 @@ extern "C" int hdg_dirk3_step(hdg_ctx_t ctx, double* V, double* Vhat, const doub
                               void* stream) {
   HDG_REQUIRE(ctx && V && Vhat && V_n && stage_iters && res_norm && dt > 0.0 && tol > 0.0 && max_newton >= 0,
               "hdg_dirk3_step: invalid argument");
-  HDG_UNIFORM_ONLY(ctx, "hdg_dirk3_step");
   HDG_REQUIRE(precision == HDG_PREC_FP64 || precision == HDG_PREC_MIXED, "hdg_dirk3_step: precision");
   DeviceGuard guard(ctx->device);
   cudaStream_t s = (cudaStream_t)stream;
-  const int64_t n = ctx->E * ctx->NV;
+  const int64_t n = len_V(ctx);
   if (!ctx->d_hist) HDG_CK(cudaMalloc(&ctx->d_hist, sizeof(double) * n));
   if (!ctx->d_dirk) HDG_CK(cudaMalloc(&ctx->d_dirk, sizeof(double) * 4 * n));
   double *Un = ctx->d_dirk, *Ui = Un + n, *K1 = Ui + n, *K2 = K1 + n, *hist = ctx->d_hist;

@@ -183,3 +183,21 @@ def test_mixed_degree_with_symmetric_stabilization():
     worst = _compare(prob, V, Vh, hist, g, res, range(prob.mesh.E))
     for (cls, k), v in worst.items():
         assert v <= (1e-12 if k in ("Rv", "Rt") else 1e-10), (cls, k, v)
+
+
+def test_mixed_degree_dirk3_step_matches_oracle():
+    """One DIRK(3,3) step (Sec. 5's integrator) on a mesh of degrees 1 and 2: the same Newton
+    updates per stage and the same state as the oracle's DIRK step."""
+    import torch
+    from oracle.hdg import dirk3_step
+    prob, V, Vh, _hist, g = _setup(1, (1, 2), 21)
+    hdg, mesh, ctx, info, lay, Vg, Vhg, _histg, pe = g
+    Q = [prob.consistent_q(e, V[e], prob.gather_trace(Vh, e)) for e in range(prob.mesh.E)]
+    dt = 0.05
+    res, iters = dirk3_step(prob, Q, V, Vh, dt, tol=1e-10, max_it=10)
+    V_gpu, Vh_gpu = Vg.clone(), Vhg.clone()
+    its, rn, tr = hdg.hdg_dirk3_step(ctx.handle, V_gpu, Vh_gpu, Vg, dt, hdg.HDG_PREC_FP64, 1e-10, 10)
+    torch.cuda.synchronize()
+    assert list(its) == list(iters), (its, iters)
+    assert rel_fro(V_gpu.cpu().numpy(), np.concatenate([v.ravel() for v in res.V])) < 1e-10
+    assert rel_fro(Vh_gpu.cpu().numpy().reshape(-1), res.Vhat.reshape(-1)) < 1e-10
