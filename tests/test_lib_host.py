@@ -191,3 +191,24 @@ def test_physics_arguments_are_checked():
         with pytest.raises(hdg.HdgError) as ei:
             hdg.hdg_ctx_create(m.handle, 1.4, 0.3, 100.0, 0.72, 0, **kw)
         assert ei.value.code == hdg.HDG_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("dim,p", [(2, 3), (3, 2), (3, 4)])
+def test_layout_of_one_degree_is_the_uniform_stride(dim, p):
+    """For a mesh of one degree the packed layout is the uniform one (also for 3D p = 4, which
+    runs on the element-class kernels): offsets e * nv, e * nt, e * nt^2, ..., faces of degree p
+    with Nf nodes each."""
+    hdg = _lib()
+    m = hdg.Mesh(dim, 2, 0.0, 1.0, p)
+    i, lay = m.info, m.layout()
+    E, F, nv, nt, Nf = i["n_elem"], i["n_faces"], i["nv"], i["nt"], i["Nf"]
+    e = np.arange(E + 1)
+    assert i["mixed"] == 0 and i["p"] == p
+    assert np.array_equal(lay["voff"], e * nv) and np.array_equal(lay["toff"], e * nt)
+    assert np.array_equal(lay["soff"], e * nt * nt) and np.array_equal(lay["roff"], e * (nv * nt + nv))
+    assert np.array_equal(lay["Roff"], e * (nv + nt))
+    assert np.all(lay["elem_p"] == p) and np.all(lay["face_deg"] == p)
+    assert np.array_equal(lay["face_node_off"], np.arange(F + 1) * Nf)
+    assert i["len_S"] == E * nt * nt and i["n_trace_nodes"] == F * Nf
+    assert np.array_equal(m.trace_map(), OMesh(dim, 2, 0.0, 1.0, p).face_of[:, :, None] * Nf
+                          + OMesh(dim, 2, 0.0, 1.0, p).fnode_map)
