@@ -138,6 +138,97 @@ __global__ void __launch_bounds__(128) k_mlp_forward(const float* params, const 
   for (int j = 0; j < NOUT; ++j) y[b * NOUT + j] = out[j];
 }
 
+// Forward on the tensor cores: each warp takes 16 samples, and a layer out = act W^T + b is a
+// 16 x N product over K in steps of 16 (mma.sync m16n8k16, bf16 operands, FP32 accumulation).
+// The FP32 activations enter as two bf16 parts, hi = bf16(a) and lo = bf16(a - hi), which carry
+// them to about 2^-16 relative; the weights are the BF16 copy, exactly as in the scalar kernel.
+HDG_DEVI void mlp_mma(float (&c)[4], const uint4& a, const uint2& b) {
+  asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a.x), "r"(a.y), "r"(a.z), "r"(a.w), "r"(b.x), "r"(b.y));
+}
+
+// the bf16 pairs (x0, x1) of hi and lo parts (x0 in the low half)
+HDG_DEVI void mlp_split2(float x0, float x1, unsigned& hi, unsigned& lo) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+  const float2 hf = __bfloat1622float2(h);
+  const __nv_bfloat162 l = __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
+  hi = *reinterpret_cast<const unsigned*>(&h);
+  lo = *reinterpret_cast<const unsigned*>(&l);
+}
+
+constexpr int kTcLd = MAXH + 4;  // row stride (floats) of a warp's activation tile
+
+// One layer of 16 samples: out[16][N] = f(in[16][K] W^T + b), W [N][K] row-major (bf16, shared).
+// Fragment layout of m16n8k16 (g = lane / 4, t = lane % 4): A rows g, g + 8 at columns 2t, 2t + 1
+// and 2t + 8, 2t + 9 of the k tile; B (col-major) rows 2t, 2t + 1 and 2t + 8, 2t + 9 of column g;
+// C rows g, g + 8 at columns 2t, 2t + 1.
+template <int K, int N, bool TANH>
+HDG_DEVI void mlp_layer_tc(const __nv_bfloat16* W, const __nv_bfloat16* bias, const float* in, float* out,
+                           int lane) {
+  const int g = lane >> 2, t = lane & 3;
+#pragma unroll 1
+  for (int nt = 0; nt < N / 8; ++nt) {
+    float c[4] = {0.f, 0.f, 0.f, 0.f};
+    const __nv_bfloat16* Wn = W + (nt * 8 + g) * K;
+#pragma unroll
+    for (int kt = 0; kt < K / 16; ++kt) {
+      const int k0 = kt * 16 + 2 * t;
+      uint4 hi, lo;
+      mlp_split2(in[g * kTcLd + k0], in[g * kTcLd + k0 + 1], hi.x, lo.x);
+      mlp_split2(in[(g + 8) * kTcLd + k0], in[(g + 8) * kTcLd + k0 + 1], hi.y, lo.y);
+      mlp_split2(in[g * kTcLd + k0 + 8], in[g * kTcLd + k0 + 9], hi.z, lo.z);
+      mlp_split2(in[(g + 8) * kTcLd + k0 + 8], in[(g + 8) * kTcLd + k0 + 9], hi.w, lo.w);
+      uint2 b;
+      b.x = *reinterpret_cast<const unsigned*>(Wn + k0);
+      b.y = *reinterpret_cast<const unsigned*>(Wn + k0 + 8);
+      mlp_mma(c, hi, b);
+      mlp_mma(c, lo, b);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int row = g + 8 * (q >> 1), col = nt * 8 + 2 * t + (q & 1);
+      const float v = c[q] + __bfloat162float(bias[col]);
+      out[row * kTcLd + col] = TANH ? tanhf(v) : v;
+    }
+  }
+  __syncwarp();
+}
+
+template <int NIN, int NH, int NOUT>
+__global__ void __launch_bounds__(64) k_mlp_forward_tc(const float* params, const float* x, int64_t B, float* y) {
+  static_assert(NIN % 16 == 0 && NH % 16 == 0 && NOUT % 8 == 0 && NIN <= MAXH && NH <= MAXH, "tile shape");
+  constexpr int P = NH * NIN + NH + NH * NH + NH + NOUT * NH + NOUT;
+  constexpr int WPB = 2;  // warps per block (static shared memory below 48 KB)
+  __shared__ __align__(16) __nv_bfloat16 w[P + 8];
+  __shared__ float act[WPB][2][16 * kTcLd];
+  const __nv_bfloat16* w16 = reinterpret_cast<const __nv_bfloat16*>(params + 3 * (int64_t)P);
+  for (int t = threadIdx.x; t < P; t += blockDim.x) w[t] = w16[t];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t b0 = ((int64_t)blockIdx.x * WPB + warp) * 16;
+  float* a0 = act[warp][0];
+  float* a1 = act[warp][1];
+  for (int t = lane; t < 16 * NIN; t += 32) {
+    const int r = t / NIN, k = t % NIN;
+    a0[r * kTcLd + k] = b0 + r < B ? x[(b0 + r) * NIN + k] : 0.f;
+  }
+  __syncthreads();
+  const __nv_bfloat16* W1 = w;
+  const __nv_bfloat16* bb1 = W1 + NH * NIN;
+  const __nv_bfloat16* W2 = bb1 + NH;
+  const __nv_bfloat16* bb2 = W2 + NH * NH;
+  const __nv_bfloat16* W3 = bb2 + NH;
+  const __nv_bfloat16* bb3 = W3 + NOUT * NH;
+  mlp_layer_tc<NIN, NH, true>(W1, bb1, a0, a1, lane);
+  mlp_layer_tc<NH, NH, true>(W2, bb2, a1, a0, lane);
+  mlp_layer_tc<NH, NOUT, false>(W3, bb3, a0, a1, lane);
+  for (int t = lane; t < 16 * NOUT; t += 32) {
+    const int r = t / NOUT, j = t % NOUT;
+    if (b0 + r < B) y[(b0 + r) * NOUT + j] = a1[r * kTcLd + j];
+  }
+}
+
 // Forward + backward of the mean-squared error (mean over the batch and the NOUT
 // outputs). A block takes SB samples: one thread per sample runs the forward and
 // back-propagates to the pre-activation gradients, kept in shared memory; then all
@@ -384,8 +475,11 @@ int hdg_mlp_forward(const float* params, int nin, int nh, int nout, const float*
   if (B == 0) return HDG_OK;
   const unsigned g = (unsigned)((B + 127) / 128);
   cudaStream_t s = (cudaStream_t)stream;
-  MLP_DISPATCH(64, 64, 16, (k_mlp_forward<64, 64, 16><<<g, 128, 0, s>>>(params, x, B, y)); HDG_CK(cudaGetLastError());
-               return HDG_OK)
+  // 64-64-16 (2D p = 3) on the tensor cores, 32 samples per block; 48-32-12 keeps the scalar kernel
+  // (its output width is not a multiple of the tile's 8 columns)
+  const unsigned g32 = (unsigned)((B + 31) / 32);
+  MLP_DISPATCH(64, 64, 16, (k_mlp_forward_tc<64, 64, 16><<<g32, 64, 0, s>>>(params, x, B, y));
+               HDG_CK(cudaGetLastError()); return HDG_OK)
   MLP_DISPATCH(48, 32, 12, (k_mlp_forward<48, 32, 12><<<g, 128, 0, s>>>(params, x, B, y)); HDG_CK(cudaGetLastError());
                return HDG_OK)
   set_error("hdg_mlp_forward: network size not compiled in");
