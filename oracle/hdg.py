@@ -346,6 +346,14 @@ class Problem:
             out += c * np.einsum("g,ga,gm->am", T.W, T.phi, u)
         return out
 
+    def source_weak(self, e, s_nodes):
+        """(s_h, phi_a)_K [Np, m] of a source term s of d u/dt + div(F + G) = s, s_h its nodal
+        interpolant (values s_nodes [Np, m] at the element's nodes). The residual takes it with
+        the history: R_v = ... - hist - (s_h, w), i.e. hist + source_weak (the paper's Couette
+        problem, Sec. 5.2, carries such a source; how it is integrated is not stated)."""
+        T = self.tables(e)
+        return np.einsum("g,ga,gm->am", T.W, T.phi, T.phi @ s_nodes)
+
     def entropy_production_terms(self, Q, V):
         """(int rho s, (1/c_v) int (Phi / T + kappa |grad T|^2 / T^2)) of Eq. PiS (Sec. 5.6) with
         Phi = grad V : tau, both from (v_h, q_h) at the volume quadrature points; s = log(p / rho^gamma)

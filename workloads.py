@@ -16,6 +16,7 @@ Sources in the paper:
     isentropic pressure law (checked in tests/test_oracle_convergence.py).
   * Taylor-Green vortex, Sec. 5.5, Eq. (initialCondTGV), with rho0 = V0 = L = 1
     and P0 = 1 / (gamma M0^2) (M0 = V0 / c0).
+  * Couette flow with its source term, Sec. 5.2, with V0 = L = 1 and P0 = 1 / (gamma M0^2).
 """
 from __future__ import annotations
 
@@ -90,6 +91,37 @@ def tgv_field(x: np.ndarray, mach: float, gamma: float = GAMMA):
     p0 = 1.0 / (gamma * mach ** 2)
     p = p0 + (np.cos(2 * X) + np.cos(2 * Y)) * (np.cos(2 * Z) + 2.0) / 16.0
     return rho, vel, p
+
+
+def couette_field(x: np.ndarray, mach: float, prandtl: float = 0.71, alpha: float = 0.8,
+                  beta: float = 0.85, L: float = 1.0, gamma: float = GAMMA):
+    """Steady compressible Couette flow of Sec. 5.2 on (0, L)^2 with V0 = 1, P0 = 1/(gamma M^2)
+    (so T0 = 1 and rho0 = 1 in this nondimensionalisation): V_x = ybar log(1 + ybar), V_y = 0,
+    p = P0, T = alpha + ybar (beta - alpha) + Pr (gamma - 1) M^2 ybar (1 - ybar) / 2 (the paper's
+    V0^2 Pr / (2 c_v gamma) with c_v = 1/(gamma (gamma - 1) M^2)), rho = 1 / T (ideal gas).
+    Accepts complex points (complex-step derivatives of the exact state)."""
+    x = np.asarray(x)
+    yb = x[..., 1] / L
+    T = alpha + yb * (beta - alpha) + 0.5 * prandtl * (gamma - 1.0) * mach ** 2 * yb * (1.0 - yb)
+    vel = np.stack([yb * np.log1p(yb), np.zeros_like(yb)], axis=-1)
+    p = np.full(yb.shape, 1.0 / (gamma * mach ** 2)) + 0.0 * yb
+    return 1.0 / T, vel, p
+
+
+def couette_source(x: np.ndarray, mu: float, L: float = 1.0):
+    """The source s [..., 4] (conservative components) that makes couette_field a steady solution
+    of d u/dt + div(F + G) = s with constant mu, kappa = c_p mu / Pr and Stokes' hypothesis. Only
+    y-derivatives survive: s_momx = -d/dy(mu V_x'), s_energy = -d/dy(mu V_x V_x' + kappa T'), where
+    kappa T'' = -mu / L^2 by the choice of T's quadratic term; this is the source the paper prints
+    for the problem (V0 = 1)."""
+    yb = np.asarray(x)[..., 1] / L
+    lg = np.log1p(yb)
+    d1 = lg + yb / (1.0 + yb)                      # L V_x'
+    d2 = (2.0 + yb) / (1.0 + yb) ** 2              # L^2 V_x''
+    s = np.zeros(yb.shape + (4,), dtype=np.result_type(yb, np.float64))
+    s[..., 1] = -mu / L ** 2 * d2
+    s[..., 3] = -mu / L ** 2 * (d1 * d1 + yb * lg * d2 - 1.0)
+    return s
 
 
 def uniform_noise(shape, seed: int) -> np.ndarray:
