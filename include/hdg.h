@@ -28,7 +28,8 @@
  *     (the library never frees it); all are row-major double unless stated.
  *       V     [E][Np][m]        element nodal entropy variables
  *       Vhat  [F][Nf][m]        trace values at the canonical nodes of each face
- *       hist  [E][Np][m]        BDF history (sum_j c_j (u(v^{n-j}), phi_a)_K), or NULL
+ *       hist  [E][Np][m]        BDF history (sum_j c_j (u(v^{n-j}), phi_a)_K) plus any source
+ *                               term (hdg_add_source), or NULL
  *       S     [E][nt][nt]       condensed trace matrix per element, nt = nF Nf m
  *       g     [E][nt]           condensed right-hand side per element
  *       recov [E][nv*nt + nv]   recovery data X = A^{-1}B (row-major nv x nt) then
@@ -231,6 +232,16 @@ int hdg_prim_to_entropy(hdg_ctx_t ctx, const double* prim, int64_t n_points, dou
  * BDF1: mass_coef = 1/dt, c0 = 1/dt. BDF2: mass_coef = 3/(2dt), c0 = 2/dt, c1 = -1/(2dt). */
 int hdg_history(hdg_ctx_t ctx, const double* V0, const double* V1, double c0, double c1, double* hist,
                 void* stream);
+
+/* Source term of d u/dt + div(F + G) = s (the paper's Couette problem, Sec. 5.2, carries one):
+ * the residual R_v of Eq. hDG_NS1 / hDG1 gains -(s_h, w)_K, s_h the nodal interpolant of s, and
+ * takes it with the history, so this call adds it there:
+ *   hist[e][a][i] += c (s_h, phi_a)_K,   s_h = sum_b src[e][b][i] phi_b.
+ * src [E][Np][m] (device, conservative components at the element nodes, hdg_mesh_copy_coords
+ * gives the nodes), hist [E][Np][m] (device, read and written: call hdg_history first, or zero
+ * it for a steady problem), c a finite scale (1 for the source itself). Meshes of one degree
+ * only (HDG_ERR_UNSUPPORTED on a mesh of mixed degree). Asynchronous on the stream. */
+int hdg_add_source(hdg_ctx_t ctx, const double* src, double c, double* hist, void* stream);
 
 /* Newton linearisation and static condensation of every element (Sec. 3.2-3.3, local
  * elimination): residuals R_v of Eq. hDG_NS1 / hDG1 (time term mass_coef (u(v), w) - hist)

@@ -2,6 +2,7 @@
 // upload, and the Newton-step driver. All numerical work runs in the kernels of
 // assemble_fp64.cu, assemble_mixed.cu and trace.cu.
 #include <algorithm>
+#include <cmath>
 #include <cstdlib>
 #include <cstring>
 #include <string>
@@ -562,6 +563,13 @@ int hdg_history(hdg_ctx_t ctx, const double* V0, const double* V1, double c0, do
   HDG_REQUIRE(ctx && V0 && hist, "hdg_history: invalid argument");
   DeviceGuard guard(ctx->device);
   return hdg::launch_history(ctx, V0, V1, c0, c1, hist, (cudaStream_t)stream);
+}
+
+int hdg_add_source(hdg_ctx_t ctx, const double* src, double c, double* hist, void* stream) {
+  HDG_REQUIRE(ctx && src && hist && std::isfinite(c), "hdg_add_source: invalid argument");
+  HDG_UNIFORM_ONLY(ctx, "hdg_add_source");
+  DeviceGuard guard(ctx->device);
+  return hdg::launch_source_weak(ctx, src, c, hist, (cudaStream_t)stream);
 }
 
 int hdg_assemble_condense(hdg_ctx_t ctx, const double* V, const double* Vhat, const double* hist, double mass_coef,

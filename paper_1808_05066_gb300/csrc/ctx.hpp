@@ -201,6 +201,7 @@ int entropy_terms(hdg_ctx* ctx, const double* V, const double* Vhat, double* acc
 int launch_prim_to_entropy(hdg_ctx* ctx, const double* prim, int64_t n, double* v, cudaStream_t s);
 int launch_history(hdg_ctx* ctx, const double* V0, const double* V1, double c0, double c1, double* hist,
                    cudaStream_t s);
+int launch_source_weak(hdg_ctx* ctx, const double* src, double c, double* hist, cudaStream_t s);
 int launch_trace_matvec(hdg_ctx* ctx, const double* S, const double* x, double* y, double* work, cudaStream_t s,
                         const int* skip = nullptr);
 int launch_trace_rhs(hdg_ctx* ctx, const double* g, double* rhs, cudaStream_t s);

@@ -712,6 +712,30 @@ __global__ void k_dense_solve(const double* K, const int* piv, int64_t n, double
 }  // namespace
 
 // ================================================================ host launchers
+// Source term s of d u/dt + div(F + G) = s given at the element nodes: its nodal interpolant
+// s_h enters R_v as -(s_h, w)_K, which the residual takes with the history, so the kernel adds
+// c (s_h, phi_a)_K = c sum_g W_g |J_e| phi_a(x_g) sum_b phi_b(x_g) s[e][b] to hist[e][a].
+// One CTA per element; the values of s_h at the volume points are staged in shared memory.
+__global__ void k_source_weak(DevTables T, const double* geo, int GEO, int detj_at, int NP, int NG, int M,
+                              const double* src, double c, double* hist) {
+  extern __shared__ double sh[];  // [NG][M]
+  const int64_t e = blockIdx.x;
+  const double w = c * geo[e * GEO + detj_at];
+  for (int t = threadIdx.x; t < NG * M; t += blockDim.x) {
+    const int g = t / M, i = t % M;
+    double s = 0.0;
+    for (int b = 0; b < NP; ++b) s += T.Phi[g * NP + b] * src[(e * NP + b) * M + i];
+    sh[t] = s * T.W[g] * w;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < NP * M; t += blockDim.x) {
+    const int a = t / M, i = t % M;
+    double s = 0.0;
+    for (int g = 0; g < NG; ++g) s += T.Phi[g * NP + a] * sh[g * M + i];
+    hist[e * NP * M + t] += s;
+  }
+}
+
 int launch_prim_to_entropy(hdg_ctx* ctx, const double* prim, int64_t n, double* v, cudaStream_t s) {
   if (n <= 0) return HDG_OK;
   if (ctx->dim == 2)
@@ -732,6 +756,16 @@ int launch_history(hdg_ctx* ctx, const double* V0, const double* V1, double c0, 
   else
     k_history<3><<<(unsigned)ctx->E, 128, sm, s>>>(ctx->T, ctx->d_geo, ctx->GEO, ctx->NP, ctx->NG, V0, V1, c0, c1,
                                                    ctx->ph.gamma, hist);
+  HDG_CK(cudaGetLastError());
+  return HDG_OK;
+}
+
+int launch_source_weak(hdg_ctx* ctx, const double* src, double c, double* hist, cudaStream_t s) {
+  if (ctx->pm) return HDG_ERR_UNSUPPORTED;
+  if (ctx->E <= 0) return HDG_OK;
+  const size_t sm = sizeof(double) * ctx->NG * ctx->M;
+  k_source_weak<<<(unsigned)ctx->E, 128, sm, s>>>(ctx->T, ctx->d_geo, ctx->GEO, ctx->dim * ctx->dim, ctx->NP, ctx->NG,
+                                                  ctx->M, src, c, hist);
   HDG_CK(cudaGetLastError());
   return HDG_OK;
 }

@@ -40,7 +40,7 @@ HDG_ELEM_TIMEOUT = 16
 EXPORTED = [
     "hdg_mesh_create", "hdg_mesh_destroy", "hdg_mesh_get_info", "hdg_mesh_copy_topology",
     "hdg_mesh_copy_coords", "hdg_ctx_create", "hdg_ctx_destroy", "hdg_prim_to_entropy",
-    "hdg_history", "hdg_assemble_condense", "hdg_trace_solve", "hdg_recover_interior",
+    "hdg_history", "hdg_add_source", "hdg_assemble_condense", "hdg_trace_solve", "hdg_recover_interior",
     "hdg_trace_matvec", "hdg_residual_norm", "hdg_newton_step", "hdg_profile_enable",
     "hdg_profile_reset", "hdg_profile_read", "hdg_last_error", "hdg_assemble_condense_noalloc",
     "hdg_mlp_param_count", "hdg_mlp_init", "hdg_mlp_features", "hdg_mlp_forward", "hdg_mlp_gradient",
@@ -115,6 +115,7 @@ def _load():
         "hdg_ctx_destroy": (None, [P]),
         "hdg_prim_to_entropy": (c_int, [P, P, c_int64, P, P]),
         "hdg_history": (c_int, [P, P, P, c_double, c_double, P, P]),
+        "hdg_add_source": (c_int, [P, P, c_double, P, P]),
         "hdg_assemble_condense": (c_int, [P, P, P, P, c_double, c_int, P, P, P, P, P, P]),
         "hdg_trace_solve": (c_int, [P, P, P, P, c_int, c_double, c_int, POINTER(c_int), POINTER(c_double), P]),
         "hdg_recover_interior": (c_int, [P, P, P, P, P]),
@@ -302,6 +303,10 @@ def hdg_prim_to_entropy(ctx, prim, n_points, v, stream=None):
 
 def hdg_history(ctx, V0, V1, c0, c1, hist, stream=None):
     _check(_lib.hdg_history(ctx, _ptr(V0), _ptr(V1), c0, c1, _ptr(hist), _stream(stream)))
+
+
+def hdg_add_source(ctx, src, c, hist, stream=None):
+    _check(_lib.hdg_add_source(ctx, _ptr(src), c, _ptr(hist), _stream(stream)))
 
 
 def hdg_assemble_condense(ctx, V, Vhat, hist, mass_coef, precision, S, g, recov, R, elem_status=None,
