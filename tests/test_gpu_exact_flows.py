@@ -1,8 +1,9 @@
-"""GPU parity of a source term and of a steady Navier-Stokes solve with the oracle: the Couette
-flow of Sec. 5.2 (periodic in x, the exact state on the walls y = 0, 1; Re0 = 0.1, M0 = 0.15).
-hdg_add_source gives the oracle's (s_h, phi_a)_K element by element, and a steady Newton solve
-(no time term, the source as the history) from the interpolated exact state takes the oracle's
-number of updates to its state, in both precisions."""
+"""GPU parity of steady solves of the paper's exact flows with the oracle, in both precisions:
+* the Couette flow of Sec. 5.2 (Navier-Stokes with a source term; periodic in x, the exact
+  state on the walls y = 0, 1; Re0 = 0.1, M0 = 0.15): hdg_add_source gives the oracle's
+  (s_h, phi_a)_K element by element, and a steady Newton solve (no time term, the source as the
+  history) from the interpolated exact state takes the oracle's number of updates to its state;
+* the Ringleb flow of Sec. 5.1 (Euler, the exact state on the whole boundary): the same."""
 import numpy as np
 import pytest
 
@@ -91,3 +92,36 @@ def test_add_source_on_mixed_degrees_is_unsupported():
     with pytest.raises(hdg.HdgError) as ei:
         hdg.hdg_add_source(ctx.handle, buf, 1.0, buf.clone())
     assert ei.value.code == hdg.HDG_ERR_UNSUPPORTED
+
+
+def test_steady_ringleb_newton_matches_oracle():
+    import torch
+    from paper_1808_05066_gb300 import hdg
+    from oracle import physics as ph
+    from oracle.hdg import Problem, interpolate_state, newton_solve
+    from oracle.mesh import Mesh
+    n, p, shift = 4, 2, np.array([-5.0, 1.0])          # the box [0, 4]^2 moved onto (-5, -1) x (1, 5)
+    bc = (("state", "state"), ("state", "state"))
+
+    def prim(x):
+        rho, vel, pr = wl.ringleb_field(np.asarray(x) + shift)
+        return np.concatenate([rho[..., None], vel, pr[..., None]], axis=-1)
+    prob = Problem(Mesh(2, n, 0.0, 4.0, p, bc=[list(b) for b in bc]), ph.Physics(mach=0.5))
+    Vo, Vho = interpolate_state(prob, lambda x: wl.ringleb_field(np.asarray(x) + shift))
+    prob.boundary_state = Vho.copy()
+    res = newton_solve(prob, None, Vo, Vho, 0.0, None, tol=1e-9, max_it=8)   # |R|: 7e-3, 8e-6, 8e-11
+    for precision in (0, 1):
+        mesh = hdg.Mesh(2, n, 0.0, 4.0, p, bc=bc)
+        ctx = hdg.Context(mesh, 1.4, 0.5, 0.0, 0.71, 0)
+        xnode, xfnode, _ = mesh.coords()
+        dev = torch.device("cuda", 0)
+        V = torch.from_numpy(np.ascontiguousarray(prim(xnode))).to(dev)
+        Vh = torch.from_numpy(np.ascontiguousarray(prim(xfnode))).to(dev)
+        hdg.hdg_prim_to_entropy(ctx.handle, V.clone(), V.numel() // 4, V)
+        hdg.hdg_prim_to_entropy(ctx.handle, Vh.clone(), Vh.numel() // 4, Vh)
+        hdg.hdg_ctx_set_boundary_state(ctx.handle, Vh.clone())
+        assert rel_fro(V.cpu().numpy(), Vo) < 1e-14
+        it, rn = hdg.hdg_newton_solve(ctx.handle, V, Vh, None, 0.0, precision, 1e-9, 8)
+        assert it == res.iters >= 1, (precision, it, res.iters)
+        assert rel_fro(V.cpu().numpy(), res.V) < 1e-10
+        assert rel_fro(Vh.cpu().numpy(), res.Vhat) < 1e-10

@@ -17,6 +17,7 @@ Sources in the paper:
   * Taylor-Green vortex, Sec. 5.5, Eq. (initialCondTGV), with rho0 = V0 = L = 1
     and P0 = 1 / (gamma M0^2) (M0 = V0 / c0).
   * Couette flow with its source term, Sec. 5.2, with V0 = L = 1 and P0 = 1 / (gamma M0^2).
+  * Ringleb flow, Sec. 5.1 (the standard hodograph form; the printed one is garbled).
 """
 from __future__ import annotations
 
@@ -122,6 +123,43 @@ def couette_source(x: np.ndarray, mu: float, L: float = 1.0):
     s[..., 1] = -mu / L ** 2 * d2
     s[..., 3] = -mu / L ** 2 * (d1 * d1 + yb * lg * d2 - 1.0)
     return s
+
+
+def _ringleb_J(c):
+    return 1.0 / c + 1.0 / (3.0 * c ** 3) + 1.0 / (5.0 * c ** 5) - 0.5 * np.log((1.0 + c) / (1.0 - c))
+
+
+def ringleb_field(x: np.ndarray, gamma: float = GAMMA):
+    """Ringleb flow (Sec. 5.1), the hodograph solution of the steady Euler equations for
+    gamma = 1.4 (Chiocchia 1985), with rho0 V0^2 = rho E0: at speed q the sound speed is
+    c = sqrt(1 - q^2/5), rho = c^5 and p = rho^gamma / gamma; q solves
+    (x - J/2)^2 + y^2 = 1 / (4 rho^2 q^4),  J = 1/c + 1/(3c^3) + 1/(5c^5) - ln((1+c)/(1-c))/2
+    on the subsonic branch (found by bisection between 0 and the sonic speed sqrt(5/6)), and the
+    flow angle is theta = arcsin(psi q), psi = sqrt(1/(2 q^2) - rho (x - J/2)).
+    The printed forms of the first equation and of J are garbled (a squared A inside the bracket,
+    the bracket not squared, c^2 in J's second term); this is the standard form, which balances
+    the Euler fluxes exactly (tests/test_oracle_ringleb.py)."""
+    x = np.asarray(x, dtype=np.float64)
+    X, Y = x[..., 0], x[..., 1]
+
+    def f(q):
+        c = np.sqrt(1.0 - q * q / 5.0)
+        return (X - 0.5 * _ringleb_J(c)) ** 2 + Y * Y - 1.0 / (4.0 * c ** 10 * q ** 4)
+    lo = np.full(X.shape, 1e-3)
+    hi = np.full(X.shape, math.sqrt(5.0 / 6.0))
+    if np.any(f(lo) >= 0.0) or np.any(f(hi) <= 0.0):
+        raise ValueError("ringleb_field: point outside the subsonic region of the flow")
+    for _ in range(80):
+        mid = 0.5 * (lo + hi)
+        neg = f(mid) < 0.0
+        lo, hi = np.where(neg, mid, lo), np.where(neg, hi, mid)
+    q = 0.5 * (lo + hi)
+    c = np.sqrt(1.0 - q * q / 5.0)
+    rho = c ** 5
+    psi = np.sqrt(1.0 / (2.0 * q * q) - rho * (X - 0.5 * _ringleb_J(c)))
+    th = np.arcsin(psi * q)
+    vel = np.stack([q * np.cos(th), q * np.sin(th)], axis=-1)
+    return rho, vel, rho ** gamma / gamma
 
 
 def uniform_noise(shape, seed: int) -> np.ndarray:
