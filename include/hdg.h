@@ -147,13 +147,16 @@ enum { HDG_BC_PERIODIC = 0, HDG_BC_STATE = 1, HDG_BC_SLIP = 2 };
  *   scheme      trace space of Sec. 3.4: HDG_SCHEME_HDG (one trace per face, Vhat [F][Nf][m]) or
  *               HDG_SCHEME_EDG (a continuous trace, one unknown per skeleton node, Vhat [N][m],
  *               nodes numbered in order of first appearance over (element, local face, face
- *               node)); HDG_SCHEME_IEDG continuous on interior faces only, which on periodic meshes
- *               (every face interior) is EDG. The local problem and the condensation are the
- *               same for all three; only the global trace numbering differs.
+ *               node)); HDG_SCHEME_IEDG continuous on the interior faces, each boundary face with
+ *               nodes of its own (shared with no other face), which on periodic meshes (every
+ *               face interior) is EDG. The local problem and the condensation are the same for
+ *               all three; only the global trace numbering differs.
  *   quad_points K Gauss-Jacobi points per direction, exact to degree 2K-1 (0 selects p+1).
  *   bc          host array [2 dim] of HDG_BC_* per axis (lo side, hi side), or NULL for a fully
  *               periodic mesh; an axis is periodic on both sides or on neither. Bounded meshes
- *               are built for the HDG scheme only (EDG / IEDG: HDG_ERR_UNSUPPORTED).
+ *               are built for the HDG and IEDG schemes (EDG: HDG_ERR_UNSUPPORTED, its boundary
+ *               nodes being shared with interior faces); the boundary state of an IEDG mesh is
+ *               given at its trace nodes like Vhat.
  * Host-only work; the mesh owns host arrays only (freed by hdg_mesh_destroy).
  * Errors: HDG_ERR_INVALID_ARG, HDG_ERR_UNSUPPORTED. */
 int hdg_mesh_create(int dim, const int64_t n[3], const double lo[3], const double hi[3], const int8_t* p_per_elem,
@@ -167,7 +170,7 @@ int hdg_mesh_copy_topology(hdg_mesh_t mesh, int32_t* face_of, int32_t* fnode_map
 /* Host copy of the boundary type of every face, face_bc [F] (HDG_BC_*; 0 for interior faces). */
 int hdg_mesh_copy_face_bc(hdg_mesh_t mesh, int8_t* face_bc);
 /* Global trace node of every local face node, tnode [E][nF][Nf] (host): HDG face * Nf + canonical
- * face node; EDG the skeleton node. The element's trace unknowns are Vhat[tnode][0..m).
+ * face node; EDG / IEDG the skeleton node. The element's trace unknowns are Vhat[tnode][0..m).
  * Mixed degrees: Nf of the largest degree; face_node_off[F] + canonical node, -1 beyond the
  * nodes of the face's own degree. */
 int hdg_mesh_copy_trace_map(hdg_mesh_t mesh, int32_t* tnode);
@@ -196,8 +199,9 @@ int hdg_mesh_copy_coords(hdg_mesh_t mesh, double* xnode, double* xfnode, double*
 int hdg_ctx_create(hdg_mesh_t mesh, const hdg_physics* phys, int device, hdg_ctx_t* out);
 void hdg_ctx_destroy(hdg_ctx_t ctx);
 
-/* The boundary state v_b of the HDG_BC_STATE faces: Vb is a device array in the trace layout
- * [n_faces][Nf][m] (entries of other faces are not read), copied on `stream` into the context
+/* The boundary state v_b of the HDG_BC_STATE faces: Vb is a device array in the trace layout,
+ * [n_faces][Nf][m] (HDG) or [n_trace_nodes][m] (IEDG), of which only the nodes of state faces
+ * are read, copied on `stream` into the context
  * (the caller may free or reuse Vb once the stream passes the copy). Every later assembly reads
  * the copy, so a time-dependent state is set before each step. A mesh with state faces must have
  * its state set before the first assembly (else HDG_ERR_INVALID_ARG there).

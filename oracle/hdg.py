@@ -11,7 +11,7 @@ hDG_NS0-hDG_NS2), with
     (the paper leaves b_h open, Sec. 3.2); two are defined:
       BC_STATE  b_h = vhat - v_b: the trace takes a given boundary state v_b (the paper's
                 prescribed exact solutions, Secs. 5.1-5.2), v_b given by its values at the
-                face nodes (Problem.boundary_state [F, Nf, m]);
+                face nodes (Problem.boundary_state [F, Nf, m], for every trace space);
       BC_SLIP   b_h = fhat(vhat, v; n) + fhat(vhat, R v; -n) (Euler only): the trace residual
                 of an interior face whose other side is the element's mirror image, R
                 reflecting the momentum components, w -> w - 2 (w . n) n; the converged state
@@ -69,9 +69,11 @@ class Problem:
     def __init__(self, mesh: Mesh, phys: ph.Physics, viscous_flux_option: int = 2, scheme: str = "hdg"):
         """viscous_flux_option: 2 = ghat = G(vhat, q) . n (Eq. numericalFluxNS_2, used in all of
         Sec. 5), 1 = ghat = G(v, q) . n (Eq. numericalFluxNS_1).
-        scheme (Sec. 3.4): "hdg" (E^E_h empty: one trace per face, Vhat [F, Nf, m]) or "edg"
-        (E^E_h = all faces: a continuous trace, one unknown per skeleton node, Vhat [N, m]);
-        on these periodic meshes every face is interior, so IEDG is EDG."""
+        scheme (Sec. 3.4): "hdg" (E^E_h empty: one trace per face, Vhat [F, Nf, m]), "edg"
+        (E^E_h = all faces: a continuous trace, one unknown per skeleton node, Vhat [N, m]) or
+        "iedg" (E^E_h = the interior faces: continuous there, one trace per boundary face; on a
+        periodic mesh every face is interior, so IEDG is EDG). The element residual is the same for
+        all three; only the numbering of the trace unknowns differs."""
         if viscous_flux_option not in (1, 2):
             raise ValueError(viscous_flux_option)
         if scheme not in ("hdg", "edg", "iedg"):
@@ -80,8 +82,11 @@ class Problem:
         self.viscous_flux_option = viscous_flux_option
         self.scheme = "edg" if scheme == "iedg" else scheme
         bounded = bool(np.any(mesh.face_bc != BC_PERIODIC))
-        if bounded and self.scheme != "hdg":
-            raise ValueError("boundaries are defined for the HDG trace space only")
+        self.iedg = scheme == "iedg" and bounded
+        if bounded and scheme == "edg":
+            # a boundary node of the continuous EDG trace is shared with interior faces, where the
+            # weak boundary term <vhat - v_b, mu> would be summed with fluxes: not defined here
+            raise ValueError("boundaries are defined for the HDG and IEDG trace spaces")
         if np.any(mesh.face_bc == BC_SLIP) and phys.viscous:
             raise ValueError("the slip boundary is defined for the Euler equations only")
         self.boundary_state = None      # [F, Nf, m] v_b at the canonical face nodes (BC_STATE faces)
@@ -89,7 +94,7 @@ class Problem:
         if self.mixed and self.scheme != "hdg":
             raise ValueError("mixed degrees are built for the HDG trace space")
         if self.scheme == "edg":
-            self.n_edg, self.edg_index = mesh.edg_numbering()
+            self.n_edg, self.edg_index = mesh.edg_numbering(interior_only=self.iedg)
         ref = mesh.ref
         self.d, self.m = mesh.dim, mesh.dim + 2
         self.Np, self.Nf, self.nF = ref.Np, ref.Nf, ref.nF
@@ -446,9 +451,16 @@ def interpolate_state(prob: Problem, prim_fn):
         Vhat = np.zeros(prob.trace_shape)
         Vhat[ids] = V[:, fn, :].reshape(-1, prob.m)[first]
         return V, Vhat
-    owner = np.array([sides[0] for sides in mesh.face_elems])          # [F, 2] (e, f)
-    Vhat = V[owner[:, 0][:, None], fn[owner[:, 1]]]                     # [F, Nf, m]
-    return V, Vhat
+    return V, face_states(prob, V)
+
+
+def face_states(prob: Problem, V):
+    """[F, Nf, m]: the element nodal values V at every face's canonical nodes, taken from the
+    face's first side (one degree): the HDG trace of an interpolated state, and the boundary
+    state v_b (Problem.boundary_state) of the BC_STATE faces of any trace space."""
+    fn = np.array(prob.mesh.ref.face_nodes)
+    owner = np.array([sides[0] for sides in prob.mesh.face_elems])     # [F, 2] (e, f)
+    return V[owner[:, 0][:, None], fn[owner[:, 1]]]
 
 
 def bdf_coefficients(order: int, dt: float):

@@ -271,16 +271,29 @@ class Mesh:
             elem_nodes.append(s)
         return ids, elem_nodes
 
-    def edg_numbering(self):
-        """The continuous trace space of EDG (Sec. 3.4, E^E_h = all faces): one unknown per
-        skeleton node, numbered in order of first appearance over (element, local face, face
-        node). Returns (number of nodes, index [E, nF, Nf] of every local face node)."""
-        ids, _ = self._trace_nodes_edg()
+    def edg_numbering(self, interior_only: bool = False):
+        """The continuous trace spaces of Sec. 3.4: one unknown per skeleton node, numbered in
+        order of first appearance over (element, local face, face node). EDG (E^E_h = all faces):
+        a node is shared by every face through it. IEDG (interior_only; E^E_h = the interior
+        faces): the trace is continuous on the interior faces only, so each node of a face on the
+        boundary is its own unknown, shared with no other face (on a periodic mesh every face is
+        interior and IEDG is EDG). Returns (number of nodes, index [E, nF, Nf] of every local face
+        node)."""
         period = self.n * self.p
+        nF, Nf = self.ref.nF, self.ref.Nf
         fn = np.array(self.ref.face_nodes)                                  # [nF, Nf]
         keys = np.where(self.periodic, self.Nint[:, fn, :] % period, self.Nint[:, fn, :])  # [E, nF, Nf, d]
-        index = np.array([ids[tuple(k)] for k in keys.reshape(-1, self.dim)], dtype=np.int64)
-        return len(ids), index.reshape(self.E, self.ref.nF, self.ref.Nf)
+        ids = {}
+        index = np.zeros((self.E, nF, Nf), dtype=np.int64)
+        for e in range(self.E):
+            for f in range(nF):
+                own = interior_only and self.face_bc[self.face_of[e, f]] != 0
+                for c in range(Nf):
+                    key = ("face", e, f, c) if own else tuple(keys[e, f, c])
+                    if key not in ids:
+                        ids[key] = len(ids)
+                    index[e, f, c] = ids[key]
+        return len(ids), index
 
     def trace_dof_edg(self):
         ids, _ = self._trace_nodes_edg()

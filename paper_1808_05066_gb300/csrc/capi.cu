@@ -139,12 +139,14 @@ int hdg_mesh_create(int dim, const int64_t n[3], const double lo[3], const doubl
       }
     }
   }
-  if (bc && scheme != HDG_SCHEME_HDG)
-    for (int d = 0; d < 2 * dim && d < 6; ++d)
-      if (bc[d] != HDG_BC_PERIODIC) {
-        set_error("hdg_mesh_create: bounded meshes are built for the HDG trace space only");
-        return HDG_ERR_UNSUPPORTED;
-      }
+  bool bounded = false;
+  for (int d = 0; bc && d < 2 * dim && d < 6; ++d) bounded = bounded || bc[d] != HDG_BC_PERIODIC;
+  if (bounded && scheme == HDG_SCHEME_EDG) {
+    // an EDG node on the boundary is shared with interior faces, where the boundary term would be
+    // summed with fluxes: boundaries are defined for the HDG and IEDG trace spaces
+    set_error("hdg_mesh_create: bounded meshes are built for the HDG and IEDG trace spaces");
+    return HDG_ERR_UNSUPPORTED;
+  }
   if (quad_points == 0) quad_points = p + 1;
   auto* m = new hdg_mesh();
   int rc = hdg::build_mesh(dim, n, lo, hi, p, quad_points, m->m, bc);
@@ -154,7 +156,8 @@ int hdg_mesh_create(int dim, const int64_t n[3], const double lo[3], const doubl
     return HDG_ERR_INVALID_ARG;
   }
   m->m.scheme = scheme;
-  if (scheme != HDG_SCHEME_HDG) hdg::build_edg(m->m);  // every face is interior: IEDG is EDG
+  // IEDG differs from EDG only on a bounded mesh (on a periodic one every face is interior)
+  if (scheme != HDG_SCHEME_HDG) hdg::build_edg(m->m, scheme == HDG_SCHEME_IEDG);
   // 3D p = 4 has no uniform kernels: a periodic HDG mesh of that one degree is served by the
   // element-class kernels too (its packed layout is the uniform one)
   bool periodic = true;

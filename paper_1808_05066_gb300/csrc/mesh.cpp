@@ -286,35 +286,46 @@ int build_mesh(int dim, const int64_t n_[3], const double lo_[3], const double h
   return 0;
 }
 
-void build_edg(Mesh& m) {
+void build_edg(Mesh& m, bool interior_only) {
   const RefElement& ref = m.ref;
   const int dim = m.dim, nF = ref.nF, Nf = ref.Nf, Np = ref.Np, p = m.p;
   std::map<V3, int32_t> ids;
+  int32_t next = 0;
   m.edg_index.assign(m.E * nF * Nf, -1);
   m.xedg.clear();
   for (int64_t e = 0; e < m.E; ++e)
-    for (int f = 0; f < nF; ++f)
+    for (int f = 0; f < nF; ++f) {
+      // IEDG: a face on the boundary keeps its own nodes (only one element visits it)
+      const bool own = interior_only && m.face_bc[m.face_of[e * nF + f]] != 0;
       for (int c = 0; c < Nf; ++c) {
         const int a = ref.face_nodes[f][c];
-        V3 key{};
-        for (int r = 0; r < dim; ++r) {  // integer coordinates (units h/p) modulo the period
-          const int64_t* L = &m.lat[(e * nF) * dim];
-          int64_t x = p * L[r];
-          for (int s = 0; s < dim; ++s) x += (L[(s + 1) * dim + r] - L[r]) * ref.idx[a * dim + s];
-          key[r] = pmod(x, p * m.n[r]);
-        }
-        auto it = ids.find(key);
         int32_t id;
-        if (it == ids.end()) {
-          id = (int32_t)ids.size();
-          ids.emplace(key, id);
-          for (int r = 0; r < dim; ++r) m.xedg.push_back(m.xnode[(e * Np + a) * dim + r]);
+        bool fresh = own;
+        if (own) {
+          id = next++;
         } else {
-          id = it->second;
+          V3 key{};
+          for (int r = 0; r < dim; ++r) {  // integer coordinates (units h/p), modulo the period if periodic
+            const int64_t* L = &m.lat[(e * nF) * dim];
+            int64_t x = p * L[r];
+            for (int s = 0; s < dim; ++s) x += (L[(s + 1) * dim + r] - L[r]) * ref.idx[a * dim + s];
+            key[r] = m.bc[r][0] == 0 ? pmod(x, p * m.n[r]) : x;
+          }
+          auto it = ids.find(key);
+          if (it == ids.end()) {
+            id = next++;
+            ids.emplace(key, id);
+            fresh = true;
+          } else {
+            id = it->second;
+          }
         }
+        if (fresh)
+          for (int r = 0; r < dim; ++r) m.xedg.push_back(m.xnode[(e * Np + a) * dim + r]);
         m.edg_index[(e * nF + f) * Nf + c] = id;
       }
-  m.n_edg = (int64_t)ids.size();
+    }
+  m.n_edg = (int64_t)next;
 }
 
 int build_mixed(Mesh& m, const int8_t* pe_in) {

@@ -67,9 +67,11 @@ struct Mesh {
 // (HDG_BC_*), or null for all periodic; an axis is periodic on both sides or on neither.
 int build_mesh(int dim, const int64_t n[3], const double lo[3], const double hi[3], int p, int K, Mesh& m,
                const int32_t* bc = nullptr);
-// The continuous (EDG) numbering of the skeleton nodes of a built mesh: identifies the face
-// nodes of all elements by their integer coordinates modulo the period.
-void build_edg(Mesh& m);
+// The continuous numbering of the skeleton nodes of a built mesh (Sec. 3.4): identifies the face
+// nodes of all elements by their integer coordinates (modulo the period on periodic axes), in
+// order of first appearance over (element, local face, face node). EDG: every face takes part;
+// IEDG (interior_only): the nodes of each boundary face are its own, shared with no other face.
+void build_edg(Mesh& m, bool interior_only);
 // The mixed-degree data of a periodic HDG mesh built with p = the largest degree in pe.
 // Returns 0 on success; -1 on invalid degrees.
 int build_mixed(Mesh& m, const int8_t* pe);

@@ -27,7 +27,7 @@ class Case:
     mass_coef: float = 20.0
     mu_exponent: float = 0.0   # power-law viscosity exponent (0: constant)
     visc_flux: int = 2         # viscous numerical flux option (Eq. numericalFluxNS_1 / _2)
-    scheme: str = "hdg"        # trace space (Sec. 3.4): "hdg" or "edg"
+    scheme: str = "hdg"        # trace space (Sec. 3.4): "hdg", "edg" or "iedg"
     stabilization: str = "slf"  # "slf" (Eq. sLxF) or "s" (Eq. symStab)
     vinf: tuple = (1.0, 0.0)    # free stream of the vortex fields
     psi: float = 5.0            # strength of the single vortex
@@ -56,7 +56,7 @@ def prim_array(case: Case, x):
 # ------------------------------------------------------------------ oracle side
 def oracle_setup(case: Case):
     from oracle import physics as ph
-    from oracle.hdg import Problem, consistent_Q, interpolate_state
+    from oracle.hdg import Problem, consistent_Q, face_states, interpolate_state
     from oracle.mesh import Mesh
     mesh = Mesh(case.dim, case.n, 0.0, case.L, case.p, bc=case.bc)
     phys = ph.Physics(mach=case.mach, reynolds=case.reynolds, prandtl=case.prandtl, mu_exponent=case.mu_exponent,
@@ -64,7 +64,7 @@ def oracle_setup(case: Case):
     prob = Problem(mesh, phys, viscous_flux_option=case.visc_flux, scheme=case.scheme)
     V, Vh = interpolate_state(prob, case.prim)
     if case.bc is not None:
-        prob.boundary_state = Vh.copy()     # the unperturbed trace: the state faces' v_b
+        prob.boundary_state = face_states(prob, V)     # the unperturbed state at the faces' nodes: v_b
     if case.noise:
         Vh = wl.perturb(Vh, case.noise, case.seed)
     Q = consistent_Q(prob, V, Vh)
@@ -85,7 +85,8 @@ class GpuCase:
         from paper_1808_05066_gb300 import hdg
         self.hdg, self.torch, self.case = hdg, torch, case
         self.mesh = hdg.Mesh(case.dim, case.n, 0.0, case.L, case.p,
-                             scheme=hdg.HDG_SCHEME_EDG if case.scheme == "edg" else hdg.HDG_SCHEME_HDG, bc=case.bc)
+                             scheme={"hdg": hdg.HDG_SCHEME_HDG, "edg": hdg.HDG_SCHEME_EDG,
+                                     "iedg": hdg.HDG_SCHEME_IEDG}[case.scheme], bc=case.bc)
         self.ctx = hdg.Context(self.mesh, 1.4, case.mach, case.reynolds, case.prandtl, device,
                                mu_exponent=case.mu_exponent, visc_flux=case.visc_flux,
                                stabilization=1 if case.stabilization == "s" else 0)

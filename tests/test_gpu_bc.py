@@ -1,8 +1,8 @@
 """GPU parity of the boundary terms b_h (Eqs. hDG2 / hDG_NS2; BC_STATE and BC_SLIP) with the
 oracle: the element blocks of bounded meshes (every element with a boundary face, and a few
-interior ones) in both precisions, with sigma_SLF and sigma_S on the slip walls, and BDF1 Newton
-steps (dense and GMRES trace solves) to the oracle's state; the boundary state is read from the
-context's copy and a missing state is an error."""
+interior ones; HDG and IEDG trace spaces) in both precisions, with sigma_SLF and sigma_S on the
+slip walls, and BDF1 Newton steps (dense and GMRES trace solves) to the oracle's state; the
+boundary state is read from the context's copy and a missing state is an error."""
 import dataclasses
 
 import numpy as np
@@ -27,6 +27,11 @@ BC_CASES = {
     "ns2d_state": dataclasses.replace(CASES["ns2d_p3"], bc=(("state", "state"), ("periodic", "periodic"))),
     "ns3d_state": dataclasses.replace(CASES["ns3d_p2"], bc=(("periodic", "periodic"), ("periodic", "periodic"),
                                                              ("state", "state"))),
+    # IEDG (Sec. 3.4): continuous on the interior faces, each boundary face with its own nodes
+    "ns2d_state_iedg": dataclasses.replace(CASES["ns2d_p3"], bc=(("state", "state"), ("periodic", "periodic")),
+                                           scheme="iedg"),
+    "euler2d_state_slip_iedg": dataclasses.replace(CASES["euler2d_p2"], bc=(("state", "state"), ("slip", "slip")),
+                                                   scheme="iedg"),
 }
 
 
@@ -64,7 +69,9 @@ def test_bc_assemble_condense_matches_oracle(name, precision):
 @pytest.mark.parametrize("name,precision,solver", [("euler2d_state_slip", 0, "dense"),
                                                     ("euler2d_state_slip", 1, "gmres"),
                                                     ("euler2d_state_sigma_s", 0, "gmres"),
-                                                    ("ns2d_state", 1, "gmres")])
+                                                    ("ns2d_state", 1, "gmres"),
+                                                    ("euler2d_state_slip_iedg", 0, "dense"),
+                                                    ("ns2d_state_iedg", 1, "gmres")])
 def test_bc_newton_step_matches_oracle(name, precision, solver):
     """One BDF1 step (dt = 0.05) to |R| <= 1e-10 max(1, |R0|): the same number of Newton updates
     and the same state as the oracle's step (dense trace solves)."""
@@ -82,10 +89,11 @@ def test_bc_newton_step_matches_oracle(name, precision, solver):
     assert it == res.iters, (it, res.iters)
     assert rel_fro(V_gpu.cpu().numpy(), res.V) < 1e-10
     assert rel_fro(Vh_gpu.cpu().numpy(), res.Vhat) < 1e-10
-    wall = prob.mesh.face_bc == 1
-    if wall.any():                      # the trace takes the boundary state on the state faces
-        vb = prob.boundary_state[wall]
-        assert np.abs(Vh_gpu.cpu().numpy()[wall] - vb).max() <= 1e-12 * np.abs(vb).max()
+    vh = Vh_gpu.cpu().numpy()
+    for F in np.flatnonzero(prob.mesh.face_bc == 1):   # the trace takes the boundary state on the state faces
+        e, f = prob.mesh.face_elems[F][0]
+        vb = prob.boundary_state[F][prob.mesh.fnode_map[e, f]]
+        assert np.abs(prob.gather_trace(vh, e)[f] - vb).max() <= 1e-12 * np.abs(vb).max()
 
 
 def test_missing_boundary_state_is_an_error():

@@ -3,7 +3,8 @@
   state on the walls y = 0, 1; Re0 = 0.1, M0 = 0.15): hdg_add_source gives the oracle's
   (s_h, phi_a)_K element by element, and a steady Newton solve (no time term, the source as the
   history) from the interpolated exact state takes the oracle's number of updates to its state;
-* the Ringleb flow of Sec. 5.1 (Euler, the exact state on the whole boundary): the same."""
+* the Ringleb flow of Sec. 5.1 (Euler, the exact state on the whole boundary): the same, with
+  the HDG and the IEDG trace spaces."""
 import numpy as np
 import pytest
 
@@ -94,11 +95,12 @@ def test_add_source_on_mixed_degrees_is_unsupported():
     assert ei.value.code == hdg.HDG_ERR_UNSUPPORTED
 
 
-def test_steady_ringleb_newton_matches_oracle():
+@pytest.mark.parametrize("scheme", ["hdg", "iedg"])
+def test_steady_ringleb_newton_matches_oracle(scheme):
     import torch
     from paper_1808_05066_gb300 import hdg
     from oracle import physics as ph
-    from oracle.hdg import Problem, interpolate_state, newton_solve
+    from oracle.hdg import Problem, face_states, interpolate_state, newton_solve
     from oracle.mesh import Mesh
     n, p, shift = 4, 2, np.array([-5.0, 1.0])          # the box [0, 4]^2 moved onto (-5, -1) x (1, 5)
     bc = (("state", "state"), ("state", "state"))
@@ -106,12 +108,13 @@ def test_steady_ringleb_newton_matches_oracle():
     def prim(x):
         rho, vel, pr = wl.ringleb_field(np.asarray(x) + shift)
         return np.concatenate([rho[..., None], vel, pr[..., None]], axis=-1)
-    prob = Problem(Mesh(2, n, 0.0, 4.0, p, bc=[list(b) for b in bc]), ph.Physics(mach=0.5))
+    prob = Problem(Mesh(2, n, 0.0, 4.0, p, bc=[list(b) for b in bc]), ph.Physics(mach=0.5), scheme=scheme)
     Vo, Vho = interpolate_state(prob, lambda x: wl.ringleb_field(np.asarray(x) + shift))
-    prob.boundary_state = Vho.copy()
+    prob.boundary_state = face_states(prob, Vo)
     res = newton_solve(prob, None, Vo, Vho, 0.0, None, tol=1e-9, max_it=8)   # |R|: 7e-3, 8e-6, 8e-11
     for precision in (0, 1):
-        mesh = hdg.Mesh(2, n, 0.0, 4.0, p, bc=bc)
+        mesh = hdg.Mesh(2, n, 0.0, 4.0, p, bc=bc,
+                        scheme=hdg.HDG_SCHEME_IEDG if scheme == "iedg" else hdg.HDG_SCHEME_HDG)
         ctx = hdg.Context(mesh, 1.4, 0.5, 0.0, 0.71, 0)
         xnode, xfnode, _ = mesh.coords()
         dev = torch.device("cuda", 0)
@@ -120,7 +123,7 @@ def test_steady_ringleb_newton_matches_oracle():
         hdg.hdg_prim_to_entropy(ctx.handle, V.clone(), V.numel() // 4, V)
         hdg.hdg_prim_to_entropy(ctx.handle, Vh.clone(), Vh.numel() // 4, Vh)
         hdg.hdg_ctx_set_boundary_state(ctx.handle, Vh.clone())
-        assert rel_fro(V.cpu().numpy(), Vo) < 1e-14
+        assert rel_fro(V.cpu().numpy(), Vo) < 1e-14 and rel_fro(Vh.cpu().numpy(), Vho) < 1e-14
         it, rn = hdg.hdg_newton_solve(ctx.handle, V, Vh, None, 0.0, precision, 1e-9, 8)
         assert it == res.iters >= 1, (precision, it, res.iters)
         assert rel_fro(V.cpu().numpy(), res.V) < 1e-10

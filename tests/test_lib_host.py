@@ -49,7 +49,7 @@ def test_invalid_arguments_are_rejected():
     with pytest.raises(hdg.HdgError) as ei:     # an unknown boundary type
         hdg.hdg_mesh_create(2, [2, 2], [0, 0], [1, 1], 2, bc=[(5, 5), (0, 0)])
     assert ei.value.code == hdg.HDG_ERR_INVALID_ARG
-    with pytest.raises(hdg.HdgError) as ei:     # boundaries are built for the HDG trace space only
+    with pytest.raises(hdg.HdgError) as ei:     # boundaries are built for the HDG and IEDG trace spaces
         hdg.hdg_mesh_create(2, [2, 2], [0, 0], [1, 1], 2, scheme=hdg.HDG_SCHEME_EDG,
                             bc=[("state", "state"), ("periodic", "periodic")])
     assert ei.value.code == hdg.HDG_ERR_UNSUPPORTED
@@ -78,6 +78,29 @@ def test_edg_numbering_matches_oracle(dim, n, p):
     # the HDG trace map is face * Nf + canonical node
     h = hdg.Mesh(dim, n, 0.0, 2.0, p)
     assert np.array_equal(h.trace_map(), o.face_of[:, :, None] * o.ref.Nf + o.fnode_map)
+
+
+@pytest.mark.parametrize("dim,n,p,bc", [(2, 3, 2, [("state", "state"), ("state", "state")]),
+                                        (2, 2, 3, [("periodic", "periodic"), ("state", "state")]),
+                                        (3, 2, 2, [("state", "state"), ("periodic", "periodic"), ("slip", "slip")])])
+def test_iedg_numbering_on_bounded_meshes_matches_oracle(dim, n, p, bc):
+    """On a bounded mesh the C++ IEDG numbering (continuous on the interior faces, each boundary
+    face with nodes of its own) equals the oracle's node for node, and the trace nodes' coordinates
+    are those of the element nodes they copy (up to the period on periodic axes)."""
+    from oracle.hdg import Problem
+    from oracle import physics as ph
+    hdg = _lib()
+    o = OMesh(dim, n, 0.0, 2.0, p, bc=bc)
+    prob = Problem(o, ph.Physics(), scheme="iedg")
+    m = hdg.Mesh(dim, n, 0.0, 2.0, p, scheme=hdg.HDG_SCHEME_IEDG, bc=bc)
+    assert m.info["n_trace_nodes"] == prob.n_edg and m.info["n_trace"] == prob.n_trace
+    tmap = m.trace_map()
+    assert np.array_equal(tmap, prob.edg_index)
+    _, xt, _ = m.coords()
+    fn = np.array(o.ref.face_nodes)
+    d = xt[tmap] - o.xnode[:, fn, :]
+    d = np.where(o.periodic, d - 2.0 * np.round(d / 2.0), d)
+    assert np.abs(d).max() <= 1e-13
 
 
 def test_mixed_degree_variants_that_are_not_built():

@@ -3,7 +3,10 @@ inviscid solution: the steady Ringleb flow of Sec. 5.1 on (-5, -1) x (1, 5), the
 prescribed on the whole boundary (b_h = vhat - v_b), solved by Newton from the interpolated
 exact state (steady: no time term). Its errors are those the paper prints for HDG (Table
 t:RinglebConvergence_HDG, tests/golden/ringleb_hdg_errors.txt) within a factor of 2 (measured:
-k = 1: 0.98 and 0.92 at 1/h = 2 and 4; k = 2: 0.57; k = 3: 0.72) and converge at order k + 1.
+k = 1: 0.98 and 0.92 at 1/h = 2 and 4; k = 2: 0.57; k = 3: 0.72) and converge at order k + 1;
+likewise for IEDG (Table t:RinglebConvergence_IEDG, tests/golden/ringleb_iedg_errors.txt;
+measured: k = 1: 1.15 and 1.18; k = 2: 0.45), whose trace is continuous on the interior faces
+and separate on each boundary face.
 
 The exact field itself (workloads.ringleb_field, the standard hodograph form in place of the
 garbled printed one) is pinned first: the Euler fluxes of the field balance over closed
@@ -15,7 +18,7 @@ import pytest
 
 import workloads as wl
 from oracle import physics as ph
-from oracle.hdg import Problem, interpolate_state, newton_solve
+from oracle.hdg import Problem, face_states, interpolate_state, newton_solve
 from oracle.mesh import BC_STATE, Mesh
 
 GOLDEN = pathlib.Path(__file__).parent / "golden"
@@ -23,9 +26,9 @@ EULER = ph.Physics(mach=0.5)          # the Euler terms do not use the Mach numb
 SHIFT = np.array([-5.0, 1.0])         # the mesh box [0, 4]^2 moved onto (-5, -1) x (1, 5)
 
 
-def _paper_table():
+def _paper_table(scheme="hdg"):
     rows = {}
-    for line in (GOLDEN / "ringleb_hdg_errors.txt").read_text().splitlines():
+    for line in (GOLDEN / f"ringleb_{scheme}_errors.txt").read_text().splitlines():
         if line.strip() and not line.startswith("#"):
             inv_h, *err = line.split()
             for k, v in enumerate(err, start=1):
@@ -37,11 +40,11 @@ def _prim(x):
     return wl.ringleb_field(np.asarray(x) + SHIFT)
 
 
-def ringleb_error(n, p):
+def ringleb_error(n, p, scheme="hdg"):
     mesh = Mesh(2, n, 0.0, 4.0, p, bc=[("state", "state"), ("state", "state")])
-    prob = Problem(mesh, EULER)
+    prob = Problem(mesh, EULER, scheme=scheme)
     V, Vh = interpolate_state(prob, _prim)
-    prob.boundary_state = Vh.copy()
+    prob.boundary_state = face_states(prob, V)
     res = newton_solve(prob, None, V, Vh, 0.0, None, tol=1e-12, max_it=8)
     err = 0.0
     for e in range(mesh.E):
@@ -72,17 +75,23 @@ def test_ringleb_field_balances_the_euler_fluxes(box):
     assert np.abs(total).max() <= 1e-12 * scale * (x1 - x0 + y1 - y0), total
 
 
-@pytest.mark.parametrize("p,n_pair", [(1, (8, 16)), (2, (8,)), (3, (8,))])
-def test_ringleb_matches_the_paper_table(p, n_pair):
-    printed = _paper_table()
+@pytest.mark.parametrize("scheme,p,n_pair", [("hdg", 1, (8, 16)), ("hdg", 2, (8,)), ("hdg", 3, (8,)),
+                                             ("iedg", 1, (8, 16)), ("iedg", 2, (8,))])
+def test_ringleb_matches_the_paper_table(scheme, p, n_pair):
+    printed = _paper_table(scheme)
     errs = []
     for n in n_pair:
-        err, res, prob = ringleb_error(n, p)
+        err, res, prob = ringleb_error(n, p, scheme)
         assert res.res_norms[-1] <= 1e-12 * max(1.0, res.res_norms[0]) and res.iters <= 4
         ratio = err / printed[(p, n // 4)]
-        assert 0.4 < ratio < 2.0, (p, n, err, ratio)
+        assert 1 / 3 < ratio < 2.0, (scheme, p, n, err, ratio)
         errs.append(err)
-        wall = prob.mesh.face_bc == BC_STATE
-        assert np.abs(res.Vhat[wall] - prob.boundary_state[wall]).max() <= 1e-12 * np.abs(res.Vhat).max()
+        # the trace takes the boundary state at the boundary faces' nodes
+        wall = np.flatnonzero(prob.mesh.face_bc == BC_STATE)
+        for F in wall:
+            e, f = prob.mesh.face_elems[F][0]
+            vh = prob.gather_trace(res.Vhat, e)[f]
+            vb = prob.boundary_state[F][prob.mesh.fnode_map[e, f]]
+            assert np.abs(vh - vb).max() <= 1e-12 * np.abs(vb).max()
     if len(errs) == 2:
         assert np.log2(errs[0] / errs[1]) >= p + 0.8          # the paper: 1.95 at 1/h = 2 -> 4
