@@ -11,7 +11,10 @@ hDG_NS0-hDG_NS2), with
     (the paper leaves b_h open, Sec. 3.2); two are defined:
       BC_STATE  b_h = vhat - v_b: the trace takes a given boundary state v_b (the paper's
                 prescribed exact solutions, Secs. 5.1-5.2), v_b given by its values at the
-                face nodes (Problem.boundary_state [F, Nf, m], for every trace space);
+                face nodes (Problem.boundary_state [F, Nf, m], for every trace space); with the
+                continuous EDG trace, whose boundary nodes are shared with interior faces, the
+                state is imposed strongly instead: the assembled equation of a node on a
+                BC_STATE face is vhat - v_b = 0 (assemble_trace, residual_norm);
       BC_SLIP   b_h = fhat(vhat, v; n) + fhat(vhat, R v; -n) (Euler only): the trace residual
                 of an interior face whose other side is the element's mirror image, R
                 reflecting the momentum components, w -> w - 2 (w . n) n; the converged state
@@ -83,10 +86,12 @@ class Problem:
         self.scheme = "edg" if scheme == "iedg" else scheme
         bounded = bool(np.any(mesh.face_bc != BC_PERIODIC))
         self.iedg = scheme == "iedg" and bounded
-        if bounded and scheme == "edg":
-            # a boundary node of the continuous EDG trace is shared with interior faces, where the
-            # weak boundary term <vhat - v_b, mu> would be summed with fluxes: not defined here
-            raise ValueError("boundaries are defined for the HDG and IEDG trace spaces")
+        # EDG on a bounded mesh: a boundary node of the continuous trace is shared with interior
+        # faces, so the given state is imposed strongly there (the node's equation is vhat = v_b,
+        # Problem.dirichlet_rows); the weak term <vhat - v_b, mu> would be summed with fluxes
+        self.edg_dirichlet = scheme == "edg" and bounded
+        if self.edg_dirichlet and np.any(mesh.face_bc == BC_SLIP):
+            raise ValueError("EDG with boundaries: the given state only")
         if np.any(mesh.face_bc == BC_SLIP) and phys.viscous:
             raise ValueError("the slip boundary is defined for the Euler equations only")
         self.boundary_state = None      # [F, Nf, m] v_b at the canonical face nodes (BC_STATE faces)
@@ -107,6 +112,28 @@ class Problem:
         self._dphi = ref.dphi(ref.qp)
         self._phif = [ref.phi(x) for x in ref.fqp_ref]
         self._cache = {}
+
+    def dirichlet_nodes(self):
+        """EDG on a bounded mesh: (trace nodes on BC_STATE faces [K], their v_b [K, m]) from
+        Problem.boundary_state; (None, None) otherwise."""
+        if not self.edg_dirichlet:
+            return None, None
+        vb = {}
+        for F in np.flatnonzero(self.mesh.face_bc == BC_STATE):
+            e, f = self.mesh.face_elems[F][0]
+            for c in range(self.Nf):
+                vb.setdefault(int(self.edg_index[e, f, c]), self.boundary_state[F][self.mesh.fnode_map[e, f, c]])
+        nodes = np.array(sorted(vb), dtype=np.int64)
+        return nodes, np.array([vb[k] for k in nodes])
+
+    def dirichlet_rows(self, Vhat):
+        """(rows of the assembled trace system whose equation is vhat - v_b = 0, vhat - v_b there),
+        or (None, None)."""
+        nodes, vb = self.dirichlet_nodes()
+        if nodes is None:
+            return None, None
+        rows = (nodes[:, None] * self.m + np.arange(self.m)).ravel()
+        return rows, (Vhat[nodes] - vb).ravel()
 
     # -- element sizes (mixed degrees: per element) ----------------------------------------
     def np_e(self, e):
@@ -483,8 +510,9 @@ class NewtonResult:
     iters: int = 0
 
 
-def assemble_trace(prob: Problem, locs):
-    """Assembled trace matrix (sparse CSR) and right-hand side -sum P^T g."""
+def assemble_trace(prob: Problem, locs, Vhat=None):
+    """Assembled trace matrix (sparse CSR) and right-hand side -sum P^T g; on the rows of a
+    strongly imposed state (EDG with boundaries; Vhat required) the identity and v_b - vhat."""
     n = prob.n_trace
     rows, cols, vals = [], [], []
     rhs = np.zeros(n)
@@ -495,6 +523,13 @@ def assemble_trace(prob: Problem, locs):
         vals.append(L["S"].ravel())
         np.add.at(rhs, gi, -L["g"])
     K = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(n, n))
+    drows, dres = prob.dirichlet_rows(Vhat) if prob.edg_dirichlet else (None, None)
+    if drows is not None:
+        keep = np.ones(n)
+        keep[drows] = 0.0
+        K = sp.diags(keep) @ K + sp.diags(1.0 - keep)
+        rhs[drows] = -dres
+        K = K.tocsr()
     return K, rhs
 
 
@@ -504,13 +539,17 @@ def solve_trace(K, rhs, dense_max=12000):
     return spla.spsolve(K.tocsc(), rhs)
 
 
-def residual_norm(prob: Problem, locs):
-    """sqrt(sum_e |R_l,e|^2 + |sum_e P_e^T R_t,e|^2)."""
+def residual_norm(prob: Problem, locs, Vhat=None):
+    """sqrt(sum_e |R_l,e|^2 + |sum_e P_e^T R_t,e|^2), the assembled trace residual being
+    vhat - v_b on the rows of a strongly imposed state (EDG with boundaries; Vhat required)."""
     rt = np.zeros(prob.n_trace)
     s = 0.0
     for e, L in enumerate(locs):
         s += float(L["Rl"] @ L["Rl"])
         np.add.at(rt, prob.trace_index(e), L["Rt"])
+    if prob.edg_dirichlet:
+        drows, dres = prob.dirichlet_rows(Vhat)
+        rt[drows] = dres
     return math.sqrt(s + float(rt @ rt))
 
 
@@ -524,8 +563,8 @@ def newton_iteration(prob: Problem, Q, V, Vhat, mass_coef, hist):
         Qe = None if Q is None else Q[e]
         locs.append(prob.condense(e, Qe, V[e], prob.gather_trace(Vhat, e), mass_coef,
                                   None if hist is None else hist[e]))
-    rn = residual_norm(prob, locs)
-    K, rhs = assemble_trace(prob, locs)
+    rn = residual_norm(prob, locs, Vhat)
+    K, rhs = assemble_trace(prob, locs, Vhat)
     dvh = solve_trace(K, rhs)
     Vhat_new = Vhat + dvh.reshape(Vhat.shape)
     cp = lambda A: [a.copy() for a in A] if isinstance(A, list) else A.copy()

@@ -5,17 +5,18 @@ unknown per skeleton node; IEDG coincides with it on periodic meshes):
 * static condensation + the assembled EDG trace solve + recovery equal one Newton step of the
   monolithic global system (all q, v and the continuous vhat; complex-step Jacobian);
 * the total generalised entropy does not increase on periodic Euler BDF1 steps (Theorem 1);
-and of IEDG on bounded meshes (E^E_h = the interior faces: each boundary face keeps its own
-trace nodes): the count of unknowns in closed form, free stream with the given-state boundary,
-and condensation + trace solve + recovery equal to the monolithic Newton step. EDG on a bounded
-mesh is refused (its boundary nodes are shared with interior faces)."""
+and on bounded meshes: IEDG (E^E_h = the interior faces: each boundary face keeps its own
+trace nodes) with the count of unknowns in closed form, and both IEDG and EDG (whose boundary
+nodes are shared with interior faces, so the given state is imposed strongly there: the node's
+equation is vhat = v_b) with free stream and with condensation + trace solve + recovery equal to
+the monolithic Newton step. EDG with a slip wall is refused."""
 import numpy as np
 import pytest
 
 import workloads as wl
 from oracle import physics as ph
 from oracle.hdg import (Problem, bdf_coefficients, consistent_Q, face_states, interpolate_state, newton_iteration,
-                        time_step)
+                        residual_norm, time_step)
 from oracle.mesh import Mesh
 from test_oracle_hdg import EULER, NS, _global_newton_update
 from test_oracle_refel_mesh import _golden
@@ -113,12 +114,12 @@ def test_iedg_unknowns_on_a_box(n, p):
             mine = set(idx[e, f].tolist())
             others = set(np.delete(idx.reshape(-1, idx.shape[-1]), e * mesh.ref.nF + f, axis=0).ravel().tolist())
             assert len(mine) == mesh.ref.Nf and not mine & others
-    with pytest.raises(ValueError):
-        Problem(mesh, EULER, scheme="edg")
+    with pytest.raises(ValueError):             # EDG with boundaries: the given state only
+        Problem(Mesh(2, n, 0.0, 1.0, p, bc=[("state", "state"), ("slip", "slip")]), EULER, scheme="edg")
 
 
-def _iedg_box(dim, n, p, phys, bc, noise=1e-2):
-    prob = Problem(Mesh(dim, n, 0.0, 4.0, p, bc=bc), phys, scheme="iedg")
+def _iedg_box(dim, n, p, phys, bc, noise=1e-2, scheme="iedg"):
+    prob = Problem(Mesh(dim, n, 0.0, 4.0, p, bc=bc), phys, scheme=scheme)
     if dim == 2:
         field = lambda x: wl.vortex_field(x, [wl.Vortex(2.0, 2.0, 3.0)], phys.mach, vinf=(0.5, 0.2))
     else:
@@ -131,12 +132,13 @@ def _iedg_box(dim, n, p, phys, bc, noise=1e-2):
     return prob, consistent_Q(prob, V, Vh), V, Vh
 
 
+@pytest.mark.parametrize("scheme", ["iedg", "edg"])
 @pytest.mark.parametrize("dim,p,phys,bc", [(2, 2, EULER, BOX2), (2, 2, NS, BOX2),
                                            (3, 1, NS, [("periodic", "periodic"), ("state", "state"),
                                                        ("periodic", "periodic")])])
-def test_iedg_free_stream_with_boundaries(dim, p, phys, bc):
+def test_iedg_free_stream_with_boundaries(dim, p, phys, bc, scheme):
     mesh = Mesh(dim, 2, 0.0, 1.0, p, bc=bc)
-    prob = Problem(mesh, phys, scheme="iedg")
+    prob = Problem(mesh, phys, scheme=scheme)
     u0 = ph.u_of_primitives(np.array(1.1), np.array([0.9, -0.4, 0.3][:dim]),
                             np.array(1 / (1.4 * phys.mach ** 2)), 1.4)
     v0 = ph.v_of_u(u0, 1.4)
@@ -145,17 +147,14 @@ def test_iedg_free_stream_with_boundaries(dim, p, phys, bc):
     prob.boundary_state = face_states(prob, V)
     Q = consistent_Q(prob, V, Vh)
     scale = np.abs(v0).max() * np.abs(u0).max()
-    rt = np.zeros(prob.n_trace)
-    for e in range(mesh.E):
-        Rl, Rt = prob.local_residual(e, None if Q is None else Q[e], V[e], prob.gather_trace(Vh, e))
-        assert np.abs(Rl).max() < 1e-13 * scale
-        np.add.at(rt, prob.trace_index(e), Rt)
-    assert np.abs(rt).max() < 1e-13 * scale
+    locs = [prob.condense(e, None if Q is None else Q[e], V[e], prob.gather_trace(Vh, e)) for e in range(mesh.E)]
+    assert residual_norm(prob, locs, Vh) < 1e-13 * scale
 
 
+@pytest.mark.parametrize("scheme", ["iedg", "edg"])
 @pytest.mark.parametrize("phys", [EULER, NS])
-def test_iedg_condensed_equals_monolithic_with_boundaries(phys):
-    prob, Q, V, Vh = _iedg_box(2, 2, 2, phys, BOX2)
+def test_iedg_condensed_equals_monolithic_with_boundaries(phys, scheme):
+    prob, Q, V, Vh = _iedg_box(2, 2, 2, phys, BOX2, scheme=scheme)
     mass, coefs = bdf_coefficients(1, 0.2)
     hist = np.stack([prob.history_weak(e, [V[e]], coefs) for e in range(prob.mesh.E)])
     Qc, Vc, Vhc, _rn, _dvh, _ = newton_iteration(prob, Q, V, Vh, mass, hist)

@@ -131,6 +131,9 @@ def _global_newton_update(prob, Q, V, Vh, mass, hist):
             Rl = Rv.reshape(-1) if Rq is None else np.concatenate([Rq.reshape(-1), Rv.reshape(-1)])
             out[e * ni:(e + 1) * ni] = Rl
             np.add.at(out, E * ni + prob.trace_index(e), Rt.reshape(-1))
+        if getattr(prob, "edg_dirichlet", False):        # EDG with boundaries: vhat = v_b there
+            nodes, vb = prob.dirichlet_nodes()
+            out[E * ni + (nodes[:, None] * m + np.arange(m)).ravel()] = (Vhz[nodes] - vb).ravel()
         return out
 
     z0 = np.concatenate([np.concatenate([Q[e].ravel(), V[e].ravel()]) if Q is not None else V[e].ravel()

@@ -6,7 +6,9 @@ t:RinglebConvergence_HDG, tests/golden/ringleb_hdg_errors.txt) within a factor o
 k = 1: 0.98 and 0.92 at 1/h = 2 and 4; k = 2: 0.57; k = 3: 0.72) and converge at order k + 1;
 likewise for IEDG (Table t:RinglebConvergence_IEDG, tests/golden/ringleb_iedg_errors.txt;
 measured: k = 1: 1.15 and 1.18; k = 2: 0.45), whose trace is continuous on the interior faces
-and separate on each boundary face.
+and separate on each boundary face, and for EDG (Table t:RinglebConvergence_EDG,
+tests/golden/ringleb_edg_errors.txt; measured: k = 1: 1.32 and 1.43; k = 2: 0.64), whose
+continuous trace takes the state strongly at the boundary nodes.
 
 The exact field itself (workloads.ringleb_field, the standard hodograph form in place of the
 garbled printed one) is pinned first: the Euler fluxes of the field balance over closed
@@ -76,7 +78,8 @@ def test_ringleb_field_balances_the_euler_fluxes(box):
 
 
 @pytest.mark.parametrize("scheme,p,n_pair", [("hdg", 1, (8, 16)), ("hdg", 2, (8,)), ("hdg", 3, (8,)),
-                                             ("iedg", 1, (8, 16)), ("iedg", 2, (8,))])
+                                             ("iedg", 1, (8, 16)), ("iedg", 2, (8,)),
+                                             ("edg", 1, (8, 16)), ("edg", 2, (8,))])
 def test_ringleb_matches_the_paper_table(scheme, p, n_pair):
     printed = _paper_table(scheme)
     errs = []
