@@ -122,7 +122,8 @@ typedef struct {
  * leaves open, Sec. 3.2):
  *   HDG_BC_PERIODIC  the two sides of the axis are identified (no boundary);
  *   HDG_BC_STATE     b_h = vhat - v_b: the trace takes a given boundary state v_b (the prescribed
- *                    exact solutions of Secs. 5.1-5.2), set by hdg_ctx_set_boundary_state;
+ *                    exact solutions of Secs. 5.1-5.2), set by hdg_ctx_set_boundary_state (EDG:
+ *                    imposed strongly at the trace nodes of these faces);
  *   HDG_BC_SLIP      b_h = fhat(vhat, v; n) + fhat(vhat, R v; -n), R reflecting the momentum
  *                    components in the wall: the trace residual of an interior face whose other
  *                    side is the element's mirror image (a slip wall; Euler only). */
@@ -154,9 +155,10 @@ enum { HDG_BC_PERIODIC = 0, HDG_BC_STATE = 1, HDG_BC_SLIP = 2 };
  *   quad_points K Gauss-Jacobi points per direction, exact to degree 2K-1 (0 selects p+1).
  *   bc          host array [2 dim] of HDG_BC_* per axis (lo side, hi side), or NULL for a fully
  *               periodic mesh; an axis is periodic on both sides or on neither. Bounded meshes
- *               are built for the HDG and IEDG schemes (EDG: HDG_ERR_UNSUPPORTED, its boundary
- *               nodes being shared with interior faces); the boundary state of an IEDG mesh is
- *               given at its trace nodes like Vhat.
+ *               are built for all three schemes; the boundary state of an EDG / IEDG mesh is
+ *               given at its trace nodes like Vhat. EDG's boundary nodes are shared with
+ *               interior faces, so there the state is imposed strongly (the node's equation is
+ *               vhat = v_b) and the slip wall is not built (HDG_ERR_UNSUPPORTED).
  * Host-only work; the mesh owns host arrays only (freed by hdg_mesh_destroy).
  * Errors: HDG_ERR_INVALID_ARG, HDG_ERR_UNSUPPORTED. */
 int hdg_mesh_create(int dim, const int64_t n[3], const double lo[3], const double hi[3], const int8_t* p_per_elem,
@@ -200,7 +202,7 @@ int hdg_ctx_create(hdg_mesh_t mesh, const hdg_physics* phys, int device, hdg_ctx
 void hdg_ctx_destroy(hdg_ctx_t ctx);
 
 /* The boundary state v_b of the HDG_BC_STATE faces: Vb is a device array in the trace layout,
- * [n_faces][Nf][m] (HDG) or [n_trace_nodes][m] (IEDG), of which only the nodes of state faces
+ * [n_faces][Nf][m] (HDG) or [n_trace_nodes][m] (EDG / IEDG), of which only the nodes of state faces
  * are read, copied on `stream` into the context
  * (the caller may free or reuse Vb once the stream passes the copy). Every later assembly reads
  * the copy, so a time-dependent state is set before each step. A mesh with state faces must have

@@ -9,6 +9,11 @@
 //                 and v by dual numbers, D on the face's own columns, C over the element's v.
 // One CTA per boundary face of the chunk; the threads of the face points evaluate b_h and its
 // derivatives, then all threads form the integrals against the trace and element bases.
+// EDG on a bounded mesh imposes the state strongly instead, since a boundary node of its
+// continuous trace is shared with interior faces: k_dirichlet_patch clears the R_t, C and D rows
+// of every occurrence of such a node in an element's local trace and gives one occurrence per
+// node the row of vhat - v_b (D = I on its own columns, R_t = vhat - v_b), so the assembled
+// equation of the node is vhat = v_b.
 #include <algorithm>
 
 #include "assemble_fp64.cuh"
@@ -176,21 +181,61 @@ __global__ void __launch_bounds__(128) k_boundary_patch(AssembleArgs a, DevTable
   }
 }
 
+// One CTA per occurrence dir[k] = (e NF + f) NFN + c of a strongly imposed node in the chunk;
+// first[k] != 0 for the one occurrence of each node that carries its equation.
+template <class C, class OutT>
+__global__ void __launch_bounds__(128) k_dirichlet_patch(AssembleArgs a, const int* dir, const int* first,
+                                                         const double* Vb) {
+  constexpr int M = C::M, NFN = C::NFN, NF = C::NF, NV = C::NV, NT = C::NT;
+  const int entry = dir[blockIdx.x];
+  const int64_t e = entry / (NF * NFN);
+  const int r0 = (entry % (NF * NFN)) * M;  // the node's first row in the local trace order
+  if (skip_element(a, e)) return;
+  const int64_t le = e - a.e0;
+  double* Rt = a.R + e * (int64_t)(NV + NT) + NV;
+  OutT* Cr = reinterpret_cast<OutT*>(a.Cp) + (le * NT + r0) * (int64_t)NV;
+  OutT* Dr = reinterpret_cast<OutT*>(a.S + e * (int64_t)NT * NT) + (int64_t)r0 * NT;
+  for (int t = threadIdx.x; t < M * NV; t += blockDim.x) put(Cr, t, 0.0);
+  for (int t = threadIdx.x; t < M * NT; t += blockDim.x) put(Dr, t, 0.0);
+  for (int t = threadIdx.x; t < M; t += blockDim.x) Rt[r0 + t] = 0.0;
+  __syncthreads();
+  if (first[blockIdx.x] && threadIdx.x < M) {
+    const int i = threadIdx.x;
+    const int64_t node = a.tgidx[entry];
+    put(Dr, i * NT + r0 + i, 1.0);
+    Rt[r0 + i] = a.Vhat[node * M + i] - Vb[node * M + i];
+  }
+}
+
+template <class C, class OutT>
+int run_dirichlet(hdg_ctx* ctx, const AssembleArgs& a, cudaStream_t s) {
+  const std::vector<int>& dir = ctx->h_dir;
+  const int per = ctx->NF * ctx->NFN;
+  const int64_t lo = std::lower_bound(dir.begin(), dir.end(), (int)(a.e0 * per)) - dir.begin();
+  const int64_t hi = std::lower_bound(dir.begin(), dir.end(), (int)((a.e0 + a.ne) * per)) - dir.begin();
+  if (hi <= lo) return HDG_OK;
+  k_dirichlet_patch<C, OutT><<<(unsigned)(hi - lo), 128, 0, s>>>(a, ctx->d_dir + lo, ctx->d_dir_first + lo, ctx->d_vb);
+  HDG_CK(cudaGetLastError());
+  return HDG_OK;
+}
+
 template <class C, class OutT>
 int run_patch(hdg_ctx* ctx, const AssembleArgs& a, int64_t lo, int64_t cnt, cudaStream_t s) {
   LaunchScope ls(ctx, HDG_KERNEL_ASSEMBLE, s);
   const int* bf = ctx->d_bface + lo;
   const int* bk = ctx->d_bkind + lo;
-  if constexpr (!C::VISC) {
-    if (ctx->ph.stab == 1) {
-      k_boundary_patch<C, OutT, true><<<(unsigned)cnt, 128, 0, s>>>(a, ctx->T, ctx->ph, bf, bk, ctx->d_vb);
-      HDG_CK(cudaGetLastError());
-      return HDG_OK;
+  if (cnt > 0) {
+    bool sym = false;
+    if constexpr (!C::VISC) sym = ctx->ph.stab == 1;
+    if (sym) {
+      if constexpr (!C::VISC) k_boundary_patch<C, OutT, true><<<(unsigned)cnt, 128, 0, s>>>(a, ctx->T, ctx->ph, bf, bk, ctx->d_vb);
+    } else {
+      k_boundary_patch<C, OutT, false><<<(unsigned)cnt, 128, 0, s>>>(a, ctx->T, ctx->ph, bf, bk, ctx->d_vb);
     }
+    HDG_CK(cudaGetLastError());
   }
-  k_boundary_patch<C, OutT, false><<<(unsigned)cnt, 128, 0, s>>>(a, ctx->T, ctx->ph, bf, bk, ctx->d_vb);
-  HDG_CK(cudaGetLastError());
-  return HDG_OK;
+  // after the boundary term: the strongly imposed nodes of EDG overwrite their rows
+  return ctx->h_dir.empty() ? HDG_OK : run_dirichlet<C, OutT>(ctx, a, s);
 }
 
 }  // namespace
@@ -210,7 +255,7 @@ int boundary_patch(hdg_ctx* ctx, const AssembleArgs& a, int precision, cudaStrea
   const int64_t lo = std::lower_bound(bf.begin(), bf.end(), (int)(a.e0 * ctx->NF)) - bf.begin();
   const int64_t hi = std::lower_bound(bf.begin(), bf.end(), (int)((a.e0 + a.ne) * ctx->NF)) - bf.begin();
   const int64_t cnt = hi - lo;
-  if (cnt <= 0) return HDG_OK;
+  if (cnt <= 0 && ctx->h_dir.empty()) return HDG_OK;
   HDG_PATCH_CASE(2, 1, false)
   HDG_PATCH_CASE(2, 2, false)
   HDG_PATCH_CASE(2, 3, false)

@@ -139,12 +139,12 @@ int hdg_mesh_create(int dim, const int64_t n[3], const double lo[3], const doubl
       }
     }
   }
-  bool bounded = false;
-  for (int d = 0; bc && d < 2 * dim && d < 6; ++d) bounded = bounded || bc[d] != HDG_BC_PERIODIC;
-  if (bounded && scheme == HDG_SCHEME_EDG) {
-    // an EDG node on the boundary is shared with interior faces, where the boundary term would be
-    // summed with fluxes: boundaries are defined for the HDG and IEDG trace spaces
-    set_error("hdg_mesh_create: bounded meshes are built for the HDG and IEDG trace spaces");
+  bool slip = false;
+  for (int d = 0; bc && d < 2 * dim && d < 6; ++d) slip = slip || bc[d] == HDG_BC_SLIP;
+  if (slip && scheme == HDG_SCHEME_EDG) {
+    // an EDG node on the boundary is shared with interior faces: the given state is imposed
+    // strongly there; the slip wall is built for the HDG and IEDG trace spaces
+    set_error("hdg_mesh_create: EDG with boundaries takes the given state (HDG_BC_STATE) only");
     return HDG_ERR_UNSUPPORTED;
   }
   if (quad_points == 0) quad_points = p + 1;
@@ -461,6 +461,26 @@ int hdg_ctx_create(hdg_mesh_t mesh, const hdg_physics* phys, int device, hdg_ctx
     hdg_ctx_destroy(c);
     return rc;
   }
+  if (m.scheme == HDG_SCHEME_EDG && !c->h_bface.empty()) {
+    // the continuous EDG trace takes the state strongly at the nodes of its BC_STATE faces
+    const int per = c->NF * c->NFN;
+    std::vector<char> on_state(m.n_edg, 0), seen(m.n_edg, 0);
+    for (size_t k = 0; k < c->h_bface.size(); ++k)
+      if (bkind[k] == HDG_BC_STATE)
+        for (int cc = 0; cc < c->NFN; ++cc) on_state[m.edg_index[(int64_t)c->h_bface[k] * c->NFN + cc]] = 1;
+    std::vector<int> first;
+    for (int64_t i = 0; i < c->E * per; ++i) {
+      const int32_t node = m.edg_index[i];
+      if (!on_state[node]) continue;
+      c->h_dir.push_back((int)i);
+      first.push_back(seen[node] ? 0 : 1);
+      seen[node] = 1;
+    }
+    if (!c->h_dir.empty() && ((rc = upload(&c->d_dir, c->h_dir)) || (rc = upload(&c->d_dir_first, first)))) {
+      hdg_ctx_destroy(c);
+      return rc;
+    }
+  }
   if ((rc = upload(&c->d_tab, tab)) || (rc = upload(&c->d_itab, itab)) || (rc = upload(&c->d_tgidx, tgidx)) ||
       (rc = upload(&c->d_geo, m.geo)) || (rc = upload(&c->d_fs_elem, fs_elem)) || (rc = upload(&c->d_fs_loc, fs_loc)) ||
       (rc = upload(&c->d_tr_ptr, tr_ptr)) || (rc = upload(&c->d_tr_occ, tr_occ))) {
@@ -489,7 +509,7 @@ void hdg_ctx_destroy(hdg_ctx_t c) {
                   c->d_sw, c->d_pc, c->d_dense, c->d_dpiv, c->d_red, c->d_S,
                   c->d_g, c->d_recov, c->d_R, c->d_dV, c->d_dVh, c->d_status, c->d_hist, c->d_V0,
                   c->d_Vh0, c->d_feat, c->d_pred, c->d_dirk, c->d_ent, c->d_tr_ptr, c->d_tr_occ, c->d_pcn,
-                  c->d_bface, c->d_bkind, c->d_vb, c->d_mv_err, c->d_Sdf};
+                  c->d_bface, c->d_bkind, c->d_vb, c->d_mv_err, c->d_Sdf, c->d_dir, c->d_dir_first};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (c->h_red) cudaFreeHost(c->h_red);

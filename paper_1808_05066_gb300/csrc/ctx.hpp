@@ -32,6 +32,12 @@ struct hdg_ctx {
   std::vector<int> h_bface;
   int* d_bface = nullptr;    // [nb] e NF + f
   int* d_bkind = nullptr;    // [nb] HDG_BC_*
+  // EDG on a bounded mesh: every occurrence (e NF + f) NFN + c, ascending, of a trace node on a
+  // BC_STATE face (the state is imposed strongly there), and which occurrence carries the node's
+  // equation (the first)
+  std::vector<int> h_dir;
+  int* d_dir = nullptr;
+  int* d_dir_first = nullptr;
   bool has_state_bc = false;
   double* d_vb = nullptr;    // [ntrace] (allocated when the state is first set)
   bool vb_set = false;

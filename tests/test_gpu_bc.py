@@ -1,8 +1,9 @@
 """GPU parity of the boundary terms b_h (Eqs. hDG2 / hDG_NS2; BC_STATE and BC_SLIP) with the
 oracle: the element blocks of bounded meshes (every element with a boundary face, and a few
 interior ones; HDG and IEDG trace spaces) in both precisions, with sigma_SLF and sigma_S on the
-slip walls, and BDF1 Newton steps (dense and GMRES trace solves) to the oracle's state; the
-boundary state is read from the context's copy and a missing state is an error."""
+slip walls; EDG's strongly imposed rows; BDF1 Newton steps (dense and GMRES trace solves) to the
+oracle's state on all three trace spaces; the boundary state is read from the context's copy and
+a missing state is an error."""
 import dataclasses
 
 import numpy as np
@@ -32,6 +33,14 @@ BC_CASES = {
                                            scheme="iedg"),
     "euler2d_state_slip_iedg": dataclasses.replace(CASES["euler2d_p2"], bc=(("state", "state"), ("slip", "slip")),
                                                    scheme="iedg"),
+}
+# EDG: the continuous trace takes the state strongly at the nodes of the state faces (their rows
+# of S and g are the identity and vhat - v_b once per node, zero at the node's other occurrences)
+EDG_CASES = {
+    "ns2d_state_edg": dataclasses.replace(CASES["ns2d_p3"], bc=(("state", "state"), ("periodic", "periodic")),
+                                          scheme="edg"),
+    "euler2d_state_edg": dataclasses.replace(CASES["euler2d_p2"], bc=(("state", "state"), ("state", "state")),
+                                             scheme="edg"),
 }
 
 
@@ -66,17 +75,61 @@ def test_bc_assemble_condense_matches_oracle(name, precision):
         assert rel_fro(g[e], L["g"]) < TOL_BLOCK, (e, rel_fro(g[e], L["g"]))
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("name", list(EDG_CASES))
+def test_edg_strong_state_rows_match_oracle(name, precision):
+    """Element blocks of EDG with boundaries: the rows of the trace nodes on state faces are the
+    identity (on the node's first occurrence over (element, local face, face node)) or zero, with
+    g = vhat - v_b there or zero; every other row equals the oracle's condensation."""
+    case = EDG_CASES[name]
+    gc = GpuCase(case)
+    prob, Q, V, Vh = oracle_setup(case)
+    hist_o = oracle_hist(prob, V, case)
+    gc.assemble(gc.history(), precision=precision)
+    assert int(gc.status.abs().sum()) == 0
+    S, g = gc.S.cpu().numpy(), gc.g.cpu().numpy()
+    m = prob.m
+    nodes, vb = prob.dirichlet_nodes()
+    vb_of = dict(zip(nodes.tolist(), vb))
+    flat = prob.edg_index.reshape(-1)
+    _, first_at = np.unique(flat, return_index=True)
+    designated = np.zeros(flat.size, dtype=bool)
+    designated[first_at] = True
+    per = prob.edg_index[0].size
+    elems = sorted({int(k) // per for k in np.flatnonzero(np.isin(flat, nodes))})
+    elems = elems[:: max(1, len(elems) // 16)] + [0, prob.mesh.E // 2]
+    for e in elems:
+        L = prob.condense(e, None if Q is None else Q[e], V[e], prob.gather_trace(Vh, e), case.mass_coef, hist_o[e])
+        loc = prob.edg_index[e].reshape(-1)
+        dir_row = np.repeat(np.isin(loc, nodes), m)
+        keep = ~dir_row
+        if keep.any():
+            assert rel_fro(S[e][keep], L["S"][keep]) < TOL_BLOCK, e
+            assert rel_fro(g[e][keep], L["g"][keep]) < TOL_BLOCK, e
+        for j in np.flatnonzero(np.isin(loc, nodes)):
+            rows = j * m + np.arange(m)
+            expect = np.zeros((m, S.shape[-1]))
+            gexp = np.zeros(m)
+            if designated[e * per + j]:
+                expect[np.arange(m), rows] = 1.0
+                gexp = Vh[loc[j]] - vb_of[int(loc[j])]
+            assert np.array_equal(S[e][rows], expect), (e, j)
+            assert np.abs(g[e][rows] - gexp).max() <= 1e-14 * max(1.0, np.abs(Vh).max()), (e, j)
+
+
 @pytest.mark.parametrize("name,precision,solver", [("euler2d_state_slip", 0, "dense"),
                                                     ("euler2d_state_slip", 1, "gmres"),
                                                     ("euler2d_state_sigma_s", 0, "gmres"),
                                                     ("ns2d_state", 1, "gmres"),
                                                     ("euler2d_state_slip_iedg", 0, "dense"),
-                                                    ("ns2d_state_iedg", 1, "gmres")])
+                                                    ("ns2d_state_iedg", 1, "gmres"),
+                                                    ("euler2d_state_edg", 0, "dense"),
+                                                    ("ns2d_state_edg", 1, "gmres")])
 def test_bc_newton_step_matches_oracle(name, precision, solver):
     """One BDF1 step (dt = 0.05) to |R| <= 1e-10 max(1, |R0|): the same number of Newton updates
     and the same state as the oracle's step (dense trace solves)."""
     from oracle.hdg import time_step
-    case = dataclasses.replace(BC_CASES[name], noise=0.0)
+    case = dataclasses.replace({**BC_CASES, **EDG_CASES}[name], noise=0.0)
     gc = GpuCase(case)
     prob, Q, V, Vh = oracle_setup(case)
     dt = 0.05

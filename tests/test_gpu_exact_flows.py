@@ -4,7 +4,7 @@
   (s_h, phi_a)_K element by element, and a steady Newton solve (no time term, the source as the
   history) from the interpolated exact state takes the oracle's number of updates to its state;
 * the Ringleb flow of Sec. 5.1 (Euler, the exact state on the whole boundary): the same, with
-  the HDG and the IEDG trace spaces."""
+  the HDG, IEDG and EDG trace spaces (EDG: the state imposed strongly at the boundary nodes)."""
 import numpy as np
 import pytest
 
@@ -95,7 +95,7 @@ def test_add_source_on_mixed_degrees_is_unsupported():
     assert ei.value.code == hdg.HDG_ERR_UNSUPPORTED
 
 
-@pytest.mark.parametrize("scheme", ["hdg", "iedg"])
+@pytest.mark.parametrize("scheme", ["hdg", "iedg", "edg"])
 def test_steady_ringleb_newton_matches_oracle(scheme):
     import torch
     from paper_1808_05066_gb300 import hdg
@@ -113,8 +113,8 @@ def test_steady_ringleb_newton_matches_oracle(scheme):
     prob.boundary_state = face_states(prob, Vo)
     res = newton_solve(prob, None, Vo, Vho, 0.0, None, tol=1e-9, max_it=8)   # |R|: 7e-3, 8e-6, 8e-11
     for precision in (0, 1):
-        mesh = hdg.Mesh(2, n, 0.0, 4.0, p, bc=bc,
-                        scheme=hdg.HDG_SCHEME_IEDG if scheme == "iedg" else hdg.HDG_SCHEME_HDG)
+        mesh = hdg.Mesh(2, n, 0.0, 4.0, p, bc=bc, scheme={"hdg": hdg.HDG_SCHEME_HDG, "iedg": hdg.HDG_SCHEME_IEDG,
+                                                          "edg": hdg.HDG_SCHEME_EDG}[scheme])
         ctx = hdg.Context(mesh, 1.4, 0.5, 0.0, 0.71, 0)
         xnode, xfnode, _ = mesh.coords()
         dev = torch.device("cuda", 0)

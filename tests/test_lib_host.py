@@ -49,9 +49,9 @@ def test_invalid_arguments_are_rejected():
     with pytest.raises(hdg.HdgError) as ei:     # an unknown boundary type
         hdg.hdg_mesh_create(2, [2, 2], [0, 0], [1, 1], 2, bc=[(5, 5), (0, 0)])
     assert ei.value.code == hdg.HDG_ERR_INVALID_ARG
-    with pytest.raises(hdg.HdgError) as ei:     # boundaries are built for the HDG and IEDG trace spaces
+    with pytest.raises(hdg.HdgError) as ei:     # EDG with boundaries takes the given state only
         hdg.hdg_mesh_create(2, [2, 2], [0, 0], [1, 1], 2, scheme=hdg.HDG_SCHEME_EDG,
-                            bc=[("state", "state"), ("periodic", "periodic")])
+                            bc=[("state", "state"), ("slip", "slip")])
     assert ei.value.code == hdg.HDG_ERR_UNSUPPORTED
     m = hdg.Mesh(2, 2, 0.0, 1.0, 3, bc=[("slip", "slip"), ("periodic", "periodic")])
     with pytest.raises(hdg.HdgError) as ei:     # the slip wall is defined for the Euler equations only
@@ -80,19 +80,24 @@ def test_edg_numbering_matches_oracle(dim, n, p):
     assert np.array_equal(h.trace_map(), o.face_of[:, :, None] * o.ref.Nf + o.fnode_map)
 
 
-@pytest.mark.parametrize("dim,n,p,bc", [(2, 3, 2, [("state", "state"), ("state", "state")]),
-                                        (2, 2, 3, [("periodic", "periodic"), ("state", "state")]),
-                                        (3, 2, 2, [("state", "state"), ("periodic", "periodic"), ("slip", "slip")])])
-def test_iedg_numbering_on_bounded_meshes_matches_oracle(dim, n, p, bc):
+@pytest.mark.parametrize("dim,n,p,bc,scheme", [(2, 3, 2, [("state", "state"), ("state", "state")], "iedg"),
+                                               (2, 3, 2, [("state", "state"), ("state", "state")], "edg"),
+                                               (2, 2, 3, [("periodic", "periodic"), ("state", "state")], "iedg"),
+                                               (3, 2, 2, [("state", "state"), ("periodic", "periodic"), ("slip", "slip")],
+                                                "iedg"),
+                                               (3, 2, 2, [("state", "state"), ("periodic", "periodic"),
+                                                          ("state", "state")], "edg")])
+def test_iedg_numbering_on_bounded_meshes_matches_oracle(dim, n, p, bc, scheme):
     """On a bounded mesh the C++ IEDG numbering (continuous on the interior faces, each boundary
-    face with nodes of its own) equals the oracle's node for node, and the trace nodes' coordinates
-    are those of the element nodes they copy (up to the period on periodic axes)."""
+    face with nodes of its own) and EDG numbering (continuous everywhere; bounded axes not wrapped)
+    equal the oracle's node for node, and the trace nodes' coordinates are those of the element
+    nodes they copy (up to the period on periodic axes)."""
     from oracle.hdg import Problem
     from oracle import physics as ph
     hdg = _lib()
     o = OMesh(dim, n, 0.0, 2.0, p, bc=bc)
-    prob = Problem(o, ph.Physics(), scheme="iedg")
-    m = hdg.Mesh(dim, n, 0.0, 2.0, p, scheme=hdg.HDG_SCHEME_IEDG, bc=bc)
+    prob = Problem(o, ph.Physics(), scheme=scheme)
+    m = hdg.Mesh(dim, n, 0.0, 2.0, p, scheme=hdg.HDG_SCHEME_IEDG if scheme == "iedg" else hdg.HDG_SCHEME_EDG, bc=bc)
     assert m.info["n_trace_nodes"] == prob.n_edg and m.info["n_trace"] == prob.n_trace
     tmap = m.trace_map()
     assert np.array_equal(tmap, prob.edg_index)
