@@ -151,7 +151,8 @@ enum { HDG_BC_PERIODIC = 0, HDG_BC_STATE = 1, HDG_BC_SLIP = 2 };
  *               node)); HDG_SCHEME_IEDG continuous on the interior faces, each boundary face with
  *               nodes of its own (shared with no other face), which on periodic meshes (every
  *               face interior) is EDG. The local problem and the condensation are the same for
- *               all three; only the global trace numbering differs.
+ *               all three; only the global trace numbering differs (and, on a bounded EDG mesh,
+ *               the strongly imposed state of the boundary nodes, see bc).
  *   quad_points K Gauss-Jacobi points per direction, exact to degree 2K-1 (0 selects p+1).
  *   bc          host array [2 dim] of HDG_BC_* per axis (lo side, hi side), or NULL for a fully
  *               periodic mesh; an axis is periodic on both sides or on neither. Bounded meshes
@@ -202,9 +203,9 @@ int hdg_ctx_create(hdg_mesh_t mesh, const hdg_physics* phys, int device, hdg_ctx
 void hdg_ctx_destroy(hdg_ctx_t ctx);
 
 /* The boundary state v_b of the HDG_BC_STATE faces: Vb is a device array in the trace layout,
- * [n_faces][Nf][m] (HDG) or [n_trace_nodes][m] (EDG / IEDG), of which only the nodes of state faces
- * are read, copied on `stream` into the context
- * (the caller may free or reuse Vb once the stream passes the copy). Every later assembly reads
+ * [n_faces][Nf][m] (HDG) or [n_trace_nodes][m] (EDG / IEDG), of which only the nodes of state
+ * faces are read, copied on `stream` into the context (the caller may free or reuse Vb once
+ * the stream passes the copy). Every later assembly reads
  * the copy, so a time-dependent state is set before each step. A mesh with state faces must have
  * its state set before the first assembly (else HDG_ERR_INVALID_ARG there).
  * Errors: HDG_ERR_INVALID_ARG (null), HDG_ERR_CUDA. */
