@@ -17,7 +17,9 @@
  * A0(vhat) (Eq. sLxF with v* = vhat, the choice of Sec. 5) in the inviscid flux of
  * Eq. numericalFlux and the viscous flux G(vhat, q) . n of Eq. numericalFluxNS_2; hdg_physics
  * selects sigma_S (Eq. symStab), the viscous flux of Eq. numericalFluxNS_1 and a power-law
- * viscosity (Sec. 5.6).
+ * viscosity (Sec. 5.6). Bounded axes take a given boundary state or a slip wall
+ * (hdg_ctx_set_boundary_state), and a source term enters with the time history
+ * (hdg_add_source), as in the steady exact-solution examples of Secs. 5.1-5.2.
  *
  * Conventions shared by all calls
  *   - m = d + 2 state components. Entropy variables (v_1, w_1..w_d, v_m), v_m < 0.
