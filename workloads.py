@@ -2,9 +2,10 @@
 
 This module is shared by the CPU oracle and the GPU path as the single source of
 inputs. It holds no arithmetic of the discretisation: it only evaluates the
-closed-form initial fields in primitive variables (density, velocity, pressure)
-at points the caller supplies, and draws the seeded random numbers (vortex
-positions and strengths, trace perturbations, per-element degrees).
+closed-form fields in primitive variables (density, velocity, pressure) at points
+the caller supplies (initial states, and the exact steady solutions of Secs.
+5.1-5.2 with the Couette flow's source term), and draws the seeded random numbers
+(vortex positions and strengths, trace perturbations, per-element degrees).
 
 Nondimensionalisation: freestream (or reference) density 1, speed 1, length 1,
 so p_inf = 1 / (gamma M^2).
